@@ -1,0 +1,382 @@
+#!/usr/bin/env python
+"""Benchmark of the data-space Hessian hot path on the layered 921x301 workload.
+
+One step = one model update through the whole path on one GPU: Green functions by finite
+differences with the on-the-fly transform (231 receivers, 4000 steps, 26 frequencies 3-8 Hz),
+Gram Hessians + mu, Cholesky factors, and the deblur of all 115 sources' residual gathers.
+
+Prints one JSON line.  `value` is the Hessian build+factor time per update (s, lower is better),
+timed with CUDA events on the stream the library launches on; `deblur_sources_per_s` and the
+per-stage times ride along.  Inputs are device-resident and larger than L2 (the transforms are
+16 GB, the residuals 425 MB), so nothing is flushed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--no-cpu-baseline]
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same workload (its
+Green solves, Gram, factorisation and deblur), extrapolated to a full update.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Hessian build+factor s/update"
+UNIT = "s/update"
+FALLBACK_HBM_GBS = 6800.0
+
+# DRAM traffic of the Green stage per update from the committed ncu capture, valid only for the
+# kernel sources it was taken from (sha256 of csrc/fd.cu); None until a capture exists.
+GREEN_TRAFFIC = {"fd_sha256": None, "bytes_per_update": None}
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--e2e-steps", type=int, default=2)
+    return p.parse_args()
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# ---------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for ln in f:
+                parts = [x.strip() for x in ln.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------------------------
+# distributed plumbing (one process per GPU; each rank runs its own independent update)
+# ---------------------------------------------------------------------------------------------
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+
+        backend = "nccl" if _cuda() else "gloo"
+        dist.init_process_group(backend)
+    return ws, rank, local
+
+
+def _cuda():
+    import torch
+
+    return torch.cuda.is_available()
+
+
+def _barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def _max_over_ranks(ws, x):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], device="cuda" if _cuda() else "cpu", dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------------------------
+# the oracle on a bounded sample (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------------------------
+def oracle_sample(c, green_steps=60, gram_receivers=None, deblur_sources=4):
+    """Times the FP64 oracle on parts of one update and extrapolates to the full update.
+
+    Green: `cores` receivers propagated concurrently (one per thread) for `green_steps` of the
+    nt steps with the 26-frequency transform, scaled by (Nr / cores) x (nt / green_steps).
+    Gram: Hessian of those receivers' transforms, scaled by (Nr / cores)^2.  Cholesky: all 26
+    frequencies of a 231 x 231 Hermitian positive-definite matrix, in full.  Deblur: a few
+    sources at full length, scaled by Ns / sources."""
+    import numpy as np
+
+    import oracle
+
+    cores = os.cpu_count() or 1
+    w = max(1, min(cores, 16))
+    nr, nf, nt = c.rec_ix.size, c.freqs.size, c.nt
+    grid = oracle.Grid(np.float32(c.vel_start).astype(np.float64), c.dz, c.dx, c.nsponge, c.sponge_R)
+    sel = np.linspace(0, nr - 1, w).round().astype(int)
+    t0 = time.perf_counter()
+    gh = oracle.green_dtft(grid, c.rec_iz[sel], c.rec_ix[sel], c.freqs, c.dt, green_steps, workers=w)
+    t_green = (time.perf_counter() - t0) * (nr / w) * (nt / green_steps)
+    t0 = time.perf_counter()
+    oracle.hessian_gram(gh)
+    t_gram = (time.perf_counter() - t0) * (nr / w) ** 2
+    rng = np.random.default_rng(0)
+    A = rng.standard_normal((nf, nr, 2 * nr)) + 1j * rng.standard_normal((nf, nr, 2 * nr))
+    Q = A @ A.conj().transpose(0, 2, 1) + nr * np.eye(nr)
+    t0 = time.perf_counter()
+    L = oracle.cholesky(Q)
+    t_chol = time.perf_counter() - t0
+    ns = c.src_ix.size
+    resid = rng.standard_normal((deblur_sources, nr, nt))
+    t0 = time.perf_counter()
+    oracle.deblur(L, resid, c.freqs, c.dt)
+    t_deb = (time.perf_counter() - t0) * ns / deblur_sources
+    sample = (f"Green: {w} receivers x {green_steps} of {nt} steps (26-frequency transform) scaled "
+              f"x{nr / w:.1f} x{nt / green_steps:.1f}; Gram of those {w} scaled x{(nr / w) ** 2:.0f}; "
+              f"Cholesky of all {nf} frequencies in full; deblur of {deblur_sources} of {ns} sources "
+              f"scaled x{ns / deblur_sources:.1f}")
+    return {"build_factor_s": t_green + t_gram + t_chol, "green_s": t_green, "gram_s": t_gram,
+            "chol_s": t_chol, "deblur_s": t_deb, "sources_per_s": ns / t_deb, "cores": w,
+            "sample": sample}
+
+
+def _workload(c, extra=None):
+    cfg = {"workload": "layered-faulted 921x301 (padded 961x341), dx 10 m, 231 receivers, 115 sources, "
+                       "nt 4000 dt 1 ms, 26 frequencies 3.0:0.2:8.0 Hz, mu 1e-2 mean diag",
+           "nz": c.nz, "nx": c.nx, "nsponge": c.nsponge, "nrec": int(c.rec_ix.size),
+           "nsrc": int(c.src_ix.size), "nt": c.nt, "nfreq": int(c.freqs.size),
+           "l2": "inputs larger than L2 (16 GB transforms, 425 MB residuals); no flush"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+def run_reference(args):
+    import synth
+
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    c = synth.case_layered()
+    for _ in range(args.warmup):
+        oracle_sample(c, green_steps=20, deblur_sources=1)
+    vals, ms = [], []
+    last = None
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        last = oracle_sample(c)
+        ms.append((time.perf_counter() - t0) * 1e3)
+        vals.append(last["build_factor_s"])
+    v = statistics.mean(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(ms),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": _workload(c, {"sample": last["sample"]}),
+        "deblur_sources_per_s": last["sources_per_s"],
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": last["cores"], "kind": "oracle",
+                         "sample": last["sample"]},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2512_16642_gb300 import egh
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    c = synth.case_layered()
+    nr, ns, nt, nf = c.rec_ix.size, c.src_ix.size, c.nt, c.freqs.size
+    ctx = egh.Context(c.nz, c.nx, c.dz, c.dx, c.nsponge, c.sponge_R, c.dt, c.nt, c.rec_iz, c.rec_ix, c.freqs)
+    stream = torch.cuda.current_stream()
+    v_start = torch.from_numpy(np.float32(c.vel_start)).cuda()
+    v_true = torch.from_numpy(np.float32(c.vel_true)).cuda()
+    w32 = synth.ricker(nt, c.dt, c.ricker_hz).astype(np.float32)
+    resid = torch.empty((ns, nr, nt), device="cuda")
+    tmp = torch.empty_like(resid)
+    ctx.forward(v_true, c.src_iz, c.src_ix, w32, resid)
+    ctx.forward(v_start, c.src_iz, c.src_ix, w32, tmp)
+    resid -= tmp
+    del tmp
+    mult = torch.empty_like(resid)
+
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def step(rec=None):
+        e = [ev() for _ in range(4)]
+        e[0].record(stream)
+        ctx.green(v_start)
+        e[1].record(stream)
+        ctx.hessian(egh.EGH_MU_REL_MEANDIAG, c.mu_alpha)
+        ctx.factor()
+        e[2].record(stream)
+        ctx.deblur(resid, mult)
+        e[3].record(stream)
+        if rec is not None:
+            rec.append(e)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    _barrier(ws)
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    l0 = ctx.stats()["kernel_launches"]
+    recs = []
+    t_start, t_end = ev(), ev()
+    t_start.record(stream)
+    for _ in range(args.steps):
+        step(recs)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    _barrier(ws)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    launches = ctx.stats()["kernel_launches"] - l0
+    total_ms = t_start.elapsed_time(t_end)
+    green_ms = [e[0].elapsed_time(e[1]) for e in recs]
+    bf_ms = [e[0].elapsed_time(e[2]) for e in recs]
+    deb_ms = [e[2].elapsed_time(e[3]) for e in recs]
+    bf_s = statistics.mean(bf_ms) / 1e3
+    bf_s_max = _max_over_ranks(ws, bf_s)
+    ms_step = _max_over_ranks(ws, total_ms / args.steps)
+    st = ctx.stats()
+
+    # end to end through the same entry points with pinned host buffers
+    v_host = torch.from_numpy(np.float32(c.vel_start)).pin_memory()
+    r_host = resid.cpu().pin_memory()
+    m_host = torch.empty_like(r_host).pin_memory()
+    e2e_bf, e2e_deb = [], []
+    for i in range(args.e2e_steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.green(v_host)
+        ctx.hessian(egh.EGH_MU_REL_MEANDIAG, c.mu_alpha)
+        ctx.factor()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        ctx.deblur(r_host, m_host)
+        t2 = time.perf_counter()
+        if i > 0:
+            e2e_bf.append(t1 - t0)
+            e2e_deb.append(t2 - t1)
+    e2e_v = _max_over_ranks(ws, statistics.mean(e2e_bf)) / ws
+
+    if rank != 0:
+        return
+    hbm, peak_kind = _peaks()
+    point_steps = st["point_steps"]
+    green_s = statistics.mean(green_ms) / 1e3
+    alg_bytes = 12.0 * point_steps
+    achieved = alg_bytes / green_s / 1e9
+    with open(os.path.join(ROOT, "paper_2512_16642_gb300", "csrc", "fd.cu"), "rb") as f:
+        fd_sha = hashlib.sha256(f.read()).hexdigest()
+    traffic = GREEN_TRAFFIC["bytes_per_update"] if GREEN_TRAFFIC["fd_sha256"] == fd_sha else None
+    line = {
+        "metric": METRIC, "value": bf_s_max / ws, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": _workload(c, {"batch_receivers": st["batch_receivers"], "dft_chunk": st["dft_chunk"],
+                                "gram_splits": st["gram_splits"]}),
+        "stages_ms": {"green": statistics.mean(green_ms), "build_factor": statistics.mean(bf_ms),
+                      "hessian_factor": statistics.mean(bf_ms) - statistics.mean(green_ms),
+                      "deblur": statistics.mean(deb_ms)},
+        "deblur_sources_per_s": ns / (statistics.mean(deb_ms) / 1e3),
+        "roofline": {"kernel": "Green stage: k_fd_step + k_dft_chunk (one egh_green)", "bound": "hbm",
+                     "achieved": achieved, "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": traffic,
+                     "algorithmic_bytes": alg_bytes, "per": "update (12 B per point-step)"},
+        "e2e": {"value": e2e_v, "unit": UNIT,
+                "h2d_bytes_per_step": int(v_host.numel() * 4 + r_host.numel() * 4),
+                "d2h_bytes_per_step": int(m_host.numel() * 4 + 8 + 4 * nf),
+                "deblur_sources_per_s": ns / statistics.mean(e2e_deb),
+                "note": "green from pinned host velocity + hessian + factor; deblur from pinned host "
+                        "residuals to pinned host multipliers"},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline and ws == 1:
+        ob = oracle_sample(c)
+        line["cpu_baseline"] = {"value": ob["build_factor_s"], "unit": UNIT, "cores": ob["cores"],
+                                "kind": "oracle", "sample": ob["sample"],
+                                "deblur_sources_per_s": ob["sources_per_s"]}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

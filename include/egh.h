@@ -1,0 +1,195 @@
+/*
+ * egh.h -- C ABI of the GB300 data-space Hessian library.
+ *
+ * The library builds, factors and applies the frequency-domain data-space
+ * Hessians of multiplier-based extended-source FWI (Sonbolestan & Gholami,
+ * arXiv 2512.16642):
+ *
+ *   Q = S S^T + mu I                                   (eq. Qmatrix)
+ *   delta d^e = Q^{-1} delta d, solved per frequency   (eqs. Qsystem, Qsystemfreq)
+ *
+ * with S = P A(m)^{-1} the forward-modelling operator of the constant-density
+ * acoustic wave equation m u_tt - lap u = delta(x - x_s) f(t) (eq. wave_eq).
+ * Per model update the pipeline is
+ *   egh_green   -> receiver-side Green functions by time-domain finite
+ *                  differences, transformed on the fly at the Nf frequencies;
+ *   egh_hessian -> Q(w_k) = sum_x ghat_i(w_k, x) conj(ghat_j(w_k, x)) + mu I;
+ *   egh_factor  -> Cholesky factors L_k L_k^H = Q(w_k), kept on the device;
+ *   egh_deblur  -> residual gathers of many sources to multipliers: forward
+ *                  transform in time, two triangular solves per frequency,
+ *                  band-limited synthesis back to time.
+ *
+ * Conventions shared by every call:
+ *   - all functions return egh_status; no exception crosses the ABI;
+ *   - arrays are C-contiguous, row-major, last index fastest;
+ *   - complex values are interleaved (re, im) float pairs ("complex64");
+ *   - a pointer documented "host or device" may be either: device memory is
+ *     used in place on the given stream; host memory (pageable or pinned) is
+ *     copied through an internal staging buffer and the call returns after
+ *     its result has reached the host buffer;
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream); device work is ordered on it and the call may return before
+ *     device-only results are complete, except where stated;
+ *   - the caller owns every buffer it passes; the context owns the Green
+ *     function transforms, the Hessians, their factors, the twiddle tables
+ *     and all scratch space until egh_destroy;
+ *   - one context is single-threaded; distinct contexts are independent.
+ *
+ * Time transform convention: X(w) = sum_n x_n exp(-i w n dt).
+ */
+#ifndef EGH_H
+#define EGH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    EGH_OK = 0,
+    EGH_EINVAL = 1,   /* bad argument (message in egh_last_error) */
+    EGH_ENOMEM = 2,   /* device or host allocation failed */
+    EGH_ECUDA = 3,    /* a CUDA runtime call failed */
+    EGH_ENOTPD = 4,   /* a Hessian was not positive definite */
+    EGH_ESTATE = 5,   /* call out of order (create -> green -> hessian -> factor -> deblur) */
+    EGH_ETIMEOUT = 6  /* a bounded device wait ran out */
+} egh_status;
+
+typedef enum {
+    EGH_MU_ABS = 0,          /* mu = mu_param */
+    EGH_MU_REL_MEANDIAG = 1, /* mu = mu_param * mean over k, i of Re H_k[i][i] */
+    EGH_MU_REL_MAXEIG = 2    /* mu = mu_param * max over k of lambda_max(H_k)  (Section
+                                "Numerical examples": a fraction of the largest eigenvalue of S S^T) */
+} egh_mu_mode;
+
+/*
+ * Problem description (Section "Theory"; the discretisation is the library's
+ * reading, the paper does not give one):
+ *   physical grid nz x nx (z down, x fastest) with spacings dz, dx (m);
+ *   an absorbing sponge of nsponge points is padded outside it on all four
+ *   sides (damping eta = eta0 (d/L)^2 per axis, eta0 = 1.5 vmax ln(1/R)/L,
+ *   R = sponge_R); velocity is extended into the pad by edge replication;
+ *   second-order leapfrog in time, eighth-order central differences in space;
+ *   Green functions: impulse of unit amplitude at step 0 at each receiver,
+ *   injected as 1/(dx dz), nt recorded levels n = 0..nt-1 of step dt (s);
+ *   receivers at physical grid points (rec_iz[r], rec_ix[r]);
+ *   nfreq frequencies freq_hz[k] in (0, 1/(2 dt)), arbitrary (not tied to
+ *   an FFT grid).
+ * Host arrays are copied by egh_create.
+ */
+typedef struct {
+    int32_t nz, nx;
+    double dz, dx;
+    int32_t nsponge;
+    double sponge_R;
+    double dt;
+    int32_t nt;
+    int32_t nrec;
+    const int32_t *rec_iz; /* [nrec], host */
+    const int32_t *rec_ix; /* [nrec], host */
+    int32_t nfreq;
+    const double *freq_hz; /* [nfreq], host */
+    int32_t batch_receivers; /* receivers propagated together; 0 = library default */
+    int32_t dft_chunk;       /* time levels per on-the-fly transform chunk; 0 = default */
+    int32_t gram_splits;     /* split of the grid sum in the Gram; 0 = default */
+    int32_t reserved[5];     /* must be zero */
+} egh_config;
+
+typedef struct egh_ctx egh_ctx;
+
+/* Timings (ms, device events) and counters of the last call of each stage. */
+typedef struct {
+    double green_ms, hessian_ms, factor_ms, deblur_ms;
+    int64_t pde_solves;        /* Green-function solves in the last egh_green (= nrec) */
+    int64_t point_steps;       /* padded grid points x time steps x receivers of the last egh_green */
+    int64_t deblur_sources;    /* sources in the last egh_deblur */
+    double mu;                 /* penalty used by the last egh_hessian */
+    int32_t nz_pad, nx_pad;    /* padded grid */
+    int32_t pitch;             /* row pitch (floats) of the device wavefield layout */
+    int32_t batch_receivers, dft_chunk, gram_splits;
+    int64_t kernel_launches;   /* kernels this library has launched since it was loaded (all contexts) */
+} egh_stats;
+
+/* Validates the configuration and allocates the device state on the current
+ * CUDA device.  Rejects (EGH_EINVAL): non-positive sizes or spacings, a
+ * receiver outside the physical grid, a frequency outside (0, 1/(2 dt)),
+ * nonzero reserved fields.  On failure *out is NULL. */
+egh_status egh_create(const egh_config *cfg, egh_ctx **out);
+
+/* Frees everything the context owns.  NULL is a no-op. */
+void egh_destroy(egh_ctx *ctx);
+
+/* Step (a): receiver-side Green functions and their transforms (Section
+ * "Direct Hessian-inverse computation": one PDE solve per receiver with a
+ * Dirac source at the receiver, Algorithm 2 step 2):
+ *   ghat[r][k](x) = sum_{n<nt} g^r(n, x) exp(-i 2 pi f_k n dt)
+ * over the whole padded grid.  vel: [nz][nx] float32 velocity (m/s), host or
+ * device.  EGH_EINVAL if a velocity is not positive and finite or the CFL
+ * number vmax dt sqrt(1/dx^2 + 1/dz^2) exceeds 0.78 (eighth-order leapfrog
+ * limit).  Invalidates any previous Hessian and factors. */
+egh_status egh_green(egh_ctx *ctx, const float *vel, void *stream);
+
+/* Step (b): per-frequency Hessians Q_k = H_k + mu I (eq. Qmatrix) with
+ * H_k[i][j] = sum_x ghat_i conj(ghat_j) (the Gram of G^{ij} = sum_x g^i g^j^T
+ * in the frequency domain; (j, i) = conj(i, j) as in Algorithm 2).  mu comes
+ * from mode/mu_param; mu_out (host, may be NULL) receives it.  Blocks until mu
+ * is known on the host.  Requires egh_green. */
+egh_status egh_hessian(egh_ctx *ctx, egh_mu_mode mode, double mu_param, double *mu_out, void *stream);
+
+/* Step (c): Cholesky factors L_k L_k^H = Q_k of all frequencies in one launch
+ * (Algorithm 2 "Invert each frequency-domain matrix").  Blocks until the
+ * status is known.  EGH_ENOTPD if a pivot is not positive; *bad_freq (host,
+ * may be NULL) receives the first failing frequency index, else -1.
+ * Requires egh_hessian. */
+egh_status egh_factor(egh_ctx *ctx, int32_t *bad_freq, void *stream);
+
+/* Step (d): multipliers delta d^e_s = Q^{-1} delta d_s for ns sources
+ * (eq. Qsystem solved per frequency, Section "Frequency domain inversion"):
+ *   D[k][r][s]  = sum_{t<nt_d} resid[s][r][t] exp(-i 2 pi f_k t dt)
+ *   X_k         = L_k^{-H} L_k^{-1} D_k
+ *   mult[s][r][t] = sum_k w_k Re(X_k[r][s] exp(+i 2 pi f_k t dt)),  t < nt_d,
+ * w_k = 2 df_k dt, df_k = half the distance between neighbouring frequencies
+ * (the full gap at the ends; 1/(nt dt) for a single frequency).
+ * resid, mult: [ns][nrec][nt_d] float32, host or device (both the same kind);
+ * nt_d may differ from the Green record length.  Requires egh_factor. */
+egh_status egh_deblur(egh_ctx *ctx, const float *resid, int32_t ns, int32_t nt_d, float *mult, void *stream);
+
+/* Same solve, returning the frequency-domain multipliers X[k][r][s]
+ * (complex64, [nfreq][nrec][ns]) instead of synthesising them in time.
+ * resid host or device; X device only. */
+egh_status egh_deblur_freq(egh_ctx *ctx, const float *resid, int32_t ns, int32_t nt_d, void *X, void *stream);
+
+/* Auxiliary (residual generation, Algorithm 1 delta d_s = d_s - S b_s):
+ * traces of point sources with signature `wavelet` ([nt] float32, host) at
+ * physical points (src_iz[s], src_ix[s]) (host), recorded at the receivers
+ * for the Green record length nt: data [nsrc][nrec][nt] float32, host or
+ * device.  vel as in egh_green.  Does not change the Hessian state. */
+egh_status egh_forward(egh_ctx *ctx, const float *vel, int32_t nsrc, const int32_t *src_iz,
+                       const int32_t *src_ix, const float *wavelet, float *data, void *stream);
+
+/* Copies the transforms of receivers r0..r0+nr-1 to host_out
+ * ([nr][nfreq][nz+2 nsponge][nx+2 nsponge] complex64).  Blocks. */
+egh_status egh_get_green(egh_ctx *ctx, int32_t r0, int32_t nr, void *host_out);
+
+/* Copies Q_k (factored = 0, Hermitian, both triangles) or L_k (factored = 1,
+ * upper triangle zero) to host_out ([nfreq][nrec][nrec] complex64).  Blocks. */
+egh_status egh_get_hessian(egh_ctx *ctx, int32_t factored, void *host_out);
+
+/* Fills *out with the last timings and counters.  Blocks on pending events. */
+egh_status egh_get_stats(egh_ctx *ctx, egh_stats *out);
+
+/* Message of the last failure on this context (or of the last failed
+ * egh_create when ctx is NULL).  Never NULL. */
+const char *egh_last_error(const egh_ctx *ctx);
+
+/* Short name of a status code. */
+const char *egh_status_string(egh_status s);
+
+/* ABI version: major * 10000 + minor * 100 + patch. */
+int32_t egh_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EGH_H */

@@ -1,0 +1,83 @@
+// Cholesky factorisation of every frequency's Hessian, Q_k = L_k L_k^H, in one launch
+// (Algorithm 2 "Invert each frequency-domain matrix": the Hermitian positive-definite blocks
+// are factored and kept resident instead of inverted).  One block per frequency, right-looking:
+// for each column j the pivot is checked (non-positive or non-finite -> status[k] = j + 1 and the
+// block stops, no trap), the column is scaled and cached in shared memory, and each warp updates
+// whole rows of the trailing lower triangle with coalesced row accesses.  The upper triangle is
+// zeroed at the end.
+#include <cmath>
+
+#include "egh_internal.cuh"
+
+namespace egh {
+
+constexpr int CH_THREADS = 512;
+
+__global__ void __launch_bounds__(CH_THREADS)
+    k_potrf(float2* __restrict__ Lh, int n, int* __restrict__ status) {
+  extern __shared__ float2 col[];  // [n]
+  __shared__ int bad;
+  const int k = blockIdx.x;
+  float2* A = Lh + (long long)k * n * n;
+  const int tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    if (tid == 0) {
+      const float d = A[(long long)j * n + j].x;
+      if (!(d > 0.f) || !isfinite(d)) {
+        bad = j + 1;
+      } else {
+        const float s = sqrtf(d);
+        A[(long long)j * n + j] = make_float2(s, 0.f);
+        col[j] = make_float2(s, 0.f);
+      }
+    }
+    __syncthreads();
+    if (bad) break;
+    const float inv = 1.f / col[j].x;
+    for (int i = j + 1 + tid; i < n; i += blockDim.x) {
+      float2 v = A[(long long)i * n + j];
+      v.x *= inv;
+      v.y *= inv;
+      A[(long long)i * n + j] = v;
+      col[i] = v;
+    }
+    __syncthreads();
+    // A[i][l] -= col[i] * conj(col[l]),  j < l <= i
+    for (int i = j + 1 + warp; i < n; i += nwarps) {
+      const float2 ci = col[i];
+      float2* rowp = A + (long long)i * n;
+      for (int l = j + 1 + lane; l <= i; l += 32) {
+        const float2 cl = col[l];
+        float2 a = rowp[l];
+        a.x -= ci.x * cl.x + ci.y * cl.y;
+        a.y -= ci.y * cl.x - ci.x * cl.y;
+        rowp[l] = a;
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0) status[k] = bad;
+  if (!bad) {
+    for (long long t = tid; t < (long long)n * n; t += blockDim.x) {
+      const int i = (int)(t / n), l = (int)(t % n);
+      if (l > i) A[t] = make_float2(0.f, 0.f);
+    }
+  }
+}
+
+cudaError_t launch_potrf(float2* Lh, int n, int nf, int* status, cudaStream_t st) {
+  const size_t smem = sizeof(float2) * (size_t)n;
+  if (smem > 48 * 1024) {
+    cudaError_t e =
+        cudaFuncSetAttribute(k_potrf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  count_launches(1);
+  k_potrf<<<nf, CH_THREADS, smem, st>>>(Lh, n, status);
+  return cudaGetLastError();
+}
+
+}  // namespace egh

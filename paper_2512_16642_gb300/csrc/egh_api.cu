@@ -1,0 +1,656 @@
+// C ABI of the egh library: context, validation, device memory and the order of launches.
+// Every numerical step runs in the kernels of fd.cu, gram.cu, chol.cu and deblur.cu; this file
+// only validates, allocates, stages host buffers and sequences launches on the caller's stream.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "egh.h"
+#include "egh_internal.cuh"
+
+using namespace egh;
+
+namespace {
+
+// Eighth-order central second derivative (textbook coefficients).
+const double kC8[5] = {-205.0 / 72.0, 8.0 / 5.0, -1.0 / 5.0, 8.0 / 315.0, -1.0 / 560.0};
+// Leapfrog stability bound on vmax dt sqrt(1/dx^2 + 1/dz^2) for that stencil:
+// 2 / sqrt(205/72 + 2 (8/5 + 1/5 + 8/315 + 1/560)) = 0.784; kept with a small margin.
+const double kCflMax = 0.78;
+
+thread_local std::string g_create_error;
+std::atomic<long long> g_launches{0};
+
+enum State { ST_CREATED = 0, ST_GREEN = 1, ST_HESSIAN = 2, ST_FACTORED = 3 };
+
+long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
+
+}  // namespace
+
+namespace egh {
+void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace egh
+
+struct egh_ctx {
+  int dev = 0;
+  int nz = 0, nx = 0, ns = 0, nt = 0, nrec = 0, nf = 0;
+  double dz = 0, dx = 0, R = 0, dt = 0;
+  std::vector<int> rec_iz, rec_ix;
+  std::vector<double> freqs;
+  std::vector<float> wsyn;
+  int B = 0, K = 0, splits = 0;
+  Layout L{};
+  Stencil S{};
+  // device state
+  float *c1 = nullptr, *c3 = nullptr, *ring = nullptr, *gh = nullptr, *part = nullptr;
+  float2 *Qh = nullptr, *Lh = nullptr, *tw = nullptr;
+  int tw_len = 0;
+  float* w_dev = nullptr;
+  int* rec_pts = nullptr;
+  int* status = nullptr;
+  double* dsum = nullptr;
+  double* lmax = nullptr;
+  float* vchk = nullptr;
+  float* vel_stage = nullptr;
+  float2* Dh = nullptr;
+  size_t Dh_cap = 0;
+  float *io_in = nullptr, *io_out = nullptr;
+  size_t io_in_cap = 0, io_out_cap = 0;
+  int state = ST_CREATED;
+  double mu = 0;
+  cudaEvent_t ev[8] = {};
+  bool ev_rec[4] = {false, false, false, false};
+  egh_stats st{};
+  std::string err;
+};
+
+namespace {
+
+egh_status fail(egh_ctx* c, egh_status s, const std::string& msg) {
+  if (c)
+    c->err = msg;
+  else
+    g_create_error = msg;
+  return s;
+}
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(ctx, EGH_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));    \
+  } while (0)
+
+egh_status dalloc(egh_ctx* ctx, void** p, size_t bytes, const char* what) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    char buf[256];
+    snprintf(buf, sizeof buf, "cudaMalloc(%s, %zu bytes): %s", what, bytes, cudaGetErrorString(e));
+    return fail(ctx, e == cudaErrorMemoryAllocation ? EGH_ENOMEM : EGH_ECUDA, buf);
+  }
+  return EGH_OK;
+}
+
+// 1 = device (or managed) memory, 0 = host memory (pinned or pageable).
+int pointer_is_device(const void* p) {
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) ? 1 : 0;
+}
+
+// exp(-i 2 pi f_k n dt) for n < len, phase reduced as 2 pi frac(f_k n dt) in double precision.
+std::vector<float2> twiddle_table(const std::vector<double>& f, double dt, int len) {
+  std::vector<float2> t((size_t)len * f.size());
+  for (int n = 0; n < len; ++n)
+    for (size_t k = 0; k < f.size(); ++k) {
+      double ph = f[k] * (double)n * dt;
+      ph -= std::floor(ph);
+      const double a = 2.0 * M_PI * ph;
+      t[(size_t)n * f.size() + k] = make_float2((float)std::cos(a), (float)-std::sin(a));
+    }
+  return t;
+}
+
+egh_status ensure_twiddles(egh_ctx* ctx, int len, cudaStream_t stream) {
+  if (len <= ctx->tw_len) return EGH_OK;
+  std::vector<float2> h = twiddle_table(ctx->freqs, ctx->dt, len);
+  CK(cudaStreamSynchronize(stream));
+  if (ctx->tw) CK(cudaFree(ctx->tw));
+  ctx->tw = nullptr;
+  ctx->tw_len = 0;
+  egh_status s = dalloc(ctx, (void**)&ctx->tw, h.size() * sizeof(float2), "twiddles");
+  if (s) return s;
+  CK(cudaMemcpy(ctx->tw, h.data(), h.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  ctx->tw_len = len;
+  return EGH_OK;
+}
+
+egh_status ensure_buf(egh_ctx* ctx, void** p, size_t* cap, size_t bytes, cudaStream_t stream,
+                      const char* what) {
+  if (bytes <= *cap) return EGH_OK;
+  CK(cudaStreamSynchronize(stream));
+  if (*p) CK(cudaFree(*p));
+  *p = nullptr;
+  *cap = 0;
+  egh_status s = dalloc(ctx, p, bytes, what);
+  if (s) return s;
+  *cap = bytes;
+  return EGH_OK;
+}
+
+// Velocity validation (positive, finite, CFL) and coefficient build; returns the device pointer
+// of the velocity actually used (the caller's, or the staging copy of a host array).
+egh_status prepare_model(egh_ctx* ctx, const float* vel, cudaStream_t stream) {
+  if (!vel) return fail(ctx, EGH_EINVAL, "velocity pointer is NULL");
+  const long long n = (long long)ctx->nz * ctx->nx;
+  const float* dv = vel;
+  if (!pointer_is_device(vel)) {
+    CK(cudaMemcpyAsync(ctx->vel_stage, vel, n * sizeof(float), cudaMemcpyHostToDevice, stream));
+    dv = ctx->vel_stage;
+  }
+  CK(launch_check_velocity(dv, n, ctx->vchk, stream));
+  float h[2];
+  CK(cudaMemcpyAsync(h, ctx->vchk, sizeof h, cudaMemcpyDeviceToHost, stream));
+  CK(cudaStreamSynchronize(stream));
+  if (h[1] != 0.f) return fail(ctx, EGH_EINVAL, "velocity has non-positive or non-finite values");
+  const double cfl = h[0] * ctx->dt * std::sqrt(1.0 / (ctx->dx * ctx->dx) + 1.0 / (ctx->dz * ctx->dz));
+  if (cfl > kCflMax) {
+    char buf[160];
+    snprintf(buf, sizeof buf, "CFL number %.4f exceeds %.2f (vmax %.1f m/s)", cfl, kCflMax, h[0]);
+    return fail(ctx, EGH_EINVAL, buf);
+  }
+  CK(launch_build_coef(dv, ctx->L, ctx->dz, ctx->dx, ctx->dt, ctx->R, ctx->vchk, ctx->c1, ctx->c3,
+                       stream));
+  return EGH_OK;
+}
+
+float* slot(egh_ctx* ctx, int t) { return ctx->ring + (long long)(t % ctx->K) * ctx->B * ctx->L.F; }
+
+void free_all(egh_ctx* c) {
+  void* ptrs[] = {c->c1, c->c3, c->ring, c->gh, c->part, c->Qh, c->Lh, c->tw, c->w_dev,
+                  c->rec_pts, c->status, c->dsum, c->lmax, c->vchk, c->vel_stage, c->Dh,
+                  c->io_in, c->io_out};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  for (cudaEvent_t& e : c->ev)
+    if (e) cudaEventDestroy(e);
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t egh_version(void) { return 10000; }
+
+const char* egh_status_string(egh_status s) {
+  switch (s) {
+    case EGH_OK: return "EGH_OK";
+    case EGH_EINVAL: return "EGH_EINVAL";
+    case EGH_ENOMEM: return "EGH_ENOMEM";
+    case EGH_ECUDA: return "EGH_ECUDA";
+    case EGH_ENOTPD: return "EGH_ENOTPD";
+    case EGH_ESTATE: return "EGH_ESTATE";
+    case EGH_ETIMEOUT: return "EGH_ETIMEOUT";
+  }
+  return "EGH_UNKNOWN";
+}
+
+const char* egh_last_error(const egh_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+egh_status egh_create(const egh_config* cfg, egh_ctx** out) {
+  egh_ctx* ctx = nullptr;
+  if (!out) return fail(nullptr, EGH_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!cfg) return fail(nullptr, EGH_EINVAL, "config is NULL");
+  const egh_config& c = *cfg;
+  for (int v : c.reserved)
+    if (v != 0) return fail(nullptr, EGH_EINVAL, "reserved config fields must be zero");
+  if (c.nz < 1 || c.nx < 1) return fail(nullptr, EGH_EINVAL, "nz and nx must be >= 1");
+  if (!(c.dz > 0) || !(c.dx > 0)) return fail(nullptr, EGH_EINVAL, "dz and dx must be > 0");
+  if (c.nsponge < 0) return fail(nullptr, EGH_EINVAL, "nsponge must be >= 0");
+  if (c.nsponge > 0 && !(c.sponge_R > 0 && c.sponge_R < 1))
+    return fail(nullptr, EGH_EINVAL, "sponge_R must be in (0, 1)");
+  if (!(c.dt > 0)) return fail(nullptr, EGH_EINVAL, "dt must be > 0");
+  if (c.nt < 1) return fail(nullptr, EGH_EINVAL, "nt must be >= 1");
+  if (c.nrec < 1 || !c.rec_iz || !c.rec_ix) return fail(nullptr, EGH_EINVAL, "need >= 1 receiver");
+  if (c.nfreq < 1 || c.nfreq > 64 || !c.freq_hz)
+    return fail(nullptr, EGH_EINVAL, "nfreq must be in 1..64");
+  for (int r = 0; r < c.nrec; ++r)
+    if (c.rec_iz[r] < 0 || c.rec_iz[r] >= c.nz || c.rec_ix[r] < 0 || c.rec_ix[r] >= c.nx)
+      return fail(nullptr, EGH_EINVAL, "receiver outside the physical grid");
+  for (int k = 0; k < c.nfreq; ++k)
+    if (!(c.freq_hz[k] > 0) || !(c.freq_hz[k] < 0.5 / c.dt))
+      return fail(nullptr, EGH_EINVAL, "frequency outside (0, 1/(2 dt))");
+  if (c.batch_receivers < 0 || c.gram_splits < 0)
+    return fail(nullptr, EGH_EINVAL, "batch_receivers and gram_splits must be >= 0");
+  if (c.dft_chunk != 0 && c.dft_chunk != 16 && c.dft_chunk != 32)
+    return fail(nullptr, EGH_EINVAL, "dft_chunk must be 0, 16 or 32");
+
+  ctx = new (std::nothrow) egh_ctx();
+  if (!ctx) return fail(nullptr, EGH_ENOMEM, "host allocation failed");
+  cudaGetDevice(&ctx->dev);
+  ctx->nz = c.nz; ctx->nx = c.nx; ctx->ns = c.nsponge; ctx->nt = c.nt; ctx->nrec = c.nrec;
+  ctx->nf = c.nfreq; ctx->dz = c.dz; ctx->dx = c.dx; ctx->R = c.nsponge > 0 ? c.sponge_R : 0.5;
+  ctx->dt = c.dt;
+  ctx->rec_iz.assign(c.rec_iz, c.rec_iz + c.nrec);
+  ctx->rec_ix.assign(c.rec_ix, c.rec_ix + c.nrec);
+  ctx->freqs.assign(c.freq_hz, c.freq_hz + c.nfreq);
+  ctx->B = c.batch_receivers ? std::min(c.batch_receivers, c.nrec) : std::min(c.nrec, 8);
+  ctx->K = c.dft_chunk ? c.dft_chunk : 32;
+
+  Layout& L = ctx->L;
+  L.nz = c.nz; L.nx = c.nx; L.ns = c.nsponge;
+  L.NZ = c.nz + 2 * c.nsponge;
+  L.NX = c.nx + 2 * c.nsponge;
+  L.PX = (int)std::max<long long>(64, round_up(L.NX + 4, 32));
+  L.F = (long long)(L.NZ + 2 * GUARD) * L.PX;
+  L.org = (long long)GUARD * L.PX;
+  L.G = round_up((long long)L.NZ * L.PX, 256);
+
+  const int ntile = gram_tiles(c.nrec);
+  const long long pairs_nf = (long long)ntile * (ntile + 1) / 2 * c.nfreq;
+  if (c.gram_splits) {
+    ctx->splits = c.gram_splits;
+  } else {
+    long long s = (3LL * 456 + pairs_nf - 1) / pairs_nf;
+    s = std::max(1LL, std::min(s, L.G / 2048));
+    ctx->splits = (int)std::max(1LL, s);
+  }
+
+  ctx->S.c0 = (float)(kC8[0] * (1.0 / (c.dx * c.dx) + 1.0 / (c.dz * c.dz)));
+  for (int k = 0; k < 4; ++k) {
+    ctx->S.cx[k] = (float)(kC8[k + 1] / (c.dx * c.dx));
+    ctx->S.cz[k] = (float)(kC8[k + 1] / (c.dz * c.dz));
+  }
+
+  // band-limited synthesis weights 2 df_k dt
+  {
+    const int nf = c.nfreq;
+    std::vector<double> df(nf);
+    if (nf == 1) {
+      df[0] = 1.0 / (c.nt * c.dt);
+    } else {
+      for (int k = 1; k < nf - 1; ++k) df[k] = 0.5 * (c.freq_hz[k + 1] - c.freq_hz[k - 1]);
+      df[0] = c.freq_hz[1] - c.freq_hz[0];
+      df[nf - 1] = c.freq_hz[nf - 1] - c.freq_hz[nf - 2];
+    }
+    ctx->wsyn.resize(nf);
+    for (int k = 0; k < nf; ++k) ctx->wsyn[k] = (float)(2.0 * df[k] * c.dt);
+  }
+
+  egh_status s = EGH_OK;
+  const size_t F = (size_t)L.F;
+#define ALLOC(ptr, bytes, what)                                 \
+  do {                                                          \
+    s = dalloc(ctx, (void**)&(ptr), (bytes), what);             \
+    if (s) {                                                    \
+      g_create_error = ctx->err;                                \
+      free_all(ctx);                                            \
+      delete ctx;                                               \
+      return s;                                                 \
+    }                                                           \
+  } while (0)
+  ALLOC(ctx->c1, F * sizeof(float), "c1");
+  ALLOC(ctx->c3, F * sizeof(float), "c3");
+  ALLOC(ctx->ring, (size_t)ctx->K * ctx->B * F * sizeof(float), "ring");
+  ALLOC(ctx->gh, (size_t)c.nrec * c.nfreq * 2 * (size_t)L.G * sizeof(float), "green transforms");
+  ALLOC(ctx->part, gram_workspace_floats(c.nrec, c.nfreq, ctx->splits) * sizeof(float), "gram");
+  ALLOC(ctx->Qh, (size_t)c.nfreq * c.nrec * c.nrec * sizeof(float2), "Qh");
+  ALLOC(ctx->Lh, (size_t)c.nfreq * c.nrec * c.nrec * sizeof(float2), "Lh");
+  ALLOC(ctx->w_dev, (size_t)c.nfreq * sizeof(float), "weights");
+  ALLOC(ctx->rec_pts, (size_t)c.nrec * sizeof(int), "receivers");
+  ALLOC(ctx->status, (size_t)c.nfreq * sizeof(int), "status");
+  ALLOC(ctx->dsum, sizeof(double), "dsum");
+  ALLOC(ctx->lmax, (size_t)c.nfreq * sizeof(double), "lmax");
+  ALLOC(ctx->vchk, 2 * sizeof(float), "vchk");
+  ALLOC(ctx->vel_stage, (size_t)c.nz * c.nx * sizeof(float), "velocity staging");
+#undef ALLOC
+  auto init = [&]() -> egh_status {
+    CK(cudaMemset(ctx->c1, 0, F * sizeof(float)));
+    CK(cudaMemset(ctx->c3, 0, F * sizeof(float)));
+    std::vector<int> rp(c.nrec);
+    for (int r = 0; r < c.nrec; ++r)
+      rp[r] = (int)(L.org + (long long)(c.rec_iz[r] + c.nsponge) * L.PX + (c.rec_ix[r] + c.nsponge));
+    CK(cudaMemcpy(ctx->rec_pts, rp.data(), rp.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->w_dev, ctx->wsyn.data(), ctx->wsyn.size() * sizeof(float),
+                  cudaMemcpyHostToDevice));
+    for (cudaEvent_t& e : ctx->ev) CK(cudaEventCreate(&e));
+    egh_status s2 = ensure_twiddles(ctx, c.nt, 0);
+    if (s2) return s2;
+    CK(cudaDeviceSynchronize());
+    return EGH_OK;
+  };
+  s = init();
+  if (s) {
+    g_create_error = ctx->err;
+    free_all(ctx);
+    delete ctx;
+    return s;
+  }
+  ctx->st.nz_pad = L.NZ;
+  ctx->st.nx_pad = L.NX;
+  ctx->st.pitch = L.PX;
+  ctx->st.batch_receivers = ctx->B;
+  ctx->st.dft_chunk = ctx->K;
+  ctx->st.gram_splits = ctx->splits;
+  *out = ctx;
+  return EGH_OK;
+}
+
+void egh_destroy(egh_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->dev);
+  cudaDeviceSynchronize();
+  free_all(ctx);
+  delete ctx;
+}
+
+egh_status egh_green(egh_ctx* ctx, const float* vel, void* stream_) {
+  if (!ctx) return fail(nullptr, EGH_EINVAL, "ctx is NULL");
+  cudaStream_t stream = (cudaStream_t)stream_;
+  CK(cudaSetDevice(ctx->dev));
+  ctx->state = ST_CREATED;
+  egh_status s = prepare_model(ctx, vel, stream);
+  if (s) return s;
+  const Layout& L = ctx->L;
+  const int K = ctx->K, B = ctx->B, nt = ctx->nt;
+  const long long slot_stride = (long long)B * L.F;
+  CK(cudaEventRecord(ctx->ev[0], stream));
+  CK(cudaMemsetAsync(ctx->gh, 0, (size_t)ctx->nrec * ctx->nf * 2 * L.G * sizeof(float), stream));
+  const float src_scale = (float)(1.0 / (ctx->dx * ctx->dz));
+  for (int b0 = 0; b0 < ctx->nrec; b0 += B) {
+    const int nb = std::min(B, ctx->nrec - b0);
+    CK(cudaMemsetAsync(ctx->ring, 0, (size_t)K * slot_stride * sizeof(float), stream));
+    auto chunk_end = [&](int t) -> egh_status {
+      if (t % K == K - 1 || t == nt - 1) {
+        CK(launch_dft_chunk(ctx->ring, slot_stride, L.F, L, ctx->tw, ctx->nf, t - t % K,
+                            t % K + 1, K, nb, ctx->gh, b0, stream));
+      }
+      return EGH_OK;
+    };
+    // level 0 is zero; level 1 is the impulse (the step from zero levels adds only the source)
+    if ((s = chunk_end(0))) return s;
+    if (nt >= 2) {
+      CK(launch_inject(slot(ctx, 1), L.F, ctx->rec_pts + b0, ctx->c3, nb, nullptr, 1.0f,
+                       src_scale, stream));
+      if ((s = chunk_end(1))) return s;
+    }
+    for (int n = 1; n + 1 < nt; ++n) {
+      CK(launch_fd_step(slot(ctx, n), slot(ctx, n - 1), slot(ctx, n + 1), ctx->c1, ctx->c3, L,
+                        ctx->S, nb, L.F, stream));
+      if ((s = chunk_end(n + 1))) return s;
+    }
+  }
+  CK(cudaEventRecord(ctx->ev[1], stream));
+  ctx->ev_rec[0] = true;
+  ctx->st.pde_solves = ctx->nrec;
+  ctx->st.point_steps = (long long)ctx->nrec * nt * L.NZ * L.NX;
+  ctx->state = ST_GREEN;
+  return EGH_OK;
+}
+
+egh_status egh_hessian(egh_ctx* ctx, egh_mu_mode mode, double mu_param, double* mu_out,
+                       void* stream_) {
+  if (!ctx) return fail(nullptr, EGH_EINVAL, "ctx is NULL");
+  cudaStream_t stream = (cudaStream_t)stream_;
+  CK(cudaSetDevice(ctx->dev));
+  if (ctx->state < ST_GREEN) return fail(ctx, EGH_ESTATE, "egh_hessian needs egh_green first");
+  if (!std::isfinite(mu_param) || mu_param < 0)
+    return fail(ctx, EGH_EINVAL, "mu_param must be finite and >= 0");
+  if (mode != EGH_MU_ABS && mode != EGH_MU_REL_MEANDIAG && mode != EGH_MU_REL_MAXEIG)
+    return fail(ctx, EGH_EINVAL, "unknown mu mode");
+  CK(cudaEventRecord(ctx->ev[2], stream));
+  CK(launch_gram_partial(ctx->gh, ctx->nrec, ctx->nf, ctx->L.G, ctx->splits, ctx->part, stream));
+  CK(launch_gram_finish(ctx->part, ctx->nrec, ctx->nf, ctx->splits, ctx->Qh, stream));
+  double mu = mu_param;
+  if (mode == EGH_MU_REL_MEANDIAG) {
+    CK(launch_diag_sum(ctx->Qh, ctx->nrec, ctx->nf, ctx->dsum, stream));
+    double sum = 0;
+    CK(cudaMemcpyAsync(&sum, ctx->dsum, sizeof sum, cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    mu = mu_param * sum / ((double)ctx->nf * ctx->nrec);
+  } else if (mode == EGH_MU_REL_MAXEIG) {
+    CK(launch_lambda_max(ctx->Qh, ctx->nrec, ctx->nf, ctx->lmax, stream));
+    std::vector<double> lm(ctx->nf);
+    CK(cudaMemcpyAsync(lm.data(), ctx->lmax, lm.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                       stream));
+    CK(cudaStreamSynchronize(stream));
+    mu = mu_param * *std::max_element(lm.begin(), lm.end());
+  }
+  if (!std::isfinite(mu)) return fail(ctx, EGH_EINVAL, "mu is not finite");
+  CK(launch_add_mu_copy(ctx->Qh, ctx->Lh, ctx->nrec, ctx->nf, (float)mu, stream));
+  CK(cudaEventRecord(ctx->ev[3], stream));
+  ctx->ev_rec[1] = true;
+  ctx->mu = mu;
+  ctx->st.mu = mu;
+  if (mu_out) *mu_out = mu;
+  ctx->state = ST_HESSIAN;
+  return EGH_OK;
+}
+
+egh_status egh_factor(egh_ctx* ctx, int32_t* bad_freq, void* stream_) {
+  if (!ctx) return fail(nullptr, EGH_EINVAL, "ctx is NULL");
+  cudaStream_t stream = (cudaStream_t)stream_;
+  CK(cudaSetDevice(ctx->dev));
+  if (bad_freq) *bad_freq = -1;
+  if (ctx->state < ST_HESSIAN) return fail(ctx, EGH_ESTATE, "egh_factor needs egh_hessian first");
+  const size_t bytes = (size_t)ctx->nf * ctx->nrec * ctx->nrec * sizeof(float2);
+  CK(cudaEventRecord(ctx->ev[4], stream));
+  CK(cudaMemcpyAsync(ctx->Lh, ctx->Qh, bytes, cudaMemcpyDeviceToDevice, stream));
+  CK(launch_potrf(ctx->Lh, ctx->nrec, ctx->nf, ctx->status, stream));
+  CK(cudaEventRecord(ctx->ev[5], stream));
+  ctx->ev_rec[2] = true;
+  std::vector<int> stv(ctx->nf);
+  CK(cudaMemcpyAsync(stv.data(), ctx->status, stv.size() * sizeof(int), cudaMemcpyDeviceToHost,
+                     stream));
+  CK(cudaStreamSynchronize(stream));
+  for (int k = 0; k < ctx->nf; ++k)
+    if (stv[k]) {
+      if (bad_freq) *bad_freq = k;
+      ctx->state = ST_HESSIAN;
+      char buf[128];
+      snprintf(buf, sizeof buf, "Hessian at frequency %d not positive definite (pivot %d)", k,
+               stv[k] - 1);
+      return fail(ctx, EGH_ENOTPD, buf);
+    }
+  ctx->state = ST_FACTORED;
+  return EGH_OK;
+}
+
+static egh_status deblur_common(egh_ctx* ctx, const float* resid, int32_t ns, int32_t nt_d,
+                                float* mult, float2* X, cudaStream_t stream) {
+  if (ctx->state < ST_FACTORED) return fail(ctx, EGH_ESTATE, "egh_deblur needs egh_factor first");
+  if (ns < 0 || nt_d < 1) return fail(ctx, EGH_EINVAL, "ns must be >= 0 and nt_d >= 1");
+  if (!resid || (!mult && !X)) return fail(ctx, EGH_EINVAL, "NULL buffer");
+  if (ns == 0) return EGH_OK;
+  const long long ntr = (long long)ns * ctx->nrec;
+  if ((ntr + 63) / 64 > 65535) return fail(ctx, EGH_EINVAL, "too many traces in one call");
+  const bool dev_in = pointer_is_device(resid);
+  const bool dev_out = X ? true : pointer_is_device(mult);
+  if (X && !pointer_is_device(X)) return fail(ctx, EGH_EINVAL, "X must be device memory");
+  if (!X && dev_in != dev_out)
+    return fail(ctx, EGH_EINVAL, "resid and mult must both be host or both be device memory");
+  egh_status s = ensure_twiddles(ctx, nt_d, stream);
+  if (s) return s;
+  const size_t nbytes = (size_t)ntr * nt_d * sizeof(float);
+  const float* din = resid;
+  if (!dev_in) {
+    if ((s = ensure_buf(ctx, (void**)&ctx->io_in, &ctx->io_in_cap, nbytes, stream, "resid staging")))
+      return s;
+    CK(cudaMemcpyAsync(ctx->io_in, resid, nbytes, cudaMemcpyHostToDevice, stream));
+    din = ctx->io_in;
+  }
+  float2* D = X;
+  if (!D) {
+    if ((s = ensure_buf(ctx, (void**)&ctx->Dh, &ctx->Dh_cap,
+                        (size_t)ctx->nf * ntr * sizeof(float2), stream, "deblur spectra")))
+      return s;
+    D = ctx->Dh;
+  }
+  float* dout = mult;
+  if (!X && !dev_out) {
+    if ((s = ensure_buf(ctx, (void**)&ctx->io_out, &ctx->io_out_cap, nbytes, stream,
+                        "mult staging")))
+      return s;
+    dout = ctx->io_out;
+  }
+  CK(cudaEventRecord(ctx->ev[6], stream));
+  CK(launch_trace_dft(din, (int)ntr, nt_d, ctx->tw, ctx->nf, ctx->nrec, ns, D, stream));
+  CK(launch_trsm(ctx->Lh, ctx->nrec, ctx->nf, D, ns, stream));
+  if (!X) CK(launch_synth(D, ctx->nrec, ns, ctx->nf, ctx->w_dev, ctx->tw, nt_d, dout, stream));
+  CK(cudaEventRecord(ctx->ev[7], stream));
+  ctx->ev_rec[3] = true;
+  ctx->st.deblur_sources = ns;
+  if (!X && !dev_out) {
+    CK(cudaMemcpyAsync(mult, dout, nbytes, cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+  } else if (!dev_in) {
+    CK(cudaStreamSynchronize(stream));
+  }
+  return EGH_OK;
+}
+
+egh_status egh_deblur(egh_ctx* ctx, const float* resid, int32_t ns, int32_t nt_d, float* mult,
+                      void* stream) {
+  if (!ctx) return fail(nullptr, EGH_EINVAL, "ctx is NULL");
+  CK(cudaSetDevice(ctx->dev));
+  if (!mult) return fail(ctx, EGH_EINVAL, "mult is NULL");
+  return deblur_common(ctx, resid, ns, nt_d, mult, nullptr, (cudaStream_t)stream);
+}
+
+egh_status egh_deblur_freq(egh_ctx* ctx, const float* resid, int32_t ns, int32_t nt_d, void* X,
+                           void* stream) {
+  if (!ctx) return fail(nullptr, EGH_EINVAL, "ctx is NULL");
+  CK(cudaSetDevice(ctx->dev));
+  if (!X) return fail(ctx, EGH_EINVAL, "X is NULL");
+  return deblur_common(ctx, resid, ns, nt_d, nullptr, (float2*)X, (cudaStream_t)stream);
+}
+
+egh_status egh_forward(egh_ctx* ctx, const float* vel, int32_t nsrc, const int32_t* src_iz,
+                       const int32_t* src_ix, const float* wavelet, float* data, void* stream_) {
+  if (!ctx) return fail(nullptr, EGH_EINVAL, "ctx is NULL");
+  cudaStream_t stream = (cudaStream_t)stream_;
+  CK(cudaSetDevice(ctx->dev));
+  if (nsrc < 1 || !src_iz || !src_ix || !wavelet || !data)
+    return fail(ctx, EGH_EINVAL, "bad forward-modelling arguments");
+  for (int s = 0; s < nsrc; ++s)
+    if (src_iz[s] < 0 || src_iz[s] >= ctx->nz || src_ix[s] < 0 || src_ix[s] >= ctx->nx)
+      return fail(ctx, EGH_EINVAL, "source outside the physical grid");
+  const int prev_state = ctx->state;
+  egh_status s = prepare_model(ctx, vel, stream);
+  ctx->state = prev_state;
+  if (s) return s;
+  const Layout& L = ctx->L;
+  const int K = ctx->K, B = ctx->B, nt = ctx->nt, nrec = ctx->nrec;
+  const long long slot_stride = (long long)B * L.F;
+  std::vector<int> sp(nsrc);
+  for (int i = 0; i < nsrc; ++i)
+    sp[i] = (int)(L.org + (long long)(src_iz[i] + L.ns) * L.PX + (src_ix[i] + L.ns));
+  int* d_sp = nullptr;
+  if ((s = dalloc(ctx, (void**)&d_sp, sp.size() * sizeof(int), "source points"))) return s;
+  struct Guard {
+    int* p;
+    ~Guard() { cudaFree(p); }
+  } guard{d_sp};
+  CK(cudaMemcpyAsync(d_sp, sp.data(), sp.size() * sizeof(int), cudaMemcpyHostToDevice, stream));
+  const bool dev_out = pointer_is_device(data);
+  const size_t nbytes = (size_t)nsrc * nrec * nt * sizeof(float);
+  float* dout = data;
+  if (!dev_out) {
+    if ((s = ensure_buf(ctx, (void**)&ctx->io_out, &ctx->io_out_cap, nbytes, stream, "traces")))
+      return s;
+    dout = ctx->io_out;
+  }
+  const float scale = (float)(1.0 / (ctx->dx * ctx->dz));
+  for (int b0 = 0; b0 < nsrc; b0 += B) {
+    const int nb = std::min(B, nsrc - b0);
+    float* tr = dout + (size_t)b0 * nrec * nt;
+    CK(cudaMemsetAsync(ctx->ring, 0, (size_t)K * slot_stride * sizeof(float), stream));
+    CK(launch_record(slot(ctx, 0), L.F, ctx->rec_pts, nrec, nb, tr, nt, 0, stream));
+    for (int n = 0; n + 1 < nt; ++n) {
+      if (n > 0)
+        CK(launch_fd_step(slot(ctx, n), slot(ctx, n - 1), slot(ctx, n + 1), ctx->c1, ctx->c3, L,
+                          ctx->S, nb, L.F, stream));
+      if (wavelet[n] != 0.f)
+        CK(launch_inject(slot(ctx, n + 1), L.F, d_sp + b0, ctx->c3, nb, nullptr, wavelet[n], scale,
+                         stream));
+      CK(launch_record(slot(ctx, n + 1), L.F, ctx->rec_pts, nrec, nb, tr, nt, n + 1, stream));
+    }
+  }
+  if (!dev_out) CK(cudaMemcpyAsync(data, dout, nbytes, cudaMemcpyDeviceToHost, stream));
+  CK(cudaStreamSynchronize(stream));
+  return EGH_OK;
+}
+
+egh_status egh_get_green(egh_ctx* ctx, int32_t r0, int32_t nr, void* host_out) {
+  if (!ctx) return fail(nullptr, EGH_EINVAL, "ctx is NULL");
+  CK(cudaSetDevice(ctx->dev));
+  if (ctx->state < ST_GREEN) return fail(ctx, EGH_ESTATE, "no Green functions yet");
+  if (r0 < 0 || nr < 0 || r0 + nr > ctx->nrec || !host_out)
+    return fail(ctx, EGH_EINVAL, "bad receiver range");
+  CK(cudaDeviceSynchronize());
+  const Layout& L = ctx->L;
+  const size_t per = (size_t)ctx->nf * 2 * L.G;
+  std::vector<float> h(per);
+  float* out = (float*)host_out;
+  for (int r = 0; r < nr; ++r) {
+    CK(cudaMemcpy(h.data(), ctx->gh + (size_t)(r0 + r) * per, per * sizeof(float),
+                  cudaMemcpyDeviceToHost));
+    for (int k = 0; k < ctx->nf; ++k) {
+      const float* re = h.data() + (size_t)k * 2 * L.G;
+      const float* im = re + L.G;
+      float* o = out + (((size_t)r * ctx->nf + k) * L.NZ * L.NX) * 2;
+      for (int z = 0; z < L.NZ; ++z)
+        for (int x = 0; x < L.NX; ++x) {
+          const size_t p = (size_t)z * L.PX + x;
+          o[2 * ((size_t)z * L.NX + x)] = re[p];
+          o[2 * ((size_t)z * L.NX + x) + 1] = im[p];
+        }
+    }
+  }
+  return EGH_OK;
+}
+
+egh_status egh_get_hessian(egh_ctx* ctx, int32_t factored, void* host_out) {
+  if (!ctx) return fail(nullptr, EGH_EINVAL, "ctx is NULL");
+  CK(cudaSetDevice(ctx->dev));
+  if (!host_out) return fail(ctx, EGH_EINVAL, "host_out is NULL");
+  if (ctx->state < (factored ? ST_FACTORED : ST_HESSIAN))
+    return fail(ctx, EGH_ESTATE, factored ? "no factors yet" : "no Hessian yet");
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpy(host_out, factored ? ctx->Lh : ctx->Qh,
+                (size_t)ctx->nf * ctx->nrec * ctx->nrec * sizeof(float2), cudaMemcpyDeviceToHost));
+  return EGH_OK;
+}
+
+egh_status egh_get_stats(egh_ctx* ctx, egh_stats* out) {
+  if (!ctx || !out) return fail(ctx, EGH_EINVAL, "NULL argument");
+  CK(cudaSetDevice(ctx->dev));
+  double* ms[4] = {&ctx->st.green_ms, &ctx->st.hessian_ms, &ctx->st.factor_ms, &ctx->st.deblur_ms};
+  for (int i = 0; i < 4; ++i)
+    if (ctx->ev_rec[i]) {
+      CK(cudaEventSynchronize(ctx->ev[2 * i + 1]));
+      float t = 0;
+      CK(cudaEventElapsedTime(&t, ctx->ev[2 * i], ctx->ev[2 * i + 1]));
+      *ms[i] = t;
+    }
+  ctx->st.kernel_launches = launches_so_far();
+  *out = ctx->st;
+  return EGH_OK;
+}
+
+}  // extern "C"

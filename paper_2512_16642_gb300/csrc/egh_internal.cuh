@@ -1,0 +1,75 @@
+// Internal declarations of the egh library (not part of the ABI).
+//
+// Device data layout (all float32 unless stated):
+//   wavefield level: [NZ + 2*GUARD][PX], rows z = -GUARD .. NZ+GUARD-1, row pitch PX >= NX + 4
+//     (multiple of 32).  Guard rows and columns x >= NX are zero and never written, so the
+//     eighth-order stencil reads them as the u = 0 boundary without any bounds test;
+//   ring of K time levels for a batch of B receivers: [K][B][F], F = (NZ + 2*GUARD) * PX,
+//     level n lives in slot n mod K;
+//   Green transforms gh: [nrec][nf][2][G], planes re/im, G = NZ*PX rounded up to 256, point
+//     p = z*PX + x (entries with x >= NX or p >= NZ*PX are zero);
+//   Hessians Qh, factors Lh: [nf][nrec][nrec] float2 (complex64).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace egh {
+
+constexpr int GUARD = 4;  // stencil radius of the eighth-order Laplacian
+
+// Counts kernel launches (every launch_* wrapper adds its launches); read by egh_get_stats.
+void count_launches(int n);
+long long launches_so_far();
+
+struct Stencil {
+  float c0;     // centre weight c_0 (1/dx^2 + 1/dz^2)
+  float cx[4];  // c_k / dx^2, k = 1..4
+  float cz[4];  // c_k / dz^2
+};
+
+struct Layout {
+  int nz, nx, ns;  // physical grid and sponge width
+  int NZ, NX, PX;  // padded grid and pitch
+  long long F;     // floats per wavefield level (with guard rows)
+  long long org;   // offset of padded point (0, 0) inside a level: GUARD * PX
+  long long G;     // Gram contraction length
+};
+
+// ---- fd.cu ------------------------------------------------------------------------------------
+cudaError_t launch_check_velocity(const float* vel, long long n, float* d_vmax_bad, cudaStream_t st);
+cudaError_t launch_build_coef(const float* vel, const Layout& L, double dz, double dx, double dt,
+                              double R, const float* d_vmax, float* c1, float* c3, cudaStream_t st);
+cudaError_t launch_fd_step(const float* ucur, const float* uprev, float* unext, const float* c1,
+                           const float* c3, const Layout& L, const Stencil& S, int nb,
+                           long long fstride, cudaStream_t st);
+cudaError_t launch_inject(float* u, long long fstride, const int* pts, const float* c3, int nb,
+                          const float* amp_dev, float amp_host, float scale, cudaStream_t st);
+cudaError_t launch_record(const float* u, long long fstride, const int* rec_pts, int nrec, int nb,
+                          float* traces, int nt, int t, cudaStream_t st);
+cudaError_t launch_dft_chunk(const float* ring, long long slot_stride, long long fstride,
+                             const Layout& L, const float2* tw, int nf, int n0, int kcount, int K,
+                             int nb, float* gh, int rec0, cudaStream_t st);
+
+// ---- gram.cu ----------------------------------------------------------------------------------
+__host__ __device__ int gram_tiles(int nrec);
+size_t gram_workspace_floats(int nrec, int nf, int splits);
+cudaError_t launch_gram_partial(const float* gh, int nrec, int nf, long long G, int splits,
+                                float* part, cudaStream_t st);
+cudaError_t launch_gram_finish(const float* part, int nrec, int nf, int splits, float2* Qh,
+                               cudaStream_t st);
+cudaError_t launch_diag_sum(const float2* Qh, int nrec, int nf, double* d_sum, cudaStream_t st);
+cudaError_t launch_lambda_max(const float2* Qh, int nrec, int nf, double* d_lmax, cudaStream_t st);
+cudaError_t launch_add_mu_copy(float2* Qh, float2* Lh, int nrec, int nf, float mu, cudaStream_t st);
+
+// ---- chol.cu ----------------------------------------------------------------------------------
+cudaError_t launch_potrf(float2* Lh, int n, int nf, int* status, cudaStream_t st);
+
+// ---- deblur.cu --------------------------------------------------------------------------------
+cudaError_t launch_trace_dft(const float* resid, int ntr, int nt_d, const float2* tw, int nf,
+                             int nrec, int ns, float2* Dh, cudaStream_t st);
+cudaError_t launch_trsm(const float2* Lh, int n, int nf, float2* Dh, int ns, cudaStream_t st);
+cudaError_t launch_synth(const float2* Dh, int nrec, int ns, int nf, const float* w,
+                         const float2* tw, int nt_d, float* mult, cudaStream_t st);
+
+}  // namespace egh

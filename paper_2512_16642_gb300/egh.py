@@ -1,0 +1,283 @@
+"""Thin ctypes binding of the egh C ABI (include/egh.h).
+
+Argument marshalling only: every numerical step runs in the CUDA kernels of
+libegh.so.  Buffers may be torch tensors (CUDA tensors are passed as device
+pointers on the current torch stream; CPU tensors as host pointers) or numpy
+arrays (host pointers).  Loading fails loudly when the library is missing;
+there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libegh.so")
+
+EGH_OK, EGH_EINVAL, EGH_ENOMEM, EGH_ECUDA, EGH_ENOTPD, EGH_ESTATE, EGH_ETIMEOUT = range(7)
+EGH_MU_ABS, EGH_MU_REL_MEANDIAG, EGH_MU_REL_MAXEIG = range(3)
+
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_f64p = ctypes.POINTER(ctypes.c_double)
+
+
+class egh_config(ctypes.Structure):
+    _fields_ = [
+        ("nz", ctypes.c_int32), ("nx", ctypes.c_int32),
+        ("dz", ctypes.c_double), ("dx", ctypes.c_double),
+        ("nsponge", ctypes.c_int32), ("sponge_R", ctypes.c_double),
+        ("dt", ctypes.c_double), ("nt", ctypes.c_int32),
+        ("nrec", ctypes.c_int32), ("rec_iz", _i32p), ("rec_ix", _i32p),
+        ("nfreq", ctypes.c_int32), ("freq_hz", _f64p),
+        ("batch_receivers", ctypes.c_int32), ("dft_chunk", ctypes.c_int32),
+        ("gram_splits", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5),
+    ]
+
+
+class egh_stats(ctypes.Structure):
+    _fields_ = [
+        ("green_ms", ctypes.c_double), ("hessian_ms", ctypes.c_double),
+        ("factor_ms", ctypes.c_double), ("deblur_ms", ctypes.c_double),
+        ("pde_solves", ctypes.c_int64), ("point_steps", ctypes.c_int64),
+        ("deblur_sources", ctypes.c_int64), ("mu", ctypes.c_double),
+        ("nz_pad", ctypes.c_int32), ("nx_pad", ctypes.c_int32), ("pitch", ctypes.c_int32),
+        ("batch_receivers", ctypes.c_int32), ("dft_chunk", ctypes.c_int32),
+        ("gram_splits", ctypes.c_int32), ("kernel_launches", ctypes.c_int64),
+    ]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+_vp = ctypes.c_void_p
+_SIGS = {
+    "egh_create": ([ctypes.POINTER(egh_config), ctypes.POINTER(_vp)], ctypes.c_int),
+    "egh_destroy": ([_vp], None),
+    "egh_green": ([_vp, _vp, _vp], ctypes.c_int),
+    "egh_hessian": ([_vp, ctypes.c_int, ctypes.c_double, _f64p, _vp], ctypes.c_int),
+    "egh_factor": ([_vp, _i32p, _vp], ctypes.c_int),
+    "egh_deblur": ([_vp, _vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp], ctypes.c_int),
+    "egh_deblur_freq": ([_vp, _vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp], ctypes.c_int),
+    "egh_forward": ([_vp, _vp, ctypes.c_int32, _i32p, _i32p, _vp, _vp, _vp], ctypes.c_int),
+    "egh_get_green": ([_vp, ctypes.c_int32, ctypes.c_int32, _vp], ctypes.c_int),
+    "egh_get_hessian": ([_vp, ctypes.c_int32, _vp], ctypes.c_int),
+    "egh_get_stats": ([_vp, ctypes.POINTER(egh_stats)], ctypes.c_int),
+    "egh_last_error": ([_vp], ctypes.c_char_p),
+    "egh_status_string": ([ctypes.c_int], ctypes.c_char_p),
+    "egh_version": ([], ctypes.c_int32),
+}
+EXPORTS = tuple(_SIGS)
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Loads libegh.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"libegh.so not built ({path}); run __graft_entry__.build()")
+        lib = ctypes.CDLL(path)
+        for name, (args, res) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+    return _lib
+
+
+class EghError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{status_string(status)}: {msg}")
+        self.status = status
+
+
+def status_string(s):
+    return load().egh_status_string(s).decode()
+
+
+def _check(rc, ctx):
+    if rc != EGH_OK:
+        raise EghError(rc, load().egh_last_error(ctx).decode())
+
+
+def _ptr(buf):
+    """(pointer, is_cuda_tensor) of a torch tensor or numpy array (must be contiguous)."""
+    if isinstance(buf, np.ndarray):
+        if not buf.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return buf.ctypes.data, False
+    if hasattr(buf, "data_ptr"):
+        if not buf.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return buf.data_ptr(), buf.is_cuda
+    raise TypeError(f"unsupported buffer type {type(buf)}")
+
+
+def _stream(stream, any_cuda):
+    if stream is not None:
+        return int(stream)
+    if any_cuda:
+        import torch
+
+        return torch.cuda.current_stream().cuda_stream
+    return 0
+
+
+def _i32(a):
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    return a, a.ctypes.data_as(_i32p)
+
+
+# ---- the ABI calls, same names -----------------------------------------------------------
+def egh_create(nz, nx, dz, dx, nsponge, sponge_R, dt, nt, rec_iz, rec_ix, freq_hz,
+               batch_receivers=0, dft_chunk=0, gram_splits=0):
+    lib = load()
+    riz, riz_p = _i32(rec_iz)
+    rix, rix_p = _i32(rec_ix)
+    f = np.ascontiguousarray(freq_hz, dtype=np.float64)
+    cfg = egh_config(int(nz), int(nx), float(dz), float(dx), int(nsponge), float(sponge_R), float(dt),
+                     int(nt), int(riz.size), riz_p, rix_p, int(f.size), f.ctypes.data_as(_f64p),
+                     int(batch_receivers), int(dft_chunk), int(gram_splits))
+    h = _vp()
+    _check(lib.egh_create(ctypes.byref(cfg), ctypes.byref(h)), None)
+    return h
+
+
+def egh_destroy(ctx):
+    load().egh_destroy(ctx)
+
+
+def egh_green(ctx, vel, stream=None):
+    p, cu = _ptr(vel)
+    _check(load().egh_green(ctx, p, _stream(stream, cu)), ctx)
+
+
+def egh_hessian(ctx, mode=EGH_MU_REL_MEANDIAG, mu_param=1e-2, stream=None):
+    mu = ctypes.c_double(0.0)
+    _check(load().egh_hessian(ctx, int(mode), float(mu_param), ctypes.byref(mu), _stream(stream, True)),
+           ctx)
+    return mu.value
+
+
+def egh_factor(ctx, stream=None):
+    bad = ctypes.c_int32(-1)
+    rc = load().egh_factor(ctx, ctypes.byref(bad), _stream(stream, True))
+    if rc == EGH_ENOTPD:
+        err = EghError(rc, load().egh_last_error(ctx).decode())
+        err.bad_freq = bad.value
+        raise err
+    _check(rc, ctx)
+    return bad.value
+
+
+def egh_deblur(ctx, resid, ns, nt_d, mult, stream=None):
+    pi, ci = _ptr(resid)
+    po, co = _ptr(mult)
+    _check(load().egh_deblur(ctx, pi, int(ns), int(nt_d), po, _stream(stream, ci or co)), ctx)
+
+
+def egh_deblur_freq(ctx, resid, ns, nt_d, X, stream=None):
+    pi, ci = _ptr(resid)
+    px, cx = _ptr(X)
+    _check(load().egh_deblur_freq(ctx, pi, int(ns), int(nt_d), px, _stream(stream, ci or cx)), ctx)
+
+
+def egh_forward(ctx, vel, src_iz, src_ix, wavelet, data, stream=None):
+    pv, cv = _ptr(vel)
+    siz, siz_p = _i32(src_iz)
+    six, six_p = _i32(src_ix)
+    w = np.ascontiguousarray(wavelet, dtype=np.float32)
+    pd, cd = _ptr(data)
+    _check(load().egh_forward(ctx, pv, int(siz.size), siz_p, six_p, w.ctypes.data, pd,
+                              _stream(stream, cv or cd)), ctx)
+
+
+def egh_get_green(ctx, r0, nr, out):
+    p, _ = _ptr(out)
+    _check(load().egh_get_green(ctx, int(r0), int(nr), p), ctx)
+
+
+def egh_get_hessian(ctx, factored, out):
+    p, _ = _ptr(out)
+    _check(load().egh_get_hessian(ctx, int(factored), p), ctx)
+
+
+def egh_get_stats(ctx):
+    st = egh_stats()
+    _check(load().egh_get_stats(ctx, ctypes.byref(st)), ctx)
+    return st.as_dict()
+
+
+def egh_version():
+    return load().egh_version()
+
+
+# ---- convenience wrapper -------------------------------------------------------------------
+class Context:
+    """Owns one egh context; methods mirror the ABI and return numpy results where a copy is
+    implied (get_green, get_hessian)."""
+
+    def __init__(self, nz, nx, dz, dx, nsponge, sponge_R, dt, nt, rec_iz, rec_ix, freq_hz, **kw):
+        self.nz, self.nx, self.ns, self.nt = int(nz), int(nx), int(nsponge), int(nt)
+        self.nrec = int(np.size(rec_iz))
+        self.freqs = np.asarray(freq_hz, dtype=np.float64)
+        self.nf = self.freqs.size
+        self.h = egh_create(nz, nx, dz, dx, nsponge, sponge_R, dt, nt, rec_iz, rec_ix, freq_hz, **kw)
+
+    def close(self):
+        if self.h:
+            egh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def green(self, vel, stream=None):
+        egh_green(self.h, vel, stream)
+
+    def hessian(self, mode=EGH_MU_REL_MEANDIAG, mu_param=1e-2, stream=None):
+        return egh_hessian(self.h, mode, mu_param, stream)
+
+    def factor(self, stream=None):
+        return egh_factor(self.h, stream)
+
+    def deblur(self, resid, mult, stream=None):
+        ns, nr, ntd = resid.shape
+        egh_deblur(self.h, resid, ns, ntd, mult, stream)
+        return mult
+
+    def deblur_freq(self, resid, X, stream=None):
+        ns, nr, ntd = resid.shape
+        egh_deblur_freq(self.h, resid, ns, ntd, X, stream)
+        return X
+
+    def forward(self, vel, src_iz, src_ix, wavelet, data, stream=None):
+        egh_forward(self.h, vel, src_iz, src_ix, wavelet, data, stream)
+        return data
+
+    def get_green(self, r0=0, nr=None):
+        nr = self.nrec - r0 if nr is None else nr
+        NZ, NX = self.nz + 2 * self.ns, self.nx + 2 * self.ns
+        out = np.zeros((nr, self.nf, NZ, NX), dtype=np.complex64)
+        egh_get_green(self.h, r0, nr, out)
+        return out
+
+    def get_hessian(self, factored=False):
+        out = np.zeros((self.nf, self.nrec, self.nrec), dtype=np.complex64)
+        egh_get_hessian(self.h, 1 if factored else 0, out)
+        return out
+
+    def stats(self):
+        return egh_get_stats(self.h)

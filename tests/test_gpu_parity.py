@@ -1,0 +1,282 @@
+"""CUDA path against the FP64 oracle, element by element, through the C ABI.
+
+Bars: relative L2 <= 1e-4 for Green-function transforms and Hessians, <= 1e-3 for multipliers
+(FP32 path against FP64).  Both sides get the same float32 inputs (velocities, wavelet,
+residuals); the oracle sees them widened to float64.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+GREEN_TOL, HESS_TOL, MULT_TOL = 1e-4, 1e-4, 1e-3
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def _torch():
+    import torch
+
+    assert torch.cuda.is_available()
+    return torch
+
+
+def _ctx(c, **kw):
+    from paper_2512_16642_gb300 import egh
+
+    return egh.Context(c.nz, c.nx, c.dz, c.dx, c.nsponge, c.sponge_R, c.dt, c.nt, c.rec_iz, c.rec_ix,
+                       c.freqs, **kw)
+
+
+def _run_both(c, vel_green, ns_src=None, resid=None, nt_d=None, mu_alpha=None, ctx_kw=None,
+              workers=None):
+    """Oracle and GPU pipelines on the same inputs; returns a dict of both sides' results."""
+    torch = _torch()
+    from paper_2512_16642_gb300 import egh
+
+    v32 = np.asarray(vel_green, np.float32)
+    grid = oracle.Grid(v32.astype(np.float64), c.dz, c.dx, c.nsponge, c.sponge_R)
+    alpha = c.mu_alpha if mu_alpha is None else mu_alpha
+    o = {}
+    o["gh"] = oracle.green_dtft(grid, c.rec_iz, c.rec_ix, c.freqs, c.dt, c.nt, workers=workers)
+    H = oracle.hessian_gram(o["gh"])
+    o["mu"] = oracle.mu_mean_diag(H, alpha)
+    o["Q"] = oracle.add_mu(H, o["mu"])
+    o["L"] = oracle.cholesky(o["Q"])
+    g = {}
+    with _ctx(c, **(ctx_kw or {})) as ctx:
+        ctx.green(torch.from_numpy(v32).cuda())
+        g["gh"] = ctx.get_green()
+        g["mu"] = ctx.hessian(egh.EGH_MU_REL_MEANDIAG, alpha)
+        g["Q"] = ctx.get_hessian(False)
+        ctx.factor()
+        g["L"] = ctx.get_hessian(True)
+        if resid is not None:
+            r32 = np.ascontiguousarray(resid, np.float32)
+            o["mult"] = oracle.deblur(o["L"], r32.astype(np.float64), c.freqs, c.dt, nt_ref=c.nt)[0]
+            rt = torch.from_numpy(r32).cuda()
+            mt = torch.empty_like(rt)
+            ctx.deblur(rt, mt)
+            torch.cuda.synchronize()
+            g["mult"] = mt.cpu().numpy()
+            mh = np.empty_like(r32)
+            ctx.deblur(r32, mh)  # host buffers through the same entry point
+            g["mult_host"] = mh
+        g["stats"] = ctx.stats()
+    return o, g
+
+
+@pytest.fixture(scope="module")
+def small():
+    """101x101 model, 21 receivers, 11 sources, nt 1000, 5 frequencies; residuals from oracle
+    modelling in the true and start models."""
+    torch = _torch()
+    c = synth.case_small()
+    w32 = synth.ricker(c.nt, c.dt, c.ricker_hz).astype(np.float32)
+    gt = oracle.Grid(np.float32(c.vel_true).astype(np.float64), c.dz, c.dx, c.nsponge, c.sponge_R)
+    gs = oracle.Grid(np.float32(c.vel_start).astype(np.float64), c.dz, c.dx, c.nsponge, c.sponge_R)
+    w64 = w32.astype(np.float64)
+    d_true = oracle.forward_traces(gt, c.src_iz, c.src_ix, c.rec_iz, c.rec_ix, w64, c.dt)
+    d_start = oracle.forward_traces(gs, c.src_iz, c.src_ix, c.rec_iz, c.rec_ix, w64, c.dt)
+    resid = d_true - d_start
+    o, g = _run_both(c, c.vel_start, resid=resid)
+    # GPU forward modelling of the true model (auxiliary kernel path)
+    with _ctx(c) as ctx:
+        fwd = torch.empty((c.src_ix.size, c.rec_ix.size, c.nt), device="cuda")
+        ctx.forward(torch.from_numpy(np.float32(c.vel_true)).cuda(), c.src_iz, c.src_ix, w32, fwd)
+        g["fwd"] = fwd.cpu().numpy()
+    o["fwd"] = d_true
+    return c, o, g
+
+
+def test_green_parity_small(small):
+    c, o, g = small
+    for r in range(c.rec_ix.size):
+        assert rel(g["gh"][r], o["gh"][r]) <= GREEN_TOL, r
+    assert rel(g["gh"], o["gh"]) <= GREEN_TOL
+
+
+def test_hessian_parity_small(small):
+    c, o, g = small
+    assert g["mu"] == pytest.approx(o["mu"], rel=1e-5)
+    for k in range(c.freqs.size):
+        assert rel(g["Q"][k], o["Q"][k]) <= HESS_TOL, k
+    Q = g["Q"]
+    assert np.array_equal(Q, Q.conj().transpose(0, 2, 1))
+    d = np.einsum("kii->ki", Q)
+    assert np.all(d.imag == 0) and np.all(d.real > 0)
+
+
+def test_factor_parity_small(small):
+    c, o, g = small
+    L = g["L"].astype(np.complex128)
+    assert np.all(np.triu(L, 1) == 0)
+    d = np.einsum("kii->ki", L)
+    assert np.all(d.imag == 0) and np.all(d.real > 0)
+    Q = g["Q"].astype(np.complex128)
+    back = L @ L.conj().transpose(0, 2, 1)
+    for k in range(c.freqs.size):
+        assert rel(back[k], Q[k]) <= 1e-5, k
+        assert rel(L[k], o["L"][k]) <= 1e-3, k
+
+
+def test_forward_parity_small(small):
+    c, o, g = small
+    assert rel(g["fwd"], o["fwd"]) <= 1e-4
+
+
+def test_deblur_parity_small(small):
+    c, o, g = small
+    assert rel(g["mult"], o["mult"]) <= MULT_TOL
+    for s in range(g["mult"].shape[0]):
+        assert rel(g["mult"][s], o["mult"][s]) <= MULT_TOL, s
+    assert np.array_equal(g["mult_host"], g["mult"])
+
+
+def test_stats_small(small):
+    c, o, g = small
+    st = g["stats"]
+    assert st["pde_solves"] == c.rec_ix.size  # one Green solve per receiver (Table 2, direct)
+    assert st["deblur_sources"] == c.src_ix.size
+    assert st["green_ms"] > 0 and st["hessian_ms"] > 0 and st["factor_ms"] > 0 and st["deblur_ms"] > 0
+
+
+def test_mu_max_eig_small():
+    torch = _torch()
+    from paper_2512_16642_gb300 import egh
+
+    c = synth.case_tiny(nz=14, nx=20, nsponge=5, nrec=9, nt=120)
+    v32 = np.float32(c.vel_true)
+    grid = oracle.Grid(v32.astype(np.float64), c.dz, c.dx, c.nsponge, c.sponge_R)
+    H = oracle.hessian_gram(oracle.green_dtft(grid, c.rec_iz, c.rec_ix, c.freqs, c.dt, c.nt))
+    with _ctx(c) as ctx:
+        ctx.green(torch.from_numpy(v32).cuda())
+        mu = ctx.hessian(egh.EGH_MU_REL_MAXEIG, 1e-3)
+    assert mu == pytest.approx(oracle.mu_max_eig(H, 1e-3), rel=1e-3)
+
+
+def test_ragged_case():
+    """Several Gram tiles (70 receivers -> 140 real rows), a ragged receiver batch (16), a partial
+    transform chunk (nt 77, chunk 16), three Gram splits, 40 sources over two solve groups, data
+    length 300 != nt, odd grid sizes."""
+    c = synth.case_tiny(seed=11, nz=23, nx=71, nsponge=6, nrec=70, nt=77, dt=1e-3)
+    c["freqs"] = np.array([12.0, 25.0, 33.3])
+    rng = np.random.default_rng(5)
+    resid = synth.bandlimited_noise(rng, (40, 70, 300), c.dt, 5.0, 40.0)
+    o, g = _run_both(c, c.vel_true, resid=resid,
+                     ctx_kw=dict(batch_receivers=16, dft_chunk=16, gram_splits=3))
+    assert rel(g["gh"], o["gh"]) <= GREEN_TOL
+    for k in range(3):
+        assert rel(g["Q"][k], o["Q"][k]) <= HESS_TOL
+    assert rel(g["mult"], o["mult"]) <= MULT_TOL
+
+
+def test_single_receiver_single_frequency_two_steps():
+    c = synth.case_tiny(seed=3, nz=9, nx=9, nsponge=2, nrec=1, nt=2)
+    c["freqs"] = np.array([50.0])
+    resid = np.random.default_rng(1).standard_normal((3, 1, 5))
+    o, g = _run_both(c, c.vel_true, resid=resid)
+    assert rel(g["gh"], o["gh"]) <= GREEN_TOL
+    assert rel(g["Q"], o["Q"]) <= HESS_TOL
+    assert rel(g["mult"], o["mult"]) <= MULT_TOL
+
+
+def test_zero_record_is_not_positive_definite():
+    """nt = 1 records only the zero initial level: every transform and every Hessian is zero, so
+    with mu = 0 the first pivot fails and the status names frequency 0."""
+    torch = _torch()
+    from paper_2512_16642_gb300 import egh
+
+    c = synth.case_tiny(nz=8, nx=8, nsponge=2, nrec=3, nt=1)
+    with _ctx(c) as ctx:
+        ctx.green(torch.from_numpy(np.float32(c.vel_true)).cuda())
+        assert np.all(ctx.get_green() == 0)
+        assert ctx.hessian(egh.EGH_MU_ABS, 0.0) == 0.0
+        with pytest.raises(egh.EghError) as ei:
+            ctx.factor()
+        assert ei.value.status == egh.EGH_ENOTPD and ei.value.bad_freq == 0
+        r = torch.zeros((1, 3, 4), device="cuda")
+        with pytest.raises(egh.EghError) as ei:
+            ctx.deblur(r, torch.empty_like(r))
+        assert ei.value.status == egh.EGH_ESTATE
+
+
+def test_argument_and_state_errors():
+    torch = _torch()
+    from paper_2512_16642_gb300 import egh
+
+    c = synth.case_tiny(nz=8, nx=8, nsponge=2, nrec=3, nt=10)
+    with _ctx(c) as ctx:
+        with pytest.raises(egh.EghError) as ei:
+            ctx.hessian()
+        assert ei.value.status == egh.EGH_ESTATE
+        v = np.float32(c.vel_true).copy()
+        v[2, 3] = np.nan
+        with pytest.raises(egh.EghError) as ei:
+            ctx.green(torch.from_numpy(v).cuda())
+        assert ei.value.status == egh.EGH_EINVAL
+        fast = np.full_like(v, 9000.0)  # 9000 * 1e-3 * sqrt(2) / 10 = 1.27 > 0.78
+        with pytest.raises(egh.EghError) as ei:
+            ctx.green(fast)
+        assert ei.value.status == egh.EGH_EINVAL and "CFL" in str(ei.value)
+        ctx.green(np.float32(c.vel_true))  # host velocity
+        ctx.hessian()
+        ctx.factor()
+        r = torch.zeros((2, 3, 16), device="cuda")
+        with pytest.raises(egh.EghError) as ei:
+            ctx.deblur(r, np.zeros((2, 3, 16), np.float32))
+        assert ei.value.status == egh.EGH_EINVAL
+
+
+def test_layered_full_size_sampled():
+    """The 921x301 layered workload in the launch configuration the benchmark times (231 receivers,
+    4000 steps, 26 frequencies, default batch/chunk/splits): transforms of sampled receivers and
+    the Hessian entries among them (exact locality: entry (i, j) depends only on g^i, g^j) against
+    the oracle; mu against the mean of the diagonal; the deblur of all 115 sources checked by its
+    normwise backward error and by source-subset consistency."""
+    torch = _torch()
+    from paper_2512_16642_gb300 import egh
+
+    c = synth.case_layered()
+    v32 = np.float32(c.vel_start)
+    sample = np.array([0, 117, 230])
+    grid = oracle.Grid(v32.astype(np.float64), c.dz, c.dx, c.nsponge, c.sponge_R)
+    o_gh = oracle.green_dtft(grid, c.rec_iz[sample], c.rec_ix[sample], c.freqs, c.dt, c.nt,
+                             workers=3, threads_per_run=max(1, (oracle.default_workers()) // 3))
+    H = oracle.hessian_gram(o_gh)
+    rng = np.random.default_rng(9)
+    resid = synth.bandlimited_noise(rng, (c.src_ix.size, c.rec_ix.size, c.nt), c.dt, 2.0, 10.0)
+    r32 = resid.astype(np.float32)
+    with _ctx(c) as ctx:
+        ctx.green(torch.from_numpy(v32).cuda())
+        for t, r in enumerate(sample):
+            assert rel(ctx.get_green(int(r), 1)[0], o_gh[t]) <= GREEN_TOL, r
+        mu = ctx.hessian(egh.EGH_MU_REL_MEANDIAG, c.mu_alpha)
+        Q = ctx.get_hessian(False).astype(np.complex128)
+        sub = Q[:, sample][:, :, sample] - mu * np.eye(3)
+        for k in range(c.freqs.size):
+            assert rel(sub[k], H[k]) <= HESS_TOL, k
+        assert mu == pytest.approx(c.mu_alpha * np.mean(np.einsum("kii->ki", Q).real - mu), rel=1e-5)
+        ctx.factor()
+        rt = torch.from_numpy(r32).cuda()
+        X = torch.empty((c.freqs.size, c.rec_ix.size, c.src_ix.size), dtype=torch.complex64, device="cuda")
+        ctx.deblur_freq(rt, X)
+        D = oracle.dtft_traces(r32.astype(np.float64), c.freqs, c.dt)
+        Xh = X.cpu().numpy().astype(np.complex128)
+        for k in range(c.freqs.size):
+            res = np.linalg.norm(Q[k] @ Xh[k] - D[k])
+            bound = np.linalg.norm(Q[k], 2) * np.linalg.norm(Xh[k]) + np.linalg.norm(D[k])
+            assert res / bound <= 2e-5, k
+        mt = torch.empty_like(rt)
+        ctx.deblur(rt, mt)
+        part = torch.empty_like(rt[5:9])
+        ctx.deblur(rt[5:9].contiguous(), part)
+        torch.cuda.synchronize()
+        assert torch.equal(part, mt[5:9])
+        st = ctx.stats()
+        assert st["pde_solves"] == 231
