@@ -91,7 +91,7 @@ typedef struct {
     int32_t nfreq;
     const double *freq_hz; /* [nfreq], host */
     int32_t batch_receivers; /* receivers propagated together; 0 = library default */
-    int32_t dft_chunk;       /* time levels per on-the-fly transform chunk; 0 = default */
+    int32_t dft_chunk;       /* time levels per on-the-fly transform chunk: 32 or 64; 0 = 64 */
     int32_t gram_splits;     /* split of the grid sum in the Gram; 0 = default */
     int32_t reserved[5];     /* must be zero */
 } egh_config;
@@ -127,7 +127,9 @@ void egh_destroy(egh_ctx *ctx);
  * over the whole padded grid.  vel: [nz][nx] float32 velocity (m/s), host or
  * device.  EGH_EINVAL if a velocity is not positive and finite or the CFL
  * number vmax dt sqrt(1/dx^2 + 1/dz^2) exceeds 0.78 (eighth-order leapfrog
- * limit).  Invalidates any previous Hessian and factors. */
+ * limit); EGH_ETIMEOUT if a bounded device wait for staged data ran out
+ * (the context stays usable).  Blocks until the transforms are complete.
+ * Invalidates any previous Hessian and factors. */
 egh_status egh_green(egh_ctx *ctx, const float *vel, void *stream);
 
 /* Step (b): per-frequency Hessians Q_k = H_k + mu I (eq. Qmatrix) with

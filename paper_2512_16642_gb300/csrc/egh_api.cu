@@ -56,6 +56,7 @@ struct egh_ctx {
   double* dsum = nullptr;
   double* lmax = nullptr;
   float* vchk = nullptr;
+  int* d_err = nullptr;  // set by bounded device waits that ran out
   float* vel_stage = nullptr;
   float2* Dh = nullptr;
   size_t Dh_cap = 0;
@@ -180,7 +181,7 @@ float* slot(egh_ctx* ctx, int t) { return ctx->ring + (long long)(t % ctx->K) * 
 
 void free_all(egh_ctx* c) {
   void* ptrs[] = {c->c1, c->c3, c->ring, c->gh, c->part, c->Qh, c->Lh, c->tw, c->w_dev,
-                  c->rec_pts, c->status, c->dsum, c->lmax, c->vchk, c->vel_stage, c->Dh,
+                  c->rec_pts, c->status, c->dsum, c->lmax, c->vchk, c->d_err, c->vel_stage, c->Dh,
                   c->io_in, c->io_out};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -237,8 +238,8 @@ egh_status egh_create(const egh_config* cfg, egh_ctx** out) {
       return fail(nullptr, EGH_EINVAL, "frequency outside (0, 1/(2 dt))");
   if (c.batch_receivers < 0 || c.gram_splits < 0)
     return fail(nullptr, EGH_EINVAL, "batch_receivers and gram_splits must be >= 0");
-  if (c.dft_chunk != 0 && c.dft_chunk != 16 && c.dft_chunk != 32)
-    return fail(nullptr, EGH_EINVAL, "dft_chunk must be 0, 16 or 32");
+  if (c.dft_chunk != 0 && c.dft_chunk != 32 && c.dft_chunk != 64)
+    return fail(nullptr, EGH_EINVAL, "dft_chunk must be 0, 32 or 64");
 
   ctx = new (std::nothrow) egh_ctx();
   if (!ctx) return fail(nullptr, EGH_ENOMEM, "host allocation failed");
@@ -250,7 +251,7 @@ egh_status egh_create(const egh_config* cfg, egh_ctx** out) {
   ctx->rec_ix.assign(c.rec_ix, c.rec_ix + c.nrec);
   ctx->freqs.assign(c.freq_hz, c.freq_hz + c.nfreq);
   ctx->B = c.batch_receivers ? std::min(c.batch_receivers, c.nrec) : std::min(c.nrec, 8);
-  ctx->K = c.dft_chunk ? c.dft_chunk : 32;
+  ctx->K = c.dft_chunk ? c.dft_chunk : 64;
 
   Layout& L = ctx->L;
   L.nz = c.nz; L.nx = c.nx; L.ns = c.nsponge;
@@ -271,7 +272,6 @@ egh_status egh_create(const egh_config* cfg, egh_ctx** out) {
     ctx->splits = (int)std::max(1LL, s);
   }
 
-  ctx->S.c0 = (float)(kC8[0] * (1.0 / (c.dx * c.dx) + 1.0 / (c.dz * c.dz)));
   for (int k = 0; k < 4; ++k) {
     ctx->S.cx[k] = (float)(kC8[k + 1] / (c.dx * c.dx));
     ctx->S.cz[k] = (float)(kC8[k + 1] / (c.dz * c.dz));
@@ -317,11 +317,13 @@ egh_status egh_create(const egh_config* cfg, egh_ctx** out) {
   ALLOC(ctx->dsum, sizeof(double), "dsum");
   ALLOC(ctx->lmax, (size_t)c.nfreq * sizeof(double), "lmax");
   ALLOC(ctx->vchk, 2 * sizeof(float), "vchk");
+  ALLOC(ctx->d_err, sizeof(int), "error flag");
   ALLOC(ctx->vel_stage, (size_t)c.nz * c.nx * sizeof(float), "velocity staging");
 #undef ALLOC
   auto init = [&]() -> egh_status {
     CK(cudaMemset(ctx->c1, 0, F * sizeof(float)));
     CK(cudaMemset(ctx->c3, 0, F * sizeof(float)));
+    CK(cudaMemset(ctx->d_err, 0, sizeof(int)));
     std::vector<int> rp(c.nrec);
     for (int r = 0; r < c.nrec; ++r)
       rp[r] = (int)(L.org + (long long)(c.rec_iz[r] + c.nsponge) * L.PX + (c.rec_ix[r] + c.nsponge));
@@ -378,7 +380,7 @@ egh_status egh_green(egh_ctx* ctx, const float* vel, void* stream_) {
     auto chunk_end = [&](int t) -> egh_status {
       if (t % K == K - 1 || t == nt - 1) {
         CK(launch_dft_chunk(ctx->ring, slot_stride, L.F, L, ctx->tw, ctx->nf, t - t % K,
-                            t % K + 1, K, nb, ctx->gh, b0, stream));
+                            t % K + 1, K, nb, ctx->gh, b0, ctx->d_err, stream));
       }
       return EGH_OK;
     };
@@ -397,6 +399,13 @@ egh_status egh_green(egh_ctx* ctx, const float* vel, void* stream_) {
   }
   CK(cudaEventRecord(ctx->ev[1], stream));
   ctx->ev_rec[0] = true;
+  int derr = 0;
+  CK(cudaMemcpyAsync(&derr, ctx->d_err, sizeof derr, cudaMemcpyDeviceToHost, stream));
+  CK(cudaStreamSynchronize(stream));
+  if (derr) {
+    CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), stream));
+    return fail(ctx, EGH_ETIMEOUT, "a bounded wait for staged snapshots ran out in the transform");
+  }
   ctx->st.pde_solves = ctx->nrec;
   ctx->st.point_steps = (long long)ctx->nrec * nt * L.NZ * L.NX;
   ctx->state = ST_GREEN;

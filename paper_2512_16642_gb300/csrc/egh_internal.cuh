@@ -23,7 +23,6 @@ void count_launches(int n);
 long long launches_so_far();
 
 struct Stencil {
-  float c0;     // centre weight c_0 (1/dx^2 + 1/dz^2)
   float cx[4];  // c_k / dx^2, k = 1..4
   float cz[4];  // c_k / dz^2
 };
@@ -49,7 +48,8 @@ cudaError_t launch_record(const float* u, long long fstride, const int* rec_pts,
                           float* traces, int nt, int t, cudaStream_t st);
 cudaError_t launch_dft_chunk(const float* ring, long long slot_stride, long long fstride,
                              const Layout& L, const float2* tw, int nf, int n0, int kcount, int K,
-                             int nb, float* gh, int rec0, cudaStream_t st);
+                             int nb, float* gh, int rec0, int* err, cudaStream_t st);
+size_t dft_chunk_smem(int K, int nf);
 
 // ---- gram.cu ----------------------------------------------------------------------------------
 __host__ __device__ int gram_tiles(int nrec);

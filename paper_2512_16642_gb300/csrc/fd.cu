@@ -100,65 +100,106 @@ cudaError_t launch_build_coef(const float* vel, const Layout& L, double dz, doub
 }
 
 // ---------------------------------------------------------------------------------------------
-// One leapfrog step for a batch of receivers.  Each warp owns 32 columns and marches down TZ rows,
+// One leapfrog step for a batch of receivers.  Each warp owns 32 columns and marches down FD_TZ
+// rows for RB receivers at once (the coefficients of a point are loaded once for all of them),
 // keeping the nine z-neighbours of its column in registers; the x-neighbours come from a
-// 40-float row staged in shared memory (32 + 4 halo on each side).  Reads of guard rows and
-// padding columns return the zero boundary, so there is no bounds test on loads.
+// 40-float row staged in shared memory (32 + 4 halo on each side).  Rows are processed in groups
+// of FD_U whose loads are all issued before the group is computed, so that many independent
+// loads are in flight per warp.  Reads of guard rows and padding columns return the zero
+// boundary, so there is no bounds test on loads; rows past the warp's range are not loaded.
 // ---------------------------------------------------------------------------------------------
 constexpr int FD_WARPS = 4;
-constexpr int FD_TZ = 32;
+constexpr int FD_TZ = 16;
+constexpr int FD_U = 4;
 
+template <int RB>
 __global__ void __launch_bounds__(32 * FD_WARPS)
     k_fd_step(const float* __restrict__ ucur, const float* __restrict__ uprev,
               float* __restrict__ unext, const float* __restrict__ c1,
               const float* __restrict__ c3, int NZ, int NX, int PX, long long org,
-              long long fstride, Stencil S) {
-  __shared__ float srow[FD_WARPS][40];
+              long long fstride, Stencil S, int nb) {
+  __shared__ float srow[FD_WARPS][RB][40];
   const int lane = threadIdx.x;
   const int w = threadIdx.y;
   const int x0 = blockIdx.x * 32;
   const int x = x0 + lane;
   const int z0 = (blockIdx.y * FD_WARPS + w) * FD_TZ;
   if (z0 >= NZ) return;  // whole warp leaves; only warp-level synchronisation below
-  const long long boff = (long long)blockIdx.z * fstride + org;
-  const float* __restrict__ uc = ucur + boff;
-  const float* __restrict__ up = uprev + boff;
-  float* __restrict__ un = unext + boff;
+  const int b0 = blockIdx.z * RB;
+  const float* uc[RB];
+  const float* up[RB];
+  float* un[RB];
+#pragma unroll
+  for (int r = 0; r < RB; ++r) {
+    // a partial last group repeats its last receiver (same values written twice)
+    const long long boff = (long long)min(b0 + r, nb - 1) * fstride + org;
+    uc[r] = ucur + boff;
+    up[r] = uprev + boff;
+    un[r] = unext + boff;
+  }
   const float* __restrict__ k1 = c1 + org;
   const float* __restrict__ k3 = c3 + org;
-  float* row = srow[w];
+  const bool halo = lane < 4 || lane >= 28;
+  const int hcol = lane < 4 ? x0 - 4 + lane : x0 + 4 + lane;
+  const int hslot = lane < 4 ? lane : lane + 8;
 
-  float q[9];
+  float q[RB][9];
 #pragma unroll
-  for (int i = 0; i < 8; ++i) q[i + 1] = uc[(long long)(z0 - 4 + i) * PX + x];
+  for (int r = 0; r < RB; ++r)
+#pragma unroll
+    for (int i = 0; i < 8; ++i) q[r][i + 1] = uc[r][(long long)(z0 - 4 + i) * PX + x];
   const int zend = min(z0 + FD_TZ, NZ);
-  for (int z = z0; z < zend; ++z) {
+  for (int zg = z0; zg < zend; zg += FD_U) {
+    float qn[RB][FD_U], hv[RB][FD_U], uo[RB][FD_U], a1[FD_U], a3[FD_U];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) q[i] = q[i + 1];
-    const long long rz = (long long)z * PX;
-    q[8] = uc[rz + (long long)4 * PX + x];
-    row[lane + 4] = q[4];
-    if (lane < 4) {
-      row[lane] = uc[rz + x0 - 4 + lane];
-    } else if (lane >= 28) {
-      row[lane + 8] = uc[rz + x0 + 4 + lane];
+    for (int i = 0; i < FD_U; ++i) {
+      if (zg + i < zend) {
+        const long long rz = (long long)(zg + i) * PX;
+        a1[i] = k1[rz + x];
+        a3[i] = k3[rz + x];
+#pragma unroll
+        for (int r = 0; r < RB; ++r) {
+          qn[r][i] = uc[r][rz + (long long)4 * PX + x];
+          uo[r][i] = up[r][rz + x];
+          hv[r][i] = halo ? uc[r][rz + hcol] : 0.f;
+        }
+      }
     }
-    __syncwarp();
-    if (x < NX) {
-      float lap = S.c0 * q[4];
-      lap = fmaf(S.cz[0], q[3] + q[5], lap);
-      lap = fmaf(S.cz[1], q[2] + q[6], lap);
-      lap = fmaf(S.cz[2], q[1] + q[7], lap);
-      lap = fmaf(S.cz[3], q[0] + q[8], lap);
-      lap = fmaf(S.cx[0], row[lane + 3] + row[lane + 5], lap);
-      lap = fmaf(S.cx[1], row[lane + 2] + row[lane + 6], lap);
-      lap = fmaf(S.cx[2], row[lane + 1] + row[lane + 7], lap);
-      lap = fmaf(S.cx[3], row[lane + 0] + row[lane + 8], lap);
-      const long long p = rz + x;
-      const float uo = up[p];
-      un[p] = fmaf(k3[p], lap, fmaf(k1[p], q[4] - uo, uo));
+#pragma unroll
+    for (int i = 0; i < FD_U; ++i) {
+      if (zg + i < zend) {
+        const long long p = (long long)(zg + i) * PX + x;
+#pragma unroll
+        for (int r = 0; r < RB; ++r) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) q[r][j] = q[r][j + 1];
+          q[r][8] = qn[r][i];
+          srow[w][r][lane + 4] = q[r][4];
+          if (halo) srow[w][r][hslot] = hv[r][i];
+        }
+        __syncwarp();
+        if (x < NX) {
+#pragma unroll
+          for (int r = 0; r < RB; ++r) {
+            // Laplacian as sum_k c_k [(u_{+k} - u) + (u_{-k} - u)] (c_0 = -2 sum_k c_k):
+            // neighbour differences of a well-sampled field are exact in float32, so the large
+            // cancelling terms of c_0 u + sum_k c_k (u_{+k} + u_{-k}) never form.
+            const float* row = srow[w][r];
+            const float u0 = q[r][4];
+            float lap = S.cz[0] * ((q[r][3] - u0) + (q[r][5] - u0));
+            lap = fmaf(S.cz[1], (q[r][2] - u0) + (q[r][6] - u0), lap);
+            lap = fmaf(S.cz[2], (q[r][1] - u0) + (q[r][7] - u0), lap);
+            lap = fmaf(S.cz[3], (q[r][0] - u0) + (q[r][8] - u0), lap);
+            lap = fmaf(S.cx[0], (row[lane + 3] - u0) + (row[lane + 5] - u0), lap);
+            lap = fmaf(S.cx[1], (row[lane + 2] - u0) + (row[lane + 6] - u0), lap);
+            lap = fmaf(S.cx[2], (row[lane + 1] - u0) + (row[lane + 7] - u0), lap);
+            lap = fmaf(S.cx[3], (row[lane + 0] - u0) + (row[lane + 8] - u0), lap);
+            un[r][p] = fmaf(a3[i], lap, fmaf(a1[i], u0 - uo[r][i], uo[r][i]));
+          }
+        }
+        __syncwarp();
+      }
     }
-    __syncwarp();
   }
 }
 
@@ -166,10 +207,18 @@ cudaError_t launch_fd_step(const float* ucur, const float* uprev, float* unext, 
                            const float* c3, const Layout& L, const Stencil& S, int nb,
                            long long fstride, cudaStream_t st) {
   dim3 block(32, FD_WARPS);
-  dim3 grid(L.PX / 32, (L.NZ + FD_WARPS * FD_TZ - 1) / (FD_WARPS * FD_TZ), nb);
-  count_launches(1);
-  k_fd_step<<<grid, block, 0, st>>>(ucur, uprev, unext, c1, c3, L.NZ, L.NX, L.PX, L.org, fstride,
-                                    S);
+  const int rows = (L.NZ + FD_WARPS * FD_TZ - 1) / (FD_WARPS * FD_TZ);
+  if (nb >= 2) {
+    dim3 grid(L.PX / 32, rows, (nb + 1) / 2);
+    count_launches(1);
+    k_fd_step<2><<<grid, block, 0, st>>>(ucur, uprev, unext, c1, c3, L.NZ, L.NX, L.PX, L.org,
+                                         fstride, S, nb);
+  } else {
+    dim3 grid(L.PX / 32, rows, nb);
+    count_launches(1);
+    k_fd_step<1><<<grid, block, 0, st>>>(ucur, uprev, unext, c1, c3, L.NZ, L.NX, L.PX, L.org,
+                                         fstride, S, nb);
+  }
   return cudaGetLastError();
 }
 
@@ -215,66 +264,156 @@ cudaError_t launch_record(const float* u, long long fstride, const int* rec_pts,
 // ---------------------------------------------------------------------------------------------
 // On-the-fly transform, one chunk of kcount <= K consecutive levels n0 .. n0+kcount-1 (ring slots
 // 0 .. kcount-1):  gh[rec0+b][k][re/im][p] += sum_j tw[n0+j][k] * u^{n0+j}[b][p].
-// Each thread owns two adjacent points; the chunk's twiddles sit in shared memory.
+// A block owns DT_P points of one receiver.  One thread stages the chunk's rows of those points
+// into shared memory with 1-D bulk (TMA) copies completing on an mbarrier; the chunk's twiddles
+// are staged alongside.  Each thread then owns two adjacent points and keeps the accumulators of
+// DT_NF frequencies in registers (several passes when nf > DT_NF), adding them into gh once per
+// chunk.  The mbarrier wait is bounded: on expiry the block records an error flag and leaves.
 // ---------------------------------------------------------------------------------------------
+constexpr int DT_P = 256;       // points per block
+constexpr int DT_THREADS = 128; // two points per thread
+constexpr int DT_NF = 26;       // frequencies per register pass
+constexpr long long kWaitLimit = 1LL << 26;  // mbarrier polls before giving up
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned bytes,
+                                         unsigned bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
 template <int K>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(DT_THREADS)
     k_dft_chunk(const float* __restrict__ ring, long long slot_stride, long long fstride,
                 long long org, const float2* __restrict__ tw, int nf, int n0, int kcount,
-                long long G, float* __restrict__ gh, int rec0) {
-  extern __shared__ float2 stw[];  // [K][nf]
-  for (int i = threadIdx.x; i < K * nf; i += blockDim.x)
-    stw[i] = (i < kcount * nf) ? tw[(long long)n0 * nf + i] : make_float2(0.f, 0.f);
-  __syncthreads();
+                long long G, float* __restrict__ gh, int rec0, int* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char dsm[];
+  float* U = reinterpret_cast<float*>(dsm);                      // [K][DT_P]
+  float2* T = reinterpret_cast<float2*>(dsm + sizeof(float) * K * DT_P);  // [K][nf]
+  __shared__ __align__(8) unsigned long long bar;
+  const int tid = threadIdx.x;
   const int b = blockIdx.y;
-  const long long p = 2 * ((long long)blockIdx.x * blockDim.x + threadIdx.x);
-  if (p >= G) return;
-  const float* src = ring + (long long)b * fstride + org + p;
-  float2 s[K];
-#pragma unroll
-  for (int j = 0; j < K; ++j)
-    s[j] = (j < kcount) ? *reinterpret_cast<const float2*>(src + j * slot_stride)
-                        : make_float2(0.f, 0.f);
-  float* g = gh + (long long)(rec0 + b) * nf * 2 * G + p;
-  for (int k = 0; k < nf; ++k) {
-    float ar0 = 0.f, ai0 = 0.f, ar1 = 0.f, ai1 = 0.f;
-#pragma unroll
-    for (int j = 0; j < K; ++j) {
-      const float2 w = stw[j * nf + k];
-      ar0 = fmaf(w.x, s[j].x, ar0);
-      ai0 = fmaf(w.y, s[j].x, ai0);
-      ar1 = fmaf(w.x, s[j].y, ar1);
-      ai1 = fmaf(w.y, s[j].y, ai1);
-    }
-    float2* gre = reinterpret_cast<float2*>(g + (long long)k * 2 * G);
-    float2* gim = reinterpret_cast<float2*>(g + (long long)k * 2 * G + G);
-    float2 r = *gre;
-    r.x += ar0;
-    r.y += ar1;
-    *gre = r;
-    float2 m = *gim;
-    m.x += ai0;
-    m.y += ai1;
-    *gim = m;
+  const long long p0 = (long long)blockIdx.x * DT_P;
+  const unsigned ubar = smem_u32(&bar);
+  if (tid == 0) {
+    mbar_init(ubar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  __syncthreads();
+  if (tid == 0) {
+    mbar_expect_tx(ubar, (unsigned)(kcount * DT_P * sizeof(float)));
+    const float* src = ring + (long long)b * fstride + org + p0;
+    for (int j = 0; j < kcount; ++j)
+      bulk_g2s(smem_u32(U + j * DT_P), src + j * slot_stride, DT_P * sizeof(float), ubar);
+  }
+  for (int i = tid; i < kcount * nf; i += DT_THREADS) T[i] = tw[(long long)n0 * nf + i];
+  long long polls = 0;
+  while (!mbar_try_wait(ubar, 0)) {
+    if (++polls > kWaitLimit) {
+      atomicExch(err, 1);
+      break;
+    }
+  }
+  __syncthreads();
+  if (polls > kWaitLimit) {
+    // copies may still be landing in shared memory; wait for them (bounded) before leaving
+    for (long long i = 0; i < kWaitLimit && !mbar_try_wait(ubar, 0); ++i) {
+    }
+    return;
+  }
+  const int lp = 2 * tid;
+  float* g = gh + (long long)(rec0 + b) * nf * 2 * G + p0 + lp;
+  for (int f0 = 0; f0 < nf; f0 += DT_NF) {
+    const int fn = min(DT_NF, nf - f0);
+    float ar[DT_NF][2], ai[DT_NF][2];
+#pragma unroll
+    for (int f = 0; f < DT_NF; ++f) ar[f][0] = ar[f][1] = ai[f][0] = ai[f][1] = 0.f;
+#pragma unroll 4
+    for (int j = 0; j < kcount; ++j) {
+      const float2 s = *reinterpret_cast<const float2*>(U + j * DT_P + lp);
+      const float2* tj = T + j * nf + f0;
+#pragma unroll
+      for (int f = 0; f < DT_NF; ++f) {
+        if (f < fn) {
+          const float2 w = tj[f];
+          ar[f][0] = fmaf(w.x, s.x, ar[f][0]);
+          ai[f][0] = fmaf(w.y, s.x, ai[f][0]);
+          ar[f][1] = fmaf(w.x, s.y, ar[f][1]);
+          ai[f][1] = fmaf(w.y, s.y, ai[f][1]);
+        }
+      }
+    }
+#pragma unroll
+    for (int f = 0; f < DT_NF; ++f) {
+      if (f < fn) {
+        float2* gre = reinterpret_cast<float2*>(g + (long long)(f0 + f) * 2 * G);
+        float2* gim = reinterpret_cast<float2*>(g + (long long)(f0 + f) * 2 * G + G);
+        float2 r = *gre;
+        r.x += ar[f][0];
+        r.y += ar[f][1];
+        *gre = r;
+        float2 m = *gim;
+        m.x += ai[f][0];
+        m.y += ai[f][1];
+        *gim = m;
+      }
+    }
+  }
+}
+
+size_t dft_chunk_smem(int K, int nf) {
+  return sizeof(float) * (size_t)K * DT_P + sizeof(float2) * (size_t)K * nf;
 }
 
 cudaError_t launch_dft_chunk(const float* ring, long long slot_stride, long long fstride,
                              const Layout& L, const float2* tw, int nf, int n0, int kcount, int K,
-                             int nb, float* gh, int rec0, cudaStream_t st) {
-  const long long threads = L.G / 2;
-  dim3 grid((unsigned)((threads + 255) / 256), nb);
-  const size_t smem = sizeof(float2) * (size_t)K * nf;
+                             int nb, float* gh, int rec0, int* err, cudaStream_t st) {
+  if (L.G % DT_P != 0) return cudaErrorInvalidValue;
+  dim3 grid((unsigned)(L.G / DT_P), nb);
+  const size_t smem = dft_chunk_smem(K, nf);
+  cudaError_t e = cudaSuccess;
   switch (K) {
-    case 16:
-      count_launches(1);
-      k_dft_chunk<16><<<grid, 256, smem, st>>>(ring, slot_stride, fstride, L.org, tw, nf, n0,
-                                               kcount, L.G, gh, rec0);
-      break;
     case 32:
+      e = cudaFuncSetAttribute(k_dft_chunk<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem);
+      if (e != cudaSuccess) return e;
       count_launches(1);
-      k_dft_chunk<32><<<grid, 256, smem, st>>>(ring, slot_stride, fstride, L.org, tw, nf, n0,
-                                               kcount, L.G, gh, rec0);
+      k_dft_chunk<32><<<grid, DT_THREADS, smem, st>>>(ring, slot_stride, fstride, L.org, tw, nf,
+                                                      n0, kcount, L.G, gh, rec0, err);
+      break;
+    case 64:
+      e = cudaFuncSetAttribute(k_dft_chunk<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem);
+      if (e != cudaSuccess) return e;
+      count_launches(1);
+      k_dft_chunk<64><<<grid, DT_THREADS, smem, st>>>(ring, slot_stride, fstride, L.org, tw, nf,
+                                                      n0, kcount, L.G, gh, rec0, err);
       break;
     default:
       return cudaErrorInvalidValue;

@@ -59,7 +59,7 @@ def test_version_and_status_strings(lib):
 
 @pytest.mark.parametrize("bad", [
     dict(nz=0), dict(dx=0.0), dict(dt=-1.0), dict(nt=0), dict(rec_ix=[0, 200]),
-    dict(freq_hz=[600.0]), dict(freq_hz=[0.0]), dict(sponge_R=1.5), dict(dft_chunk=7),
+    dict(freq_hz=[600.0]), dict(freq_hz=[0.0]), dict(sponge_R=1.5), dict(dft_chunk=7), dict(dft_chunk=16),
     dict(freq_hz=np.arange(1, 66) * 1.0),
 ])
 def test_create_rejects_bad_config(lib, bad):

@@ -162,14 +162,14 @@ def test_mu_max_eig_small():
 
 def test_ragged_case():
     """Several Gram tiles (70 receivers -> 140 real rows), a ragged receiver batch (16), a partial
-    transform chunk (nt 77, chunk 16), three Gram splits, 40 sources over two solve groups, data
+    transform chunk (nt 77, chunk 32), three Gram splits, 40 sources over two solve groups, data
     length 300 != nt, odd grid sizes."""
     c = synth.case_tiny(seed=11, nz=23, nx=71, nsponge=6, nrec=70, nt=77, dt=1e-3)
     c["freqs"] = np.array([12.0, 25.0, 33.3])
     rng = np.random.default_rng(5)
     resid = synth.bandlimited_noise(rng, (40, 70, 300), c.dt, 5.0, 40.0)
     o, g = _run_both(c, c.vel_true, resid=resid,
-                     ctx_kw=dict(batch_receivers=16, dft_chunk=16, gram_splits=3))
+                     ctx_kw=dict(batch_receivers=16, dft_chunk=32, gram_splits=3))
     assert rel(g["gh"], o["gh"]) <= GREEN_TOL
     for k in range(3):
         assert rel(g["Q"][k], o["Q"][k]) <= HESS_TOL
