@@ -178,6 +178,32 @@ egh_status egh_get_green(egh_ctx *ctx, int32_t r0, int32_t nr, void *host_out);
  * upper triangle zero) to host_out ([nfreq][nrec][nrec] complex64).  Blocks. */
 egh_status egh_get_hessian(egh_ctx *ctx, int32_t factored, void *host_out);
 
+/* Allocation-free variant of the Hessian Gram.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc -- a process
+ * whose device memory is already reserved by another allocator (a framework's
+ * caching pool, an arena sized at start-up), or a service loop that forbids
+ * device allocation and its implicit synchronisation once running.  It
+ * computes, with the kernels of egh_hessian,
+ *   H[k][i][j] = sum_{p<npts} (gh[i][k][0][p] + i gh[i][k][1][p])
+ *                            (gh[j][k][0][p] - i gh[j][k][1][p])
+ * (no mu added), from caller-owned device buffers:
+ *   gh  [nrec][nfreq][2][npts] float32 planes (re, im), 16-byte aligned,
+ *       npts a positive multiple of 16 (pad with zeros);
+ *   H   [nfreq][nrec][nrec] complex64 output, 8-byte aligned.
+ * It allocates nothing: its split-sum workspace is a fixed 32 MiB array in
+ * device memory defined by the library (every GPU that loads the library
+ * holds it until the process exits), which limits nfreq x (number of 32-
+ * receiver tile pairs, t (t + 1) / 2 with t = ceil(nrec / 32)) to 2048; larger
+ * sizes return EGH_EINVAL with a message in egh_last_error(NULL).  The first
+ * call on a device, made while that device is current, looks up the array's
+ * device address; make that first call before any stream capture.  All calls
+ * share the one array and each overwrites what it uses, so calls that overlap
+ * on the GPU (different streams, or different host threads) race and must be
+ * ordered by the caller.  Work is queued on `stream`; the call returns
+ * without waiting. */
+egh_status egh_gram_noalloc(const float *gh, int32_t nrec, int32_t nfreq, int64_t npts, void *H,
+                            void *stream);
+
 /* Fills *out with the last timings and counters.  Blocks on pending events. */
 egh_status egh_get_stats(egh_ctx *ctx, egh_stats *out);
 

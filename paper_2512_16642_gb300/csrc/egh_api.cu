@@ -34,6 +34,7 @@ long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
 namespace egh {
 void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+void set_context_free_error(const std::string& msg) { g_create_error = msg; }
 }  // namespace egh
 
 struct egh_ctx {

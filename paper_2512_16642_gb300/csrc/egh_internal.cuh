@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <string>
 
 namespace egh {
 
@@ -21,6 +22,8 @@ constexpr int GUARD = 4;  // stencil radius of the eighth-order Laplacian
 // Counts kernel launches (every launch_* wrapper adds its launches); read by egh_get_stats.
 void count_launches(int n);
 long long launches_so_far();
+// Message returned by egh_last_error(NULL) for calls that have no context.
+void set_context_free_error(const std::string& msg);
 
 struct Stencil {
   float cx[4];  // c_k / dx^2, k = 1..4

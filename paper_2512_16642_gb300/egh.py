@@ -64,6 +64,7 @@ _SIGS = {
     "egh_get_green": ([_vp, ctypes.c_int32, ctypes.c_int32, _vp], ctypes.c_int),
     "egh_get_hessian": ([_vp, ctypes.c_int32, _vp], ctypes.c_int),
     "egh_get_stats": ([_vp, ctypes.POINTER(egh_stats)], ctypes.c_int),
+    "egh_gram_noalloc": ([_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _vp, _vp], ctypes.c_int),
     "egh_last_error": ([_vp], ctypes.c_char_p),
     "egh_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "egh_version": ([], ctypes.c_int32),
@@ -209,6 +210,14 @@ def egh_get_stats(ctx):
     st = egh_stats()
     _check(load().egh_get_stats(ctx, ctypes.byref(st)), ctx)
     return st.as_dict()
+
+
+def egh_gram_noalloc(gh, nrec, nfreq, npts, H, stream=None):
+    """Gram of caller-owned device transforms into caller-owned H, allocating nothing."""
+    pg, cg = _ptr(gh)
+    ph, chh = _ptr(H)
+    _check(load().egh_gram_noalloc(pg, int(nrec), int(nfreq), int(npts), ph, _stream(stream, cg or chh)),
+           None)
 
 
 def egh_version():

@@ -1,0 +1,84 @@
+"""egh_gram_noalloc, the allocation-free Gram entry point, against egh_hessian.
+
+For callers that cannot call cudaMalloc (device memory already reserved by another allocator,
+or a running service loop that forbids allocation), egh_gram_noalloc computes the per-frequency
+Gram from caller-owned device buffers with a fixed scratch array inside the library.  This test
+compares it, through the C ABI, with the Hessian of the regular entry point (mu = 0) on the same
+Green-function transforms, within the Hessian tolerance of the parity tests, on two calls in a
+row (the second on a smaller problem, so stale scratch from the first would show)."""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+HESS_TOL = 1e-4
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _planar(gh, npts):
+    nr, nf = gh.shape[:2]
+    flat = gh.reshape(nr, nf, -1)
+    out = np.zeros((nr, nf, 2, npts), np.float32)
+    out[:, :, 0, :flat.shape[2]] = flat.real
+    out[:, :, 1, :flat.shape[2]] = flat.imag
+    return out
+
+
+def test_gram_noalloc_matches_hessian_two_calls():
+    import torch
+
+    from paper_2512_16642_gb300 import egh
+
+    c = synth.case_tiny(seed=13, nz=20, nx=60, nsponge=6, nrec=70, nt=150)
+    c["freqs"] = np.array([8.0, 17.5, 30.0, 44.0])
+    with egh.Context(c.nz, c.nx, c.dz, c.dx, c.nsponge, c.sponge_R, c.dt, c.nt, c.rec_iz, c.rec_ix,
+                     c.freqs) as ctx:
+        ctx.green(torch.from_numpy(np.float32(c.vel_true)).cuda())
+        assert ctx.hessian(egh.EGH_MU_ABS, 0.0) == 0.0
+        ref = ctx.get_hessian(False).astype(np.complex128)
+        gh = ctx.get_green()
+    nr, nf = gh.shape[:2]
+    npts = (gh[0, 0].size + 15) // 16 * 16
+    d_gh = torch.from_numpy(_planar(gh, npts)).cuda()
+
+    # call 1: all 70 receivers (3 tiles of 32)
+    H = torch.full((nf, nr, nr), float("nan"), dtype=torch.complex64, device="cuda")
+    egh.egh_gram_noalloc(d_gh, nr, nf, npts, H)
+    torch.cuda.synchronize()
+    h = H.cpu().numpy().astype(np.complex128)
+    for k in range(nf):
+        assert rel(h[k], ref[k]) <= HESS_TOL, k
+
+    # call 2: the first 20 receivers only
+    sub = 20
+    d_sub = d_gh[:sub].contiguous()
+    H2 = torch.full((nf, sub, sub), float("nan"), dtype=torch.complex64, device="cuda")
+    egh.egh_gram_noalloc(d_sub, sub, nf, npts, H2)
+    torch.cuda.synchronize()
+    h2 = H2.cpu().numpy().astype(np.complex128)
+    for k in range(nf):
+        assert rel(h2[k], ref[k][:sub, :sub]) <= HESS_TOL, k
+
+
+def test_gram_noalloc_rejects_what_it_cannot_do():
+    import torch
+
+    from paper_2512_16642_gb300 import egh
+
+    H = torch.empty((64, 8, 8), dtype=torch.complex64, device="cuda")
+    big = torch.empty((16,), device="cuda")
+    with pytest.raises(egh.EghError) as ei:  # 1000 receivers x 64 frequencies exceed the scratch
+        egh.egh_gram_noalloc(big, 1000, 64, 16, H)
+    assert ei.value.status == egh.EGH_EINVAL and "scratch" in str(ei.value)
+    host = np.zeros((8, 1, 2, 16), np.float32)
+    with pytest.raises(egh.EghError) as ei:  # host memory is refused before any launch
+        egh.egh_gram_noalloc(host, 8, 1, 16, H)
+    assert ei.value.status == egh.EGH_EINVAL
+    with pytest.raises(egh.EghError) as ei:
+        egh.egh_gram_noalloc(big, 1, 1, 10, H)
+    assert ei.value.status == egh.EGH_EINVAL
