@@ -48,9 +48,13 @@ struct egh_ctx {
   Layout L{};
   Stencil S{};
   // device state
-  float *c1 = nullptr, *c3 = nullptr, *ring = nullptr, *gh = nullptr, *part = nullptr;
+  float2 *coef = nullptr, *ring = nullptr;  // (c1, c3) per point; paired levels [2K][B/2][F]
+  float *gh = nullptr, *part = nullptr;
   float2 *Qh = nullptr, *Lh = nullptr, *tw = nullptr;
+  float4* tw4 = nullptr;  // [nt][nf] (cos, cos, -sin, -sin) for the paired transform
   int tw_len = 0;
+  cudaStream_t side = nullptr;                 // the transform's stream inside egh_green
+  cudaEvent_t fd_done[2] = {}, dft_done[2] = {}, ev_side = nullptr;
   float* w_dev = nullptr;
   int* rec_pts = nullptr;
   int* status = nullptr;
@@ -173,21 +177,26 @@ egh_status prepare_model(egh_ctx* ctx, const float* vel, cudaStream_t stream) {
     snprintf(buf, sizeof buf, "CFL number %.4f exceeds %.2f (vmax %.1f m/s)", cfl, kCflMax, h[0]);
     return fail(ctx, EGH_EINVAL, buf);
   }
-  CK(launch_build_coef(dv, ctx->L, ctx->dz, ctx->dx, ctx->dt, ctx->R, ctx->vchk, ctx->c1, ctx->c3,
-                       stream));
+  CK(launch_build_coef(dv, ctx->L, ctx->dz, ctx->dx, ctx->dt, ctx->R, ctx->vchk, ctx->coef, stream));
   return EGH_OK;
 }
 
-float* slot(egh_ctx* ctx, int t) { return ctx->ring + (long long)(t % ctx->K) * ctx->B * ctx->L.F; }
+// Ring slot of level t: [2K][B/2][F] float2.
+float2* slot(egh_ctx* ctx, int t) {
+  return ctx->ring + (long long)(t % (2 * ctx->K)) * ((ctx->B + 1) / 2) * ctx->L.F;
+}
 
 void free_all(egh_ctx* c) {
-  void* ptrs[] = {c->c1, c->c3, c->ring, c->gh, c->part, c->Qh, c->Lh, c->tw, c->w_dev,
+  void* ptrs[] = {c->coef, c->ring, c->tw4, c->gh, c->part, c->Qh, c->Lh, c->tw, c->w_dev,
                   c->rec_pts, c->status, c->dsum, c->lmax, c->vchk, c->d_err, c->vel_stage, c->Dh,
                   c->io_in, c->io_out};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t& e : c->ev)
     if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : {c->fd_done[0], c->fd_done[1], c->dft_done[0], c->dft_done[1], c->ev_side})
+    if (e) cudaEventDestroy(e);
+  if (c->side) cudaStreamDestroy(c->side);
 }
 
 }  // namespace
@@ -239,8 +248,9 @@ egh_status egh_create(const egh_config* cfg, egh_ctx** out) {
       return fail(nullptr, EGH_EINVAL, "frequency outside (0, 1/(2 dt))");
   if (c.batch_receivers < 0 || c.gram_splits < 0)
     return fail(nullptr, EGH_EINVAL, "batch_receivers and gram_splits must be >= 0");
-  if (c.dft_chunk != 0 && c.dft_chunk != 32 && c.dft_chunk != 64)
-    return fail(nullptr, EGH_EINVAL, "dft_chunk must be 0, 32 or 64");
+  if (c.dft_chunk != 0 && c.dft_chunk != 32 && c.dft_chunk != 64 && c.dft_chunk != 128 &&
+      c.dft_chunk != 256)
+    return fail(nullptr, EGH_EINVAL, "dft_chunk must be 0, 32, 64, 128 or 256");
 
   ctx = new (std::nothrow) egh_ctx();
   if (!ctx) return fail(nullptr, EGH_ENOMEM, "host allocation failed");
@@ -251,8 +261,8 @@ egh_status egh_create(const egh_config* cfg, egh_ctx** out) {
   ctx->rec_iz.assign(c.rec_iz, c.rec_iz + c.nrec);
   ctx->rec_ix.assign(c.rec_ix, c.rec_ix + c.nrec);
   ctx->freqs.assign(c.freq_hz, c.freq_hz + c.nfreq);
-  ctx->B = c.batch_receivers ? std::min(c.batch_receivers, c.nrec) : std::min(c.nrec, 8);
-  ctx->K = c.dft_chunk ? c.dft_chunk : 64;
+  ctx->B = c.batch_receivers ? std::min(c.batch_receivers, c.nrec) : std::min(c.nrec, 16);
+  ctx->K = c.dft_chunk ? c.dft_chunk : 128;
 
   Layout& L = ctx->L;
   L.nz = c.nz; L.nx = c.nx; L.ns = c.nsponge;
@@ -305,9 +315,9 @@ egh_status egh_create(const egh_config* cfg, egh_ctx** out) {
       return s;                                                 \
     }                                                           \
   } while (0)
-  ALLOC(ctx->c1, F * sizeof(float), "c1");
-  ALLOC(ctx->c3, F * sizeof(float), "c3");
-  ALLOC(ctx->ring, (size_t)ctx->K * ctx->B * F * sizeof(float), "ring");
+  ALLOC(ctx->coef, F * sizeof(float2), "coefficients");
+  ALLOC(ctx->ring, (size_t)2 * ctx->K * ((ctx->B + 1) / 2) * F * sizeof(float2), "ring");
+  ALLOC(ctx->tw4, (size_t)c.nt * c.nfreq * sizeof(float4), "paired twiddles");
   ALLOC(ctx->gh, (size_t)c.nrec * c.nfreq * 2 * (size_t)L.G * sizeof(float), "green transforms");
   ALLOC(ctx->part, gram_workspace_floats(c.nrec, c.nfreq, ctx->splits) * sizeof(float), "gram");
   ALLOC(ctx->Qh, (size_t)c.nfreq * c.nrec * c.nrec * sizeof(float2), "Qh");
@@ -322,8 +332,19 @@ egh_status egh_create(const egh_config* cfg, egh_ctx** out) {
   ALLOC(ctx->vel_stage, (size_t)c.nz * c.nx * sizeof(float), "velocity staging");
 #undef ALLOC
   auto init = [&]() -> egh_status {
-    CK(cudaMemset(ctx->c1, 0, F * sizeof(float)));
-    CK(cudaMemset(ctx->c3, 0, F * sizeof(float)));
+    CK(cudaMemset(ctx->coef, 0, F * sizeof(float2)));
+    // guard rows and padding columns of every slot stay zero for the life of the context
+    CK(cudaMemset(ctx->ring, 0, (size_t)2 * ctx->K * ((ctx->B + 1) / 2) * F * sizeof(float2)));
+    {
+      std::vector<float2> t2 = twiddle_table(ctx->freqs, c.dt, c.nt);
+      std::vector<float4> t4(t2.size());
+      for (size_t i = 0; i < t2.size(); ++i) t4[i] = make_float4(t2[i].x, t2[i].x, t2[i].y, t2[i].y);
+      CK(cudaMemcpy(ctx->tw4, t4.data(), t4.size() * sizeof(float4), cudaMemcpyHostToDevice));
+    }
+    CK(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
+    for (cudaEvent_t* e : {&ctx->fd_done[0], &ctx->fd_done[1], &ctx->dft_done[0], &ctx->dft_done[1],
+                           &ctx->ev_side})
+      CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
     CK(cudaMemset(ctx->d_err, 0, sizeof(int)));
     std::vector<int> rp(c.nrec);
     for (int r = 0; r < c.nrec; ++r)
@@ -371,33 +392,51 @@ egh_status egh_green(egh_ctx* ctx, const float* vel, void* stream_) {
   if (s) return s;
   const Layout& L = ctx->L;
   const int K = ctx->K, B = ctx->B, nt = ctx->nt;
-  const long long slot_stride = (long long)B * L.F;
+  const int npmax = (B + 1) / 2;
+  const long long slot_stride = (long long)npmax * L.F;  // float2 between ring slots
   CK(cudaEventRecord(ctx->ev[0], stream));
   CK(cudaMemsetAsync(ctx->gh, 0, (size_t)ctx->nrec * ctx->nf * 2 * L.G * sizeof(float), stream));
+  // the transform stream starts after the coefficients and the zeroed accumulators
+  CK(cudaEventRecord(ctx->ev_side, stream));
+  CK(cudaStreamWaitEvent(ctx->side, ctx->ev_side, 0));
   const float src_scale = (float)(1.0 / (ctx->dx * ctx->dz));
+  cudaEvent_t last_dft = nullptr;
   for (int b0 = 0; b0 < ctx->nrec; b0 += B) {
     const int nb = std::min(B, ctx->nrec - b0);
-    CK(cudaMemsetAsync(ctx->ring, 0, (size_t)K * slot_stride * sizeof(float), stream));
+    const int np = (nb + 1) / 2;
+    // the previous batch's last transform still reads the ring
+    if (last_dft) CK(cudaStreamWaitEvent(stream, last_dft, 0));
+    // level 0 is zero; level 1 is the impulse (the step from zero levels adds only the source)
+    CK(cudaMemsetAsync(slot(ctx, 0), 0, (size_t)np * L.F * sizeof(float2), stream));
+    CK(cudaMemsetAsync(slot(ctx, 1), 0, (size_t)np * L.F * sizeof(float2), stream));
     auto chunk_end = [&](int t) -> egh_status {
       if (t % K == K - 1 || t == nt - 1) {
-        CK(launch_dft_chunk(ctx->ring, slot_stride, L.F, L, ctx->tw, ctx->nf, t - t % K,
-                            t % K + 1, K, nb, ctx->gh, b0, ctx->d_err, stream));
+        const int c = t / K;
+        CK(cudaEventRecord(ctx->fd_done[c & 1], stream));
+        CK(cudaStreamWaitEvent(ctx->side, ctx->fd_done[c & 1], 0));
+        CK(launch_dft_chunk(ctx->ring, slot_stride, L, (c * K) % (2 * K), t - c * K + 1, ctx->tw4,
+                            ctx->nf, c * K, np, nb, ctx->gh, b0, ctx->d_err, ctx->side));
+        CK(cudaEventRecord(ctx->dft_done[c & 1], ctx->side));
+        last_dft = ctx->dft_done[c & 1];
       }
       return EGH_OK;
     };
-    // level 0 is zero; level 1 is the impulse (the step from zero levels adds only the source)
     if ((s = chunk_end(0))) return s;
     if (nt >= 2) {
-      CK(launch_inject(slot(ctx, 1), L.F, ctx->rec_pts + b0, ctx->c3, nb, nullptr, 1.0f,
-                       src_scale, stream));
+      CK(launch_inject(slot(ctx, 1), L.F, ctx->rec_pts + b0, ctx->coef, nb, 1.0f, src_scale,
+                       stream));
       if ((s = chunk_end(1))) return s;
     }
     for (int n = 1; n + 1 < nt; ++n) {
-      CK(launch_fd_step(slot(ctx, n), slot(ctx, n - 1), slot(ctx, n + 1), ctx->c1, ctx->c3, L,
-                        ctx->S, nb, L.F, stream));
-      if ((s = chunk_end(n + 1))) return s;
+      const int t = n + 1;
+      // the first level of chunk c overwrites chunk c - 2's slots: wait for its transform
+      if (t % K == 0 && t / K >= 2) CK(cudaStreamWaitEvent(stream, ctx->dft_done[(t / K) & 1], 0));
+      CK(launch_fd_step(slot(ctx, n), slot(ctx, n - 1), slot(ctx, t), ctx->coef, L, ctx->S, np,
+                        stream));
+      if ((s = chunk_end(t))) return s;
     }
   }
+  if (last_dft) CK(cudaStreamWaitEvent(stream, last_dft, 0));
   CK(cudaEventRecord(ctx->ev[1], stream));
   ctx->ev_rec[0] = true;
   int derr = 0;
@@ -565,8 +604,7 @@ egh_status egh_forward(egh_ctx* ctx, const float* vel, int32_t nsrc, const int32
   ctx->state = prev_state;
   if (s) return s;
   const Layout& L = ctx->L;
-  const int K = ctx->K, B = ctx->B, nt = ctx->nt, nrec = ctx->nrec;
-  const long long slot_stride = (long long)B * L.F;
+  const int B = ctx->B, nt = ctx->nt, nrec = ctx->nrec;
   std::vector<int> sp(nsrc);
   for (int i = 0; i < nsrc; ++i)
     sp[i] = (int)(L.org + (long long)(src_iz[i] + L.ns) * L.PX + (src_ix[i] + L.ns));
@@ -588,15 +626,17 @@ egh_status egh_forward(egh_ctx* ctx, const float* vel, int32_t nsrc, const int32
   const float scale = (float)(1.0 / (ctx->dx * ctx->dz));
   for (int b0 = 0; b0 < nsrc; b0 += B) {
     const int nb = std::min(B, nsrc - b0);
+    const int np = (nb + 1) / 2;
     float* tr = dout + (size_t)b0 * nrec * nt;
-    CK(cudaMemsetAsync(ctx->ring, 0, (size_t)K * slot_stride * sizeof(float), stream));
+    CK(cudaMemsetAsync(slot(ctx, 0), 0, (size_t)np * L.F * sizeof(float2), stream));
+    CK(cudaMemsetAsync(slot(ctx, 1), 0, (size_t)np * L.F * sizeof(float2), stream));
     CK(launch_record(slot(ctx, 0), L.F, ctx->rec_pts, nrec, nb, tr, nt, 0, stream));
     for (int n = 0; n + 1 < nt; ++n) {
       if (n > 0)
-        CK(launch_fd_step(slot(ctx, n), slot(ctx, n - 1), slot(ctx, n + 1), ctx->c1, ctx->c3, L,
-                          ctx->S, nb, L.F, stream));
+        CK(launch_fd_step(slot(ctx, n), slot(ctx, n - 1), slot(ctx, n + 1), ctx->coef, L, ctx->S,
+                          np, stream));
       if (wavelet[n] != 0.f)
-        CK(launch_inject(slot(ctx, n + 1), L.F, d_sp + b0, ctx->c3, nb, nullptr, wavelet[n], scale,
+        CK(launch_inject(slot(ctx, n + 1), L.F, d_sp + b0, ctx->coef, nb, wavelet[n], scale,
                          stream));
       CK(launch_record(slot(ctx, n + 1), L.F, ctx->rec_pts, nrec, nb, tr, nt, n + 1, stream));
     }

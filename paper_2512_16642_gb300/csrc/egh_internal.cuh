@@ -4,8 +4,9 @@
 //   wavefield level: [NZ + 2*GUARD][PX], rows z = -GUARD .. NZ+GUARD-1, row pitch PX >= NX + 4
 //     (multiple of 32).  Guard rows and columns x >= NX are zero and never written, so the
 //     eighth-order stencil reads them as the u = 0 boundary without any bounds test;
-//   ring of K time levels for a batch of B receivers: [K][B][F], F = (NZ + 2*GUARD) * PX,
-//     level n lives in slot n mod K;
+//   ring of 2K time levels for a batch of B receivers in pairs: [2K][B/2][F] float2,
+//     F = (NZ + 2*GUARD) * PX, level n lives in slot n mod 2K (two chunks of K: the transform of
+//     one chunk runs while the next is stepped);
 //   Green transforms gh: [nrec][nf][2][G], planes re/im, G = NZ*PX rounded up to 256, point
 //     p = z*PX + x (entries with x >= NX or p >= NZ*PX are zero);
 //   Hessians Qh, factors Lh: [nf][nrec][nrec] float2 (complex64).
@@ -39,20 +40,21 @@ struct Layout {
 };
 
 // ---- fd.cu ------------------------------------------------------------------------------------
+// Paired levels: float2 per grid point = (receiver 2i, receiver 2i+1); coef = (c1, c3).
 cudaError_t launch_check_velocity(const float* vel, long long n, float* d_vmax_bad, cudaStream_t st);
 cudaError_t launch_build_coef(const float* vel, const Layout& L, double dz, double dx, double dt,
-                              double R, const float* d_vmax, float* c1, float* c3, cudaStream_t st);
-cudaError_t launch_fd_step(const float* ucur, const float* uprev, float* unext, const float* c1,
-                           const float* c3, const Layout& L, const Stencil& S, int nb,
-                           long long fstride, cudaStream_t st);
-cudaError_t launch_inject(float* u, long long fstride, const int* pts, const float* c3, int nb,
-                          const float* amp_dev, float amp_host, float scale, cudaStream_t st);
-cudaError_t launch_record(const float* u, long long fstride, const int* rec_pts, int nrec, int nb,
+                              double R, const float* d_vmax, float2* coef, cudaStream_t st);
+cudaError_t launch_fd_step(const float2* ucur, const float2* uprev, float2* unext,
+                           const float2* coef, const Layout& L, const Stencil& S, int npairs,
+                           cudaStream_t st);
+cudaError_t launch_inject(float2* u, long long pstride, const int* pts, const float2* coef, int nb,
+                          float amp, float scale, cudaStream_t st);
+cudaError_t launch_record(const float2* u, long long pstride, const int* rec_pts, int nrec, int nb,
                           float* traces, int nt, int t, cudaStream_t st);
-cudaError_t launch_dft_chunk(const float* ring, long long slot_stride, long long fstride,
-                             const Layout& L, const float2* tw, int nf, int n0, int kcount, int K,
-                             int nb, float* gh, int rec0, int* err, cudaStream_t st);
-size_t dft_chunk_smem(int K, int nf);
+cudaError_t launch_dft_chunk(const float2* ring, long long slot_stride, const Layout& L,
+                             int slot0, int kcount, const float4* tw4, int nf, int n0, int npairs,
+                             int nvalid, float* gh, int rec0, int* err, cudaStream_t st);
+size_t dft_chunk_smem(int nf);
 
 // ---- gram.cu ----------------------------------------------------------------------------------
 __host__ __device__ int gram_tiles(int nrec);
