@@ -90,8 +90,8 @@ typedef struct {
     const int32_t *rec_ix; /* [nrec], host */
     int32_t nfreq;
     const double *freq_hz; /* [nfreq], host */
-    int32_t batch_receivers; /* receivers propagated together; 0 = library default */
-    int32_t dft_chunk;       /* time levels per on-the-fly transform chunk: 32 or 64; 0 = 64 */
+    int32_t batch_receivers; /* receivers propagated together; 0 = min(nrec, 16) */
+    int32_t dft_chunk;       /* levels per transform chunk: 32, 64, 128 or 256; 0 = 256 */
     int32_t gram_splits;     /* split of the grid sum in the Gram; 0 = default */
     int32_t reserved[5];     /* must be zero */
 } egh_config;

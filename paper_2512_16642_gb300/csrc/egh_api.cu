@@ -51,7 +51,7 @@ struct egh_ctx {
   float2 *coef = nullptr, *ring = nullptr;  // (c1, c3) per point; paired levels [2K][B/2][F]
   float *gh = nullptr, *part = nullptr;
   float2 *Qh = nullptr, *Lh = nullptr, *tw = nullptr;
-  float* twt = nullptr;  // swizzled hi/lo twiddle tiles of the tensor-core transform
+  float4* tw4 = nullptr;  // [nt][nf] (cos, cos, -sin, -sin) for the paired transform
   int tw_len = 0;
   cudaStream_t side = nullptr;                 // the transform's stream inside egh_green
   cudaEvent_t fd_done[2] = {}, dft_done[2] = {}, ev_side = nullptr;
@@ -187,7 +187,7 @@ float2* slot(egh_ctx* ctx, int t) {
 }
 
 void free_all(egh_ctx* c) {
-  void* ptrs[] = {c->coef, c->ring, c->twt, c->gh, c->part, c->Qh, c->Lh, c->tw, c->w_dev,
+  void* ptrs[] = {c->coef, c->ring, c->tw4, c->gh, c->part, c->Qh, c->Lh, c->tw, c->w_dev,
                   c->rec_pts, c->status, c->dsum, c->lmax, c->vchk, c->d_err, c->vel_stage, c->Dh,
                   c->io_in, c->io_out};
   for (void* p : ptrs)
@@ -262,7 +262,7 @@ egh_status egh_create(const egh_config* cfg, egh_ctx** out) {
   ctx->rec_ix.assign(c.rec_ix, c.rec_ix + c.nrec);
   ctx->freqs.assign(c.freq_hz, c.freq_hz + c.nfreq);
   ctx->B = c.batch_receivers ? std::min(c.batch_receivers, c.nrec) : std::min(c.nrec, 16);
-  ctx->K = c.dft_chunk ? c.dft_chunk : 128;
+  ctx->K = c.dft_chunk ? c.dft_chunk : 256;
 
   Layout& L = ctx->L;
   L.nz = c.nz; L.nx = c.nx; L.ns = c.nsponge;
@@ -317,8 +317,7 @@ egh_status egh_create(const egh_config* cfg, egh_ctx** out) {
   } while (0)
   ALLOC(ctx->coef, F * sizeof(float2), "coefficients");
   ALLOC(ctx->ring, (size_t)2 * ctx->K * ((ctx->B + 1) / 2) * F * sizeof(float2), "ring");
-  const std::vector<float> twt_host = dft_twiddle_tiles(ctx->freqs, c.dt, c.nt);
-  ALLOC(ctx->twt, twt_host.size() * sizeof(float), "transform twiddle tiles");
+  ALLOC(ctx->tw4, (size_t)c.nt * c.nfreq * sizeof(float4), "paired twiddles");
   ALLOC(ctx->gh, (size_t)c.nrec * c.nfreq * 2 * (size_t)L.G * sizeof(float), "green transforms");
   ALLOC(ctx->part, gram_workspace_floats(c.nrec, c.nfreq, ctx->splits) * sizeof(float), "gram");
   ALLOC(ctx->Qh, (size_t)c.nfreq * c.nrec * c.nrec * sizeof(float2), "Qh");
@@ -336,8 +335,12 @@ egh_status egh_create(const egh_config* cfg, egh_ctx** out) {
     CK(cudaMemset(ctx->coef, 0, F * sizeof(float2)));
     // guard rows and padding columns of every slot stay zero for the life of the context
     CK(cudaMemset(ctx->ring, 0, (size_t)2 * ctx->K * ((ctx->B + 1) / 2) * F * sizeof(float2)));
-    CK(cudaMemcpy(ctx->twt, twt_host.data(), twt_host.size() * sizeof(float),
-                  cudaMemcpyHostToDevice));
+    {
+      std::vector<float2> t2 = twiddle_table(ctx->freqs, c.dt, c.nt);
+      std::vector<float4> t4(t2.size());
+      for (size_t i = 0; i < t2.size(); ++i) t4[i] = make_float4(t2[i].x, t2[i].x, t2[i].y, t2[i].y);
+      CK(cudaMemcpy(ctx->tw4, t4.data(), t4.size() * sizeof(float4), cudaMemcpyHostToDevice));
+    }
     CK(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
     for (cudaEvent_t* e : {&ctx->fd_done[0], &ctx->fd_done[1], &ctx->dft_done[0], &ctx->dft_done[1],
                            &ctx->ev_side})
@@ -411,7 +414,7 @@ egh_status egh_green(egh_ctx* ctx, const float* vel, void* stream_) {
         const int c = t / K;
         CK(cudaEventRecord(ctx->fd_done[c & 1], stream));
         CK(cudaStreamWaitEvent(ctx->side, ctx->fd_done[c & 1], 0));
-        CK(launch_dft_chunk(ctx->ring, slot_stride, L, (c * K) % (2 * K), t - c * K + 1, ctx->twt,
+        CK(launch_dft_chunk(ctx->ring, slot_stride, L, (c * K) % (2 * K), t - c * K + 1, ctx->tw4,
                             ctx->nf, c * K, np, nb, ctx->gh, b0, ctx->d_err, ctx->side));
         CK(cudaEventRecord(ctx->dft_done[c & 1], ctx->side));
         last_dft = ctx->dft_done[c & 1];

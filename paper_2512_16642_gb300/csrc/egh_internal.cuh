@@ -15,7 +15,6 @@
 
 #include <cstdint>
 #include <string>
-#include <vector>
 
 namespace egh {
 
@@ -53,10 +52,9 @@ cudaError_t launch_inject(float2* u, long long pstride, const int* pts, const fl
 cudaError_t launch_record(const float2* u, long long pstride, const int* rec_pts, int nrec, int nb,
                           float* traces, int nt, int t, cudaStream_t st);
 cudaError_t launch_dft_chunk(const float2* ring, long long slot_stride, const Layout& L,
-                             int slot0, int kcount, const float* twt, int nf, int n0, int npairs,
+                             int slot0, int kcount, const float4* tw4, int nf, int n0, int npairs,
                              int nvalid, float* gh, int rec0, int* err, cudaStream_t st);
 size_t dft_chunk_smem(int nf);
-std::vector<float> dft_twiddle_tiles(const std::vector<double>& f, double dt, int nt);
 
 // ---- gram.cu ----------------------------------------------------------------------------------
 __host__ __device__ int gram_tiles(int nrec);

@@ -14,10 +14,7 @@
 #include <cfloat>
 #include <cmath>
 
-#include <vector>
-
 #include "egh_internal.cuh"
-#include "tc.cuh"
 
 namespace egh {
 
@@ -245,216 +242,183 @@ cudaError_t launch_record(const float2* u, long long pstride, const int* rec_pts
 
 // ---------------------------------------------------------------------------------------------
 // On-the-fly transform of one chunk of kcount consecutive levels n0 .. n0+kcount-1 of a batch
-// (ring slots slot0 .. slot0+kcount-1), on the tensor cores:
-//     gh[rec][k][re/im][p] += sum_j tw[n0+j][k] * u^{n0+j}[rec][p]
-// is the product D[p][c] = sum_j U[p][j] W[c][j] with c = 2k (cos row) / 2k+1 (-sin row),
-// M = 128 points per block, N = 2 nf padded to 16, K = levels.  Per stage of 32 levels one
-// thread brings the 32 level rows of the block's 128 points of a receiver pair (1-D bulk TMA
-// copies) and the stage's pre-swizzled twiddle tiles into shared memory on an mbarrier
-// (double-buffered); the threads transpose the levels into K-major 128-byte-swizzled tiles
-// (point = row), splitting each value into tf32 hi + lo; one thread issues, per receiver,
-// hi*hi + hi*lo + lo*hi (3xTF32) MMAs accumulating in TMEM (two N-column accumulators, one per
-// receiver).  After the last stage the accumulators are read with tcgen05.ld and added into gh,
-// which is therefore read and written once per chunk.  Every mbarrier wait is bounded; on expiry
-// the block records the error flag, waits (bounded) for its copies and MMAs in flight, frees
-// its TMEM and leaves.
+// (ring slots slot0 .. slot0+kcount-1):
+//     gh[rec][k][re/im][p] += sum_j tw[n0+j][k] * u^{n0+j}[rec][p].
+// A block owns D_P points of one receiver pair.  One thread streams the chunk through shared
+// memory in stages of D_SUB levels with 1-D bulk (TMA) copies completing on two mbarriers
+// (double buffer: the next stage lands while the current one is summed); each stage carries the
+// matching twiddle rows, stored as (cos, cos, -sin, -sin) so that one 16-byte load feeds the
+// packed products of both receivers.  Two threads share a pair of adjacent points, each summing
+// half of the frequencies, and keep their accumulators in registers for the whole chunk; gh is
+// read and written once per chunk.  Every mbarrier wait is bounded: on expiry the block records
+// the error flag, waits (bounded) for its copies in flight and leaves.
 // ---------------------------------------------------------------------------------------------
-constexpr int T_P = 128;   // points per block (MMA M)
-constexpr int T_SUB = 32;  // levels per stage (MMA K per stage)
+constexpr int D_P = 128;     // points per block
+constexpr int D_SUB = 16;    // levels per stage
+constexpr int D_NFH = 13;    // frequencies per thread and pass
+constexpr long long kWaitLimit = 1LL << 26;  // mbarrier polls before giving up
 
-int dft_ncomp(int nf) { return (2 * nf + 15) / 16 * 16; }
-
-size_t dft_chunk_smem(int nf) {
-  const int N = dft_ncomp(nf);
-  return 1024 + sizeof(float2) * 2 * T_SUB * T_P + sizeof(float) * 4 * T_P * T_SUB +
-         sizeof(float) * 2 * 2 * (size_t)N * T_SUB;
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
 }
 
-__global__ void __launch_bounds__(T_P)
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned bytes,
+                                         unsigned bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity) {
+  for (long long i = 0; i < kWaitLimit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+size_t dft_chunk_smem(int nf) {
+  return 2 * (sizeof(float2) * D_SUB * D_P + sizeof(float4) * D_SUB * (size_t)nf);
+}
+
+__global__ void __launch_bounds__(D_P)
     k_dft_chunk(const float2* __restrict__ ring, long long slot_stride, long long pstride,
-                long long org, int slot0, int kcount, const float* __restrict__ twt, int stage0,
-                int N, int nf, long long G, float* __restrict__ gh, int rec0, int nvalid,
+                long long org, int slot0, int kcount, const float4* __restrict__ tw4, int nf,
+                int n0, long long G, float* __restrict__ gh, int rec0, int nvalid,
                 int* __restrict__ err) {
-  extern __shared__ __align__(1024) unsigned char dsm_raw[];
-  unsigned char* sm = dsm_raw + ((1024 - (tc::smem_u32(dsm_raw) & 1023)) & 1023);
-  float2* raw = reinterpret_cast<float2*>(sm);                      // [2][T_SUB][T_P]
-  unsigned char* At = sm + sizeof(float2) * 2 * T_SUB * T_P;        // a_hi, a_lo, b_hi, b_lo
-  unsigned char* Bt = At + sizeof(float) * 4 * T_P * T_SUB;         // [2][hi, lo][N][T_SUB]
-  constexpr unsigned kAT = sizeof(float) * T_P * T_SUB;             // one A tile: 16 KB
-  const unsigned kBT = sizeof(float) * N * T_SUB;                   // one twiddle tile
-  __shared__ __align__(8) unsigned long long bars[3];               // stage[0], stage[1], mma
-  __shared__ unsigned tslot;
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const unsigned ncols = 2 * N <= 32 ? 32u : 2 * N <= 64 ? 64u : 2 * N <= 128 ? 128u : 256u;
-  if (warp == 0) tc::tmem_alloc(&tslot, ncols);
-  const unsigned bst0 = tc::smem_u32(&bars[0]), bst1 = tc::smem_u32(&bars[1]);
-  const unsigned bmma = tc::smem_u32(&bars[2]);
-  if (tid == 0) {
-    tc::mbar_init(bst0, 1);
-    tc::mbar_init(bst1, 1);
-    tc::mbar_init(bmma, 1);
-    tc::mbar_init_fence();
-  }
-  tc::tc_fence_before();
-  __syncthreads();
-  tc::tc_fence_after();
-  const unsigned tmem = tslot;
+  extern __shared__ __align__(128) unsigned char dsm[];
+  float2* U = reinterpret_cast<float2*>(dsm);                                    // [2][D_SUB][D_P]
+  float4* T = reinterpret_cast<float4*>(dsm + sizeof(float2) * 2 * D_SUB * D_P);  // [2][D_SUB][nf]
+  __shared__ __align__(8) unsigned long long bars[2];
+  const int tid = threadIdx.x;
   const int pair = blockIdx.y;
-  const long long p0 = (long long)blockIdx.x * T_P;
+  const long long p0 = (long long)blockIdx.x * D_P;
   const float2* src = ring + (long long)pair * pstride + org + p0;
-  const int nst = (kcount + T_SUB - 1) / T_SUB;
-  auto issue = [&](int s) {
-    const int buf = s & 1, j0 = s * T_SUB, jn = min(T_SUB, kcount - j0);
-    const unsigned bar = buf ? bst1 : bst0;
-    tc::mbar_expect_tx(bar, (unsigned)(jn * T_P * sizeof(float2)) + 2 * kBT);
+  const unsigned ub0 = smem_u32(&bars[0]), ub1 = smem_u32(&bars[1]);
+  if (tid == 0) {
+    mbar_init(ub0, 1);
+    mbar_init(ub1, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const int nst = (kcount + D_SUB - 1) / D_SUB;
+  const int npass = (nf + 2 * D_NFH - 1) / (2 * D_NFH);
+  const int total = nst * npass;  // stages over all passes (each pass re-streams the chunk)
+  auto issue = [&](int gs) {
+    const int s = gs % nst, buf = gs & 1;
+    const int j0 = s * D_SUB, jn = min(D_SUB, kcount - j0);
+    const unsigned bar = buf ? ub1 : ub0;
+    mbar_expect_tx(bar, (unsigned)(jn * D_P * sizeof(float2) + jn * nf * sizeof(float4)));
     for (int j = 0; j < jn; ++j)
-      tc::bulk_g2s(tc::smem_u32(raw + (buf * T_SUB + j) * T_P),
-                   src + (long long)(slot0 + j0 + j) * slot_stride, T_P * sizeof(float2), bar);
-    tc::bulk_g2s(tc::smem_u32(Bt + buf * 2 * kBT), twt + (long long)(stage0 + s) * 2 * N * T_SUB,
-                 2 * kBT, bar);
+      bulk_g2s(smem_u32(U + (buf * D_SUB + j) * D_P), src + (long long)(slot0 + j0 + j) * slot_stride,
+               D_P * sizeof(float2), bar);
+    bulk_g2s(smem_u32(T + buf * D_SUB * nf), tw4 + (long long)(n0 + j0) * nf,
+             (unsigned)(jn * nf * sizeof(float4)), bar);
   };
   if (tid == 0) {
     issue(0);
-    if (nst > 1) issue(1);
+    if (total > 1) issue(1);
   }
-  const unsigned idesc = tc::idesc_tf32(T_P, N);
-  int s_fail = -1;
-  for (int s = 0; s < nst; ++s) {
-    const int buf = s & 1;
-    bool ok = tc::mbar_wait(buf ? bst1 : bst0, (s >> 1) & 1);
-    if (s > 0) ok = ok && tc::mbar_wait(bmma, (s - 1) & 1);  // the A tiles are free again
-    if (__syncthreads_or(!ok)) {
-      s_fail = s;
-      break;
-    }
-    tc::tc_fence_after();
-    const int jn = min(T_SUB, kcount - s * T_SUB);
-    const float2* rb = raw + buf * T_SUB * T_P + tid;
+  const int fh = tid & 1, pt = tid >> 1;
+  const int lp = 2 * pt;  // this thread's two points
+  for (int pass = 0; pass < npass; ++pass) {
+    const int fbase = pass * 2 * D_NFH + fh * D_NFH;
+    const int fn = max(0, min(D_NFH, nf - fbase));
+    float2 ar0[D_NFH], ai0[D_NFH], ar1[D_NFH], ai1[D_NFH];
 #pragma unroll
-    for (int jc = 0; jc < T_SUB / 4; ++jc) {
-      float ax[4], bx[4];
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int j = 4 * jc + e;
-        const float2 v = j < jn ? rb[j * T_P] : make_float2(0.f, 0.f);
-        ax[e] = v.x;
-        bx[e] = v.y;
+    for (int i = 0; i < D_NFH; ++i)
+      ar0[i] = ai0[i] = ar1[i] = ai1[i] = make_float2(0.f, 0.f);
+    for (int s = 0; s < nst; ++s) {
+      const int gs = pass * nst + s, buf = gs & 1;
+      const unsigned bar = buf ? ub1 : ub0;
+      const bool ok = mbar_wait_bounded(bar, (gs >> 1) & 1);
+      if (__syncthreads_or(!ok)) {  // block-uniform decision: every thread leaves together
+        if (tid == 0) atomicExch(err, 1);
+        // let this block's copies in flight land before leaving (bounded)
+        mbar_wait_bounded(bar, (gs >> 1) & 1);
+        if (gs + 1 < total) mbar_wait_bounded(buf ? ub0 : ub1, ((gs + 1) >> 1) & 1);
+        return;
       }
-      float4 ah, al, bh, bl;
-      ah.x = tc::tf32_hi(ax[0]); ah.y = tc::tf32_hi(ax[1]); ah.z = tc::tf32_hi(ax[2]); ah.w = tc::tf32_hi(ax[3]);
-      bh.x = tc::tf32_hi(bx[0]); bh.y = tc::tf32_hi(bx[1]); bh.z = tc::tf32_hi(bx[2]); bh.w = tc::tf32_hi(bx[3]);
-      al = make_float4(ax[0] - ah.x, ax[1] - ah.y, ax[2] - ah.z, ax[3] - ah.w);
-      bl = make_float4(bx[0] - bh.x, bx[1] - bh.y, bx[2] - bh.z, bx[3] - bh.w);
-      const unsigned off = tc::sw128_offset(tid, 4 * jc);
-      *reinterpret_cast<float4*>(At + 0 * kAT + off) = ah;
-      *reinterpret_cast<float4*>(At + 1 * kAT + off) = al;
-      *reinterpret_cast<float4*>(At + 2 * kAT + off) = bh;
-      *reinterpret_cast<float4*>(At + 3 * kAT + off) = bl;
-    }
-    tc::fence_proxy_async();
-    tc::tc_fence_before();
-    __syncthreads();
-    if (tid == 0) {
-      if (s + 2 < nst) issue(s + 2);  // this stage's raw buffer has been consumed
-      tc::tc_fence_after();
-      const unsigned abase = tc::smem_u32(At);
-      const unsigned bhi = tc::smem_u32(Bt + buf * 2 * kBT), blo = bhi + kBT;
+      const int jn = min(D_SUB, kcount - s * D_SUB);
+      const float2* Ub = U + buf * D_SUB * D_P + lp;
+      const float4* Tb = T + buf * D_SUB * nf + fbase;
+      for (int j = 0; j < jn; ++j) {
+        const float4 sv = *reinterpret_cast<const float4*>(Ub + j * D_P);
+        const float2 s0 = make_float2(sv.x, sv.y), s1 = make_float2(sv.z, sv.w);
+        const float4* tj = Tb + j * nf;
 #pragma unroll
-      for (int r = 0; r < 2; ++r) {
-        const unsigned dt = tmem + (unsigned)(r * N);
-        const unsigned ahi = abase + (2 * r) * kAT, alo = ahi + kAT;
-#pragma unroll
-        for (int ks = 0; ks < T_SUB / 8; ++ks) {
-          const unsigned ko = 32u * ks;
-          tc::mma_tf32(dt, tc::sdesc_sw128(ahi + ko), tc::sdesc_sw128(bhi + ko), idesc,
-                       s > 0 || ks > 0);
-          tc::mma_tf32(dt, tc::sdesc_sw128(ahi + ko), tc::sdesc_sw128(blo + ko), idesc, true);
-          tc::mma_tf32(dt, tc::sdesc_sw128(alo + ko), tc::sdesc_sw128(bhi + ko), idesc, true);
+        for (int i = 0; i < D_NFH; ++i) {
+          if (i < fn) {
+            const float4 w = tj[i];
+            const float2 c = make_float2(w.x, w.y), sn = make_float2(w.z, w.w);
+            ar0[i] = __ffma2_rn(c, s0, ar0[i]);
+            ai0[i] = __ffma2_rn(sn, s0, ai0[i]);
+            ar1[i] = __ffma2_rn(c, s1, ar1[i]);
+            ai1[i] = __ffma2_rn(sn, s1, ai1[i]);
+          }
         }
       }
-      tc::mma_commit(bmma);
+      __syncthreads();  // everyone is done with this buffer
+      if (tid == 0 && gs + 2 < total) issue(gs + 2);
     }
-  }
-  if (s_fail < 0) {
-    const bool ok = tc::mbar_wait(bmma, (nst - 1) & 1);
-    if (__syncthreads_or(!ok)) s_fail = nst;
-  }
-  if (s_fail < 0) {
-    tc::tc_fence_after();
+    // add into gh: receiver a = lane x, receiver b = lane y of each packed accumulator
 #pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      const int b = 2 * pair + r;
-      if (b >= nvalid) continue;  // block-uniform
-      float* g = gh + (long long)(rec0 + b) * nf * 2 * G + p0 + tid;
-      for (int c0 = 0; c0 < N; c0 += 16) {
-        float v[16];
-        tc::tmem_ld16(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(r * N + c0), v);
+    for (int i = 0; i < D_NFH; ++i) {
+      if (i < fn) {
+        const int f = fbase + i;
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const int c = c0 + i;
-          if (c < 2 * nf) g[(long long)c * G] += v[i];  // c = 2k + plane -> (k * 2 + plane) * G
+        for (int r = 0; r < 2; ++r) {
+          const int b = 2 * pair + r;
+          if (b >= nvalid) continue;
+          float* g = gh + ((long long)(rec0 + b) * nf + f) * 2 * G + p0 + lp;
+          float2* gre = reinterpret_cast<float2*>(g);
+          float2* gim = reinterpret_cast<float2*>(g + G);
+          float2 re = *gre, im = *gim;
+          re.x += r ? ar0[i].y : ar0[i].x;
+          re.y += r ? ar1[i].y : ar1[i].x;
+          im.x += r ? ai0[i].y : ai0[i].x;
+          im.y += r ? ai1[i].y : ai1[i].x;
+          *gre = re;
+          *gim = im;
         }
       }
     }
-  } else {
-    if (tid == 0) atomicExch(err, 1);
-    // let this block's copies and MMAs in flight finish before leaving (bounded waits)
-    const int s = s_fail;
-    if (s < nst) {
-      tc::mbar_wait((s & 1) ? bst1 : bst0, (s >> 1) & 1);
-      if (s + 1 < nst) tc::mbar_wait(((s + 1) & 1) ? bst1 : bst0, ((s + 1) >> 1) & 1);
-    }
-    if (s > 0) tc::mbar_wait(bmma, (s - 1) & 1);
   }
-  tc::tc_fence_before();
-  __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, ncols);
 }
 
 cudaError_t launch_dft_chunk(const float2* ring, long long slot_stride, const Layout& L,
-                             int slot0, int kcount, const float* twt, int nf, int n0, int npairs,
+                             int slot0, int kcount, const float4* tw4, int nf, int n0, int npairs,
                              int nvalid, float* gh, int rec0, int* err, cudaStream_t st) {
-  if (L.G % T_P != 0 || n0 % T_SUB != 0) return cudaErrorInvalidValue;
+  if (L.G % D_P != 0) return cudaErrorInvalidValue;
   const size_t smem = dft_chunk_smem(nf);
   cudaError_t e =
       cudaFuncSetAttribute(k_dft_chunk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  dim3 grid((unsigned)(L.G / T_P), npairs);
+  dim3 grid((unsigned)(L.G / D_P), npairs);
   count_launches(1);
-  k_dft_chunk<<<grid, T_P, smem, st>>>(ring, slot_stride, L.F, L.org, slot0, kcount, twt,
-                                       n0 / T_SUB, dft_ncomp(nf), nf, L.G, gh, rec0, nvalid, err);
+  k_dft_chunk<<<grid, D_P, smem, st>>>(ring, slot_stride, L.F, L.org, slot0, kcount, tw4, nf, n0,
+                                       L.G, gh, rec0, nvalid, err);
   return cudaGetLastError();
-}
-
-// Twiddle tiles for the tensor-core transform: for every stage of 32 levels, a hi tile and a lo
-// tile of [N][32] floats in the 128-byte-swizzled K-major layout; row 2k = cos(2 pi f_k n dt),
-// row 2k+1 = -sin(2 pi f_k n dt) (phase reduced as 2 pi frac(f_k n dt) in double precision),
-// rows >= 2 nf and levels >= nt zero.
-std::vector<float> dft_twiddle_tiles(const std::vector<double>& f, double dt, int nt) {
-  const int nf = (int)f.size(), N = dft_ncomp(nf);
-  const int nstg = (nt + T_SUB - 1) / T_SUB;
-  std::vector<float> out((size_t)nstg * 2 * N * T_SUB, 0.f);
-  for (int sg = 0; sg < nstg; ++sg) {
-    unsigned char* hi = reinterpret_cast<unsigned char*>(out.data() + (size_t)sg * 2 * N * T_SUB);
-    unsigned char* lo = hi + sizeof(float) * N * T_SUB;
-    for (int j = 0; j < T_SUB; ++j) {
-      const int n = sg * T_SUB + j;
-      if (n >= nt) continue;
-      for (int k = 0; k < nf; ++k) {
-        double ph = f[k] * (double)n * dt;
-        ph -= std::floor(ph);
-        const double a = 2.0 * M_PI * ph;
-        const float v[2] = {(float)std::cos(a), (float)-std::sin(a)};
-        for (int q = 0; q < 2; ++q) {
-          const unsigned off = tc::sw128_offset(2 * k + q, j);
-          const float h = tc::tf32_hi(v[q]);
-          *reinterpret_cast<float*>(hi + off) = h;
-          *reinterpret_cast<float*>(lo + off) = v[q] - h;
-        }
-      }
-    }
-  }
-  return out;
 }
 
 }  // namespace egh
