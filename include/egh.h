@@ -91,9 +91,11 @@ typedef struct {
     int32_t nfreq;
     const double *freq_hz; /* [nfreq], host */
     int32_t batch_receivers; /* receivers propagated together; 0 = min(nrec, 16) */
-    int32_t dft_chunk;       /* levels per transform chunk: 32, 64, 128 or 256; 0 = 256 */
+    int32_t dft_chunk;       /* levels per transform chunk: 32, 64, 128, 256 or 512; 0 = 512 */
     int32_t gram_splits;     /* split of the grid sum in the Gram; 0 = default */
-    int32_t reserved[5];     /* must be zero */
+    int32_t fd_rows;         /* FD rows per warp: 12, 16, 20, 24 or 32; 0 = timed on the first
+                                egh_green of the context and the fastest kept */
+    int32_t reserved[4];     /* must be zero */
 } egh_config;
 
 typedef struct egh_ctx egh_ctx;
@@ -109,6 +111,8 @@ typedef struct {
     int32_t pitch;             /* row pitch (floats) of the device wavefield layout */
     int32_t batch_receivers, dft_chunk, gram_splits;
     int64_t kernel_launches;   /* kernels this library has launched since it was loaded (all contexts) */
+    int32_t fd_rows;           /* FD rows per warp in use (0 until chosen) */
+    int32_t pad_;
 } egh_stats;
 
 /* Validates the configuration and allocates the device state on the current

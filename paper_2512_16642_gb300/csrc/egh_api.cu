@@ -6,7 +6,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "egh.h"
@@ -45,16 +47,25 @@ struct egh_ctx {
   std::vector<double> freqs;
   std::vector<float> wsyn;
   int B = 0, K = 0, splits = 0;
+  int fd_tz = 0;  // FD rows per warp (0 = library default)
   Layout L{};
   Stencil S{};
   // device state
-  float2 *coef = nullptr, *ring = nullptr;  // (c1, c3) per point; paired levels [2K][B/2][F]
+  float2 *coef = nullptr, *lev = nullptr;    // (c1, c3) per point; paired FD levels [3][B/2][F]
+  __nv_bfloat16* snap = nullptr;             // [2][2K][Bp][G] hi/lo snapshots of the transform
+  unsigned char* twt = nullptr;              // tensor-core twiddle tiles (64 levels each)
+  CUtensorMap tmap{};                        // TMA map of the snapshot ring (64-byte aligned type)
+  int Bp = 0;                                // receivers per snapshot slot (B rounded up to even)
   float *gh = nullptr, *part = nullptr;
   float2 *Qh = nullptr, *Lh = nullptr, *tw = nullptr;
-  float4* tw4 = nullptr;  // [nt][nf] (cos, cos, -sin, -sin) for the paired transform
   int tw_len = 0;
-  cudaStream_t side = nullptr;                 // the transform's stream inside egh_green
+  cudaStream_t side = nullptr;                 // the transform's stream inside egh_green (low priority)
+  cudaStream_t fdst = nullptr;                 // the FD stream inside egh_green (high priority)
+  // FD steps of a chunk as CUDA graphs, keyed by (first level mod 3, its offset in the chunk,
+  // steps, ring slot of the chunk's level 0, pairs, rows per warp)
+  std::map<std::tuple<int, int, int, int, int, int>, cudaGraphExec_t> fd_graphs;
   cudaEvent_t fd_done[2] = {}, dft_done[2] = {}, ev_side = nullptr;
+  cudaEvent_t ev_tune[2] = {};                 // FD rows-per-warp timing
   float* w_dev = nullptr;
   int* rec_pts = nullptr;
   int* status = nullptr;
@@ -181,22 +192,71 @@ egh_status prepare_model(egh_ctx* ctx, const float* vel, cudaStream_t stream) {
   return EGH_OK;
 }
 
-// Ring slot of level t: [2K][B/2][F] float2.
+// FD state slot of level t: [3][B/2][F] float2.
 float2* slot(egh_ctx* ctx, int t) {
-  return ctx->ring + (long long)(t % (2 * ctx->K)) * ((ctx->B + 1) / 2) * ctx->L.F;
+  return ctx->lev + (long long)(t % 3) * ((ctx->B + 1) / 2) * ctx->L.F;
+}
+
+// Snapshot output for ring slot j (0 .. 2K-1).
+SnapOut snap_slot(egh_ctx* ctx, int j) {
+  const long long per = (long long)ctx->Bp * ctx->L.G;
+  return SnapOut{ctx->snap + (long long)j * per, 2LL * ctx->K * per, ctx->L.G};
+}
+
+// Zero both planes of ring slot j for the receivers of a batch.
+cudaError_t zero_snap_slot(egh_ctx* ctx, int j, cudaStream_t st) {
+  const SnapOut so = snap_slot(ctx, j);
+  const size_t bytes = (size_t)ctx->Bp * ctx->L.G * sizeof(__nv_bfloat16);
+  cudaError_t e = cudaMemsetAsync(so.lvl, 0, bytes, st);
+  if (e != cudaSuccess) return e;
+  return cudaMemsetAsync(so.lvl + so.plane, 0, bytes, st);
 }
 
 void free_all(egh_ctx* c) {
-  void* ptrs[] = {c->coef, c->ring, c->tw4, c->gh, c->part, c->Qh, c->Lh, c->tw, c->w_dev,
+  void* ptrs[] = {c->coef, c->lev, c->snap, c->twt, c->gh, c->part, c->Qh, c->Lh, c->tw, c->w_dev,
                   c->rec_pts, c->status, c->dsum, c->lmax, c->vchk, c->d_err, c->vel_stage, c->Dh,
                   c->io_in, c->io_out};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t& e : c->ev)
     if (e) cudaEventDestroy(e);
-  for (cudaEvent_t e : {c->fd_done[0], c->fd_done[1], c->dft_done[0], c->dft_done[1], c->ev_side})
+  for (cudaEvent_t e : {c->fd_done[0], c->fd_done[1], c->dft_done[0], c->dft_done[1], c->ev_side,
+                        c->ev_tune[0], c->ev_tune[1]})
     if (e) cudaEventDestroy(e);
+  for (auto& kv : c->fd_graphs) cudaGraphExecDestroy(kv.second);
+  c->fd_graphs.clear();
   if (c->side) cudaStreamDestroy(c->side);
+  if (c->fdst) cudaStreamDestroy(c->fdst);
+}
+
+
+// FD steps t = ta .. t1-1 of a chunk whose level t0 sits in ring slot sbase, on the FD stream, as
+// one CUDA graph (captured on first use, then replayed: the kernel nodes' arguments depend only
+// on the key, since state slots follow t mod 3 and ring slots follow t - t0).
+egh_status fd_chunk_steps(egh_ctx* ctx, int ta, int t0, int t1, int sbase, int np) {
+  if (ta >= t1) return EGH_OK;
+  const auto key = std::make_tuple(ta % 3, ta - t0, t1 - ta, sbase, np, ctx->fd_tz);
+  auto it = ctx->fd_graphs.find(key);
+  if (it == ctx->fd_graphs.end()) {
+    CK(cudaStreamBeginCapture(ctx->fdst, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int t = ta; t < t1 && e == cudaSuccess; ++t)
+      e = launch_fd_step(slot(ctx, t - 1), slot(ctx, t - 2), slot(ctx, t), ctx->coef, ctx->L,
+                         ctx->S, np, snap_slot(ctx, sbase + (t - t0)), ctx->fdst, ctx->fd_tz);
+    count_launches(-(t1 - ta));  // counted again at each replay
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(ctx->fdst, &graph);
+    if (e == cudaSuccess) e = e2;
+    cudaGraphExec_t exec = nullptr;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess)
+      return fail(ctx, EGH_ECUDA, std::string("FD chunk graph: ") + cudaGetErrorString(e));
+    it = ctx->fd_graphs.emplace(key, exec).first;
+  }
+  CK(cudaGraphLaunch(it->second, ctx->fdst));
+  count_launches(t1 - ta);
+  return EGH_OK;
 }
 
 }  // namespace
@@ -246,11 +306,15 @@ egh_status egh_create(const egh_config* cfg, egh_ctx** out) {
   for (int k = 0; k < c.nfreq; ++k)
     if (!(c.freq_hz[k] > 0) || !(c.freq_hz[k] < 0.5 / c.dt))
       return fail(nullptr, EGH_EINVAL, "frequency outside (0, 1/(2 dt))");
+  if (c.fd_rows != 0 && c.fd_rows != 12 && c.fd_rows != 16 && c.fd_rows != 20 && c.fd_rows != 24 &&
+      c.fd_rows != 32)
+    return fail(nullptr, EGH_EINVAL, "fd_rows must be 0, 12, 16, 20, 24 or 32");
+  if (c.batch_receivers > 32) return fail(nullptr, EGH_EINVAL, "batch_receivers must be <= 32");
   if (c.batch_receivers < 0 || c.gram_splits < 0)
     return fail(nullptr, EGH_EINVAL, "batch_receivers and gram_splits must be >= 0");
   if (c.dft_chunk != 0 && c.dft_chunk != 32 && c.dft_chunk != 64 && c.dft_chunk != 128 &&
-      c.dft_chunk != 256)
-    return fail(nullptr, EGH_EINVAL, "dft_chunk must be 0, 32, 64, 128 or 256");
+      c.dft_chunk != 256 && c.dft_chunk != 512)
+    return fail(nullptr, EGH_EINVAL, "dft_chunk must be 0, 32, 64, 128, 256 or 512");
 
   ctx = new (std::nothrow) egh_ctx();
   if (!ctx) return fail(nullptr, EGH_ENOMEM, "host allocation failed");
@@ -262,13 +326,15 @@ egh_status egh_create(const egh_config* cfg, egh_ctx** out) {
   ctx->rec_ix.assign(c.rec_ix, c.rec_ix + c.nrec);
   ctx->freqs.assign(c.freq_hz, c.freq_hz + c.nfreq);
   ctx->B = c.batch_receivers ? std::min(c.batch_receivers, c.nrec) : std::min(c.nrec, 16);
-  ctx->K = c.dft_chunk ? c.dft_chunk : 256;
+  ctx->K = c.dft_chunk ? c.dft_chunk : 512;
+  ctx->Bp = 2 * ((ctx->B + 1) / 2);
+  ctx->fd_tz = c.fd_rows;
 
   Layout& L = ctx->L;
   L.nz = c.nz; L.nx = c.nx; L.ns = c.nsponge;
   L.NZ = c.nz + 2 * c.nsponge;
   L.NX = c.nx + 2 * c.nsponge;
-  L.PX = (int)std::max<long long>(64, round_up(L.NX + 4, 32));
+  L.PX = (int)std::max<long long>(64, round_up(L.NX + 4, 64));
   L.F = (long long)(L.NZ + 2 * GUARD) * L.PX;
   L.org = (long long)GUARD * L.PX;
   L.G = round_up((long long)L.NZ * L.PX, 256);
@@ -316,8 +382,11 @@ egh_status egh_create(const egh_config* cfg, egh_ctx** out) {
     }                                                           \
   } while (0)
   ALLOC(ctx->coef, F * sizeof(float2), "coefficients");
-  ALLOC(ctx->ring, (size_t)2 * ctx->K * ((ctx->B + 1) / 2) * F * sizeof(float2), "ring");
-  ALLOC(ctx->tw4, (size_t)c.nt * c.nfreq * sizeof(float4), "paired twiddles");
+  ALLOC(ctx->lev, (size_t)3 * ((ctx->B + 1) / 2) * F * sizeof(float2), "FD state");
+  ALLOC(ctx->snap, (size_t)2 * 2 * ctx->K * ctx->Bp * (size_t)L.G * sizeof(__nv_bfloat16),
+        "snapshot ring");
+  std::vector<unsigned char> twt = dft_twiddle_tiles(ctx->freqs, c.dt, c.nt);
+  ALLOC(ctx->twt, twt.size(), "twiddle tiles");
   ALLOC(ctx->gh, (size_t)c.nrec * c.nfreq * 2 * (size_t)L.G * sizeof(float), "green transforms");
   ALLOC(ctx->part, gram_workspace_floats(c.nrec, c.nfreq, ctx->splits) * sizeof(float), "gram");
   ALLOC(ctx->Qh, (size_t)c.nfreq * c.nrec * c.nrec * sizeof(float2), "Qh");
@@ -333,18 +402,27 @@ egh_status egh_create(const egh_config* cfg, egh_ctx** out) {
 #undef ALLOC
   auto init = [&]() -> egh_status {
     CK(cudaMemset(ctx->coef, 0, F * sizeof(float2)));
-    // guard rows and padding columns of every slot stay zero for the life of the context
-    CK(cudaMemset(ctx->ring, 0, (size_t)2 * ctx->K * ((ctx->B + 1) / 2) * F * sizeof(float2)));
+    // guard rows and padding columns of every state slot, and the padding points of every
+    // snapshot slot, stay zero for the life of the context
+    CK(cudaMemset(ctx->lev, 0, (size_t)3 * ((ctx->B + 1) / 2) * F * sizeof(float2)));
+    CK(cudaMemset(ctx->snap, 0,
+                  (size_t)2 * 2 * ctx->K * ctx->Bp * (size_t)L.G * sizeof(__nv_bfloat16)));
+    CK(cudaMemcpy(ctx->twt, twt.data(), twt.size(), cudaMemcpyHostToDevice));
+    CK(make_snap_tmap(&ctx->tmap, ctx->snap, L.G, ctx->Bp, 2 * ctx->K));
+    CK(fd_prepare(c.nfreq));
     {
-      std::vector<float2> t2 = twiddle_table(ctx->freqs, c.dt, c.nt);
-      std::vector<float4> t4(t2.size());
-      for (size_t i = 0; i < t2.size(); ++i) t4[i] = make_float4(t2[i].x, t2[i].x, t2[i].y, t2[i].y);
-      CK(cudaMemcpy(ctx->tw4, t4.data(), t4.size() * sizeof(float4), cudaMemcpyHostToDevice));
+      // FD steps are a serial chain of short kernels: their stream gets the highest priority so
+      // that their blocks are placed ahead of the transform's, which fills the rest of the GPU
+      int least = 0, greatest = 0;
+      CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+      CK(cudaStreamCreateWithPriority(&ctx->side, cudaStreamNonBlocking, least));
+      CK(cudaStreamCreateWithPriority(&ctx->fdst, cudaStreamNonBlocking, greatest));
     }
-    CK(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
     for (cudaEvent_t* e : {&ctx->fd_done[0], &ctx->fd_done[1], &ctx->dft_done[0], &ctx->dft_done[1],
                            &ctx->ev_side})
       CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    CK(cudaEventCreate(&ctx->ev_tune[0]));
+    CK(cudaEventCreate(&ctx->ev_tune[1]));
     CK(cudaMemset(ctx->d_err, 0, sizeof(int)));
     std::vector<int> rp(c.nrec);
     for (int r = 0; r < c.nrec; ++r)
@@ -392,51 +470,69 @@ egh_status egh_green(egh_ctx* ctx, const float* vel, void* stream_) {
   if (s) return s;
   const Layout& L = ctx->L;
   const int K = ctx->K, B = ctx->B, nt = ctx->nt;
-  const int npmax = (B + 1) / 2;
-  const long long slot_stride = (long long)npmax * L.F;  // float2 between ring slots
   CK(cudaEventRecord(ctx->ev[0], stream));
-  CK(cudaMemsetAsync(ctx->gh, 0, (size_t)ctx->nrec * ctx->nf * 2 * L.G * sizeof(float), stream));
-  // the transform stream starts after the coefficients and the zeroed accumulators
+  // the FD and transform streams start after the coefficients
   CK(cudaEventRecord(ctx->ev_side, stream));
   CK(cudaStreamWaitEvent(ctx->side, ctx->ev_side, 0));
+  CK(cudaStreamWaitEvent(ctx->fdst, ctx->ev_side, 0));
+  cudaStream_t fs = ctx->fdst;
   const float src_scale = (float)(1.0 / (ctx->dx * ctx->dz));
-  cudaEvent_t last_dft = nullptr;
+  if (ctx->fd_tz == 0) {
+    // Rows per warp of the FD step: time each choice on this grid (a few steps of a full batch,
+    // no snapshots; the run below rewrites every state slot it reads) and keep the fastest.
+    const int np = (std::min(B, ctx->nrec) + 1) / 2;
+    const SnapOut none{nullptr, 0, 0};
+    float best = 1e30f;
+    int best_tz = fd_rows_per_warp_default();
+    for (int tz : {12, 16, 20, 24, 32}) {
+      float ms = 0.f;
+      for (int rep = 0; rep < 2; ++rep) {  // the first pass warms up
+        CK(cudaEventRecord(ctx->ev_tune[0], fs));
+        for (int t = 2; t < 14; ++t)
+          CK(launch_fd_step(slot(ctx, t - 1), slot(ctx, t - 2), slot(ctx, t), ctx->coef, L, ctx->S,
+                            np, none, fs, tz));
+        CK(cudaEventRecord(ctx->ev_tune[1], fs));
+        CK(cudaEventSynchronize(ctx->ev_tune[1]));
+        CK(cudaEventElapsedTime(&ms, ctx->ev_tune[0], ctx->ev_tune[1]));
+      }
+      if (ms < best) {
+        best = ms;
+        best_tz = tz;
+      }
+    }
+    ctx->fd_tz = best_tz;
+  }
+  const int nchunk = (nt + K - 1) / K;
+  long long g = 0;  // chunks so far over all batches: chunk g uses ring slots (g % 2) K ..
   for (int b0 = 0; b0 < ctx->nrec; b0 += B) {
     const int nb = std::min(B, ctx->nrec - b0);
     const int np = (nb + 1) / 2;
-    // the previous batch's last transform still reads the ring
-    if (last_dft) CK(cudaStreamWaitEvent(stream, last_dft, 0));
-    // level 0 is zero; level 1 is the impulse (the step from zero levels adds only the source)
-    CK(cudaMemsetAsync(slot(ctx, 0), 0, (size_t)np * L.F * sizeof(float2), stream));
-    CK(cudaMemsetAsync(slot(ctx, 1), 0, (size_t)np * L.F * sizeof(float2), stream));
-    auto chunk_end = [&](int t) -> egh_status {
-      if (t % K == K - 1 || t == nt - 1) {
-        const int c = t / K;
-        CK(cudaEventRecord(ctx->fd_done[c & 1], stream));
-        CK(cudaStreamWaitEvent(ctx->side, ctx->fd_done[c & 1], 0));
-        CK(launch_dft_chunk(ctx->ring, slot_stride, L, (c * K) % (2 * K), t - c * K + 1, ctx->tw4,
-                            ctx->nf, c * K, np, nb, ctx->gh, b0, ctx->d_err, ctx->side));
-        CK(cudaEventRecord(ctx->dft_done[c & 1], ctx->side));
-        last_dft = ctx->dft_done[c & 1];
+    for (int c = 0; c < nchunk; ++c, ++g) {
+      const int t0 = c * K, t1 = std::min(nt, t0 + K);
+      const int sbase = (int)(g & 1) * K;
+      // this chunk's slots were read by the transform of chunk g - 2
+      if (g >= 2) CK(cudaStreamWaitEvent(fs, ctx->dft_done[g & 1], 0));
+      for (int t = t0; t < std::min(t1, 2); ++t) {
+        // level 0 is zero; level 1 is the impulse (the step from zero levels adds only the source)
+        const int sj = sbase + (t - t0);
+        CK(cudaMemsetAsync(slot(ctx, t), 0, (size_t)np * L.F * sizeof(float2), fs));
+        CK(zero_snap_slot(ctx, sj, fs));
+        if (t == 1)
+          CK(launch_inject(slot(ctx, 1), L.F, ctx->rec_pts + b0, ctx->coef, nb, 1.0f, src_scale,
+                           L.org, snap_slot(ctx, sj), fs));
       }
-      return EGH_OK;
-    };
-    if ((s = chunk_end(0))) return s;
-    if (nt >= 2) {
-      CK(launch_inject(slot(ctx, 1), L.F, ctx->rec_pts + b0, ctx->coef, nb, 1.0f, src_scale,
-                       stream));
-      if ((s = chunk_end(1))) return s;
-    }
-    for (int n = 1; n + 1 < nt; ++n) {
-      const int t = n + 1;
-      // the first level of chunk c overwrites chunk c - 2's slots: wait for its transform
-      if (t % K == 0 && t / K >= 2) CK(cudaStreamWaitEvent(stream, ctx->dft_done[(t / K) & 1], 0));
-      CK(launch_fd_step(slot(ctx, n), slot(ctx, n - 1), slot(ctx, t), ctx->coef, L, ctx->S, np,
-                        stream));
-      if ((s = chunk_end(t))) return s;
+      if ((s = fd_chunk_steps(ctx, std::max(t0, 2), t0, t1, sbase, np))) return s;
+      CK(cudaEventRecord(ctx->fd_done[g & 1], fs));
+      CK(cudaStreamWaitEvent(ctx->side, ctx->fd_done[g & 1], 0));
+      CK(launch_dft_tc(ctx->tmap, ctx->twt, ctx->nf, sbase, t1 - t0, t0, L, ctx->gh, b0, nb,
+                       ctx->d_err, ctx->side));
+      CK(cudaEventRecord(ctx->dft_done[g & 1], ctx->side));
     }
   }
-  if (last_dft) CK(cudaStreamWaitEvent(stream, last_dft, 0));
+  CK(cudaEventRecord(ctx->ev_side, ctx->side));
+  CK(cudaStreamWaitEvent(stream, ctx->ev_side, 0));
+  CK(cudaEventRecord(ctx->ev_tune[0], fs));
+  CK(cudaStreamWaitEvent(stream, ctx->ev_tune[0], 0));
   CK(cudaEventRecord(ctx->ev[1], stream));
   ctx->ev_rec[0] = true;
   int derr = 0;
@@ -624,6 +720,7 @@ egh_status egh_forward(egh_ctx* ctx, const float* vel, int32_t nsrc, const int32
     dout = ctx->io_out;
   }
   const float scale = (float)(1.0 / (ctx->dx * ctx->dz));
+  const SnapOut none{nullptr, 0, 0};
   for (int b0 = 0; b0 < nsrc; b0 += B) {
     const int nb = std::min(B, nsrc - b0);
     const int np = (nb + 1) / 2;
@@ -634,10 +731,10 @@ egh_status egh_forward(egh_ctx* ctx, const float* vel, int32_t nsrc, const int32
     for (int n = 0; n + 1 < nt; ++n) {
       if (n > 0)
         CK(launch_fd_step(slot(ctx, n), slot(ctx, n - 1), slot(ctx, n + 1), ctx->coef, L, ctx->S,
-                          np, stream));
+                          np, none, stream, ctx->fd_tz));
       if (wavelet[n] != 0.f)
-        CK(launch_inject(slot(ctx, n + 1), L.F, d_sp + b0, ctx->coef, nb, wavelet[n], scale,
-                         stream));
+        CK(launch_inject(slot(ctx, n + 1), L.F, d_sp + b0, ctx->coef, nb, wavelet[n], scale, L.org,
+                         none, stream));
       CK(launch_record(slot(ctx, n + 1), L.F, ctx->rec_pts, nrec, nb, tr, nt, n + 1, stream));
     }
   }
@@ -699,6 +796,7 @@ egh_status egh_get_stats(egh_ctx* ctx, egh_stats* out) {
       *ms[i] = t;
     }
   ctx->st.kernel_launches = launches_so_far();
+  ctx->st.fd_rows = ctx->fd_tz;
   *out = ctx->st;
   return EGH_OK;
 }

@@ -2,19 +2,24 @@
 //
 // Device data layout (all float32 unless stated):
 //   wavefield level: [NZ + 2*GUARD][PX], rows z = -GUARD .. NZ+GUARD-1, row pitch PX >= NX + 4
-//     (multiple of 32).  Guard rows and columns x >= NX are zero and never written, so the
+//     (multiple of 64).  Guard rows and columns x >= NX are zero and never written, so the
 //     eighth-order stencil reads them as the u = 0 boundary without any bounds test;
-//   ring of 2K time levels for a batch of B receivers in pairs: [2K][B/2][F] float2,
-//     F = (NZ + 2*GUARD) * PX, level n lives in slot n mod 2K (two chunks of K: the transform of
-//     one chunk runs while the next is stepped);
+//   FD state of a batch of B receivers in pairs: [3][B/2][F] float2, F = (NZ + 2*GUARD) * PX,
+//     level n in slot n mod 3 (float2 = receivers 2i, 2i+1 at one point);
+//   snapshot ring of the transform: [2 planes hi/lo][2K slots][Bp receivers][G] bf16, level n of
+//     a chunk in slot (chunk parity) * K + n mod K, point p = z*PX + x (x >= NX and p >= NZ*PX
+//     stay zero); u = hi + lo;
 //   Green transforms gh: [nrec][nf][2][G], planes re/im, G = NZ*PX rounded up to 256, point
 //     p = z*PX + x (entries with x >= NX or p >= NZ*PX are zero);
 //   Hessians Qh, factors Lh: [nf][nrec][nrec] float2 (complex64).
 #pragma once
+#include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
 #include <string>
+#include <vector>
 
 namespace egh {
 
@@ -41,20 +46,33 @@ struct Layout {
 
 // ---- fd.cu ------------------------------------------------------------------------------------
 // Paired levels: float2 per grid point = (receiver 2i, receiver 2i+1); coef = (c1, c3).
+// Snapshot output of one level: hi plane of its slot (receiver 0, point 0) or nullptr for none.
+struct SnapOut {
+  __nv_bfloat16* lvl;
+  long long plane;  // elements from the hi plane to the lo plane
+  long long rec;    // elements between receivers (G)
+};
 cudaError_t launch_check_velocity(const float* vel, long long n, float* d_vmax_bad, cudaStream_t st);
 cudaError_t launch_build_coef(const float* vel, const Layout& L, double dz, double dx, double dt,
                               double R, const float* d_vmax, float2* coef, cudaStream_t st);
+// tz: rows per warp (12, 16, 20, 24 or 32; 0 = default)
 cudaError_t launch_fd_step(const float2* ucur, const float2* uprev, float2* unext,
                            const float2* coef, const Layout& L, const Stencil& S, int npairs,
-                           cudaStream_t st);
+                           const SnapOut& so, cudaStream_t st, int tz);
+int fd_rows_per_warp_default();
+cudaError_t fd_prepare(int nf);  // once per context, before any capture
 cudaError_t launch_inject(float2* u, long long pstride, const int* pts, const float2* coef, int nb,
-                          float amp, float scale, cudaStream_t st);
+                          float amp, float scale, long long org, const SnapOut& so,
+                          cudaStream_t st);
 cudaError_t launch_record(const float2* u, long long pstride, const int* rec_pts, int nrec, int nb,
                           float* traces, int nt, int t, cudaStream_t st);
-cudaError_t launch_dft_chunk(const float2* ring, long long slot_stride, const Layout& L,
-                             int slot0, int kcount, const float4* tw4, int nf, int n0, int npairs,
-                             int nvalid, float* gh, int rec0, int* err, cudaStream_t st);
-size_t dft_chunk_smem(int nf);
+int dft_ncomp(int nf);
+size_t dft_smem(int nf);
+std::vector<unsigned char> dft_twiddle_tiles(const std::vector<double>& f, double dt, int nt);
+cudaError_t make_snap_tmap(CUtensorMap* tm, void* base, long long G, int Bp, int nslot);
+cudaError_t launch_dft_tc(const CUtensorMap& tmap, const unsigned char* twt, int nf, int slot0,
+                          int kcount, int n0, const Layout& L, float* gh, int rec0, int nvalid,
+                          int* err, cudaStream_t st);
 
 // ---- gram.cu ----------------------------------------------------------------------------------
 __host__ __device__ int gram_tiles(int nrec);

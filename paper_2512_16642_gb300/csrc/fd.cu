@@ -11,10 +11,16 @@
 // Receivers are propagated in pairs: a level of a pair stores float2 (receiver 2i, receiver 2i+1)
 // per grid point, so every load, store and arithmetic instruction of the step serves two
 // receivers (packed FP32x2 arithmetic of sm_100+).
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
 #include <cfloat>
 #include <cmath>
+#include <cstring>
+#include <vector>
 
 #include "egh_internal.cuh"
+#include "tc.cuh"
 
 namespace egh {
 
@@ -101,123 +107,305 @@ cudaError_t launch_build_coef(const float* vel, const Layout& L, double dz, doub
 }
 
 // ---------------------------------------------------------------------------------------------
-// One leapfrog step for a batch of receiver pairs.  Each warp owns 32 columns of one pair and
-// marches down FD_TZ rows (fully unrolled, so the nine z-neighbours of its column rotate through
-// registers without moves); the x-neighbours come from a 40-entry row staged in shared memory
-// (32 + 4 halo on each side).  Rows are processed in groups of FD_U whose loads are all issued
-// before the group is computed.  Reads of guard rows and padding columns return the zero
-// boundary, so there is no bounds test on loads; rows past the warp's range are not loaded.
+// One leapfrog step for a batch of receiver pairs.  A warp owns 64 columns of one pair, two
+// adjacent points per lane (one float4 = both receivers at both points), and marches down TZ rows
+// (fully unrolled, so the z-window rotates through registers).  The u^n rows stream through a
+// per-warp ring of FD_RING shared-memory rows (64 points + 4 halo points on each side) filled by
+// cp.async FD_D rows ahead of use; the same ring rows give the x-neighbours (five 16-byte loads
+// per lane).  u^{n-1} and the coefficients are prefetched into registers FD_P rows ahead.  Reads
+// of guard rows and padding columns return the zero boundary, so loads need no bounds test.
+//
+// The Laplacian is taken in first differences: with D_j = u_j - u_{j-1} along an axis,
+//   sum_k c_k (u_{+k} + u_{-k} - 2u) = sum_{j=1..4} C_j (D_{+j} - D_{1-j}),  C_j = sum_{k>=j} c_k,
+// so every rounding is relative to neighbour differences (the large cancelling terms of
+// c_0 u + sum_k c_k (u_{+k} + u_{-k}) never form) and each first difference is formed once.
+//
+// The new level goes to its state slot and, when `so.lvl` is set, its bf16 split u = hi + lo
+// (hi = bf16(u), lo = bf16(u - hi); about 2^-17 relative) goes to the snapshot ring the
+// transform reads.
 // ---------------------------------------------------------------------------------------------
-constexpr int FD_WARPS = 4;
-constexpr int FD_TZ = 16;
-constexpr int FD_U = 4;
+#ifndef EGH_FD_P
+#define EGH_FD_P 4
+#endif
+#ifndef EGH_FD_MINB
+#define EGH_FD_MINB 1
+#endif
+constexpr int FD_RING = 16;     // ring rows per warp (power of two)
+constexpr int FD_D = 11;        // u^n rows in flight ahead of the window's leading row
+constexpr int FD_P = EGH_FD_P;  // u^{n-1} / coefficient rows prefetched ahead
+static_assert(FD_D + 5 <= FD_RING && FD_D + 8 >= FD_RING, "ring rows must cover the prefetch distance");
 
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) {
   return __ffma2_rn(b, make_float2(-1.f, -1.f), a);  // a - b, one rounding
 }
 
-__global__ void __launch_bounds__(32 * FD_WARPS)
+__device__ __forceinline__ unsigned bf2_bits(__nv_bfloat162 v) {
+  return *reinterpret_cast<unsigned*>(&v);
+}
+
+// hi/lo bf16 split of two values of one receiver at adjacent points, packed (point x, point x+1)
+__device__ __forceinline__ void split_bf16(float a, float b, unsigned& hi, unsigned& lo) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  const float2 hf = __bfloat1622float2(h);
+  const float2 r = sub2(make_float2(a, b), hf);
+  hi = bf2_bits(h);
+  lo = bf2_bits(__floats2bfloat162_rn(r.x, r.y));
+}
+
+__device__ __forceinline__ void cp_async16(unsigned dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Scalar arithmetic on purpose: packed FP32x2 instructions bring no extra FMA throughput, and
+// scalar FMAs take the stencil coefficients straight from the kernel parameters.
+__device__ __forceinline__ float lap1(const float (&dz)[8], const float (&e)[8], const Stencil& C) {
+  // C holds the cumulative weights C_j = sum_{k>=j} c_k (see launch_fd_step)
+  float l = C.cz[0] * (dz[4] - dz[3]);
+  l = fmaf(C.cz[1], dz[5] - dz[2], l);
+  l = fmaf(C.cz[2], dz[6] - dz[1], l);
+  l = fmaf(C.cz[3], dz[7] - dz[0], l);
+  l = fmaf(C.cx[0], e[4] - e[3], l);
+  l = fmaf(C.cx[1], e[5] - e[2], l);
+  l = fmaf(C.cx[2], e[6] - e[1], l);
+  l = fmaf(C.cx[3], e[7] - e[0], l);
+  return l;
+}
+
+// A CTA holds one warp per receiver pair of the batch (threadIdx.y = pair), all on the same
+// 64-column x TZ-row tile, so the coefficient rows are read from L2 once and served to the other
+// pairs from L1.
+constexpr int FD_MAXPAIRS = 16;
+
+template <int TZ>
+__global__ void __launch_bounds__(32 * FD_MAXPAIRS, EGH_FD_MINB)
     k_fd_step(const float2* __restrict__ ucur, const float2* __restrict__ uprev,
               float2* __restrict__ unext, const float2* __restrict__ coef, int NZ, int NX, int PX,
-              int org, long long pstride, Stencil S) {
-  __shared__ float2 srow[FD_WARPS][40];
+              int org, long long pstride, Stencil C, SnapOut so) {
+  extern __shared__ __align__(16) float4 ring_all[];  // [pairs][FD_RING][36]
+  float4 (*ring)[36] = reinterpret_cast<float4 (*)[36]>(ring_all + threadIdx.y * FD_RING * 36);
   const int lane = threadIdx.x;
-  const int w = threadIdx.y;
-  const int x0 = blockIdx.x * 32;
-  const int x = x0 + lane;
-  const int z0 = (blockIdx.y * FD_WARPS + w) * FD_TZ;
-  if (z0 >= NZ) return;  // whole warp leaves; only warp-level synchronisation below
-  const long long boff = (long long)blockIdx.z * pstride + org;
-  const float2* __restrict__ uc = ucur + boff;
-  const float2* __restrict__ up = uprev + boff;
-  float2* __restrict__ un = unext + boff;
-  const float2* __restrict__ cf = coef + org;
-  const bool halo = lane < 4 || lane >= 28;
-  const int hcol = lane < 4 ? x0 - 4 + lane : x0 + 4 + lane;
-  const int hslot = lane < 4 ? lane : lane + 8;
-  float2* row = srow[w];
-  const float2 cz0 = make_float2(S.cz[0], S.cz[0]), cz1 = make_float2(S.cz[1], S.cz[1]);
-  const float2 cz2 = make_float2(S.cz[2], S.cz[2]), cz3 = make_float2(S.cz[3], S.cz[3]);
-  const float2 cx0 = make_float2(S.cx[0], S.cx[0]), cx1 = make_float2(S.cx[1], S.cx[1]);
-  const float2 cx2 = make_float2(S.cx[2], S.cx[2]), cx3 = make_float2(S.cx[3], S.cx[3]);
-
-  float2 q[9];
-  const int o0 = (z0 - 4) * PX + x;
-#pragma unroll
-  for (int i = 0; i < 8; ++i) q[i + 1] = uc[o0 + i * PX];
-  const int nrows = min(FD_TZ, NZ - z0);
-#pragma unroll
-  for (int g = 0; g < FD_TZ; g += FD_U) {
-    float2 qn[FD_U], hv[FD_U], uo[FD_U], cc[FD_U];
-#pragma unroll
-    for (int i = 0; i < FD_U; ++i) {
-      if (g + i < nrows) {
-        const int r = (z0 + g + i) * PX;
-        cc[i] = cf[r + x];
-        qn[i] = uc[r + 4 * PX + x];
-        uo[i] = up[r + x];
-        hv[i] = halo ? uc[r + hcol] : make_float2(0.f, 0.f);
-      }
+  const int pair = threadIdx.y;
+  const int x0 = blockIdx.x * 64;
+  const int x = x0 + 2 * lane;  // this lane's first point
+  const int z0 = blockIdx.y * TZ;
+  const int nrows = min(TZ, NZ - z0);
+  const int PX2 = PX >> 1;
+  const int xh = x >> 1;
+  const long long boff = (long long)pair * pstride + org;  // even: float4-aligned
+  const float4* __restrict__ uc = reinterpret_cast<const float4*>(ucur + boff);
+  const float4* __restrict__ up = reinterpret_cast<const float4*>(uprev + boff) + xh;
+  float4* __restrict__ un = reinterpret_cast<float4*>(unext + boff) + xh;
+  const float4* __restrict__ cf = reinterpret_cast<const float4*>(coef + org) + xh;
+  const bool halo = lane < 2 || lane >= 30;
+  const int hcol = lane < 2 ? (x0 >> 1) - 2 + lane : (x0 >> 1) + 32 + (lane - 30);
+  const int hslot = lane < 2 ? lane : 34 + (lane - 30);
+  const unsigned ring0 = (unsigned)__cvta_generic_to_shared(&ring[0][0]);
+  const bool ok0 = x < NX, ok1 = x + 1 < NX;
+  // ring row k holds u^n row z0 - 4 + k; rows z0 - 4 .. z0 + nrows + 3 exist (guard rows included)
+  const int nload = nrows + 8;
+  auto load_row = [&](int k) {
+    if (k < nload) {
+      const int r = (z0 - 4 + k) * PX2;
+      const unsigned dst = ring0 + (unsigned)((k & (FD_RING - 1)) * 36) * 16u;
+      cp_async16(dst + (unsigned)(lane + 2) * 16u, uc + r + xh);
+      if (halo) cp_async16(dst + (unsigned)hslot * 16u, uc + r + hcol);
     }
+    cp_async_commit();  // empty groups keep the group count uniform
+  };
 #pragma unroll
-    for (int i = 0; i < FD_U; ++i) {
-      if (g + i >= nrows) return;
+  for (int k = 0; k < FD_RING; ++k) load_row(k);
+  float4 pu[FD_P], pc[FD_P];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) q[j] = q[j + 1];
-      q[8] = qn[i];
-      row[lane + 4] = q[4];
-      if (halo) row[hslot] = hv[i];
-      __syncwarp();
-      if (x < NX) {
-        // Laplacian as sum_k c_k [(u_{+k} - u) + (u_{-k} - u)] (c_0 = -2 sum_k c_k): neighbour
-        // differences of a well-sampled field are exact in float32, so the large cancelling
-        // terms of c_0 u + sum_k c_k (u_{+k} + u_{-k}) never form.
-        const float2 u0 = q[4];
-        float2 lap = __fmul2_rn(cz0, __fadd2_rn(sub2(q[3], u0), sub2(q[5], u0)));
-        lap = __ffma2_rn(cz1, __fadd2_rn(sub2(q[2], u0), sub2(q[6], u0)), lap);
-        lap = __ffma2_rn(cz2, __fadd2_rn(sub2(q[1], u0), sub2(q[7], u0)), lap);
-        lap = __ffma2_rn(cz3, __fadd2_rn(sub2(q[0], u0), sub2(q[8], u0)), lap);
-        lap = __ffma2_rn(cx0, __fadd2_rn(sub2(row[lane + 3], u0), sub2(row[lane + 5], u0)), lap);
-        lap = __ffma2_rn(cx1, __fadd2_rn(sub2(row[lane + 2], u0), sub2(row[lane + 6], u0)), lap);
-        lap = __ffma2_rn(cx2, __fadd2_rn(sub2(row[lane + 1], u0), sub2(row[lane + 7], u0)), lap);
-        lap = __ffma2_rn(cx3, __fadd2_rn(sub2(row[lane + 0], u0), sub2(row[lane + 8], u0)), lap);
-        const float2 c1 = make_float2(cc[i].x, cc[i].x), c3 = make_float2(cc[i].y, cc[i].y);
-        un[(z0 + g + i) * PX + x] = __ffma2_rn(c3, lap, __ffma2_rn(c1, sub2(u0, uo[i]), uo[i]));
-      }
-      __syncwarp();
+  for (int i = 0; i < FD_P; ++i) {
+    if (i < nrows) {
+      pu[i] = __ldcg(up + (z0 + i) * PX2);
+      pc[i] = __ldg(cf + (z0 + i) * PX2);
     }
   }
+  cp_async_wait<FD_RING - 8>();  // rows 0 .. 7 have landed
+  __syncwarp();
+  // z first differences, component c = (point, receiver) of the lane's float4:
+  // dz[c][m] = D at row z - 3 + m for the current row z; ul = u^n at row z + 3
+  float dz[4][8], ul[4];
+  {
+    const float4 v = ring[0][lane + 2];
+    ul[0] = v.x; ul[1] = v.y; ul[2] = v.z; ul[3] = v.w;
+  }
+#pragma unroll
+  for (int k = 1; k < 8; ++k) {
+    const float4 v = ring[k][lane + 2];
+    const float nv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      dz[c][k] = nv[c] - ul[c];
+      ul[c] = nv[c];
+    }
+  }
+  __syncwarp();  // ring rows 0 .. 2 are refilled next
+#pragma unroll
+  for (int k = FD_RING; k < FD_D + 8; ++k) load_row(k);
+  __nv_bfloat16* sbase = so.lvl ? so.lvl + (long long)(2 * pair) * so.rec + x : nullptr;
+#pragma unroll
+  for (int i = 0; i < TZ; ++i) {
+    if (i >= nrows) break;
+    // row i + 8 (z + 4) was committed FD_D groups ago
+    load_row(FD_D + 8 + i);
+    cp_async_wait<FD_D>();
+    __syncwarp();
+    const float4 uo = pu[i % FD_P], cc = pc[i % FD_P];
+    if (i + FD_P < nrows) {
+      pu[i % FD_P] = __ldcg(up + (z0 + i + FD_P) * PX2);
+      pc[i % FD_P] = __ldg(cf + (z0 + i + FD_P) * PX2);
+    }
+    {
+      const float4 v = ring[(i + 8) & (FD_RING - 1)][lane + 2];  // u^n at row z + 4
+      const float nv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+#pragma unroll
+        for (int m = 0; m < 7; ++m) dz[c][m] = dz[c][m + 1];
+        dz[c][7] = nv[c] - ul[c];
+        ul[c] = nv[c];
+      }
+    }
+    const float4* xr = ring[(i + 4) & (FD_RING - 1)];  // u^n at row z, points x0 - 4 .. x0 + 67
+    const float4 A0 = xr[lane], A1 = xr[lane + 1], A2 = xr[lane + 2], A3 = xr[lane + 3],
+                 A4 = xr[lane + 4];
+    __syncwarp();  // every lane has read ring row i + 4 before it is refilled
+    // receiver a (.x/.z components) and b (.y/.w) at points x - 4 .. x + 5
+    const float wa[10] = {A0.x, A0.z, A1.x, A1.z, A2.x, A2.z, A3.x, A3.z, A4.x, A4.z};
+    const float wb[10] = {A0.y, A0.w, A1.y, A1.w, A2.y, A2.w, A3.y, A3.w, A4.y, A4.w};
+    float ea[9], eb[9];
+#pragma unroll
+    for (int m = 0; m < 9; ++m) {
+      ea[m] = wa[m + 1] - wa[m];
+      eb[m] = wb[m + 1] - wb[m];
+    }
+    const int z = z0 + i;
+    float v[4];
+    {
+      const float e0a[8] = {ea[0], ea[1], ea[2], ea[3], ea[4], ea[5], ea[6], ea[7]};
+      const float e0b[8] = {eb[0], eb[1], eb[2], eb[3], eb[4], eb[5], eb[6], eb[7]};
+      const float e1a[8] = {ea[1], ea[2], ea[3], ea[4], ea[5], ea[6], ea[7], ea[8]};
+      const float e1b[8] = {eb[1], eb[2], eb[3], eb[4], eb[5], eb[6], eb[7], eb[8]};
+      const float la = lap1(dz[0], e0a, C), lb = lap1(dz[1], e0b, C);
+      const float lc = lap1(dz[2], e1a, C), ld = lap1(dz[3], e1b, C);
+      // u^{n+1} = c3 L u + c1 (u - u^{n-1}) + u^{n-1}
+      v[0] = fmaf(cc.y, la, fmaf(cc.x, wa[4] - uo.x, uo.x));
+      v[1] = fmaf(cc.y, lb, fmaf(cc.x, wb[4] - uo.y, uo.y));
+      v[2] = ok1 ? fmaf(cc.w, lc, fmaf(cc.z, wa[5] - uo.z, uo.z)) : 0.f;
+      v[3] = ok1 ? fmaf(cc.w, ld, fmaf(cc.z, wb[5] - uo.w, uo.w)) : 0.f;
+    }
+    if (ok0) {
+      un[z * PX2] = make_float4(v[0], v[1], v[2], v[3]);
+      if (sbase) {
+        unsigned ha, la, hb, lb;
+        split_bf16(v[0], v[2], ha, la);
+        split_bf16(v[1], v[3], hb, lb);
+        __nv_bfloat16* sp = sbase + z * PX;
+        __stcs(reinterpret_cast<unsigned*>(sp), ha);
+        __stcs(reinterpret_cast<unsigned*>(sp + so.plane), la);
+        __stcs(reinterpret_cast<unsigned*>(sp + so.rec), hb);
+        __stcs(reinterpret_cast<unsigned*>(sp + so.rec + so.plane), lb);
+      }
+    }
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+#ifndef EGH_FD_TZDEF
+#define EGH_FD_TZDEF 20
+#endif
+
+int fd_rows_per_warp_default() { return EGH_FD_TZDEF; }
+
+// Raises the dynamic shared-memory limit of every FD and transform kernel instance once per
+// process (outside any stream capture).
+cudaError_t fd_prepare(int nf) {
+  const int fd_smem = (int)(sizeof(float4) * FD_RING * 36 * FD_MAXPAIRS);
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_fd_step<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, fd_smem))) return e;
+  if ((e = cudaFuncSetAttribute(k_fd_step<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, fd_smem))) return e;
+  if ((e = cudaFuncSetAttribute(k_fd_step<20>, cudaFuncAttributeMaxDynamicSharedMemorySize, fd_smem))) return e;
+  if ((e = cudaFuncSetAttribute(k_fd_step<24>, cudaFuncAttributeMaxDynamicSharedMemorySize, fd_smem))) return e;
+  if ((e = cudaFuncSetAttribute(k_fd_step<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, fd_smem))) return e;
+  (void)nf;
+  return cudaSuccess;
 }
 
 cudaError_t launch_fd_step(const float2* ucur, const float2* uprev, float2* unext,
                            const float2* coef, const Layout& L, const Stencil& S, int npairs,
-                           cudaStream_t st) {
-  dim3 block(32, FD_WARPS);
-  const int rows = (L.NZ + FD_WARPS * FD_TZ - 1) / (FD_WARPS * FD_TZ);
-  dim3 grid(L.PX / 32, rows, npairs);
+                           const SnapOut& so, cudaStream_t st, int tz) {
+  if (L.PX % 64 != 0) return cudaErrorInvalidValue;
+  if (tz <= 0) tz = EGH_FD_TZDEF;
+  // cumulative weights C_j = sum_{k>=j} c_k of the first-difference form
+  Stencil C;
+  float az = 0.f, ax = 0.f;
+  for (int k = 3; k >= 0; --k) {
+    az += S.cz[k];
+    ax += S.cx[k];
+    C.cz[k] = az;
+    C.cx[k] = ax;
+  }
+  if (npairs < 1 || npairs > FD_MAXPAIRS) return cudaErrorInvalidValue;
   count_launches(1);
-  k_fd_step<<<grid, block, 0, st>>>(ucur, uprev, unext, coef, L.NZ, L.NX, L.PX, (int)L.org, L.F,
-                                    S);
+  const dim3 blk(32, npairs);
+  const size_t smem = sizeof(float4) * FD_RING * 36 * npairs;
+  const int org = (int)L.org;
+  switch (tz) {
+#define EGH_FD_CASE(T)                                                                          \
+  case T:                                                                                       \
+    k_fd_step<T><<<dim3(L.PX / 64, (L.NZ + T - 1) / T), blk, smem, st>>>(                        \
+        ucur, uprev, unext, coef, L.NZ, L.NX, L.PX, org, L.F, C, so);                           \
+    break;
+    EGH_FD_CASE(12)
+    EGH_FD_CASE(16)
+    EGH_FD_CASE(20)
+    EGH_FD_CASE(24)
+    EGH_FD_CASE(32)
+#undef EGH_FD_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------------------------
 // Point sources on paired levels: receiver b is lane b % 2 of pair b / 2.
 //   u[b][pts[b]] += c3[pts[b]] * amp * scale   (source term dt^2 v^2 f^n / (1 + a), f^n = amp/(dx dz))
+// With `so.lvl` set, the new value's hi/lo split is also written to the snapshot slot (used for
+// level 1 of a Green-function batch, the impulse, whose slot holds zeros).
 // ---------------------------------------------------------------------------------------------
 __global__ void k_inject(float2* __restrict__ u, long long pstride, const int* __restrict__ pts,
-                         const float2* __restrict__ coef, int nb, float amp, float scale) {
+                         const float2* __restrict__ coef, int nb, float amp, float scale,
+                         long long org, SnapOut so) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= nb) return;
   const int p = pts[b];
   float* v = reinterpret_cast<float*>(u + (long long)(b >> 1) * pstride + p) + (b & 1);
-  *v += coef[p].y * amp * scale;
+  const float nv = *v + coef[p].y * amp * scale;
+  *v = nv;
+  if (so.lvl) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(nv);
+    const __nv_bfloat16 l = __float2bfloat16_rn(nv - __bfloat162float(h));
+    __nv_bfloat16* s = so.lvl + (long long)b * so.rec + (p - org);
+    s[0] = h;
+    s[so.plane] = l;
+  }
 }
 
 cudaError_t launch_inject(float2* u, long long pstride, const int* pts, const float2* coef, int nb,
-                          float amp, float scale, cudaStream_t st) {
+                          float amp, float scale, long long org, const SnapOut& so,
+                          cudaStream_t st) {
   count_launches(1);
-  k_inject<<<(nb + 127) / 128, 128, 0, st>>>(u, pstride, pts, coef, nb, amp, scale);
+  k_inject<<<(nb + 127) / 128, 128, 0, st>>>(u, pstride, pts, coef, nb, amp, scale, org, so);
   return cudaGetLastError();
 }
 
@@ -241,184 +429,238 @@ cudaError_t launch_record(const float2* u, long long pstride, const int* rec_pts
 }
 
 // ---------------------------------------------------------------------------------------------
-// On-the-fly transform of one chunk of kcount consecutive levels n0 .. n0+kcount-1 of a batch
-// (ring slots slot0 .. slot0+kcount-1):
-//     gh[rec][k][re/im][p] += sum_j tw[n0+j][k] * u^{n0+j}[rec][p].
-// A block owns D_P points of one receiver pair.  One thread streams the chunk through shared
-// memory in stages of D_SUB levels with 1-D bulk (TMA) copies completing on two mbarriers
-// (double buffer: the next stage lands while the current one is summed); each stage carries the
-// matching twiddle rows, stored as (cos, cos, -sin, -sin) so that one 16-byte load feeds the
-// packed products of both receivers.  Two threads share a pair of adjacent points, each summing
-// half of the frequencies, and keep their accumulators in registers for the whole chunk; gh is
-// read and written once per chunk.  Every mbarrier wait is bounded: on expiry the block records
-// the error flag, waits (bounded) for its copies in flight and leaves.
+// On-the-fly transform of one chunk of levels n0 .. n0+kcount-1 of a batch, on the tensor cores:
+//     gh[rec][c][p] (+)= sum_j u^{n0+j}[rec][p] W[c][n0+j],   W[2k][n] = cos(2 pi f_k n dt),
+//                                                             W[2k+1][n] = -sin(2 pi f_k n dt),
+// in bf16x3: u = u_hi + u_lo (split by the FD step), W = W_hi + W_lo (split on the host), and
+// u_hi W_hi + u_hi W_lo + u_lo W_hi accumulated in FP32 in TMEM (the dropped u_lo W_lo and the
+// splits themselves are ~2^-17 relative).  D = A B^T with M = 128 points per CTA, N = 2 nf
+// rounded up to 32, K = levels in stages of 32; TD_R receivers per CTA share the twiddle tiles.
+// A (snapshots) is MN-major: a 4-D TMA box {64 points, 1 receiver, 32 levels, 2 planes} lands as
+// [plane][level][64 points] 128-byte rows with the 128-byte swizzle (two boxes per receiver).
+// B (twiddles) is K-major in host-swizzled tiles of 64 levels (one 128-byte row per component),
+// one 1-D bulk copy per tile.  One thread issues the copies and the MMAs over a TD_ST-stage ring;
+// at the end every thread reads its point's row of TMEM and adds it into gh (plain store for the
+// chunk that starts at level 0).  Every mbarrier wait is bounded: on expiry the CTA records the
+// error flag, waits (bounded) for its copies and MMAs in flight, frees its TMEM and leaves.
 // ---------------------------------------------------------------------------------------------
-constexpr int D_P = 128;     // points per block
-constexpr int D_SUB = 16;    // levels per stage
-constexpr int D_NFH = 13;    // frequencies per thread and pass
-constexpr long long kWaitLimit = 1LL << 26;  // mbarrier polls before giving up
+#ifndef EGH_TD_R
+#define EGH_TD_R 1
+#endif
+#ifndef EGH_TD_ST
+#define EGH_TD_ST 2
+#endif
+constexpr int TD_M = 128;                // points per CTA (MMA M)
+constexpr int TD_R = EGH_TD_R;           // receivers per CTA
+constexpr int TD_S = 32;                 // levels per stage
+constexpr int TD_ST = EGH_TD_ST;         // stages in flight
+constexpr unsigned TD_AB = 16384;        // one receiver's stage: 2 atoms x 2 planes x 32 x 128 B
 
-__device__ __forceinline__ unsigned smem_u32(const void* p) {
-  return (unsigned)__cvta_generic_to_shared(p);
+int dft_ncomp(int nf) { return (2 * nf + 31) / 32 * 32; }
+
+size_t dft_smem(int nf) {
+  return 1024 + (size_t)TD_ST * TD_R * TD_AB + 2 * 2 * (size_t)dft_ncomp(nf) * 128;
 }
 
-__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-__device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned bytes,
-                                         unsigned bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          dst),
-      "l"(src), "r"(bytes), "r"(bar)
-      : "memory");
-}
-
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity) {
-  for (long long i = 0; i < kWaitLimit; ++i)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
-
-size_t dft_chunk_smem(int nf) {
-  return 2 * (sizeof(float2) * D_SUB * D_P + sizeof(float4) * D_SUB * (size_t)nf);
-}
-
-__global__ void __launch_bounds__(D_P)
-    k_dft_chunk(const float2* __restrict__ ring, long long slot_stride, long long pstride,
-                long long org, int slot0, int kcount, const float4* __restrict__ tw4, int nf,
-                int n0, long long G, float* __restrict__ gh, int rec0, int nvalid,
-                int* __restrict__ err) {
-  extern __shared__ __align__(128) unsigned char dsm[];
-  float2* U = reinterpret_cast<float2*>(dsm);                                    // [2][D_SUB][D_P]
-  float4* T = reinterpret_cast<float4*>(dsm + sizeof(float2) * 2 * D_SUB * D_P);  // [2][D_SUB][nf]
-  __shared__ __align__(8) unsigned long long bars[2];
-  const int tid = threadIdx.x;
-  const int pair = blockIdx.y;
-  const long long p0 = (long long)blockIdx.x * D_P;
-  const float2* src = ring + (long long)pair * pstride + org + p0;
-  const unsigned ub0 = smem_u32(&bars[0]), ub1 = smem_u32(&bars[1]);
+__global__ void __launch_bounds__(128)
+    k_dft_tc(const __grid_constant__ CUtensorMap tmap, const unsigned char* __restrict__ twt,
+             int N, int nf, int slot0, int kcount, int n0, long long G, float* __restrict__ gh,
+             int rec0, int nvalid, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char dsm[];
+  unsigned char* sm = dsm + ((1024 - (tc::smem_u32(dsm) & 1023)) & 1023);
+  unsigned char* As = sm;                               // [TD_ST][TD_R][TD_AB]
+  unsigned char* Bs = sm + TD_ST * TD_R * TD_AB;        // [2][plane][N][128 B]
+  const unsigned tile = 2u * (unsigned)N * 128u;
+  __shared__ __align__(8) unsigned long long bars[2 * TD_ST + 1];  // full[], empty[], done
+  __shared__ unsigned tslot;
+  __shared__ int fail;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int rg = blockIdx.y * TD_R;
+  const int nr = min(TD_R, nvalid - rg);
+  unsigned ncols = 32;
+  while (ncols < (unsigned)(TD_R * N)) ncols <<= 1;
+  if (warp == 0) tc::tmem_alloc(&tslot, ncols);
+  const unsigned bar0 = tc::smem_u32(&bars[0]);
+  auto full = [&](int i) { return bar0 + 8u * i; };
+  auto empty = [&](int i) { return bar0 + 8u * (TD_ST + i); };
+  const unsigned done = bar0 + 8u * (2 * TD_ST);
   if (tid == 0) {
-    mbar_init(ub0, 1);
-    mbar_init(ub1, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    for (int i = 0; i < 2 * TD_ST + 1; ++i) tc::mbar_init(bar0 + 8u * i, 1);
+    fail = 0;
+    tc::mbar_init_fence();
   }
+  tc::tc_fence_before();
   __syncthreads();
-  const int nst = (kcount + D_SUB - 1) / D_SUB;
-  const int npass = (nf + 2 * D_NFH - 1) / (2 * D_NFH);
-  const int total = nst * npass;  // stages over all passes (each pass re-streams the chunk)
-  auto issue = [&](int gs) {
-    const int s = gs % nst, buf = gs & 1;
-    const int j0 = s * D_SUB, jn = min(D_SUB, kcount - j0);
-    const unsigned bar = buf ? ub1 : ub0;
-    mbar_expect_tx(bar, (unsigned)(jn * D_P * sizeof(float2) + jn * nf * sizeof(float4)));
-    for (int j = 0; j < jn; ++j)
-      bulk_g2s(smem_u32(U + (buf * D_SUB + j) * D_P), src + (long long)(slot0 + j0 + j) * slot_stride,
-               D_P * sizeof(float2), bar);
-    bulk_g2s(smem_u32(T + buf * D_SUB * nf), tw4 + (long long)(n0 + j0) * nf,
-             (unsigned)(jn * nf * sizeof(float4)), bar);
-  };
-  if (tid == 0) {
-    issue(0);
-    if (total > 1) issue(1);
-  }
-  const int fh = tid & 1, pt = tid >> 1;
-  const int lp = 2 * pt;  // this thread's two points
-  for (int pass = 0; pass < npass; ++pass) {
-    const int fbase = pass * 2 * D_NFH + fh * D_NFH;
-    const int fn = max(0, min(D_NFH, nf - fbase));
-    float2 ar0[D_NFH], ai0[D_NFH], ar1[D_NFH], ai1[D_NFH];
+  tc::tc_fence_after();
+  const unsigned tmem = tslot;
+  const int p0 = blockIdx.x * TD_M;
+  const int nst = (kcount + TD_S - 1) / TD_S;
+  if (warp == 0) {
+    if (tid == 0) {
+      const unsigned idesc = tc::idesc_bf16(TD_M, N, 1, 0);
+      // snapshots are read once: stream them through L2 as evict-first so that the FD's state
+      // levels, which the concurrent FD steps re-read, stay resident
+      const uint64_t pol = tc::l2_evict_first_policy();
+      auto issue = [&](int s) {
+        const int buf = s % TD_ST;
+        const int n = n0 + s * TD_S;
+        const bool newtile = s == 0 || (n & 63) == 0;
+        tc::mbar_expect_tx(full(buf), (unsigned)nr * TD_AB + (newtile ? tile : 0u));
+        for (int r = 0; r < nr; ++r)
+          for (int m = 0; m < 2; ++m)
+            tc::tma_load_4d_hint(tc::smem_u32(As + (buf * TD_R + r) * TD_AB + m * 8192), &tmap,
+                                 p0 + 64 * m, rg + r, slot0 + s * TD_S, 0, full(buf), pol);
+        if (newtile)
+          tc::bulk_g2s(tc::smem_u32(Bs + ((n >> 6) & 1) * tile), twt + (size_t)(n >> 6) * tile, tile,
+                       full(buf));
+      };
+      int issued = 0, landed = 0;
+      bool ok = true;
+      for (; issued < min(nst, TD_ST); ++issued) issue(issued);
+      for (int s = 0; s < nst; ++s) {
+        const int buf = s % TD_ST;
+        if (!tc::mbar_wait(full(buf), (s / TD_ST) & 1)) {
+          ok = false;
+          break;
+        }
+        landed = s + 1;
+        tc::tc_fence_after();
+        const int n = n0 + s * TD_S;
+        const unsigned bh = tc::smem_u32(Bs + ((n >> 6) & 1) * tile) + (unsigned)(n & 63) * 2u;
+        const unsigned bl = bh + (unsigned)N * 128u;
+        for (int r = 0; r < nr; ++r) {
+          const unsigned ab = tc::smem_u32(As + (buf * TD_R + r) * TD_AB);
+          const unsigned dt = tmem + (unsigned)(r * N);
 #pragma unroll
-    for (int i = 0; i < D_NFH; ++i)
-      ar0[i] = ai0[i] = ar1[i] = ai1[i] = make_float2(0.f, 0.f);
-    for (int s = 0; s < nst; ++s) {
-      const int gs = pass * nst + s, buf = gs & 1;
-      const unsigned bar = buf ? ub1 : ub0;
-      const bool ok = mbar_wait_bounded(bar, (gs >> 1) & 1);
-      if (__syncthreads_or(!ok)) {  // block-uniform decision: every thread leaves together
-        if (tid == 0) atomicExch(err, 1);
-        // let this block's copies in flight land before leaving (bounded)
-        mbar_wait_bounded(bar, (gs >> 1) & 1);
-        if (gs + 1 < total) mbar_wait_bounded(buf ? ub0 : ub1, ((gs + 1) >> 1) & 1);
-        return;
-      }
-      const int jn = min(D_SUB, kcount - s * D_SUB);
-      const float2* Ub = U + buf * D_SUB * D_P + lp;
-      const float4* Tb = T + buf * D_SUB * nf + fbase;
-      for (int j = 0; j < jn; ++j) {
-        const float4 sv = *reinterpret_cast<const float4*>(Ub + j * D_P);
-        const float2 s0 = make_float2(sv.x, sv.y), s1 = make_float2(sv.z, sv.w);
-        const float4* tj = Tb + j * nf;
-#pragma unroll
-        for (int i = 0; i < D_NFH; ++i) {
-          if (i < fn) {
-            const float4 w = tj[i];
-            const float2 c = make_float2(w.x, w.y), sn = make_float2(w.z, w.w);
-            ar0[i] = __ffma2_rn(c, s0, ar0[i]);
-            ai0[i] = __ffma2_rn(sn, s0, ai0[i]);
-            ar1[i] = __ffma2_rn(c, s1, ar1[i]);
-            ai1[i] = __ffma2_rn(sn, s1, ai1[i]);
+          for (int ks = 0; ks < 2; ++ks) {
+            const uint64_t ahi = tc::sdesc_sw128_lbo_sbo(ab + ks * 2048, 8192, 1024);
+            const uint64_t alo = tc::sdesc_sw128_lbo_sbo(ab + 4096 + ks * 2048, 8192, 1024);
+            const uint64_t bhi = tc::sdesc_sw128(bh + ks * 32), blo = tc::sdesc_sw128(bl + ks * 32);
+            tc::mma_bf16(dt, ahi, bhi, idesc, s > 0 || ks > 0);
+            tc::mma_bf16(dt, ahi, blo, idesc, true);
+            tc::mma_bf16(dt, alo, bhi, idesc, true);
           }
         }
-      }
-      __syncthreads();  // everyone is done with this buffer
-      if (tid == 0 && gs + 2 < total) issue(gs + 2);
-    }
-    // add into gh: receiver a = lane x, receiver b = lane y of each packed accumulator
-#pragma unroll
-    for (int i = 0; i < D_NFH; ++i) {
-      if (i < fn) {
-        const int f = fbase + i;
-#pragma unroll
-        for (int r = 0; r < 2; ++r) {
-          const int b = 2 * pair + r;
-          if (b >= nvalid) continue;
-          float* g = gh + ((long long)(rec0 + b) * nf + f) * 2 * G + p0 + lp;
-          float2* gre = reinterpret_cast<float2*>(g);
-          float2* gim = reinterpret_cast<float2*>(g + G);
-          float2 re = *gre, im = *gim;
-          re.x += r ? ar0[i].y : ar0[i].x;
-          re.y += r ? ar1[i].y : ar1[i].x;
-          im.x += r ? ai0[i].y : ai0[i].x;
-          im.y += r ? ai1[i].y : ai1[i].x;
-          *gre = re;
-          *gim = im;
+        tc::mma_commit(empty(buf));
+        if (issued < nst) {  // the next stage to issue reuses this stage's buffer
+          if (!tc::mbar_wait(empty(buf), (s / TD_ST) & 1)) {
+            ok = false;
+            break;
+          }
+          issue(issued);
+          ++issued;
         }
+      }
+      if (!ok) {
+        fail = 1;
+        atomicExch(err, 1);
+        // let the copies in flight land (bounded) before the CTA leaves
+        for (int s = landed; s < issued; ++s) tc::mbar_wait(full(s % TD_ST), (s / TD_ST) & 1);
+      }
+      tc::mma_commit(done);  // arrives once every MMA issued so far has completed
+    }
+    __syncwarp();
+  }
+  const bool okd = tc::mbar_wait(done, 0);
+  if (!__syncthreads_or(!okd) && !fail) {
+    tc::tc_fence_after();
+    const bool first = n0 == 0;
+    const long long p = p0 + tid;
+    for (int r = 0; r < nr; ++r) {
+      float* g = gh + (long long)(rec0 + rg + r) * 2 * nf * G + p;
+      for (int c0 = 0; c0 < N; c0 += 32) {
+        float v[32], o[32];
+        tc::tmem_ld32(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(r * N + c0), v);
+        // all loads of the group before any store: the 32 column planes are distinct
+#pragma unroll
+        for (int i = 0; i < 32; ++i)
+          o[i] = (!first && c0 + i < 2 * nf) ? __ldcs(g + (long long)(c0 + i) * G) : 0.f;
+#pragma unroll
+        for (int i = 0; i < 32; ++i)
+          if (c0 + i < 2 * nf) __stcs(g + (long long)(c0 + i) * G, o[i] + v[i]);
+      }
+    }
+  } else if (tid == 0) {
+    atomicExch(err, 1);
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, ncols);
+}
+
+cudaError_t launch_dft_tc(const CUtensorMap& tmap, const unsigned char* twt, int nf, int slot0,
+                          int kcount, int n0, const Layout& L, float* gh, int rec0, int nvalid,
+                          int* err, cudaStream_t st) {
+  const int N = dft_ncomp(nf);
+  if (L.G % TD_M != 0 || N > 128 || kcount < 1 || slot0 % TD_S != 0 || n0 % TD_S != 0 ||
+      nvalid < 1)
+    return cudaErrorInvalidValue;
+  const size_t smem = dft_smem(nf);
+  cudaError_t e =
+      cudaFuncSetAttribute(k_dft_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((unsigned)(L.G / TD_M), (unsigned)((nvalid + TD_R - 1) / TD_R));
+  count_launches(1);
+  k_dft_tc<<<grid, 128, smem, st>>>(tmap, twt, N, nf, slot0, kcount, n0, L.G, gh, rec0, nvalid,
+                                    err);
+  return cudaGetLastError();
+}
+
+// Twiddle tiles for k_dft_tc: for every 64 levels, a hi tile and a lo tile of [N][64] bf16 in the
+// 128-byte-swizzled K-major layout (row c, level j at byte (c/8)*1024 + (c%8)*128 +
+// (((2j/16) ^ (c%8)) * 16) + 2j%16); row 2k = cos(2 pi f_k n dt), row 2k+1 = -sin(2 pi f_k n dt)
+// with the phase reduced as 2 pi frac(f_k n dt) in double precision; hi = bf16(w),
+// lo = bf16(w - hi); rows >= 2 nf and levels >= nt are zero.
+std::vector<unsigned char> dft_twiddle_tiles(const std::vector<double>& f, double dt, int nt) {
+  const int nf = (int)f.size(), N = dft_ncomp(nf);
+  const int ntile = (nt + 63) / 64;
+  const size_t tile = 2ull * N * 128;
+  std::vector<unsigned char> out((size_t)ntile * tile, 0);
+  for (int n = 0; n < nt; ++n) {
+    unsigned char* hi = out.data() + (size_t)(n / 64) * tile;
+    unsigned char* lo = hi + (size_t)N * 128;
+    const int j = n % 64;
+    for (int k = 0; k < nf; ++k) {
+      double ph = f[k] * (double)n * dt;
+      ph -= std::floor(ph);
+      const double a = 2.0 * M_PI * ph;
+      const double v[2] = {std::cos(a), -std::sin(a)};
+      for (int q = 0; q < 2; ++q) {
+        const int c = 2 * k + q;
+        const size_t off = (size_t)(c >> 3) * 1024 + (c & 7) * 128 +
+                           ((((2 * j) >> 4) ^ (c & 7)) << 4) + ((2 * j) & 15);
+        const __nv_bfloat16 h = __float2bfloat16_rn((float)v[q]);
+        const __nv_bfloat16 l = __float2bfloat16_rn((float)(v[q] - (double)__bfloat162float(h)));
+        std::memcpy(hi + off, &h, 2);
+        std::memcpy(lo + off, &l, 2);
       }
     }
   }
+  return out;
 }
 
-cudaError_t launch_dft_chunk(const float2* ring, long long slot_stride, const Layout& L,
-                             int slot0, int kcount, const float4* tw4, int nf, int n0, int npairs,
-                             int nvalid, float* gh, int rec0, int* err, cudaStream_t st) {
-  if (L.G % D_P != 0) return cudaErrorInvalidValue;
-  const size_t smem = dft_chunk_smem(nf);
-  cudaError_t e =
-      cudaFuncSetAttribute(k_dft_chunk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  dim3 grid((unsigned)(L.G / D_P), npairs);
-  count_launches(1);
-  k_dft_chunk<<<grid, D_P, smem, st>>>(ring, slot_stride, L.F, L.org, slot0, kcount, tw4, nf, n0,
-                                       L.G, gh, rec0, nvalid, err);
-  return cudaGetLastError();
+// Tensor map of the snapshot ring [2 planes][nslot][Bp receivers][G] bf16 for k_dft_tc's boxes
+// {64 points, 1 receiver, 32 levels, 2 planes} with the 128-byte swizzle.
+cudaError_t make_snap_tmap(CUtensorMap* tm, void* base, long long G, int Bp, int nslot) {
+  static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
+  if (!enc) {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    cudaError_t e =
+        cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const cuuint64_t dims[4] = {(cuuint64_t)G, (cuuint64_t)Bp, (cuuint64_t)nslot, 2};
+  const cuuint64_t str[3] = {(cuuint64_t)G * 2, (cuuint64_t)G * 2 * Bp,
+                             (cuuint64_t)G * 2 * Bp * nslot};
+  const cuuint32_t box[4] = {64, 1, (cuuint32_t)TD_S, 2};
+  const cuuint32_t es[4] = {1, 1, 1, 1};
+  const CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, base, dims, str, box, es,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 }  // namespace egh

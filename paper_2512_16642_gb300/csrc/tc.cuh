@@ -1,12 +1,13 @@
-// Blackwell (sm_100+) building blocks used by the tensor-core kernels: mbarriers, 1-D bulk (TMA)
-// copies, tcgen05 (TMEM allocation, MMA issue, commit, loads) and the 128-byte-swizzled K-major
-// shared-memory layout the MMA reads.
+// Blackwell (sm_100+) building blocks used by the tensor-core kernels: mbarriers, 1-D bulk and
+// tiled (TMA) copies, tcgen05 (TMEM allocation, MMA issue, commit, loads) and the shared-memory
+// matrix descriptors of the 128-byte-swizzled layouts the MMA reads.
 //
-// Layout: a [rows][32] float tile is stored as 8-row atoms of 1024 bytes; row r of the tile is
-// 128 bytes at atom (r / 8), row (r % 8), and its 16-byte chunk c sits at chunk position
-// c ^ (r % 8).  Tiles start on 1024-byte boundaries.  The MMA descriptor of such a tile has
-// stride-byte-offset 1024 (between atoms) and the K offset of an 8-element (32-byte) step is
-// added to its start address.
+// 128-byte swizzle: a tile is stored as 8-row atoms of 1024 bytes (rows of 128 bytes); the
+// 16-byte chunk c of row r sits at chunk position c ^ (r % 8).  Tiles start on 1024-byte
+// boundaries.  K-major operands (rows = M/N index, 128 bytes of K per row): stride-byte-offset =
+// 1024 between 8-row groups, and a K step inside the 128 bytes is added to the start address.
+// MN-major operands (rows = K index, 128 bytes of M/N per row): leading-byte-offset = bytes
+// between 128-byte-wide M/N atoms, stride-byte-offset = bytes between 8-row K groups.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -15,28 +16,8 @@
 namespace egh {
 namespace tc {
 
-constexpr long long kWaitLimit = 1LL << 26;  // mbarrier polls before a wait gives up
-
-__host__ __device__ inline unsigned sw128_offset(int r, int k) {
-  const int c = k >> 2, e = k & 3;
-  return (unsigned)((r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4) + (e << 2));
-}
-
-// tf32 operand split x = hi + lo with hi exactly representable in tf32 (low 13 mantissa bits
-// cleared) and lo = x - hi exact in float32.
-__host__ __device__ inline float tf32_hi(float x) {
-#ifdef __CUDA_ARCH__
-  return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
-#else
-  union {
-    float f;
-    uint32_t u;
-  } v;
-  v.f = x;
-  v.u &= 0xFFFFE000u;
-  return v.f;
-#endif
-}
+constexpr long long kWaitLimit = 1LL << 26;       // mbarrier polls before a wait gives up
+constexpr unsigned long long kWaitNs = 2000000000ull;  // or this many nanoseconds
 
 #ifdef __CUDACC__
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
@@ -67,9 +48,20 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
   return ok != 0;
 }
 
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait: gives up after kWaitLimit polls or kWaitNs nanoseconds, whichever comes first.
 __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
-  for (long long i = 0; i < kWaitLimit; ++i)
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer_ns();
+  for (long long i = 0; i < kWaitLimit; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 63) == 63 && globaltimer_ns() - t0 > kWaitNs) return false;
+  }
   return false;
 }
 
@@ -118,18 +110,47 @@ __device__ __forceinline__ uint64_t sdesc_sw128(unsigned saddr) {
   return d;
 }
 
-// instruction descriptor: D f32, A and B tf32, both K-major, M x N
-__host__ __device__ inline unsigned idesc_tf32(int M, int N) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((unsigned)(N >> 3) << 17) |
-         ((unsigned)(M >> 4) << 24);
+// shared-memory matrix descriptor with explicit leading/stride byte offsets, 128-byte swizzle.
+// K-major: lbo unused, sbo = bytes between 8-row groups.  MN-major: lbo = bytes between
+// 64-element (128-byte) atoms along M/N, sbo = bytes between 8-row groups along K.
+__device__ __forceinline__ uint64_t sdesc_sw128_lbo_sbo(unsigned saddr, unsigned lbo, unsigned sbo) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
 }
 
-__device__ __forceinline__ void mma_tf32(unsigned dtmem, uint64_t adesc, uint64_t bdesc,
+// instruction descriptor: D f32, A and B bf16, M x N; a_mn = 1 for an MN-major A
+__host__ __device__ inline unsigned idesc_bf16(int M, int N, int a_mn, int b_mn) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)a_mn << 15) | ((unsigned)b_mn << 16) |
+         ((unsigned)(N >> 3) << 17) | ((unsigned)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(unsigned dtmem, uint64_t adesc, uint64_t bdesc,
                                          unsigned idesc, bool accumulate) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"((int)accumulate)
+      : "memory");
+}
+
+// L2 policy for data read once (streamed through L2 without displacing resident working sets)
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+// 4-D tiled TMA load with an L2 cache policy
+__device__ __forceinline__ void tma_load_4d_hint(unsigned dst, const void* tmap, int c0, int c1,
+                                                 int c2, int c3, unsigned bar, uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6], %7;" ::"r"(dst),
+      "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar), "l"(policy)
       : "memory");
 }
 
@@ -140,19 +161,21 @@ __device__ __forceinline__ void mma_commit(unsigned bar) {
       : "memory");
 }
 
-// 16 consecutive columns of this warp's 32 TMEM lanes (one lane per thread)
-__device__ __forceinline__ void tmem_ld16(unsigned taddr, float (&v)[16]) {
-  unsigned r[16];
+// 32 consecutive columns of this warp's 32 TMEM lanes (one lane per thread), one wait
+__device__ __forceinline__ void tmem_ld32(unsigned taddr, float (&v)[32]) {
+  unsigned r[32];
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
-      "%15}, [%16];"
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
         "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+        "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+        "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 #endif
 

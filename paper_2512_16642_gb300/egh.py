@@ -32,7 +32,8 @@ class egh_config(ctypes.Structure):
         ("nrec", ctypes.c_int32), ("rec_iz", _i32p), ("rec_ix", _i32p),
         ("nfreq", ctypes.c_int32), ("freq_hz", _f64p),
         ("batch_receivers", ctypes.c_int32), ("dft_chunk", ctypes.c_int32),
-        ("gram_splits", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5),
+        ("gram_splits", ctypes.c_int32), ("fd_rows", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 4),
     ]
 
 
@@ -45,6 +46,7 @@ class egh_stats(ctypes.Structure):
         ("nz_pad", ctypes.c_int32), ("nx_pad", ctypes.c_int32), ("pitch", ctypes.c_int32),
         ("batch_receivers", ctypes.c_int32), ("dft_chunk", ctypes.c_int32),
         ("gram_splits", ctypes.c_int32), ("kernel_launches", ctypes.c_int64),
+        ("fd_rows", ctypes.c_int32), ("pad_", ctypes.c_int32),
     ]
 
     def as_dict(self):
@@ -134,14 +136,14 @@ def _i32(a):
 
 # ---- the ABI calls, same names -----------------------------------------------------------
 def egh_create(nz, nx, dz, dx, nsponge, sponge_R, dt, nt, rec_iz, rec_ix, freq_hz,
-               batch_receivers=0, dft_chunk=0, gram_splits=0):
+               batch_receivers=0, dft_chunk=0, gram_splits=0, fd_rows=0):
     lib = load()
     riz, riz_p = _i32(rec_iz)
     rix, rix_p = _i32(rec_ix)
     f = np.ascontiguousarray(freq_hz, dtype=np.float64)
     cfg = egh_config(int(nz), int(nx), float(dz), float(dx), int(nsponge), float(sponge_R), float(dt),
                      int(nt), int(riz.size), riz_p, rix_p, int(f.size), f.ctypes.data_as(_f64p),
-                     int(batch_receivers), int(dft_chunk), int(gram_splits))
+                     int(batch_receivers), int(dft_chunk), int(gram_splits), int(fd_rows))
     h = _vp()
     _check(lib.egh_create(ctypes.byref(cfg), ctypes.byref(h)), None)
     return h
