@@ -35,9 +35,12 @@ METRIC = "Hessian build+factor s/update"
 UNIT = "s/update"
 FALLBACK_HBM_GBS = 6800.0
 
-# DRAM traffic of the Green stage per update from the committed ncu capture, valid only for the
-# kernel sources it was taken from (sha256 of csrc/fd.cu); None until a capture exists.
-GREEN_TRAFFIC = {"fd_sha256": None, "bytes_per_update": None}
+# DRAM traffic (read + write bytes) per launch of the FD step and of the transform from the
+# committed ncu capture (profiles/), valid only for the kernel sources it was taken from (sha256
+# of csrc/fd.cu); None until a capture exists.
+KERNEL_TRAFFIC = {"fd_sha256": "0dbde35b7433ee9a6a2c7ed837f8842a2a2f9e9bb9fbb1654a1ef2eac6495fce",
+                  "k_fd_step": 31.22e6,   # 2.52 MB read + 28.70 MB write per launch
+                  "k_dft_tc": 13.19e9}    # 12.02 GB read + 1.16 GB write per 512-level launch
 
 
 def _args():
@@ -48,6 +51,13 @@ def _args():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--resid", choices=["model", "noise"], default="model",
+                   help="residual gathers from forward modelling in the true and start models, or "
+                        "seeded band-limited noise of the same shape (skips the modelling launches)")
+    p.add_argument("--slice", action="store_true",
+                   help="profiling slice: one batch of 16 receivers, nt 1024, no e2e or CPU baseline")
+    p.add_argument("--dft-chunk", type=int, default=0,
+                   help="levels per transform chunk (0 = library default); for bounded ncu captures")
     return p.parse_args()
 
 
@@ -202,8 +212,13 @@ def oracle_sample(c, green_steps=60, gram_receivers=None, deblur_sources=4):
 
 
 def _workload(c, extra=None):
-    cfg = {"workload": "layered-faulted 921x301 (padded 961x341), dx 10 m, 231 receivers, 115 sources, "
-                       "nt 4000 dt 1 ms, 26 frequencies 3.0:0.2:8.0 Hz, mu 1e-2 mean diag",
+    if c.rec_ix.size == 231 and c.nt == 4000:
+        name = ("layered-faulted 921x301 (padded 961x341), dx 10 m, 231 receivers, 115 sources, "
+                "nt 4000 dt 1 ms, 26 frequencies 3.0:0.2:8.0 Hz, mu 1e-2 mean diag")
+    else:
+        name = (f"profiling slice of the layered-faulted 921x301 workload: {c.rec_ix.size} receivers, "
+                f"{c.src_ix.size} sources, nt {c.nt}")
+    cfg = {"workload": name,
            "nz": c.nz, "nx": c.nx, "nsponge": c.nsponge, "nrec": int(c.rec_ix.size),
            "nsrc": int(c.src_ix.size), "nt": c.nt, "nfreq": int(c.freqs.size),
            "l2": "inputs larger than L2 (16 GB transforms, 425 MB residuals); no flush"}
@@ -252,18 +267,26 @@ def run_ours(args):
     ws, rank, local = _dist()
     torch.cuda.set_device(local)
     c = synth.case_layered()
+    if args.slice:
+        c = synth.slice_case(c, nrec=16, nt=1024)
+        args.e2e_steps, args.no_cpu_baseline = 0, True
     nr, ns, nt, nf = c.rec_ix.size, c.src_ix.size, c.nt, c.freqs.size
-    ctx = egh.Context(c.nz, c.nx, c.dz, c.dx, c.nsponge, c.sponge_R, c.dt, c.nt, c.rec_iz, c.rec_ix, c.freqs)
+    ctx = egh.Context(c.nz, c.nx, c.dz, c.dx, c.nsponge, c.sponge_R, c.dt, c.nt, c.rec_iz, c.rec_ix, c.freqs,
+                      dft_chunk=args.dft_chunk)
     stream = torch.cuda.current_stream()
     v_start = torch.from_numpy(np.float32(c.vel_start)).cuda()
-    v_true = torch.from_numpy(np.float32(c.vel_true)).cuda()
-    w32 = synth.ricker(nt, c.dt, c.ricker_hz).astype(np.float32)
-    resid = torch.empty((ns, nr, nt), device="cuda")
-    tmp = torch.empty_like(resid)
-    ctx.forward(v_true, c.src_iz, c.src_ix, w32, resid)
-    ctx.forward(v_start, c.src_iz, c.src_ix, w32, tmp)
-    resid -= tmp
-    del tmp
+    if args.resid == "noise":
+        noise = synth.bandlimited_noise(np.random.default_rng(5), (ns, nr, nt), c.dt, 2.0, 10.0)
+        resid = torch.from_numpy(noise.astype(np.float32)).cuda()
+    else:
+        v_true = torch.from_numpy(np.float32(c.vel_true)).cuda()
+        w32 = synth.ricker(nt, c.dt, c.ricker_hz).astype(np.float32)
+        resid = torch.empty((ns, nr, nt), device="cuda")
+        tmp = torch.empty_like(resid)
+        ctx.forward(v_true, c.src_iz, c.src_ix, w32, resid)
+        ctx.forward(v_start, c.src_iz, c.src_ix, w32, tmp)
+        resid -= tmp
+        del tmp
     mult = torch.empty_like(resid)
 
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
@@ -272,6 +295,9 @@ def run_ours(args):
         e = [ev() for _ in range(4)]
         e[0].record(stream)
         ctx.green(v_start)
+        if rec is not None:
+            st_g = ctx.stats()
+            kern.append((st_g["fd_ms"], st_g["fd_launches"], st_g["dft_ms"], st_g["dft_launches"]))
         e[1].record(stream)
         ctx.hessian(egh.EGH_MU_REL_MEANDIAG, c.mu_alpha)
         ctx.factor()
@@ -289,7 +315,7 @@ def run_ours(args):
     clk = ClockSampler(local)
     clk.start()
     l0 = ctx.stats()["kernel_launches"]
-    recs = []
+    recs, kern = [], []
     t_start, t_end = ev(), ev()
     t_start.record(stream)
     for _ in range(args.steps):
@@ -314,7 +340,7 @@ def run_ours(args):
     r_host = resid.cpu().pin_memory()
     m_host = torch.empty_like(r_host).pin_memory()
     e2e_bf, e2e_deb = [], []
-    for i in range(args.e2e_steps + 1):
+    for i in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ctx.green(v_host)
@@ -327,33 +353,63 @@ def run_ours(args):
         if i > 0:
             e2e_bf.append(t1 - t0)
             e2e_deb.append(t2 - t1)
-    e2e_v = _max_over_ranks(ws, statistics.mean(e2e_bf)) / ws
+    e2e_v = _max_over_ranks(ws, statistics.mean(e2e_bf)) / ws if e2e_bf else None
 
     if rank != 0:
         return
     hbm, peak_kind = _peaks()
     point_steps = st["point_steps"]
     green_s = statistics.mean(green_ms) / 1e3
-    alg_bytes = 12.0 * point_steps
-    achieved = alg_bytes / green_s / 1e9
     with open(os.path.join(ROOT, "paper_2512_16642_gb300", "csrc", "fd.cu"), "rb") as f:
         fd_sha = hashlib.sha256(f.read()).hexdigest()
-    traffic = GREEN_TRAFFIC["bytes_per_update"] if GREEN_TRAFFIC["fd_sha256"] == fd_sha else None
+    traffic_ok = KERNEL_TRAFFIC["fd_sha256"] == fd_sha
+    fd_ms = statistics.mean(k[0] for k in kern)
+    fd_n = kern[-1][1]
+    dft_ms = statistics.mean(k[2] for k in kern)
+    dft_n = kern[-1][3]
+    npts = point_steps // (nr * nt)  # padded grid points NZ * NX
+    nchunk = dft_n // ((nr + st["batch_receivers"] - 1) // st["batch_receivers"])
+    # FD step: 12 algorithmic bytes per receiver point-step (read u^n, u^{n-1}, write u^{n+1})
+    fd_alg = 12.0 * point_steps / fd_n
+    fd_achieved = fd_alg / (fd_ms / fd_n * 1e-3) / 1e9
+    # transform: 4 B per receiver point-step (bf16 hi + lo snapshot) + the gh read-modify-write
+    # of 2 nf floats per receiver point per chunk (write only for the first chunk)
+    dft_alg = (4.0 * point_steps + nr * npts * 2 * nf * 4 * (2 * nchunk - 1)) / dft_n
+    dft_achieved = dft_alg / (dft_ms / dft_n * 1e-3) / 1e9
     line = {
         "metric": METRIC, "value": bf_s_max / ws, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": _workload(c, {"batch_receivers": st["batch_receivers"], "dft_chunk": st["dft_chunk"],
-                                "gram_splits": st["gram_splits"]}),
-        "stages_ms": {"green": statistics.mean(green_ms), "build_factor": statistics.mean(bf_ms),
+                                "gram_splits": st["gram_splits"], "fd_rows": st["fd_rows"],
+                                "residuals": "forward modelling (true - start)" if args.resid == "model"
+                                else "seeded band-limited noise 2-10 Hz"}),
+        "stages_ms": {"green": statistics.mean(green_ms), "green_fd": fd_ms, "green_transform": dft_ms,
+                      "build_factor": statistics.mean(bf_ms),
                       "hessian_factor": statistics.mean(bf_ms) - statistics.mean(green_ms),
                       "deblur": statistics.mean(deb_ms)},
         "deblur_sources_per_s": ns / (statistics.mean(deb_ms) / 1e3),
-        "roofline": {"kernel": "Green stage: k_fd_step + k_dft_chunk (one egh_green)", "bound": "hbm",
-                     "achieved": achieved, "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": traffic,
-                     "algorithmic_bytes": alg_bytes, "per": "update (12 B per point-step)"},
-        "e2e": {"value": e2e_v, "unit": UNIT,
+        "roofline": {"kernel": "k_fd_step (FD step, 60% of the update)", "bound": "hbm",
+                     "achieved": fd_achieved, "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": fd_achieved / hbm,
+                     "traffic": KERNEL_TRAFFIC["k_fd_step"] if traffic_ok else None,
+                     "algorithmic_bytes_per_launch": fd_alg,
+                     "launches": fd_n, "avg_launch_ms": fd_ms / fd_n,
+                     "note": "12 B per receiver point-step; duration = per-chunk CUDA events on the FD "
+                             "stream / launches (graph-replayed steps, gaps included); the measured "
+                             "limiter is L2 bandwidth (see profiles/)"},
+        "roofline_transform": {"kernel": "k_dft_tc (tensor-core transform)", "bound": "hbm",
+                               "achieved": dft_achieved, "peak": hbm, "peak_kind": peak_kind,
+                               "unit": "GB/s", "frac": dft_achieved / hbm,
+                               "traffic": KERNEL_TRAFFIC["k_dft_tc"] if traffic_ok else None,
+                               "algorithmic_bytes_per_launch": dft_alg, "launches": dft_n,
+                               "avg_launch_ms": dft_ms / dft_n,
+                               "note": "runs beside the next chunk's FD steps on a low-priority stream"},
+        "green_stage": {"achieved": 12.0 * point_steps / green_s / 1e9, "unit": "GB/s",
+                        "frac": 12.0 * point_steps / green_s / 1e9 / hbm,
+                        "note": "whole egh_green (FD + transform), 12 B per receiver point-step"},
+        "e2e": None if e2e_v is None else {
+                "value": e2e_v, "unit": UNIT,
                 "h2d_bytes_per_step": int(v_host.numel() * 4 + r_host.numel() * 4),
                 "d2h_bytes_per_step": int(m_host.numel() * 4 + 8 + 4 * nf),
                 "deblur_sources_per_s": ns / statistics.mean(e2e_deb),

@@ -113,6 +113,10 @@ typedef struct {
     int64_t kernel_launches;   /* kernels this library has launched since it was loaded (all contexts) */
     int32_t fd_rows;           /* FD rows per warp in use (0 until chosen) */
     int32_t pad_;
+    double fd_ms;              /* last egh_green: device time of the FD steps (per-chunk events) */
+    double dft_ms;             /* last egh_green: device time of the transform launches */
+    int64_t fd_launches;       /* last egh_green: FD step launches */
+    int64_t dft_launches;      /* last egh_green: transform launches */
 } egh_stats;
 
 /* Validates the configuration and allocates the device state on the current

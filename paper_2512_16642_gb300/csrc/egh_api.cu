@@ -66,6 +66,9 @@ struct egh_ctx {
   std::map<std::tuple<int, int, int, int, int, int>, cudaGraphExec_t> fd_graphs;
   cudaEvent_t fd_done[2] = {}, dft_done[2] = {}, ev_side = nullptr;
   cudaEvent_t ev_tune[2] = {};                 // FD rows-per-warp timing
+  // per-chunk start/end events of the FD steps and of the transform in the last egh_green
+  std::vector<cudaEvent_t> ev_fd, ev_dft;
+  long long fd_launches = 0, dft_launches = 0;
   float* w_dev = nullptr;
   int* rec_pts = nullptr;
   int* status = nullptr;
@@ -223,6 +226,8 @@ void free_all(egh_ctx* c) {
   for (cudaEvent_t e : {c->fd_done[0], c->fd_done[1], c->dft_done[0], c->dft_done[1], c->ev_side,
                         c->ev_tune[0], c->ev_tune[1]})
     if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : c->ev_fd) cudaEventDestroy(e);
+  for (cudaEvent_t e : c->ev_dft) cudaEventDestroy(e);
   for (auto& kv : c->fd_graphs) cudaGraphExecDestroy(kv.second);
   c->fd_graphs.clear();
   if (c->side) cudaStreamDestroy(c->side);
@@ -423,6 +428,13 @@ egh_status egh_create(const egh_config* cfg, egh_ctx** out) {
       CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
     CK(cudaEventCreate(&ctx->ev_tune[0]));
     CK(cudaEventCreate(&ctx->ev_tune[1]));
+    {
+      const long long nchunks = (long long)((c.nrec + ctx->B - 1) / ctx->B) * ((c.nt + ctx->K - 1) / ctx->K);
+      ctx->ev_fd.assign(2 * nchunks, nullptr);
+      ctx->ev_dft.assign(2 * nchunks, nullptr);
+      for (cudaEvent_t& e : ctx->ev_fd) CK(cudaEventCreate(&e));
+      for (cudaEvent_t& e : ctx->ev_dft) CK(cudaEventCreate(&e));
+    }
     CK(cudaMemset(ctx->d_err, 0, sizeof(int)));
     std::vector<int> rp(c.nrec);
     for (int r = 0; r < c.nrec; ++r)
@@ -512,6 +524,7 @@ egh_status egh_green(egh_ctx* ctx, const float* vel, void* stream_) {
       const int sbase = (int)(g & 1) * K;
       // this chunk's slots were read by the transform of chunk g - 2
       if (g >= 2) CK(cudaStreamWaitEvent(fs, ctx->dft_done[g & 1], 0));
+      CK(cudaEventRecord(ctx->ev_fd[2 * g], fs));
       for (int t = t0; t < std::min(t1, 2); ++t) {
         // level 0 is zero; level 1 is the impulse (the step from zero levels adds only the source)
         const int sj = sbase + (t - t0);
@@ -522,10 +535,13 @@ egh_status egh_green(egh_ctx* ctx, const float* vel, void* stream_) {
                            L.org, snap_slot(ctx, sj), fs));
       }
       if ((s = fd_chunk_steps(ctx, std::max(t0, 2), t0, t1, sbase, np))) return s;
+      CK(cudaEventRecord(ctx->ev_fd[2 * g + 1], fs));
       CK(cudaEventRecord(ctx->fd_done[g & 1], fs));
       CK(cudaStreamWaitEvent(ctx->side, ctx->fd_done[g & 1], 0));
+      CK(cudaEventRecord(ctx->ev_dft[2 * g], ctx->side));
       CK(launch_dft_tc(ctx->tmap, ctx->twt, ctx->nf, sbase, t1 - t0, t0, L, ctx->gh, b0, nb,
                        ctx->d_err, ctx->side));
+      CK(cudaEventRecord(ctx->ev_dft[2 * g + 1], ctx->side));
       CK(cudaEventRecord(ctx->dft_done[g & 1], ctx->side));
     }
   }
@@ -541,6 +557,22 @@ egh_status egh_green(egh_ctx* ctx, const float* vel, void* stream_) {
   if (derr) {
     CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), stream));
     return fail(ctx, EGH_ETIMEOUT, "a bounded wait for staged snapshots ran out in the transform");
+  }
+  {
+    // per-kernel device time of this call: FD steps (memsets, impulse and graph replay of each
+    // chunk, on the FD stream) and the transform launches (on their own stream)
+    double fd = 0, dft = 0;
+    for (long long i = 0; i < g; ++i) {
+      float a = 0, b = 0;
+      CK(cudaEventElapsedTime(&a, ctx->ev_fd[2 * i], ctx->ev_fd[2 * i + 1]));
+      CK(cudaEventElapsedTime(&b, ctx->ev_dft[2 * i], ctx->ev_dft[2 * i + 1]));
+      fd += a;
+      dft += b;
+    }
+    ctx->st.fd_ms = fd;
+    ctx->st.dft_ms = dft;
+    ctx->st.fd_launches = (long long)((ctx->nrec + B - 1) / B) * std::max(0, nt - 2);
+    ctx->st.dft_launches = g;
   }
   ctx->st.pde_solves = ctx->nrec;
   ctx->st.point_steps = (long long)ctx->nrec * nt * L.NZ * L.NX;

@@ -47,6 +47,8 @@ class egh_stats(ctypes.Structure):
         ("batch_receivers", ctypes.c_int32), ("dft_chunk", ctypes.c_int32),
         ("gram_splits", ctypes.c_int32), ("kernel_launches", ctypes.c_int64),
         ("fd_rows", ctypes.c_int32), ("pad_", ctypes.c_int32),
+        ("fd_ms", ctypes.c_double), ("dft_ms", ctypes.c_double),
+        ("fd_launches", ctypes.c_int64), ("dft_launches", ctypes.c_int64),
     ]
 
     def as_dict(self):

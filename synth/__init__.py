@@ -27,6 +27,7 @@ __all__ = [
     "case_layered",
     "case_salt_patches",
     "case_tiny",
+    "slice_case",
 ]
 
 
@@ -199,3 +200,14 @@ def case_tiny(seed: int = 7, nz: int = 10, nx: int = 12, nsponge: int = 4, nrec:
         vel_true=v, vel_start=v, rec_iz=np.zeros(nrec, np.int32), rec_ix=rix,
         freqs=np.array([15.0, 30.0, 45.0]), mu_alpha=1e-2,
     )
+
+
+def slice_case(c: Case, nrec: int, nt: int, nsrc: int = 8) -> Case:
+    """The same model and grid with fewer receivers (evenly spread), fewer sources and a shorter
+    record: a bounded case for profiling captures."""
+    d = Case(c)
+    sel = np.linspace(0, c.rec_ix.size - 1, nrec).round().astype(int)
+    ssel = np.linspace(0, c.src_ix.size - 1, nsrc).round().astype(int)
+    d.update(name=f"{c.name}-slice-nr{nrec}-nt{nt}", nt=nt, rec_iz=c.rec_iz[sel], rec_ix=c.rec_ix[sel],
+             src_iz=c.src_iz[ssel], src_ix=c.src_ix[ssel])
+    return d
