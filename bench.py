@@ -56,6 +56,8 @@ def _args():
                         "seeded band-limited noise of the same shape (skips the modelling launches)")
     p.add_argument("--slice", action="store_true",
                    help="profiling slice: one batch of 16 receivers, nt 1024, no e2e or CPU baseline")
+    p.add_argument("--precision", choices=["mixed", "fp32"], default="mixed",
+                   help="Hessian arithmetic: bf16x3 tensor-core Gram (mixed) or FP32 CUDA-core Gram")
     p.add_argument("--dft-chunk", type=int, default=0,
                    help="levels per transform chunk (0 = library default); for bounded ncu captures")
     return p.parse_args()
@@ -272,7 +274,8 @@ def run_ours(args):
         args.e2e_steps, args.no_cpu_baseline = 0, True
     nr, ns, nt, nf = c.rec_ix.size, c.src_ix.size, c.nt, c.freqs.size
     ctx = egh.Context(c.nz, c.nx, c.dz, c.dx, c.nsponge, c.sponge_R, c.dt, c.nt, c.rec_iz, c.rec_ix, c.freqs,
-                      dft_chunk=args.dft_chunk)
+                      dft_chunk=args.dft_chunk,
+                      precision=egh.EGH_PREC_MIXED if args.precision == "mixed" else egh.EGH_PREC_FP32)
     stream = torch.cuda.current_stream()
     v_start = torch.from_numpy(np.float32(c.vel_start)).cuda()
     if args.resid == "noise":
@@ -376,12 +379,31 @@ def run_ours(args):
     # of 2 nf floats per receiver point per chunk (write only for the first chunk)
     dft_alg = (4.0 * point_steps + nr * npts * 2 * nf * 4 * (2 * nchunk - 1)) / dft_n
     dft_achieved = dft_alg / (dft_ms / dft_n * 1e-3) / 1e9
+    # the other Hessian arithmetic on the same transforms, for comparison (not the headline)
+    other = {}
+    if not args.slice:
+        alt = egh.EGH_PREC_FP32 if args.precision == "mixed" else egh.EGH_PREC_MIXED
+        with egh.Context(c.nz, c.nx, c.dz, c.dx, c.nsponge, c.sponge_R, c.dt, c.nt, c.rec_iz,
+                         c.rec_ix, c.freqs, precision=alt) as ctx2:
+            ctx2.green(v_start)
+            hf = []
+            for _ in range(2):
+                e0, e1 = ev(), ev()
+                e0.record(stream)
+                ctx2.hessian(egh.EGH_MU_REL_MEANDIAG, c.mu_alpha)
+                ctx2.factor()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                hf.append(e0.elapsed_time(e1))
+            other = {"precision": "fp32" if alt == egh.EGH_PREC_FP32 else "mixed",
+                     "hessian_factor_ms": min(hf)}
     line = {
         "metric": METRIC, "value": bf_s_max / ws, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": _workload(c, {"batch_receivers": st["batch_receivers"], "dft_chunk": st["dft_chunk"],
                                 "gram_splits": st["gram_splits"], "fd_rows": st["fd_rows"],
+                                "precision": args.precision,
                                 "residuals": "forward modelling (true - start)" if args.resid == "model"
                                 else "seeded band-limited noise 2-10 Hz"}),
         "stages_ms": {"green": statistics.mean(green_ms), "green_fd": fd_ms, "green_transform": dft_ms,
@@ -389,6 +411,7 @@ def run_ours(args):
                       "hessian_factor": statistics.mean(bf_ms) - statistics.mean(green_ms),
                       "deblur": statistics.mean(deb_ms)},
         "deblur_sources_per_s": ns / (statistics.mean(deb_ms) / 1e3),
+        "other_precision": other or None,
         "roofline": {"kernel": "k_fd_step (FD step, 60% of the update)", "bound": "hbm",
                      "achieved": fd_achieved, "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": fd_achieved / hbm,

@@ -63,6 +63,16 @@ typedef enum {
                                 "Numerical examples": a fraction of the largest eigenvalue of S S^T) */
 } egh_mu_mode;
 
+/* Arithmetic of the Hessian stage (the transform is bf16x3 on the tensor cores in both, about
+ * 2e-6 relative against FP64):
+ *   EGH_PREC_FP32:  Gram as FP32 products and sums on the CUDA cores (the plain path);
+ *   EGH_PREC_MIXED: Gram as bf16x3 products on the tensor cores with FP32 accumulation (each
+ *                   transform stored as bf16 hi + lo; about 1e-5 relative against FP64). */
+typedef enum {
+    EGH_PREC_FP32 = 0,
+    EGH_PREC_MIXED = 1
+} egh_precision;
+
 /*
  * Problem description (Section "Theory"; the discretisation is the library's
  * reading, the paper does not give one):
@@ -95,7 +105,8 @@ typedef struct {
     int32_t gram_splits;     /* split of the grid sum in the Gram; 0 = default */
     int32_t fd_rows;         /* FD rows per warp: 12, 16, 20, 24 or 32; 0 = timed on the first
                                 egh_green of the context and the fastest kept */
-    int32_t reserved[4];     /* must be zero */
+    int32_t precision;       /* egh_precision of the Hessian stage (0 = EGH_PREC_FP32) */
+    int32_t reserved[3];     /* must be zero */
 } egh_config;
 
 typedef struct egh_ctx egh_ctx;

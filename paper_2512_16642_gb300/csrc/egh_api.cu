@@ -48,6 +48,8 @@ struct egh_ctx {
   std::vector<float> wsyn;
   int B = 0, K = 0, splits = 0;
   int fd_tz = 0;  // FD rows per warp (0 = library default)
+  int prec = EGH_PREC_FP32;
+  int splits_tc = 0;  // grid-sum splits of the tensor-core Gram
   Layout L{};
   Stencil S{};
   // device state
@@ -57,6 +59,8 @@ struct egh_ctx {
   CUtensorMap tmap{};                        // TMA map of the snapshot ring (64-byte aligned type)
   int Bp = 0;                                // receivers per snapshot slot (B rounded up to even)
   float *gh = nullptr, *part = nullptr;
+  __nv_bfloat16* ghb = nullptr;              // [nrec][nf][re/im][hi/lo][G] Gram operands
+  CUtensorMap tmap_ghb{};                    // TMA map of ghb
   float2 *Qh = nullptr, *Lh = nullptr, *tw = nullptr;
   int tw_len = 0;
   cudaStream_t side = nullptr;                 // the transform's stream inside egh_green (low priority)
@@ -216,7 +220,7 @@ cudaError_t zero_snap_slot(egh_ctx* ctx, int j, cudaStream_t st) {
 }
 
 void free_all(egh_ctx* c) {
-  void* ptrs[] = {c->coef, c->lev, c->snap, c->twt, c->gh, c->part, c->Qh, c->Lh, c->tw, c->w_dev,
+  void* ptrs[] = {c->coef, c->lev, c->snap, c->twt, c->gh, c->ghb, c->part, c->Qh, c->Lh, c->tw, c->w_dev,
                   c->rec_pts, c->status, c->dsum, c->lmax, c->vchk, c->d_err, c->vel_stage, c->Dh,
                   c->io_in, c->io_out};
   for (void* p : ptrs)
@@ -315,6 +319,8 @@ egh_status egh_create(const egh_config* cfg, egh_ctx** out) {
       c.fd_rows != 32)
     return fail(nullptr, EGH_EINVAL, "fd_rows must be 0, 12, 16, 20, 24 or 32");
   if (c.batch_receivers > 32) return fail(nullptr, EGH_EINVAL, "batch_receivers must be <= 32");
+  if (c.precision != EGH_PREC_FP32 && c.precision != EGH_PREC_MIXED)
+    return fail(nullptr, EGH_EINVAL, "unknown precision");
   if (c.batch_receivers < 0 || c.gram_splits < 0)
     return fail(nullptr, EGH_EINVAL, "batch_receivers and gram_splits must be >= 0");
   if (c.dft_chunk != 0 && c.dft_chunk != 32 && c.dft_chunk != 64 && c.dft_chunk != 128 &&
@@ -344,14 +350,14 @@ egh_status egh_create(const egh_config* cfg, egh_ctx** out) {
   L.org = (long long)GUARD * L.PX;
   L.G = round_up((long long)L.NZ * L.PX, 256);
 
-  const int ntile = gram_tiles(c.nrec);
-  const long long pairs_nf = (long long)ntile * (ntile + 1) / 2 * c.nfreq;
-  if (c.gram_splits) {
-    ctx->splits = c.gram_splits;
-  } else {
+  ctx->prec = c.precision;
+  {
+    const int ntile = gram_tiles(c.nrec);
+    const long long pairs_nf = (long long)ntile * (ntile + 1) / 2 * c.nfreq;
     long long s = (3LL * 456 + pairs_nf - 1) / pairs_nf;
     s = std::max(1LL, std::min(s, L.G / 2048));
-    ctx->splits = (int)std::max(1LL, s);
+    ctx->splits = c.gram_splits ? c.gram_splits : (int)std::max(1LL, s);
+    ctx->splits_tc = c.gram_splits ? c.gram_splits : gram_tc_splits(c.nrec, c.nfreq, L.G);
   }
 
   for (int k = 0; k < 4; ++k) {
@@ -393,7 +399,13 @@ egh_status egh_create(const egh_config* cfg, egh_ctx** out) {
   std::vector<unsigned char> twt = dft_twiddle_tiles(ctx->freqs, c.dt, c.nt);
   ALLOC(ctx->twt, twt.size(), "twiddle tiles");
   ALLOC(ctx->gh, (size_t)c.nrec * c.nfreq * 2 * (size_t)L.G * sizeof(float), "green transforms");
-  ALLOC(ctx->part, gram_workspace_floats(c.nrec, c.nfreq, ctx->splits) * sizeof(float), "gram");
+  if (ctx->prec == EGH_PREC_MIXED)
+    ALLOC(ctx->ghb, (size_t)c.nrec * c.nfreq * 4 * (size_t)L.G * sizeof(__nv_bfloat16),
+          "bf16 transforms");
+  ALLOC(ctx->part,
+        std::max(gram_workspace_floats(c.nrec, c.nfreq, ctx->splits),
+                 gram_tc_workspace_floats(c.nrec, c.nfreq, ctx->splits_tc)) * sizeof(float),
+        "gram");
   ALLOC(ctx->Qh, (size_t)c.nfreq * c.nrec * c.nrec * sizeof(float2), "Qh");
   ALLOC(ctx->Lh, (size_t)c.nfreq * c.nrec * c.nrec * sizeof(float2), "Lh");
   ALLOC(ctx->w_dev, (size_t)c.nfreq * sizeof(float), "weights");
@@ -415,6 +427,7 @@ egh_status egh_create(const egh_config* cfg, egh_ctx** out) {
     CK(cudaMemcpy(ctx->twt, twt.data(), twt.size(), cudaMemcpyHostToDevice));
     CK(make_snap_tmap(&ctx->tmap, ctx->snap, L.G, ctx->Bp, 2 * ctx->K));
     CK(fd_prepare(c.nfreq));
+    if (ctx->ghb) CK(make_ghb_tmap(&ctx->tmap_ghb, ctx->ghb, L.G, c.nfreq, c.nrec));
     {
       // FD steps are a serial chain of short kernels: their stream gets the highest priority so
       // that their blocks are placed ahead of the transform's, which fills the rest of the GPU
@@ -460,7 +473,7 @@ egh_status egh_create(const egh_config* cfg, egh_ctx** out) {
   ctx->st.pitch = L.PX;
   ctx->st.batch_receivers = ctx->B;
   ctx->st.dft_chunk = ctx->K;
-  ctx->st.gram_splits = ctx->splits;
+  ctx->st.gram_splits = ctx->prec == EGH_PREC_MIXED ? ctx->splits_tc : ctx->splits;
   *out = ctx;
   return EGH_OK;
 }
@@ -539,8 +552,8 @@ egh_status egh_green(egh_ctx* ctx, const float* vel, void* stream_) {
       CK(cudaEventRecord(ctx->fd_done[g & 1], fs));
       CK(cudaStreamWaitEvent(ctx->side, ctx->fd_done[g & 1], 0));
       CK(cudaEventRecord(ctx->ev_dft[2 * g], ctx->side));
-      CK(launch_dft_tc(ctx->tmap, ctx->twt, ctx->nf, sbase, t1 - t0, t0, L, ctx->gh, b0, nb,
-                       ctx->d_err, ctx->side));
+      CK(launch_dft_tc(ctx->tmap, ctx->twt, ctx->nf, sbase, t1 - t0, t0, L, ctx->gh, ctx->ghb,
+                       (t1 == nt && ctx->ghb) ? 1 : 0, b0, nb, ctx->d_err, ctx->side));
       CK(cudaEventRecord(ctx->ev_dft[2 * g + 1], ctx->side));
       CK(cudaEventRecord(ctx->dft_done[g & 1], ctx->side));
     }
@@ -591,8 +604,14 @@ egh_status egh_hessian(egh_ctx* ctx, egh_mu_mode mode, double mu_param, double* 
   if (mode != EGH_MU_ABS && mode != EGH_MU_REL_MEANDIAG && mode != EGH_MU_REL_MAXEIG)
     return fail(ctx, EGH_EINVAL, "unknown mu mode");
   CK(cudaEventRecord(ctx->ev[2], stream));
-  CK(launch_gram_partial(ctx->gh, ctx->nrec, ctx->nf, ctx->L.G, ctx->splits, ctx->part, stream));
-  CK(launch_gram_finish(ctx->part, ctx->nrec, ctx->nf, ctx->splits, ctx->Qh, stream));
+  if (ctx->prec == EGH_PREC_MIXED) {
+    CK(launch_gram_tc(ctx->tmap_ghb, ctx->nrec, ctx->nf, ctx->L.G, ctx->splits_tc, ctx->part,
+                      ctx->d_err, stream));
+    CK(launch_gram_tc_finish(ctx->part, ctx->nrec, ctx->nf, ctx->splits_tc, ctx->Qh, stream));
+  } else {
+    CK(launch_gram_partial(ctx->gh, ctx->nrec, ctx->nf, ctx->L.G, ctx->splits, ctx->part, stream));
+    CK(launch_gram_finish(ctx->part, ctx->nrec, ctx->nf, ctx->splits, ctx->Qh, stream));
+  }
   double mu = mu_param;
   if (mode == EGH_MU_REL_MEANDIAG) {
     CK(launch_diag_sum(ctx->Qh, ctx->nrec, ctx->nf, ctx->dsum, stream));
@@ -607,6 +626,15 @@ egh_status egh_hessian(egh_ctx* ctx, egh_mu_mode mode, double mu_param, double* 
                        stream));
     CK(cudaStreamSynchronize(stream));
     mu = mu_param * *std::max_element(lm.begin(), lm.end());
+  }
+  {
+    int derr = 0;
+    CK(cudaMemcpyAsync(&derr, ctx->d_err, sizeof derr, cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    if (derr) {
+      CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), stream));
+      return fail(ctx, EGH_ETIMEOUT, "a bounded wait for staged operands ran out in the Gram");
+    }
   }
   if (!std::isfinite(mu)) return fail(ctx, EGH_EINVAL, "mu is not finite");
   CK(launch_add_mu_copy(ctx->Qh, ctx->Lh, ctx->nrec, ctx->nf, (float)mu, stream));

@@ -71,8 +71,19 @@ size_t dft_smem(int nf);
 std::vector<unsigned char> dft_twiddle_tiles(const std::vector<double>& f, double dt, int nt);
 cudaError_t make_snap_tmap(CUtensorMap* tm, void* base, long long G, int Bp, int nslot);
 cudaError_t launch_dft_tc(const CUtensorMap& tmap, const unsigned char* twt, int nf, int slot0,
-                          int kcount, int n0, const Layout& L, float* gh, int rec0, int nvalid,
-                          int* err, cudaStream_t st);
+                          int kcount, int n0, const Layout& L, float* gh, __nv_bfloat16* ghb,
+                          int last, int rec0, int nvalid, int* err, cudaStream_t st);
+
+// ---- gram_tc.cu -------------------------------------------------------------------------------
+// Gram on the tensor cores from the bf16 hi/lo transforms ghb[nrec][nf][re/im][hi/lo][G].
+__host__ __device__ int gram_tc_tiles(int nrec);
+size_t gram_tc_workspace_floats(int nrec, int nf, int splits);
+int gram_tc_splits(int nrec, int nf, long long G);
+cudaError_t make_ghb_tmap(CUtensorMap* tm, void* base, long long G, int nf, int nrec);
+cudaError_t launch_gram_tc(const CUtensorMap& tmap, int nrec, int nf, long long G, int splits,
+                           float* part, int* err, cudaStream_t st);
+cudaError_t launch_gram_tc_finish(const float* part, int nrec, int nf, int splits, float2* Qh,
+                                  cudaStream_t st);
 
 // ---- gram.cu ----------------------------------------------------------------------------------
 __host__ __device__ int gram_tiles(int nrec);

@@ -212,10 +212,14 @@ __global__ void __launch_bounds__(32 * FD_MAXPAIRS, EGH_FD_MINB)
   const int nload = nrows + 8;
   auto load_row = [&](int k) {
     if (k < nload) {
-      const int r = (z0 - 4 + k) * PX2;
+      const int z = z0 - 4 + k;
+      const int r = z * PX2;
       const unsigned dst = ring0 + (unsigned)((k & (FD_RING - 1)) * 36) * 16u;
       cp_async16(dst + (unsigned)(lane + 2) * 16u, uc + r + xh);
-      if (halo) cp_async16(dst + (unsigned)hslot * 16u, uc + r + hcol);
+      // halo columns are read only for rows that are computed (0 <= z < NZ): there they stay
+      // inside the level (previous row's padding, next row's first columns); a guard row's halo
+      // would reach past the level
+      if (halo && z >= 0 && z < NZ) cp_async16(dst + (unsigned)hslot * 16u, uc + r + hcol);
     }
     cp_async_commit();  // empty groups keep the group count uniform
   };
@@ -434,7 +438,8 @@ cudaError_t launch_record(const float2* u, long long pstride, const int* rec_pts
 //                                                             W[2k+1][n] = -sin(2 pi f_k n dt),
 // in bf16x3: u = u_hi + u_lo (split by the FD step), W = W_hi + W_lo (split on the host), and
 // u_hi W_hi + u_hi W_lo + u_lo W_hi accumulated in FP32 in TMEM (the dropped u_lo W_lo and the
-// splits themselves are ~2^-17 relative).  D = A B^T with M = 128 points per CTA, N = 2 nf
+// splits themselves are ~2^-17 relative).  The chunk that ends the record also writes the final
+// transforms' bf16 hi/lo split (the Gram's operands).  D = A B^T with M = 128 points per CTA, N = 2 nf
 // rounded up to 32, K = levels in stages of 32; TD_R receivers per CTA share the twiddle tiles.
 // A (snapshots) is MN-major: a 4-D TMA box {64 points, 1 receiver, 32 levels, 2 planes} lands as
 // [plane][level][64 points] 128-byte rows with the 128-byte swizzle (two boxes per receiver).
@@ -465,7 +470,8 @@ size_t dft_smem(int nf) {
 __global__ void __launch_bounds__(128)
     k_dft_tc(const __grid_constant__ CUtensorMap tmap, const unsigned char* __restrict__ twt,
              int N, int nf, int slot0, int kcount, int n0, long long G, float* __restrict__ gh,
-             int rec0, int nvalid, int* __restrict__ err) {
+             __nv_bfloat16* __restrict__ ghb, int last, int rec0, int nvalid,
+             int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char dsm[];
   unsigned char* sm = dsm + ((1024 - (tc::smem_u32(dsm) & 1023)) & 1023);
   unsigned char* As = sm;                               // [TD_ST][TD_R][TD_AB]
@@ -567,7 +573,8 @@ __global__ void __launch_bounds__(128)
     const bool first = n0 == 0;
     const long long p = p0 + tid;
     for (int r = 0; r < nr; ++r) {
-      float* g = gh + (long long)(rec0 + rg + r) * 2 * nf * G + p;
+      const long long row0 = (long long)(rec0 + rg + r) * 2 * nf;  // first plane of this receiver
+      float* g = gh + row0 * G + p;
       for (int c0 = 0; c0 < N; c0 += 32) {
         float v[32], o[32];
         tc::tmem_ld32(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(r * N + c0), v);
@@ -576,8 +583,21 @@ __global__ void __launch_bounds__(128)
         for (int i = 0; i < 32; ++i)
           o[i] = (!first && c0 + i < 2 * nf) ? __ldcs(g + (long long)(c0 + i) * G) : 0.f;
 #pragma unroll
-        for (int i = 0; i < 32; ++i)
-          if (c0 + i < 2 * nf) __stcs(g + (long long)(c0 + i) * G, o[i] + v[i]);
+        for (int i = 0; i < 32; ++i) {
+          const int c = c0 + i;
+          if (c < 2 * nf) {
+            const float sum = o[i] + v[i];
+            __stcs(g + (long long)c * G, sum);
+            if (last) {
+              // the Gram's operands: hi = bf16(g), lo = bf16(g - hi), planes [..][c][hi|lo][G]
+              const __nv_bfloat16 h = __float2bfloat16_rn(sum);
+              const __nv_bfloat16 l = __float2bfloat16_rn(sum - __bfloat162float(h));
+              __nv_bfloat16* q = ghb + ((row0 + c) * 2) * G + p;
+              q[0] = h;
+              q[G] = l;
+            }
+          }
+        }
       }
     }
   } else if (tid == 0) {
@@ -589,8 +609,8 @@ __global__ void __launch_bounds__(128)
 }
 
 cudaError_t launch_dft_tc(const CUtensorMap& tmap, const unsigned char* twt, int nf, int slot0,
-                          int kcount, int n0, const Layout& L, float* gh, int rec0, int nvalid,
-                          int* err, cudaStream_t st) {
+                          int kcount, int n0, const Layout& L, float* gh, __nv_bfloat16* ghb,
+                          int last, int rec0, int nvalid, int* err, cudaStream_t st) {
   const int N = dft_ncomp(nf);
   if (L.G % TD_M != 0 || N > 128 || kcount < 1 || slot0 % TD_S != 0 || n0 % TD_S != 0 ||
       nvalid < 1)
@@ -601,8 +621,8 @@ cudaError_t launch_dft_tc(const CUtensorMap& tmap, const unsigned char* twt, int
   if (e != cudaSuccess) return e;
   dim3 grid((unsigned)(L.G / TD_M), (unsigned)((nvalid + TD_R - 1) / TD_R));
   count_launches(1);
-  k_dft_tc<<<grid, 128, smem, st>>>(tmap, twt, N, nf, slot0, kcount, n0, L.G, gh, rec0, nvalid,
-                                    err);
+  k_dft_tc<<<grid, 128, smem, st>>>(tmap, twt, N, nf, slot0, kcount, n0, L.G, gh, ghb, last, rec0,
+                                    nvalid, err);
   return cudaGetLastError();
 }
 

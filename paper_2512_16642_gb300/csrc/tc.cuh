@@ -154,6 +154,11 @@ __device__ __forceinline__ void tma_load_4d_hint(unsigned dst, const void* tmap,
       : "memory");
 }
 
+// plain arrive of this thread on an mbarrier
+__device__ __forceinline__ void mbar_arrive(unsigned bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
 // arrive on the mbarrier once all tcgen05 operations issued so far by this thread complete
 __device__ __forceinline__ void mma_commit(unsigned bar) {
   asm volatile(

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libegh.so")
 
 EGH_OK, EGH_EINVAL, EGH_ENOMEM, EGH_ECUDA, EGH_ENOTPD, EGH_ESTATE, EGH_ETIMEOUT = range(7)
 EGH_MU_ABS, EGH_MU_REL_MEANDIAG, EGH_MU_REL_MAXEIG = range(3)
+EGH_PREC_FP32, EGH_PREC_MIXED = range(2)
 
 _i32p = ctypes.POINTER(ctypes.c_int32)
 _f64p = ctypes.POINTER(ctypes.c_double)
@@ -33,7 +34,7 @@ class egh_config(ctypes.Structure):
         ("nfreq", ctypes.c_int32), ("freq_hz", _f64p),
         ("batch_receivers", ctypes.c_int32), ("dft_chunk", ctypes.c_int32),
         ("gram_splits", ctypes.c_int32), ("fd_rows", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 4),
+        ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3),
     ]
 
 
@@ -138,14 +139,15 @@ def _i32(a):
 
 # ---- the ABI calls, same names -----------------------------------------------------------
 def egh_create(nz, nx, dz, dx, nsponge, sponge_R, dt, nt, rec_iz, rec_ix, freq_hz,
-               batch_receivers=0, dft_chunk=0, gram_splits=0, fd_rows=0):
+               batch_receivers=0, dft_chunk=0, gram_splits=0, fd_rows=0, precision=0):
     lib = load()
     riz, riz_p = _i32(rec_iz)
     rix, rix_p = _i32(rec_ix)
     f = np.ascontiguousarray(freq_hz, dtype=np.float64)
     cfg = egh_config(int(nz), int(nx), float(dz), float(dx), int(nsponge), float(sponge_R), float(dt),
                      int(nt), int(riz.size), riz_p, rix_p, int(f.size), f.ctypes.data_as(_f64p),
-                     int(batch_receivers), int(dft_chunk), int(gram_splits), int(fd_rows))
+                     int(batch_receivers), int(dft_chunk), int(gram_splits), int(fd_rows),
+                     int(precision))
     h = _vp()
     _check(lib.egh_create(ctypes.byref(cfg), ctypes.byref(h)), None)
     return h

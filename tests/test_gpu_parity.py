@@ -85,6 +85,7 @@ def small():
     d_start = oracle.forward_traces(gs, c.src_iz, c.src_ix, c.rec_iz, c.rec_ix, w64, c.dt)
     resid = d_true - d_start
     o, g = _run_both(c, c.vel_start, resid=resid)
+    o["resid"] = resid
     # GPU forward modelling of the true model (auxiliary kernel path)
     with _ctx(c) as ctx:
         fwd = torch.empty((c.src_ix.size, c.rec_ix.size, c.nt), device="cuda")
@@ -110,6 +111,43 @@ def test_hessian_parity_small(small):
     assert np.array_equal(Q, Q.conj().transpose(0, 2, 1))
     d = np.einsum("kii->ki", Q)
     assert np.all(d.imag == 0) and np.all(d.real > 0)
+
+
+def _gpu_only(c, vel, resid, **kw):
+    """The GPU pipeline alone (same calls as _run_both) with context options kw."""
+    torch = _torch()
+    from paper_2512_16642_gb300 import egh
+
+    g = {}
+    with _ctx(c, **kw) as ctx:
+        ctx.green(torch.from_numpy(np.asarray(vel, np.float32)).cuda())
+        g["gh"] = ctx.get_green()
+        g["mu"] = ctx.hessian(egh.EGH_MU_REL_MEANDIAG, c.mu_alpha)
+        g["Q"] = ctx.get_hessian(False)
+        ctx.factor()
+        r32 = np.ascontiguousarray(resid, np.float32)
+        rt = torch.from_numpy(r32).cuda()
+        mt = torch.empty_like(rt)
+        ctx.deblur(rt, mt)
+        torch.cuda.synchronize()
+        g["mult"] = mt.cpu().numpy()
+    return g
+
+
+def test_mixed_precision_small(small):
+    """Mixed precision (bf16x3 tensor-core Gram): the same bars against the FP64 oracle; mu is
+    the mean Hessian diagonal, so it carries the Hessian bar."""
+    from paper_2512_16642_gb300 import egh
+
+    c, o, _ = small
+    g = _gpu_only(c, c.vel_start, o["resid"], precision=egh.EGH_PREC_MIXED)
+    assert rel(g["gh"], o["gh"]) <= GREEN_TOL
+    assert g["mu"] == pytest.approx(o["mu"], rel=HESS_TOL)
+    for k in range(c.freqs.size):
+        assert rel(g["Q"][k], o["Q"][k]) <= HESS_TOL, k
+    Q = g["Q"]
+    assert np.array_equal(Q, Q.conj().transpose(0, 2, 1))
+    assert rel(g["mult"], o["mult"]) <= MULT_TOL
 
 
 def test_factor_parity_small(small):
@@ -174,6 +212,14 @@ def test_ragged_case():
     for k in range(3):
         assert rel(g["Q"][k], o["Q"][k]) <= HESS_TOL
     assert rel(g["mult"], o["mult"]) <= MULT_TOL
+    # mixed precision: two 128-row Gram tiles (receivers 70..127 of the second are padding)
+    from paper_2512_16642_gb300 import egh
+
+    gm = _gpu_only(c, c.vel_true, resid, batch_receivers=16, dft_chunk=32, gram_splits=3,
+                   precision=egh.EGH_PREC_MIXED)
+    for k in range(3):
+        assert rel(gm["Q"][k], o["Q"][k]) <= HESS_TOL
+    assert rel(gm["mult"], o["mult"]) <= MULT_TOL
 
 
 def test_single_receiver_single_frequency_two_steps():
@@ -184,6 +230,11 @@ def test_single_receiver_single_frequency_two_steps():
     assert rel(g["gh"], o["gh"]) <= GREEN_TOL
     assert rel(g["Q"], o["Q"]) <= HESS_TOL
     assert rel(g["mult"], o["mult"]) <= MULT_TOL
+    from paper_2512_16642_gb300 import egh
+
+    gm = _gpu_only(c, c.vel_true, resid, precision=egh.EGH_PREC_MIXED)
+    assert rel(gm["Q"], o["Q"]) <= HESS_TOL
+    assert rel(gm["mult"], o["mult"]) <= MULT_TOL
 
 
 def test_zero_record_is_not_positive_definite():
@@ -252,31 +303,35 @@ def test_layered_full_size_sampled():
     rng = np.random.default_rng(9)
     resid = synth.bandlimited_noise(rng, (c.src_ix.size, c.rec_ix.size, c.nt), c.dt, 2.0, 10.0)
     r32 = resid.astype(np.float32)
-    with _ctx(c) as ctx:
-        ctx.green(torch.from_numpy(v32).cuda())
-        for t, r in enumerate(sample):
-            assert rel(ctx.get_green(int(r), 1)[0], o_gh[t]) <= GREEN_TOL, r
-        mu = ctx.hessian(egh.EGH_MU_REL_MEANDIAG, c.mu_alpha)
-        Q = ctx.get_hessian(False).astype(np.complex128)
-        sub = Q[:, sample][:, :, sample] - mu * np.eye(3)
-        for k in range(c.freqs.size):
-            assert rel(sub[k], H[k]) <= HESS_TOL, k
-        assert mu == pytest.approx(c.mu_alpha * np.mean(np.einsum("kii->ki", Q).real - mu), rel=1e-5)
-        ctx.factor()
-        rt = torch.from_numpy(r32).cuda()
-        X = torch.empty((c.freqs.size, c.rec_ix.size, c.src_ix.size), dtype=torch.complex64, device="cuda")
-        ctx.deblur_freq(rt, X)
-        D = oracle.dtft_traces(r32.astype(np.float64), c.freqs, c.dt)
-        Xh = X.cpu().numpy().astype(np.complex128)
-        for k in range(c.freqs.size):
-            res = np.linalg.norm(Q[k] @ Xh[k] - D[k])
-            bound = np.linalg.norm(Q[k], 2) * np.linalg.norm(Xh[k]) + np.linalg.norm(D[k])
-            assert res / bound <= 2e-5, k
-        mt = torch.empty_like(rt)
-        ctx.deblur(rt, mt)
-        part = torch.empty_like(rt[5:9])
-        ctx.deblur(rt[5:9].contiguous(), part)
-        torch.cuda.synchronize()
-        assert torch.equal(part, mt[5:9])
-        st = ctx.stats()
-        assert st["pde_solves"] == 231
+    D = oracle.dtft_traces(r32.astype(np.float64), c.freqs, c.dt)
+    # both Hessian arithmetics; the benchmark times the mixed one
+    for prec, mu_tol in ((egh.EGH_PREC_MIXED, HESS_TOL), (egh.EGH_PREC_FP32, 1e-5)):
+        with _ctx(c, precision=prec) as ctx:
+            ctx.green(torch.from_numpy(v32).cuda())
+            for t, r in enumerate(sample):
+                assert rel(ctx.get_green(int(r), 1)[0], o_gh[t]) <= GREEN_TOL, (prec, r)
+            mu = ctx.hessian(egh.EGH_MU_REL_MEANDIAG, c.mu_alpha)
+            Q = ctx.get_hessian(False).astype(np.complex128)
+            sub = Q[:, sample][:, :, sample] - mu * np.eye(3)
+            for k in range(c.freqs.size):
+                assert rel(sub[k], H[k]) <= HESS_TOL, (prec, k)
+            assert mu == pytest.approx(c.mu_alpha * np.mean(np.einsum("kii->ki", Q).real - mu),
+                                       rel=mu_tol)
+            ctx.factor()
+            rt = torch.from_numpy(r32).cuda()
+            X = torch.empty((c.freqs.size, c.rec_ix.size, c.src_ix.size), dtype=torch.complex64,
+                            device="cuda")
+            ctx.deblur_freq(rt, X)
+            Xh = X.cpu().numpy().astype(np.complex128)
+            for k in range(c.freqs.size):
+                res = np.linalg.norm(Q[k] @ Xh[k] - D[k])
+                bound = np.linalg.norm(Q[k], 2) * np.linalg.norm(Xh[k]) + np.linalg.norm(D[k])
+                assert res / bound <= 2e-5, (prec, k)
+            mt = torch.empty_like(rt)
+            ctx.deblur(rt, mt)
+            part = torch.empty_like(rt[5:9])
+            ctx.deblur(rt[5:9].contiguous(), part)
+            torch.cuda.synchronize()
+            assert torch.equal(part, mt[5:9])
+            st = ctx.stats()
+            assert st["pde_solves"] == 231
