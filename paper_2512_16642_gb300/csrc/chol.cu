@@ -13,23 +13,30 @@ namespace egh {
 
 constexpr int CH_THREADS = 512;
 
+// piv64: the diagonal is carried in FP64 (dg[i] = Q[i][i] - sum_l |L[i][l]|^2 accumulated in
+// double from the stored FP32 columns) and each pivot is taken from it, so the pivots of
+// ill-conditioned matrices do not inherit the FP32 cancellation of the trailing updates; the
+// off-diagonal entries stay FP32.
 __global__ void __launch_bounds__(CH_THREADS)
-    k_potrf(float2* __restrict__ Lh, int n, int* __restrict__ status) {
-  extern __shared__ float2 col[];  // [n]
+    k_potrf(float2* __restrict__ Lh, int n, int* __restrict__ status, int piv64) {
+  extern __shared__ float2 col[];  // [n] columns, then [n] doubles of the FP64 diagonal
+  double* dg = reinterpret_cast<double*>(col + n + (n & 1));
   __shared__ int bad;
   const int k = blockIdx.x;
   float2* A = Lh + (long long)k * n * n;
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   if (tid == 0) bad = 0;
+  if (piv64)
+    for (int i = tid; i < n; i += blockDim.x) dg[i] = (double)A[(long long)i * n + i].x;
   __syncthreads();
   for (int j = 0; j < n; ++j) {
     if (tid == 0) {
-      const float d = A[(long long)j * n + j].x;
-      if (!(d > 0.f) || !isfinite(d)) {
+      const double d = piv64 ? dg[j] : (double)A[(long long)j * n + j].x;
+      if (!(d > 0.0) || !isfinite(d)) {
         bad = j + 1;
       } else {
-        const float s = sqrtf(d);
+        const float s = piv64 ? (float)sqrt(d) : sqrtf((float)d);
         A[(long long)j * n + j] = make_float2(s, 0.f);
         col[j] = make_float2(s, 0.f);
       }
@@ -43,6 +50,7 @@ __global__ void __launch_bounds__(CH_THREADS)
       v.y *= inv;
       A[(long long)i * n + j] = v;
       col[i] = v;
+      if (piv64) dg[i] -= (double)v.x * v.x + (double)v.y * v.y;
     }
     __syncthreads();
     // A[i][l] -= col[i] * conj(col[l]),  j < l <= i
@@ -68,15 +76,15 @@ __global__ void __launch_bounds__(CH_THREADS)
   }
 }
 
-cudaError_t launch_potrf(float2* Lh, int n, int nf, int* status, cudaStream_t st) {
-  const size_t smem = sizeof(float2) * (size_t)n;
+cudaError_t launch_potrf(float2* Lh, int n, int nf, int* status, cudaStream_t st, int piv64) {
+  const size_t smem = sizeof(float2) * (size_t)(n + (n & 1)) + sizeof(double) * (size_t)n;
   if (smem > 48 * 1024) {
     cudaError_t e =
         cudaFuncSetAttribute(k_potrf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
   count_launches(1);
-  k_potrf<<<nf, CH_THREADS, smem, st>>>(Lh, n, status);
+  k_potrf<<<nf, CH_THREADS, smem, st>>>(Lh, n, status, piv64);
   return cudaGetLastError();
 }
 

@@ -2,6 +2,7 @@
 // Section "Frequency domain inversion"):
 //   D[k][r][s] = sum_t resid[s][r][t] exp(-i w_k t dt)           (k_trace_dft)
 //   X_k = L_k^{-H} L_k^{-1} D_k                                   (k_trsm, all sources as RHS)
+//   mixed precision: X_k += L_k^{-H} L_k^{-1} (D_k - Q_k X_k)      (k_resid64 in FP64, k_trsm)
 //   mult[s][r][t] = sum_k w_k Re(X_k[r][s] exp(+i w_k t dt))      (k_synth)
 // Traces are indexed q = s * nrec + r (the [ns][nrec][nt] gather layout).
 #include "egh_internal.cuh"
@@ -223,6 +224,73 @@ __global__ void __launch_bounds__(256)
       if (q < ntr) mult[(long long)q * nt_d + t] = acc[m];
     }
   }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Refinement residual in FP64: R_k = D_k - Q_k X_k, products of the FP32 operands (exact in FP64)
+// accumulated in double and rounded once (mixed-precision iterative refinement of the solves).
+// One block per (frequency, 32 sources); X_k's columns sit in shared memory; warp w takes rows
+// w, w + 8, ...; lane = source.
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(32 * TS_W)
+    k_resid64(const float2* __restrict__ Qh, int n, const float2* __restrict__ Xh,
+              const float2* __restrict__ Dh, int ns, float2* __restrict__ Rh) {
+  extern __shared__ float2 Xs[];  // [n][32]
+  const int k = blockIdx.y;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int col = blockIdx.x * 32 + lane;
+  const bool valid = col < ns;
+  const float2* Q = Qh + (long long)k * n * n;
+  const long long off = (long long)k * n * ns;
+  for (int i = warp; i < n; i += TS_W)
+    Xs[i * 32 + lane] = valid ? Xh[off + (long long)i * ns + col] : make_float2(0.f, 0.f);
+  __syncthreads();
+  for (int i = warp; i < n; i += TS_W) {
+    double re = 0.0, im = 0.0;
+    const float2* q = Q + (long long)i * n;
+    for (int j = 0; j < n; ++j) {
+      const float2 a = q[j], x = Xs[j * 32 + lane];
+      re = fma((double)a.x, (double)x.x, fma(-(double)a.y, (double)x.y, re));
+      im = fma((double)a.x, (double)x.y, fma((double)a.y, (double)x.x, im));
+    }
+    if (valid) {
+      const float2 d = Dh[off + (long long)i * ns + col];
+      Rh[off + (long long)i * ns + col] = make_float2((float)((double)d.x - re), (float)((double)d.y - im));
+    }
+  }
+}
+
+cudaError_t launch_resid64(const float2* Qh, int n, int nf, const float2* Xh, const float2* Dh,
+                           int ns, float2* Rh, cudaStream_t st) {
+  const size_t smem = sizeof(float2) * 32 * (size_t)n;
+  if (smem > 48 * 1024) {
+    cudaError_t e =
+        cudaFuncSetAttribute(k_resid64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  count_launches(1);
+  k_resid64<<<dim3((ns + 31) / 32, nf), 32 * TS_W, smem, st>>>(Qh, n, Xh, Dh, ns, Rh);
+  return cudaGetLastError();
+}
+
+// X += R (complex, all frequencies and sources)
+__global__ void k_add_correction(float2* __restrict__ X, const float2* __restrict__ R, long long m) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float2 r = R[i];
+    float2 x = X[i];
+    x.x += r.x;
+    x.y += r.y;
+    X[i] = x;
+  }
+}
+
+cudaError_t launch_add_correction(float2* X, const float2* R, long long m, cudaStream_t st) {
+  long long blocks = (m + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  count_launches(1);
+  k_add_correction<<<(int)blocks, 256, 0, st>>>(X, R, m);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_synth(const float2* Dh, int nrec, int ns, int nf, const float* w,

@@ -83,6 +83,8 @@ struct egh_ctx {
   float* vel_stage = nullptr;
   float2* Dh = nullptr;
   size_t Dh_cap = 0;
+  float2 *Dr = nullptr, *Rr = nullptr;  // refinement: right-hand sides kept, residuals
+  size_t Dr_cap = 0, Rr_cap = 0;
   float *io_in = nullptr, *io_out = nullptr;
   size_t io_in_cap = 0, io_out_cap = 0;
   int state = ST_CREATED;
@@ -220,7 +222,7 @@ cudaError_t zero_snap_slot(egh_ctx* ctx, int j, cudaStream_t st) {
 }
 
 void free_all(egh_ctx* c) {
-  void* ptrs[] = {c->coef, c->lev, c->snap, c->twt, c->gh, c->ghb, c->part, c->Qh, c->Lh, c->tw, c->w_dev,
+  void* ptrs[] = {c->Dr, c->Rr, c->coef, c->lev, c->snap, c->twt, c->gh, c->ghb, c->part, c->Qh, c->Lh, c->tw, c->w_dev,
                   c->rec_pts, c->status, c->dsum, c->lmax, c->vchk, c->d_err, c->vel_stage, c->Dh,
                   c->io_in, c->io_out};
   for (void* p : ptrs)
@@ -656,7 +658,8 @@ egh_status egh_factor(egh_ctx* ctx, int32_t* bad_freq, void* stream_) {
   const size_t bytes = (size_t)ctx->nf * ctx->nrec * ctx->nrec * sizeof(float2);
   CK(cudaEventRecord(ctx->ev[4], stream));
   CK(cudaMemcpyAsync(ctx->Lh, ctx->Qh, bytes, cudaMemcpyDeviceToDevice, stream));
-  CK(launch_potrf(ctx->Lh, ctx->nrec, ctx->nf, ctx->status, stream));
+  CK(launch_potrf(ctx->Lh, ctx->nrec, ctx->nf, ctx->status, stream,
+                  ctx->prec == EGH_PREC_MIXED ? 1 : 0));
   CK(cudaEventRecord(ctx->ev[5], stream));
   ctx->ev_rec[2] = true;
   std::vector<int> stv(ctx->nf);
@@ -715,7 +718,21 @@ static egh_status deblur_common(egh_ctx* ctx, const float* resid, int32_t ns, in
   }
   CK(cudaEventRecord(ctx->ev[6], stream));
   CK(launch_trace_dft(din, (int)ntr, nt_d, ctx->tw, ctx->nf, ctx->nrec, ns, D, stream));
+  const size_t dbytes = (size_t)ctx->nf * ntr * sizeof(float2);
+  if (ctx->prec == EGH_PREC_MIXED) {
+    // one step of iterative refinement: residual in FP64, correction solved with the FP32 factors
+    if ((s = ensure_buf(ctx, (void**)&ctx->Dr, &ctx->Dr_cap, dbytes, stream, "refinement rhs")))
+      return s;
+    if ((s = ensure_buf(ctx, (void**)&ctx->Rr, &ctx->Rr_cap, dbytes, stream, "refinement residual")))
+      return s;
+    CK(cudaMemcpyAsync(ctx->Dr, D, dbytes, cudaMemcpyDeviceToDevice, stream));
+  }
   CK(launch_trsm(ctx->Lh, ctx->nrec, ctx->nf, D, ns, stream));
+  if (ctx->prec == EGH_PREC_MIXED) {
+    CK(launch_resid64(ctx->Qh, ctx->nrec, ctx->nf, D, ctx->Dr, ns, ctx->Rr, stream));
+    CK(launch_trsm(ctx->Lh, ctx->nrec, ctx->nf, ctx->Rr, ns, stream));
+    CK(launch_add_correction(D, ctx->Rr, (long long)ctx->nf * ntr, stream));
+  }
   if (!X) CK(launch_synth(D, ctx->nrec, ns, ctx->nf, ctx->w_dev, ctx->tw, nt_d, dout, stream));
   CK(cudaEventRecord(ctx->ev[7], stream));
   ctx->ev_rec[3] = true;

@@ -97,12 +97,16 @@ cudaError_t launch_lambda_max(const float2* Qh, int nrec, int nf, double* d_lmax
 cudaError_t launch_add_mu_copy(float2* Qh, float2* Lh, int nrec, int nf, float mu, cudaStream_t st);
 
 // ---- chol.cu ----------------------------------------------------------------------------------
-cudaError_t launch_potrf(float2* Lh, int n, int nf, int* status, cudaStream_t st);
+// piv64: FP64 diagonal and pivots (mixed precision)
+cudaError_t launch_potrf(float2* Lh, int n, int nf, int* status, cudaStream_t st, int piv64);
 
 // ---- deblur.cu --------------------------------------------------------------------------------
 cudaError_t launch_trace_dft(const float* resid, int ntr, int nt_d, const float2* tw, int nf,
                              int nrec, int ns, float2* Dh, cudaStream_t st);
 cudaError_t launch_trsm(const float2* Lh, int n, int nf, float2* Dh, int ns, cudaStream_t st);
+cudaError_t launch_resid64(const float2* Qh, int n, int nf, const float2* Xh, const float2* Dh,
+                           int ns, float2* Rh, cudaStream_t st);
+cudaError_t launch_add_correction(float2* X, const float2* R, long long m, cudaStream_t st);
 cudaError_t launch_synth(const float2* Dh, int nrec, int ns, int nf, const float* w,
                          const float2* tw, int nt_d, float* mult, cudaStream_t st);
 

@@ -150,6 +150,44 @@ def test_mixed_precision_small(small):
     assert rel(g["mult"], o["mult"]) <= MULT_TOL
 
 
+def test_precision_form_small(small):
+    """Precision form of the 101x101 case, per frequency against the FP64 oracle: Hessians and
+    frequency-domain solutions of the FP32 path and of the mixed path (bf16x3 tensor-core Gram,
+    FP64 pivots, one refinement step with FP64 residuals), and the backward error of each
+    path's solves with respect to its own Hessian (refinement takes it to the FP32 rounding of
+    the solution)."""
+    torch = _torch()
+    from paper_2512_16642_gb300 import egh
+
+    c, o, _ = small
+    r32 = np.ascontiguousarray(o["resid"], np.float32)
+    _, Xo, Do = oracle.deblur(o["L"], r32.astype(np.float64), c.freqs, c.dt, nt_ref=c.nt)
+    nf, nr, ns = c.freqs.size, c.rec_ix.size, r32.shape[0]
+    bw, table = {}, []
+    for prec in (egh.EGH_PREC_FP32, egh.EGH_PREC_MIXED):
+        with _ctx(c, precision=prec) as ctx:
+            ctx.green(torch.from_numpy(np.float32(c.vel_start)).cuda())
+            ctx.hessian(egh.EGH_MU_REL_MEANDIAG, c.mu_alpha)
+            Q = ctx.get_hessian(False).astype(np.complex128)
+            ctx.factor()
+            X = torch.empty((nf, nr, ns), dtype=torch.complex64, device="cuda")
+            ctx.deblur_freq(torch.from_numpy(r32).cuda(), X)
+            Xh = X.cpu().numpy().astype(np.complex128)
+        bw[prec] = []
+        for k in range(nf):
+            eq, ex = rel(Q[k], o["Q"][k]), rel(Xh[k], Xo[k])
+            b = np.linalg.norm(Q[k] @ Xh[k] - Do[k]) / (
+                np.linalg.norm(Q[k], 2) * np.linalg.norm(Xh[k]) + np.linalg.norm(Do[k]))
+            bw[prec].append(b)
+            table.append((prec, c.freqs[k], eq, ex, b))
+            assert eq <= HESS_TOL, (prec, k)
+            assert ex <= MULT_TOL, (prec, k)
+    for row in table:
+        print("precision %d  f %.1f Hz  Q rel %.2e  X rel %.2e  backward %.2e" % row)
+    assert max(bw[egh.EGH_PREC_MIXED]) <= max(bw[egh.EGH_PREC_FP32])
+    assert max(bw[egh.EGH_PREC_MIXED]) <= 1e-6
+
+
 def test_factor_parity_small(small):
     c, o, g = small
     L = g["L"].astype(np.complex128)
