@@ -56,6 +56,7 @@ def _args():
                         "seeded band-limited noise of the same shape (skips the modelling launches)")
     p.add_argument("--slice", action="store_true",
                    help="profiling slice: one batch of 16 receivers, nt 1024, no e2e or CPU baseline")
+    p.add_argument("--no-serving", action="store_true", help="skip the serving-form measurement")
     p.add_argument("--precision", choices=["mixed", "fp32"], default="mixed",
                    help="Hessian arithmetic: bf16x3 tensor-core Gram (mixed) or FP32 CUDA-core Gram")
     p.add_argument("--dft-chunk", type=int, default=0,
@@ -229,6 +230,77 @@ def _workload(c, extra=None):
     return cfg
 
 
+def serve_bench(torch, egh, precision, requests=240, seed=11):
+    """Serving form: Poisson-arriving deblur requests against 4 resident factored Hessian sets
+    (Nr 101/211/331/461, Nf 20/27/33/40, 2-10 Hz; seeded synthetic Hermitian positive-definite
+    Q_k = A A^H / m + 0.05 mean diag I); each request U{1..64} sources, nt U{2000..4000}, FP32
+    band-limited (2-10 Hz) seeded Gaussian residuals from pinned host memory, results back to
+    pinned host memory.  The arrival rate is 70% of the throughput measured with all requests
+    queued at once.  Returns p50/p99 latency and sources/s."""
+    import numpy as np
+
+    import synth
+
+    rng = np.random.default_rng(seed)
+    shapes = ((101, 20), (211, 27), (331, 33), (461, 40))
+    dt, max_nt = 1e-3, 4096
+    with egh.Server(24 << 30, slots=6, max_batch_sources=128, precision=precision) as sv:
+        ids = []
+        for nrec, nf in shapes:
+            A = torch.randn((nf, nrec, 2 * nrec), dtype=torch.complex64, device="cuda",
+                            generator=torch.Generator(device="cuda").manual_seed(seed + nrec))
+            Q = A @ A.conj().transpose(1, 2) / (2 * nrec)
+            mu = 0.05 * torch.diagonal(Q, dim1=1, dim2=2).real.mean()
+            Q = Q + mu * torch.eye(nrec, device="cuda")
+            ids.append(sv.add_set(Q.cpu().numpy(), np.linspace(2.0, 10.0, nf), dt, 4000, max_nt))
+        # a pool of pinned buffers, one per request in flight at most
+        pool = 8
+        maxb = 64 * 461 * 4000
+        ins = [torch.empty(maxb, dtype=torch.float32, pin_memory=True) for _ in range(pool)]
+        outs = [torch.empty(maxb, dtype=torch.float32, pin_memory=True) for _ in range(pool)]
+        base = torch.from_numpy(
+            synth.bandlimited_noise(rng, (461, 4000), dt, 2.0, 10.0).astype(np.float32).reshape(-1))
+        for b in ins:
+            b.view(64, -1).copy_(base.expand(64, -1))
+        spec = [(int(rng.integers(4)), int(rng.integers(1, 65)), int(rng.integers(2000, 4001)))
+                for _ in range(requests)]
+
+        def run(arrivals):
+            sv.reset_stats()
+            live = []
+            t0 = time.perf_counter()
+            for i, (sid, ns, nt_d) in enumerate(spec):
+                if arrivals is not None:
+                    while time.perf_counter() - t0 < arrivals[i]:
+                        pass
+                if len(live) == pool:
+                    sv.wait(live.pop(0)[0])
+                slot = i % pool
+                shape = (ns, shapes[sid][0], nt_d)
+                n = ns * shapes[sid][0] * nt_d
+                rid = sv.submit(ids[sid], ins[slot][:n].view(shape), outs[slot][:n].view(shape))
+                live.append((rid, slot))
+            for rid, _ in live:
+                sv.wait(rid)
+            return sv.stats()
+
+        run(None)                       # warm-up (launch paths, arena)
+        full = run(None)                # all requests queued at once: capacity
+        srcs = sum(s[1] for s in spec)
+        rate = 0.7 * full["completed"] / full["span_s"]
+        gaps = rng.exponential(1.0 / rate, size=requests)
+        st = run(np.cumsum(gaps) - gaps[0])
+    return {"workload": "4 resident Hessian sets Nr 101/211/331/461, Nf 20/27/33/40 (synthetic HPD "
+                        "A A^H/m + 0.05 mean diag I), Poisson arrivals at 70% of capacity, "
+                        f"{requests} requests of U{{1..64}} sources x nt U{{2000..4000}}",
+            "precision": "mixed" if precision == egh.EGH_PREC_MIXED else "fp32",
+            "sources_per_s": st["sources_done"] / st["span_s"],
+            "p50_ms": st["p50_s"] * 1e3, "p99_ms": st["p99_s"] * 1e3, "mean_ms": st["mean_s"] * 1e3,
+            "arrival_rate_per_s": rate, "capacity_sources_per_s": srcs / full["span_s"],
+            "batches": st["batches"], "requests": st["completed"],
+            "peak_in_flight": st["peak_in_flight"], "peak_arena_bytes": st["peak_bytes_in_use"]}
+
+
 def run_reference(args):
     import synth
 
@@ -379,6 +451,10 @@ def run_ours(args):
     # of 2 nf floats per receiver point per chunk (write only for the first chunk)
     dft_alg = (4.0 * point_steps + nr * npts * 2 * nf * 4 * (2 * nchunk - 1)) / dft_n
     dft_achieved = dft_alg / (dft_ms / dft_n * 1e-3) / 1e9
+    serving = None
+    if not args.slice and not args.no_serving:
+        serving = serve_bench(torch, egh, egh.EGH_PREC_MIXED if args.precision == "mixed"
+                              else egh.EGH_PREC_FP32)
     # the other Hessian arithmetic on the same transforms, for comparison (not the headline)
     other = {}
     if not args.slice:
@@ -412,6 +488,7 @@ def run_ours(args):
                       "deblur": statistics.mean(deb_ms)},
         "deblur_sources_per_s": ns / (statistics.mean(deb_ms) / 1e3),
         "other_precision": other or None,
+        "serving": serving,
         "roofline": {"kernel": "k_fd_step (FD step, 60% of the update)", "bound": "hbm",
                      "achieved": fd_achieved, "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": fd_achieved / hbm,

@@ -223,6 +223,69 @@ egh_status egh_get_hessian(egh_ctx *ctx, int32_t factored, void *host_out);
 egh_status egh_gram_noalloc(const float *gh, int32_t nrec, int32_t nfreq, int64_t npts, void *H,
                             void *stream);
 
+/* ---- Serving (continuous batching of deblur requests) ------------------------------------- *
+ * The paper builds each frequency's Hessian once and reuses it for every source (Algorithm 1's
+ * loop over sources, Algorithm 2); a server keeps several factored Hessian sets resident and
+ * deblurs residual gathers submitted at any time.  A worker thread admits queued requests in
+ * arrival order into `slots` CUDA streams while their device buffers fit in an arena of
+ * `hbm_budget_bytes` reserved at creation (admission by HBM budget; no device allocation after
+ * creation); queued requests for the same set are packed into one batch (at most
+ * `max_batch_sources` sources) that shares the per-frequency solve.  Batches in different slots
+ * run concurrently; when one finishes, its memory and slot go to the next requests at once.
+ * Results are the same whether a request runs alone or in a batch (each source is its own
+ * right-hand side).  Host buffers should be pinned (page-locked) for asynchronous copies and
+ * must stay valid until the request is waited for. */
+typedef struct egh_server egh_server;
+
+typedef struct {
+    int64_t hbm_budget_bytes;  /* device arena for request buffers (>= 1 MiB) */
+    int32_t slots;             /* batches in flight at once, 1..16 */
+    int32_t max_batch_sources; /* sources packed into one batch, >= 1 */
+    int32_t precision;         /* egh_precision of the sets' factorisations and solves */
+    int32_t reserved[3];       /* must be zero */
+} egh_server_config;
+
+typedef struct {
+    int64_t submitted, completed, rejected, sources_done, batches;
+    int64_t peak_bytes_in_use;  /* arena high-water mark */
+    int32_t peak_in_flight;     /* most batches in flight at once */
+    int32_t pad_;
+    double p50_s, p99_s, mean_s; /* request latency, submission to completion */
+    double span_s;              /* first submission to last completion */
+} egh_server_stats;
+
+egh_status egh_server_create(const egh_server_config *cfg, egh_server **out);
+
+/* Adds a resident Hessian set: Q_host [nfreq][nrec][nrec] complex64 (Hermitian positive
+ * definite, host) at frequencies freq_hz (Hz) of a record with step dt (s); nt_record sets the
+ * synthesis weight of a single frequency (1/(nt_record dt)); requests may have up to max_nt
+ * samples per trace.  Q is factored on the device (EGH_ENOTPD if a pivot fails).  Blocks. */
+egh_status egh_server_add_set(egh_server *sv, int32_t nrec, int32_t nfreq, const double *freq_hz,
+                              double dt, int32_t nt_record, int32_t max_nt, const void *Q_host,
+                              int32_t *set_id);
+
+/* Queues the deblur of resid [ns][nrec][nt_d] float32 (host) against set `set_id` into
+ * mult [ns][nrec][nt_d] float32 (host).  EGH_ENOMEM if the request alone exceeds the budget.
+ * Returns at once with *request_id. */
+egh_status egh_server_submit(egh_server *sv, int32_t set_id, const float *resid_host, int32_t ns,
+                             int32_t nt_d, float *mult_host, int64_t *request_id);
+
+/* Waits (up to timeout_s) for a request; *latency_s (may be NULL) receives its submission-to-
+ * completion time.  The id is released.  EGH_ETIMEOUT if it has not finished. */
+egh_status egh_server_wait(egh_server *sv, int64_t request_id, double timeout_s, double *latency_s);
+
+/* Waits (up to timeout_s) until nothing is queued or in flight. */
+egh_status egh_server_drain(egh_server *sv, double timeout_s);
+
+egh_status egh_server_get_stats(egh_server *sv, egh_server_stats *out);
+egh_status egh_server_reset_stats(egh_server *sv);
+
+/* Message of the server's last failure (of the last failed egh_server_create when NULL). */
+const char *egh_server_last_error(const egh_server *sv);
+
+/* Finishes queued requests, then frees the server. */
+void egh_server_destroy(egh_server *sv);
+
 /* Fills *out with the last timings and counters.  Blocks on pending events. */
 egh_status egh_get_stats(egh_ctx *ctx, egh_stats *out);
 

@@ -4,7 +4,11 @@
 //   X_k = L_k^{-H} L_k^{-1} D_k                                   (k_trsm, all sources as RHS)
 //   mixed precision: X_k += L_k^{-H} L_k^{-1} (D_k - Q_k X_k)      (k_resid64 in FP64, k_trsm)
 //   mult[s][r][t] = sum_k w_k Re(X_k[r][s] exp(+i w_k t dt))      (k_synth)
-// Traces are indexed q = s * nrec + r (the [ns][nrec][nt] gather layout).
+// Traces are indexed q = s * nrec + r (the [ns][nrec][nt] gather layout); the spectra of one call
+// occupy columns s0 .. s0 + ns - 1 of a [nf][nrec][ld] array, so that several gathers (of
+// different lengths) can share one solve.
+#include <algorithm>
+
 #include "egh_internal.cuh"
 
 namespace egh {
@@ -20,7 +24,7 @@ constexpr int TD_TR = 64, TD_T = 64;
 
 __global__ void __launch_bounds__(256)
     k_trace_dft(const float* __restrict__ resid, int ntr, int nt_d, const float2* __restrict__ tw,
-                int nf, int nrec, int ns, float2* __restrict__ Dh) {
+                int nf, int nrec, int ld, int s0, float2* __restrict__ Dh) {
   __shared__ float R[TD_TR][TD_T + 1];
   extern __shared__ float2 stw[];  // [TD_T][nf]
   const int tid = threadIdx.x, m = tid & 63, g = tid >> 6;
@@ -69,13 +73,13 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int j = 0; j < NFMAX / 4; ++j) {
       const int k = g + 4 * j;
-      if (k < nf) Dh[((long long)k * nrec + r) * ns + s] = tot[j];
+      if (k < nf) Dh[((long long)k * nrec + r) * ld + s0 + s] = tot[j];
     }
   }
 }
 
 cudaError_t launch_trace_dft(const float* resid, int ntr, int nt_d, const float2* tw, int nf,
-                             int nrec, int ns, float2* Dh, cudaStream_t st) {
+                             int nrec, int ld, int s0, float2* Dh, cudaStream_t st) {
   if (nf > NFMAX) return cudaErrorInvalidValue;
   const size_t smem = sizeof(float2) * TD_T * nf;
   if (smem + sizeof(float) * TD_TR * (TD_T + 1) > 48 * 1024) {
@@ -84,7 +88,8 @@ cudaError_t launch_trace_dft(const float* resid, int ntr, int nt_d, const float2
     if (e != cudaSuccess) return e;
   }
   count_launches(1);
-  k_trace_dft<<<(ntr + TD_TR - 1) / TD_TR, 256, smem, st>>>(resid, ntr, nt_d, tw, nf, nrec, ns, Dh);
+  k_trace_dft<<<(ntr + TD_TR - 1) / TD_TR, 256, smem, st>>>(resid, ntr, nt_d, tw, nf, nrec, ld, s0,
+                                                          Dh);
   return cudaGetLastError();
 }
 
@@ -182,8 +187,9 @@ cudaError_t launch_trsm(const float2* Lh, int n, int nf, float2* Dh, int ns, cud
 constexpr int SY_TR = 64, SY_T = 128;
 
 __global__ void __launch_bounds__(256)
-    k_synth(const float2* __restrict__ Dh, int nrec, int ns, int nf, const float* __restrict__ w,
-            const float2* __restrict__ tw, int nt_d, float* __restrict__ mult, int ntr) {
+    k_synth(const float2* __restrict__ Dh, int nrec, int ld, int s0, int nf,
+            const float* __restrict__ w, const float2* __restrict__ tw, int nt_d,
+            float* __restrict__ mult, int ntr) {
   extern __shared__ float2 sm[];
   float2* X = sm;                 // [SY_TR][nf]
   float2* T = sm + SY_TR * nf;    // [nf][SY_T]
@@ -193,7 +199,7 @@ __global__ void __launch_bounds__(256)
     const int rr = e / nf, k = e % nf, q = q0 + rr;
     float2 v = make_float2(0.f, 0.f);
     if (q < ntr) {
-      v = Dh[((long long)k * nrec + q % nrec) * ns + q / nrec];
+      v = Dh[((long long)k * nrec + q % nrec) * ld + s0 + q / nrec];
       v.x *= w[k];
       v.y *= w[k];
     }
@@ -229,8 +235,8 @@ __global__ void __launch_bounds__(256)
 // ---------------------------------------------------------------------------------------------
 // Refinement residual in FP64: R_k = D_k - Q_k X_k, products of the FP32 operands (exact in FP64)
 // accumulated in double and rounded once (mixed-precision iterative refinement of the solves).
-// One block per (frequency, 32 sources); X_k's columns sit in shared memory; warp w takes rows
-// w, w + 8, ...; lane = source.
+// One block per (frequency, 32 sources, group of rows); X_k's columns sit in shared memory;
+// warp w takes rows w, w + 8, ... of its group; lane = source.
 // ---------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(32 * TS_W)
     k_resid64(const float2* __restrict__ Qh, int n, const float2* __restrict__ Xh,
@@ -245,7 +251,9 @@ __global__ void __launch_bounds__(32 * TS_W)
   for (int i = warp; i < n; i += TS_W)
     Xs[i * 32 + lane] = valid ? Xh[off + (long long)i * ns + col] : make_float2(0.f, 0.f);
   __syncthreads();
-  for (int i = warp; i < n; i += TS_W) {
+  const int rows = (n + gridDim.z - 1) / gridDim.z;
+  const int i0 = blockIdx.z * rows, i1 = min(n, i0 + rows);
+  for (int i = i0 + warp; i < i1; i += TS_W) {
     double re = 0.0, im = 0.0;
     const float2* q = Q + (long long)i * n;
     for (int j = 0; j < n; ++j) {
@@ -269,7 +277,10 @@ cudaError_t launch_resid64(const float2* Qh, int n, int nf, const float2* Xh, co
     if (e != cudaSuccess) return e;
   }
   count_launches(1);
-  k_resid64<<<dim3((ns + 31) / 32, nf), 32 * TS_W, smem, st>>>(Qh, n, Xh, Dh, ns, Rh);
+  // enough blocks for every SM: split the rows of each (frequency, source group)
+  const int blocks = ((ns + 31) / 32) * nf;
+  const int groups = std::max(1, std::min((n + TS_W - 1) / TS_W, (4 * 152 + blocks - 1) / blocks));
+  k_resid64<<<dim3((ns + 31) / 32, nf, groups), 32 * TS_W, smem, st>>>(Qh, n, Xh, Dh, ns, Rh);
   return cudaGetLastError();
 }
 
@@ -293,7 +304,7 @@ cudaError_t launch_add_correction(float2* X, const float2* R, long long m, cudaS
   return cudaGetLastError();
 }
 
-cudaError_t launch_synth(const float2* Dh, int nrec, int ns, int nf, const float* w,
+cudaError_t launch_synth(const float2* Dh, int nrec, int ns, int ld, int s0, int nf, const float* w,
                          const float2* tw, int nt_d, float* mult, cudaStream_t st) {
   if (nf > NFMAX) return cudaErrorInvalidValue;
   const int ntr = nrec * ns;
@@ -305,7 +316,7 @@ cudaError_t launch_synth(const float2* Dh, int nrec, int ns, int nf, const float
   }
   dim3 grid((nt_d + SY_T - 1) / SY_T, (ntr + SY_TR - 1) / SY_TR);
   count_launches(1);
-  k_synth<<<grid, 256, smem, st>>>(Dh, nrec, ns, nf, w, tw, nt_d, mult, ntr);
+  k_synth<<<grid, 256, smem, st>>>(Dh, nrec, ld, s0, nf, w, tw, nt_d, mult, ntr);
   return cudaGetLastError();
 }
 

@@ -136,6 +136,9 @@ int pointer_is_device(const void* p) {
   return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) ? 1 : 0;
 }
 
+}  // namespace
+
+namespace egh {
 // exp(-i 2 pi f_k n dt) for n < len, phase reduced as 2 pi frac(f_k n dt) in double precision.
 std::vector<float2> twiddle_table(const std::vector<double>& f, double dt, int len) {
   std::vector<float2> t((size_t)len * f.size());
@@ -148,6 +151,26 @@ std::vector<float2> twiddle_table(const std::vector<double>& f, double dt, int l
     }
   return t;
 }
+
+// Band-limited synthesis weights w_k = 2 df_k dt (df_k: half the distance between the
+// neighbouring frequencies, the full gap at the ends, 1/(nt dt) for a single frequency).
+std::vector<float> synthesis_weights(const std::vector<double>& f, double dt, int nt) {
+  const int nf = (int)f.size();
+  std::vector<double> df(nf);
+  if (nf == 1) {
+    df[0] = 1.0 / (nt * dt);
+  } else {
+    for (int k = 1; k < nf - 1; ++k) df[k] = 0.5 * (f[k + 1] - f[k - 1]);
+    df[0] = f[1] - f[0];
+    df[nf - 1] = f[nf - 1] - f[nf - 2];
+  }
+  std::vector<float> w(nf);
+  for (int k = 0; k < nf; ++k) w[k] = (float)(2.0 * df[k] * dt);
+  return w;
+}
+}  // namespace egh
+
+namespace {
 
 egh_status ensure_twiddles(egh_ctx* ctx, int len, cudaStream_t stream) {
   if (len <= ctx->tw_len) return EGH_OK;
@@ -367,20 +390,7 @@ egh_status egh_create(const egh_config* cfg, egh_ctx** out) {
     ctx->S.cz[k] = (float)(kC8[k + 1] / (c.dz * c.dz));
   }
 
-  // band-limited synthesis weights 2 df_k dt
-  {
-    const int nf = c.nfreq;
-    std::vector<double> df(nf);
-    if (nf == 1) {
-      df[0] = 1.0 / (c.nt * c.dt);
-    } else {
-      for (int k = 1; k < nf - 1; ++k) df[k] = 0.5 * (c.freq_hz[k + 1] - c.freq_hz[k - 1]);
-      df[0] = c.freq_hz[1] - c.freq_hz[0];
-      df[nf - 1] = c.freq_hz[nf - 1] - c.freq_hz[nf - 2];
-    }
-    ctx->wsyn.resize(nf);
-    for (int k = 0; k < nf; ++k) ctx->wsyn[k] = (float)(2.0 * df[k] * c.dt);
-  }
+  ctx->wsyn = synthesis_weights(ctx->freqs, c.dt, c.nt);
 
   egh_status s = EGH_OK;
   const size_t F = (size_t)L.F;
@@ -717,7 +727,7 @@ static egh_status deblur_common(egh_ctx* ctx, const float* resid, int32_t ns, in
     dout = ctx->io_out;
   }
   CK(cudaEventRecord(ctx->ev[6], stream));
-  CK(launch_trace_dft(din, (int)ntr, nt_d, ctx->tw, ctx->nf, ctx->nrec, ns, D, stream));
+  CK(launch_trace_dft(din, (int)ntr, nt_d, ctx->tw, ctx->nf, ctx->nrec, ns, 0, D, stream));
   const size_t dbytes = (size_t)ctx->nf * ntr * sizeof(float2);
   if (ctx->prec == EGH_PREC_MIXED) {
     // one step of iterative refinement: residual in FP64, correction solved with the FP32 factors
@@ -733,7 +743,7 @@ static egh_status deblur_common(egh_ctx* ctx, const float* resid, int32_t ns, in
     CK(launch_trsm(ctx->Lh, ctx->nrec, ctx->nf, ctx->Rr, ns, stream));
     CK(launch_add_correction(D, ctx->Rr, (long long)ctx->nf * ntr, stream));
   }
-  if (!X) CK(launch_synth(D, ctx->nrec, ns, ctx->nf, ctx->w_dev, ctx->tw, nt_d, dout, stream));
+  if (!X) CK(launch_synth(D, ctx->nrec, ns, ns, 0, ctx->nf, ctx->w_dev, ctx->tw, nt_d, dout, stream));
   CK(cudaEventRecord(ctx->ev[7], stream));
   ctx->ev_rec[3] = true;
   ctx->st.deblur_sources = ns;

@@ -44,6 +44,10 @@ struct Layout {
   long long G;     // Gram contraction length
 };
 
+// ---- egh_api.cu (host helpers shared with the serving loop) -----------------------------------
+std::vector<float2> twiddle_table(const std::vector<double>& f, double dt, int len);
+std::vector<float> synthesis_weights(const std::vector<double>& f, double dt, int nt);
+
 // ---- fd.cu ------------------------------------------------------------------------------------
 // Paired levels: float2 per grid point = (receiver 2i, receiver 2i+1); coef = (c1, c3).
 // Snapshot output of one level: hi plane of its slot (receiver 0, point 0) or nullptr for none.
@@ -101,13 +105,14 @@ cudaError_t launch_add_mu_copy(float2* Qh, float2* Lh, int nrec, int nf, float m
 cudaError_t launch_potrf(float2* Lh, int n, int nf, int* status, cudaStream_t st, int piv64);
 
 // ---- deblur.cu --------------------------------------------------------------------------------
+// spectra of ntr = nrec * ns traces into columns s0 .. s0+ns-1 of D[nf][nrec][ld]
 cudaError_t launch_trace_dft(const float* resid, int ntr, int nt_d, const float2* tw, int nf,
-                             int nrec, int ns, float2* Dh, cudaStream_t st);
+                             int nrec, int ld, int s0, float2* Dh, cudaStream_t st);
 cudaError_t launch_trsm(const float2* Lh, int n, int nf, float2* Dh, int ns, cudaStream_t st);
 cudaError_t launch_resid64(const float2* Qh, int n, int nf, const float2* Xh, const float2* Dh,
                            int ns, float2* Rh, cudaStream_t st);
 cudaError_t launch_add_correction(float2* X, const float2* R, long long m, cudaStream_t st);
-cudaError_t launch_synth(const float2* Dh, int nrec, int ns, int nf, const float* w,
+cudaError_t launch_synth(const float2* Dh, int nrec, int ns, int ld, int s0, int nf, const float* w,
                          const float2* tw, int nt_d, float* mult, cudaStream_t st);
 
 }  // namespace egh

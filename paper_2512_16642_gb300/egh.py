@@ -56,6 +56,27 @@ class egh_stats(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class egh_server_config(ctypes.Structure):
+    _fields_ = [
+        ("hbm_budget_bytes", ctypes.c_int64), ("slots", ctypes.c_int32),
+        ("max_batch_sources", ctypes.c_int32), ("precision", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 3),
+    ]
+
+
+class egh_server_stats(ctypes.Structure):
+    _fields_ = [
+        ("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("rejected", ctypes.c_int64),
+        ("sources_done", ctypes.c_int64), ("batches", ctypes.c_int64),
+        ("peak_bytes_in_use", ctypes.c_int64), ("peak_in_flight", ctypes.c_int32),
+        ("pad_", ctypes.c_int32), ("p50_s", ctypes.c_double), ("p99_s", ctypes.c_double),
+        ("mean_s", ctypes.c_double), ("span_s", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_ if name != "pad_"}
+
+
 _vp = ctypes.c_void_p
 _SIGS = {
     "egh_create": ([ctypes.POINTER(egh_config), ctypes.POINTER(_vp)], ctypes.c_int),
@@ -73,6 +94,17 @@ _SIGS = {
     "egh_last_error": ([_vp], ctypes.c_char_p),
     "egh_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "egh_version": ([], ctypes.c_int32),
+    "egh_server_create": ([ctypes.POINTER(egh_server_config), ctypes.POINTER(_vp)], ctypes.c_int),
+    "egh_server_add_set": ([_vp, ctypes.c_int32, ctypes.c_int32, _f64p, ctypes.c_double, ctypes.c_int32,
+                            ctypes.c_int32, _vp, _i32p], ctypes.c_int),
+    "egh_server_submit": ([_vp, ctypes.c_int32, _vp, ctypes.c_int32, ctypes.c_int32, _vp,
+                           ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    "egh_server_wait": ([_vp, ctypes.c_int64, ctypes.c_double, _f64p], ctypes.c_int),
+    "egh_server_drain": ([_vp, ctypes.c_double], ctypes.c_int),
+    "egh_server_get_stats": ([_vp, ctypes.POINTER(egh_server_stats)], ctypes.c_int),
+    "egh_server_reset_stats": ([_vp], ctypes.c_int),
+    "egh_server_last_error": ([_vp], ctypes.c_char_p),
+    "egh_server_destroy": ([_vp], None),
 }
 EXPORTS = tuple(_SIGS)
 
@@ -296,3 +328,82 @@ class Context:
 
     def stats(self):
         return egh_get_stats(self.h)
+
+
+# ---- serving ------------------------------------------------------------------------------
+def _check_server(rc, sv):
+    if rc != EGH_OK:
+        raise EghError(rc, load().egh_server_last_error(sv).decode())
+
+
+class Server:
+    """Continuous batching of deblur requests against resident factored Hessian sets
+    (egh_server_* in include/egh.h).  Host buffers should be pinned and must stay alive until
+    wait() returns for their request."""
+
+    def __init__(self, hbm_budget_bytes, slots=4, max_batch_sources=128, precision=EGH_PREC_FP32):
+        cfg = egh_server_config(int(hbm_budget_bytes), int(slots), int(max_batch_sources), int(precision))
+        h = _vp()
+        _check_server(load().egh_server_create(ctypes.byref(cfg), ctypes.byref(h)), None)
+        self.h = h
+        self._keep = {}
+
+    def add_set(self, Q, freq_hz, dt, nt_record, max_nt):
+        """Q: [nf][nrec][nrec] complex64 host array (Hermitian positive definite)."""
+        Q = np.ascontiguousarray(Q, dtype=np.complex64)
+        f = np.ascontiguousarray(freq_hz, dtype=np.float64)
+        sid = ctypes.c_int32(0)
+        _check_server(load().egh_server_add_set(self.h, int(Q.shape[1]), int(f.size), f.ctypes.data_as(_f64p),
+                                                float(dt), int(nt_record), int(max_nt), Q.ctypes.data,
+                                                ctypes.byref(sid)), self.h)
+        return sid.value
+
+    def submit(self, set_id, resid, mult):
+        """resid, mult: [ns][nrec][nt_d] float32 host buffers (torch pinned tensors or numpy)."""
+        pi, _ = _ptr(resid)
+        po, _ = _ptr(mult)
+        ns, _, nt_d = resid.shape
+        rid = ctypes.c_int64(0)
+        _check_server(load().egh_server_submit(self.h, int(set_id), pi, int(ns), int(nt_d), po,
+                                               ctypes.byref(rid)), self.h)
+        self._keep[rid.value] = (resid, mult)
+        return rid.value
+
+    def wait(self, request_id, timeout_s=60.0):
+        lat = ctypes.c_double(0.0)
+        try:
+            _check_server(load().egh_server_wait(self.h, int(request_id), float(timeout_s), ctypes.byref(lat)),
+                          self.h)
+        finally:
+            pass
+        self._keep.pop(request_id, None)
+        return lat.value
+
+    def drain(self, timeout_s=120.0):
+        _check_server(load().egh_server_drain(self.h, float(timeout_s)), self.h)
+
+    def stats(self):
+        s = egh_server_stats()
+        _check_server(load().egh_server_get_stats(self.h, ctypes.byref(s)), self.h)
+        return s.as_dict()
+
+    def reset_stats(self):
+        _check_server(load().egh_server_reset_stats(self.h), self.h)
+
+    def close(self):
+        if self.h:
+            load().egh_server_destroy(self.h)
+            self.h = None
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

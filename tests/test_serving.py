@@ -1,0 +1,123 @@
+"""Serving loop (egh_server_*): continuous batching of deblur requests against resident factored
+Hessian sets, through the C ABI.
+
+Each request's multipliers are checked against the FP64 oracle (Cholesky of the same Hessian,
+transform, solve, synthesis), and against the same request run alone: a request's sources are
+its own right-hand sides, so its result does not depend on what it is batched or overlapped
+with.  Admission keeps the device buffers inside the HBM budget; a request larger than the
+budget is refused at submission.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+MULT_TOL = 1e-3
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def _hpd_set(rng, nrec, nf):
+    """Seeded synthetic Hermitian positive-definite Hessians Q_k = A A^H / m + mu I (complex64),
+    frequencies evenly spaced in 2-10 Hz."""
+    m = 2 * nrec
+    A = (rng.standard_normal((nf, nrec, m)) + 1j * rng.standard_normal((nf, nrec, m))) / np.sqrt(m)
+    Q = A @ A.conj().transpose(0, 2, 1)
+    Q += 0.05 * np.mean(np.einsum("kii->ki", Q).real) * np.eye(nrec)
+    Q = 0.5 * (Q + Q.conj().transpose(0, 2, 1))
+    return Q.astype(np.complex64), np.linspace(2.0, 10.0, nf)
+
+
+def _pinned(shape, torch, fill=None):
+    t = torch.empty(shape, dtype=torch.float32, pin_memory=True)
+    if fill is not None:
+        t.copy_(torch.from_numpy(np.ascontiguousarray(fill, np.float32)))
+    return t
+
+
+def _requests(rng, sets, n):
+    out = []
+    for _ in range(n):
+        sid = int(rng.integers(len(sets)))
+        ns = int(rng.integers(1, 10))
+        nt_d = int(rng.integers(256, 700))  # long enough for several 2-10 Hz bins
+        nrec = sets[sid][0].shape[1]
+        out.append((sid, synth.bandlimited_noise(rng, (ns, nrec, nt_d), 1e-3, 2.0, 10.0)))
+    return out
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_alone_equals_mix_and_oracle(precision):
+    import torch
+    from paper_2512_16642_gb300 import egh
+
+    rng = np.random.default_rng(41 + precision)
+    sets = [_hpd_set(rng, nrec, nf) for nrec, nf in ((8, 3), (13, 5), (21, 7))]
+    reqs = _requests(rng, sets, 14)
+    dt, nt_record, max_nt = 1e-3, 1000, 1024
+    with egh.Server(256 << 20, slots=4, max_batch_sources=24, precision=precision) as sv:
+        ids = [sv.add_set(Q, f, dt, nt_record, max_nt) for Q, f in sets]
+        ins = [_pinned(r.shape, torch, r) for _, r in reqs]
+        alone = []
+        for (sid, r), rin in zip(reqs, ins):
+            out = _pinned(r.shape, torch)
+            sv.wait(sv.submit(ids[sid], rin, out))
+            alone.append(out.numpy().copy())
+        # the same requests all at once, in a shuffled order: batched and overlapped
+        outs = [_pinned(r.shape, torch) for _, r in reqs]
+        order = rng.permutation(len(reqs))
+        rids = {i: sv.submit(ids[reqs[i][0]], ins[i], outs[i]) for i in order}
+        for i in order:
+            sv.wait(rids[i])
+        st = sv.stats()
+    for i in range(len(reqs)):
+        np.testing.assert_array_equal(outs[i].numpy(), alone[i])
+    assert st["batches"] < st["completed"]  # some requests shared a solve
+    assert st["peak_bytes_in_use"] <= 256 << 20
+    for i in range(len(reqs)):
+        sid, r = reqs[i]
+        Q, f = sets[sid]
+        L = oracle.cholesky(Q.astype(np.complex128))
+        m = oracle.deblur(L, r.astype(np.float32).astype(np.float64), f, dt, nt_ref=nt_record)[0]
+        assert rel(alone[i], m) <= MULT_TOL, i
+
+
+def test_admission_by_budget_and_overlap():
+    import torch
+    from paper_2512_16642_gb300 import egh
+
+    rng = np.random.default_rng(7)
+    Q, f = _hpd_set(rng, 64, 12)
+    ns, nt_d = 16, 2000
+    per_request = 2 * ns * 64 * nt_d * 4 + 12 * 64 * ns * 8  # in + out traces + spectra
+    budget = int(2.5 * per_request) + (1 << 20)
+    with egh.Server(budget, slots=8, max_batch_sources=ns, precision=0) as sv:
+        sid = sv.add_set(Q, f, 1e-3, 4000, 4096)
+        big = _pinned((200, 64, 4000), torch)
+        with pytest.raises(egh.EghError) as ei:
+            sv.submit(sid, big, big)
+        assert ei.value.status == egh.EGH_ENOMEM
+        r = synth.bandlimited_noise(rng, (ns, 64, nt_d), 1e-3, 2.0, 10.0)
+        rin = _pinned(r.shape, torch, r)
+        outs = [_pinned(r.shape, torch) for _ in range(10)]
+        rids = [sv.submit(sid, rin, o) for o in outs]
+        for rid in rids:
+            assert sv.wait(rid) > 0.0
+        st = sv.stats()
+        assert st["completed"] == 10 and st["rejected"] == 1
+        assert st["peak_bytes_in_use"] <= budget
+        assert 1 <= st["peak_in_flight"] <= 2  # the budget holds two requests at a time
+        for o in outs[1:]:
+            np.testing.assert_array_equal(o.numpy(), outs[0].numpy())
+    with egh.Server(64 * per_request, slots=8, max_batch_sources=ns, precision=0) as sv:
+        sid = sv.add_set(Q, f, 1e-3, 4000, 4096)
+        rids = [sv.submit(sid, rin, o) for o in outs]
+        sv.drain()
+        for rid in rids:
+            sv.wait(rid)
+        assert sv.stats()["peak_in_flight"] >= 2  # batches overlapped on the device
