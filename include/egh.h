@@ -131,9 +131,10 @@ typedef struct {
 } egh_stats;
 
 /* Validates the configuration and allocates the device state on the current
- * CUDA device.  Rejects (EGH_EINVAL): non-positive sizes or spacings, a
- * receiver outside the physical grid, a frequency outside (0, 1/(2 dt)),
- * nonzero reserved fields.  On failure *out is NULL. */
+ * CUDA device (the Green-stage buffers, the largest, on the first egh_green).
+ * Rejects (EGH_EINVAL): non-positive sizes or spacings, a receiver outside the
+ * physical grid, a frequency outside (0, 1/(2 dt)), nonzero reserved fields.
+ * On failure *out is NULL. */
 egh_status egh_create(const egh_config *cfg, egh_ctx **out);
 
 /* Frees everything the context owns.  NULL is a no-op. */
@@ -285,6 +286,27 @@ const char *egh_server_last_error(const egh_server *sv);
 
 /* Finishes queued requests, then frees the server. */
 void egh_server_destroy(egh_server *sv);
+
+/* Frees the Green-stage buffers (transforms, bf16 transforms, snapshot ring) of a context whose
+ * Hessians are built; the next egh_green allocates them again.  Lets several survey patches
+ * keep their factored Hessians resident while only one holds its Green functions.  egh_hessian
+ * and egh_get_green then return EGH_ESTATE until egh_green runs again.  Blocks. */
+egh_status egh_release_green(egh_ctx *ctx);
+
+/* ---- Batched factorisation --------------------------------------------------------------- *
+ * A batch groups contexts (survey patches of one model, any receiver counts, one device, one
+ * precision) whose Hessians are factored together: egh_batch_factor factors every frequency of
+ * every context in one persistent launch (blocks take matrices b, b + grid, ...), replayed as a
+ * CUDA graph together with the Q -> L copies.  On the first call the launch's block size is
+ * chosen by timing the candidates on the batch's own matrices.  Contexts must have passed
+ * egh_hessian and must outlive the batch.  EGH_ENOTPD names the first failing context and
+ * frequency in *bad_ctx, *bad_freq (host, may be NULL; -1 when all succeed).  Blocks until the
+ * pivot status is known. */
+typedef struct egh_batch egh_batch;
+egh_status egh_batch_create(egh_ctx *const *ctxs, int32_t n, egh_batch **out);
+egh_status egh_batch_factor(egh_batch *b, int32_t *bad_ctx, int32_t *bad_freq, void *stream);
+const char *egh_batch_last_error(const egh_batch *b);
+void egh_batch_destroy(egh_batch *b);
 
 /* Fills *out with the last timings and counters.  Blocks on pending events. */
 egh_status egh_get_stats(egh_ctx *ctx, egh_stats *out);

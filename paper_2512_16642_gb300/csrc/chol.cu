@@ -17,16 +17,13 @@ constexpr int CH_THREADS = 512;
 // double from the stored FP32 columns) and each pivot is taken from it, so the pivots of
 // ill-conditioned matrices do not inherit the FP32 cancellation of the trailing updates; the
 // off-diagonal entries stay FP32.
-__global__ void __launch_bounds__(CH_THREADS)
-    k_potrf(float2* __restrict__ Lh, int n, int* __restrict__ status, int piv64) {
-  extern __shared__ float2 col[];  // [n] columns, then [n] doubles of the FP64 diagonal
-  double* dg = reinterpret_cast<double*>(col + n + (n & 1));
-  __shared__ int bad;
-  const int k = blockIdx.x;
-  float2* A = Lh + (long long)k * n * n;
+// Factors one n x n matrix in place with the calling block (status: 0 or failing pivot + 1).
+__device__ void potrf_block(float2* __restrict__ A, int n, int* __restrict__ status_k, int piv64,
+                            float2* col, double* dg, int& bad) {
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   if (tid == 0) bad = 0;
+  __syncthreads();
   if (piv64)
     for (int i = tid; i < n; i += blockDim.x) dg[i] = (double)A[(long long)i * n + i].x;
   __syncthreads();
@@ -67,13 +64,62 @@ __global__ void __launch_bounds__(CH_THREADS)
     }
     __syncthreads();
   }
-  if (tid == 0) status[k] = bad;
+  if (tid == 0) *status_k = bad;
   if (!bad) {
     for (long long t = tid; t < (long long)n * n; t += blockDim.x) {
       const int i = (int)(t / n), l = (int)(t % n);
       if (l > i) A[t] = make_float2(0.f, 0.f);
     }
   }
+}
+
+__global__ void __launch_bounds__(CH_THREADS)
+    k_potrf(float2* __restrict__ Lh, int n, int* __restrict__ status, int piv64) {
+  extern __shared__ float2 col[];  // [n] columns, then [n] doubles of the FP64 diagonal
+  double* dg = reinterpret_cast<double*>(col + n + (n & 1));
+  __shared__ int bad;
+  const int k = blockIdx.x;
+  potrf_block(Lh + (long long)k * n * n, n, status + k, piv64, col, dg, bad);
+}
+
+// Batched form: every matrix of a list (several survey patches x all their frequencies, of
+// different sizes) in one persistent launch; block b factors matrices b, b + gridDim.x, ...
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS)
+    k_potrf_many(const PotrfItem* __restrict__ items, int count, int piv64) {
+  extern __shared__ float2 col[];  // sized for the largest matrix
+  __shared__ int bad;
+  for (int m = blockIdx.x; m < count; m += gridDim.x) {
+    const PotrfItem it = items[m];
+    double* dg = reinterpret_cast<double*>(col + it.n + (it.n & 1));
+    potrf_block(it.A, it.n, it.status, piv64, col, dg, bad);
+    __syncthreads();
+  }
+}
+
+size_t potrf_smem(int nmax) {
+  return sizeof(float2) * (size_t)(nmax + (nmax & 1)) + sizeof(double) * (size_t)nmax;
+}
+
+cudaError_t potrf_many_prepare(int nmax) {
+  const int smem = (int)potrf_smem(nmax);
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_potrf_many<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
+  if ((e = cudaFuncSetAttribute(k_potrf_many<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem))) return e;
+  return cudaFuncSetAttribute(k_potrf_many<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+cudaError_t launch_potrf_many(const PotrfItem* items, int count, int nmax, int blocks, int threads,
+                              int piv64, cudaStream_t st) {
+  const size_t smem = potrf_smem(nmax);
+  count_launches(1);
+  switch (threads) {
+    case 256: k_potrf_many<256><<<blocks, 256, smem, st>>>(items, count, piv64); break;
+    case 512: k_potrf_many<512><<<blocks, 512, smem, st>>>(items, count, piv64); break;
+    case 1024: k_potrf_many<1024><<<blocks, 1024, smem, st>>>(items, count, piv64); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_potrf(float2* Lh, int n, int nf, int* status, cudaStream_t st, int piv64) {

@@ -95,6 +95,19 @@ struct egh_ctx {
   std::string err;
 };
 
+
+// Several contexts (survey patches of one model) whose Hessians are factored together.
+struct egh_batch {
+  std::vector<egh_ctx*> ctxs;
+  int dev = 0, nmax = 0, count = 0, piv64 = 0, threads = 0;
+  PotrfItem* items = nullptr;  // device list of every (context, frequency) matrix
+  int* status = nullptr;       // device, one per item
+  cudaStream_t cap = nullptr;  // capture stream
+  cudaGraphExec_t graph = nullptr;
+  cudaEvent_t ev[2] = {};
+  std::string err;
+};
+
 namespace {
 
 egh_status fail(egh_ctx* c, egh_status s, const std::string& msg) {
@@ -264,6 +277,41 @@ void free_all(egh_ctx* c) {
 }
 
 
+// The Green-stage buffers (snapshot ring, transforms, bf16 transforms) are the largest; egh_green
+// allocates them on its first call and again after egh_release_green freed them.
+egh_status ensure_green_buffers(egh_ctx* ctx) {
+  if (ctx->gh) return EGH_OK;
+  const Layout& L = ctx->L;
+  const size_t snap_bytes = (size_t)2 * 2 * ctx->K * ctx->Bp * (size_t)L.G * sizeof(__nv_bfloat16);
+  egh_status s;
+  if ((s = dalloc(ctx, (void**)&ctx->snap, snap_bytes, "snapshot ring"))) return s;
+  if ((s = dalloc(ctx, (void**)&ctx->gh, (size_t)ctx->nrec * ctx->nf * 2 * (size_t)L.G * sizeof(float),
+                  "green transforms")))
+    return s;
+  if (ctx->prec == EGH_PREC_MIXED &&
+      (s = dalloc(ctx, (void**)&ctx->ghb,
+                  (size_t)ctx->nrec * ctx->nf * 4 * (size_t)L.G * sizeof(__nv_bfloat16),
+                  "bf16 transforms")))
+    return s;
+  // padding points of every snapshot slot stay zero for the life of the buffer
+  CK(cudaMemset(ctx->snap, 0, snap_bytes));
+  CK(make_snap_tmap(&ctx->tmap, ctx->snap, L.G, ctx->Bp, 2 * ctx->K));
+  if (ctx->ghb) CK(make_ghb_tmap(&ctx->tmap_ghb, ctx->ghb, L.G, ctx->nf, ctx->nrec));
+  return EGH_OK;
+}
+
+void release_green_buffers(egh_ctx* ctx) {
+  cudaFree(ctx->snap);
+  cudaFree(ctx->gh);
+  cudaFree(ctx->ghb);
+  ctx->snap = nullptr;
+  ctx->gh = nullptr;
+  ctx->ghb = nullptr;
+  // graphs captured the ring slots' addresses
+  for (auto& kv : ctx->fd_graphs) cudaGraphExecDestroy(kv.second);
+  ctx->fd_graphs.clear();
+}
+
 // FD steps t = ta .. t1-1 of a chunk whose level t0 sits in ring slot sbase, on the FD stream, as
 // one CUDA graph (captured on first use, then replayed: the kernel nodes' arguments depend only
 // on the key, since state slots follow t mod 3 and ring slots follow t - t0).
@@ -406,14 +454,8 @@ egh_status egh_create(const egh_config* cfg, egh_ctx** out) {
   } while (0)
   ALLOC(ctx->coef, F * sizeof(float2), "coefficients");
   ALLOC(ctx->lev, (size_t)3 * ((ctx->B + 1) / 2) * F * sizeof(float2), "FD state");
-  ALLOC(ctx->snap, (size_t)2 * 2 * ctx->K * ctx->Bp * (size_t)L.G * sizeof(__nv_bfloat16),
-        "snapshot ring");
   std::vector<unsigned char> twt = dft_twiddle_tiles(ctx->freqs, c.dt, c.nt);
   ALLOC(ctx->twt, twt.size(), "twiddle tiles");
-  ALLOC(ctx->gh, (size_t)c.nrec * c.nfreq * 2 * (size_t)L.G * sizeof(float), "green transforms");
-  if (ctx->prec == EGH_PREC_MIXED)
-    ALLOC(ctx->ghb, (size_t)c.nrec * c.nfreq * 4 * (size_t)L.G * sizeof(__nv_bfloat16),
-          "bf16 transforms");
   ALLOC(ctx->part,
         std::max(gram_workspace_floats(c.nrec, c.nfreq, ctx->splits),
                  gram_tc_workspace_floats(c.nrec, c.nfreq, ctx->splits_tc)) * sizeof(float),
@@ -434,12 +476,9 @@ egh_status egh_create(const egh_config* cfg, egh_ctx** out) {
     // guard rows and padding columns of every state slot, and the padding points of every
     // snapshot slot, stay zero for the life of the context
     CK(cudaMemset(ctx->lev, 0, (size_t)3 * ((ctx->B + 1) / 2) * F * sizeof(float2)));
-    CK(cudaMemset(ctx->snap, 0,
-                  (size_t)2 * 2 * ctx->K * ctx->Bp * (size_t)L.G * sizeof(__nv_bfloat16)));
+
     CK(cudaMemcpy(ctx->twt, twt.data(), twt.size(), cudaMemcpyHostToDevice));
-    CK(make_snap_tmap(&ctx->tmap, ctx->snap, L.G, ctx->Bp, 2 * ctx->K));
     CK(fd_prepare(c.nfreq));
-    if (ctx->ghb) CK(make_ghb_tmap(&ctx->tmap_ghb, ctx->ghb, L.G, c.nfreq, c.nrec));
     {
       // FD steps are a serial chain of short kernels: their stream gets the highest priority so
       // that their blocks are placed ahead of the transform's, which fills the rest of the GPU
@@ -503,7 +542,9 @@ egh_status egh_green(egh_ctx* ctx, const float* vel, void* stream_) {
   cudaStream_t stream = (cudaStream_t)stream_;
   CK(cudaSetDevice(ctx->dev));
   ctx->state = ST_CREATED;
-  egh_status s = prepare_model(ctx, vel, stream);
+  egh_status s = ensure_green_buffers(ctx);
+  if (s) return s;
+  s = prepare_model(ctx, vel, stream);
   if (s) return s;
   const Layout& L = ctx->L;
   const int K = ctx->K, B = ctx->B, nt = ctx->nt;
@@ -610,7 +651,8 @@ egh_status egh_hessian(egh_ctx* ctx, egh_mu_mode mode, double mu_param, double* 
   if (!ctx) return fail(nullptr, EGH_EINVAL, "ctx is NULL");
   cudaStream_t stream = (cudaStream_t)stream_;
   CK(cudaSetDevice(ctx->dev));
-  if (ctx->state < ST_GREEN) return fail(ctx, EGH_ESTATE, "egh_hessian needs egh_green first");
+  if (ctx->state < ST_GREEN || !ctx->gh)
+    return fail(ctx, EGH_ESTATE, "egh_hessian needs egh_green first");
   if (!std::isfinite(mu_param) || mu_param < 0)
     return fail(ctx, EGH_EINVAL, "mu_param must be finite and >= 0");
   if (mode != EGH_MU_ABS && mode != EGH_MU_REL_MEANDIAG && mode != EGH_MU_REL_MAXEIG)
@@ -833,7 +875,7 @@ egh_status egh_forward(egh_ctx* ctx, const float* vel, int32_t nsrc, const int32
 egh_status egh_get_green(egh_ctx* ctx, int32_t r0, int32_t nr, void* host_out) {
   if (!ctx) return fail(nullptr, EGH_EINVAL, "ctx is NULL");
   CK(cudaSetDevice(ctx->dev));
-  if (ctx->state < ST_GREEN) return fail(ctx, EGH_ESTATE, "no Green functions yet");
+  if (ctx->state < ST_GREEN || !ctx->gh) return fail(ctx, EGH_ESTATE, "no Green functions yet");
   if (r0 < 0 || nr < 0 || r0 + nr > ctx->nrec || !host_out)
     return fail(ctx, EGH_EINVAL, "bad receiver range");
   CK(cudaDeviceSynchronize());
@@ -886,6 +928,162 @@ egh_status egh_get_stats(egh_ctx* ctx, egh_stats* out) {
   ctx->st.fd_rows = ctx->fd_tz;
   *out = ctx->st;
   return EGH_OK;
+}
+
+egh_status egh_release_green(egh_ctx* ctx) {
+  if (!ctx) return fail(nullptr, EGH_EINVAL, "ctx is NULL");
+  CK(cudaSetDevice(ctx->dev));
+  CK(cudaDeviceSynchronize());
+  release_green_buffers(ctx);
+  return EGH_OK;
+}
+
+static egh_status bfail(egh_batch* b, egh_status s, const std::string& msg) {
+  if (b)
+    b->err = msg;
+  else
+    set_context_free_error(msg);
+  return s;
+}
+
+#define BCK(call)                                                                         \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return bfail(b, EGH_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));     \
+  } while (0)
+
+void egh_batch_destroy(egh_batch* b) {
+  if (!b) return;
+  cudaSetDevice(b->dev);
+  cudaDeviceSynchronize();
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  for (cudaEvent_t e : b->ev)
+    if (e) cudaEventDestroy(e);
+  cudaFree(b->items);
+  cudaFree(b->status);
+  delete b;
+}
+
+egh_status egh_batch_create(egh_ctx* const* ctxs, int32_t n, egh_batch** out) {
+  if (!out || !ctxs || n < 1) return bfail(nullptr, EGH_EINVAL, "need >= 1 context");
+  *out = nullptr;
+  egh_batch* b = new (std::nothrow) egh_batch();
+  if (!b) return bfail(nullptr, EGH_ENOMEM, "host allocation failed");
+  std::vector<PotrfItem> items;
+  for (int i = 0; i < n; ++i) {
+    egh_ctx* c = ctxs[i];
+    if (!c) {
+      delete b;
+      return bfail(nullptr, EGH_EINVAL, "NULL context in the batch");
+    }
+    if (i > 0 && (c->dev != ctxs[0]->dev || c->prec != ctxs[0]->prec)) {
+      delete b;
+      return bfail(nullptr, EGH_EINVAL, "batched contexts must share device and precision");
+    }
+    b->ctxs.push_back(c);
+    b->nmax = std::max(b->nmax, c->nrec);
+  }
+  b->dev = ctxs[0]->dev;
+  b->piv64 = ctxs[0]->prec == EGH_PREC_MIXED ? 1 : 0;
+  cudaSetDevice(b->dev);
+  int off = 0;
+  for (egh_ctx* c : b->ctxs) off += c->nf;
+  b->count = off;
+  auto setup = [&]() -> egh_status {
+    BCK(cudaMalloc(&b->status, sizeof(int) * b->count));
+    BCK(cudaMalloc(&b->items, sizeof(PotrfItem) * b->count));
+    int o = 0;
+    for (egh_ctx* c : b->ctxs)
+      for (int k = 0; k < c->nf; ++k, ++o)
+        items.push_back(PotrfItem{c->Lh + (size_t)k * c->nrec * c->nrec, c->nrec, b->status + o});
+    BCK(cudaMemcpy(b->items, items.data(), sizeof(PotrfItem) * items.size(), cudaMemcpyHostToDevice));
+    BCK(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
+    BCK(cudaEventCreate(&b->ev[0]));
+    BCK(cudaEventCreate(&b->ev[1]));
+    BCK(potrf_many_prepare(b->nmax));
+    return EGH_OK;
+  };
+  egh_status s = setup();
+  if (s) {
+    const std::string m = b->err;
+    egh_batch_destroy(b);
+    return bfail(nullptr, s, m);
+  }
+  *out = b;
+  return EGH_OK;
+}
+
+// Q -> L copies of every context and one persistent factorisation launch, on `st`.
+static cudaError_t batch_enqueue(egh_batch* b, int threads, cudaStream_t st) {
+  cudaError_t e;
+  for (egh_ctx* c : b->ctxs)
+    if ((e = cudaMemcpyAsync(c->Lh, c->Qh, (size_t)c->nf * c->nrec * c->nrec * sizeof(float2),
+                             cudaMemcpyDeviceToDevice, st)))
+      return e;
+  return launch_potrf_many(b->items, b->count, b->nmax, std::min(b->count, 2 * 152), threads, b->piv64, st);
+}
+
+egh_status egh_batch_factor(egh_batch* b, int32_t* bad_ctx, int32_t* bad_freq, void* stream_) {
+  if (!b) return bfail(nullptr, EGH_EINVAL, "batch is NULL");
+  cudaStream_t stream = (cudaStream_t)stream_;
+  if (bad_ctx) *bad_ctx = -1;
+  if (bad_freq) *bad_freq = -1;
+  BCK(cudaSetDevice(b->dev));
+  for (egh_ctx* c : b->ctxs)
+    if (c->state < ST_HESSIAN) return bfail(b, EGH_ESTATE, "every context needs egh_hessian first");
+  if (!b->graph) {
+    // launch shape: time each block size on these matrices and keep the fastest; then capture
+    // the copies and the launch once as a CUDA graph
+    float best = 1e30f;
+    for (int th : {256, 512, 1024}) {
+      float ms = 0.f;
+      for (int rep = 0; rep < 2; ++rep) {
+        BCK(cudaEventRecord(b->ev[0], stream));
+        BCK(batch_enqueue(b, th, stream));
+        BCK(cudaEventRecord(b->ev[1], stream));
+        BCK(cudaEventSynchronize(b->ev[1]));
+        BCK(cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]));
+      }
+      if (ms < best) {
+        best = ms;
+        b->threads = th;
+      }
+    }
+    count_launches(-6);  // tuning launches are not part of the factorisation
+    BCK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = batch_enqueue(b, b->threads, b->cap);
+    count_launches(-1);  // counted at each replay
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(b->cap, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) return bfail(b, EGH_ECUDA, std::string("batch graph: ") + cudaGetErrorString(e));
+  }
+  BCK(cudaGraphLaunch(b->graph, stream));
+  count_launches(1);
+  std::vector<int> stv(b->count);
+  BCK(cudaMemcpyAsync(stv.data(), b->status, sizeof(int) * b->count, cudaMemcpyDeviceToHost, stream));
+  BCK(cudaStreamSynchronize(stream));
+  int o = 0;
+  for (int i = 0; i < (int)b->ctxs.size(); ++i) {
+    egh_ctx* c = b->ctxs[i];
+    for (int k = 0; k < c->nf; ++k, ++o)
+      if (stv[o]) {
+        if (bad_ctx) *bad_ctx = i;
+        if (bad_freq) *bad_freq = k;
+        return bfail(b, EGH_ENOTPD, "Hessian " + std::to_string(k) + " of batch context " +
+                                        std::to_string(i) + " not positive definite");
+      }
+  }
+  for (egh_ctx* c : b->ctxs) c->state = ST_FACTORED;
+  return EGH_OK;
+}
+
+const char* egh_batch_last_error(const egh_batch* b) {
+  return b ? b->err.c_str() : egh_last_error(nullptr);
 }
 
 }  // extern "C"

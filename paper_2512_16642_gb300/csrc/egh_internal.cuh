@@ -102,6 +102,15 @@ cudaError_t launch_add_mu_copy(float2* Qh, float2* Lh, int nrec, int nf, float m
 
 // ---- chol.cu ----------------------------------------------------------------------------------
 // piv64: FP64 diagonal and pivots (mixed precision)
+struct PotrfItem {
+  float2* A;    // n x n, factored in place
+  int n;
+  int* status;  // 0, or the failing pivot + 1
+};
+size_t potrf_smem(int nmax);
+cudaError_t potrf_many_prepare(int nmax);
+cudaError_t launch_potrf_many(const PotrfItem* items, int count, int nmax, int blocks, int threads,
+                              int piv64, cudaStream_t st);
 cudaError_t launch_potrf(float2* Lh, int n, int nf, int* status, cudaStream_t st, int piv64);
 
 // ---- deblur.cu --------------------------------------------------------------------------------

@@ -94,6 +94,11 @@ _SIGS = {
     "egh_last_error": ([_vp], ctypes.c_char_p),
     "egh_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "egh_version": ([], ctypes.c_int32),
+    "egh_release_green": ([_vp], ctypes.c_int),
+    "egh_batch_create": ([ctypes.POINTER(_vp), ctypes.c_int32, ctypes.POINTER(_vp)], ctypes.c_int),
+    "egh_batch_factor": ([_vp, _i32p, _i32p, _vp], ctypes.c_int),
+    "egh_batch_last_error": ([_vp], ctypes.c_char_p),
+    "egh_batch_destroy": ([_vp], None),
     "egh_server_create": ([ctypes.POINTER(egh_server_config), ctypes.POINTER(_vp)], ctypes.c_int),
     "egh_server_add_set": ([_vp, ctypes.c_int32, ctypes.c_int32, _f64p, ctypes.c_double, ctypes.c_int32,
                             ctypes.c_int32, _vp, _i32p], ctypes.c_int),
@@ -321,6 +326,9 @@ class Context:
         egh_get_green(self.h, r0, nr, out)
         return out
 
+    def release_green(self):
+        _check(load().egh_release_green(self.h), self.h)
+
     def get_hessian(self, factored=False):
         out = np.zeros((self.nf, self.nrec, self.nrec), dtype=np.complex64)
         egh_get_hessian(self.h, 1 if factored else 0, out)
@@ -328,6 +336,46 @@ class Context:
 
     def stats(self):
         return egh_get_stats(self.h)
+
+
+# ---- batched factorisation -------------------------------------------------------------------
+class Batch:
+    """Contexts (survey patches) factored together in one persistent launch replayed as a CUDA
+    graph (egh_batch_* in include/egh.h).  The contexts must outlive the batch."""
+
+    def __init__(self, contexts):
+        self._ctxs = list(contexts)
+        arr = (_vp * len(self._ctxs))(*[c.h for c in self._ctxs])
+        h = _vp()
+        rc = load().egh_batch_create(arr, len(self._ctxs), ctypes.byref(h))
+        if rc != EGH_OK:
+            raise EghError(rc, load().egh_batch_last_error(None).decode())
+        self.h = h
+
+    def factor(self, stream=None):
+        bc, bf = ctypes.c_int32(-1), ctypes.c_int32(-1)
+        rc = load().egh_batch_factor(self.h, ctypes.byref(bc), ctypes.byref(bf), _stream(stream, True))
+        if rc != EGH_OK:
+            err = EghError(rc, load().egh_batch_last_error(self.h).decode())
+            err.bad_ctx, err.bad_freq = bc.value, bf.value
+            raise err
+
+    def close(self):
+        if self.h:
+            load().egh_batch_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ---- serving ------------------------------------------------------------------------------
