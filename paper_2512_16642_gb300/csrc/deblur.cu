@@ -233,6 +233,145 @@ __global__ void __launch_bounds__(256)
 }
 
 // ---------------------------------------------------------------------------------------------
+// Explicit inverse of the Cholesky factor, W_k = L_k^{-1} (lower triangular), for solves as
+// matrix products X = W^H (W D).  Column j of W solves L w = e_j by forward substitution,
+// w_i = -(sum_{l=j}^{i-1} L_il w_l) / L_ii.  One warp per (frequency, column): the lanes split
+// each row's sum (coalesced reads of row i of L) and the column so far sits in shared memory.
+// ---------------------------------------------------------------------------------------------
+constexpr int TRI_WARPS = 4;
+
+__global__ void __launch_bounds__(32 * TRI_WARPS)
+    k_trtri(const float2* __restrict__ Lh, int n, int nf, float2* __restrict__ Wh) {
+  extern __shared__ float2 wcol[];  // [TRI_WARPS][n]
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const long long t = blockIdx.x * (long long)TRI_WARPS + wp;
+  if (t >= (long long)n * nf) return;  // warp-uniform
+  const int k = (int)(t / n), j = (int)(t % n);
+  const float2* L = Lh + (long long)k * n * n;
+  float2* W = Wh + (long long)k * n * n;
+  float2* w = wcol + (size_t)wp * n;
+  for (int i = lane; i < j; i += 32) W[(long long)i * n + j] = make_float2(0.f, 0.f);
+  const float wjj = 1.f / L[(long long)j * n + j].x;
+  if (lane == 0) {
+    w[j] = make_float2(wjj, 0.f);
+    W[(long long)j * n + j] = w[j];
+  }
+  __syncwarp();
+  for (int i = j + 1; i < n; ++i) {
+    const float2* Li = L + (long long)i * n;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int l = j + lane; l < i; l += 32) {
+      const float2 a = Li[l], v = w[l];
+      acc.x = fmaf(a.x, v.x, fmaf(-a.y, v.y, acc.x));
+      acc.y = fmaf(a.x, v.y, fmaf(a.y, v.x, acc.y));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    }
+    const float d = -1.f / Li[i].x;
+    if (lane == 0) {
+      w[i] = make_float2(acc.x * d, acc.y * d);
+      W[(long long)i * n + j] = w[i];
+    }
+    __syncwarp();
+  }
+}
+
+cudaError_t launch_trtri(const float2* Lh, int n, int nf, float2* Wh, cudaStream_t st) {
+  const long long m = (long long)n * nf;
+  const size_t smem = (size_t)TRI_WARPS * n * sizeof(float2);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_trtri, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  count_launches(1);
+  k_trtri<<<(unsigned)((m + TRI_WARPS - 1) / TRI_WARPS), 32 * TRI_WARPS, smem, st>>>(Lh, n, nf, Wh);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------
+// Batched complex products C_k = op(W_k) B_k, op = identity or conjugate transpose, W_k n x n,
+// B_k and C_k n x ld (all frequencies in one launch).  32 x 32 output tiles, 32-deep K steps
+// staged in shared memory over the triangle's nonzero range; each of the 256 threads computes a
+// 2 x 2 block.
+// ---------------------------------------------------------------------------------------------
+constexpr int CG_T = 32;
+
+template <bool CONJT>
+__global__ void __launch_bounds__(256)
+    k_cgemm(const float2* __restrict__ Wh, int n, const float2* __restrict__ Bh, int ld,
+            float2* __restrict__ Ch) {
+  __shared__ float2 As[CG_T][CG_T + 1];  // As[r][kk] = op(W)[row0 + r][k0 + kk]
+  __shared__ float2 Bs[CG_T][CG_T + 1];  // Bs[kk][c] = B[k0 + kk][col0 + c]
+  const int k = blockIdx.z;
+  const float2* W = Wh + (long long)k * n * n;
+  const float2* B = Bh + (long long)k * n * ld;
+  float2* C = Ch + (long long)k * n * ld;
+  const int row0 = blockIdx.y * CG_T, col0 = blockIdx.x * CG_T;
+  const int tid = threadIdx.x, tr = (tid >> 4) * 2, tc = (tid & 15) * 2;
+  float2 acc[2][2];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) acc[a][b] = make_float2(0.f, 0.f);
+  // W is lower triangular (its upper part stored as zeros): rows row0.. of W need k < row0 + 32,
+  // rows of W^H need k >= row0
+  const int kbeg = CONJT ? row0 : 0, kend = CONJT ? n : min(n, row0 + CG_T);
+  for (int k0 = kbeg; k0 < kend; k0 += CG_T) {
+    for (int e = tid; e < CG_T * CG_T; e += 256) {
+      const int r = e / CG_T, c = e % CG_T;
+      float2 a = make_float2(0.f, 0.f);
+      if (CONJT) {
+        // op(W)[i][kk] = conj(W[kk][i]): read rows of W, coalesced along i
+        const int kk = k0 + r, i = row0 + c;
+        if (kk < n && i < n) a = W[(long long)kk * n + i];
+        As[c][r] = make_float2(a.x, -a.y);
+      } else {
+        const int i = row0 + r, kk = k0 + c;
+        if (i < n && kk < n) a = W[(long long)i * n + kk];
+        As[r][c] = a;
+      }
+      const int kk = k0 + r, cc = col0 + c;
+      Bs[r][c] = (kk < n && cc < ld) ? B[(long long)kk * ld + cc] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < CG_T; ++kk) {
+      const float2 a0 = As[tr][kk], a1 = As[tr + 1][kk];
+      const float2 b0 = Bs[kk][tc], b1 = Bs[kk][tc + 1];
+      const float2 av[2] = {a0, a1}, bv[2] = {b0, b1};
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+          acc[a][b].x = fmaf(av[a].x, bv[b].x, fmaf(-av[a].y, bv[b].y, acc[a][b].x));
+          acc[a][b].y = fmaf(av[a].x, bv[b].y, fmaf(av[a].y, bv[b].x, acc[a][b].y));
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const int i = row0 + tr + a, c = col0 + tc + b;
+      if (i < n && c < ld) C[(long long)i * ld + c] = acc[a][b];
+    }
+}
+
+// X = W^H (W D) through the scratch Y (both n x ld per frequency); D and X may alias.
+cudaError_t launch_inverse_solve(const float2* Wh, int n, int nf, const float2* D, float2* Y,
+                                 float2* X, int ld, cudaStream_t st) {
+  const dim3 grid((ld + CG_T - 1) / CG_T, (n + CG_T - 1) / CG_T, nf);
+  count_launches(2);
+  k_cgemm<false><<<grid, 256, 0, st>>>(Wh, n, D, ld, Y);
+  k_cgemm<true><<<grid, 256, 0, st>>>(Wh, n, Y, ld, X);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------
 // Refinement residual in FP64: R_k = D_k - Q_k X_k, products of the FP32 operands (exact in FP64)
 // accumulated in double and rounded once (mixed-precision iterative refinement of the solves).
 // One block per (frequency, 32 sources, group of rows); X_k's columns sit in shared memory;

@@ -62,6 +62,7 @@ struct egh_ctx {
   __nv_bfloat16* ghb = nullptr;              // [nrec][nf][re/im][hi/lo][G] Gram operands
   CUtensorMap tmap_ghb{};                    // TMA map of ghb
   float2 *Qh = nullptr, *Lh = nullptr, *tw = nullptr;
+  float2* Wh = nullptr;  // mixed precision: W = L^{-1} per frequency (solves as products)
   int tw_len = 0;
   cudaStream_t side = nullptr;                 // the transform's stream inside egh_green (low priority)
   cudaStream_t fdst = nullptr;                 // the FD stream inside egh_green (high priority)
@@ -258,7 +259,7 @@ cudaError_t zero_snap_slot(egh_ctx* ctx, int j, cudaStream_t st) {
 }
 
 void free_all(egh_ctx* c) {
-  void* ptrs[] = {c->Dr, c->Rr, c->coef, c->lev, c->snap, c->twt, c->gh, c->ghb, c->part, c->Qh, c->Lh, c->tw, c->w_dev,
+  void* ptrs[] = {c->Wh, c->Dr, c->Rr, c->coef, c->lev, c->snap, c->twt, c->gh, c->ghb, c->part, c->Qh, c->Lh, c->tw, c->w_dev,
                   c->rec_pts, c->status, c->dsum, c->lmax, c->vchk, c->d_err, c->vel_stage, c->Dh,
                   c->io_in, c->io_out};
   for (void* p : ptrs)
@@ -462,6 +463,8 @@ egh_status egh_create(const egh_config* cfg, egh_ctx** out) {
         "gram");
   ALLOC(ctx->Qh, (size_t)c.nfreq * c.nrec * c.nrec * sizeof(float2), "Qh");
   ALLOC(ctx->Lh, (size_t)c.nfreq * c.nrec * c.nrec * sizeof(float2), "Lh");
+  if (ctx->prec == EGH_PREC_MIXED)
+    ALLOC(ctx->Wh, (size_t)c.nfreq * c.nrec * c.nrec * sizeof(float2), "inverse factors");
   ALLOC(ctx->w_dev, (size_t)c.nfreq * sizeof(float), "weights");
   ALLOC(ctx->rec_pts, (size_t)c.nrec * sizeof(int), "receivers");
   ALLOC(ctx->status, (size_t)c.nfreq * sizeof(int), "status");
@@ -712,6 +715,7 @@ egh_status egh_factor(egh_ctx* ctx, int32_t* bad_freq, void* stream_) {
   CK(cudaMemcpyAsync(ctx->Lh, ctx->Qh, bytes, cudaMemcpyDeviceToDevice, stream));
   CK(launch_potrf(ctx->Lh, ctx->nrec, ctx->nf, ctx->status, stream,
                   ctx->prec == EGH_PREC_MIXED ? 1 : 0));
+  if (ctx->Wh) CK(launch_trtri(ctx->Lh, ctx->nrec, ctx->nf, ctx->Wh, stream));
   CK(cudaEventRecord(ctx->ev[5], stream));
   ctx->ev_rec[2] = true;
   std::vector<int> stv(ctx->nf);
@@ -779,11 +783,15 @@ static egh_status deblur_common(egh_ctx* ctx, const float* resid, int32_t ns, in
       return s;
     CK(cudaMemcpyAsync(ctx->Dr, D, dbytes, cudaMemcpyDeviceToDevice, stream));
   }
-  CK(launch_trsm(ctx->Lh, ctx->nrec, ctx->nf, D, ns, stream));
   if (ctx->prec == EGH_PREC_MIXED) {
+    // X = W^H W D (products with the explicit inverse factor), residual D - Q X in FP64, the
+    // correction solved the same way
+    CK(launch_inverse_solve(ctx->Wh, ctx->nrec, ctx->nf, D, ctx->Rr, D, ns, stream));
     CK(launch_resid64(ctx->Qh, ctx->nrec, ctx->nf, D, ctx->Dr, ns, ctx->Rr, stream));
-    CK(launch_trsm(ctx->Lh, ctx->nrec, ctx->nf, ctx->Rr, ns, stream));
+    CK(launch_inverse_solve(ctx->Wh, ctx->nrec, ctx->nf, ctx->Rr, ctx->Dr, ctx->Rr, ns, stream));
     CK(launch_add_correction(D, ctx->Rr, (long long)ctx->nf * ntr, stream));
+  } else {
+    CK(launch_trsm(ctx->Lh, ctx->nrec, ctx->nf, D, ns, stream));
   }
   if (!X) CK(launch_synth(D, ctx->nrec, ns, ns, 0, ctx->nf, ctx->w_dev, ctx->tw, nt_d, dout, stream));
   CK(cudaEventRecord(ctx->ev[7], stream));
@@ -1022,7 +1030,12 @@ static cudaError_t batch_enqueue(egh_batch* b, int threads, cudaStream_t st) {
     if ((e = cudaMemcpyAsync(c->Lh, c->Qh, (size_t)c->nf * c->nrec * c->nrec * sizeof(float2),
                              cudaMemcpyDeviceToDevice, st)))
       return e;
-  return launch_potrf_many(b->items, b->count, b->nmax, std::min(b->count, 2 * 152), threads, b->piv64, st);
+  if ((e = launch_potrf_many(b->items, b->count, b->nmax, std::min(b->count, 2 * 152), threads,
+                             b->piv64, st)))
+    return e;
+  for (egh_ctx* c : b->ctxs)
+    if (c->Wh && (e = launch_trtri(c->Lh, c->nrec, c->nf, c->Wh, st))) return e;
+  return cudaSuccess;
 }
 
 egh_status egh_batch_factor(egh_batch* b, int32_t* bad_ctx, int32_t* bad_freq, void* stream_) {

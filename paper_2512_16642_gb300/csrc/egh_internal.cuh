@@ -118,6 +118,10 @@ cudaError_t launch_potrf(float2* Lh, int n, int nf, int* status, cudaStream_t st
 cudaError_t launch_trace_dft(const float* resid, int ntr, int nt_d, const float2* tw, int nf,
                              int nrec, int ld, int s0, float2* Dh, cudaStream_t st);
 cudaError_t launch_trsm(const float2* Lh, int n, int nf, float2* Dh, int ns, cudaStream_t st);
+// W = L^{-1} per frequency; X = W^H (W D) with scratch Y
+cudaError_t launch_trtri(const float2* Lh, int n, int nf, float2* Wh, cudaStream_t st);
+cudaError_t launch_inverse_solve(const float2* Wh, int n, int nf, const float2* D, float2* Y,
+                                 float2* X, int ld, cudaStream_t st);
 cudaError_t launch_resid64(const float2* Qh, int n, int nf, const float2* Xh, const float2* Dh,
                            int ns, float2* Rh, cudaStream_t st);
 cudaError_t launch_add_correction(float2* X, const float2* R, long long m, cudaStream_t st);

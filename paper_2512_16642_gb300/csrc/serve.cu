@@ -87,6 +87,7 @@ class Arena {
 struct HSet {
   int nrec = 0, nf = 0, tw_len = 0;
   float2 *Qh = nullptr, *Lh = nullptr, *tw = nullptr;
+  float2* Wh = nullptr;  // mixed precision: W = L^{-1}
   float* w = nullptr;
 };
 
@@ -196,9 +197,9 @@ cudaError_t run_batch(Server* sv, Batch* b, const HSet& h) {
     float2* Dr = D + dsz;
     float2* R = D + 2 * dsz;
     if ((e = cudaMemcpyAsync(Dr, D, dsz * sizeof(float2), cudaMemcpyDeviceToDevice, st))) return e;
-    if ((e = launch_trsm(h.Lh, h.nrec, h.nf, D, ld, st))) return e;
+    if ((e = launch_inverse_solve(h.Wh, h.nrec, h.nf, D, R, D, ld, st))) return e;
     if ((e = launch_resid64(h.Qh, h.nrec, h.nf, D, Dr, ld, R, st))) return e;
-    if ((e = launch_trsm(h.Lh, h.nrec, h.nf, R, ld, st))) return e;
+    if ((e = launch_inverse_solve(h.Wh, h.nrec, h.nf, R, Dr, R, ld, st))) return e;
     if ((e = launch_add_correction(D, R, (long long)dsz, st))) return e;
   } else {
     if ((e = launch_trsm(h.Lh, h.nrec, h.nf, D, ld, st))) return e;
@@ -380,6 +381,7 @@ egh_status egh_server_add_set(egh_server* sv, int32_t nrec, int32_t nfreq, const
   int* status = nullptr;
   cudaStream_t st = sv->streams[0];
   auto cleanup = [&]() {
+    cudaFree(h.Wh);
     cudaFree(h.Qh);
     cudaFree(h.Lh);
     cudaFree(h.tw);
@@ -397,6 +399,10 @@ egh_status egh_server_add_set(egh_server* sv, int32_t nrec, int32_t nfreq, const
   if (!e) e = cudaMemcpy(h.tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice);
   if (!e) e = cudaMemcpy(h.w, w.data(), w.size() * sizeof(float), cudaMemcpyHostToDevice);
   if (!e) e = launch_potrf(h.Lh, nrec, nfreq, status, st, sv->prec == EGH_PREC_MIXED ? 1 : 0);
+  if (!e && sv->prec == EGH_PREC_MIXED) {
+    e = cudaMalloc(&h.Wh, qn * sizeof(float2));
+    if (!e) e = launch_trtri(h.Lh, nrec, nfreq, h.Wh, st);
+  }
   std::vector<int> stv(nfreq, 0);
   if (!e) e = cudaMemcpyAsync(stv.data(), status, nfreq * sizeof(int), cudaMemcpyDeviceToHost, st);
   if (!e) e = cudaStreamSynchronize(st);
@@ -537,6 +543,7 @@ void egh_server_destroy(egh_server* sv) {
   for (auto& s : sv->streams) cudaStreamSynchronize(s);
   for (auto& s : sv->streams) cudaStreamDestroy(s);
   for (HSet& h : sv->sets) {
+    cudaFree(h.Wh);
     cudaFree(h.Qh);
     cudaFree(h.Lh);
     cudaFree(h.tw);
