@@ -63,14 +63,23 @@ typedef enum {
                                 "Numerical examples": a fraction of the largest eigenvalue of S S^T) */
 } egh_mu_mode;
 
-/* Arithmetic of the Hessian stage (the transform is bf16x3 on the tensor cores in both, about
- * 2e-6 relative against FP64):
- *   EGH_PREC_FP32:  Gram as FP32 products and sums on the CUDA cores (the plain path);
- *   EGH_PREC_MIXED: Gram as bf16x3 products on the tensor cores with FP32 accumulation (each
- *                   transform stored as bf16 hi + lo; about 1e-5 relative against FP64). */
+/* Arithmetic of the Hessian, factorisation and solve stages (the transform is bf16x3 on the
+ * tensor cores in all three, about 2e-6 relative against FP64):
+ *   EGH_PREC_FP32:       Gram as FP32 products and sums on the CUDA cores, FP32 Cholesky,
+ *                        triangular substitution (the plain path);
+ *   EGH_PREC_MIXED:      Gram as bf16x3 products on the tensor cores with FP32 accumulation (each
+ *                        transform stored as bf16 hi + lo; about 1e-5 relative against FP64);
+ *                        FP32 Cholesky with FP64 pivots; solves as products with the explicit
+ *                        inverse factor followed by one step of iterative refinement whose
+ *                        residual D - Q X is accumulated to FP64-class accuracy (about 2^-48
+ *                        relative) by a compensated FP32 dot product;
+ *   EGH_PREC_MIXED_FP64: as EGH_PREC_MIXED with the refinement residual accumulated in FP64
+ *                        arithmetic (the same rounded residual, several times slower on a GB300,
+ *                        whose FP64 rate is a small fraction of its FP32 rate). */
 typedef enum {
     EGH_PREC_FP32 = 0,
-    EGH_PREC_MIXED = 1
+    EGH_PREC_MIXED = 1,
+    EGH_PREC_MIXED_FP64 = 2
 } egh_precision;
 
 /*

@@ -60,7 +60,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
             objs = list(ex.map(compile_one, sources()))
         tmp_lib = os.path.join(tmpdir, "libegh.so")
-        r = subprocess.run([cc, *ARCH, "-shared", "-o", tmp_lib, *objs], capture_output=True, text=True)
+        r = subprocess.run([cc, *ARCH, "-shared", "-Xlinker", "--no-undefined", "-o", tmp_lib, *objs], capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")
         os.replace(tmp_lib, LIB)

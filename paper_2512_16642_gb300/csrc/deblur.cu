@@ -2,94 +2,154 @@
 // Section "Frequency domain inversion"):
 //   D[k][r][s] = sum_t resid[s][r][t] exp(-i w_k t dt)           (k_trace_dft)
 //   X_k = L_k^{-H} L_k^{-1} D_k                                   (k_trsm, all sources as RHS)
-//   mixed precision: X_k += L_k^{-H} L_k^{-1} (D_k - Q_k X_k)      (k_resid64 in FP64, k_trsm)
+//   mixed precision: X_k = W_k^H W_k D_k with W_k = L_k^{-1} (k_trtri once, k_cgemm), then
+//                    X_k += W_k^H W_k (D_k - Q_k X_k)             (k_resid_dot2 or k_resid64)
 //   mult[s][r][t] = sum_k w_k Re(X_k[r][s] exp(+i w_k t dt))      (k_synth)
 // Traces are indexed q = s * nrec + r (the [ns][nrec][nt] gather layout); the spectra of one call
 // occupy columns s0 .. s0 + ns - 1 of a [nf][nrec][ld] array, so that several gathers (of
 // different lengths) can share one solve.
 #include <algorithm>
+#include <cstdint>
 
 #include "egh_internal.cuh"
+#include "tc.cuh"
 
 namespace egh {
 
 constexpr int NFMAX = 64;
 
 // ---------------------------------------------------------------------------------------------
-// Forward transform: 64 traces per block, the time axis staged 64 samples at a time with the
-// twiddles of the stage in shared memory.  Thread (m, g) accumulates trace m at frequencies
-// k = g, g+4, ...; each stage's partial sum is added into the running total (two-level sum).
+// Forward transform: 128 traces per block and one warp per group of 8 frequencies; lane l
+// accumulates traces l, l + 32, l + 64, l + 96 at its warp's 8 frequencies (64 running sums per
+// thread, each twiddle read reused over 4 traces and each sample over 8 frequencies).  The time
+// axis is staged 32 samples at a time through a 3-deep ring of cp.async copies (zero-filled
+// outside the gather): the samples transposed into shared memory (row length 129,
+// conflict-free both ways) and the stage's twiddles padded to 8 per group.  Each stage's
+// partial sums are added into the running totals (two-level sum).
 // ---------------------------------------------------------------------------------------------
-constexpr int TD_TR = 64, TD_T = 64;
+constexpr int TD_TR = 128, TD_T = 32, TD_RL = TD_TR + 1, TD_NS = 3;
+
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, bool ok) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(tc::smem_u32(dst)), "l"(src),
+               "r"(ok ? 4 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, bool ok) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(tc::smem_u32(dst)), "l"(src),
+               "r"(ok ? 8 : 0)
+               : "memory");
+}
+
+size_t trace_dft_smem(int nf) {
+  const int nfp = 8 * ((nf + 7) / 8);
+  return (size_t)TD_NS * (TD_T * TD_RL * sizeof(float) + TD_T * nfp * sizeof(float2));
+}
 
 __global__ void __launch_bounds__(256)
     k_trace_dft(const float* __restrict__ resid, int ntr, int nt_d, const float2* __restrict__ tw,
                 int nf, int nrec, int ld, int s0, float2* __restrict__ Dh) {
-  __shared__ float R[TD_TR][TD_T + 1];
-  extern __shared__ float2 stw[];  // [TD_T][nf]
-  const int tid = threadIdx.x, m = tid & 63, g = tid >> 6;
+  extern __shared__ float4 td_sm[];
+  const int tid = threadIdx.x, lane = tid & 31, wg = tid >> 5;
+  const int nfp = blockDim.x >> 2;  // 8 per warp
+  float* Rb = reinterpret_cast<float*>(td_sm);       // [TD_NS][TD_T][TD_RL]
+  float2* Wb = reinterpret_cast<float2*>(Rb + TD_NS * TD_T * TD_RL);  // [TD_NS][TD_T][nfp]
   const int q0 = blockIdx.x * TD_TR;
-  float2 tot[NFMAX / 4];
-#pragma unroll
-  for (int j = 0; j < NFMAX / 4; ++j) tot[j] = make_float2(0.f, 0.f);
-  for (int t0 = 0; t0 < nt_d; t0 += TD_T) {
-#pragma unroll 4
-    for (int i = 0; i < (TD_TR * TD_T) / 256; ++i) {
-      const int e = tid + 256 * i;
-      const int r = e >> 6, c = e & 63;
-      const int q = q0 + r, t = t0 + c;
-      R[r][c] = (q < ntr && t < nt_d) ? resid[(long long)q * nt_d + t] : 0.f;
-    }
-    for (int e = tid; e < TD_T * nf; e += 256) {
-      const int t = t0 + e / nf;
-      stw[e] = t < nt_d ? tw[(long long)t0 * nf + e] : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-    float2 acc[NFMAX / 4];
-#pragma unroll
-    for (int j = 0; j < NFMAX / 4; ++j) acc[j] = make_float2(0.f, 0.f);
-    for (int tt = 0; tt < TD_T; ++tt) {
-      const float x = R[m][tt];
-#pragma unroll
-      for (int j = 0; j < NFMAX / 4; ++j) {
-        const int k = g + 4 * j;
-        if (k < nf) {
-          const float2 w = stw[tt * nf + k];
-          acc[j].x = fmaf(x, w.x, acc[j].x);
-          acc[j].y = fmaf(x, w.y, acc[j].y);
-        }
+  const int nst = (nt_d + TD_T - 1) / TD_T;
+  auto issue = [&](int s) {
+    if (s < nst) {
+      float* R = Rb + (s % TD_NS) * (TD_T * TD_RL);
+      float2* W = Wb + (s % TD_NS) * (TD_T * nfp);
+      const int t0 = s * TD_T;
+      // consecutive threads copy consecutive samples of one trace (coalesced)
+      for (int e = tid; e < TD_TR * TD_T; e += blockDim.x) {
+        const int tt = e & (TD_T - 1), r = e >> 5;
+        const int q = q0 + r, t = t0 + tt;
+        const bool ok = q < ntr && t < nt_d;
+        cp_async4(R + tt * TD_RL + r, ok ? resid + (long long)q * nt_d + t : resid, ok);
+      }
+      for (int e = tid; e < TD_T * nfp; e += blockDim.x) {
+        const int tt = e / nfp, k = e % nfp, t = t0 + tt;
+        const bool ok = t < nt_d && k < nf;
+        cp_async8(W + e, ok ? tw + (long long)t * nf + k : tw, ok);
       }
     }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  float2 tot[4][8];
 #pragma unroll
-    for (int j = 0; j < NFMAX / 4; ++j) {
-      tot[j].x += acc[j].x;
-      tot[j].y += acc[j].y;
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) tot[i][j] = make_float2(0.f, 0.f);
+  for (int s = 0; s < TD_NS - 1; ++s) issue(s);
+  for (int s = 0; s < nst; ++s) {
+    issue(s + TD_NS - 1);
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(TD_NS - 1) : "memory");
+    __syncthreads();
+    const float* R = Rb + (s % TD_NS) * (TD_T * TD_RL);
+    const float2* W = Wb + (s % TD_NS) * (TD_T * nfp);
+    float2 acc[4][8];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[i][j] = make_float2(0.f, 0.f);
+#pragma unroll 4
+    for (int tt = 0; tt < TD_T; ++tt) {
+      float x[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) x[i] = R[tt * TD_RL + lane + 32 * i];
+      const float4* wp = reinterpret_cast<const float4*>(W + tt * nfp + 8 * wg);
+      float2 w[8];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float4 v = wp[j];
+        w[2 * j] = make_float2(v.x, v.y);
+        w[2 * j + 1] = make_float2(v.z, v.w);
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          acc[i][j].x = fmaf(x[i], w[j].x, acc[i][j].x);
+          acc[i][j].y = fmaf(x[i], w[j].y, acc[i][j].y);
+        }
     }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        tot[i][j].x += acc[i][j].x;
+        tot[i][j].y += acc[i][j].y;
+      }
     __syncthreads();
   }
-  const int q = q0 + m;
-  if (q < ntr) {
-    const int s = q / nrec, r = q % nrec;
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 #pragma unroll
-    for (int j = 0; j < NFMAX / 4; ++j) {
-      const int k = g + 4 * j;
-      if (k < nf) Dh[((long long)k * nrec + r) * ld + s0 + s] = tot[j];
+  for (int i = 0; i < 4; ++i) {
+    const int q = q0 + lane + 32 * i;
+    if (q < ntr) {
+      const int s = q / nrec, r = q % nrec;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int k = 8 * wg + j;
+        if (k < nf) Dh[((long long)k * nrec + r) * ld + s0 + s] = tot[i][j];
+      }
     }
   }
 }
 
 cudaError_t launch_trace_dft(const float* resid, int ntr, int nt_d, const float2* tw, int nf,
                              int nrec, int ld, int s0, float2* Dh, cudaStream_t st) {
-  if (nf > NFMAX) return cudaErrorInvalidValue;
-  const size_t smem = sizeof(float2) * TD_T * nf;
-  if (smem + sizeof(float) * TD_TR * (TD_T + 1) > 48 * 1024) {
+  if (nf < 1 || nf > NFMAX) return cudaErrorInvalidValue;
+  const int groups = (nf + 7) / 8;
+  const size_t smem = trace_dft_smem(nf);
+  if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_trace_dft, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
   }
   count_launches(1);
-  k_trace_dft<<<(ntr + TD_TR - 1) / TD_TR, 256, smem, st>>>(resid, ntr, nt_d, tw, nf, nrec, ld, s0,
-                                                          Dh);
+  k_trace_dft<<<(ntr + TD_TR - 1) / TD_TR, 32 * groups, smem, st>>>(resid, ntr, nt_d, tw, nf, nrec,
+                                                                    ld, s0, Dh);
   return cudaGetLastError();
 }
 
@@ -180,9 +240,11 @@ cudaError_t launch_trsm(const float2* Lh, int n, int nf, float2* Dh, int ns, cud
 }
 
 // ---------------------------------------------------------------------------------------------
-// Synthesis: 64 traces x 128 samples per block.  The weighted solutions of the block's traces and
-// the twiddles of its time range sit in shared memory; thread (t, half) produces sample t of 32
-// traces.  Re(X e^{+i theta}) = Re X cos(theta) + Im X (-sin(theta)) with tw = e^{-i theta}.
+// Synthesis: 64 traces x 128 samples per block.  The weighted solutions of the block's traces
+// (X[k][trace]) and the twiddles of its time range (T[k][sample]) sit in shared memory; thread
+// (g, p) produces samples 4p .. 4p + 3 of traces 8g .. 8g + 7 (per frequency: two 16-byte
+// twiddle reads, four broadcast solution reads, 64 FMAs).
+// Re(X e^{+i theta}) = Re X cos(theta) + Im X (-sin(theta)) with tw = e^{-i theta}.
 // ---------------------------------------------------------------------------------------------
 constexpr int SY_TR = 64, SY_T = 128;
 
@@ -190,13 +252,13 @@ __global__ void __launch_bounds__(256)
     k_synth(const float2* __restrict__ Dh, int nrec, int ld, int s0, int nf,
             const float* __restrict__ w, const float2* __restrict__ tw, int nt_d,
             float* __restrict__ mult, int ntr) {
-  extern __shared__ float2 sm[];
-  float2* X = sm;                 // [SY_TR][nf]
-  float2* T = sm + SY_TR * nf;    // [nf][SY_T]
+  extern __shared__ float4 sm4[];
+  float2* X = reinterpret_cast<float2*>(sm4);  // [nf][SY_TR]
+  float2* T = X + SY_TR * nf;                  // [nf][SY_T]
   const int tid = threadIdx.x;
   const int q0 = blockIdx.y * SY_TR, t0 = blockIdx.x * SY_T;
   for (int e = tid; e < SY_TR * nf; e += 256) {
-    const int rr = e / nf, k = e % nf, q = q0 + rr;
+    const int k = e / SY_TR, rr = e % SY_TR, q = q0 + rr;
     float2 v = make_float2(0.f, 0.f);
     if (q < ntr) {
       v = Dh[((long long)k * nrec + q % nrec) * ld + s0 + q / nrec];
@@ -210,24 +272,43 @@ __global__ void __launch_bounds__(256)
     T[e] = t < nt_d ? tw[(long long)t * nf + k] : make_float2(0.f, 0.f);
   }
   __syncthreads();
-  const int tl = tid & (SY_T - 1), half = tid >> 7;
-  float acc[32];
+  const int p = tid & 31, g = tid >> 5;
+  float acc[8][4];
 #pragma unroll
-  for (int m = 0; m < 32; ++m) acc[m] = 0.f;
+  for (int m = 0; m < 8; ++m)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) acc[m][i] = 0.f;
   for (int k = 0; k < nf; ++k) {
-    const float2 c = T[k * SY_T + tl];
+    const float4* tp = reinterpret_cast<const float4*>(T + k * SY_T + 4 * p);
+    const float4 c01 = tp[0], c23 = tp[1];
+    const float2 c[4] = {make_float2(c01.x, c01.y), make_float2(c01.z, c01.w),
+                         make_float2(c23.x, c23.y), make_float2(c23.z, c23.w)};
+    const float4* xp = reinterpret_cast<const float4*>(X + k * SY_TR + 8 * g);
 #pragma unroll
-    for (int m = 0; m < 32; ++m) {
-      const float2 x = X[(half * 32 + m) * nf + k];
-      acc[m] = fmaf(x.x, c.x, fmaf(x.y, c.y, acc[m]));
+    for (int h = 0; h < 4; ++h) {
+      const float4 xv = xp[h];
+      const float2 x[2] = {make_float2(xv.x, xv.y), make_float2(xv.z, xv.w)};
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          acc[2 * h + u][i] = fmaf(x[u].x, c[i].x, fmaf(x[u].y, c[i].y, acc[2 * h + u][i]));
     }
   }
-  const int t = t0 + tl;
-  if (t < nt_d) {
+  const int tb = t0 + 4 * p;
+  const bool vec =
+      (nt_d & 3) == 0 && tb + 3 < nt_d && (reinterpret_cast<uintptr_t>(mult) & 15) == 0;
 #pragma unroll
-    for (int m = 0; m < 32; ++m) {
-      const int q = q0 + half * 32 + m;
-      if (q < ntr) mult[(long long)q * nt_d + t] = acc[m];
+  for (int m = 0; m < 8; ++m) {
+    const int q = q0 + 8 * g + m;
+    if (q >= ntr) break;
+    float* out = mult + (long long)q * nt_d + tb;
+    if (vec) {
+      *reinterpret_cast<float4*>(out) = make_float4(acc[m][0], acc[m][1], acc[m][2], acc[m][3]);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (tb + i < nt_d) out[i] = acc[m][i];
     }
   }
 }
@@ -407,19 +488,91 @@ __global__ void __launch_bounds__(32 * TS_W)
   }
 }
 
-cudaError_t launch_resid64(const float2* Qh, int n, int nf, const float2* Xh, const float2* Dh,
-                           int ns, float2* Rh, cudaStream_t st) {
+// ---------------------------------------------------------------------------------------------
+// The same residual with FP64-class accuracy from FP32 arithmetic: the compensated dot product
+// Dot2 of Ogita, Rump and Oishi ("Accurate sum and dot product", SIAM J. Sci. Comput. 26, 2005).
+// Each product a*b is split exactly into p + e (p = fl(a*b), e = fma(a, b, -p)); the p are summed
+// with Knuth's TwoSum, whose rounding errors are gathered with the e in a second FP32 word, so
+// the result is as accurate as if summed in twice the working precision (about 2^-48 relative to
+// sum |q x|) and then rounded.  The GB300 issues FP64 at a small fraction of the FP32 rate, so this
+// is the fast route to a residual whose FP32 rounding matches the FP64 one.  Every step uses the
+// _rn intrinsics so that no product is contracted into an FMA.  Layout as k_resid64; each warp
+// takes two rows per pass so that each solution read serves both.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ void dot2_add(float& s, float& c, float a, float b) {
+  const float p = __fmul_rn(a, b);
+  const float e = __fmaf_rn(a, b, -p);
+  const float t = __fadd_rn(s, p);
+  const float bp = __fsub_rn(t, s);
+  const float q = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(q, e));
+}
+
+__global__ void __launch_bounds__(32 * TS_W)
+    k_resid_dot2(const float2* __restrict__ Qh, int n, const float2* __restrict__ Xh,
+                 const float2* __restrict__ Dh, int ns, float2* __restrict__ Rh) {
+  extern __shared__ float2 Xs[];  // [n][32]
+  const int k = blockIdx.y;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int col = blockIdx.x * 32 + lane;
+  const bool valid = col < ns;
+  const float2* Q = Qh + (long long)k * n * n;
+  const long long off = (long long)k * n * ns;
+  for (int i = warp; i < n; i += TS_W)
+    Xs[i * 32 + lane] = valid ? Xh[off + (long long)i * ns + col] : make_float2(0.f, 0.f);
+  __syncthreads();
+  const int rows = (n + gridDim.z - 1) / gridDim.z;
+  const int i0 = blockIdx.z * rows, i1 = min(n, i0 + rows);
+  for (int i = i0 + 2 * warp; i < i1; i += 2 * TS_W) {
+    const bool two = i + 1 < i1;
+    const float2* qa = Q + (long long)i * n;
+    const float2* qb = Q + (long long)(two ? i + 1 : i) * n;
+    float2 da = make_float2(0.f, 0.f), db = make_float2(0.f, 0.f);
+    if (valid) {
+      da = Dh[off + (long long)i * ns + col];
+      if (two) db = Dh[off + (long long)(i + 1) * ns + col];
+    }
+    // R = D - Q X: real part adds (-q.x) x.x and q.y x.y, imaginary part (-q.x) x.y and (-q.y) x.x
+    float sar = da.x, car = 0.f, sai = da.y, cai = 0.f;
+    float sbr = db.x, cbr = 0.f, sbi = db.y, cbi = 0.f;
+    for (int j = 0; j < n; ++j) {
+      const float2 x = Xs[j * 32 + lane];
+      const float2 a = __ldg(qa + j), b = __ldg(qb + j);
+      dot2_add(sar, car, -a.x, x.x);
+      dot2_add(sar, car, a.y, x.y);
+      dot2_add(sai, cai, -a.x, x.y);
+      dot2_add(sai, cai, -a.y, x.x);
+      dot2_add(sbr, cbr, -b.x, x.x);
+      dot2_add(sbr, cbr, b.y, x.y);
+      dot2_add(sbi, cbi, -b.x, x.y);
+      dot2_add(sbi, cbi, -b.y, x.x);
+    }
+    if (valid) {
+      Rh[off + (long long)i * ns + col] = make_float2(__fadd_rn(sar, car), __fadd_rn(sai, cai));
+      if (two)
+        Rh[off + (long long)(i + 1) * ns + col] = make_float2(__fadd_rn(sbr, cbr), __fadd_rn(sbi, cbi));
+    }
+  }
+}
+
+cudaError_t launch_resid(const float2* Qh, int n, int nf, const float2* Xh, const float2* Dh,
+                         int ns, float2* Rh, bool fp64, cudaStream_t st) {
   const size_t smem = sizeof(float2) * 32 * (size_t)n;
   if (smem > 48 * 1024) {
-    cudaError_t e =
-        cudaFuncSetAttribute(k_resid64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = fp64 ? cudaFuncSetAttribute(k_resid64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                         : cudaFuncSetAttribute(k_resid_dot2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
   count_launches(1);
   // enough blocks for every SM: split the rows of each (frequency, source group)
   const int blocks = ((ns + 31) / 32) * nf;
   const int groups = std::max(1, std::min((n + TS_W - 1) / TS_W, (4 * 152 + blocks - 1) / blocks));
-  k_resid64<<<dim3((ns + 31) / 32, nf, groups), 32 * TS_W, smem, st>>>(Qh, n, Xh, Dh, ns, Rh);
+  const dim3 grid((ns + 31) / 32, nf, groups);
+  if (fp64)
+    k_resid64<<<grid, 32 * TS_W, smem, st>>>(Qh, n, Xh, Dh, ns, Rh);
+  else
+    k_resid_dot2<<<grid, 32 * TS_W, smem, st>>>(Qh, n, Xh, Dh, ns, Rh);
   return cudaGetLastError();
 }
 

@@ -289,7 +289,7 @@ egh_status ensure_green_buffers(egh_ctx* ctx) {
   if ((s = dalloc(ctx, (void**)&ctx->gh, (size_t)ctx->nrec * ctx->nf * 2 * (size_t)L.G * sizeof(float),
                   "green transforms")))
     return s;
-  if (ctx->prec == EGH_PREC_MIXED &&
+  if (prec_mixed(ctx->prec) &&
       (s = dalloc(ctx, (void**)&ctx->ghb,
                   (size_t)ctx->nrec * ctx->nf * 4 * (size_t)L.G * sizeof(__nv_bfloat16),
                   "bf16 transforms")))
@@ -393,7 +393,7 @@ egh_status egh_create(const egh_config* cfg, egh_ctx** out) {
       c.fd_rows != 32)
     return fail(nullptr, EGH_EINVAL, "fd_rows must be 0, 12, 16, 20, 24 or 32");
   if (c.batch_receivers > 32) return fail(nullptr, EGH_EINVAL, "batch_receivers must be <= 32");
-  if (c.precision != EGH_PREC_FP32 && c.precision != EGH_PREC_MIXED)
+  if (c.precision != EGH_PREC_FP32 && !prec_mixed(c.precision))
     return fail(nullptr, EGH_EINVAL, "unknown precision");
   if (c.batch_receivers < 0 || c.gram_splits < 0)
     return fail(nullptr, EGH_EINVAL, "batch_receivers and gram_splits must be >= 0");
@@ -463,7 +463,7 @@ egh_status egh_create(const egh_config* cfg, egh_ctx** out) {
         "gram");
   ALLOC(ctx->Qh, (size_t)c.nfreq * c.nrec * c.nrec * sizeof(float2), "Qh");
   ALLOC(ctx->Lh, (size_t)c.nfreq * c.nrec * c.nrec * sizeof(float2), "Lh");
-  if (ctx->prec == EGH_PREC_MIXED)
+  if (prec_mixed(ctx->prec))
     ALLOC(ctx->Wh, (size_t)c.nfreq * c.nrec * c.nrec * sizeof(float2), "inverse factors");
   ALLOC(ctx->w_dev, (size_t)c.nfreq * sizeof(float), "weights");
   ALLOC(ctx->rec_pts, (size_t)c.nrec * sizeof(int), "receivers");
@@ -527,7 +527,7 @@ egh_status egh_create(const egh_config* cfg, egh_ctx** out) {
   ctx->st.pitch = L.PX;
   ctx->st.batch_receivers = ctx->B;
   ctx->st.dft_chunk = ctx->K;
-  ctx->st.gram_splits = ctx->prec == EGH_PREC_MIXED ? ctx->splits_tc : ctx->splits;
+  ctx->st.gram_splits = prec_mixed(ctx->prec) ? ctx->splits_tc : ctx->splits;
   *out = ctx;
   return EGH_OK;
 }
@@ -661,7 +661,7 @@ egh_status egh_hessian(egh_ctx* ctx, egh_mu_mode mode, double mu_param, double* 
   if (mode != EGH_MU_ABS && mode != EGH_MU_REL_MEANDIAG && mode != EGH_MU_REL_MAXEIG)
     return fail(ctx, EGH_EINVAL, "unknown mu mode");
   CK(cudaEventRecord(ctx->ev[2], stream));
-  if (ctx->prec == EGH_PREC_MIXED) {
+  if (prec_mixed(ctx->prec)) {
     CK(launch_gram_tc(ctx->tmap_ghb, ctx->nrec, ctx->nf, ctx->L.G, ctx->splits_tc, ctx->part,
                       ctx->d_err, stream));
     CK(launch_gram_tc_finish(ctx->part, ctx->nrec, ctx->nf, ctx->splits_tc, ctx->Qh, stream));
@@ -714,7 +714,7 @@ egh_status egh_factor(egh_ctx* ctx, int32_t* bad_freq, void* stream_) {
   CK(cudaEventRecord(ctx->ev[4], stream));
   CK(cudaMemcpyAsync(ctx->Lh, ctx->Qh, bytes, cudaMemcpyDeviceToDevice, stream));
   CK(launch_potrf(ctx->Lh, ctx->nrec, ctx->nf, ctx->status, stream,
-                  ctx->prec == EGH_PREC_MIXED ? 1 : 0));
+                  prec_mixed(ctx->prec) ? 1 : 0));
   if (ctx->Wh) CK(launch_trtri(ctx->Lh, ctx->nrec, ctx->nf, ctx->Wh, stream));
   CK(cudaEventRecord(ctx->ev[5], stream));
   ctx->ev_rec[2] = true;
@@ -775,7 +775,7 @@ static egh_status deblur_common(egh_ctx* ctx, const float* resid, int32_t ns, in
   CK(cudaEventRecord(ctx->ev[6], stream));
   CK(launch_trace_dft(din, (int)ntr, nt_d, ctx->tw, ctx->nf, ctx->nrec, ns, 0, D, stream));
   const size_t dbytes = (size_t)ctx->nf * ntr * sizeof(float2);
-  if (ctx->prec == EGH_PREC_MIXED) {
+  if (prec_mixed(ctx->prec)) {
     // one step of iterative refinement: residual in FP64, correction solved with the FP32 factors
     if ((s = ensure_buf(ctx, (void**)&ctx->Dr, &ctx->Dr_cap, dbytes, stream, "refinement rhs")))
       return s;
@@ -783,11 +783,12 @@ static egh_status deblur_common(egh_ctx* ctx, const float* resid, int32_t ns, in
       return s;
     CK(cudaMemcpyAsync(ctx->Dr, D, dbytes, cudaMemcpyDeviceToDevice, stream));
   }
-  if (ctx->prec == EGH_PREC_MIXED) {
+  if (prec_mixed(ctx->prec)) {
     // X = W^H W D (products with the explicit inverse factor), residual D - Q X in FP64, the
     // correction solved the same way
     CK(launch_inverse_solve(ctx->Wh, ctx->nrec, ctx->nf, D, ctx->Rr, D, ns, stream));
-    CK(launch_resid64(ctx->Qh, ctx->nrec, ctx->nf, D, ctx->Dr, ns, ctx->Rr, stream));
+    CK(launch_resid(ctx->Qh, ctx->nrec, ctx->nf, D, ctx->Dr, ns, ctx->Rr,
+                    ctx->prec == EGH_PREC_MIXED_FP64, stream));
     CK(launch_inverse_solve(ctx->Wh, ctx->nrec, ctx->nf, ctx->Rr, ctx->Dr, ctx->Rr, ns, stream));
     CK(launch_add_correction(D, ctx->Rr, (long long)ctx->nf * ntr, stream));
   } else {
@@ -994,7 +995,7 @@ egh_status egh_batch_create(egh_ctx* const* ctxs, int32_t n, egh_batch** out) {
     b->nmax = std::max(b->nmax, c->nrec);
   }
   b->dev = ctxs[0]->dev;
-  b->piv64 = ctxs[0]->prec == EGH_PREC_MIXED ? 1 : 0;
+  b->piv64 = prec_mixed(ctxs[0]->prec) ? 1 : 0;
   cudaSetDevice(b->dev);
   int off = 0;
   for (egh_ctx* c : b->ctxs) off += c->nf;

@@ -17,6 +17,8 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include "egh.h"
+
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -122,8 +124,10 @@ cudaError_t launch_trsm(const float2* Lh, int n, int nf, float2* Dh, int ns, cud
 cudaError_t launch_trtri(const float2* Lh, int n, int nf, float2* Wh, cudaStream_t st);
 cudaError_t launch_inverse_solve(const float2* Wh, int n, int nf, const float2* D, float2* Y,
                                  float2* X, int ld, cudaStream_t st);
-cudaError_t launch_resid64(const float2* Qh, int n, int nf, const float2* Xh, const float2* Dh,
-                           int ns, float2* Rh, cudaStream_t st);
+// refinement residual R = D - Q X: FP64 arithmetic (fp64) or the compensated FP32 dot product
+cudaError_t launch_resid(const float2* Qh, int n, int nf, const float2* Xh, const float2* Dh,
+                         int ns, float2* Rh, bool fp64, cudaStream_t st);
+inline bool prec_mixed(int prec) { return prec == EGH_PREC_MIXED || prec == EGH_PREC_MIXED_FP64; }
 cudaError_t launch_add_correction(float2* X, const float2* R, long long m, cudaStream_t st);
 cudaError_t launch_synth(const float2* Dh, int nrec, int ns, int ld, int s0, int nf, const float* w,
                          const float2* tw, int nt_d, float* mult, cudaStream_t st);

@@ -144,7 +144,7 @@ egh_status fail(Server* sv, egh_status s, const std::string& msg) {
 }
 
 size_t d_bytes(const Server* sv, const HSet& h, int ns_total) {
-  return (size_t)h.nf * h.nrec * ns_total * sizeof(float2) * (sv->prec == EGH_PREC_MIXED ? 3 : 1);
+  return (size_t)h.nf * h.nrec * ns_total * sizeof(float2) * (prec_mixed(sv->prec) ? 3 : 1);
 }
 
 size_t trace_bytes(const HSet& h, int ns, int nt_d) {
@@ -193,12 +193,13 @@ cudaError_t run_batch(Server* sv, Batch* b, const HSet& h) {
       return e;
     s0 += r->ns;
   }
-  if (sv->prec == EGH_PREC_MIXED) {
+  if (prec_mixed(sv->prec)) {
     float2* Dr = D + dsz;
     float2* R = D + 2 * dsz;
     if ((e = cudaMemcpyAsync(Dr, D, dsz * sizeof(float2), cudaMemcpyDeviceToDevice, st))) return e;
     if ((e = launch_inverse_solve(h.Wh, h.nrec, h.nf, D, R, D, ld, st))) return e;
-    if ((e = launch_resid64(h.Qh, h.nrec, h.nf, D, Dr, ld, R, st))) return e;
+    if ((e = launch_resid(h.Qh, h.nrec, h.nf, D, Dr, ld, R, sv->prec == EGH_PREC_MIXED_FP64, st)))
+      return e;
     if ((e = launch_inverse_solve(h.Wh, h.nrec, h.nf, R, Dr, R, ld, st))) return e;
     if ((e = launch_add_correction(D, R, (long long)dsz, st))) return e;
   } else {
@@ -337,7 +338,7 @@ egh_status egh_server_create(const egh_server_config* cfg, egh_server** out) {
   if (cfg->hbm_budget_bytes < (1 << 20)) return fail(nullptr, EGH_EINVAL, "hbm_budget_bytes must be >= 1 MiB");
   if (cfg->slots < 1 || cfg->slots > 16) return fail(nullptr, EGH_EINVAL, "slots must be in 1..16");
   if (cfg->max_batch_sources < 1) return fail(nullptr, EGH_EINVAL, "max_batch_sources must be >= 1");
-  if (cfg->precision != EGH_PREC_FP32 && cfg->precision != EGH_PREC_MIXED)
+  if (cfg->precision != EGH_PREC_FP32 && !prec_mixed(cfg->precision))
     return fail(nullptr, EGH_EINVAL, "unknown precision");
   egh_server* sv = new (std::nothrow) egh_server();
   if (!sv) return fail(nullptr, EGH_ENOMEM, "host allocation failed");
@@ -398,8 +399,8 @@ egh_status egh_server_add_set(egh_server* sv, int32_t nrec, int32_t nfreq, const
   if (!e) e = cudaMemcpy(h.Lh, Q_host, qn * sizeof(float2), cudaMemcpyHostToDevice);
   if (!e) e = cudaMemcpy(h.tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice);
   if (!e) e = cudaMemcpy(h.w, w.data(), w.size() * sizeof(float), cudaMemcpyHostToDevice);
-  if (!e) e = launch_potrf(h.Lh, nrec, nfreq, status, st, sv->prec == EGH_PREC_MIXED ? 1 : 0);
-  if (!e && sv->prec == EGH_PREC_MIXED) {
+  if (!e) e = launch_potrf(h.Lh, nrec, nfreq, status, st, prec_mixed(sv->prec) ? 1 : 0);
+  if (!e && prec_mixed(sv->prec)) {
     e = cudaMalloc(&h.Wh, qn * sizeof(float2));
     if (!e) e = launch_trtri(h.Lh, nrec, nfreq, h.Wh, st);
   }

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libegh.so")
 
 EGH_OK, EGH_EINVAL, EGH_ENOMEM, EGH_ECUDA, EGH_ENOTPD, EGH_ESTATE, EGH_ETIMEOUT = range(7)
 EGH_MU_ABS, EGH_MU_REL_MEANDIAG, EGH_MU_REL_MAXEIG = range(3)
-EGH_PREC_FP32, EGH_PREC_MIXED = range(2)
+EGH_PREC_FP32, EGH_PREC_MIXED, EGH_PREC_MIXED_FP64 = range(3)
 
 _i32p = ctypes.POINTER(ctypes.c_int32)
 _f64p = ctypes.POINTER(ctypes.c_double)

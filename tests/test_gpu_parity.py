@@ -153,7 +153,8 @@ def test_mixed_precision_small(small):
 def test_precision_form_small(small):
     """Precision form of the 101x101 case, per frequency against the FP64 oracle: Hessians and
     frequency-domain solutions of the FP32 path and of the mixed path (bf16x3 tensor-core Gram,
-    FP64 pivots, one refinement step with FP64 residuals), and the backward error of each
+    FP64 pivots, one refinement step whose residual has FP64 accuracy, from compensated FP32
+    arithmetic or from FP64 arithmetic), and the backward error of each
     path's solves with respect to its own Hessian (refinement takes it to the FP32 rounding of
     the solution)."""
     torch = _torch()
@@ -164,7 +165,8 @@ def test_precision_form_small(small):
     _, Xo, Do = oracle.deblur(o["L"], r32.astype(np.float64), c.freqs, c.dt, nt_ref=c.nt)
     nf, nr, ns = c.freqs.size, c.rec_ix.size, r32.shape[0]
     bw, table = {}, []
-    for prec in (egh.EGH_PREC_FP32, egh.EGH_PREC_MIXED):
+    Xs = {}
+    for prec in (egh.EGH_PREC_FP32, egh.EGH_PREC_MIXED, egh.EGH_PREC_MIXED_FP64):
         with _ctx(c, precision=prec) as ctx:
             ctx.green(torch.from_numpy(np.float32(c.vel_start)).cuda())
             ctx.hessian(egh.EGH_MU_REL_MEANDIAG, c.mu_alpha)
@@ -173,6 +175,7 @@ def test_precision_form_small(small):
             X = torch.empty((nf, nr, ns), dtype=torch.complex64, device="cuda")
             ctx.deblur_freq(torch.from_numpy(r32).cuda(), X)
             Xh = X.cpu().numpy().astype(np.complex128)
+        Xs[prec] = Xh
         bw[prec] = []
         for k in range(nf):
             eq, ex = rel(Q[k], o["Q"][k]), rel(Xh[k], Xo[k])
@@ -184,8 +187,14 @@ def test_precision_form_small(small):
             assert ex <= MULT_TOL, (prec, k)
     for row in table:
         print("precision %d  f %.1f Hz  Q rel %.2e  X rel %.2e  backward %.2e" % row)
-    assert max(bw[egh.EGH_PREC_MIXED]) <= max(bw[egh.EGH_PREC_FP32])
-    assert max(bw[egh.EGH_PREC_MIXED]) <= 1e-6
+    for prec in (egh.EGH_PREC_MIXED, egh.EGH_PREC_MIXED_FP64):
+        assert max(bw[prec]) <= max(bw[egh.EGH_PREC_FP32])
+        assert max(bw[prec]) <= 1e-6
+    # the compensated FP32 residual and the FP64 one round to the same refinement (up to a last
+    # bit here and there): the two mixed solutions agree far inside the FP32 rounding of X
+    for k in range(nf):
+        d = rel(Xs[egh.EGH_PREC_MIXED][k], Xs[egh.EGH_PREC_MIXED_FP64][k])
+        assert d <= 1e-6, (k, d)
 
 
 def test_factor_parity_small(small):
