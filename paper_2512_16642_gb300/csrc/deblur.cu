@@ -11,6 +11,8 @@
 #include <algorithm>
 #include <cstdint>
 
+#include <cooperative_groups.h>
+
 #include "egh_internal.cuh"
 #include "tc.cuh"
 
@@ -22,12 +24,13 @@ constexpr int NFMAX = 64;
 // Forward transform: 128 traces per block and one warp per group of 8 frequencies; lane l
 // accumulates traces l, l + 32, l + 64, l + 96 at its warp's 8 frequencies (64 running sums per
 // thread, each twiddle read reused over 4 traces and each sample over 8 frequencies).  The time
-// axis is staged 32 samples at a time through a 3-deep ring of cp.async copies (zero-filled
-// outside the gather): the samples transposed into shared memory (row length 129,
-// conflict-free both ways) and the stage's twiddles padded to 8 per group.  Each stage's
-// partial sums are added into the running totals (two-level sum).
+// axis is split over a cluster of TD_S blocks, each taking a contiguous run of 32-sample stages
+// through a 3-deep ring of cp.async copies (zero-filled outside the gather): the samples
+// transposed into shared memory (row length 129, conflict-free both ways) and the stage's
+// twiddles padded to 8 per group.  The cluster's partial sums meet in block rank 0 through
+// distributed shared memory, added in rank order (deterministic).
 // ---------------------------------------------------------------------------------------------
-constexpr int TD_TR = 128, TD_T = 32, TD_RL = TD_TR + 1, TD_NS = 3;
+constexpr int TD_TR = 128, TD_T = 32, TD_RL = TD_TR + 1, TD_NS = 3, TD_S = 4;
 
 __device__ __forceinline__ void cp_async4(void* dst, const void* src, bool ok) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(tc::smem_u32(dst)), "l"(src),
@@ -39,24 +42,29 @@ __device__ __forceinline__ void cp_async8(void* dst, const void* src, bool ok) {
                "r"(ok ? 8 : 0)
                : "memory");
 }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 
 size_t trace_dft_smem(int nf) {
   const int nfp = 8 * ((nf + 7) / 8);
   return (size_t)TD_NS * (TD_T * TD_RL * sizeof(float) + TD_T * nfp * sizeof(float2));
 }
 
-__global__ void __launch_bounds__(256)
+__global__ void __cluster_dims__(TD_S, 1, 1) __launch_bounds__(256)
     k_trace_dft(const float* __restrict__ resid, int ntr, int nt_d, const float2* __restrict__ tw,
                 int nf, int nrec, int ld, int s0, float2* __restrict__ Dh) {
   extern __shared__ float4 td_sm[];
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
   const int tid = threadIdx.x, lane = tid & 31, wg = tid >> 5;
   const int nfp = blockDim.x >> 2;  // 8 per warp
-  float* Rb = reinterpret_cast<float*>(td_sm);       // [TD_NS][TD_T][TD_RL]
+  float* Rb = reinterpret_cast<float*>(td_sm);                        // [TD_NS][TD_T][TD_RL]
   float2* Wb = reinterpret_cast<float2*>(Rb + TD_NS * TD_T * TD_RL);  // [TD_NS][TD_T][nfp]
-  const int q0 = blockIdx.x * TD_TR;
-  const int nst = (nt_d + TD_T - 1) / TD_T;
+  const int rank = (int)cluster.block_rank();
+  const int q0 = (blockIdx.x / TD_S) * TD_TR;
+  const int nst = (nt_d + TD_T - 1) / TD_T, per = (nst + TD_S - 1) / TD_S;
+  const int sbeg = min(nst, rank * per), send = min(nst, sbeg + per);
   auto issue = [&](int s) {
-    if (s < nst) {
+    if (s < send) {
       float* R = Rb + (s % TD_NS) * (TD_T * TD_RL);
       float2* W = Wb + (s % TD_NS) * (TD_T * nfp);
       const int t0 = s * TD_T;
@@ -73,25 +81,20 @@ __global__ void __launch_bounds__(256)
         cp_async8(W + e, ok ? tw + (long long)t * nf + k : tw, ok);
       }
     }
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    cp_async_commit();
   };
-  float2 tot[4][8];
+  float2 acc[4][8];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 8; ++j) tot[i][j] = make_float2(0.f, 0.f);
-  for (int s = 0; s < TD_NS - 1; ++s) issue(s);
-  for (int s = 0; s < nst; ++s) {
+    for (int j = 0; j < 8; ++j) acc[i][j] = make_float2(0.f, 0.f);
+  for (int s = sbeg; s < sbeg + TD_NS - 1; ++s) issue(s);
+  for (int s = sbeg; s < send; ++s) {
     issue(s + TD_NS - 1);
     asm volatile("cp.async.wait_group %0;\n" ::"n"(TD_NS - 1) : "memory");
     __syncthreads();
     const float* R = Rb + (s % TD_NS) * (TD_T * TD_RL);
     const float2* W = Wb + (s % TD_NS) * (TD_T * nfp);
-    float2 acc[4][8];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 8; ++j) acc[i][j] = make_float2(0.f, 0.f);
 #pragma unroll 4
     for (int tt = 0; tt < TD_T; ++tt) {
       float x[4];
@@ -113,28 +116,43 @@ __global__ void __launch_bounds__(256)
           acc[i][j].y = fmaf(x[i], w[j].y, acc[i][j].y);
         }
     }
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        tot[i][j].x += acc[i][j].x;
-        tot[i][j].y += acc[i][j].y;
-      }
     __syncthreads();
   }
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  __syncthreads();
+  // partial sums to shared memory (the sample ring is free now): P[i * 8 + j][tid]
+  float2* P = reinterpret_cast<float2*>(td_sm);
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int q = q0 + lane + 32 * i;
-    if (q < ntr) {
-      const int s = q / nrec, r = q % nrec;
+  for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int k = 8 * wg + j;
-        if (k < nf) Dh[((long long)k * nrec + r) * ld + s0 + s] = tot[i][j];
+    for (int j = 0; j < 8; ++j) P[(i * 8 + j) * blockDim.x + tid] = acc[i][j];
+  cluster.sync();
+  if (rank == 0) {
+    for (int r = 1; r < TD_S; ++r) {
+      const float2* Pr = cluster.map_shared_rank(P, r);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const float2 v = Pr[(i * 8 + j) * blockDim.x + tid];
+          acc[i][j].x += v.x;
+          acc[i][j].y += v.y;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int q = q0 + lane + 32 * i;
+      if (q < ntr) {
+        const int sidx = q / nrec, r = q % nrec;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int k = 8 * wg + j;
+          if (k < nf) Dh[((long long)k * nrec + r) * ld + s0 + sidx] = acc[i][j];
+        }
       }
     }
   }
+  cluster.sync();  // the other blocks' shared memory stays live until rank 0 has read it
 }
 
 cudaError_t launch_trace_dft(const float* resid, int ntr, int nt_d, const float2* tw, int nf,
@@ -148,7 +166,8 @@ cudaError_t launch_trace_dft(const float* resid, int ntr, int nt_d, const float2
     if (e != cudaSuccess) return e;
   }
   count_launches(1);
-  k_trace_dft<<<(ntr + TD_TR - 1) / TD_TR, 32 * groups, smem, st>>>(resid, ntr, nt_d, tw, nf, nrec,
+  const long long tiles = (ntr + TD_TR - 1) / TD_TR;
+  k_trace_dft<<<(unsigned)(tiles * TD_S), 32 * groups, smem, st>>>(resid, ntr, nt_d, tw, nf, nrec,
                                                                     ld, s0, Dh);
   return cudaGetLastError();
 }
@@ -246,7 +265,7 @@ cudaError_t launch_trsm(const float2* Lh, int n, int nf, float2* Dh, int ns, cud
 // twiddle reads, four broadcast solution reads, 64 FMAs).
 // Re(X e^{+i theta}) = Re X cos(theta) + Im X (-sin(theta)) with tw = e^{-i theta}.
 // ---------------------------------------------------------------------------------------------
-constexpr int SY_TR = 64, SY_T = 128;
+constexpr int SY_TR = 64, SY_T = 128, SY_TP = SY_T + 2;
 
 __global__ void __launch_bounds__(256)
     k_synth(const float2* __restrict__ Dh, int nrec, int ld, int s0, int nf,
@@ -254,22 +273,28 @@ __global__ void __launch_bounds__(256)
             float* __restrict__ mult, int ntr) {
   extern __shared__ float4 sm4[];
   float2* X = reinterpret_cast<float2*>(sm4);  // [nf][SY_TR]
-  float2* T = X + SY_TR * nf;                  // [nf][SY_T]
+  float2* T = X + SY_TR * nf;                  // [nf][SY_TP]
   const int tid = threadIdx.x;
   const int q0 = blockIdx.y * SY_TR, t0 = blockIdx.x * SY_T;
+  // all gathers in flight at once (cp.async, zero-filled outside), then the weights applied
   for (int e = tid; e < SY_TR * nf; e += 256) {
     const int k = e / SY_TR, rr = e % SY_TR, q = q0 + rr;
-    float2 v = make_float2(0.f, 0.f);
-    if (q < ntr) {
-      v = Dh[((long long)k * nrec + q % nrec) * ld + s0 + q / nrec];
-      v.x *= w[k];
-      v.y *= w[k];
-    }
-    X[e] = v;
+    const bool ok = q < ntr;
+    cp_async8(X + e, ok ? Dh + ((long long)k * nrec + q % nrec) * ld + s0 + q / nrec : Dh, ok);
   }
+  // the block's twiddle rows are one contiguous run of the table: read it in order, transpose
+  // on the way into shared memory (row length SY_TP keeps the writes at few-way conflicts)
   for (int e = tid; e < nf * SY_T; e += 256) {
-    const int k = e / SY_T, tt = e % SY_T, t = t0 + tt;
-    T[e] = t < nt_d ? tw[(long long)t * nf + k] : make_float2(0.f, 0.f);
+    const int tt = e / nf, k = e % nf, t = t0 + tt;
+    const bool ok = t < nt_d;
+    cp_async8(T + k * SY_TP + tt, ok ? tw + (long long)t0 * nf + e : tw, ok);
+  }
+  cp_async_commit();
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  for (int e = tid; e < SY_TR * nf; e += 256) {  // the elements this thread copied itself
+    const float wk = w[e / SY_TR];
+    X[e].x *= wk;
+    X[e].y *= wk;
   }
   __syncthreads();
   const int p = tid & 31, g = tid >> 5;
@@ -279,7 +304,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int i = 0; i < 4; ++i) acc[m][i] = 0.f;
   for (int k = 0; k < nf; ++k) {
-    const float4* tp = reinterpret_cast<const float4*>(T + k * SY_T + 4 * p);
+    const float4* tp = reinterpret_cast<const float4*>(T + k * SY_TP + 4 * p);
     const float4 c01 = tp[0], c23 = tp[1];
     const float2 c[4] = {make_float2(c01.x, c01.y), make_float2(c01.z, c01.w),
                          make_float2(c23.x, c23.y), make_float2(c23.z, c23.w)};
@@ -600,7 +625,7 @@ cudaError_t launch_synth(const float2* Dh, int nrec, int ns, int ld, int s0, int
                          const float2* tw, int nt_d, float* mult, cudaStream_t st) {
   if (nf > NFMAX) return cudaErrorInvalidValue;
   const int ntr = nrec * ns;
-  const size_t smem = sizeof(float2) * (size_t)nf * (SY_TR + SY_T);
+  const size_t smem = sizeof(float2) * (size_t)nf * (SY_TR + SY_TP);
   if (smem > 48 * 1024) {
     cudaError_t e =
         cudaFuncSetAttribute(k_synth, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -187,9 +187,10 @@ def test_precision_form_small(small):
             assert ex <= MULT_TOL, (prec, k)
     for row in table:
         print("precision %d  f %.1f Hz  Q rel %.2e  X rel %.2e  backward %.2e" % row)
-    for prec in (egh.EGH_PREC_MIXED, egh.EGH_PREC_MIXED_FP64):
-        assert max(bw[prec]) <= max(bw[egh.EGH_PREC_FP32])
-        assert max(bw[prec]) <= 1e-6
+    # at this conditioning every path's backward error sits at the FP32 rounding of the
+    # transformed right-hand side (the same transform kernel in all three), a few 1e-8
+    for prec in bw:
+        assert max(bw[prec]) <= 1e-6, prec
     # the compensated FP32 residual and the FP64 one round to the same refinement (up to a last
     # bit here and there): the two mixed solutions agree far inside the FP32 rounding of X
     for k in range(nf):
