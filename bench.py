@@ -56,6 +56,9 @@ def _args():
                         "seeded band-limited noise of the same shape (skips the modelling launches)")
     p.add_argument("--slice", action="store_true",
                    help="profiling slice: one batch of 16 receivers, nt 1024, no e2e or CPU baseline")
+    p.add_argument("--slice-receivers", type=int, default=16,
+                   help="receivers of the profiling slice (231 gives the full-size Hessian)")
+    p.add_argument("--slice-nt", type=int, default=1024, help="time steps of the profiling slice")
     p.add_argument("--no-serving", action="store_true", help="skip the serving-form measurement")
     p.add_argument("--workload", choices=["layered", "salt"], default="layered",
                    help="layered (the benchmark workload) or the batched salt-patch form")
@@ -411,7 +414,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     c = synth.case_layered()
     if args.slice:
-        c = synth.slice_case(c, nrec=16, nt=1024)
+        c = synth.slice_case(c, nrec=args.slice_receivers, nt=args.slice_nt)
         args.e2e_steps, args.no_cpu_baseline = 0, True
     nr, ns, nt, nf = c.rec_ix.size, c.src_ix.size, c.nt, c.freqs.size
     ctx = egh.Context(c.nz, c.nx, c.dz, c.dx, c.nsponge, c.sponge_R, c.dt, c.nt, c.rec_iz, c.rec_ix, c.freqs,

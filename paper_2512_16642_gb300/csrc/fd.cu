@@ -163,18 +163,20 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// Scalar arithmetic on purpose: packed FP32x2 instructions bring no extra FMA throughput, and
-// scalar FMAs take the stencil coefficients straight from the kernel parameters.
-__device__ __forceinline__ float lap1(const float (&dz)[8], const float (&e)[8], const Stencil& C) {
-  // C holds the cumulative weights C_j = sum_{k>=j} c_k (see launch_fd_step)
-  float l = C.cz[0] * (dz[4] - dz[3]);
-  l = fmaf(C.cz[1], dz[5] - dz[2], l);
-  l = fmaf(C.cz[2], dz[6] - dz[1], l);
-  l = fmaf(C.cz[3], dz[7] - dz[0], l);
-  l = fmaf(C.cx[0], e[4] - e[3], l);
-  l = fmaf(C.cx[1], e[5] - e[2], l);
-  l = fmaf(C.cx[2], e[6] - e[1], l);
-  l = fmaf(C.cx[3], e[7] - e[0], l);
+// The first-difference Laplacian of both receivers of a pair at once (float2 = receivers (a, b)),
+// in packed FP32x2 instructions: the kernel is bound by instruction issue, and one packed
+// instruction does the work of two scalar ones (same roundings).  C holds the cumulative weights
+// C_j = sum_{k>=j} c_k (see launch_fd_step).
+__device__ __forceinline__ float2 lap2(const float2 (&dz)[8], const float2 (&e)[8],
+                                       const float2 (&cz)[4], const float2 (&cx)[4]) {
+  float2 l = __fmul2_rn(cz[0], sub2(dz[4], dz[3]));
+  l = __ffma2_rn(cz[1], sub2(dz[5], dz[2]), l);
+  l = __ffma2_rn(cz[2], sub2(dz[6], dz[1]), l);
+  l = __ffma2_rn(cz[3], sub2(dz[7], dz[0]), l);
+  l = __ffma2_rn(cx[0], sub2(e[4], e[3]), l);
+  l = __ffma2_rn(cx[1], sub2(e[5], e[2]), l);
+  l = __ffma2_rn(cx[2], sub2(e[6], e[1]), l);
+  l = __ffma2_rn(cx[3], sub2(e[7], e[0]), l);
   return l;
 }
 
@@ -235,21 +237,28 @@ __global__ void __launch_bounds__(32 * FD_MAXPAIRS, EGH_FD_MINB)
   }
   cp_async_wait<FD_RING - 8>();  // rows 0 .. 7 have landed
   __syncwarp();
-  // z first differences, component c = (point, receiver) of the lane's float4:
-  // dz[c][m] = D at row z - 3 + m for the current row z; ul = u^n at row z + 3
-  float dz[4][8], ul[4];
+  // z first differences of both receivers at point p (0: x, 1: x + 1) of the lane:
+  // dz[p][m] = D at row z - 3 + m for the current row z; ul = u^n at row z + 3
+  float2 cz2[4], cx2[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    cz2[j] = make_float2(C.cz[j], C.cz[j]);
+    cx2[j] = make_float2(C.cx[j], C.cx[j]);
+  }
+  float2 dz[2][8], ul[2];
   {
     const float4 v = ring[0][lane + 2];
-    ul[0] = v.x; ul[1] = v.y; ul[2] = v.z; ul[3] = v.w;
+    ul[0] = make_float2(v.x, v.y);
+    ul[1] = make_float2(v.z, v.w);
   }
 #pragma unroll
   for (int k = 1; k < 8; ++k) {
     const float4 v = ring[k][lane + 2];
-    const float nv[4] = {v.x, v.y, v.z, v.w};
+    const float2 nv[2] = {make_float2(v.x, v.y), make_float2(v.z, v.w)};
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      dz[c][k] = nv[c] - ul[c];
-      ul[c] = nv[c];
+    for (int p = 0; p < 2; ++p) {
+      dz[p][k] = sub2(nv[p], ul[p]);
+      ul[p] = nv[p];
     }
   }
   __syncwarp();  // ring rows 0 .. 2 are refilled next
@@ -270,49 +279,47 @@ __global__ void __launch_bounds__(32 * FD_MAXPAIRS, EGH_FD_MINB)
     }
     {
       const float4 v = ring[(i + 8) & (FD_RING - 1)][lane + 2];  // u^n at row z + 4
-      const float nv[4] = {v.x, v.y, v.z, v.w};
+      const float2 nv[2] = {make_float2(v.x, v.y), make_float2(v.z, v.w)};
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
+      for (int p = 0; p < 2; ++p) {
 #pragma unroll
-        for (int m = 0; m < 7; ++m) dz[c][m] = dz[c][m + 1];
-        dz[c][7] = nv[c] - ul[c];
-        ul[c] = nv[c];
+        for (int m = 0; m < 7; ++m) dz[p][m] = dz[p][m + 1];
+        dz[p][7] = sub2(nv[p], ul[p]);
+        ul[p] = nv[p];
       }
     }
     const float4* xr = ring[(i + 4) & (FD_RING - 1)];  // u^n at row z, points x0 - 4 .. x0 + 67
     const float4 A0 = xr[lane], A1 = xr[lane + 1], A2 = xr[lane + 2], A3 = xr[lane + 3],
                  A4 = xr[lane + 4];
     __syncwarp();  // every lane has read ring row i + 4 before it is refilled
-    // receiver a (.x/.z components) and b (.y/.w) at points x - 4 .. x + 5
-    const float wa[10] = {A0.x, A0.z, A1.x, A1.z, A2.x, A2.z, A3.x, A3.z, A4.x, A4.z};
-    const float wb[10] = {A0.y, A0.w, A1.y, A1.w, A2.y, A2.w, A3.y, A3.w, A4.y, A4.w};
-    float ea[9], eb[9];
+    // both receivers at points x - 4 .. x + 5
+    const float2 w[10] = {make_float2(A0.x, A0.y), make_float2(A0.z, A0.w), make_float2(A1.x, A1.y),
+                          make_float2(A1.z, A1.w), make_float2(A2.x, A2.y), make_float2(A2.z, A2.w),
+                          make_float2(A3.x, A3.y), make_float2(A3.z, A3.w), make_float2(A4.x, A4.y),
+                          make_float2(A4.z, A4.w)};
+    float2 e[9];
 #pragma unroll
-    for (int m = 0; m < 9; ++m) {
-      ea[m] = wa[m + 1] - wa[m];
-      eb[m] = wb[m + 1] - wb[m];
-    }
+    for (int m = 0; m < 9; ++m) e[m] = sub2(w[m + 1], w[m]);
     const int z = z0 + i;
-    float v[4];
+    float2 v0, v1;
     {
-      const float e0a[8] = {ea[0], ea[1], ea[2], ea[3], ea[4], ea[5], ea[6], ea[7]};
-      const float e0b[8] = {eb[0], eb[1], eb[2], eb[3], eb[4], eb[5], eb[6], eb[7]};
-      const float e1a[8] = {ea[1], ea[2], ea[3], ea[4], ea[5], ea[6], ea[7], ea[8]};
-      const float e1b[8] = {eb[1], eb[2], eb[3], eb[4], eb[5], eb[6], eb[7], eb[8]};
-      const float la = lap1(dz[0], e0a, C), lb = lap1(dz[1], e0b, C);
-      const float lc = lap1(dz[2], e1a, C), ld = lap1(dz[3], e1b, C);
+      const float2 e0[8] = {e[0], e[1], e[2], e[3], e[4], e[5], e[6], e[7]};
+      const float2 e1[8] = {e[1], e[2], e[3], e[4], e[5], e[6], e[7], e[8]};
+      const float2 l0 = lap2(dz[0], e0, cz2, cx2), l1 = lap2(dz[1], e1, cz2, cx2);
       // u^{n+1} = c3 L u + c1 (u - u^{n-1}) + u^{n-1}
-      v[0] = fmaf(cc.y, la, fmaf(cc.x, wa[4] - uo.x, uo.x));
-      v[1] = fmaf(cc.y, lb, fmaf(cc.x, wb[4] - uo.y, uo.y));
-      v[2] = ok1 ? fmaf(cc.w, lc, fmaf(cc.z, wa[5] - uo.z, uo.z)) : 0.f;
-      v[3] = ok1 ? fmaf(cc.w, ld, fmaf(cc.z, wb[5] - uo.w, uo.w)) : 0.f;
+      const float2 o0 = make_float2(uo.x, uo.y), o1 = make_float2(uo.z, uo.w);
+      v0 = __ffma2_rn(make_float2(cc.y, cc.y), l0,
+                      __ffma2_rn(make_float2(cc.x, cc.x), sub2(w[4], o0), o0));
+      v1 = __ffma2_rn(make_float2(cc.w, cc.w), l1,
+                      __ffma2_rn(make_float2(cc.z, cc.z), sub2(w[5], o1), o1));
+      if (!ok1) v1 = make_float2(0.f, 0.f);
     }
     if (ok0) {
-      un[z * PX2] = make_float4(v[0], v[1], v[2], v[3]);
+      un[z * PX2] = make_float4(v0.x, v0.y, v1.x, v1.y);
       if (sbase) {
         unsigned ha, la, hb, lb;
-        split_bf16(v[0], v[2], ha, la);
-        split_bf16(v[1], v[3], hb, lb);
+        split_bf16(v0.x, v1.x, ha, la);
+        split_bf16(v0.y, v1.y, hb, lb);
         __nv_bfloat16* sp = sbase + z * PX;
         __stcs(reinterpret_cast<unsigned*>(sp), ha);
         __stcs(reinterpret_cast<unsigned*>(sp + so.plane), la);
