@@ -161,6 +161,21 @@ void egh_destroy(egh_ctx *ctx);
  * Invalidates any previous Hessian and factors. */
 egh_status egh_green(egh_ctx *ctx, const float *vel, void *stream);
 
+/* Step (a) in the paper's cheaper form (Section "Randomized receiver inversion" and the
+ * examples: Green functions of a band-limited source, resampled in time to the source's Nyquist
+ * rate): the same solves with the wavelet s_n (n < nw, host float32) injected at the receiver
+ * (sample s_n into level n + 1, the Dirac's level 1 taking s_0), every decim-th level recorded,
+ * and the transform divided by the wavelet's spectrum:
+ *   ghat[r][k](x) = decim / S(f_k) * sum_{m: m decim < nt} u^r(m decim, x) exp(-i 2 pi f_k m decim dt),
+ *   S(f) = sum_{n<nw} s_n exp(-i 2 pi f n dt).
+ * Equal to egh_green's result up to the aliasing of the band above 1/(2 decim dt) and the
+ * record truncation (the convolved field runs nw steps longer); the transform's work and the
+ * snapshot traffic drop by decim.  Inputs and errors as egh_green, plus EGH_EINVAL for nw
+ * outside 1 .. nt, decim outside 1 .. nt, a non-finite sample, or |S(f_k)| below 1e-6 of its
+ * largest value at some frequency. */
+egh_status egh_green_bandlimited(egh_ctx *ctx, const float *vel, const float *wavelet, int32_t nw,
+                                 int32_t decim, void *stream);
+
 /* Step (b): per-frequency Hessians Q_k = H_k + mu I (eq. Qmatrix) with
  * H_k[i][j] = sum_x ghat_i conj(ghat_j) (the Gram of G^{ij} = sum_x g^i g^j^T
  * in the frequency domain; (j, i) = conj(i, j) as in Algorithm 2).  mu comes
@@ -190,6 +205,24 @@ egh_status egh_deblur(egh_ctx *ctx, const float *resid, int32_t ns, int32_t nt_d
  * (complex64, [nfreq][nrec][ns]) instead of synthesising them in time.
  * resid host or device; X device only. */
 egh_status egh_deblur_freq(egh_ctx *ctx, const float *resid, int32_t ns, int32_t nt_d, void *X, void *stream);
+
+/* The diagonal-Hessian baseline the paper compares against (its introduction: earlier work
+ * replaced the Hessian by a scaled identity; its examples run multiplier-based FWI with the
+ * diagonal Hessian approximation): each frequency's system Q_k X_k = D_k solved with Q_k's
+ * diagonal only, X_k[r][s] = D_k[r][s] / Q_k[r][r], then synthesised as egh_deblur.  Same
+ * buffers and errors as egh_deblur; requires egh_hessian (no factorisation). */
+egh_status egh_deblur_diag(egh_ctx *ctx, const float *resid, int32_t ns, int32_t nt_d, float *mult,
+                           void *stream);
+
+/* Randomised receiver subsets (Section "Randomized receiver inversion": the receiver axis is
+ * split into nsub subsets and one receiver is drawn at random from each at every iteration).
+ * Subset j covers indices floor(j nrec / nsub) .. floor((j + 1) nrec / nsub) - 1; out[j] =
+ * lo_j + floor(x_j (hi_j - lo_j) / 2^64) with x_j the SplitMix64 output number
+ * iteration * nsub + j of `seed` (counter form: x = mix(seed + (i + 1) * 0x9E3779B97F4A7C15)).
+ * Host-only (no device work).  out: [nsub] int32, caller-owned.  EGH_EINVAL unless
+ * 1 <= nsub <= nrec and out is not NULL. */
+egh_status egh_sample_receivers(int32_t nrec, int32_t nsub, uint64_t seed, uint64_t iteration,
+                                int32_t *out);
 
 /* Auxiliary (residual generation, Algorithm 1 delta d_s = d_s - S b_s):
  * traces of point sources with signature `wavelet` ([nt] float32, host) at

@@ -166,6 +166,30 @@ def green_dtft(grid: Grid, rec_iz, rec_ix, freqs, dt, nt, workers=None, threads_
     return np.stack(_parallel(one, list(range(rp.size)), workers))
 
 
+def green_dtft_bandlimited(grid: Grid, rec_iz, rec_ix, freqs, dt, nt, wavelet, decim, workers=1):
+    """Green transforms from a band-limited source, resampled in time (Section "Randomized
+    receiver inversion" resamples Green functions to the source's Nyquist rate; the examples use a
+    band-pass Ricker source): the solve of receiver r injects wavelet sample s_n at step n (the
+    Dirac's convention, sample 0 into level 1), every decim-th level is kept and the transform is
+    divided by the wavelet's spectrum,
+        ghat[r, k] = decim / S(f_k) * sum_{m: m decim < nt} u^r(m decim) exp(-i 2 pi f_k m decim dt),
+        S(f) = sum_n s_n exp(-i 2 pi f n dt)."""
+    s = np.asarray(wavelet, dtype=np.float64)
+    assert 1 <= s.size <= nt and decim >= 1
+    src = np.zeros((1, nt))
+    src[0, :s.size] = s
+    S = s @ twiddle(freqs, dt, s.size)  # [nf]
+    ntd = (nt + decim - 1) // decim
+    E = twiddle(freqs, dt * decim, ntd)  # [ntd, nf]
+    rp = grid.index(rec_iz, rec_ix)
+
+    def one(r):
+        u = fd_run(grid, dt, nt, src_p=rp[r:r + 1], src_f=src, want_snaps=True)["snaps"]
+        return np.einsum("mzx,mk->kzx", u[::decim], E) * (decim / S)[:, None, None]
+
+    return np.stack(_parallel(one, list(range(rp.size)), workers))
+
+
 def green_time(grid: Grid, rec_iz, rec_ix, dt, nt):
     """g[r, n, z, x]: full Green-function time histories (tiny grids only)."""
     rp = grid.index(rec_iz, rec_ix)
@@ -300,6 +324,46 @@ def deblur(L, resid, freqs, dt, nt_ref=None):
     D = dtft_traces(resid, freqs, dt)
     X = chol_solve(L, D)
     return synth(X, freqs, dt, resid.shape[2], nt_ref=nt_ref), X, D
+
+
+def deblur_diag(Q, resid, freqs, dt, nt_ref=None):
+    """Diagonal-Hessian baseline (the introduction's scaled-identity approximation of earlier
+    work; the examples' multiplier-based FWI with a diagonal Hessian): X_k = D_k / diag(Q_k),
+    then the same synthesis."""
+    D = dtft_traces(resid, freqs, dt)
+    d = np.real(np.einsum("kii->ki", Q))
+    X = D / d[:, :, None]
+    return synth(X, freqs, dt, resid.shape[2], nt_ref=nt_ref), X, D
+
+
+# ----------------------------------------------------------------------------
+# Randomised receiver subsets (Section "Randomized receiver inversion": the
+# receiver axis is divided into subsets and one receiver is drawn at random from
+# each at every iteration).
+# ----------------------------------------------------------------------------
+_M64 = (1 << 64) - 1
+
+
+def splitmix64(seed, i):
+    """Output number i of SplitMix64 (Steele, Lea and Flood, OOPSLA 2014) from state `seed`:
+    the state advances by the golden gamma 0x9E3779B97F4A7C15 before each output, which is
+    the state passed through two xor-shift-multiply rounds and a final xor-shift."""
+    z = (seed + (i + 1) * 0x9E3779B97F4A7C15) & _M64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M64
+    return z ^ (z >> 31)
+
+
+def sample_receivers(nrec, nsub, seed, iteration=0):
+    """Subset j = receivers floor(j nrec / nsub) .. floor((j+1) nrec / nsub) - 1; the pick is
+    lo + floor(x (hi - lo) / 2^64) with x = splitmix64(seed, iteration * nsub + j)."""
+    assert 1 <= nsub <= nrec
+    out = []
+    for j in range(nsub):
+        lo, hi = j * nrec // nsub, (j + 1) * nrec // nsub
+        x = splitmix64(seed & _M64, iteration * nsub + j)
+        out.append(lo + ((x * (hi - lo)) >> 64))
+    return np.array(out, dtype=np.int64)
 
 
 # ----------------------------------------------------------------------------

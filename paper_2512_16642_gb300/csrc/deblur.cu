@@ -601,6 +601,29 @@ cudaError_t launch_resid(const float2* Qh, int n, int nf, const float2* Xh, cons
   return cudaGetLastError();
 }
 
+// Diagonal-Hessian baseline: X_k[r][s] = D_k[r][s] / Q_k[r][r] (Q's diagonal is real, >= mu)
+__global__ void k_diag_solve(const float2* __restrict__ Qh, int n, float2* __restrict__ Dh, int ns,
+                             long long m) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long kr = i / ns;  // k * n + r
+    const long long k = kr / n, r = kr % n;
+    const float q = Qh[(k * n + r) * n + r].x;
+    float2 d = Dh[i];
+    d.x /= q;
+    d.y /= q;
+    Dh[i] = d;
+  }
+}
+
+cudaError_t launch_diag_solve(const float2* Qh, int n, int nf, float2* Dh, int ns, cudaStream_t st) {
+  const long long m = (long long)nf * n * ns;
+  const int blocks = (int)std::min<long long>((m + 255) / 256, 4 * 152);
+  count_launches(1);
+  k_diag_solve<<<blocks, 256, 0, st>>>(Qh, n, Dh, ns, m);
+  return cudaGetLastError();
+}
+
 // X += R (complex, all frequencies and sources)
 __global__ void k_add_correction(float2* __restrict__ X, const float2* __restrict__ R, long long m) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m;

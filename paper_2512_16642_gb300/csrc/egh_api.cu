@@ -56,6 +56,8 @@ struct egh_ctx {
   float2 *coef = nullptr, *lev = nullptr;    // (c1, c3) per point; paired FD levels [3][B/2][F]
   __nv_bfloat16* snap = nullptr;             // [2][2K][Bp][G] hi/lo snapshots of the transform
   unsigned char* twt = nullptr;              // tensor-core twiddle tiles (64 levels each)
+  unsigned char* twt_bl = nullptr;           // the same for the band-limited, decimated form
+  size_t twt_bl_cap = 0;
   CUtensorMap tmap{};                        // TMA map of the snapshot ring (64-byte aligned type)
   int Bp = 0;                                // receivers per snapshot slot (B rounded up to even)
   float *gh = nullptr, *part = nullptr;
@@ -67,8 +69,8 @@ struct egh_ctx {
   cudaStream_t side = nullptr;                 // the transform's stream inside egh_green (low priority)
   cudaStream_t fdst = nullptr;                 // the FD stream inside egh_green (high priority)
   // FD steps of a chunk as CUDA graphs, keyed by (first level mod 3, its offset in the chunk,
-  // steps, ring slot of the chunk's level 0, pairs, rows per warp)
-  std::map<std::tuple<int, int, int, int, int, int>, cudaGraphExec_t> fd_graphs;
+  // steps, ring slot of the chunk's level 0, pairs, rows per warp, levels per recorded level)
+  std::map<std::tuple<int, int, int, int, int, int, int>, cudaGraphExec_t> fd_graphs;
   cudaEvent_t fd_done[2] = {}, dft_done[2] = {}, ev_side = nullptr;
   cudaEvent_t ev_tune[2] = {};                 // FD rows-per-warp timing
   // per-chunk start/end events of the FD steps and of the transform in the last egh_green
@@ -259,7 +261,7 @@ cudaError_t zero_snap_slot(egh_ctx* ctx, int j, cudaStream_t st) {
 }
 
 void free_all(egh_ctx* c) {
-  void* ptrs[] = {c->Wh, c->Dr, c->Rr, c->coef, c->lev, c->snap, c->twt, c->gh, c->ghb, c->part, c->Qh, c->Lh, c->tw, c->w_dev,
+  void* ptrs[] = {c->twt_bl, c->Wh, c->Dr, c->Rr, c->coef, c->lev, c->snap, c->twt, c->gh, c->ghb, c->part, c->Qh, c->Lh, c->tw, c->w_dev,
                   c->rec_pts, c->status, c->dsum, c->lmax, c->vchk, c->d_err, c->vel_stage, c->Dh,
                   c->io_in, c->io_out};
   for (void* p : ptrs)
@@ -313,19 +315,26 @@ void release_green_buffers(egh_ctx* ctx) {
   ctx->fd_graphs.clear();
 }
 
+// Snapshot output of level t in a chunk whose level t0 (a multiple of `decim`) sits in ring slot
+// sbase: every decim-th level is recorded, the others write none.
+SnapOut level_snap(egh_ctx* ctx, int t, int t0, int sbase, int decim) {
+  if (t % decim) return SnapOut{nullptr, 0, 0};
+  return snap_slot(ctx, sbase + (t - t0) / decim);
+}
+
 // FD steps t = ta .. t1-1 of a chunk whose level t0 sits in ring slot sbase, on the FD stream, as
 // one CUDA graph (captured on first use, then replayed: the kernel nodes' arguments depend only
 // on the key, since state slots follow t mod 3 and ring slots follow t - t0).
-egh_status fd_chunk_steps(egh_ctx* ctx, int ta, int t0, int t1, int sbase, int np) {
+egh_status fd_chunk_steps(egh_ctx* ctx, int ta, int t0, int t1, int sbase, int np, int decim) {
   if (ta >= t1) return EGH_OK;
-  const auto key = std::make_tuple(ta % 3, ta - t0, t1 - ta, sbase, np, ctx->fd_tz);
+  const auto key = std::make_tuple(ta % 3, ta - t0, t1 - ta, sbase, np, ctx->fd_tz, decim);
   auto it = ctx->fd_graphs.find(key);
   if (it == ctx->fd_graphs.end()) {
     CK(cudaStreamBeginCapture(ctx->fdst, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
     for (int t = ta; t < t1 && e == cudaSuccess; ++t)
       e = launch_fd_step(slot(ctx, t - 1), slot(ctx, t - 2), slot(ctx, t), ctx->coef, ctx->L,
-                         ctx->S, np, snap_slot(ctx, sbase + (t - t0)), ctx->fdst, ctx->fd_tz);
+                         ctx->S, np, level_snap(ctx, t, t0, sbase, decim), ctx->fdst, ctx->fd_tz);
     count_launches(-(t1 - ta));  // counted again at each replay
     cudaGraph_t graph = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(ctx->fdst, &graph);
@@ -540,9 +549,16 @@ void egh_destroy(egh_ctx* ctx) {
   delete ctx;
 }
 
-egh_status egh_green(egh_ctx* ctx, const float* vel, void* stream_) {
-  if (!ctx) return fail(nullptr, EGH_EINVAL, "ctx is NULL");
-  cudaStream_t stream = (cudaStream_t)stream_;
+}  // extern "C"
+
+namespace {
+
+// The Green stage.  wav == nullptr: Dirac source (impulse at level 1), every level transformed
+// with the table ctx->twt.  Otherwise the band-limited form: wavelet sample s_n is injected at
+// the receiver into level n + 1, every decim-th level is recorded and transformed with `twt`
+// (which folds in the factor decim and the division by the wavelet's spectrum).
+egh_status green_run(egh_ctx* ctx, const float* vel, cudaStream_t stream, const float* wav, int nw,
+                     int decim, const unsigned char* twt) {
   CK(cudaSetDevice(ctx->dev));
   ctx->state = ST_CREATED;
   egh_status s = ensure_green_buffers(ctx);
@@ -583,33 +599,48 @@ egh_status egh_green(egh_ctx* ctx, const float* vel, void* stream_) {
     }
     ctx->fd_tz = best_tz;
   }
-  const int nchunk = (nt + K - 1) / K;
+  const int D = decim;
+  const int ntd = (nt + D - 1) / D;  // recorded levels 0, D, 2D, ... < nt
+  const int nchunk = (ntd + K - 1) / K;
   long long g = 0;  // chunks so far over all batches: chunk g uses ring slots (g % 2) K ..
   for (int b0 = 0; b0 < ctx->nrec; b0 += B) {
     const int nb = std::min(B, ctx->nrec - b0);
     const int np = (nb + 1) / 2;
     for (int c = 0; c < nchunk; ++c, ++g) {
-      const int t0 = c * K, t1 = std::min(nt, t0 + K);
+      // recorded levels m0 .. m1-1 of this chunk; time levels t0 .. t1-1
+      const int m0 = c * K, m1 = std::min(ntd, m0 + K);
+      const int t0 = m0 * D, t1 = std::min(nt, m1 * D);
       const int sbase = (int)(g & 1) * K;
       // this chunk's slots were read by the transform of chunk g - 2
       if (g >= 2) CK(cudaStreamWaitEvent(fs, ctx->dft_done[g & 1], 0));
       CK(cudaEventRecord(ctx->ev_fd[2 * g], fs));
       for (int t = t0; t < std::min(t1, 2); ++t) {
-        // level 0 is zero; level 1 is the impulse (the step from zero levels adds only the source)
-        const int sj = sbase + (t - t0);
+        // level 0 is zero; level 1 is the first source sample (the step from zero levels adds only
+        // the source): the impulse, or s_0 of the wavelet
+        const SnapOut so = level_snap(ctx, t, t0, sbase, D);
         CK(cudaMemsetAsync(slot(ctx, t), 0, (size_t)np * L.F * sizeof(float2), fs));
-        CK(zero_snap_slot(ctx, sj, fs));
+        if (so.lvl) CK(zero_snap_slot(ctx, sbase + (t - t0) / D, fs));
         if (t == 1)
-          CK(launch_inject(slot(ctx, 1), L.F, ctx->rec_pts + b0, ctx->coef, nb, 1.0f, src_scale,
-                           L.org, snap_slot(ctx, sj), fs));
+          CK(launch_inject(slot(ctx, 1), L.F, ctx->rec_pts + b0, ctx->coef, nb, wav ? wav[0] : 1.0f,
+                           src_scale, L.org, so, fs));
       }
-      if ((s = fd_chunk_steps(ctx, std::max(t0, 2), t0, t1, sbase, np))) return s;
+      // levels that still take a wavelet sample: a step, then the injection, launched directly
+      const int ta = std::max(t0, 2);
+      const int tw = wav ? std::max(ta, std::min(t1, nw + 1)) : ta;
+      for (int t = ta; t < tw; ++t) {
+        const SnapOut so = level_snap(ctx, t, t0, sbase, D);
+        CK(launch_fd_step(slot(ctx, t - 1), slot(ctx, t - 2), slot(ctx, t), ctx->coef, L, ctx->S, np,
+                          so, fs, ctx->fd_tz));
+        CK(launch_inject(slot(ctx, t), L.F, ctx->rec_pts + b0, ctx->coef, nb, wav[t - 1], src_scale,
+                         L.org, so, fs));
+      }
+      if ((s = fd_chunk_steps(ctx, tw, t0, t1, sbase, np, D))) return s;
       CK(cudaEventRecord(ctx->ev_fd[2 * g + 1], fs));
       CK(cudaEventRecord(ctx->fd_done[g & 1], fs));
       CK(cudaStreamWaitEvent(ctx->side, ctx->fd_done[g & 1], 0));
       CK(cudaEventRecord(ctx->ev_dft[2 * g], ctx->side));
-      CK(launch_dft_tc(ctx->tmap, ctx->twt, ctx->nf, sbase, t1 - t0, t0, L, ctx->gh, ctx->ghb,
-                       (t1 == nt && ctx->ghb) ? 1 : 0, b0, nb, ctx->d_err, ctx->side));
+      CK(launch_dft_tc(ctx->tmap, twt, ctx->nf, sbase, m1 - m0, m0, L, ctx->gh, ctx->ghb,
+                       (m1 == ntd && ctx->ghb) ? 1 : 0, b0, nb, ctx->d_err, ctx->side));
       CK(cudaEventRecord(ctx->ev_dft[2 * g + 1], ctx->side));
       CK(cudaEventRecord(ctx->dft_done[g & 1], ctx->side));
     }
@@ -647,6 +678,63 @@ egh_status egh_green(egh_ctx* ctx, const float* vel, void* stream_) {
   ctx->st.point_steps = (long long)ctx->nrec * nt * L.NZ * L.NX;
   ctx->state = ST_GREEN;
   return EGH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+egh_status egh_green(egh_ctx* ctx, const float* vel, void* stream_) {
+  if (!ctx) return fail(nullptr, EGH_EINVAL, "ctx is NULL");
+  return green_run(ctx, vel, (cudaStream_t)stream_, nullptr, 0, 1, ctx->twt);
+}
+
+egh_status egh_green_bandlimited(egh_ctx* ctx, const float* vel, const float* wavelet,
+                                 int32_t nw, int32_t decim, void* stream_) {
+  if (!ctx) return fail(nullptr, EGH_EINVAL, "ctx is NULL");
+  if (!wavelet || nw < 1 || nw > ctx->nt)
+    return fail(ctx, EGH_EINVAL, "need a wavelet of 1 .. nt samples");
+  if (decim < 1 || decim > ctx->nt) return fail(ctx, EGH_EINVAL, "decim must be in 1 .. nt");
+  for (int n = 0; n < nw; ++n)
+    if (!std::isfinite(wavelet[n])) return fail(ctx, EGH_EINVAL, "wavelet samples must be finite");
+  // spectral division and the decimation factor, folded into the twiddles:
+  // g(w_k) = decim / S(w_k) * sum_m u_{m decim} exp(-i w_k m decim dt), S(w) = sum_n s_n e^{-i w n dt}
+  std::vector<std::complex<double>> scale(ctx->nf);
+  double smax = 0.0;
+  for (int k = 0; k < ctx->nf; ++k) {
+    std::complex<double> S(0.0, 0.0);
+    for (int n = 0; n < nw; ++n) {
+      double ph = ctx->freqs[k] * (double)n * ctx->dt;
+      ph -= std::floor(ph);
+      S += (double)wavelet[n] * std::polar(1.0, -2.0 * M_PI * ph);
+    }
+    scale[k] = S;
+    smax = std::max(smax, std::abs(S));
+  }
+  for (int k = 0; k < ctx->nf; ++k) {
+    if (!(std::abs(scale[k]) > 1e-6 * smax))
+      return fail(ctx, EGH_EINVAL, "the wavelet's spectrum vanishes at frequency " + std::to_string(k));
+    scale[k] = (double)decim / scale[k];
+  }
+  const int ntd = (ctx->nt + decim - 1) / decim;
+  const std::vector<unsigned char> twt =
+      dft_twiddle_tiles(ctx->freqs, ctx->dt * decim, ntd, &scale);
+  CK(cudaSetDevice(ctx->dev));
+  cudaStream_t stream = (cudaStream_t)stream_;
+  if (twt.size() > ctx->twt_bl_cap) {
+    CK(cudaStreamSynchronize(stream));
+    CK(cudaDeviceSynchronize());
+    cudaFree(ctx->twt_bl);
+    ctx->twt_bl = nullptr;
+    ctx->twt_bl_cap = 0;
+    egh_status s = dalloc(ctx, (void**)&ctx->twt_bl, twt.size(), "band-limited twiddle tiles");
+    if (s) return s;
+    ctx->twt_bl_cap = twt.size();
+  }
+  // the previous Green stage may still read the table
+  CK(cudaStreamSynchronize(ctx->side));
+  CK(cudaMemcpy(ctx->twt_bl, twt.data(), twt.size(), cudaMemcpyHostToDevice));
+  return green_run(ctx, vel, stream, wavelet, nw, decim, ctx->twt_bl);
 }
 
 egh_status egh_hessian(egh_ctx* ctx, egh_mu_mode mode, double mu_param, double* mu_out,
@@ -736,8 +824,10 @@ egh_status egh_factor(egh_ctx* ctx, int32_t* bad_freq, void* stream_) {
 }
 
 static egh_status deblur_common(egh_ctx* ctx, const float* resid, int32_t ns, int32_t nt_d,
-                                float* mult, float2* X, cudaStream_t stream) {
-  if (ctx->state < ST_FACTORED) return fail(ctx, EGH_ESTATE, "egh_deblur needs egh_factor first");
+                                float* mult, float2* X, cudaStream_t stream, bool diag = false) {
+  if (diag && ctx->state < ST_HESSIAN)
+    return fail(ctx, EGH_ESTATE, "egh_deblur_diag needs egh_hessian first");
+  if (!diag && ctx->state < ST_FACTORED) return fail(ctx, EGH_ESTATE, "egh_deblur needs egh_factor first");
   if (ns < 0 || nt_d < 1) return fail(ctx, EGH_EINVAL, "ns must be >= 0 and nt_d >= 1");
   if (!resid || (!mult && !X)) return fail(ctx, EGH_EINVAL, "NULL buffer");
   if (ns == 0) return EGH_OK;
@@ -775,7 +865,7 @@ static egh_status deblur_common(egh_ctx* ctx, const float* resid, int32_t ns, in
   CK(cudaEventRecord(ctx->ev[6], stream));
   CK(launch_trace_dft(din, (int)ntr, nt_d, ctx->tw, ctx->nf, ctx->nrec, ns, 0, D, stream));
   const size_t dbytes = (size_t)ctx->nf * ntr * sizeof(float2);
-  if (prec_mixed(ctx->prec)) {
+  if (!diag && prec_mixed(ctx->prec)) {
     // one step of iterative refinement: residual in FP64, correction solved with the FP32 factors
     if ((s = ensure_buf(ctx, (void**)&ctx->Dr, &ctx->Dr_cap, dbytes, stream, "refinement rhs")))
       return s;
@@ -783,7 +873,9 @@ static egh_status deblur_common(egh_ctx* ctx, const float* resid, int32_t ns, in
       return s;
     CK(cudaMemcpyAsync(ctx->Dr, D, dbytes, cudaMemcpyDeviceToDevice, stream));
   }
-  if (prec_mixed(ctx->prec)) {
+  if (diag) {
+    CK(launch_diag_solve(ctx->Qh, ctx->nrec, ctx->nf, D, ns, stream));
+  } else if (prec_mixed(ctx->prec)) {
     // X = W^H W D (products with the explicit inverse factor), residual D - Q X in FP64, the
     // correction solved the same way
     CK(launch_inverse_solve(ctx->Wh, ctx->nrec, ctx->nf, D, ctx->Rr, D, ns, stream));
@@ -821,6 +913,37 @@ egh_status egh_deblur_freq(egh_ctx* ctx, const float* resid, int32_t ns, int32_t
   CK(cudaSetDevice(ctx->dev));
   if (!X) return fail(ctx, EGH_EINVAL, "X is NULL");
   return deblur_common(ctx, resid, ns, nt_d, nullptr, (float2*)X, (cudaStream_t)stream);
+}
+
+egh_status egh_deblur_diag(egh_ctx* ctx, const float* resid, int32_t ns, int32_t nt_d, float* mult,
+                           void* stream) {
+  if (!ctx) return fail(nullptr, EGH_EINVAL, "ctx is NULL");
+  CK(cudaSetDevice(ctx->dev));
+  if (!mult) return fail(ctx, EGH_EINVAL, "mult is NULL");
+  return deblur_common(ctx, resid, ns, nt_d, mult, nullptr, (cudaStream_t)stream, true);
+}
+
+// SplitMix64 (Steele, Lea and Flood, "Fast splittable pseudorandom number generators", OOPSLA
+// 2014) used as a counter-based generator: output i = mix(seed + (i + 1) * golden gamma).
+static uint64_t splitmix64_at(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+egh_status egh_sample_receivers(int32_t nrec, int32_t nsub, uint64_t seed, uint64_t iteration,
+                                int32_t* out) {
+  if (!out) return fail(nullptr, EGH_EINVAL, "out is NULL");
+  if (nrec < 1 || nsub < 1 || nsub > nrec)
+    return fail(nullptr, EGH_EINVAL, "need 1 <= nsub <= nrec");
+  for (int32_t j = 0; j < nsub; ++j) {
+    const int64_t lo = (int64_t)j * nrec / nsub, hi = (int64_t)(j + 1) * nrec / nsub;
+    const uint64_t x = splitmix64_at(seed, iteration * (uint64_t)nsub + (uint64_t)j);
+    const uint64_t pick = (uint64_t)(((unsigned __int128)x * (uint64_t)(hi - lo)) >> 64);
+    out[j] = (int32_t)(lo + (int64_t)pick);
+  }
+  return EGH_OK;
 }
 
 egh_status egh_forward(egh_ctx* ctx, const float* vel, int32_t nsrc, const int32_t* src_iz,

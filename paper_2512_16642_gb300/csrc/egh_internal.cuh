@@ -19,6 +19,7 @@
 
 #include "egh.h"
 
+#include <complex>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -74,7 +75,8 @@ cudaError_t launch_record(const float2* u, long long pstride, const int* rec_pts
                           float* traces, int nt, int t, cudaStream_t st);
 int dft_ncomp(int nf);
 size_t dft_smem(int nf);
-std::vector<unsigned char> dft_twiddle_tiles(const std::vector<double>& f, double dt, int nt);
+std::vector<unsigned char> dft_twiddle_tiles(const std::vector<double>& f, double dt, int nt,
+                                             const std::vector<std::complex<double>>* scale = nullptr);
 cudaError_t make_snap_tmap(CUtensorMap* tm, void* base, long long G, int Bp, int nslot);
 cudaError_t launch_dft_tc(const CUtensorMap& tmap, const unsigned char* twt, int nf, int slot0,
                           int kcount, int n0, const Layout& L, float* gh, __nv_bfloat16* ghb,
@@ -124,6 +126,8 @@ cudaError_t launch_trsm(const float2* Lh, int n, int nf, float2* Dh, int ns, cud
 cudaError_t launch_trtri(const float2* Lh, int n, int nf, float2* Wh, cudaStream_t st);
 cudaError_t launch_inverse_solve(const float2* Wh, int n, int nf, const float2* D, float2* Y,
                                  float2* X, int ld, cudaStream_t st);
+// diagonal-Hessian baseline: D_k[r][s] /= Q_k[r][r]
+cudaError_t launch_diag_solve(const float2* Qh, int n, int nf, float2* Dh, int ns, cudaStream_t st);
 // refinement residual R = D - Q X: FP64 arithmetic (fp64) or the compensated FP32 dot product
 cudaError_t launch_resid(const float2* Qh, int n, int nf, const float2* Xh, const float2* Dh,
                          int ns, float2* Rh, bool fp64, cudaStream_t st);

@@ -16,6 +16,7 @@
 
 #include <cfloat>
 #include <cmath>
+#include <complex>
 #include <cstring>
 #include <vector>
 
@@ -637,8 +638,11 @@ cudaError_t launch_dft_tc(const CUtensorMap& tmap, const unsigned char* twt, int
 // 128-byte-swizzled K-major layout (row c, level j at byte (c/8)*1024 + (c%8)*128 +
 // (((2j/16) ^ (c%8)) * 16) + 2j%16); row 2k = cos(2 pi f_k n dt), row 2k+1 = -sin(2 pi f_k n dt)
 // with the phase reduced as 2 pi frac(f_k n dt) in double precision; hi = bf16(w),
-// lo = bf16(w - hi); rows >= 2 nf and levels >= nt are zero.
-std::vector<unsigned char> dft_twiddle_tiles(const std::vector<double>& f, double dt, int nt) {
+// lo = bf16(w - hi); rows >= 2 nf and levels >= nt are zero.  With `scale`, row pair k holds
+// Re and Im of scale[k] exp(-i 2 pi f_k n dt) instead (the band-limited, decimated form folds its
+// decimation factor and spectral division into the twiddles).
+std::vector<unsigned char> dft_twiddle_tiles(const std::vector<double>& f, double dt, int nt,
+                                             const std::vector<std::complex<double>>* scale) {
   const int nf = (int)f.size(), N = dft_ncomp(nf);
   const int ntile = (nt + 63) / 64;
   const size_t tile = 2ull * N * 128;
@@ -651,7 +655,9 @@ std::vector<unsigned char> dft_twiddle_tiles(const std::vector<double>& f, doubl
       double ph = f[k] * (double)n * dt;
       ph -= std::floor(ph);
       const double a = 2.0 * M_PI * ph;
-      const double v[2] = {std::cos(a), -std::sin(a)};
+      std::complex<double> w(std::cos(a), -std::sin(a));
+      if (scale) w *= (*scale)[k];
+      const double v[2] = {w.real(), w.imag()};
       for (int q = 0; q < 2; ++q) {
         const int c = 2 * k + q;
         const size_t off = (size_t)(c >> 3) * 1024 + (c & 7) * 128 +

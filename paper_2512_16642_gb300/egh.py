@@ -82,6 +82,10 @@ _SIGS = {
     "egh_create": ([ctypes.POINTER(egh_config), ctypes.POINTER(_vp)], ctypes.c_int),
     "egh_destroy": ([_vp], None),
     "egh_green": ([_vp, _vp, _vp], ctypes.c_int),
+    "egh_deblur_diag": ([_vp, _vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp], ctypes.c_int),
+    "egh_sample_receivers": ([ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, ctypes.c_uint64, _vp],
+                             ctypes.c_int),
+    "egh_green_bandlimited": ([_vp, _vp, _vp, ctypes.c_int32, ctypes.c_int32, _vp], ctypes.c_int),
     "egh_hessian": ([_vp, ctypes.c_int, ctypes.c_double, _f64p, _vp], ctypes.c_int),
     "egh_factor": ([_vp, _i32p, _vp], ctypes.c_int),
     "egh_deblur": ([_vp, _vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp], ctypes.c_int),
@@ -199,6 +203,13 @@ def egh_green(ctx, vel, stream=None):
     _check(load().egh_green(ctx, p, _stream(stream, cu)), ctx)
 
 
+def egh_green_bandlimited(ctx, vel, wavelet, decim, stream=None):
+    p, cu = _ptr(vel)
+    w = np.ascontiguousarray(wavelet, dtype=np.float32)
+    _check(load().egh_green_bandlimited(ctx, p, w.ctypes.data, int(w.size), int(decim),
+                                        _stream(stream, cu)), ctx)
+
+
 def egh_hessian(ctx, mode=EGH_MU_REL_MEANDIAG, mu_param=1e-2, stream=None):
     mu = ctypes.c_double(0.0)
     _check(load().egh_hessian(ctx, int(mode), float(mu_param), ctypes.byref(mu), _stream(stream, True)),
@@ -221,6 +232,20 @@ def egh_deblur(ctx, resid, ns, nt_d, mult, stream=None):
     pi, ci = _ptr(resid)
     po, co = _ptr(mult)
     _check(load().egh_deblur(ctx, pi, int(ns), int(nt_d), po, _stream(stream, ci or co)), ctx)
+
+
+def egh_deblur_diag(ctx, resid, ns, nt_d, mult, stream=None):
+    pi, ci = _ptr(resid)
+    po, co = _ptr(mult)
+    _check(load().egh_deblur_diag(ctx, pi, int(ns), int(nt_d), po, _stream(stream, ci or co)), ctx)
+
+
+def sample_receivers(nrec, nsub, seed, iteration=0):
+    """One receiver index drawn from each of nsub contiguous subsets of 0 .. nrec-1 (int32)."""
+    out = np.empty(int(nsub), dtype=np.int32)
+    _check(load().egh_sample_receivers(int(nrec), int(nsub), int(seed) & (2**64 - 1),
+                                       int(iteration) & (2**64 - 1), out.ctypes.data), None)
+    return out
 
 
 def egh_deblur_freq(ctx, resid, ns, nt_d, X, stream=None):
@@ -299,6 +324,9 @@ class Context:
     def green(self, vel, stream=None):
         egh_green(self.h, vel, stream)
 
+    def green_bandlimited(self, vel, wavelet, decim, stream=None):
+        egh_green_bandlimited(self.h, vel, wavelet, decim, stream)
+
     def hessian(self, mode=EGH_MU_REL_MEANDIAG, mu_param=1e-2, stream=None):
         return egh_hessian(self.h, mode, mu_param, stream)
 
@@ -308,6 +336,11 @@ class Context:
     def deblur(self, resid, mult, stream=None):
         ns, nr, ntd = resid.shape
         egh_deblur(self.h, resid, ns, ntd, mult, stream)
+        return mult
+
+    def deblur_diag(self, resid, mult, stream=None):
+        ns, nr, ntd = resid.shape
+        egh_deblur_diag(self.h, resid, ns, ntd, mult, stream)
         return mult
 
     def deblur_freq(self, resid, X, stream=None):

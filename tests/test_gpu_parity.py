@@ -198,6 +198,28 @@ def test_precision_form_small(small):
         assert d <= 1e-6, (k, d)
 
 
+def test_diagonal_baseline_small(small):
+    """The diagonal-Hessian baseline (egh_deblur_diag, no factorisation) against the oracle's, and
+    its data misfit against the full solve's: the full Hessian inverse fits the system better."""
+    torch = _torch()
+    from paper_2512_16642_gb300 import egh
+
+    c, o, _ = small
+    r32 = np.ascontiguousarray(o["resid"], np.float32)
+    ref, Xd, Dd = oracle.deblur_diag(o["Q"], r32.astype(np.float64), c.freqs, c.dt, nt_ref=c.nt)
+    with _ctx(c) as ctx:
+        ctx.green(torch.from_numpy(np.float32(c.vel_start)).cuda())
+        ctx.hessian(egh.EGH_MU_REL_MEANDIAG, c.mu_alpha)
+        with pytest.raises(egh.EghError):  # the full solve still needs the factorisation
+            ctx.deblur(r32, np.empty_like(r32))
+        m = np.empty_like(r32)
+        ctx.deblur_diag(r32, m)
+    assert rel(m, ref) <= MULT_TOL
+    _, Xf, _ = oracle.deblur(o["L"], r32.astype(np.float64), c.freqs, c.dt, nt_ref=c.nt)
+    fit = lambda X: np.linalg.norm(np.einsum("kij,kjs->kis", o["Q"], X) - Dd) / np.linalg.norm(Dd)
+    assert fit(Xf) < 1e-10 < fit(Xd)
+
+
 def test_factor_parity_small(small):
     c, o, g = small
     L = g["L"].astype(np.complex128)

@@ -85,6 +85,92 @@ def test_on_the_fly_dtft_matches_stored_history():
     assert np.abs(out["ghat"] - ref).max() <= 1e-12 * np.abs(ref).max()
 
 
+def test_bandlimited_impulse_is_the_dirac_transform():
+    """A one-sample unit wavelet without decimation (S = 1) gives exactly the Dirac transform."""
+    c, g = _tiny(nt=40)
+    a = oracle.green_dtft(g, c.rec_iz, c.rec_ix, c.freqs, c.dt, c.nt, workers=1)
+    b = oracle.green_dtft_bandlimited(g, c.rec_iz, c.rec_ix, c.freqs, c.dt, c.nt, [1.0], 1)
+    assert np.abs(a - b).max() <= 1e-14 * np.abs(a).max()
+
+
+def test_bandlimited_equals_convolved_dirac_histories():
+    """Linearity and time invariance of the stepper: the wavelet-driven solve equals the
+    wavelet convolved with the Dirac time histories (sample s_n delayed by n steps), here
+    decimated by 3 and divided by the wavelet's spectrum computed as a plain sum."""
+    c, g = _tiny(nt=45)
+    rng = np.random.default_rng(3)
+    s = rng.standard_normal(7)
+    D = 3
+    gt = oracle.green_time(g, c.rec_iz, c.rec_ix, c.dt, c.nt)  # [r, n, z, x]
+    u = np.zeros_like(gt)
+    for n in range(s.size):
+        u[:, n:] += s[n] * gt[:, :c.nt - n]
+    t = np.arange(0, c.nt, D) * c.dt
+    S = np.array([np.sum(s * np.exp(-2j * np.pi * f * np.arange(s.size) * c.dt)) for f in c.freqs])
+    ref = np.stack([np.einsum("rmzx,m->rzx", u[:, ::D], np.exp(-2j * np.pi * f * t)) * D / S[k]
+                    for k, f in enumerate(c.freqs)], axis=1)
+    got = oracle.green_dtft_bandlimited(g, c.rec_iz, c.rec_ix, c.freqs, c.dt, c.nt, s, D)
+    assert np.linalg.norm(got - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+def test_bandlimited_approximates_dirac_until_aliasing():
+    """With a long record (fields absorbed by the sponge) the band-limited, decimated transform
+    approaches the Dirac one while the wavelet's band stays below the decimated Nyquist
+    frequency 1/(2 D dt), and fails once it does not (Ricker 15 Hz: D = 10 keeps 50 Hz, D = 30
+    folds 16.7 Hz onto the band)."""
+    c = synth.case_tiny(nz=30, nx=30, nsponge=10, nt=2400)
+    g = oracle.Grid(c.vel_true, c.dz, c.dx, c.nsponge, R=1e-3)
+    fr = np.array([10.0, 15.0, 20.0])
+    gd = oracle.green_dtft(g, c.rec_iz, c.rec_ix, fr, c.dt, c.nt, workers=1)
+    w = synth.ricker(150, c.dt, 15.0)
+    err = {}
+    for D in (1, 10, 30):
+        gb = oracle.green_dtft_bandlimited(g, c.rec_iz, c.rec_ix, fr, c.dt, c.nt, w, D)
+        err[D] = max(np.linalg.norm(gb[:, k] - gd[:, k]) / np.linalg.norm(gd[:, k]) for k in range(3))
+    assert err[1] <= 1e-3 and err[10] <= 1e-3
+    assert err[30] >= 0.1
+
+
+def test_splitmix64_published_outputs():
+    """SplitMix64's first outputs as published with its reference implementation (state 0:
+    0xe220a8397b1dcdaf, 0x6e789e6aa1b965f4, 0x06c45d188009454f; state 1234567:
+    6457827717110365317, 3203168211198807973)."""
+    assert [oracle.splitmix64(0, i) for i in range(3)] == [
+        0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+    assert [oracle.splitmix64(1234567, i) for i in range(2)] == [
+        6457827717110365317, 3203168211198807973]
+
+
+def test_sample_receivers_one_per_subset_and_uniform():
+    """One pick inside each contiguous subset, and each position of a subset equally likely
+    (chi-square over many iterations)."""
+    nrec, nsub = 231, 100
+    counts = np.zeros(3)
+    for it in range(3000):
+        p = oracle.sample_receivers(nrec, nsub, seed=11, iteration=it)
+        lo = np.arange(nsub) * nrec // nsub
+        hi = (np.arange(nsub) + 1) * nrec // nsub
+        assert np.all((p >= lo) & (p < hi))
+        counts += np.bincount(p[hi - lo == 3] - lo[hi - lo == 3], minlength=3)
+    exp = counts.sum() / 3
+    chi2 = float(np.sum((counts - exp) ** 2 / exp))
+    assert chi2 < 13.8  # 2 degrees of freedom, p = 0.001
+    assert np.array_equal(oracle.sample_receivers(10, 10, 5), np.arange(10))  # nsub = nrec
+
+
+def test_deblur_diag_exact_for_diagonal_hessian():
+    """For a diagonal Hessian the diagonal baseline is the exact solve."""
+    rng = np.random.default_rng(2)
+    nf, nr, ns, nt = 3, 5, 2, 64
+    d = rng.uniform(1.0, 3.0, (nf, nr))
+    Q = np.stack([np.diag(d[k]).astype(np.complex128) for k in range(nf)])
+    resid = rng.standard_normal((ns, nr, nt))
+    freqs = np.array([20.0, 40.0, 60.0])
+    a = oracle.deblur_diag(Q, resid, freqs, 1e-3)[0]
+    b = oracle.deblur(oracle.cholesky(Q), resid, freqs, 1e-3)[0]
+    assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max()
+
+
 def test_trace_dtft_closed_form():
     """sum_{t<N} cos(w0 t dt) exp(-i w t dt) equals its geometric-series closed form."""
     dt, N, f0 = 1e-3, 1000, 5.3
