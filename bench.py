@@ -38,9 +38,9 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM traffic (read + write bytes) per launch of the FD step and of the transform from the
 # committed ncu capture (profiles/), valid only for the kernel sources it was taken from (sha256
 # of csrc/fd.cu); None until a capture exists.
-KERNEL_TRAFFIC = {"fd_sha256": "0dbde35b7433ee9a6a2c7ed837f8842a2a2f9e9bb9fbb1654a1ef2eac6495fce",
-                  "k_fd_step": 31.22e6,   # 2.52 MB read + 28.70 MB write per launch
-                  "k_dft_tc": 13.19e9}    # 12.02 GB read + 1.16 GB write per 512-level launch
+KERNEL_TRAFFIC = {"fd_sha256": "bf9a1528aa400f066f1fc8a2dbd5e627c7a6b73f1c60b893cdf1f10c1cd2dc3f",
+                  "k_fd_step": 32.46e6,   # 3.01 MB read + 29.46 MB write per launch
+                  "k_dft_tc": 13.77e9}    # 12.03 GB read + 1.74 GB write per 512-level launch
 
 
 def _args():
@@ -233,6 +233,49 @@ def _workload(c, extra=None):
     if extra:
         cfg.update(extra)
     return cfg
+
+
+def variants_bench(torch, egh, ctx, c, v_start, resid, mult, stream, ev):
+    """The paper's cheaper forms on the benchmark workload, after the timed steps (not part of
+    the headline): Green functions of a band-limited source with the transform decimated 10x in
+    time (its Hessian against the Dirac one), the diagonal-Hessian deblur, and a Hessian of 100
+    receivers drawn one per subset."""
+    import numpy as np
+
+    import synth
+
+    def timed(fn):
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    Qd = ctx.get_hessian(False)
+    w = synth.ricker(250, c.dt, 8.0, t0=0.125).astype(np.float32)
+    decim = 10
+    g_ms = timed(lambda: ctx.green_bandlimited(v_start, w, decim))
+    st = ctx.stats()
+    ctx.hessian(egh.EGH_MU_REL_MEANDIAG, c.mu_alpha)
+    Qb = ctx.get_hessian(False)
+    err = [float(np.linalg.norm(Qb[k] - Qd[k]) / np.linalg.norm(Qd[k])) for k in range(Qd.shape[0])]
+    diag_ms = timed(lambda: ctx.deblur_diag(resid, mult))
+    sel = egh.sample_receivers(c.rec_ix.size, 100, seed=2025, iteration=0)
+    with egh.Context(c.nz, c.nx, c.dz, c.dx, c.nsponge, c.sponge_R, c.dt, c.nt, c.rec_iz[sel],
+                     c.rec_ix[sel], c.freqs, precision=egh.EGH_PREC_MIXED) as c100:
+        c100.green(v_start)
+        sub_green = timed(lambda: c100.green(v_start))
+        sub_hf = timed(lambda: (c100.hessian(egh.EGH_MU_REL_MEANDIAG, c.mu_alpha), c100.factor()))
+    return {
+        "bandlimited_decimated": {
+            "wavelet": "Ricker 8 Hz, 250 samples", "decim": decim, "green_ms": g_ms,
+            "green_fd_ms": st["fd_ms"], "green_transform_ms": st["dft_ms"],
+            "hessian_rel_err_vs_dirac_max": max(err), "hessian_rel_err_vs_dirac_min": min(err)},
+        "diagonal_hessian_deblur_ms": diag_ms,
+        "random_receivers_100": {"green_ms": sub_green, "hessian_factor_ms": sub_hf,
+                                 "receivers": "one per subset of 231, SplitMix64 seed 2025"},
+    }
 
 
 def serve_bench(torch, egh, precision, requests=240, seed=11):
@@ -545,6 +588,9 @@ def run_ours(args):
                 hf.append(e0.elapsed_time(e1))
             other = {"precision": "fp32" if alt == egh.EGH_PREC_FP32 else "mixed",
                      "hessian_factor_ms": min(hf)}
+    variants = None
+    if not args.slice and not args.no_serving:
+        variants = variants_bench(torch, egh, ctx, c, v_start, resid, mult, stream, ev)
     line = {
         "metric": METRIC, "value": bf_s_max / ws, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
@@ -561,6 +607,7 @@ def run_ours(args):
         "deblur_sources_per_s": ns / (statistics.mean(deb_ms) / 1e3),
         "other_precision": other or None,
         "serving": serving,
+        "variants": variants,
         "roofline": {"kernel": "k_fd_step (FD step, 60% of the update)", "bound": "hbm",
                      "achieved": fd_achieved, "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": fd_achieved / hbm,
