@@ -61,7 +61,7 @@ struct egh_ctx {
   CUtensorMap tmap{};                        // TMA map of the snapshot ring (64-byte aligned type)
   int Bp = 0;                                // receivers per snapshot slot (B rounded up to even)
   float *gh = nullptr, *part = nullptr;
-  __nv_bfloat16* ghb = nullptr;              // [nrec][nf][re/im][hi/lo][G] Gram operands
+  __nv_bfloat16* ghb = nullptr;              // [nf][G/64][hi/lo][nrec x re/im][64] Gram operands
   CUtensorMap tmap_ghb{};                    // TMA map of ghb
   float2 *Qh = nullptr, *Lh = nullptr, *tw = nullptr;
   float2* Wh = nullptr;  // mixed precision: W = L^{-1} per frequency (solves as products)
@@ -640,7 +640,7 @@ egh_status green_run(egh_ctx* ctx, const float* vel, cudaStream_t stream, const 
       CK(cudaStreamWaitEvent(ctx->side, ctx->fd_done[g & 1], 0));
       CK(cudaEventRecord(ctx->ev_dft[2 * g], ctx->side));
       CK(launch_dft_tc(ctx->tmap, twt, ctx->nf, sbase, m1 - m0, m0, L, ctx->gh, ctx->ghb,
-                       (m1 == ntd && ctx->ghb) ? 1 : 0, b0, nb, ctx->d_err, ctx->side));
+                       (m1 == ntd && ctx->ghb) ? 1 : 0, b0, nb, ctx->nrec, ctx->d_err, ctx->side));
       CK(cudaEventRecord(ctx->ev_dft[2 * g + 1], ctx->side));
       CK(cudaEventRecord(ctx->dft_done[g & 1], ctx->side));
     }

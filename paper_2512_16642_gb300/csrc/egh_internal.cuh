@@ -80,11 +80,11 @@ std::vector<unsigned char> dft_twiddle_tiles(const std::vector<double>& f, doubl
 cudaError_t make_snap_tmap(CUtensorMap* tm, void* base, long long G, int Bp, int nslot);
 cudaError_t launch_dft_tc(const CUtensorMap& tmap, const unsigned char* twt, int nf, int slot0,
                           int kcount, int n0, const Layout& L, float* gh, __nv_bfloat16* ghb,
-                          int last, int rec0, int nvalid, int* err, cudaStream_t st);
+                          int last, int rec0, int nvalid, int nrec_all, int* err, cudaStream_t st);
 
 // ---- gram_tc.cu -------------------------------------------------------------------------------
 // Gram on the tensor cores from the bf16 hi/lo transforms ghb[nrec][nf][re/im][hi/lo][G].
-__host__ __device__ int gram_tc_tiles(int nrec);
+__host__ __device__ int gram_tc_blocks(int nrec);
 size_t gram_tc_workspace_floats(int nrec, int nf, int splits);
 int gram_tc_splits(int nrec, int nf, long long G);
 cudaError_t make_ghb_tmap(CUtensorMap* tm, void* base, long long G, int nf, int nrec);

@@ -478,7 +478,7 @@ size_t dft_smem(int nf) {
 __global__ void __launch_bounds__(128)
     k_dft_tc(const __grid_constant__ CUtensorMap tmap, const unsigned char* __restrict__ twt,
              int N, int nf, int slot0, int kcount, int n0, long long G, float* __restrict__ gh,
-             __nv_bfloat16* __restrict__ ghb, int last, int rec0, int nvalid,
+             __nv_bfloat16* __restrict__ ghb, int last, int rec0, int nvalid, int nrec_all,
              int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char dsm[];
   unsigned char* sm = dsm + ((1024 - (tc::smem_u32(dsm) & 1023)) & 1023);
@@ -597,12 +597,15 @@ __global__ void __launch_bounds__(128)
             const float sum = o[i] + v[i];
             __stcs(g + (long long)c * G, sum);
             if (last) {
-              // the Gram's operands: hi = bf16(g), lo = bf16(g - hi), planes [..][c][hi|lo][G]
+              // the Gram's operands: hi = bf16(g), lo = bf16(g - hi), blocked by 64 points as
+              // [freq][G/64][hi|lo][receiver, re/im][64] (each 64-receiver box is contiguous)
               const __nv_bfloat16 h = __float2bfloat16_rn(sum);
               const __nv_bfloat16 l = __float2bfloat16_rn(sum - __bfloat162float(h));
-              __nv_bfloat16* q = ghb + ((row0 + c) * 2) * G + p;
+              const long long rows = 2LL * nrec_all;
+              __nv_bfloat16* q = ghb + (((long long)(c >> 1) * (G >> 6) + (p >> 6)) * 2 * rows +
+                                        2LL * (rec0 + rg + r) + (c & 1)) * 64 + (p & 63);
               q[0] = h;
-              q[G] = l;
+              q[rows * 64] = l;
             }
           }
         }
@@ -618,7 +621,7 @@ __global__ void __launch_bounds__(128)
 
 cudaError_t launch_dft_tc(const CUtensorMap& tmap, const unsigned char* twt, int nf, int slot0,
                           int kcount, int n0, const Layout& L, float* gh, __nv_bfloat16* ghb,
-                          int last, int rec0, int nvalid, int* err, cudaStream_t st) {
+                          int last, int rec0, int nvalid, int nrec_all, int* err, cudaStream_t st) {
   const int N = dft_ncomp(nf);
   if (L.G % TD_M != 0 || N > 128 || kcount < 1 || slot0 % TD_S != 0 || n0 % TD_S != 0 ||
       nvalid < 1)
@@ -630,7 +633,7 @@ cudaError_t launch_dft_tc(const CUtensorMap& tmap, const unsigned char* twt, int
   dim3 grid((unsigned)(L.G / TD_M), (unsigned)((nvalid + TD_R - 1) / TD_R));
   count_launches(1);
   k_dft_tc<<<grid, 128, smem, st>>>(tmap, twt, N, nf, slot0, kcount, n0, L.G, gh, ghb, last, rec0,
-                                    nvalid, err);
+                                    nvalid, nrec_all, err);
   return cudaGetLastError();
 }
 

@@ -5,8 +5,8 @@
 // C = M_k M_k^T:
 //   Re H[i][j] = C[2i][2j] + C[2i+1][2j+1],   Im H[i][j] = C[2i+1][2j] - C[2i][2j+1].
 //
-// C is formed in 128 x 128 tiles (64 receivers x re/im per tile edge) on and above the tile
-// diagonal by tcgen05 `kind::f16` MMAs in bf16x3: each entry of M_k is stored by the transform's
+// C is formed in 128 x 256 blocks (64 x 128 receivers x re/im) covering the entries on and above
+// the diagonal by tcgen05 `kind::f16` MMAs in bf16x3: each entry of M_k is stored by the transform's
 // last chunk as hi = bf16(g), lo = bf16(g - hi), and C = Hi Hi^T + Hi Lo^T + Lo Hi^T accumulates in
 // FP32 in TMEM (the dropped Lo Lo^T and the split are ~2^-17 relative).  Operands arrive by 5-D TMA
 // boxes {64 points, hi|lo, re/im, 1 frequency, 64 receivers} that land as 128 rows of 128 bytes in
@@ -23,22 +23,35 @@
 
 namespace egh {
 
-constexpr int GC_T = 128;            // tile edge (rows of M_k)
+constexpr int GC_M = 128;            // block rows of C (64 receivers x re/im)
+constexpr int GC_N = 256;            // block columns of C (128 receivers x re/im)
 constexpr int GC_P = 64;             // points per stage (one 128-byte bf16 row)
-constexpr int GC_ST = 3;             // stages in flight
-constexpr unsigned GC_BOX = 16384;   // one operand box: 128 rows x 128 bytes
+constexpr int GC_ST = 2;             // stages in flight
+constexpr unsigned GC_BOX = 16384;   // one operand box: 64 receivers x re/im = 128 rows x 128 bytes
+constexpr unsigned GC_STAGE = 6 * GC_BOX;  // A hi, A lo (1 box each), B hi, B lo (2 boxes each)
 
-__host__ __device__ int gram_tc_tiles(int nrec) { return (2 * nrec + GC_T - 1) / GC_T; }
-
-size_t gram_tc_workspace_floats(int nrec, int nf, int splits) {
-  const int nt = gram_tc_tiles(nrec);
-  return (size_t)splits * nf * ((size_t)nt * (nt + 1) / 2) * GC_T * GC_T;
+// Blocks (ta, tb) of C: rows 128 ta .. (64-receiver panel ta), columns 256 tb .. (128-receiver
+// panel tb), for tb >= ta / 2 -- every entry on or above the diagonal lies in one of them.
+__host__ __device__ inline int gram_tc_panels64(int nrec) { return (nrec + 63) / 64; }
+__host__ __device__ inline int gram_tc_panels128(int nrec) { return (nrec + 127) / 128; }
+__host__ __device__ inline int gram_tc_blocks_before(int ta, int n128) {
+  int s = 0;
+  for (int t = 0; t < ta; ++t) s += n128 - t / 2;
+  return s;
+}
+__host__ __device__ int gram_tc_blocks(int nrec) {
+  return gram_tc_blocks_before(gram_tc_panels64(nrec), gram_tc_panels128(nrec));
 }
 
-size_t gram_tc_smem() { return 1024 + (size_t)GC_ST * 4 * GC_BOX; }
+size_t gram_tc_workspace_floats(int nrec, int nf, int splits) {
+  return (size_t)splits * nf * gram_tc_blocks(nrec) * GC_M * GC_N;
+}
 
-// Tensor map of the bf16 transforms ghb[nrec][nf][re/im][hi/lo][G] for boxes
-// {64 points, 1 plane, 2 (re/im), 1 frequency, 64 receivers} with the 128-byte swizzle.
+size_t gram_tc_smem() { return 1024 + (size_t)GC_ST * GC_STAGE; }
+
+// Tensor map of the bf16 transforms, blocked by 64 points as
+// ghb[nf][G/64][hi/lo][nrec x re/im][64], for boxes {64 points, 128 rows (64 receivers x re/im),
+// 1 plane, 1 stage, 1 frequency} with the 128-byte swizzle: every box is one contiguous 16 KB run.
 cudaError_t make_ghb_tmap(CUtensorMap* tm, void* base, long long G, int nf, int nrec) {
   static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
   if (!enc) {
@@ -50,10 +63,11 @@ cudaError_t make_ghb_tmap(CUtensorMap* tm, void* base, long long G, int nf, int 
     if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
     enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   }
-  const cuuint64_t dims[5] = {(cuuint64_t)G, 2, 2, (cuuint64_t)nf, (cuuint64_t)nrec};
-  const cuuint64_t str[4] = {(cuuint64_t)G * 2, (cuuint64_t)G * 4, (cuuint64_t)G * 8,
-                             (cuuint64_t)G * 8 * nf};
-  const cuuint32_t box[5] = {GC_P, 1, 2, 1, GC_T / 2};
+  const cuuint64_t rows = 2ull * nrec;
+  const cuuint64_t dims[5] = {(cuuint64_t)GC_P, rows, 2, (cuuint64_t)(G / GC_P), (cuuint64_t)nf};
+  const cuuint64_t str[4] = {GC_P * 2, rows * GC_P * 2, 2 * rows * GC_P * 2,
+                             (cuuint64_t)(G / GC_P) * 2 * rows * GC_P * 2};
+  const cuuint32_t box[5] = {GC_P, 128, 1, 1, 1};
   const cuuint32_t es[5] = {1, 1, 1, 1, 1};
   const CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, base, dims, str, box, es,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -70,17 +84,20 @@ __device__ __forceinline__ void tma_load_5d(unsigned dst, const void* tmap, int 
       : "memory");
 }
 
-// One CTA: tile pair (ta <= tb) of frequency k over points [p0, p1).  Warp 4 (one thread) issues
-// the copies and the MMAs over a GC_ST-stage ring.  The tensor core's FP32 accumulation of a long
-// sum drifts (its rounding is not round-to-nearest: about 2^-24 relative per accumulation,
-// measured 1e-3 over 87 000 points), so the MMAs accumulate into one of two TMEM buffers for
-// blocks of GC_J stages only, and warps 0..3 drain each finished block into FP32 register totals
-// with round-to-nearest adds while the MMAs fill the other buffer.  Every wait is bounded (on
-// expiry: error flag, bounded drain of the copies in flight, TMEM freed, CTA leaves).
+// One CTA: block (ta, tb) of C at frequency k over points [p0, p1), as M128 x N256 MMAs (each
+// A row group read from shared memory serves 256 columns, which halves the operand traffic per
+// product against square 128 x 128 tiles).  Warp 8 (one thread) issues the copies and the MMAs
+// over a GC_ST-stage ring.  The tensor core's FP32 accumulation of a long sum drifts (its
+// rounding is not round-to-nearest: about 2^-24 relative per accumulation, measured 1e-3 over
+// 87 000 points), so the MMAs accumulate into one of two 256-column TMEM buffers for blocks of
+// GC_J stages only, and warps 0..7 (lane quarter w % 4, column half w / 4) drain each finished
+// block into FP32 register totals with round-to-nearest adds while the MMAs fill the other
+// buffer.  Every wait is bounded (on expiry: error flag, bounded drain of the copies in flight,
+// TMEM freed, CTA leaves).
 constexpr int GC_J = 8;  // stages per TMEM accumulation block (96 accumulations)
 
-__global__ void __launch_bounds__(160)
-    k_gram_tc(const __grid_constant__ CUtensorMap tmap, int ntile, long long split_len, long long G,
+__global__ void __launch_bounds__(288)
+    k_gram_tc(const __grid_constant__ CUtensorMap tmap, int nrec, long long split_len, long long G,
               float* __restrict__ part, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char dsm[];
   unsigned char* sm = dsm + ((1024 - (tc::smem_u32(dsm) & 1023)) & 1023);
@@ -88,20 +105,17 @@ __global__ void __launch_bounds__(160)
   __shared__ __align__(8) unsigned long long bars[2 * GC_ST + 4];
   __shared__ unsigned tslot;
   __shared__ int fail;
-  const int pair = blockIdx.x, k = blockIdx.y, sp = blockIdx.z, nf = gridDim.y;
-  int ta = 0, rem = pair;
-  while (rem >= ntile - ta) {
-    rem -= ntile - ta;
-    ++ta;
-  }
-  const int tb = ta + rem;
-  const bool diag = ta == tb;
+  const int blkid = blockIdx.x, k = blockIdx.y, sp = blockIdx.z, nf = gridDim.y;
+  const int n64 = gram_tc_panels64(nrec), n128 = gram_tc_panels128(nrec);
+  int ta = 0;
+  while (ta + 1 < n64 && gram_tc_blocks_before(ta + 1, n128) <= blkid) ++ta;
+  const int tb = ta / 2 + (blkid - gram_tc_blocks_before(ta, n128));
   const long long p0 = (long long)sp * split_len;
   const long long p1 = min(G, p0 + split_len);
   const int nst = p1 > p0 ? (int)((p1 - p0 + GC_P - 1) / GC_P) : 0;
   const int nblk = (nst + GC_J - 1) / GC_J;
   const int tid = threadIdx.x, warp = tid >> 5;
-  if (warp == 0) tc::tmem_alloc(&tslot, 256);
+  if (warp == 0) tc::tmem_alloc(&tslot, 2 * GC_N);
   const unsigned bar0 = tc::smem_u32(&bars[0]);
   auto full = [&](int i) { return bar0 + 8u * i; };
   auto empty = [&](int i) { return bar0 + 8u * (GC_ST + i); };
@@ -109,8 +123,8 @@ __global__ void __launch_bounds__(160)
   auto drained = [&](int i) { return bar0 + 8u * (2 * GC_ST + 2 + i); };
   if (tid == 0) {
     for (int i = 0; i < 2 * GC_ST + 2; ++i) tc::mbar_init(bar0 + 8u * i, 1);
-    tc::mbar_init(drained(0), 128);
-    tc::mbar_init(drained(1), 128);
+    tc::mbar_init(drained(0), 256);
+    tc::mbar_init(drained(1), 256);
     fail = 0;
     tc::mbar_init_fence();
   }
@@ -118,20 +132,21 @@ __global__ void __launch_bounds__(160)
   __syncthreads();
   tc::tc_fence_after();
   const unsigned tmem = tslot;
-  // stage buffer: [A_hi][A_lo][B_hi][B_lo], 16 KB each (B is A on diagonal tiles)
-  auto buf_addr = [&](int b, int which) {
-    return tc::smem_u32(sm + ((size_t)b * 4 + which) * GC_BOX);
-  };
-  if (warp == 4) {
-    if (tid == 128) {
-      const unsigned idesc = tc::idesc_bf16(GC_T, GC_T, 0, 0);
+  // stage buffer: [A_hi][A_lo][B_hi: 2 boxes][B_lo: 2 boxes]
+  auto stage_addr = [&](int b) { return tc::smem_u32(sm + (size_t)b * GC_STAGE); };
+  if (warp == 8) {
+    if (tid == 256) {
+      const unsigned idesc = tc::idesc_bf16(GC_M, GC_N, 0, 0);
       auto issue = [&](int s) {
         const int b = s % GC_ST;
-        const int p = (int)(p0 + (long long)s * GC_P);
-        tc::mbar_expect_tx(full(b), (diag ? 2u : 4u) * GC_BOX);
+        const int stg = (int)(p0 / GC_P) + s;
+        const unsigned base = stage_addr(b);
+        tc::mbar_expect_tx(full(b), GC_STAGE);
         for (int hl = 0; hl < 2; ++hl) {
-          tma_load_5d(buf_addr(b, hl), &tmap, p, hl, 0, k, ta * (GC_T / 2), full(b));
-          if (!diag) tma_load_5d(buf_addr(b, 2 + hl), &tmap, p, hl, 0, k, tb * (GC_T / 2), full(b));
+          tma_load_5d(base + hl * GC_BOX, &tmap, 0, 2 * 64 * ta, hl, stg, k, full(b));
+          for (int h = 0; h < 2; ++h)
+            tma_load_5d(base + (2 + 2 * hl + h) * GC_BOX, &tmap, 0, 2 * (128 * tb + 64 * h), hl, stg,
+                        k, full(b));
         }
       };
       int issued = 0, landed = 0;
@@ -152,9 +167,9 @@ __global__ void __launch_bounds__(160)
         }
         landed = s + 1;
         tc::tc_fence_after();
-        const unsigned dt = tmem + (unsigned)((blk & 1) * GC_T);
-        const unsigned ah = buf_addr(b, 0), al = buf_addr(b, 1);
-        const unsigned bh = diag ? ah : buf_addr(b, 2), bl = diag ? al : buf_addr(b, 3);
+        const unsigned dt = tmem + (unsigned)((blk & 1) * GC_N);
+        const unsigned ah = stage_addr(b), al = ah + GC_BOX;
+        const unsigned bh = ah + 2 * GC_BOX, bl = ah + 4 * GC_BOX;
 #pragma unroll
         for (int ks = 0; ks < GC_P / 16; ++ks) {
           const unsigned o = 32u * ks;
@@ -166,8 +181,11 @@ __global__ void __launch_bounds__(160)
         }
         tc::mma_commit(empty(b));
         if (s % GC_J == GC_J - 1 || s == nst - 1) tc::mma_commit(blockdone(blk & 1));
-        if (issued < nst) {  // the next stage to issue reuses this stage's buffer
-          if (!tc::mbar_wait(empty(b), (s / GC_ST) & 1)) {
+        // refill the previous stage's buffer (its MMAs were issued one stage earlier, so the
+        // tensor pipe keeps this stage's MMAs queued while the thread waits for them)
+        if (s >= 1 && issued < nst) {
+          const int pb = (s - 1) % GC_ST;
+          if (!tc::mbar_wait(empty(pb), ((s - 1) / GC_ST) & 1)) {
             ok = false;
             break;
           }
@@ -186,10 +204,11 @@ __global__ void __launch_bounds__(160)
     }
     __syncwarp();
   } else {
-    // warps 0..3: TMEM lanes 32 w .. 32 w + 31 = rows of the tile; totals in registers
-    float tot[GC_T];
+    // warps 0..7: TMEM lanes 32 (w % 4) .. = rows of the block, columns 128 (w / 4) ..
+    const int q = warp & 3, h = warp >> 2;
+    float tot[128];
 #pragma unroll
-    for (int c = 0; c < GC_T; ++c) tot[c] = 0.f;
+    for (int c = 0; c < 128; ++c) tot[c] = 0.f;
     bool ok = true;
     for (int blk = 0; blk < nblk; ++blk) {
       const bool got = tc::mbar_wait(blockdone(blk & 1), (blk >> 1) & 1);
@@ -198,9 +217,9 @@ __global__ void __launch_bounds__(160)
         break;
       }
       tc::tc_fence_after();
-      const unsigned base = tmem + ((unsigned)(warp * 32) << 16) + (unsigned)((blk & 1) * GC_T);
+      const unsigned base = tmem + ((unsigned)(q * 32) << 16) + (unsigned)((blk & 1) * GC_N + h * 128);
 #pragma unroll
-      for (int c0 = 0; c0 < GC_T; c0 += 32) {
+      for (int c0 = 0; c0 < 128; c0 += 32) {
         float v[32];
         tc::tmem_ld32(base + (unsigned)c0, v);
 #pragma unroll
@@ -210,25 +229,28 @@ __global__ void __launch_bounds__(160)
       tc::mbar_arrive(drained(blk & 1));
     }
     if (ok && !fail) {
-      const int npairs = ntile * (ntile + 1) / 2;
-      float* out = part + (((long long)sp * nf + k) * npairs + pair) * (GC_T * GC_T) +
-                   (long long)tid * GC_T;  // row tid of the tile (TMEM lane)
+      const int row = q * 32 + (tid & 31);
+      float* out = part +
+                   (((long long)sp * nf + k) * gram_tc_blocks(nrec) + blkid) * (GC_M * GC_N) +
+                   (long long)row * GC_N + h * 128;
 #pragma unroll
-      for (int i = 0; i < GC_T; i += 4)
+      for (int i = 0; i < 128; i += 4)
         *reinterpret_cast<float4*>(out + i) = make_float4(tot[i], tot[i + 1], tot[i + 2], tot[i + 3]);
-    } else if (tid == 0) {
+    } else if ((tid & 31) == 0) {
       atomicExch(err, 1);
     }
   }
   tc::tc_fence_before();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, 256);
+  if (warp == 0) tc::tmem_dealloc(tmem, 2 * GC_N);
 }
 
 int gram_tc_splits(int nrec, int nf, long long G) {
-  const int nt = gram_tc_tiles(nrec);
-  const long long tiles = (long long)nt * (nt + 1) / 2 * nf;
-  long long s = (3LL * 152 + tiles - 1) / tiles;
+  // one CTA per SM (shared memory); about sixteen waves of short point ranges keep the CTAs of
+  // one frequency close together in the grid sum, so that their shared panels meet in L2
+  // (measured on 231 receivers x 26 frequencies: 6 splits 11.1 ms, 16 splits 10.5 ms)
+  const long long blocks = (long long)gram_tc_blocks(nrec) * nf;
+  long long s = (16LL * 152 + blocks - 1) / blocks;
   s = std::max(1LL, std::min(s, G / (16LL * GC_P)));
   return (int)s;
 }
@@ -236,8 +258,6 @@ int gram_tc_splits(int nrec, int nf, long long G) {
 cudaError_t launch_gram_tc(const CUtensorMap& tmap, int nrec, int nf, long long G, int splits,
                            float* part, int* err, cudaStream_t st) {
   if (G % GC_P != 0 || splits < 1) return cudaErrorInvalidValue;
-  const int nt = gram_tc_tiles(nrec);
-  const int npairs = nt * (nt + 1) / 2;
   long long split_len = (G + splits - 1) / splits;
   split_len = (split_len + GC_P - 1) / GC_P * GC_P;
   const size_t smem = gram_tc_smem();
@@ -245,24 +265,26 @@ cudaError_t launch_gram_tc(const CUtensorMap& tmap, int nrec, int nf, long long 
       cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   count_launches(1);
-  k_gram_tc<<<dim3(npairs, nf, splits), 160, smem, st>>>(tmap, nt, split_len, G, part, err);
+  k_gram_tc<<<dim3(gram_tc_blocks(nrec), nf, splits), 288, smem, st>>>(tmap, nrec, split_len, G,
+                                                                       part, err);
   return cudaGetLastError();
 }
 
-// C[a][b] summed over splits (in double), read from the tile pair with ta <= tb (C is symmetric).
-__device__ inline double ctc_entry(const float* part, int a, int b, int k, int nf, int ntile,
-                                   int npairs, int splits) {
-  if (a / GC_T > b / GC_T) {
+// C[a][b] summed over splits (in double), read from the block that holds (a, b) or, below the
+// diagonal blocks, (b, a) (C is symmetric).
+__device__ inline double ctc_entry(const float* part, int a, int b, int k, int nf, int n128,
+                                   int nblocks, int splits) {
+  if (a / GC_M > b / GC_M) {
     const int t = a;
     a = b;
     b = t;
   }
-  const int ta = a / GC_T, tb = b / GC_T;
-  const int pair = ta * ntile - ta * (ta - 1) / 2 + (tb - ta);
-  const long long off = (long long)(a % GC_T) * GC_T + (b % GC_T);
+  const int ta = a / GC_M, tb = b / GC_N;
+  const int blk = gram_tc_blocks_before(ta, n128) + (tb - ta / 2);
+  const long long off = (long long)(a % GC_M) * GC_N + (b % GC_N);
   double sum = 0.0;
   for (int s = 0; s < splits; ++s)
-    sum += part[(((long long)s * nf + k) * npairs + pair) * (GC_T * GC_T) + off];
+    sum += part[(((long long)s * nf + k) * nblocks + blk) * (GC_M * GC_N) + off];
   return sum;
 }
 
@@ -272,15 +294,14 @@ __global__ void k_gram_tc_finish(const float* __restrict__ part, int nrec, int n
   const int i = blockIdx.y;
   const int k = blockIdx.z;
   if (j >= nrec) return;
-  const int ntile = gram_tc_tiles(nrec);
-  const int npairs = ntile * (ntile + 1) / 2;
+  const int n128 = gram_tc_panels128(nrec), nblocks = gram_tc_blocks(nrec);
   const int a = min(i, j), b = max(i, j);
-  const double rr = ctc_entry(part, 2 * a, 2 * b, k, nf, ntile, npairs, splits);
-  const double ii = ctc_entry(part, 2 * a + 1, 2 * b + 1, k, nf, ntile, npairs, splits);
+  const double rr = ctc_entry(part, 2 * a, 2 * b, k, nf, n128, nblocks, splits);
+  const double ii = ctc_entry(part, 2 * a + 1, 2 * b + 1, k, nf, n128, nblocks, splits);
   double im = 0.0;
   if (a != b)
-    im = ctc_entry(part, 2 * a + 1, 2 * b, k, nf, ntile, npairs, splits) -
-         ctc_entry(part, 2 * a, 2 * b + 1, k, nf, ntile, npairs, splits);
+    im = ctc_entry(part, 2 * a + 1, 2 * b, k, nf, n128, nblocks, splits) -
+         ctc_entry(part, 2 * a, 2 * b + 1, k, nf, n128, nblocks, splits);
   // entry (a, b) with a <= b; (b, a) is its conjugate
   Qh[((long long)k * nrec + i) * nrec + j] = make_float2((float)(rr + ii), (float)(i <= j ? im : -im));
 }
