@@ -5,8 +5,9 @@
 // C = M_k M_k^T:
 //   Re H[i][j] = C[2i][2j] + C[2i+1][2j+1],   Im H[i][j] = C[2i+1][2j] - C[2i][2j+1].
 //
-// C is formed in 128 x 256 blocks (64 x 128 receivers x re/im) covering the entries on and above
-// the diagonal by tcgen05 `kind::f16` MMAs in bf16x3: each entry of M_k is stored by the transform's
+// C is formed in 128 x 256 blocks (64 x 128 receivers x re/im; 128 x 128 at the last panel)
+// covering exactly the panel pairs on and above the diagonal, by tcgen05 `kind::f16` MMAs in
+// bf16x3: each entry of M_k is stored by the transform's
 // last chunk as hi = bf16(g), lo = bf16(g - hi), and C = Hi Hi^T + Hi Lo^T + Lo Hi^T accumulates in
 // FP32 in TMEM (the dropped Lo Lo^T and the split are ~2^-17 relative).  Operands arrive by 5-D TMA
 // boxes {64 points, hi|lo, re/im, 1 frequency, 64 receivers} that land as 128 rows of 128 bytes in
@@ -30,17 +31,19 @@ constexpr int GC_ST = 2;             // stages in flight
 constexpr unsigned GC_BOX = 16384;   // one operand box: 64 receivers x re/im = 128 rows x 128 bytes
 constexpr unsigned GC_STAGE = 6 * GC_BOX;  // A hi, A lo (1 box each), B hi, B lo (2 boxes each)
 
-// Blocks (ta, tb) of C: rows 128 ta .. (64-receiver panel ta), columns 256 tb .. (128-receiver
-// panel tb), for tb >= ta / 2 -- every entry on or above the diagonal lies in one of them.
+// Blocks (ta, j) of C: rows of 64-receiver panel ta (128 rows), columns of panels ta + 2j and
+// ta + 2j + 1 (256 columns; a "half" block when the second panel is past the last), j = 0, 1, ...
+// -- exactly the panel pairs on and above the diagonal.  Block (ta, 0) is "inner": its A panel is
+// the first half of its B panels.
 __host__ __device__ inline int gram_tc_panels64(int nrec) { return (nrec + 63) / 64; }
-__host__ __device__ inline int gram_tc_panels128(int nrec) { return (nrec + 127) / 128; }
-__host__ __device__ inline int gram_tc_blocks_before(int ta, int n128) {
+__host__ __device__ inline int gram_tc_blocks_before(int ta, int n64) {
   int s = 0;
-  for (int t = 0; t < ta; ++t) s += n128 - t / 2;
+  for (int t = 0; t < ta; ++t) s += (n64 - t + 1) / 2;
   return s;
 }
 __host__ __device__ int gram_tc_blocks(int nrec) {
-  return gram_tc_blocks_before(gram_tc_panels64(nrec), gram_tc_panels128(nrec));
+  const int n64 = gram_tc_panels64(nrec);
+  return gram_tc_blocks_before(n64, n64);
 }
 
 size_t gram_tc_workspace_floats(int nrec, int nf, int splits) {
@@ -106,10 +109,12 @@ __global__ void __launch_bounds__(288)
   __shared__ unsigned tslot;
   __shared__ int fail;
   const int blkid = blockIdx.x, k = blockIdx.y, sp = blockIdx.z, nf = gridDim.y;
-  const int n64 = gram_tc_panels64(nrec), n128 = gram_tc_panels128(nrec);
+  const int n64 = gram_tc_panels64(nrec);
   int ta = 0;
-  while (ta + 1 < n64 && gram_tc_blocks_before(ta + 1, n128) <= blkid) ++ta;
-  const int tb = ta / 2 + (blkid - gram_tc_blocks_before(ta, n128));
+  while (ta + 1 < n64 && gram_tc_blocks_before(ta + 1, n64) <= blkid) ++ta;
+  const int bp = ta + 2 * (blkid - gram_tc_blocks_before(ta, n64));  // first B panel
+  const bool inner = bp == ta;         // the A panel is the first half of the B panels
+  const bool half = bp + 1 >= n64;     // one B panel only: N = 128
   const long long p0 = (long long)sp * split_len;
   const long long p1 = min(G, p0 + split_len);
   const int nst = p1 > p0 ? (int)((p1 - p0 + GC_P - 1) / GC_P) : 0;
@@ -136,17 +141,17 @@ __global__ void __launch_bounds__(288)
   auto stage_addr = [&](int b) { return tc::smem_u32(sm + (size_t)b * GC_STAGE); };
   if (warp == 8) {
     if (tid == 256) {
-      const unsigned idesc = tc::idesc_bf16(GC_M, GC_N, 0, 0);
+      const unsigned idesc = tc::idesc_bf16(GC_M, half ? GC_N / 2 : GC_N, 0, 0);
       auto issue = [&](int s) {
         const int b = s % GC_ST;
         const int stg = (int)(p0 / GC_P) + s;
         const unsigned base = stage_addr(b);
-        tc::mbar_expect_tx(full(b), GC_STAGE);
+        tc::mbar_expect_tx(full(b), (unsigned)((inner ? 0 : 2) + (half ? 2 : 4)) * GC_BOX);
         for (int hl = 0; hl < 2; ++hl) {
-          tma_load_5d(base + hl * GC_BOX, &tmap, 0, 2 * 64 * ta, hl, stg, k, full(b));
-          for (int h = 0; h < 2; ++h)
-            tma_load_5d(base + (2 + 2 * hl + h) * GC_BOX, &tmap, 0, 2 * (128 * tb + 64 * h), hl, stg,
-                        k, full(b));
+          if (!inner) tma_load_5d(base + hl * GC_BOX, &tmap, 0, 2 * 64 * ta, hl, stg, k, full(b));
+          for (int h = 0; h < (half ? 1 : 2); ++h)
+            tma_load_5d(base + (2 + 2 * hl + h) * GC_BOX, &tmap, 0, 2 * 64 * (bp + h), hl, stg, k,
+                        full(b));
         }
       };
       int issued = 0, landed = 0;
@@ -168,8 +173,10 @@ __global__ void __launch_bounds__(288)
         landed = s + 1;
         tc::tc_fence_after();
         const unsigned dt = tmem + (unsigned)((blk & 1) * GC_N);
-        const unsigned ah = stage_addr(b), al = ah + GC_BOX;
-        const unsigned bh = ah + 2 * GC_BOX, bl = ah + 4 * GC_BOX;
+        const unsigned bh = stage_addr(b) + 2 * GC_BOX, bl = stage_addr(b) + 4 * GC_BOX;
+        // an inner block's A rows are the first 128 B rows
+        const unsigned ah = inner ? bh : stage_addr(b);
+        const unsigned al = inner ? bl : ah + GC_BOX;
 #pragma unroll
         for (int ks = 0; ks < GC_P / 16; ++ks) {
           const unsigned o = 32u * ks;
@@ -210,6 +217,7 @@ __global__ void __launch_bounds__(288)
 #pragma unroll
     for (int c = 0; c < 128; ++c) tot[c] = 0.f;
     bool ok = true;
+    const bool idle = half && h == 1;  // columns past the last panel: nothing to drain
     for (int blk = 0; blk < nblk; ++blk) {
       const bool got = tc::mbar_wait(blockdone(blk & 1), (blk >> 1) & 1);
       if (!__all_sync(0xffffffffu, got && !fail)) {  // warp-uniform: TMEM loads are collective
@@ -217,18 +225,21 @@ __global__ void __launch_bounds__(288)
         break;
       }
       tc::tc_fence_after();
-      const unsigned base = tmem + ((unsigned)(q * 32) << 16) + (unsigned)((blk & 1) * GC_N + h * 128);
+      if (!idle) {
+        const unsigned base =
+            tmem + ((unsigned)(q * 32) << 16) + (unsigned)((blk & 1) * GC_N + h * 128);
 #pragma unroll
-      for (int c0 = 0; c0 < 128; c0 += 32) {
-        float v[32];
-        tc::tmem_ld32(base + (unsigned)c0, v);
+        for (int c0 = 0; c0 < 128; c0 += 32) {
+          float v[32];
+          tc::tmem_ld32(base + (unsigned)c0, v);
 #pragma unroll
-        for (int i = 0; i < 32; ++i) tot[c0 + i] += v[i];
+          for (int i = 0; i < 32; ++i) tot[c0 + i] += v[i];
+        }
       }
       tc::tc_fence_before();
       tc::mbar_arrive(drained(blk & 1));
     }
-    if (ok && !fail) {
+    if (ok && !fail && !idle) {
       const int row = q * 32 + (tid & 31);
       float* out = part +
                    (((long long)sp * nf + k) * gram_tc_blocks(nrec) + blkid) * (GC_M * GC_N) +
@@ -236,7 +247,7 @@ __global__ void __launch_bounds__(288)
 #pragma unroll
       for (int i = 0; i < 128; i += 4)
         *reinterpret_cast<float4*>(out + i) = make_float4(tot[i], tot[i + 1], tot[i + 2], tot[i + 3]);
-    } else if ((tid & 31) == 0) {
+    } else if (!(ok && !fail) && (tid & 31) == 0) {
       atomicExch(err, 1);
     }
   }
@@ -272,16 +283,16 @@ cudaError_t launch_gram_tc(const CUtensorMap& tmap, int nrec, int nf, long long 
 
 // C[a][b] summed over splits (in double), read from the block that holds (a, b) or, below the
 // diagonal blocks, (b, a) (C is symmetric).
-__device__ inline double ctc_entry(const float* part, int a, int b, int k, int nf, int n128,
+__device__ inline double ctc_entry(const float* part, int a, int b, int k, int nf, int n64,
                                    int nblocks, int splits) {
   if (a / GC_M > b / GC_M) {
     const int t = a;
     a = b;
     b = t;
   }
-  const int ta = a / GC_M, tb = b / GC_N;
-  const int blk = gram_tc_blocks_before(ta, n128) + (tb - ta / 2);
-  const long long off = (long long)(a % GC_M) * GC_N + (b % GC_N);
+  const int pa = a / GC_M, pb = b / GC_M;
+  const int blk = gram_tc_blocks_before(pa, n64) + (pb - pa) / 2;
+  const long long off = (long long)(a % GC_M) * GC_N + ((pb - pa) & 1) * GC_M + (b % GC_M);
   double sum = 0.0;
   for (int s = 0; s < splits; ++s)
     sum += part[(((long long)s * nf + k) * nblocks + blk) * (GC_M * GC_N) + off];
@@ -294,14 +305,14 @@ __global__ void k_gram_tc_finish(const float* __restrict__ part, int nrec, int n
   const int i = blockIdx.y;
   const int k = blockIdx.z;
   if (j >= nrec) return;
-  const int n128 = gram_tc_panels128(nrec), nblocks = gram_tc_blocks(nrec);
+  const int n64 = gram_tc_panels64(nrec), nblocks = gram_tc_blocks(nrec);
   const int a = min(i, j), b = max(i, j);
-  const double rr = ctc_entry(part, 2 * a, 2 * b, k, nf, n128, nblocks, splits);
-  const double ii = ctc_entry(part, 2 * a + 1, 2 * b + 1, k, nf, n128, nblocks, splits);
+  const double rr = ctc_entry(part, 2 * a, 2 * b, k, nf, n64, nblocks, splits);
+  const double ii = ctc_entry(part, 2 * a + 1, 2 * b + 1, k, nf, n64, nblocks, splits);
   double im = 0.0;
   if (a != b)
-    im = ctc_entry(part, 2 * a + 1, 2 * b, k, nf, n128, nblocks, splits) -
-         ctc_entry(part, 2 * a, 2 * b + 1, k, nf, n128, nblocks, splits);
+    im = ctc_entry(part, 2 * a + 1, 2 * b, k, nf, n64, nblocks, splits) -
+         ctc_entry(part, 2 * a, 2 * b + 1, k, nf, n64, nblocks, splits);
   // entry (a, b) with a <= b; (b, a) is its conjugate
   Qh[((long long)k * nrec + i) * nrec + j] = make_float2((float)(rr + ii), (float)(i <= j ? im : -im));
 }
