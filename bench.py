@@ -79,6 +79,17 @@ def _peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+def _bf16_peak():
+    """(TFLOP/s, kind): the sustained cuBLAS bf16 figure (the Gram runs inside a long step)."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["bf16_tflops_sustained"]), "measured (sustained)"
+    except Exception:
+        return 1700.0, "fallback (sustained)"
+
+
 # ---------------------------------------------------------------------------------------------
 # clocks during the timed region
 # ---------------------------------------------------------------------------------------------
@@ -233,6 +244,27 @@ def _workload(c, extra=None):
     if extra:
         cfg.update(extra)
     return cfg
+
+
+def gram_roofline(precision, nr, nf, npts, c, ms, peak, kind):
+    """The Gram kernel against the tensor peak (mixed) or as FP32 CUDA-core work (fp32).  Issued
+    tensor work: 64-receiver panel pairs on and above the diagonal, each 128 x 128 x G per
+    frequency, 3 bf16 products (hi hi, hi lo, lo hi); algorithmic work: the Hermitian half of
+    8 Nf Nr^2 G real flops of the complex Gram."""
+    NZ, NX = c.nz + 2 * c.nsponge, c.nx + 2 * c.nsponge
+    PX = max(64, -(-(NX + 4) // 64) * 64)  # row pitch of the device levels
+    G = -(-(NZ * PX) // 256) * 256  # padded point count the Gram sums over
+    n64 = -(-nr // 64)
+    issued = n64 * (n64 + 1) / 2 * 128 * 128 * 2 * 3 * G * nf
+    alg = 8.0 * nf * nr * nr * G * (nr + 1) / (2 * nr)
+    out = {"kernel": "k_gram_tc (bf16x3 tcgen05 Gram)" if precision == "mixed" else "k_gram_partial (FP32)",
+           "ms": ms, "algorithmic_tflops": alg / (ms * 1e-3) / 1e12}
+    if precision == "mixed":
+        out.update({"bound": "tensor", "achieved": issued / (ms * 1e-3) / 1e12, "peak": peak,
+                    "peak_kind": kind, "unit": "TFLOP/s", "frac": issued / (ms * 1e-3) / 1e12 / peak,
+                    "note": "achieved = issued bf16 MMA flops (3 products) / kernel time (CUDA events "
+                            "around the launch inside egh_hessian)"})
+    return out
 
 
 def variants_bench(torch, egh, ctx, c, v_start, resid, mult, stream, ev):
@@ -490,6 +522,8 @@ def run_ours(args):
             kern.append((st_g["fd_ms"], st_g["fd_launches"], st_g["dft_ms"], st_g["dft_launches"]))
         e[1].record(stream)
         ctx.hessian(egh.EGH_MU_REL_MEANDIAG, c.mu_alpha)
+        if rec is not None:
+            gram_ms.append(ctx.stats()["gram_ms"])
         ctx.factor()
         e[2].record(stream)
         ctx.deblur(resid, mult)
@@ -505,7 +539,7 @@ def run_ours(args):
     clk = ClockSampler(local)
     clk.start()
     l0 = ctx.stats()["kernel_launches"]
-    recs, kern = [], []
+    recs, kern, gram_ms = [], [], []
     t_start, t_end = ev(), ev()
     t_start.record(stream)
     for _ in range(args.steps):
@@ -548,6 +582,7 @@ def run_ours(args):
     if rank != 0:
         return
     hbm, peak_kind = _peaks()
+    tc_peak, tc_kind = _bf16_peak()
     point_steps = st["point_steps"]
     green_s = statistics.mean(green_ms) / 1e3
     with open(os.path.join(ROOT, "paper_2512_16642_gb300", "csrc", "fd.cu"), "rb") as f:
@@ -624,6 +659,8 @@ def run_ours(args):
                                "algorithmic_bytes_per_launch": dft_alg, "launches": dft_n,
                                "avg_launch_ms": dft_ms / dft_n,
                                "note": "runs beside the next chunk's FD steps on a low-priority stream"},
+        "roofline_gram": gram_roofline(args.precision, nr, nf, npts, c, statistics.mean(gram_ms),
+                                       tc_peak, tc_kind),
         "green_stage": {"achieved": 12.0 * point_steps / green_s / 1e9, "unit": "GB/s",
                         "frac": 12.0 * point_steps / green_s / 1e9 / hbm,
                         "note": "whole egh_green (FD + transform), 12 B per receiver point-step"},

@@ -137,6 +137,7 @@ typedef struct {
     double dft_ms;             /* last egh_green: device time of the transform launches */
     int64_t fd_launches;       /* last egh_green: FD step launches */
     int64_t dft_launches;      /* last egh_green: transform launches */
+    double gram_ms;            /* last egh_hessian: device time of the Gram kernel */
 } egh_stats;
 
 /* Validates the configuration and allocates the device state on the current

@@ -73,6 +73,7 @@ struct egh_ctx {
   std::map<std::tuple<int, int, int, int, int, int, int>, cudaGraphExec_t> fd_graphs;
   cudaEvent_t fd_done[2] = {}, dft_done[2] = {}, ev_side = nullptr;
   cudaEvent_t ev_tune[2] = {};                 // FD rows-per-warp timing
+  cudaEvent_t ev_gram[2] = {};                 // the Gram kernel in the last egh_hessian
   // per-chunk start/end events of the FD steps and of the transform in the last egh_green
   std::vector<cudaEvent_t> ev_fd, ev_dft;
   long long fd_launches = 0, dft_launches = 0;
@@ -269,7 +270,7 @@ void free_all(egh_ctx* c) {
   for (cudaEvent_t& e : c->ev)
     if (e) cudaEventDestroy(e);
   for (cudaEvent_t e : {c->fd_done[0], c->fd_done[1], c->dft_done[0], c->dft_done[1], c->ev_side,
-                        c->ev_tune[0], c->ev_tune[1]})
+                        c->ev_tune[0], c->ev_tune[1], c->ev_gram[0], c->ev_gram[1]})
     if (e) cudaEventDestroy(e);
   for (cudaEvent_t e : c->ev_fd) cudaEventDestroy(e);
   for (cudaEvent_t e : c->ev_dft) cudaEventDestroy(e);
@@ -504,6 +505,8 @@ egh_status egh_create(const egh_config* cfg, egh_ctx** out) {
       CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
     CK(cudaEventCreate(&ctx->ev_tune[0]));
     CK(cudaEventCreate(&ctx->ev_tune[1]));
+    CK(cudaEventCreate(&ctx->ev_gram[0]));
+    CK(cudaEventCreate(&ctx->ev_gram[1]));
     {
       const long long nchunks = (long long)((c.nrec + ctx->B - 1) / ctx->B) * ((c.nt + ctx->K - 1) / ctx->K);
       ctx->ev_fd.assign(2 * nchunks, nullptr);
@@ -749,12 +752,15 @@ egh_status egh_hessian(egh_ctx* ctx, egh_mu_mode mode, double mu_param, double* 
   if (mode != EGH_MU_ABS && mode != EGH_MU_REL_MEANDIAG && mode != EGH_MU_REL_MAXEIG)
     return fail(ctx, EGH_EINVAL, "unknown mu mode");
   CK(cudaEventRecord(ctx->ev[2], stream));
+  CK(cudaEventRecord(ctx->ev_gram[0], stream));
   if (prec_mixed(ctx->prec)) {
     CK(launch_gram_tc(ctx->tmap_ghb, ctx->nrec, ctx->nf, ctx->L.G, ctx->splits_tc, ctx->part,
                       ctx->d_err, stream));
+    CK(cudaEventRecord(ctx->ev_gram[1], stream));
     CK(launch_gram_tc_finish(ctx->part, ctx->nrec, ctx->nf, ctx->splits_tc, ctx->Qh, stream));
   } else {
     CK(launch_gram_partial(ctx->gh, ctx->nrec, ctx->nf, ctx->L.G, ctx->splits, ctx->part, stream));
+    CK(cudaEventRecord(ctx->ev_gram[1], stream));
     CK(launch_gram_finish(ctx->part, ctx->nrec, ctx->nf, ctx->splits, ctx->Qh, stream));
   }
   double mu = mu_param;
@@ -782,6 +788,11 @@ egh_status egh_hessian(egh_ctx* ctx, egh_mu_mode mode, double mu_param, double* 
     }
   }
   if (!std::isfinite(mu)) return fail(ctx, EGH_EINVAL, "mu is not finite");
+  {
+    float gms = 0.f;
+    CK(cudaEventElapsedTime(&gms, ctx->ev_gram[0], ctx->ev_gram[1]));
+    ctx->st.gram_ms = gms;
+  }
   CK(launch_add_mu_copy(ctx->Qh, ctx->Lh, ctx->nrec, ctx->nf, (float)mu, stream));
   CK(cudaEventRecord(ctx->ev[3], stream));
   ctx->ev_rec[1] = true;

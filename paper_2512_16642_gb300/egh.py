@@ -50,6 +50,7 @@ class egh_stats(ctypes.Structure):
         ("fd_rows", ctypes.c_int32), ("pad_", ctypes.c_int32),
         ("fd_ms", ctypes.c_double), ("dft_ms", ctypes.c_double),
         ("fd_launches", ctypes.c_int64), ("dft_launches", ctypes.c_int64),
+        ("gram_ms", ctypes.c_double),
     ]
 
     def as_dict(self):
