@@ -38,9 +38,11 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM traffic (read + write bytes) per launch of the FD step and of the transform from the
 # committed ncu capture (profiles/), valid only for the kernel sources it was taken from (sha256
 # of csrc/fd.cu); None until a capture exists.
-KERNEL_TRAFFIC = {"fd_sha256": "bf9a1528aa400f066f1fc8a2dbd5e627c7a6b73f1c60b893cdf1f10c1cd2dc3f",
-                  "k_fd_step": 32.46e6,   # 3.01 MB read + 29.46 MB write per launch
-                  "k_dft_tc": 13.77e9}    # 12.03 GB read + 1.74 GB write per 512-level launch
+KERNEL_TRAFFIC = {"fd_sha256": "10e918ab7dda65d80708a08a47135bd441ea0df259900e9a45a079c77b7db383",
+                  "k_fd_step": 30.07e6,   # 1.95 MB read + 28.12 MB write per launch
+                  "k_dft_tc": 13.77e9,    # 12.03 GB read + 1.74 GB write per 512-level launch
+                  "gram_sha256": "5f3ab19d0b4c43a7200d1b923a74a90149eff3ddcd05def4594f422e847969fc",
+                  "k_gram_tc": 22.36e9}   # 22.03 GB read + 0.33 GB write per launch (231 x 26)
 
 
 def _args():
@@ -588,6 +590,9 @@ def run_ours(args):
     with open(os.path.join(ROOT, "paper_2512_16642_gb300", "csrc", "fd.cu"), "rb") as f:
         fd_sha = hashlib.sha256(f.read()).hexdigest()
     traffic_ok = KERNEL_TRAFFIC["fd_sha256"] == fd_sha
+    with open(os.path.join(ROOT, "paper_2512_16642_gb300", "csrc", "gram_tc.cu"), "rb") as f:
+        gram_traffic = (KERNEL_TRAFFIC["k_gram_tc"] if KERNEL_TRAFFIC["gram_sha256"] ==
+                        hashlib.sha256(f.read()).hexdigest() and args.precision == "mixed" else None)
     fd_ms = statistics.mean(k[0] for k in kern)
     fd_n = kern[-1][1]
     dft_ms = statistics.mean(k[2] for k in kern)
@@ -659,8 +664,8 @@ def run_ours(args):
                                "algorithmic_bytes_per_launch": dft_alg, "launches": dft_n,
                                "avg_launch_ms": dft_ms / dft_n,
                                "note": "runs beside the next chunk's FD steps on a low-priority stream"},
-        "roofline_gram": gram_roofline(args.precision, nr, nf, npts, c, statistics.mean(gram_ms),
-                                       tc_peak, tc_kind),
+        "roofline_gram": dict(gram_roofline(args.precision, nr, nf, npts, c, statistics.mean(gram_ms),
+                                            tc_peak, tc_kind), traffic=gram_traffic),
         "green_stage": {"achieved": 12.0 * point_steps / green_s / 1e9, "unit": "GB/s",
                         "frac": 12.0 * point_steps / green_s / 1e9 / hbm,
                         "note": "whole egh_green (FD + transform), 12 B per receiver point-step"},
