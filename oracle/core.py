@@ -504,6 +504,18 @@ def apply_St(grid: Grid, dt, nt, rec_p, traces, counter=None):
     return snaps[::-1].copy()
 
 
+def data_fit(grid: Grid, dt, nt, src_p, wavelet, rec_p, d_obs, mult):
+    """The paper's Hessian accuracy test (Section "Hessian accuracy test"): the multipliers,
+    back-propagated as the adjoint source S^T mult, extend the source b; the extended wavefield
+    u^e = A^{-1}(b + S^T mult) sampled at the receivers predicts the data,
+        P u^e = P A^{-1} b + S S^T mult   (linearity),
+    and the relative error is ||d - P u^e||^2 / ||d||^2.  Returns (d - P u^e, relative error)."""
+    d_model = fd_run(grid, dt, nt, src_p=src_p, src_f=np.atleast_2d(wavelet), rec_p=rec_p)["traces"]
+    pred = d_model + apply_S(grid, dt, nt, rec_p, apply_St(grid, dt, nt, rec_p, mult))
+    r = d_obs - pred
+    return r, float(np.sum(r * r) / np.sum(d_obs * d_obs))
+
+
 def cg_time_domain(grid: Grid, dt, nt, rec_p, d, mu, tol=1e-10, maxiter=500, counter=None):
     """CG on (S~ S~^T + mu I) x = d, d[r, t] (one source gather)."""
     def op(x):
