@@ -109,12 +109,11 @@ __global__ void __cluster_dims__(TD_S, 1, 1) __launch_bounds__(256)
         w[2 * j + 1] = make_float2(v.z, v.w);
       }
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < 4; ++i) {
+        const float2 xx = make_float2(x[i], x[i]);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          acc[i][j].x = fmaf(x[i], w[j].x, acc[i][j].x);
-          acc[i][j].y = fmaf(x[i], w[j].y, acc[i][j].y);
-        }
+        for (int j = 0; j < 8; ++j) acc[i][j] = __ffma2_rn(xx, w[j], acc[i][j]);  // packed FP32x2
+      }
     }
     __syncthreads();
   }
@@ -262,18 +261,19 @@ cudaError_t launch_trsm(const float2* Lh, int n, int nf, float2* Dh, int ns, cud
 // Synthesis: 64 traces x 128 samples per block.  The weighted solutions of the block's traces
 // (X[k][trace]) and the twiddles of its time range (T[k][sample]) sit in shared memory; thread
 // (g, p) produces samples 4p .. 4p + 3 of traces 8g .. 8g + 7 (per frequency: two 16-byte
-// twiddle reads, four broadcast solution reads, 64 FMAs).
+// twiddle reads, four broadcast solution reads, 32 packed FP32x2 FMAs).
 // Re(X e^{+i theta}) = Re X cos(theta) + Im X (-sin(theta)) with tw = e^{-i theta}.
 // ---------------------------------------------------------------------------------------------
-constexpr int SY_TR = 64, SY_T = 128, SY_TP = SY_T + 2;
+constexpr int SY_TR = 64, SY_T = 128, SY_TP = SY_T + 4;
 
 __global__ void __launch_bounds__(256)
     k_synth(const float2* __restrict__ Dh, int nrec, int ld, int s0, int nf,
             const float* __restrict__ w, const float2* __restrict__ tw, int nt_d,
             float* __restrict__ mult, int ntr) {
   extern __shared__ float4 sm4[];
-  float2* X = reinterpret_cast<float2*>(sm4);  // [nf][SY_TR]
-  float2* T = X + SY_TR * nf;                  // [nf][SY_TP]
+  float2* X = reinterpret_cast<float2*>(sm4);            // [nf][SY_TR]
+  float* Tc = reinterpret_cast<float*>(X + SY_TR * nf);  // [nf][SY_TP] cos(theta)
+  float* Ts = Tc + nf * SY_TP;                           // [nf][SY_TP] -sin(theta)
   const int tid = threadIdx.x;
   const int q0 = blockIdx.y * SY_TR, t0 = blockIdx.x * SY_T;
   // all gathers in flight at once (cp.async, zero-filled outside), then the weights applied
@@ -283,11 +283,14 @@ __global__ void __launch_bounds__(256)
     cp_async8(X + e, ok ? Dh + ((long long)k * nrec + q % nrec) * ld + s0 + q / nrec : Dh, ok);
   }
   // the block's twiddle rows are one contiguous run of the table: read it in order, transpose
-  // on the way into shared memory (row length SY_TP keeps the writes at few-way conflicts)
+  // on the way into shared memory as separate cos and -sin planes (row length SY_TP keeps the
+  // writes at few-way conflicts)
   for (int e = tid; e < nf * SY_T; e += 256) {
     const int tt = e / nf, k = e % nf, t = t0 + tt;
     const bool ok = t < nt_d;
-    cp_async8(T + k * SY_TP + tt, ok ? tw + (long long)t0 * nf + e : tw, ok);
+    const float* src = reinterpret_cast<const float*>(ok ? tw + (long long)t0 * nf + e : tw);
+    cp_async4(Tc + k * SY_TP + tt, src, ok);
+    cp_async4(Ts + k * SY_TP + tt, src + 1, ok);
   }
   cp_async_commit();
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
@@ -298,26 +301,28 @@ __global__ void __launch_bounds__(256)
   }
   __syncthreads();
   const int p = tid & 31, g = tid >> 5;
-  float acc[8][4];
+  // acc[m][h] = samples 4p + 2h, 4p + 2h + 1 of trace 8g + m (packed FP32x2, same roundings as
+  // the scalar sum Re X cos + Im X (-sin), the sine term first)
+  float2 acc[8][2];
 #pragma unroll
-  for (int m = 0; m < 8; ++m)
-#pragma unroll
-    for (int i = 0; i < 4; ++i) acc[m][i] = 0.f;
+  for (int m = 0; m < 8; ++m) acc[m][0] = acc[m][1] = make_float2(0.f, 0.f);
   for (int k = 0; k < nf; ++k) {
-    const float4* tp = reinterpret_cast<const float4*>(T + k * SY_TP + 4 * p);
-    const float4 c01 = tp[0], c23 = tp[1];
-    const float2 c[4] = {make_float2(c01.x, c01.y), make_float2(c01.z, c01.w),
-                         make_float2(c23.x, c23.y), make_float2(c23.z, c23.w)};
+    const float4 cc = *reinterpret_cast<const float4*>(Tc + k * SY_TP + 4 * p);
+    const float4 ss = *reinterpret_cast<const float4*>(Ts + k * SY_TP + 4 * p);
+    const float2 c2[2] = {make_float2(cc.x, cc.y), make_float2(cc.z, cc.w)};
+    const float2 s2[2] = {make_float2(ss.x, ss.y), make_float2(ss.z, ss.w)};
     const float4* xp = reinterpret_cast<const float4*>(X + k * SY_TR + 8 * g);
 #pragma unroll
     for (int h = 0; h < 4; ++h) {
       const float4 xv = xp[h];
       const float2 x[2] = {make_float2(xv.x, xv.y), make_float2(xv.z, xv.w)};
 #pragma unroll
-      for (int u = 0; u < 2; ++u)
+      for (int u = 0; u < 2; ++u) {
+        const float2 re = make_float2(x[u].x, x[u].x), im = make_float2(x[u].y, x[u].y);
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
-          acc[2 * h + u][i] = fmaf(x[u].x, c[i].x, fmaf(x[u].y, c[i].y, acc[2 * h + u][i]));
+        for (int hh = 0; hh < 2; ++hh)
+          acc[2 * h + u][hh] = __ffma2_rn(re, c2[hh], __ffma2_rn(im, s2[hh], acc[2 * h + u][hh]));
+      }
     }
   }
   const int tb = t0 + 4 * p;
@@ -329,11 +334,12 @@ __global__ void __launch_bounds__(256)
     if (q >= ntr) break;
     float* out = mult + (long long)q * nt_d + tb;
     if (vec) {
-      *reinterpret_cast<float4*>(out) = make_float4(acc[m][0], acc[m][1], acc[m][2], acc[m][3]);
+      *reinterpret_cast<float4*>(out) = make_float4(acc[m][0].x, acc[m][0].y, acc[m][1].x, acc[m][1].y);
     } else {
+      const float v[4] = {acc[m][0].x, acc[m][0].y, acc[m][1].x, acc[m][1].y};
 #pragma unroll
       for (int i = 0; i < 4; ++i)
-        if (tb + i < nt_d) out[i] = acc[m][i];
+        if (tb + i < nt_d) out[i] = v[i];
     }
   }
 }
@@ -648,7 +654,7 @@ cudaError_t launch_synth(const float2* Dh, int nrec, int ns, int ld, int s0, int
                          const float2* tw, int nt_d, float* mult, cudaStream_t st) {
   if (nf > NFMAX) return cudaErrorInvalidValue;
   const int ntr = nrec * ns;
-  const size_t smem = sizeof(float2) * (size_t)nf * (SY_TR + SY_TP);
+  const size_t smem = sizeof(float2) * (size_t)nf * SY_TR + 2 * sizeof(float) * (size_t)nf * SY_TP;
   if (smem > 48 * 1024) {
     cudaError_t e =
         cudaFuncSetAttribute(k_synth, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
