@@ -121,3 +121,29 @@ def test_admission_by_budget_and_overlap():
         for rid in rids:
             sv.wait(rid)
         assert sv.stats()["peak_in_flight"] >= 2  # batches overlapped on the device
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_full_size_set_sampled(precision):
+    """The largest set of the benchmark's serving mix (461 receivers, 40 frequencies 2-10 Hz) and
+    its largest request (64 sources x 4000 samples) in the launch configuration the benchmark
+    times; the multipliers of sampled sources against the FP64 oracle (sources are independent
+    right-hand sides, so the oracle solves only the sampled ones)."""
+    import torch
+    from paper_2512_16642_gb300 import egh
+
+    rng = np.random.default_rng(77)
+    Q, f = _hpd_set(rng, 461, 40)
+    ns, nt_d, dt = 64, 4000, 1e-3
+    r = synth.bandlimited_noise(rng, (ns, 461, nt_d), dt, 2.0, 10.0)
+    sample = np.array([0, 37, 63])
+    L = oracle.cholesky(Q.astype(np.complex128))
+    ref = oracle.deblur(L, r[sample].astype(np.float32).astype(np.float64), f, dt, nt_ref=4000)[0]
+    with egh.Server(8 << 30, slots=4, max_batch_sources=128, precision=precision) as sv:
+        sid = sv.add_set(Q, f, dt, 4000, 4096)
+        rin = _pinned(r.shape, torch, r)
+        out = _pinned(r.shape, torch)
+        sv.wait(sv.submit(sid, rin, out))
+    got = out.numpy()[sample]
+    for i in range(sample.size):
+        assert rel(got[i], ref[i]) <= MULT_TOL, (precision, int(sample[i]))
