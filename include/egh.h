@@ -318,7 +318,8 @@ egh_status egh_server_submit(egh_server *sv, int32_t set_id, const float *resid_
  * completion time.  The id is released.  EGH_ETIMEOUT if it has not finished. */
 egh_status egh_server_wait(egh_server *sv, int64_t request_id, double timeout_s, double *latency_s);
 
-/* Waits (up to timeout_s) until nothing is queued or in flight. */
+/* Waits (up to timeout_s) until nothing is queued or in flight.  EGH_ETIMEOUT also when a
+ * transform's bounded device wait ran out since the last drain (the server stays usable). */
 egh_status egh_server_drain(egh_server *sv, double timeout_s);
 
 egh_status egh_server_get_stats(egh_server *sv, egh_server_stats *out);

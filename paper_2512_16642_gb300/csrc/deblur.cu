@@ -16,6 +16,8 @@
 #include "egh_internal.cuh"
 #include "tc.cuh"
 
+#include <cuda_bf16.h>
+
 namespace egh {
 
 constexpr int NFMAX = 64;
@@ -31,6 +33,9 @@ constexpr int NFMAX = 64;
 // distributed shared memory, added in rank order (deterministic).
 // ---------------------------------------------------------------------------------------------
 constexpr int TD_TR = 128, TD_T = 32, TD_RL = TD_TR + 1, TD_NS = 3, TD_S = 4;
+
+// components of the tensor-core transform: 2 nf rounded up to 32
+__host__ __device__ inline int tt_ncomp(int nf) { return (2 * nf + 31) / 32 * 32; }
 
 __device__ __forceinline__ void cp_async4(void* dst, const void* src, bool ok) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(tc::smem_u32(dst)), "l"(src),
@@ -154,9 +159,17 @@ __global__ void __cluster_dims__(TD_S, 1, 1) __launch_bounds__(256)
   cluster.sync();  // the other blocks' shared memory stays live until rank 0 has read it
 }
 
+cudaError_t launch_trace_dft_tc(const float* resid, int ntr, int nt_d, const unsigned char* twt,
+                                int nf, int nrec, int ld, int s0, float2* Dh, int* err,
+                                cudaStream_t st);
+
 cudaError_t launch_trace_dft(const float* resid, int ntr, int nt_d, const float2* tw, int nf,
-                             int nrec, int ld, int s0, float2* Dh, cudaStream_t st) {
+                             int nrec, int ld, int s0, float2* Dh, cudaStream_t st,
+                             const unsigned char* twt, int* err) {
   if (nf < 1 || nf > NFMAX) return cudaErrorInvalidValue;
+  // tensor cores when the twiddle tiles are given and N = 2 nf rounded up to 32 is at most 64
+  if (twt && err && tt_ncomp(nf) <= 64)
+    return launch_trace_dft_tc(resid, ntr, nt_d, twt, nf, nrec, ld, s0, Dh, err, st);
   const int groups = (nf + 7) / 8;
   const size_t smem = trace_dft_smem(nf);
   if (smem > 48 * 1024) {
@@ -169,6 +182,261 @@ cudaError_t launch_trace_dft(const float* resid, int ntr, int nt_d, const float2
   k_trace_dft<<<(unsigned)(tiles * TD_S), 32 * groups, smem, st>>>(resid, ntr, nt_d, tw, nf, nrec,
                                                                     ld, s0, Dh);
   return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------
+// Forward transform on the tensor cores: D[q][c] = sum_t resid[q][t] W[c][t] with W the twiddle
+// tiles of the Green-stage transform (component c = 2k: cos, 2k + 1: -sin; 64 levels per tile,
+// bf16 hi/lo, K-major 128-byte swizzle).  128 traces per CTA (MMA M = 128), N = 2 nf rounded up
+// to 32, 64 samples per stage.  The traces are read with coalesced 16-byte loads one stage ahead
+// into registers, split u = hi + lo into bf16 (about 2^-17 relative) and written by the threads
+// into the K-major swizzled A tiles; one thread issues the bf16x3 MMAs (hi hi, hi lo, lo hi).
+// The tensor core's FP32 accumulation drifts over long sums, so blocks of TT_J stages alternate
+// between two TMEM buffers and the threads drain each finished block into FP32 register totals.
+// The time axis is split over a cluster of TD_S CTAs whose totals meet in rank 0 through
+// distributed shared memory, in rank order.  Every wait is bounded.
+// ---------------------------------------------------------------------------------------------
+constexpr int TT_M = 128, TT_K = 64, TT_J = 8;
+constexpr unsigned TT_A = TT_M * 128;  // one A plane (hi or lo): 128 rows x 128 bytes
+
+size_t trace_dft_tc_smem(int nf) {
+  const size_t N = tt_ncomp(nf);
+  // 2 stages x (A hi + A lo + B hi + B lo), 1024-byte alignment slack
+  return 1024 + 2 * (2 * (size_t)TT_A + 2 * N * 128);
+}
+
+__device__ __forceinline__ void st_shared_v2(unsigned addr, unsigned a, unsigned b) {
+  asm volatile("st.shared.v2.u32 [%0], {%1, %2};" ::"r"(addr), "r"(a), "r"(b) : "memory");
+}
+
+template <int N, bool VEC>
+__global__ void __cluster_dims__(TD_S, 1, 1) __launch_bounds__(128)
+    k_trace_dft_tc(const float* __restrict__ resid, int ntr, int nt_d,
+                   const unsigned char* __restrict__ twt, int nf, int nrec, int ld, int s0,
+                   float2* __restrict__ Dh, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char tt_dsm[];
+  unsigned char* sm = tt_dsm + ((1024 - (tc::smem_u32(tt_dsm) & 1023)) & 1023);
+  constexpr unsigned BT = 2u * N * 128u;           // one twiddle tile (hi + lo)
+  constexpr unsigned STG = 2u * TT_A + BT;         // one stage
+  __shared__ __align__(8) unsigned long long bars[6];  // bfull[2], mdone[2], blk[2]
+  __shared__ unsigned tslot;
+  __shared__ int fail;
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int rank = (int)cluster.block_rank();
+  const int q0 = (blockIdx.x / TD_S) * TT_M;
+  const int nst_all = (nt_d + TT_K - 1) / TT_K, per = (nst_all + TD_S - 1) / TD_S;
+  const int sbeg = min(nst_all, rank * per), send = min(nst_all, sbeg + per);
+  const int nst = send - sbeg;
+  const unsigned bar0 = tc::smem_u32(&bars[0]);
+  auto bfull = [&](int i) { return bar0 + 8u * i; };
+  auto mdone = [&](int i) { return bar0 + 8u * (2 + i); };
+  auto blkd = [&](int i) { return bar0 + 8u * (4 + i); };
+  constexpr unsigned NCOL = 2 * N <= 32 ? 32 : (2 * N <= 64 ? 64 : (2 * N <= 128 ? 128 : 256));
+  if (warp == 0) tc::tmem_alloc(&tslot, NCOL);
+  if (tid == 0) {
+    for (int i = 0; i < 6; ++i) tc::mbar_init(bar0 + 8u * i, 1);
+    fail = 0;
+    tc::mbar_init_fence();
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const unsigned tmem = tslot;
+  auto a_hi = [&](int b) { return tc::smem_u32(sm + (size_t)b * STG); };
+  auto b_hi = [&](int b) { return tc::smem_u32(sm + (size_t)b * STG + 2 * TT_A); };
+  auto issue_b = [&](int s) {  // twiddle tile of stage s (relative to sbeg) into buffer s % 2
+    tc::mbar_expect_tx(bfull(s & 1), BT);
+    tc::bulk_g2s(b_hi(s & 1), twt + (size_t)(sbeg + s) * BT, BT, bfull(s & 1));
+  };
+  // this thread's 16 float4 of a stage: element e = i * 128 + tid -> row e / 16, float4 e % 16
+  float4 pre[16];
+  auto load = [&](int s) {
+    const int t0 = (sbeg + s) * TT_K;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int e = i * 128 + tid, m = e >> 4, c4 = e & 15;
+      const int q = q0 + m, t = t0 + 4 * c4;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (q < ntr) {
+        const float* src = resid + (long long)q * nt_d + t;
+        if (VEC) {
+          if (t < nt_d) v = __ldcs(reinterpret_cast<const float4*>(src));  // nt_d % 4 == 0
+        } else {
+          if (t < nt_d) v.x = __ldcs(src);
+          if (t + 1 < nt_d) v.y = __ldcs(src + 1);
+          if (t + 2 < nt_d) v.z = __ldcs(src + 2);
+          if (t + 3 < nt_d) v.w = __ldcs(src + 3);
+        }
+      }
+      pre[i] = v;
+    }
+  };
+  auto convert = [&](int b) {  // pre -> A hi / lo planes of buffer b, K-major 128-byte swizzle
+    const unsigned ah = a_hi(b);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int e = i * 128 + tid, m = e >> 4, c4 = e & 15;
+      const float4 v = pre[i];
+      const __nv_bfloat162 h01 = __floats2bfloat162_rn(v.x, v.y), h23 = __floats2bfloat162_rn(v.z, v.w);
+      const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
+      const __nv_bfloat162 l01 = __floats2bfloat162_rn(v.x - f01.x, v.y - f01.y);
+      const __nv_bfloat162 l23 = __floats2bfloat162_rn(v.z - f23.x, v.w - f23.y);
+      // samples 4 c4 .. 4 c4 + 3 = bytes 8 c4 .. 8 c4 + 7 of row m: chunk c4 / 2, half c4 % 2
+      const unsigned off = (unsigned)((m >> 3) * 1024 + (m & 7) * 128 +
+                                      ((((c4 >> 1) ^ (m & 7))) << 4) + ((c4 & 1) << 3));
+      st_shared_v2(ah + off, *reinterpret_cast<const unsigned*>(&h01),
+                   *reinterpret_cast<const unsigned*>(&h23));
+      st_shared_v2(ah + TT_A + off, *reinterpret_cast<const unsigned*>(&l01),
+                   *reinterpret_cast<const unsigned*>(&l23));
+    }
+  };
+  float tot[N];
+#pragma unroll
+  for (int c = 0; c < N; ++c) tot[c] = 0.f;
+  bool ok = true;
+  auto drain = [&](int blk) {  // add TMEM buffer blk % 2 into the totals (whole warp)
+    const bool got = tc::mbar_wait(blkd(blk & 1), (blk >> 1) & 1);
+    if (!__all_sync(0xffffffffu, got)) {
+      ok = false;
+      return;
+    }
+    tc::tc_fence_after();
+    const unsigned base = tmem + ((unsigned)(warp * 32) << 16) + (unsigned)((blk & 1) * N);
+#pragma unroll
+    for (int c0 = 0; c0 < N; c0 += 32) {
+      float v[32];
+      tc::tmem_ld32(base + (unsigned)c0, v);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) tot[c0 + i] += v[i];
+    }
+    tc::tc_fence_before();
+  };
+  int issued_b = 0, waited_b = 0;  // twiddle copies issued / waited for (thread 0)
+  if (nst > 0) {
+    if (tid == 0) {
+      issue_b(0);
+      issued_b = 1;
+    }
+    load(0);
+  }
+  const unsigned idesc = tc::idesc_bf16(TT_M, N, 0, 0);
+  for (int s = 0; s < nst; ++s) {
+    const int b = s & 1, blk = s / TT_J;
+    // A and B of buffer b were last read by the MMAs of stage s - 2 (block-uniform decision)
+    const bool freed = s < 2 || tc::mbar_wait(mdone(b), ((s - 2) >> 1) & 1);
+    if (!__syncthreads_and(freed)) {
+      ok = false;
+      break;
+    }
+    convert(b);
+    if (s + 1 < nst) load(s + 1);  // the next stage's traces in flight during this stage
+    tc::fence_proxy_async();
+    __syncthreads();
+    if (tid == 0) {
+      if (!tc::mbar_wait(bfull(b), (s >> 1) & 1)) {
+        fail = 1;
+      } else {
+        waited_b = s + 1;
+        tc::tc_fence_after();
+        const unsigned dt = tmem + (unsigned)((blk & 1) * N);
+        const unsigned ah = a_hi(b), al = ah + TT_A, bh = b_hi(b), bl = bh + N * 128;
+        const bool first = s % TT_J == 0;
+#pragma unroll
+        for (int ks = 0; ks < TT_K / 16; ++ks) {
+          const unsigned o = 32u * ks;
+          const uint64_t dah = tc::sdesc_sw128(ah + o), dal = tc::sdesc_sw128(al + o);
+          const uint64_t dbh = tc::sdesc_sw128(bh + o), dbl = tc::sdesc_sw128(bl + o);
+          tc::mma_bf16(dt, dah, dbh, idesc, !(first && ks == 0));
+          tc::mma_bf16(dt, dah, dbl, idesc, true);
+          tc::mma_bf16(dt, dal, dbh, idesc, true);
+        }
+        tc::mma_commit(mdone(b));
+        if (s % TT_J == TT_J - 1 || s == nst - 1) tc::mma_commit(blkd(blk & 1));
+        // the next stage's twiddles go to the other buffer once stage s - 1's MMAs are done
+        if (s + 1 < nst) {
+          if (s >= 1 && !tc::mbar_wait(mdone(b ^ 1), ((s - 1) >> 1) & 1)) {
+            fail = 1;
+          } else {
+            issue_b(s + 1);
+            issued_b = s + 2;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (fail) {
+      ok = false;
+      break;
+    }
+    // a block's buffer is drained during the next block (its MMAs go to the other buffer)
+    if (s % TT_J == 0 && blk >= 1) {
+      drain(blk - 1);
+      if (!__syncthreads_and(ok)) {
+        ok = false;
+        break;
+      }
+    }
+  }
+  if (ok && nst > 0) drain((nst - 1) / TT_J);
+  // leave no copy or MMA in flight: copies issued but not consumed, and the last MMAs issued
+  // (commit order covers the earlier ones); all bounded
+  if (nst > 0 && tid == 0) {
+    for (int sc = waited_b; sc < issued_b; ++sc) tc::mbar_wait(bfull(sc & 1), (sc >> 1) & 1);
+    const int sl = waited_b - 1;
+    if (sl >= 0) tc::mbar_wait(mdone(sl & 1), (sl >> 1) & 1);
+  }
+  const bool okall = __syncthreads_and(ok) && !fail;
+  if (!okall && tid == 0) atomicExch(err, 1);
+  // totals to shared memory (the stage buffers are free): P[c][tid]
+  float* P = reinterpret_cast<float*>(sm);
+#pragma unroll
+  for (int c = 0; c < N; ++c) P[c * TT_M + tid] = okall ? tot[c] : 0.f;
+  cluster.sync();
+  if (rank == 0) {
+    for (int r = 1; r < TD_S; ++r) {
+      const float* Pr = cluster.map_shared_rank(P, r);
+#pragma unroll
+      for (int c = 0; c < N; ++c) tot[c] += Pr[c * TT_M + tid];
+    }
+    const int q = q0 + tid;
+    if (q < ntr) {
+      const int sidx = q / nrec, r = q % nrec;
+#pragma unroll
+      for (int k = 0; k < N / 2; ++k)
+        if (k < nf)
+          Dh[((long long)k * nrec + r) * ld + s0 + sidx] = make_float2(tot[2 * k], tot[2 * k + 1]);
+    }
+  }
+  cluster.sync();
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, NCOL);
+}
+
+cudaError_t launch_trace_dft_tc(const float* resid, int ntr, int nt_d, const unsigned char* twt,
+                                int nf, int nrec, int ld, int s0, float2* Dh, int* err,
+                                cudaStream_t st) {
+  const int N = tt_ncomp(nf);
+  const size_t smem = trace_dft_tc_smem(nf);
+  const bool vec = (nt_d & 3) == 0 && (reinterpret_cast<uintptr_t>(resid) & 15) == 0;
+  const long long tiles = (ntr + TT_M - 1) / TT_M;
+  const dim3 grid((unsigned)(tiles * TD_S));
+  cudaError_t e = cudaSuccess;
+#define EGH_TT_CASE(NN)                                                                        \
+  if (N == NN) {                                                                               \
+    auto kern = vec ? k_trace_dft_tc<NN, true> : k_trace_dft_tc<NN, false>;                    \
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) \
+      return e;                                                                                \
+    count_launches(1);                                                                         \
+    kern<<<grid, 128, smem, st>>>(resid, ntr, nt_d, twt, nf, nrec, ld, s0, Dh, err);           \
+    return cudaGetLastError();                                                                 \
+  }
+  EGH_TT_CASE(32)
+  EGH_TT_CASE(64)
+#undef EGH_TT_CASE
+  return cudaErrorInvalidValue;
 }
 
 // ---------------------------------------------------------------------------------------------

@@ -64,6 +64,7 @@ struct egh_ctx {
   __nv_bfloat16* ghb = nullptr;              // [nf][G/64][hi/lo][nrec x re/im][64] Gram operands
   CUtensorMap tmap_ghb{};                    // TMA map of ghb
   float2 *Qh = nullptr, *Lh = nullptr, *tw = nullptr;
+  unsigned char* twt_deb = nullptr;  // the deblur transform's twiddle tiles (tw_len levels)
   float2* Wh = nullptr;  // mixed precision: W = L^{-1} per frequency (solves as products)
   int tw_len = 0;
   cudaStream_t side = nullptr;                 // the transform's stream inside egh_green (low priority)
@@ -194,11 +195,16 @@ egh_status ensure_twiddles(egh_ctx* ctx, int len, cudaStream_t stream) {
   std::vector<float2> h = twiddle_table(ctx->freqs, ctx->dt, len);
   CK(cudaStreamSynchronize(stream));
   if (ctx->tw) CK(cudaFree(ctx->tw));
+  if (ctx->twt_deb) CK(cudaFree(ctx->twt_deb));
   ctx->tw = nullptr;
+  ctx->twt_deb = nullptr;
   ctx->tw_len = 0;
   egh_status s = dalloc(ctx, (void**)&ctx->tw, h.size() * sizeof(float2), "twiddles");
   if (s) return s;
   CK(cudaMemcpy(ctx->tw, h.data(), h.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  const std::vector<unsigned char> t = dft_twiddle_tiles(ctx->freqs, ctx->dt, len);
+  if ((s = dalloc(ctx, (void**)&ctx->twt_deb, t.size(), "deblur twiddle tiles"))) return s;
+  CK(cudaMemcpy(ctx->twt_deb, t.data(), t.size(), cudaMemcpyHostToDevice));
   ctx->tw_len = len;
   return EGH_OK;
 }
@@ -262,7 +268,7 @@ cudaError_t zero_snap_slot(egh_ctx* ctx, int j, cudaStream_t st) {
 }
 
 void free_all(egh_ctx* c) {
-  void* ptrs[] = {c->twt_bl, c->Wh, c->Dr, c->Rr, c->coef, c->lev, c->snap, c->twt, c->gh, c->ghb, c->part, c->Qh, c->Lh, c->tw, c->w_dev,
+  void* ptrs[] = {c->twt_deb, c->twt_bl, c->Wh, c->Dr, c->Rr, c->coef, c->lev, c->snap, c->twt, c->gh, c->ghb, c->part, c->Qh, c->Lh, c->tw, c->w_dev,
                   c->rec_pts, c->status, c->dsum, c->lmax, c->vchk, c->d_err, c->vel_stage, c->Dh,
                   c->io_in, c->io_out};
   for (void* p : ptrs)
@@ -876,7 +882,8 @@ static egh_status deblur_common(egh_ctx* ctx, const float* resid, int32_t ns, in
     dout = ctx->io_out;
   }
   CK(cudaEventRecord(ctx->ev[6], stream));
-  CK(launch_trace_dft(din, (int)ntr, nt_d, ctx->tw, ctx->nf, ctx->nrec, ns, 0, D, stream));
+  CK(launch_trace_dft(din, (int)ntr, nt_d, ctx->tw, ctx->nf, ctx->nrec, ns, 0, D, stream,
+                      ctx->twt_deb, ctx->d_err));
   const size_t dbytes = (size_t)ctx->nf * ntr * sizeof(float2);
   if (!diag && prec_mixed(ctx->prec)) {
     // one step of iterative refinement: residual in FP64, correction solved with the FP32 factors
@@ -908,6 +915,14 @@ static egh_status deblur_common(egh_ctx* ctx, const float* resid, int32_t ns, in
     CK(cudaStreamSynchronize(stream));
   } else if (!dev_in) {
     CK(cudaStreamSynchronize(stream));
+  }
+  if (!dev_in || (!X && !dev_out)) {  // synchronised: report a bounded wait that ran out
+    int derr = 0;
+    CK(cudaMemcpy(&derr, ctx->d_err, sizeof derr, cudaMemcpyDeviceToHost));
+    if (derr) {
+      CK(cudaMemset(ctx->d_err, 0, sizeof(int)));
+      return fail(ctx, EGH_ETIMEOUT, "a bounded wait for staged twiddles ran out in the transform");
+    }
   }
   return EGH_OK;
 }

@@ -88,6 +88,7 @@ struct HSet {
   int nrec = 0, nf = 0, tw_len = 0;
   float2 *Qh = nullptr, *Lh = nullptr, *tw = nullptr;
   float2* Wh = nullptr;  // mixed precision: W = L^{-1}
+  unsigned char* twt = nullptr;  // tensor-core transform twiddle tiles (tw_len levels)
   float* w = nullptr;
 };
 
@@ -115,6 +116,7 @@ struct Server {
   int prec = EGH_PREC_FP32;
   int nslots = 0, max_batch = 0;
   char* arena_base = nullptr;
+  int* d_err = nullptr;  // set by a kernel whose bounded wait ran out
   Arena arena;
   std::vector<HSet> sets;
   std::vector<cudaStream_t> streams;
@@ -189,7 +191,8 @@ cudaError_t run_batch(Server* sv, Batch* b, const HSet& h) {
   for (Request* r : b->reqs) {
     float* din = reinterpret_cast<float*>(sv->arena_base + r->off_in);
     if ((e = cudaMemcpyAsync(din, r->resid, r->bytes, cudaMemcpyHostToDevice, st))) return e;
-    if ((e = launch_trace_dft(din, r->ns * h.nrec, r->nt_d, h.tw, h.nf, h.nrec, ld, s0, D, st)))
+    if ((e = launch_trace_dft(din, r->ns * h.nrec, r->nt_d, h.tw, h.nf, h.nrec, ld, s0, D, st,
+                              h.twt, sv->d_err)))
       return e;
     s0 += r->ns;
   }
@@ -352,6 +355,13 @@ egh_status egh_server_create(const egh_server_config* cfg, egh_server** out) {
     delete sv;
     return fail(nullptr, EGH_ENOMEM, std::string("arena: ") + cudaGetErrorString(e));
   }
+  if ((e = cudaMalloc(&sv->d_err, sizeof(int))) != cudaSuccess ||
+      (e = cudaMemset(sv->d_err, 0, sizeof(int))) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(sv->arena_base);
+    delete sv;
+    return fail(nullptr, EGH_ENOMEM, std::string("error flag: ") + cudaGetErrorString(e));
+  }
   sv->arena.reset((size_t)cfg->hbm_budget_bytes);
   sv->streams.resize(sv->nslots);
   sv->slot_busy.assign(sv->nslots, false);
@@ -382,6 +392,7 @@ egh_status egh_server_add_set(egh_server* sv, int32_t nrec, int32_t nfreq, const
   int* status = nullptr;
   cudaStream_t st = sv->streams[0];
   auto cleanup = [&]() {
+    cudaFree(h.twt);
     cudaFree(h.Wh);
     cudaFree(h.Qh);
     cudaFree(h.Lh);
@@ -398,6 +409,11 @@ egh_status egh_server_add_set(egh_server* sv, int32_t nrec, int32_t nfreq, const
   if (!e) e = cudaMemcpy(h.Qh, Q_host, qn * sizeof(float2), cudaMemcpyHostToDevice);
   if (!e) e = cudaMemcpy(h.Lh, Q_host, qn * sizeof(float2), cudaMemcpyHostToDevice);
   if (!e) e = cudaMemcpy(h.tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice);
+  if (!e) {
+    const std::vector<unsigned char> t = dft_twiddle_tiles(f, dt, max_nt);
+    e = cudaMalloc(&h.twt, t.size());
+    if (!e) e = cudaMemcpy(h.twt, t.data(), t.size(), cudaMemcpyHostToDevice);
+  }
   if (!e) e = cudaMemcpy(h.w, w.data(), w.size() * sizeof(float), cudaMemcpyHostToDevice);
   if (!e) e = launch_potrf(h.Lh, nrec, nfreq, status, st, prec_mixed(sv->prec) ? 1 : 0);
   if (!e && prec_mixed(sv->prec)) {
@@ -486,6 +502,14 @@ egh_status egh_server_drain(egh_server* sv, double timeout_s) {
   });
   if (!sv->worker_error.empty()) return fail(sv, EGH_ECUDA, sv->worker_error);
   if (!ok) return fail(sv, EGH_ETIMEOUT, "requests still in flight after the timeout");
+  int derr = 0;  // every batch has completed: the flag is final for them
+  if (cudaSetDevice(sv->dev) != cudaSuccess ||
+      cudaMemcpy(&derr, sv->d_err, sizeof derr, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(sv, EGH_ECUDA, "reading the error flag");
+  if (derr) {
+    cudaMemset(sv->d_err, 0, sizeof(int));
+    return fail(sv, EGH_ETIMEOUT, "a bounded wait for staged twiddles ran out in a transform");
+  }
   return EGH_OK;
 }
 
@@ -544,6 +568,7 @@ void egh_server_destroy(egh_server* sv) {
   for (auto& s : sv->streams) cudaStreamSynchronize(s);
   for (auto& s : sv->streams) cudaStreamDestroy(s);
   for (HSet& h : sv->sets) {
+    cudaFree(h.twt);
     cudaFree(h.Wh);
     cudaFree(h.Qh);
     cudaFree(h.Lh);
@@ -551,6 +576,7 @@ void egh_server_destroy(egh_server* sv) {
     cudaFree(h.w);
   }
   cudaFree(sv->arena_base);
+  cudaFree(sv->d_err);
   for (auto& kv : sv->reqs) delete kv.second;
   delete sv;
 }
