@@ -10,6 +10,9 @@
 // different lengths) can share one solve.
 #include <algorithm>
 #include <cstdint>
+#include <cstring>
+#include <cmath>
+#include <vector>
 
 #include <cooperative_groups.h>
 
@@ -918,9 +921,219 @@ cudaError_t launch_add_correction(float2* X, const float2* R, long long m, cudaS
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------------------------
+// Synthesis on the tensor cores: mult[q][t] = sum_c A[q][c] B[t][c] with A[q][2k] = w_k Re X_k,
+// A[q][2k+1] = w_k Im X_k (the weighted solutions of trace q) and B[t][2k] = cos(theta),
+// B[t][2k+1] = -sin(theta) (host tiles of 256 samples x 64 components, bf16 hi/lo, K-major
+// 128-byte swizzle).  128 traces per CTA: the threads gather, weight and split their solutions
+// into the A tile once, then every 256-sample tile is one bf16x3 M128 x N256 x K64 product into
+// one of two TMEM buffers, drained by the threads straight to global memory while the next
+// tile's MMAs run.  Needs 2 nf <= 64.  Every wait is bounded.
+// ---------------------------------------------------------------------------------------------
+constexpr int SC_M = 128, SC_N = 256;
+constexpr unsigned SC_A = SC_M * 128;         // one A plane (hi or lo)
+constexpr unsigned SC_B = 2u * SC_N * 128u;   // one B tile (hi + lo)
+
+size_t synth_tc_smem() { return 1024 + 2 * (size_t)SC_A + 2 * (size_t)SC_B; }
+
+template <bool VEC>
+__global__ void __launch_bounds__(128)
+    k_synth_tc(const float2* __restrict__ Dh, int nrec, int ld, int s0, int nf,
+               const float* __restrict__ w, const unsigned char* __restrict__ tws, int nt_d,
+               float* __restrict__ mult, int ntr, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char sc_dsm[];
+  unsigned char* sm = sc_dsm + ((1024 - (tc::smem_u32(sc_dsm) & 1023)) & 1023);
+  __shared__ __align__(8) unsigned long long bars[4];  // bfull[2], mdone[2]
+  __shared__ unsigned tslot;
+  __shared__ int fail;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int q0 = blockIdx.x * SC_M;
+  const int ntile = (nt_d + SC_N - 1) / SC_N;
+  const unsigned bar0 = tc::smem_u32(&bars[0]);
+  auto bfull = [&](int i) { return bar0 + 8u * i; };
+  auto mdone = [&](int i) { return bar0 + 8u * (2 + i); };
+  if (warp == 0) tc::tmem_alloc(&tslot, 2 * SC_N);
+  if (tid == 0) {
+    for (int i = 0; i < 4; ++i) tc::mbar_init(bar0 + 8u * i, 1);
+    fail = 0;
+    tc::mbar_init_fence();
+  }
+  const unsigned ah = tc::smem_u32(sm), al = ah + SC_A;
+  auto b_hi = [&](int b) { return tc::smem_u32(sm + 2 * SC_A + (size_t)b * SC_B); };
+  // A tile: row m = trace q0 + m, components c = 2k (re), 2k + 1 (im), zero past 2 nf and ntr
+  {
+    const int m = tid, q = q0 + m;
+    const int sidx = q / nrec, r = q % nrec;
+#pragma unroll 4
+    for (int k = 0; k < 32; ++k) {
+      float2 x = make_float2(0.f, 0.f);
+      if (q < ntr && k < nf) {
+        x = Dh[((long long)k * nrec + r) * ld + s0 + sidx];
+        const float wk = w[k];
+        x.x *= wk;
+        x.y *= wk;
+      }
+      const __nv_bfloat162 h = __floats2bfloat162_rn(x.x, x.y);
+      const float2 hf = __bfloat1622float2(h);
+      const __nv_bfloat162 l = __floats2bfloat162_rn(x.x - hf.x, x.y - hf.y);
+      // bytes 4k .. 4k + 3 of row m: chunk k / 4, offset 4 (k % 4)
+      const unsigned off =
+          (unsigned)((m >> 3) * 1024 + (m & 7) * 128 + ((((k >> 2) ^ (m & 7))) << 4) + ((k & 3) << 2));
+      asm volatile("st.shared.u32 [%0], %1;" ::"r"(ah + off), "r"(*reinterpret_cast<const unsigned*>(&h))
+                   : "memory");
+      asm volatile("st.shared.u32 [%0], %1;" ::"r"(al + off), "r"(*reinterpret_cast<const unsigned*>(&l))
+                   : "memory");
+    }
+  }
+  tc::fence_proxy_async();
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const unsigned tmem = tslot;
+  auto issue_b = [&](int j) {
+    tc::mbar_expect_tx(bfull(j & 1), SC_B);
+    tc::bulk_g2s(b_hi(j & 1), tws + (size_t)j * SC_B, SC_B, bfull(j & 1));
+  };
+  if (tid == 0 && ntile > 0) issue_b(0);
+  const unsigned idesc = tc::idesc_bf16(SC_M, SC_N, 0, 0);
+  const bool vec = VEC;
+  int issued = ntile > 0 ? 1 : 0, waited = 0;
+  bool ok = true;
+  auto epilogue = [&](int j) {  // TMEM buffer j % 2 -> mult[q][256 j ..]
+    const bool got = tc::mbar_wait(mdone(j & 1), (j >> 1) & 1);
+    if (!__all_sync(0xffffffffu, got)) {
+      ok = false;
+      return;
+    }
+    tc::tc_fence_after();
+    const int q = q0 + tid;
+    float* out = mult + (long long)q * nt_d + (long long)j * SC_N;
+    const unsigned base = tmem + ((unsigned)(warp * 32) << 16) + (unsigned)((j & 1) * SC_N);
+#pragma unroll 1
+    for (int c0 = 0; c0 < SC_N; c0 += 32) {
+      float v[32];
+      tc::tmem_ld32(base + (unsigned)c0, v);
+      if (q < ntr) {
+        const int t0 = j * SC_N + c0;
+        if (vec && t0 + 32 <= nt_d) {
+#pragma unroll
+          for (int i = 0; i < 32; i += 4)
+            __stcs(reinterpret_cast<float4*>(out + c0 + i), make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]));
+        } else {
+#pragma unroll
+          for (int i = 0; i < 32; ++i)
+            if (t0 + i < nt_d) out[c0 + i] = v[i];
+        }
+      }
+    }
+    tc::tc_fence_before();
+  };
+  for (int j = 0; j < ntile; ++j) {
+    if (tid == 0) {
+      // TMEM buffer j % 2 was drained by the epilogue of tile j - 2 (before the last barrier)
+      if (!tc::mbar_wait(bfull(j & 1), (j >> 1) & 1)) {
+        fail = 1;
+      } else {
+        waited = j + 1;
+        tc::tc_fence_after();
+        const unsigned dt = tmem + (unsigned)((j & 1) * SC_N);
+        const unsigned bh = b_hi(j & 1), bl = bh + SC_N * 128;
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks) {
+          const unsigned o = 32u * ks;
+          const uint64_t dah = tc::sdesc_sw128(ah + o), dal = tc::sdesc_sw128(al + o);
+          const uint64_t dbh = tc::sdesc_sw128(bh + o), dbl = tc::sdesc_sw128(bl + o);
+          tc::mma_bf16(dt, dah, dbh, idesc, ks > 0);
+          tc::mma_bf16(dt, dah, dbl, idesc, true);
+          tc::mma_bf16(dt, dal, dbh, idesc, true);
+        }
+        tc::mma_commit(mdone(j & 1));
+      }
+    }
+    __syncthreads();
+    if (fail) {
+      ok = false;
+      break;
+    }
+    if (j >= 1) {
+      epilogue(j - 1);  // also proves the MMAs of tile j - 1 done: its B buffer is free
+      if (!__syncthreads_and(ok)) {
+        ok = false;
+        break;
+      }
+    }
+    if (tid == 0 && j + 1 < ntile) {
+      if (j == 0 || ok) {
+        issue_b(j + 1);
+        issued = j + 2;
+      }
+    }
+    __syncthreads();
+  }
+  if (ok && ntile > 0) epilogue(ntile - 1);
+  if (tid == 0) {  // no copy or MMA left in flight (bounded)
+    for (int j = waited; j < issued; ++j) tc::mbar_wait(bfull(j & 1), (j >> 1) & 1);
+    if (waited > 0) tc::mbar_wait(mdone((waited - 1) & 1), ((waited - 1) >> 1) & 1);
+  }
+  const bool okall = __syncthreads_and(ok) && !fail;
+  if (!okall && tid == 0) atomicExch(err, 1);
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, 2 * SC_N);
+}
+
+// Synthesis twiddle tiles: for every 256 samples, a hi and a lo tile of [256 samples][64
+// components] bf16 in the K-major 128-byte swizzle (row t, component c at byte (t/8)*1024 +
+// (t%8)*128 + (((2c/16) ^ (t%8)) * 16) + 2c%16); component 2k = cos(2 pi f_k t dt), 2k + 1 =
+// -sin(2 pi f_k t dt) with the phase reduced as 2 pi frac(f_k t dt) in double precision; hi =
+// bf16(w), lo = bf16(w - hi); components >= 2 nf and samples >= nt are zero.
+std::vector<unsigned char> synth_twiddle_tiles(const std::vector<double>& f, double dt, int nt) {
+  const int nf = (int)f.size();
+  const int ntile = (nt + SC_N - 1) / SC_N;
+  std::vector<unsigned char> out((size_t)ntile * SC_B, 0);
+  for (int t = 0; t < nt; ++t) {
+    unsigned char* hi = out.data() + (size_t)(t / SC_N) * SC_B;
+    unsigned char* lo = hi + (size_t)SC_N * 128;
+    const int r = t % SC_N;
+    for (int k = 0; k < nf && 2 * k + 1 < 64; ++k) {
+      double ph = f[k] * (double)t * dt;
+      ph -= std::floor(ph);
+      const double a = 2.0 * M_PI * ph;
+      const double v[2] = {std::cos(a), -std::sin(a)};
+      for (int qq = 0; qq < 2; ++qq) {
+        const int c = 2 * k + qq;
+        const size_t off = (size_t)(r >> 3) * 1024 + (r & 7) * 128 +
+                           ((((2 * c) >> 4) ^ (r & 7)) << 4) + ((2 * c) & 15);
+        const __nv_bfloat16 h = __float2bfloat16_rn((float)v[qq]);
+        const __nv_bfloat16 l = __float2bfloat16_rn((float)(v[qq] - (double)__bfloat162float(h)));
+        std::memcpy(hi + off, &h, 2);
+        std::memcpy(lo + off, &l, 2);
+      }
+    }
+  }
+  return out;
+}
+
+cudaError_t launch_synth_tc(const float2* Dh, int nrec, int ns, int ld, int s0, int nf,
+                            const float* w, const unsigned char* tws, int nt_d, float* mult,
+                            int* err, cudaStream_t st) {
+  const int ntr = nrec * ns;
+  const size_t smem = synth_tc_smem();
+  const bool vec = (nt_d & 3) == 0 && (reinterpret_cast<uintptr_t>(mult) & 15) == 0;
+  auto kern = vec ? k_synth_tc<true> : k_synth_tc<false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  count_launches(1);
+  kern<<<(ntr + SC_M - 1) / SC_M, 128, smem, st>>>(Dh, nrec, ld, s0, nf, w, tws, nt_d, mult, ntr, err);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_synth(const float2* Dh, int nrec, int ns, int ld, int s0, int nf, const float* w,
-                         const float2* tw, int nt_d, float* mult, cudaStream_t st) {
+                         const float2* tw, int nt_d, float* mult, cudaStream_t st,
+                         const unsigned char* tws, int* err) {
   if (nf > NFMAX) return cudaErrorInvalidValue;
+  if (tws && err && 2 * nf <= 64)
+    return launch_synth_tc(Dh, nrec, ns, ld, s0, nf, w, tws, nt_d, mult, err, st);
   const int ntr = nrec * ns;
   const size_t smem = sizeof(float2) * (size_t)nf * SY_TR + 2 * sizeof(float) * (size_t)nf * SY_TP;
   if (smem > 48 * 1024) {

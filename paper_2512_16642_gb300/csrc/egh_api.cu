@@ -65,6 +65,7 @@ struct egh_ctx {
   CUtensorMap tmap_ghb{};                    // TMA map of ghb
   float2 *Qh = nullptr, *Lh = nullptr, *tw = nullptr;
   unsigned char* twt_deb = nullptr;  // the deblur transform's twiddle tiles (tw_len levels)
+  unsigned char* tws_deb = nullptr;  // the synthesis twiddle tiles (tw_len samples)
   float2* Wh = nullptr;  // mixed precision: W = L^{-1} per frequency (solves as products)
   int tw_len = 0;
   cudaStream_t side = nullptr;                 // the transform's stream inside egh_green (low priority)
@@ -196,8 +197,10 @@ egh_status ensure_twiddles(egh_ctx* ctx, int len, cudaStream_t stream) {
   CK(cudaStreamSynchronize(stream));
   if (ctx->tw) CK(cudaFree(ctx->tw));
   if (ctx->twt_deb) CK(cudaFree(ctx->twt_deb));
+  if (ctx->tws_deb) CK(cudaFree(ctx->tws_deb));
   ctx->tw = nullptr;
   ctx->twt_deb = nullptr;
+  ctx->tws_deb = nullptr;
   ctx->tw_len = 0;
   egh_status s = dalloc(ctx, (void**)&ctx->tw, h.size() * sizeof(float2), "twiddles");
   if (s) return s;
@@ -205,6 +208,9 @@ egh_status ensure_twiddles(egh_ctx* ctx, int len, cudaStream_t stream) {
   const std::vector<unsigned char> t = dft_twiddle_tiles(ctx->freqs, ctx->dt, len);
   if ((s = dalloc(ctx, (void**)&ctx->twt_deb, t.size(), "deblur twiddle tiles"))) return s;
   CK(cudaMemcpy(ctx->twt_deb, t.data(), t.size(), cudaMemcpyHostToDevice));
+  const std::vector<unsigned char> u = synth_twiddle_tiles(ctx->freqs, ctx->dt, len);
+  if ((s = dalloc(ctx, (void**)&ctx->tws_deb, u.size(), "synthesis twiddle tiles"))) return s;
+  CK(cudaMemcpy(ctx->tws_deb, u.data(), u.size(), cudaMemcpyHostToDevice));
   ctx->tw_len = len;
   return EGH_OK;
 }
@@ -268,7 +274,7 @@ cudaError_t zero_snap_slot(egh_ctx* ctx, int j, cudaStream_t st) {
 }
 
 void free_all(egh_ctx* c) {
-  void* ptrs[] = {c->twt_deb, c->twt_bl, c->Wh, c->Dr, c->Rr, c->coef, c->lev, c->snap, c->twt, c->gh, c->ghb, c->part, c->Qh, c->Lh, c->tw, c->w_dev,
+  void* ptrs[] = {c->tws_deb, c->twt_deb, c->twt_bl, c->Wh, c->Dr, c->Rr, c->coef, c->lev, c->snap, c->twt, c->gh, c->ghb, c->part, c->Qh, c->Lh, c->tw, c->w_dev,
                   c->rec_pts, c->status, c->dsum, c->lmax, c->vchk, c->d_err, c->vel_stage, c->Dh,
                   c->io_in, c->io_out};
   for (void* p : ptrs)
@@ -906,7 +912,8 @@ static egh_status deblur_common(egh_ctx* ctx, const float* resid, int32_t ns, in
   } else {
     CK(launch_trsm(ctx->Lh, ctx->nrec, ctx->nf, D, ns, stream));
   }
-  if (!X) CK(launch_synth(D, ctx->nrec, ns, ns, 0, ctx->nf, ctx->w_dev, ctx->tw, nt_d, dout, stream));
+  if (!X) CK(launch_synth(D, ctx->nrec, ns, ns, 0, ctx->nf, ctx->w_dev, ctx->tw, nt_d, dout, stream,
+                           ctx->tws_deb, ctx->d_err));
   CK(cudaEventRecord(ctx->ev[7], stream));
   ctx->ev_rec[3] = true;
   ctx->st.deblur_sources = ns;

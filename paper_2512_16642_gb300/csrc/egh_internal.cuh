@@ -136,7 +136,11 @@ cudaError_t launch_resid(const float2* Qh, int n, int nf, const float2* Xh, cons
                          int ns, float2* Rh, bool fp64, cudaStream_t st);
 inline bool prec_mixed(int prec) { return prec == EGH_PREC_MIXED || prec == EGH_PREC_MIXED_FP64; }
 cudaError_t launch_add_correction(float2* X, const float2* R, long long m, cudaStream_t st);
+// (on the tensor cores when tws, the synthesis twiddle tiles for at least nt_d samples, and err
+// are given and 2 nf <= 64; else on the CUDA cores)
 cudaError_t launch_synth(const float2* Dh, int nrec, int ns, int ld, int s0, int nf, const float* w,
-                         const float2* tw, int nt_d, float* mult, cudaStream_t st);
+                         const float2* tw, int nt_d, float* mult, cudaStream_t st,
+                         const unsigned char* tws = nullptr, int* err = nullptr);
+std::vector<unsigned char> synth_twiddle_tiles(const std::vector<double>& f, double dt, int nt);
 
 }  // namespace egh

@@ -89,6 +89,7 @@ struct HSet {
   float2 *Qh = nullptr, *Lh = nullptr, *tw = nullptr;
   float2* Wh = nullptr;  // mixed precision: W = L^{-1}
   unsigned char* twt = nullptr;  // tensor-core transform twiddle tiles (tw_len levels)
+  unsigned char* tws = nullptr;  // tensor-core synthesis twiddle tiles (tw_len samples)
   float* w = nullptr;
 };
 
@@ -211,7 +212,9 @@ cudaError_t run_batch(Server* sv, Batch* b, const HSet& h) {
   s0 = 0;
   for (Request* r : b->reqs) {
     float* dout = reinterpret_cast<float*>(sv->arena_base + r->off_out);
-    if ((e = launch_synth(D, h.nrec, r->ns, ld, s0, h.nf, h.w, h.tw, r->nt_d, dout, st))) return e;
+    if ((e = launch_synth(D, h.nrec, r->ns, ld, s0, h.nf, h.w, h.tw, r->nt_d, dout, st, h.tws,
+                          sv->d_err)))
+      return e;
     if ((e = cudaMemcpyAsync(r->mult, dout, r->bytes, cudaMemcpyDeviceToHost, st))) return e;
     s0 += r->ns;
   }
@@ -393,6 +396,7 @@ egh_status egh_server_add_set(egh_server* sv, int32_t nrec, int32_t nfreq, const
   cudaStream_t st = sv->streams[0];
   auto cleanup = [&]() {
     cudaFree(h.twt);
+    cudaFree(h.tws);
     cudaFree(h.Wh);
     cudaFree(h.Qh);
     cudaFree(h.Lh);
@@ -413,6 +417,11 @@ egh_status egh_server_add_set(egh_server* sv, int32_t nrec, int32_t nfreq, const
     const std::vector<unsigned char> t = dft_twiddle_tiles(f, dt, max_nt);
     e = cudaMalloc(&h.twt, t.size());
     if (!e) e = cudaMemcpy(h.twt, t.data(), t.size(), cudaMemcpyHostToDevice);
+  }
+  if (!e) {
+    const std::vector<unsigned char> u = synth_twiddle_tiles(f, dt, max_nt);
+    e = cudaMalloc(&h.tws, u.size());
+    if (!e) e = cudaMemcpy(h.tws, u.data(), u.size(), cudaMemcpyHostToDevice);
   }
   if (!e) e = cudaMemcpy(h.w, w.data(), w.size() * sizeof(float), cudaMemcpyHostToDevice);
   if (!e) e = launch_potrf(h.Lh, nrec, nfreq, status, st, prec_mixed(sv->prec) ? 1 : 0);
@@ -569,6 +578,7 @@ void egh_server_destroy(egh_server* sv) {
   for (auto& s : sv->streams) cudaStreamDestroy(s);
   for (HSet& h : sv->sets) {
     cudaFree(h.twt);
+    cudaFree(h.tws);
     cudaFree(h.Wh);
     cudaFree(h.Qh);
     cudaFree(h.Lh);
