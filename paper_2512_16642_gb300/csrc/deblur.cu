@@ -925,19 +925,20 @@ cudaError_t launch_add_correction(float2* X, const float2* R, long long m, cudaS
 // Synthesis on the tensor cores: mult[q][t] = sum_c A[q][c] B[t][c] with A[q][2k] = w_k Re X_k,
 // A[q][2k+1] = w_k Im X_k (the weighted solutions of trace q) and B[t][2k] = cos(theta),
 // B[t][2k+1] = -sin(theta) (host tiles of 256 samples x 64 components, bf16 hi/lo, K-major
-// 128-byte swizzle).  128 traces per CTA: the threads gather, weight and split their solutions
-// into the A tile once, then every 256-sample tile is one bf16x3 M128 x N256 x K64 product into
-// one of two TMEM buffers, drained by the threads straight to global memory while the next
-// tile's MMAs run.  Needs 2 nf <= 64.  Every wait is bounded.
+// 128-byte swizzle).  128 traces x SC_SEG tiles of 256 samples per CTA: the threads gather,
+// weight and split their solutions into the A tile once, then every 256-sample tile is one
+// bf16x3 M128 x N256 x K64 product into one of two TMEM buffers, drained by eight warps (lane
+// quarter w % 4, column half w / 4) straight to global memory while the next tile's MMAs run.
+// Needs 2 nf <= 64.  Every wait is bounded.
 // ---------------------------------------------------------------------------------------------
-constexpr int SC_M = 128, SC_N = 256;
+constexpr int SC_M = 128, SC_N = 256, SC_SEG = 4;  // tiles of 256 samples per CTA
 constexpr unsigned SC_A = SC_M * 128;         // one A plane (hi or lo)
 constexpr unsigned SC_B = 2u * SC_N * 128u;   // one B tile (hi + lo)
 
 size_t synth_tc_smem() { return 1024 + 2 * (size_t)SC_A + 2 * (size_t)SC_B; }
 
 template <bool VEC>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(256)
     k_synth_tc(const float2* __restrict__ Dh, int nrec, int ld, int s0, int nf,
                const float* __restrict__ w, const unsigned char* __restrict__ tws, int nt_d,
                float* __restrict__ mult, int ntr, int* __restrict__ err) {
@@ -948,7 +949,8 @@ __global__ void __launch_bounds__(128)
   __shared__ int fail;
   const int tid = threadIdx.x, warp = tid >> 5;
   const int q0 = blockIdx.x * SC_M;
-  const int ntile = (nt_d + SC_N - 1) / SC_N;
+  const int j0 = blockIdx.y * SC_SEG;  // first 256-sample tile of this CTA
+  const int ntile = min(SC_SEG, (nt_d + SC_N - 1) / SC_N - j0);
   const unsigned bar0 = tc::smem_u32(&bars[0]);
   auto bfull = [&](int i) { return bar0 + 8u * i; };
   auto mdone = [&](int i) { return bar0 + 8u * (2 + i); };
@@ -962,10 +964,10 @@ __global__ void __launch_bounds__(128)
   auto b_hi = [&](int b) { return tc::smem_u32(sm + 2 * SC_A + (size_t)b * SC_B); };
   // A tile: row m = trace q0 + m, components c = 2k (re), 2k + 1 (im), zero past 2 nf and ntr
   {
-    const int m = tid, q = q0 + m;
+    const int m = tid & (SC_M - 1), q = q0 + m;
     const int sidx = q / nrec, r = q % nrec;
 #pragma unroll 4
-    for (int k = 0; k < 32; ++k) {
+    for (int k = (tid >> 7) * 16; k < (tid >> 7) * 16 + 16; ++k) {
       float2 x = make_float2(0.f, 0.f);
       if (q < ntr && k < nf) {
         x = Dh[((long long)k * nrec + r) * ld + s0 + sidx];
@@ -992,29 +994,31 @@ __global__ void __launch_bounds__(128)
   const unsigned tmem = tslot;
   auto issue_b = [&](int j) {
     tc::mbar_expect_tx(bfull(j & 1), SC_B);
-    tc::bulk_g2s(b_hi(j & 1), tws + (size_t)j * SC_B, SC_B, bfull(j & 1));
+    tc::bulk_g2s(b_hi(j & 1), tws + (size_t)(j0 + j) * SC_B, SC_B, bfull(j & 1));
   };
   if (tid == 0 && ntile > 0) issue_b(0);
   const unsigned idesc = tc::idesc_bf16(SC_M, SC_N, 0, 0);
   const bool vec = VEC;
   int issued = ntile > 0 ? 1 : 0, waited = 0;
   bool ok = true;
-  auto epilogue = [&](int j) {  // TMEM buffer j % 2 -> mult[q][256 j ..]
+  auto epilogue = [&](int j) {  // TMEM buffer j % 2 -> mult[q][256 (j0 + j) ..]
     const bool got = tc::mbar_wait(mdone(j & 1), (j >> 1) & 1);
     if (!__all_sync(0xffffffffu, got)) {
       ok = false;
       return;
     }
     tc::tc_fence_after();
-    const int q = q0 + tid;
-    float* out = mult + (long long)q * nt_d + (long long)j * SC_N;
-    const unsigned base = tmem + ((unsigned)(warp * 32) << 16) + (unsigned)((j & 1) * SC_N);
+    const int qq = warp & 3, hh = warp >> 2;
+    const int q = q0 + qq * 32 + (tid & 31);
+    float* out = mult + (long long)q * nt_d + (long long)(j0 + j) * SC_N;
+    const unsigned base =
+        tmem + ((unsigned)(qq * 32) << 16) + (unsigned)((j & 1) * SC_N + hh * (SC_N / 2));
 #pragma unroll 1
-    for (int c0 = 0; c0 < SC_N; c0 += 32) {
+    for (int c0 = hh * (SC_N / 2); c0 < (hh + 1) * (SC_N / 2); c0 += 32) {
       float v[32];
-      tc::tmem_ld32(base + (unsigned)c0, v);
+      tc::tmem_ld32(base + (unsigned)(c0 - hh * (SC_N / 2)), v);
       if (q < ntr) {
-        const int t0 = j * SC_N + c0;
+        const int t0 = (j0 + j) * SC_N + c0;
         if (vec && t0 + 32 <= nt_d) {
 #pragma unroll
           for (int i = 0; i < 32; i += 4)
@@ -1124,7 +1128,9 @@ cudaError_t launch_synth_tc(const float2* Dh, int nrec, int ns, int ld, int s0, 
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   count_launches(1);
-  kern<<<(ntr + SC_M - 1) / SC_M, 128, smem, st>>>(Dh, nrec, ld, s0, nf, w, tws, nt_d, mult, ntr, err);
+  const int ntile = (nt_d + SC_N - 1) / SC_N;
+  const dim3 grid((ntr + SC_M - 1) / SC_M, (ntile + SC_SEG - 1) / SC_SEG);
+  kern<<<grid, 256, smem, st>>>(Dh, nrec, ld, s0, nf, w, tws, nt_d, mult, ntr, err);
   return cudaGetLastError();
 }
 
