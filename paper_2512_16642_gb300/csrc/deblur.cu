@@ -811,6 +811,19 @@ __device__ __forceinline__ void dot2_add(float& s, float& c, float a, float b) {
   c = __fadd_rn(c, __fadd_rn(q, e));
 }
 
+// The same for a pair of sums at once (real and imaginary parts) in packed FP32x2 instructions:
+// element by element the operations and their roundings are those of dot2_add.
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ void dot2_add2(float2& s, float2& c, float2 a, float2 b) {
+  const float2 p = __fmul2_rn(a, b);
+  const float2 e = __ffma2_rn(a, b, neg2(p));
+  const float2 t = __fadd2_rn(s, p);
+  const float2 bp = __fadd2_rn(t, neg2(s));
+  const float2 q = __fadd2_rn(__fadd2_rn(s, neg2(__fadd2_rn(t, neg2(bp)))), __fadd2_rn(p, neg2(bp)));
+  s = t;
+  c = __fadd2_rn(c, __fadd2_rn(q, e));
+}
+
 __global__ void __launch_bounds__(32 * TS_W)
     k_resid_dot2(const float2* __restrict__ Qh, int n, const float2* __restrict__ Xh,
                  const float2* __restrict__ Dh, int ns, float2* __restrict__ Rh) {
@@ -835,25 +848,20 @@ __global__ void __launch_bounds__(32 * TS_W)
       da = Dh[off + (long long)i * ns + col];
       if (two) db = Dh[off + (long long)(i + 1) * ns + col];
     }
-    // R = D - Q X: real part adds (-q.x) x.x and q.y x.y, imaginary part (-q.x) x.y and (-q.y) x.x
-    float sar = da.x, car = 0.f, sai = da.y, cai = 0.f;
-    float sbr = db.x, cbr = 0.f, sbi = db.y, cbi = 0.f;
+    // R = D - Q X: the real part adds (-q.x) x.x then q.y x.y, the imaginary part (-q.x) x.y then
+    // (-q.y) x.x; (real, imaginary) sums and their compensations run as packed pairs
+    float2 sa = da, ca = make_float2(0.f, 0.f), sb = db, cb = make_float2(0.f, 0.f);
     for (int j = 0; j < n; ++j) {
-      const float2 x = Xs[j * 32 + lane];
+      const float2 x = Xs[j * 32 + lane], xs = make_float2(x.y, x.x);
       const float2 a = __ldg(qa + j), b = __ldg(qb + j);
-      dot2_add(sar, car, -a.x, x.x);
-      dot2_add(sar, car, a.y, x.y);
-      dot2_add(sai, cai, -a.x, x.y);
-      dot2_add(sai, cai, -a.y, x.x);
-      dot2_add(sbr, cbr, -b.x, x.x);
-      dot2_add(sbr, cbr, b.y, x.y);
-      dot2_add(sbi, cbi, -b.x, x.y);
-      dot2_add(sbi, cbi, -b.y, x.x);
+      dot2_add2(sa, ca, make_float2(-a.x, -a.x), x);
+      dot2_add2(sa, ca, make_float2(a.y, -a.y), xs);
+      dot2_add2(sb, cb, make_float2(-b.x, -b.x), x);
+      dot2_add2(sb, cb, make_float2(b.y, -b.y), xs);
     }
     if (valid) {
-      Rh[off + (long long)i * ns + col] = make_float2(__fadd_rn(sar, car), __fadd_rn(sai, cai));
-      if (two)
-        Rh[off + (long long)(i + 1) * ns + col] = make_float2(__fadd_rn(sbr, cbr), __fadd_rn(sbi, cbi));
+      Rh[off + (long long)i * ns + col] = __fadd2_rn(sa, ca);
+      if (two) Rh[off + (long long)(i + 1) * ns + col] = __fadd2_rn(sb, cb);
     }
   }
 }
