@@ -62,8 +62,9 @@ def _args():
                    help="receivers of the profiling slice (231 gives the full-size Hessian)")
     p.add_argument("--slice-nt", type=int, default=1024, help="time steps of the profiling slice")
     p.add_argument("--no-serving", action="store_true", help="skip the serving-form measurement")
-    p.add_argument("--workload", choices=["layered", "salt"], default="layered",
-                   help="layered (the benchmark workload) or the batched salt-patch form")
+    p.add_argument("--workload", choices=["layered", "salt", "deblur"], default="layered",
+                   help="layered (the benchmark workload), the batched salt-patch form, or the "
+                        "deblur kernels alone at the layered shape (for profiling captures)")
     p.add_argument("--precision", choices=["mixed", "fp32"], default="mixed",
                    help="Hessian arithmetic: bf16x3 tensor-core Gram (mixed) or FP32 CUDA-core Gram")
     p.add_argument("--dft-chunk", type=int, default=0,
@@ -687,12 +688,47 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
 
 
+def run_deblur(args):
+    """The deblur kernels alone at the layered workload's shape (231 receivers, 26 frequencies
+    3.0:0.2:8.0 Hz, 115 sources x 4000 samples), through a serving set so that no Green stage
+    runs: a seeded synthetic Hermitian positive-definite Hessian set (Q_k = A A^H / m + 0.05 mean
+    diag I) and band-limited noise residuals from pinned host memory.  Prints one JSON line with
+    the request latency (host copies included) for profiling captures; not the benchmark."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2512_16642_gb300 import egh
+
+    rng = np.random.default_rng(3)
+    n, nf, ns, nt = 231, 26, 115, 4000
+    A = (rng.standard_normal((nf, n, 2 * n)) + 1j * rng.standard_normal((nf, n, 2 * n))) / np.sqrt(2 * n)
+    Q = A @ A.conj().transpose(0, 2, 1)
+    Q += 0.05 * np.mean(np.einsum("kii->ki", Q).real) * np.eye(n)
+    Q = (0.5 * (Q + Q.conj().transpose(0, 2, 1))).astype(np.complex64)
+    f = np.round(np.arange(3.0, 8.0 + 1e-9, 0.2), 6)
+    r = synth.bandlimited_noise(rng, (ns, n, nt), 1e-3, 3.0, 8.0)
+    prec = egh.EGH_PREC_MIXED if args.precision == "mixed" else egh.EGH_PREC_FP32
+    lat = []
+    with egh.Server(8 << 30, slots=2, max_batch_sources=ns, precision=prec) as sv:
+        sid = sv.add_set(Q, f, 1e-3, nt, nt)
+        rin = torch.from_numpy(np.ascontiguousarray(r, np.float32)).pin_memory()
+        out = torch.empty_like(rin).pin_memory()
+        for _ in range(max(1, args.steps)):
+            lat.append(sv.wait(sv.submit(sid, rin, out)))
+    print(json.dumps({"workload": "deblur kernels alone, layered shape (231 receivers, 26 frequencies, "
+                                  "115 sources x 4000 samples), synthetic HPD Hessians",
+                      "precision": args.precision, "latency_s": lat}), flush=True)
+
+
 def main():
     args = _args()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "salt":
         run_salt(args)
+    elif args.workload == "deblur":
+        run_deblur(args)
     else:
         run_ours(args)
 
