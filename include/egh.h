@@ -111,7 +111,9 @@ typedef struct {
     const double *freq_hz; /* [nfreq], host */
     int32_t batch_receivers; /* receivers propagated together; 0 = min(nrec, 16) */
     int32_t dft_chunk;       /* levels per transform chunk: 32, 64, 128, 256 or 512; 0 = 512 */
-    int32_t gram_splits;     /* split of the grid sum in the Gram; 0 = default */
+    int32_t gram_splits;     /* split of the grid sum in the Gram; 0 = chosen by the library
+                                (tensor-core Gram: half, once or twice a default, timed on the
+                                first egh_hessian) */
     int32_t fd_rows;         /* FD rows per warp: 12, 16, 20, 24 or 32; 0 = timed on the first
                                 egh_green of the context and the fastest kept */
     int32_t precision;       /* egh_precision of the Hessian stage (0 = EGH_PREC_FP32) */

@@ -940,10 +940,13 @@ cudaError_t launch_add_correction(float2* X, const float2* R, long long m, cudaS
 // Needs 2 nf <= 64.  Every wait is bounded.
 // ---------------------------------------------------------------------------------------------
 constexpr int SC_M = 128, SC_N = 256, SC_SEG = 4;  // tiles of 256 samples per CTA
+constexpr int SC_STG = 36;  // row length (floats) of the per-warp 32 x 32 staging tiles
 constexpr unsigned SC_A = SC_M * 128;         // one A plane (hi or lo)
 constexpr unsigned SC_B = 2u * SC_N * 128u;   // one B tile (hi + lo)
 
-size_t synth_tc_smem() { return 1024 + 2 * (size_t)SC_A + 2 * (size_t)SC_B; }
+size_t synth_tc_smem() {
+  return 1024 + 2 * (size_t)SC_A + 2 * (size_t)SC_B + 8 * 32 * SC_STG * sizeof(float);
+}
 
 template <bool VEC>
 __global__ void __launch_bounds__(256)
@@ -970,6 +973,7 @@ __global__ void __launch_bounds__(256)
   }
   const unsigned ah = tc::smem_u32(sm), al = ah + SC_A;
   auto b_hi = [&](int b) { return tc::smem_u32(sm + 2 * SC_A + (size_t)b * SC_B); };
+  float* stage_all = reinterpret_cast<float*>(sm + 2 * SC_A + 2 * SC_B);  // [8 warps][32][SC_STG]
   // A tile: row m = trace q0 + m, components c = 2k (re), 2k + 1 (im), zero past 2 nf and ntr
   {
     const int m = tid & (SC_M - 1), q = q0 + m;
@@ -1016,27 +1020,39 @@ __global__ void __launch_bounds__(256)
       return;
     }
     tc::tc_fence_after();
-    const int qq = warp & 3, hh = warp >> 2;
-    const int q = q0 + qq * 32 + (tid & 31);
-    float* out = mult + (long long)q * nt_d + (long long)(j0 + j) * SC_N;
+    const int qq = warp & 3, hh = warp >> 2, lane = tid & 31;
     const unsigned base =
         tmem + ((unsigned)(qq * 32) << 16) + (unsigned)((j & 1) * SC_N + hh * (SC_N / 2));
+    // each 32 x 32 block goes through this warp's staging tile so that a store instruction
+    // writes four full 128-byte rows: lanes 8i .. 8i + 7 cover row 4p + i of pass p
+    float* stg = stage_all + warp * (32 * SC_STG);
 #pragma unroll 1
     for (int c0 = hh * (SC_N / 2); c0 < (hh + 1) * (SC_N / 2); c0 += 32) {
       float v[32];
       tc::tmem_ld32(base + (unsigned)(c0 - hh * (SC_N / 2)), v);
-      if (q < ntr) {
-        const int t0 = (j0 + j) * SC_N + c0;
-        if (vec && t0 + 32 <= nt_d) {
 #pragma unroll
-          for (int i = 0; i < 32; i += 4)
-            __stcs(reinterpret_cast<float4*>(out + c0 + i), make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]));
-        } else {
+      for (int i = 0; i < 32; i += 4)
+        *reinterpret_cast<float4*>(stg + lane * SC_STG + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+      __syncwarp();
+      const int t = (j0 + j) * SC_N + c0 + 4 * (lane & 7);
 #pragma unroll
-          for (int i = 0; i < 32; ++i)
-            if (t0 + i < nt_d) out[c0 + i] = v[i];
+      for (int pp = 0; pp < 8; ++pp) {
+        const int rl = 4 * pp + (lane >> 3);
+        const int q = q0 + qq * 32 + rl;
+        const float4 x = *reinterpret_cast<const float4*>(stg + rl * SC_STG + 4 * (lane & 7));
+        if (q < ntr) {
+          float* out = mult + (long long)q * nt_d + t;
+          if (vec && t + 3 < nt_d) {
+            __stcs(reinterpret_cast<float4*>(out), x);
+          } else {
+            const float xv[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+              if (t + i < nt_d) out[i] = xv[i];
+          }
         }
       }
+      __syncwarp();
     }
     tc::tc_fence_before();
   };

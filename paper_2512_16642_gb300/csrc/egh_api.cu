@@ -50,6 +50,7 @@ struct egh_ctx {
   int fd_tz = 0;  // FD rows per warp (0 = library default)
   int prec = EGH_PREC_FP32;
   int splits_tc = 0;  // grid-sum splits of the tensor-core Gram
+  bool tune_splits = false;  // time half / once / twice the default splits on the first Gram
   Layout L{};
   Stencil S{};
   // device state
@@ -454,6 +455,7 @@ egh_status egh_create(const egh_config* cfg, egh_ctx** out) {
     s = std::max(1LL, std::min(s, L.G / 2048));
     ctx->splits = c.gram_splits ? c.gram_splits : (int)std::max(1LL, s);
     ctx->splits_tc = c.gram_splits ? c.gram_splits : gram_tc_splits(c.nrec, c.nfreq, L.G);
+    ctx->tune_splits = c.gram_splits == 0;
   }
 
   for (int k = 0; k < 4; ++k) {
@@ -481,7 +483,9 @@ egh_status egh_create(const egh_config* cfg, egh_ctx** out) {
   ALLOC(ctx->twt, twt.size(), "twiddle tiles");
   ALLOC(ctx->part,
         std::max(gram_workspace_floats(c.nrec, c.nfreq, ctx->splits),
-                 gram_tc_workspace_floats(c.nrec, c.nfreq, ctx->splits_tc)) * sizeof(float),
+                 gram_tc_workspace_floats(c.nrec, c.nfreq,
+                                          ctx->tune_splits ? 2 * ctx->splits_tc : ctx->splits_tc)) *
+            sizeof(float),
         "gram");
   ALLOC(ctx->Qh, (size_t)c.nfreq * c.nrec * c.nrec * sizeof(float2), "Qh");
   ALLOC(ctx->Lh, (size_t)c.nfreq * c.nrec * c.nrec * sizeof(float2), "Lh");
@@ -766,6 +770,33 @@ egh_status egh_hessian(egh_ctx* ctx, egh_mu_mode mode, double mu_param, double* 
   if (mode != EGH_MU_ABS && mode != EGH_MU_REL_MEANDIAG && mode != EGH_MU_REL_MAXEIG)
     return fail(ctx, EGH_EINVAL, "unknown mu mode");
   CK(cudaEventRecord(ctx->ev[2], stream));
+  if (prec_mixed(ctx->prec) && ctx->tune_splits) {
+    // grid-sum splits of the tensor-core Gram: time half, once and twice the default on this
+    // problem (the result is discarded; the run below recomputes it) and keep the fastest
+    const int base = ctx->splits_tc;
+    const long long cap = ctx->L.G / (16LL * 64);
+    float best = 1e30f;
+    int best_s = base;
+    for (int cand : {std::max(1, base / 2), base, 2 * base}) {
+      if (cand > cap && cand != base) continue;
+      float ms = 0.f;
+      for (int rep = 0; rep < 2; ++rep) {  // the first pass warms up
+        CK(cudaEventRecord(ctx->ev_gram[0], stream));
+        CK(launch_gram_tc(ctx->tmap_ghb, ctx->nrec, ctx->nf, ctx->L.G, cand, ctx->part,
+                          ctx->d_err, stream));
+        CK(launch_gram_tc_finish(ctx->part, ctx->nrec, ctx->nf, cand, ctx->Qh, stream));
+        CK(cudaEventRecord(ctx->ev_gram[1], stream));
+        CK(cudaEventSynchronize(ctx->ev_gram[1]));
+        CK(cudaEventElapsedTime(&ms, ctx->ev_gram[0], ctx->ev_gram[1]));
+      }
+      if (ms < best) {
+        best = ms;
+        best_s = cand;
+      }
+    }
+    ctx->splits_tc = best_s;
+    ctx->tune_splits = false;
+  }
   CK(cudaEventRecord(ctx->ev_gram[0], stream));
   if (prec_mixed(ctx->prec)) {
     CK(launch_gram_tc(ctx->tmap_ghb, ctx->nrec, ctx->nf, ctx->L.G, ctx->splits_tc, ctx->part,
