@@ -851,6 +851,7 @@ __global__ void __launch_bounds__(32 * TS_W)
     // R = D - Q X: the real part adds (-q.x) x.x then q.y x.y, the imaginary part (-q.x) x.y then
     // (-q.y) x.x; (real, imaginary) sums and their compensations run as packed pairs
     float2 sa = da, ca = make_float2(0.f, 0.f), sb = db, cb = make_float2(0.f, 0.f);
+#pragma unroll 4
     for (int j = 0; j < n; ++j) {
       const float2 x = Xs[j * 32 + lane], xs = make_float2(x.y, x.x);
       const float2 a = __ldg(qa + j), b = __ldg(qb + j);
