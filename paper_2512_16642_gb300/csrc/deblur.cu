@@ -170,8 +170,8 @@ cudaError_t launch_trace_dft(const float* resid, int ntr, int nt_d, const float2
                              int nrec, int ld, int s0, float2* Dh, cudaStream_t st,
                              const unsigned char* twt, int* err) {
   if (nf < 1 || nf > NFMAX) return cudaErrorInvalidValue;
-  // tensor cores when the twiddle tiles are given and N = 2 nf rounded up to 32 is at most 64
-  if (twt && err && tt_ncomp(nf) <= 64)
+  // tensor cores when the twiddle tiles are given (N = 2 nf rounded up to 32 is at most 128)
+  if (twt && err && tt_ncomp(nf) <= 128)
     return launch_trace_dft_tc(resid, ntr, nt_d, twt, nf, nrec, ld, s0, Dh, err, st);
   const int groups = (nf + 7) / 8;
   const size_t smem = trace_dft_smem(nf);
@@ -190,8 +190,8 @@ cudaError_t launch_trace_dft(const float* resid, int ntr, int nt_d, const float2
 // ---------------------------------------------------------------------------------------------
 // Forward transform on the tensor cores: D[q][c] = sum_t resid[q][t] W[c][t] with W the twiddle
 // tiles of the Green-stage transform (component c = 2k: cos, 2k + 1: -sin; 64 levels per tile,
-// bf16 hi/lo, K-major 128-byte swizzle).  128 traces per CTA (MMA M = 128), N = 2 nf rounded up
-// to 32, 64 samples per stage.  The traces are read with coalesced 16-byte loads one stage ahead
+// bf16 hi/lo, K-major 128-byte swizzle).  128 traces per CTA (MMA M = 128, 8 warps), N = 2 nf
+// rounded up to 32 (at most 128), 64 samples per stage.  The traces are read with coalesced 16-byte loads one stage ahead
 // into registers, split u = hi + lo into bf16 (about 2^-17 relative) and written by the threads
 // into the K-major swizzled A tiles; one thread issues the bf16x3 MMAs (hi hi, hi lo, lo hi).
 // The tensor core's FP32 accumulation drifts over long sums, so blocks of TT_J stages alternate
@@ -213,7 +213,7 @@ __device__ __forceinline__ void st_shared_v2(unsigned addr, unsigned a, unsigned
 }
 
 template <int N, bool VEC>
-__global__ void __cluster_dims__(TD_S, 1, 1) __launch_bounds__(128)
+__global__ void __cluster_dims__(TD_S, 1, 1) __launch_bounds__(256)
     k_trace_dft_tc(const float* __restrict__ resid, int ntr, int nt_d,
                    const unsigned char* __restrict__ twt, int nf, int nrec, int ld, int s0,
                    float2* __restrict__ Dh, int* __restrict__ err) {
@@ -253,13 +253,13 @@ __global__ void __cluster_dims__(TD_S, 1, 1) __launch_bounds__(128)
     tc::mbar_expect_tx(bfull(s & 1), BT);
     tc::bulk_g2s(b_hi(s & 1), twt + (size_t)(sbeg + s) * BT, BT, bfull(s & 1));
   };
-  // this thread's 16 float4 of a stage: element e = i * 128 + tid -> row e / 16, float4 e % 16
-  float4 pre[16];
+  // this thread's 8 float4 of a stage: element e = i * 256 + tid -> row e / 16, float4 e % 16
+  float4 pre[8];
   auto load = [&](int s) {
     const int t0 = (sbeg + s) * TT_K;
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      const int e = i * 128 + tid, m = e >> 4, c4 = e & 15;
+    for (int i = 0; i < 8; ++i) {
+      const int e = i * 256 + tid, m = e >> 4, c4 = e & 15;
       const int q = q0 + m, t = t0 + 4 * c4;
       float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
       if (q < ntr) {
@@ -279,8 +279,8 @@ __global__ void __cluster_dims__(TD_S, 1, 1) __launch_bounds__(128)
   auto convert = [&](int b) {  // pre -> A hi / lo planes of buffer b, K-major 128-byte swizzle
     const unsigned ah = a_hi(b);
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      const int e = i * 128 + tid, m = e >> 4, c4 = e & 15;
+    for (int i = 0; i < 8; ++i) {
+      const int e = i * 256 + tid, m = e >> 4, c4 = e & 15;
       const float4 v = pre[i];
       const __nv_bfloat162 h01 = __floats2bfloat162_rn(v.x, v.y), h23 = __floats2bfloat162_rn(v.z, v.w);
       const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
@@ -295,9 +295,12 @@ __global__ void __cluster_dims__(TD_S, 1, 1) __launch_bounds__(128)
                    *reinterpret_cast<const unsigned*>(&l23));
     }
   };
-  float tot[N];
+  // warp w drains TMEM lanes 32 (w % 4) .. (rows) and columns (w / 4) N / 2 .. (a half)
+  constexpr int NH = N / 2;
+  const int qq = warp & 3, hh = warp >> 2, row = qq * 32 + (tid & 31);
+  float tot[NH];
 #pragma unroll
-  for (int c = 0; c < N; ++c) tot[c] = 0.f;
+  for (int c = 0; c < NH; ++c) tot[c] = 0.f;
   bool ok = true;
   auto drain = [&](int blk) {  // add TMEM buffer blk % 2 into the totals (whole warp)
     const bool got = tc::mbar_wait(blkd(blk & 1), (blk >> 1) & 1);
@@ -306,13 +309,13 @@ __global__ void __cluster_dims__(TD_S, 1, 1) __launch_bounds__(128)
       return;
     }
     tc::tc_fence_after();
-    const unsigned base = tmem + ((unsigned)(warp * 32) << 16) + (unsigned)((blk & 1) * N);
+    const unsigned base = tmem + ((unsigned)(qq * 32) << 16) + (unsigned)((blk & 1) * N + hh * NH);
 #pragma unroll
-    for (int c0 = 0; c0 < N; c0 += 32) {
-      float v[32];
-      tc::tmem_ld32(base + (unsigned)c0, v);
+    for (int c0 = 0; c0 < NH; c0 += 16) {
+      float v[16];
+      tc::tmem_ld16(base + (unsigned)c0, v);
 #pragma unroll
-      for (int i = 0; i < 32; ++i) tot[c0 + i] += v[i];
+      for (int i = 0; i < 16; ++i) tot[c0 + i] += v[i];
     }
     tc::tc_fence_before();
   };
@@ -392,24 +395,26 @@ __global__ void __cluster_dims__(TD_S, 1, 1) __launch_bounds__(128)
   }
   const bool okall = __syncthreads_and(ok) && !fail;
   if (!okall && tid == 0) atomicExch(err, 1);
-  // totals to shared memory (the stage buffers are free): P[c][tid]
+  // totals to shared memory (the stage buffers are free): P[column][row]
   float* P = reinterpret_cast<float*>(sm);
 #pragma unroll
-  for (int c = 0; c < N; ++c) P[c * TT_M + tid] = okall ? tot[c] : 0.f;
+  for (int c = 0; c < NH; ++c) P[(hh * NH + c) * TT_M + row] = okall ? tot[c] : 0.f;
   cluster.sync();
   if (rank == 0) {
     for (int r = 1; r < TD_S; ++r) {
       const float* Pr = cluster.map_shared_rank(P, r);
 #pragma unroll
-      for (int c = 0; c < N; ++c) tot[c] += Pr[c * TT_M + tid];
+      for (int c = 0; c < NH; ++c) tot[c] += Pr[(hh * NH + c) * TT_M + row];
     }
-    const int q = q0 + tid;
+    const int q = q0 + row;
     if (q < ntr) {
       const int sidx = q / nrec, r = q % nrec;
 #pragma unroll
-      for (int k = 0; k < N / 2; ++k)
-        if (k < nf)
-          Dh[((long long)k * nrec + r) * ld + s0 + sidx] = make_float2(tot[2 * k], tot[2 * k + 1]);
+      for (int k = 0; k < NH / 2; ++k) {
+        const int kk = hh * (NH / 2) + k;  // components 2 kk, 2 kk + 1 of this half
+        if (kk < nf)
+          Dh[((long long)kk * nrec + r) * ld + s0 + sidx] = make_float2(tot[2 * k], tot[2 * k + 1]);
+      }
     }
   }
   cluster.sync();
@@ -433,11 +438,13 @@ cudaError_t launch_trace_dft_tc(const float* resid, int ntr, int nt_d, const uns
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) \
       return e;                                                                                \
     count_launches(1);                                                                         \
-    kern<<<grid, 128, smem, st>>>(resid, ntr, nt_d, twt, nf, nrec, ld, s0, Dh, err);           \
+    kern<<<grid, 256, smem, st>>>(resid, ntr, nt_d, twt, nf, nrec, ld, s0, Dh, err);           \
     return cudaGetLastError();                                                                 \
   }
   EGH_TT_CASE(32)
   EGH_TT_CASE(64)
+  EGH_TT_CASE(96)
+  EGH_TT_CASE(128)
 #undef EGH_TT_CASE
   return cudaErrorInvalidValue;
 }

@@ -147,3 +147,23 @@ def test_full_size_set_sampled(precision):
     got = out.numpy()[sample]
     for i in range(sample.size):
         assert rel(got[i], ref[i]) <= MULT_TOL, (precision, int(sample[i]))
+
+
+@pytest.mark.parametrize("nt_d", [1200, 1001])
+def test_many_frequencies(nt_d):
+    """60 frequencies (the tensor-core transform's widest component block, 2 nf up to 128),
+    a trace length that is and one that is not a multiple of four, against the FP64 oracle."""
+    import torch
+    from paper_2512_16642_gb300 import egh
+
+    rng = np.random.default_rng(5 + nt_d)
+    Q, f = _hpd_set(rng, 37, 60)
+    r = synth.bandlimited_noise(rng, (3, 37, nt_d), 1e-3, 2.0, 10.0)
+    L = oracle.cholesky(Q.astype(np.complex128))
+    ref = oracle.deblur(L, r.astype(np.float32).astype(np.float64), f, 1e-3, nt_ref=2000)[0]
+    with egh.Server(1 << 30, slots=2, max_batch_sources=8, precision=1) as sv:
+        sid = sv.add_set(Q, f, 1e-3, 2000, 2048)
+        rin = _pinned(r.shape, torch, r)
+        out = _pinned(r.shape, torch)
+        sv.wait(sv.submit(sid, rin, out))
+    assert rel(out.numpy(), ref) <= MULT_TOL
