@@ -110,7 +110,8 @@ typedef struct {
     int32_t nfreq;
     const double *freq_hz; /* [nfreq], host */
     int32_t batch_receivers; /* receivers propagated together; 0 = min(nrec, 16) */
-    int32_t dft_chunk;       /* levels per transform chunk: 32, 64, 128, 256 or 512; 0 = 512 */
+    int32_t dft_chunk;       /* levels per transform chunk: 32, 64, ..., 2048; 0 = 512 (the
+                                snapshot ring holds 2 chunks x batch_receivers levels) */
     int32_t gram_splits;     /* split of the grid sum in the Gram; 0 = chosen by the library
                                 (tensor-core Gram: half, once or twice a default, timed on the
                                 first egh_hessian) */

@@ -421,8 +421,9 @@ egh_status egh_create(const egh_config* cfg, egh_ctx** out) {
   if (c.batch_receivers < 0 || c.gram_splits < 0)
     return fail(nullptr, EGH_EINVAL, "batch_receivers and gram_splits must be >= 0");
   if (c.dft_chunk != 0 && c.dft_chunk != 32 && c.dft_chunk != 64 && c.dft_chunk != 128 &&
-      c.dft_chunk != 256 && c.dft_chunk != 512)
-    return fail(nullptr, EGH_EINVAL, "dft_chunk must be 0, 32, 64, 128, 256 or 512");
+      c.dft_chunk != 256 && c.dft_chunk != 512 && c.dft_chunk != 1024 &&
+      c.dft_chunk != 2048)
+    return fail(nullptr, EGH_EINVAL, "dft_chunk must be 0 or a power of two from 32 to 2048");
 
   ctx = new (std::nothrow) egh_ctx();
   if (!ctx) return fail(nullptr, EGH_ENOMEM, "host allocation failed");
@@ -598,7 +599,7 @@ egh_status green_run(egh_ctx* ctx, const float* vel, cudaStream_t stream, const 
     // write their snapshots, as the run does; the run below rewrites every state slot and ring
     // slot it reads) and keep the fastest (best of three passes of 24 steps per choice).
     const int np = (std::min(B, ctx->nrec) + 1) / 2;
-    float best = 1e30f;
+    float best = 1e30f, def_ms = 1e30f;
     int best_tz = fd_rows_per_warp_default();
     for (int tz : {12, 16, 20, 24, 32}) {
       float tz_best = 1e30f;
@@ -617,8 +618,11 @@ egh_status green_run(egh_ctx* ctx, const float* vel, cudaStream_t stream, const 
         best = tz_best;
         best_tz = tz;
       }
+      if (tz == fd_rows_per_warp_default()) def_ms = tz_best;
     }
-    ctx->fd_tz = best_tz;
+    // keep the default unless another choice is clearly faster: the pass runs without the
+    // transform beside it, and close calls there have gone either way in the full stage
+    ctx->fd_tz = best < 0.97f * def_ms ? best_tz : fd_rows_per_warp_default();
   }
   const int D = decim;
   const int ntd = (nt + D - 1) / D;  // recorded levels 0, D, 2D, ... < nt
