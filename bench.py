@@ -39,8 +39,8 @@ FALLBACK_HBM_GBS = 6800.0
 # committed ncu capture (profiles/), valid only for the kernel sources it was taken from (sha256
 # of csrc/fd.cu); None until a capture exists.
 KERNEL_TRAFFIC = {"fd_sha256": "10e918ab7dda65d80708a08a47135bd441ea0df259900e9a45a079c77b7db383",
-                  "k_fd_step": 30.07e6,   # 1.95 MB read + 28.12 MB write per launch
-                  "k_dft_tc": 13.77e9,    # 12.03 GB read + 1.74 GB write per 512-level launch
+                  "k_fd_step": 33.26e6,   # 2.34 MB read + 30.93 MB write per launch
+                  "k_dft_tc": 25.24e9,    # 22.91 GB read + 2.33 GB write per 1024-level launch
                   "gram_sha256": "5f3ab19d0b4c43a7200d1b923a74a90149eff3ddcd05def4594f422e847969fc",
                   "k_gram_tc": 22.36e9}   # 22.03 GB read + 0.33 GB write per launch (231 x 26)
 
