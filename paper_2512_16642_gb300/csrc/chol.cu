@@ -73,13 +73,121 @@ __device__ void potrf_block(float2* __restrict__ A, int n, int* __restrict__ sta
   }
 }
 
+// Blocked form (matrices whose 32-column panel fits in shared memory): the panel of rows
+// p0 .. n-1 and columns p0 .. p0+31 is factored in shared memory column by column (pivot, scale,
+// rank-1 update of the panel's later columns), written back, and the trailing lower triangle
+// takes the panel's rank-32 update in one pass over global memory, A[i][l] -= sum_c P[i][c]
+// conj(P[l][c]) -- a thirty-second of the global read-modify-write passes of the column form.
+// Same pivot rule and FP64 diagonal; the trailing sums are taken in a different order.
+constexpr int CH_PB = 32, CH_PS = CH_PB + 1;  // panel width, panel row stride (float2)
+constexpr int CH_PANEL_NMAX = 800;            // panel of n x 33 float2 + n doubles in 227 KB
+
+__device__ void potrf_block_panel(float2* __restrict__ A, int n, int* __restrict__ status_k,
+                                  int piv64, float2* P, double* dg, int& bad) {
+  const int tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  if (tid == 0) bad = 0;
+  for (int i = tid; i < n; i += blockDim.x) dg[i] = (double)A[(long long)i * n + i].x;
+  __syncthreads();
+  for (int p0 = 0; p0 < n && !bad; p0 += CH_PB) {
+    const int pw = min(CH_PB, n - p0), R = n - p0;
+    // panel rows p0 .. n-1, columns p0 .. p0+pw-1 (entries above the diagonal are not used)
+    for (int e = tid; e < R * pw; e += blockDim.x) {
+      const int r = e / pw, c = e % pw;
+      P[r * CH_PS + c] = A[(long long)(p0 + r) * n + p0 + c];
+    }
+    __syncthreads();
+    for (int jj = 0; jj < pw; ++jj) {
+      if (tid == 0) {
+        const double d = piv64 ? dg[p0 + jj] : (double)P[jj * CH_PS + jj].x;
+        if (!(d > 0.0) || !isfinite(d)) {
+          bad = p0 + jj + 1;
+        } else {
+          P[jj * CH_PS + jj] = make_float2(piv64 ? (float)sqrt(d) : sqrtf((float)d), 0.f);
+        }
+      }
+      __syncthreads();
+      if (bad) break;
+      const float inv = 1.f / P[jj * CH_PS + jj].x;
+      for (int r = jj + 1 + tid; r < R; r += blockDim.x) {
+        float2 v = P[r * CH_PS + jj];
+        v.x *= inv;
+        v.y *= inv;
+        P[r * CH_PS + jj] = v;
+        if (piv64) dg[p0 + r] -= (double)v.x * v.x + (double)v.y * v.y;
+      }
+      __syncthreads();
+      // the panel's later columns c (rows r >= c): P[r][c] -= P[r][jj] conj(P[c][jj])
+      for (int r = jj + 1 + tid; r < R; r += blockDim.x) {
+        const float2 ci = P[r * CH_PS + jj];
+        const int cmax = min(r, pw - 1);
+        for (int c = jj + 1; c <= cmax; ++c) {
+          const float2 cl = P[c * CH_PS + jj];
+          float2 a = P[r * CH_PS + c];
+          a.x -= ci.x * cl.x + ci.y * cl.y;
+          a.y -= ci.y * cl.x - ci.x * cl.y;
+          P[r * CH_PS + c] = a;
+        }
+      }
+      __syncthreads();
+    }
+    if (bad) break;
+    // the factored panel back to A (lower part only)
+    for (int e = tid; e < R * pw; e += blockDim.x) {
+      const int r = e / pw, c = e % pw;
+      if (c <= r) A[(long long)(p0 + r) * n + p0 + c] = P[r * CH_PS + c];
+    }
+    // trailing rank-pw update, rows i and columns l beyond the panel, l <= i
+    for (int i = p0 + pw + warp; i < n; i += nwarps) {
+      const float2* pi = P + (i - p0) * CH_PS;
+      float2* rowp = A + (long long)i * n;
+      for (int l = p0 + pw + lane; l <= i; l += 32) {
+        const float2* pl = P + (l - p0) * CH_PS;
+        float2 sum = make_float2(0.f, 0.f);
+        for (int c = 0; c < pw; ++c) {
+          const float2 a = pi[c], b = pl[c];
+          sum.x = fmaf(a.x, b.x, fmaf(a.y, b.y, sum.x));
+          sum.y = fmaf(a.y, b.x, fmaf(-a.x, b.y, sum.y));
+        }
+        float2 v = rowp[l];
+        v.x -= sum.x;
+        v.y -= sum.y;
+        rowp[l] = v;
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0) *status_k = bad;
+  if (!bad) {
+    for (long long t = tid; t < (long long)n * n; t += blockDim.x) {
+      const int i = (int)(t / n), l = (int)(t % n);
+      if (l > i) A[t] = make_float2(0.f, 0.f);
+    }
+  }
+}
+
+// shared memory of either form for matrices up to nmax
+size_t potrf_smem(int nmax) {
+  if (nmax <= CH_PANEL_NMAX)
+    return sizeof(float2) * (size_t)nmax * CH_PS + sizeof(double) * (size_t)nmax;
+  return sizeof(float2) * (size_t)(nmax + (nmax & 1)) + sizeof(double) * (size_t)nmax;
+}
+
+__device__ inline void potrf_any(float2* A, int n, int* status_k, int piv64, float2* buf, int& bad) {
+  if (n <= CH_PANEL_NMAX) {
+    potrf_block_panel(A, n, status_k, piv64, buf, reinterpret_cast<double*>(buf + (size_t)n * CH_PS),
+                      bad);
+  } else {
+    potrf_block(A, n, status_k, piv64, buf, reinterpret_cast<double*>(buf + n + (n & 1)), bad);
+  }
+}
+
 __global__ void __launch_bounds__(CH_THREADS)
     k_potrf(float2* __restrict__ Lh, int n, int* __restrict__ status, int piv64) {
-  extern __shared__ float2 col[];  // [n] columns, then [n] doubles of the FP64 diagonal
-  double* dg = reinterpret_cast<double*>(col + n + (n & 1));
+  extern __shared__ float2 pbuf[];  // panel (or column) cache, then the FP64 diagonal
   __shared__ int bad;
   const int k = blockIdx.x;
-  potrf_block(Lh + (long long)k * n * n, n, status + k, piv64, col, dg, bad);
+  potrf_any(Lh + (long long)k * n * n, n, status + k, piv64, pbuf, bad);
 }
 
 // Batched form: every matrix of a list (several survey patches x all their frequencies, of
@@ -91,14 +199,9 @@ __global__ void __launch_bounds__(THREADS)
   __shared__ int bad;
   for (int m = blockIdx.x; m < count; m += gridDim.x) {
     const PotrfItem it = items[m];
-    double* dg = reinterpret_cast<double*>(col + it.n + (it.n & 1));
-    potrf_block(it.A, it.n, it.status, piv64, col, dg, bad);
+    potrf_any(it.A, it.n, it.status, piv64, col, bad);
     __syncthreads();
   }
-}
-
-size_t potrf_smem(int nmax) {
-  return sizeof(float2) * (size_t)(nmax + (nmax & 1)) + sizeof(double) * (size_t)nmax;
 }
 
 cudaError_t potrf_many_prepare(int nmax) {
@@ -123,7 +226,7 @@ cudaError_t launch_potrf_many(const PotrfItem* items, int count, int nmax, int b
 }
 
 cudaError_t launch_potrf(float2* Lh, int n, int nf, int* status, cudaStream_t st, int piv64) {
-  const size_t smem = sizeof(float2) * (size_t)(n + (n & 1)) + sizeof(double) * (size_t)n;
+  const size_t smem = potrf_smem(n);
   if (smem > 48 * 1024) {
     cudaError_t e =
         cudaFuncSetAttribute(k_potrf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
