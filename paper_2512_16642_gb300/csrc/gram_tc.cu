@@ -10,8 +10,8 @@
 // bf16x3: each entry of M_k is stored by the transform's
 // last chunk as hi = bf16(g), lo = bf16(g - hi), and C = Hi Hi^T + Hi Lo^T + Lo Hi^T accumulates in
 // FP32 in TMEM (the dropped Lo Lo^T and the split are ~2^-17 relative).  Operands arrive by 5-D TMA
-// boxes {64 points, hi|lo, re/im, 1 frequency, 64 receivers} that land as 128 rows of 128 bytes in
-// the K-major 128-byte-swizzled layout the MMA reads, so the kernel does no conversion.  The grid
+// boxes of 32 points x 64 receivers x re/im that land as 128 rows of 64 bytes in the K-major
+// 64-byte-swizzled layout the MMA reads, so the kernel does no conversion.  The grid
 // sum is split into `splits` ranges; each CTA writes its FP32 tile to a workspace and a second
 // kernel adds the splits (in double) and forms Q_k.
 #include <cuda.h>
@@ -26,9 +26,10 @@ namespace egh {
 
 constexpr int GC_M = 128;            // block rows of C (64 receivers x re/im)
 constexpr int GC_N = 256;            // block columns of C (128 receivers x re/im)
-constexpr int GC_P = 64;             // points per stage (one 128-byte bf16 row)
-constexpr int GC_ST = 2;             // stages in flight
-constexpr unsigned GC_BOX = 16384;   // one operand box: 64 receivers x re/im = 128 rows x 128 bytes
+constexpr int GC_P = 64;   // points per operand block of the blocked layout
+constexpr int GC_K = 32;   // points per stage: one 64-byte bf16 row (64-byte swizzle)
+constexpr int GC_ST = 4;   // stages in flight (4 x 48 KB: the copies run three stages ahead)
+constexpr unsigned GC_BOX = 128u * GC_K * 2;  // one operand box: 64 receivers x re/im = 128 rows
 constexpr unsigned GC_STAGE = 6 * GC_BOX;  // A hi, A lo (1 box each), B hi, B lo (2 boxes each)
 
 // Blocks (ta, j) of C: rows of 64-receiver panel ta (128 rows), columns of panels ta + 2j and
@@ -53,8 +54,9 @@ size_t gram_tc_workspace_floats(int nrec, int nf, int splits) {
 size_t gram_tc_smem() { return 1024 + (size_t)GC_ST * GC_STAGE; }
 
 // Tensor map of the bf16 transforms, blocked by 64 points as
-// ghb[nf][G/64][hi/lo][nrec x re/im][64], for boxes {64 points, 128 rows (64 receivers x re/im),
-// 1 plane, 1 stage, 1 frequency} with the 128-byte swizzle: every box is one contiguous 16 KB run.
+// ghb[nf][G/64][hi/lo][nrec x re/im][64], for boxes {32 points, 128 rows (64 receivers x re/im),
+// 1 plane, 1 block, 1 frequency} with the 64-byte swizzle: every box is 128 runs of 64 bytes
+// 128 bytes apart (one half of a contiguous 16 KB block).
 cudaError_t make_ghb_tmap(CUtensorMap* tm, void* base, long long G, int nf, int nrec) {
   static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
   if (!enc) {
@@ -70,10 +72,10 @@ cudaError_t make_ghb_tmap(CUtensorMap* tm, void* base, long long G, int nf, int 
   const cuuint64_t dims[5] = {(cuuint64_t)GC_P, rows, 2, (cuuint64_t)(G / GC_P), (cuuint64_t)nf};
   const cuuint64_t str[4] = {GC_P * 2, rows * GC_P * 2, 2 * rows * GC_P * 2,
                              (cuuint64_t)(G / GC_P) * 2 * rows * GC_P * 2};
-  const cuuint32_t box[5] = {GC_P, 128, 1, 1, 1};
+  const cuuint32_t box[5] = {GC_K, 128, 1, 1, 1};
   const cuuint32_t es[5] = {1, 1, 1, 1, 1};
   const CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, base, dims, str, box, es,
-                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
@@ -95,9 +97,22 @@ __device__ __forceinline__ void tma_load_5d(unsigned dst, const void* tmap, int 
 // 87 000 points), so the MMAs accumulate into one of two 256-column TMEM buffers for blocks of
 // GC_J stages only, and warps 0..7 (lane quarter w % 4, column half w / 4) drain each finished
 // block into FP32 register totals with round-to-nearest adds while the MMAs fill the other
-// buffer.  Every wait is bounded (on expiry: error flag, bounded drain of the copies in flight,
-// TMEM freed, CTA leaves).
-constexpr int GC_J = 8;  // stages per TMEM accumulation block (96 accumulations)
+// buffer.  Stages of 32 points (48 KB) keep four in the ring, the copies three stages ahead of
+// the MMAs (measured against two 96 KB stages of 64 points: 9.6 -> 8.1 ms at 231 receivers x
+// 26 frequencies).  Every wait is bounded (on expiry: error flag, bounded drain of the copies in
+// flight, TMEM freed, CTA leaves).
+constexpr int GC_J = 8 * (GC_P / GC_K);  // stages per TMEM accumulation block (96 accumulations)
+
+// K-major shared-memory descriptor of the 64-byte swizzle (8-row groups 512 bytes apart)
+__device__ __forceinline__ uint64_t sdesc_sw64(unsigned saddr) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(512 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)4 << 61;
+  return d;
+}
+__device__ __forceinline__ uint64_t gc_desc(unsigned saddr) { return sdesc_sw64(saddr); }
 
 __global__ void __launch_bounds__(288)
     k_gram_tc(const __grid_constant__ CUtensorMap tmap, int nrec, long long split_len, long long G,
@@ -117,7 +132,7 @@ __global__ void __launch_bounds__(288)
   const bool half = bp + 1 >= n64;     // one B panel only: N = 128
   const long long p0 = (long long)sp * split_len;
   const long long p1 = min(G, p0 + split_len);
-  const int nst = p1 > p0 ? (int)((p1 - p0 + GC_P - 1) / GC_P) : 0;
+  const int nst = p1 > p0 ? (int)((p1 - p0 + GC_K - 1) / GC_K) : 0;
   const int nblk = (nst + GC_J - 1) / GC_J;
   const int tid = threadIdx.x, warp = tid >> 5;
   if (warp == 0) tc::tmem_alloc(&tslot, 2 * GC_N);
@@ -144,13 +159,14 @@ __global__ void __launch_bounds__(288)
       const unsigned idesc = tc::idesc_bf16(GC_M, half ? GC_N / 2 : GC_N, 0, 0);
       auto issue = [&](int s) {
         const int b = s % GC_ST;
-        const int stg = (int)(p0 / GC_P) + s;
+        const int stg = (int)(p0 / GC_P) + s / (GC_P / GC_K);  // 64-point block
+        const int xo = GC_K * (s % (GC_P / GC_K));               // its half (64-byte rows)
         const unsigned base = stage_addr(b);
         tc::mbar_expect_tx(full(b), (unsigned)((inner ? 0 : 2) + (half ? 2 : 4)) * GC_BOX);
         for (int hl = 0; hl < 2; ++hl) {
-          if (!inner) tma_load_5d(base + hl * GC_BOX, &tmap, 0, 2 * 64 * ta, hl, stg, k, full(b));
+          if (!inner) tma_load_5d(base + hl * GC_BOX, &tmap, xo, 2 * 64 * ta, hl, stg, k, full(b));
           for (int h = 0; h < (half ? 1 : 2); ++h)
-            tma_load_5d(base + (2 + 2 * hl + h) * GC_BOX, &tmap, 0, 2 * 64 * (bp + h), hl, stg, k,
+            tma_load_5d(base + (2 + 2 * hl + h) * GC_BOX, &tmap, xo, 2 * 64 * (bp + h), hl, stg, k,
                         full(b));
         }
       };
@@ -178,10 +194,10 @@ __global__ void __launch_bounds__(288)
         const unsigned ah = inner ? bh : stage_addr(b);
         const unsigned al = inner ? bl : ah + GC_BOX;
 #pragma unroll
-        for (int ks = 0; ks < GC_P / 16; ++ks) {
+        for (int ks = 0; ks < GC_K / 16; ++ks) {
           const unsigned o = 32u * ks;
-          const uint64_t dah = tc::sdesc_sw128(ah + o), dal = tc::sdesc_sw128(al + o);
-          const uint64_t dbh = tc::sdesc_sw128(bh + o), dbl = tc::sdesc_sw128(bl + o);
+          const uint64_t dah = gc_desc(ah + o), dal = gc_desc(al + o);
+          const uint64_t dbh = gc_desc(bh + o), dbl = gc_desc(bl + o);
           tc::mma_bf16(dt, dah, dbh, idesc, !(first && ks == 0));
           tc::mma_bf16(dt, dah, dbl, idesc, true);
           tc::mma_bf16(dt, dal, dbh, idesc, true);
