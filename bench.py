@@ -41,8 +41,9 @@ FALLBACK_HBM_GBS = 6800.0
 KERNEL_TRAFFIC = {"fd_sha256": "10e918ab7dda65d80708a08a47135bd441ea0df259900e9a45a079c77b7db383",
                   "k_fd_step": 33.26e6,   # 2.34 MB read + 30.93 MB write per launch
                   "k_dft_tc": 25.24e9,    # 22.91 GB read + 2.33 GB write per 1024-level launch
-                  "gram_sha256": "5f3ab19d0b4c43a7200d1b923a74a90149eff3ddcd05def4594f422e847969fc",
-                  "k_gram_tc": 22.36e9}   # 22.03 GB read + 0.33 GB write per launch (231 x 26)
+                  "gram_sha256": "682849b31f88e080d88eac726ad064d6333912cf0dabc8e3c5b5ba70d80e6346",
+                  # per launch at 231 receivers x 26 frequencies, by grid-sum splits (read + write)
+                  "k_gram_tc": {8: 32.52e9, 16: 24.13e9, 32: 18.02e9}}
 
 
 def _args():
@@ -52,7 +53,7 @@ def _args():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--resid", choices=["model", "noise"], default="model",
                    help="residual gathers from forward modelling in the true and start models, or "
                         "seeded band-limited noise of the same shape (skips the modelling launches)")
@@ -593,8 +594,9 @@ def run_ours(args):
         fd_sha = hashlib.sha256(f.read()).hexdigest()
     traffic_ok = KERNEL_TRAFFIC["fd_sha256"] == fd_sha
     with open(os.path.join(ROOT, "paper_2512_16642_gb300", "csrc", "gram_tc.cu"), "rb") as f:
-        gram_traffic = (KERNEL_TRAFFIC["k_gram_tc"] if KERNEL_TRAFFIC["gram_sha256"] ==
-                        hashlib.sha256(f.read()).hexdigest() and args.precision == "mixed" else None)
+        gram_traffic = (KERNEL_TRAFFIC["k_gram_tc"].get(st["gram_splits"])
+                        if KERNEL_TRAFFIC["gram_sha256"] == hashlib.sha256(f.read()).hexdigest()
+                        and args.precision == "mixed" and nr == 231 else None)
     fd_ms = statistics.mean(k[0] for k in kern)
     fd_n = kern[-1][1]
     dft_ms = statistics.mean(k[2] for k in kern)
@@ -675,7 +677,8 @@ def run_ours(args):
                 "value": e2e_v, "unit": UNIT,
                 "h2d_bytes_per_step": int(v_host.numel() * 4 + r_host.numel() * 4),
                 "d2h_bytes_per_step": int(m_host.numel() * 4 + 8 + 4 * nf),
-                "deblur_sources_per_s": ns / statistics.mean(e2e_deb),
+                "deblur_sources_per_s": ns / statistics.median(e2e_deb),
+                "deblur_ms": [round(t * 1e3, 3) for t in e2e_deb],
                 "note": "green from pinned host velocity + hessian + factor; deblur from pinned host "
                         "residuals to pinned host multipliers"},
         "gpu_launches": int(launches),

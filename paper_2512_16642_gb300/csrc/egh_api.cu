@@ -799,6 +799,7 @@ egh_status egh_hessian(egh_ctx* ctx, egh_mu_mode mode, double mu_param, double* 
       }
     }
     ctx->splits_tc = best_s;
+    ctx->st.gram_splits = best_s;
     ctx->tune_splits = false;
   }
   CK(cudaEventRecord(ctx->ev_gram[0], stream));
