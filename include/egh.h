@@ -115,7 +115,7 @@ typedef struct {
     int32_t gram_splits;     /* split of the grid sum in the Gram; 0 = chosen by the library
                                 (tensor-core Gram: half, once or twice a default, timed on the
                                 first egh_hessian) */
-    int32_t fd_rows;         /* FD rows per warp: 12, 16, 20, 24 or 32; 0 = timed on the first
+    int32_t fd_rows;         /* FD rows per warp: 12, 16, 18, 20, 24 or 32; 0 = timed on the first
                                 egh_green of the context and the fastest kept */
     int32_t precision;       /* egh_precision of the Hessian stage (0 = EGH_PREC_FP32) */
     int32_t reserved[3];     /* must be zero */

@@ -412,9 +412,9 @@ egh_status egh_create(const egh_config* cfg, egh_ctx** out) {
   for (int k = 0; k < c.nfreq; ++k)
     if (!(c.freq_hz[k] > 0) || !(c.freq_hz[k] < 0.5 / c.dt))
       return fail(nullptr, EGH_EINVAL, "frequency outside (0, 1/(2 dt))");
-  if (c.fd_rows != 0 && c.fd_rows != 12 && c.fd_rows != 16 && c.fd_rows != 20 && c.fd_rows != 24 &&
-      c.fd_rows != 32)
-    return fail(nullptr, EGH_EINVAL, "fd_rows must be 0, 12, 16, 20, 24 or 32");
+  if (c.fd_rows != 0 && c.fd_rows != 12 && c.fd_rows != 16 && c.fd_rows != 18 && c.fd_rows != 20 &&
+      c.fd_rows != 24 && c.fd_rows != 32)
+    return fail(nullptr, EGH_EINVAL, "fd_rows must be 0, 12, 16, 18, 20, 24 or 32");
   if (c.batch_receivers > 32) return fail(nullptr, EGH_EINVAL, "batch_receivers must be <= 32");
   if (c.precision != EGH_PREC_FP32 && !prec_mixed(c.precision))
     return fail(nullptr, EGH_EINVAL, "unknown precision");
@@ -600,8 +600,9 @@ egh_status green_run(egh_ctx* ctx, const float* vel, cudaStream_t stream, const 
     // slot it reads) and keep the fastest (best of three passes of 24 steps per choice).
     const int np = (std::min(B, ctx->nrec) + 1) / 2;
     float best = 1e30f, def_ms = 1e30f;
-    int best_tz = fd_rows_per_warp_default();
-    for (int tz : {12, 16, 20, 24, 32}) {
+    const int def_tz = fd_rows_one_wave(L, np);
+    int best_tz = def_tz;
+    for (int tz : {12, 16, 18, 20, 24, 32}) {
       float tz_best = 1e30f;
       for (int rep = 0; rep < 4; ++rep) {  // the first pass warms up
         float ms = 0.f;
@@ -618,11 +619,11 @@ egh_status green_run(egh_ctx* ctx, const float* vel, cudaStream_t stream, const 
         best = tz_best;
         best_tz = tz;
       }
-      if (tz == fd_rows_per_warp_default()) def_ms = tz_best;
+      if (tz == def_tz) def_ms = tz_best;
     }
-    // keep the default unless another choice is clearly faster: the pass runs without the
+    // keep the one-wave choice unless another is clearly faster: the pass runs without the
     // transform beside it, and close calls there have gone either way in the full stage
-    ctx->fd_tz = best < 0.97f * def_ms ? best_tz : fd_rows_per_warp_default();
+    ctx->fd_tz = best < 0.97f * def_ms ? best_tz : def_tz;
   }
   const int D = decim;
   const int ntd = (nt + D - 1) / D;  // recorded levels 0, D, 2D, ... < nt

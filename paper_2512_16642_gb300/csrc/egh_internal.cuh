@@ -66,6 +66,7 @@ cudaError_t launch_build_coef(const float* vel, const Layout& L, double dz, doub
 cudaError_t launch_fd_step(const float2* ucur, const float2* uprev, float2* unext,
                            const float2* coef, const Layout& L, const Stencil& S, int npairs,
                            const SnapOut& so, cudaStream_t st, int tz);
+int fd_rows_one_wave(const Layout& L, int npairs);
 int fd_rows_per_warp_default();
 cudaError_t fd_prepare(int nf);  // once per context, before any capture
 cudaError_t launch_inject(float2* u, long long pstride, const int* pts, const float2* coef, int nb,

@@ -338,6 +338,31 @@ __global__ void __launch_bounds__(32 * FD_MAXPAIRS, EGH_FD_MINB)
 
 int fd_rows_per_warp_default() { return EGH_FD_TZDEF; }
 
+// Rows per warp that fill one wave: the smallest choice whose tiles (PX/64 x ceil(NZ / TZ) CTAs)
+// all fit the GPU's resident CTA slots at once, so that no SM carries more rows than another;
+// the library default if none does.
+int fd_rows_one_wave(const Layout& L, int npairs) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return EGH_FD_TZDEF;
+  const size_t smem = sizeof(float4) * FD_RING * 36 * npairs;
+  const int threads = 32 * npairs;
+  auto fits = [&](auto kern, int tz) {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem) != cudaSuccess)
+      return false;
+    return (long long)(L.PX / 64) * ((L.NZ + tz - 1) / tz) <= (long long)occ * sms;
+  };
+  if (fits(k_fd_step<12>, 12)) return 12;
+  if (fits(k_fd_step<16>, 16)) return 16;
+  if (fits(k_fd_step<18>, 18)) return 18;
+  if (fits(k_fd_step<20>, 20)) return 20;
+  if (fits(k_fd_step<24>, 24)) return 24;
+  if (fits(k_fd_step<32>, 32)) return 32;
+  return EGH_FD_TZDEF;
+}
+
 // Raises the dynamic shared-memory limit of every FD and transform kernel instance once per
 // process (outside any stream capture).
 cudaError_t fd_prepare(int nf) {
@@ -345,6 +370,7 @@ cudaError_t fd_prepare(int nf) {
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(k_fd_step<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, fd_smem))) return e;
   if ((e = cudaFuncSetAttribute(k_fd_step<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, fd_smem))) return e;
+  if ((e = cudaFuncSetAttribute(k_fd_step<18>, cudaFuncAttributeMaxDynamicSharedMemorySize, fd_smem))) return e;
   if ((e = cudaFuncSetAttribute(k_fd_step<20>, cudaFuncAttributeMaxDynamicSharedMemorySize, fd_smem))) return e;
   if ((e = cudaFuncSetAttribute(k_fd_step<24>, cudaFuncAttributeMaxDynamicSharedMemorySize, fd_smem))) return e;
   if ((e = cudaFuncSetAttribute(k_fd_step<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, fd_smem))) return e;
@@ -379,6 +405,7 @@ cudaError_t launch_fd_step(const float2* ucur, const float2* uprev, float2* unex
     break;
     EGH_FD_CASE(12)
     EGH_FD_CASE(16)
+    EGH_FD_CASE(18)
     EGH_FD_CASE(20)
     EGH_FD_CASE(24)
     EGH_FD_CASE(32)
