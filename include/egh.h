@@ -325,6 +325,12 @@ egh_status egh_server_wait(egh_server *sv, int64_t request_id, double timeout_s,
  * transform's bounded device wait ran out since the last drain (the server stays usable). */
 egh_status egh_server_drain(egh_server *sv, double timeout_s);
 
+/* hold != 0: admission pauses (requests already in flight finish; new submissions queue);
+ * hold == 0: admission resumes, and the queued requests are packed into batches together
+ * (queued requests of one set share a solve up to max_batch_sources).  A drain while held
+ * times out unless the queue is empty; destroying a held server still finishes its queue. */
+egh_status egh_server_hold(egh_server *sv, int32_t hold);
+
 egh_status egh_server_get_stats(egh_server *sv, egh_server_stats *out);
 egh_status egh_server_reset_stats(egh_server *sv);
 

@@ -129,6 +129,7 @@ struct Server {
   std::condition_variable cv_work, cv_done;
   std::thread worker;
   bool stop = false;
+  bool held = false;  // admission paused by egh_server_hold
   std::string worker_error;
   int in_flight = 0, peak_in_flight = 0;
   // statistics
@@ -230,6 +231,7 @@ void worker_loop(Server* sv) {
     sv->cv_work.wait(lk, [&] {
       if (!sv->worker_error.empty()) return true;
       if (sv->queue.empty()) return sv->stop;
+      if (sv->held && !sv->stop) return false;
       for (bool b : sv->slot_busy)
         if (!b) return true;
       return false;
@@ -548,6 +550,16 @@ egh_status egh_server_get_stats(egh_server* sv, egh_server_stats* out) {
     s.mean_s = m / (double)sv->latencies.size();
   }
   *out = s;
+  return EGH_OK;
+}
+
+egh_status egh_server_hold(egh_server* sv, int32_t hold) {
+  if (!sv) return fail(sv, EGH_EINVAL, "NULL server");
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->held = hold != 0;
+  }
+  sv->cv_work.notify_all();
   return EGH_OK;
 }
 

@@ -113,6 +113,7 @@ _SIGS = {
     "egh_server_drain": ([_vp, ctypes.c_double], ctypes.c_int),
     "egh_server_get_stats": ([_vp, ctypes.POINTER(egh_server_stats)], ctypes.c_int),
     "egh_server_reset_stats": ([_vp], ctypes.c_int),
+    "egh_server_hold": ([_vp, ctypes.c_int32], ctypes.c_int),
     "egh_server_last_error": ([_vp], ctypes.c_char_p),
     "egh_server_destroy": ([_vp], None),
 }
@@ -471,6 +472,11 @@ class Server:
 
     def reset_stats(self):
         _check_server(load().egh_server_reset_stats(self.h), self.h)
+
+    def hold(self, on=True):
+        """Pauses (on) or resumes (off) admission; requests submitted while held queue and are
+        packed into batches together when admission resumes."""
+        _check_server(load().egh_server_hold(self.h, 1 if on else 0), self.h)
 
     def close(self):
         if self.h:

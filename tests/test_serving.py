@@ -68,15 +68,21 @@ def test_alone_equals_mix_and_oracle(precision):
             out = _pinned(r.shape, torch)
             sv.wait(sv.submit(ids[sid], rin, out))
             alone.append(out.numpy().copy())
-        # the same requests all at once, in a shuffled order: batched and overlapped
+        # the same requests all at once, in a shuffled order: batched and overlapped.  Admission
+        # is held while they are submitted so that they queue together whatever the host's timing
         outs = [_pinned(r.shape, torch) for _, r in reqs]
         order = rng.permutation(len(reqs))
+        sv.reset_stats()
+        sv.hold(True)
         rids = {i: sv.submit(ids[reqs[i][0]], ins[i], outs[i]) for i in order}
+        assert sv.stats()["completed"] == 0
+        sv.hold(False)
         for i in order:
             sv.wait(rids[i])
         st = sv.stats()
     for i in range(len(reqs)):
         np.testing.assert_array_equal(outs[i].numpy(), alone[i])
+    assert st["completed"] == len(reqs)
     assert st["batches"] < st["completed"]  # some requests shared a solve
     assert st["peak_bytes_in_use"] <= 256 << 20
     for i in range(len(reqs)):
@@ -116,7 +122,9 @@ def test_admission_by_budget_and_overlap():
             np.testing.assert_array_equal(o.numpy(), outs[0].numpy())
     with egh.Server(64 * per_request, slots=8, max_batch_sources=ns, precision=0) as sv:
         sid = sv.add_set(Q, f, 1e-3, 4000, 4096)
+        sv.hold(True)  # queued together, so that the admissions follow each other at once
         rids = [sv.submit(sid, rin, o) for o in outs]
+        sv.hold(False)
         sv.drain()
         for rid in rids:
             sv.wait(rid)
