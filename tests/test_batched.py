@@ -88,3 +88,73 @@ def test_batched_factor_reports_failing_patch():
     finally:
         for ctx in ctxs:
             ctx.close()
+
+
+def test_salt_patches_full_size_sampled():
+    """The batched form at full size, in the launch configuration the benchmark's salt workload
+    times: the 1701x351 salt model, nt 6000, 40 frequencies 2-10 Hz, patches of 161/257/341
+    receivers in mixed precision with the default batch, chunk and split choices, each patch's
+    Green-stage buffers released after its Hessians, the 120 Hessians factored in one persistent
+    launch.  Sampled against the FP64 oracle (run on the host cores beside the GPU work):
+    transforms of four receivers (two of the first patch, one of each other) at four of the 40
+    frequencies, and the Hessian entries among them (entry (i, j) depends only on g^i and g^j).
+    Every one of the 120 batched factors equals the per-context factor bit for bit and
+    reproduces its Hessian to FP32 backward-error level; mu is alpha times the mean diagonal."""
+    import torch
+    from concurrent.futures import ThreadPoolExecutor
+    from paper_2512_16642_gb300 import egh
+
+    c = synth.case_salt_patches()
+    v32 = np.float32(c.vel_true)
+    kf = np.array([0, 13, 26, 39])  # 2.0, 4.67, 7.33, 10.0 Hz
+    picks = [(0, 0), (0, 160), (1, 128), (2, 340)]  # (patch, receiver within the patch)
+    rix = np.array([c.patches[p][i] for p, i in picks], np.int32)
+    grid = oracle.Grid(v32.astype(np.float64), c.dz, c.dx, c.nsponge, c.sponge_R)
+    tpr = max(1, oracle.default_workers() // rix.size)
+    ctxs = []
+    with ThreadPoolExecutor(max_workers=1) as ex:
+        fut = ex.submit(oracle.green_dtft, grid, np.zeros(rix.size, np.int32), rix, c.freqs[kf], c.dt,
+                        c.nt, workers=rix.size, threads_per_run=tpr)
+        try:
+            vt = torch.from_numpy(v32).cuda()
+            gh, Q, L1, mu = {}, [], [], []
+            for pi, p in enumerate(c.patches):
+                ctx = _patch_ctx(c, p, egh.EGH_PREC_MIXED)
+                ctxs.append(ctx)
+                ctx.green(vt)
+                for t, (pp, i) in enumerate(picks):
+                    if pp == pi:
+                        gh[t] = ctx.get_green(i, 1)[0][kf]
+                mu.append(ctx.hessian(egh.EGH_MU_REL_MEANDIAG, c.mu_alpha))
+                ctx.factor()
+                Q.append(ctx.get_hessian(False).astype(np.complex128))
+                L1.append(ctx.get_hessian(True))
+                ctx.release_green()
+            with egh.Batch(ctxs) as b:
+                for _ in range(2):  # first call tunes and captures, second replays the graph
+                    b.factor()
+                    for ctx, L in zip(ctxs, L1):
+                        np.testing.assert_array_equal(ctx.get_hessian(True), L)
+        finally:
+            for ctx in ctxs:
+                ctx.close()
+        o_gh = fut.result()
+    tol = 1e-4
+    for t in range(len(picks)):
+        for j in range(kf.size):
+            assert rel(gh[t][j], o_gh[t, j]) <= tol, (picks[t], j)
+    H = oracle.hessian_gram(o_gh)  # [4 frequencies][4][4]
+    for k in range(kf.size):
+        sub = Q[0][kf[k]][np.ix_([0, 160], [0, 160])] - mu[0] * np.eye(2)
+        assert rel(sub, H[k][:2, :2]) <= tol, k
+        for t in (2, 3):
+            p, i = picks[t]
+            d = Q[p][kf[k], i, i] - mu[p]
+            assert abs(d - H[k][t, t]) <= tol * abs(H[k][t, t]), (picks[t], k)
+    for p in range(3):
+        assert mu[p] == pytest.approx(c.mu_alpha * np.mean(np.einsum("kii->ki", Q[p]).real - mu[p]),
+                                      rel=tol)
+        L = L1[p].astype(np.complex128)
+        for k in range(c.freqs.size):
+            back = np.linalg.norm(L[k] @ L[k].conj().T - Q[p][k]) / np.linalg.norm(Q[p][k])
+            assert back <= 1e-5, (p, k, back)
