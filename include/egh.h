@@ -116,7 +116,8 @@ typedef struct {
                                 (tensor-core Gram: half, once or twice a default, timed on the
                                 first egh_hessian) */
     int32_t fd_rows;         /* FD rows per warp: 12, 16, 18, 20, 24 or 32; 0 = timed on the first
-                                egh_green of the context and the fastest kept */
+                                egh_green of the context: the smallest count whose tiles fit one
+                                wave of resident blocks is kept unless another is 3% faster */
     int32_t precision;       /* egh_precision of the Hessian stage (0 = EGH_PREC_FP32) */
     int32_t reserved[3];     /* must be zero */
 } egh_config;

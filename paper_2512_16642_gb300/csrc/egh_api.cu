@@ -597,7 +597,7 @@ egh_status green_run(egh_ctx* ctx, const float* vel, cudaStream_t stream, const 
   if (ctx->fd_tz == 0) {
     // Rows per warp of the FD step: time each choice on this grid (steps of a full batch that
     // write their snapshots, as the run does; the run below rewrites every state slot and ring
-    // slot it reads) and keep the fastest (best of three passes of 24 steps per choice).
+    // slot it reads), best of three passes of 24 steps per choice.
     const int np = (std::min(B, ctx->nrec) + 1) / 2;
     float best = 1e30f, def_ms = 1e30f;
     const int def_tz = fd_rows_one_wave(L, np);

@@ -62,7 +62,7 @@ struct SnapOut {
 cudaError_t launch_check_velocity(const float* vel, long long n, float* d_vmax_bad, cudaStream_t st);
 cudaError_t launch_build_coef(const float* vel, const Layout& L, double dz, double dx, double dt,
                               double R, const float* d_vmax, float2* coef, cudaStream_t st);
-// tz: rows per warp (12, 16, 20, 24 or 32; 0 = default)
+// tz: rows per warp (12, 16, 18, 20, 24 or 32; 0 = default)
 cudaError_t launch_fd_step(const float2* ucur, const float2* uprev, float2* unext,
                            const float2* coef, const Layout& L, const Stencil& S, int npairs,
                            const SnapOut& so, cudaStream_t st, int tz);
