@@ -85,6 +85,31 @@ def test_on_the_fly_dtft_matches_stored_history():
     assert np.abs(out["ghat"] - ref).max() <= 1e-12 * np.abs(ref).max()
 
 
+def test_forward_traces_reciprocity_impulse_and_convolution():
+    """Residual modelling (Algorithm 1's S b_s, the residuals' source): (i) swapping sources and
+    receivers gives the same traces (source-receiver reciprocity of the symmetric scheme, exact);
+    (ii) an impulse signature records the Green function of the source position at the
+    receivers; (iii) a Ricker trace is the impulse trace convolved with the signature (the
+    scheme is linear and time-invariant from rest), which fixes where each wavelet sample
+    enters."""
+    c, g = _tiny(nt=70, nz=10, nx=14, nsponge=4, nrec=5)
+    s_iz, s_ix = np.array([0, 3, 7], np.int32), np.array([2, 9, 5], np.int32)
+    r_iz, r_ix = c.rec_iz, c.rec_ix
+    w = synth.ricker(c.nt, c.dt, 60.0)
+    T = oracle.forward_traces(g, s_iz, s_ix, r_iz, r_ix, w, c.dt, workers=1)
+    Tr = oracle.forward_traces(g, r_iz, r_ix, s_iz, s_ix, w, c.dt, workers=1)
+    assert T.shape == (3, 5, c.nt)
+    assert np.abs(T - Tr.transpose(1, 0, 2)).max() <= 1e-12 * np.abs(T).max()
+    Ti = oracle.forward_traces(g, s_iz, s_ix, r_iz, r_ix, oracle.impulse(c.nt)[0], c.dt, workers=1)
+    gt = oracle.green_time(g, s_iz, s_ix, c.dt, c.nt)  # [source][n][z][x]
+    rz, rx = r_iz + c.nsponge, r_ix + c.nsponge
+    assert np.abs(Ti - gt[:, :, rz, rx].transpose(0, 2, 1)).max() <= 1e-14 * np.abs(Ti).max()
+    conv = np.zeros_like(T)
+    for t in range(c.nt):
+        conv[..., t] = Ti[..., :t + 1] @ w[t::-1]
+    assert np.abs(T - conv).max() <= 1e-12 * np.abs(T).max()
+
+
 def test_bandlimited_impulse_is_the_dirac_transform():
     """A one-sample unit wavelet without decimation (S = 1) gives exactly the Dirac transform."""
     c, g = _tiny(nt=40)
