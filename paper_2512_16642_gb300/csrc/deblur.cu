@@ -1,10 +1,11 @@
 // Deblurring of residual gathers against the factored Hessians (eq. Qsystem solved per frequency,
 // Section "Frequency domain inversion"):
-//   D[k][r][s] = sum_t resid[s][r][t] exp(-i w_k t dt)           (k_trace_dft)
+//   D[k][r][s] = sum_t resid[s][r][t] exp(-i w_k t dt)           (k_trace_dft_tc)
 //   X_k = L_k^{-H} L_k^{-1} D_k                                   (k_trsm, all sources as RHS)
 //   mixed precision: X_k = W_k^H W_k D_k with W_k = L_k^{-1} (k_trtri once, k_cgemm), then
 //                    X_k += W_k^H W_k (D_k - Q_k X_k)             (k_resid_dot2 or k_resid64)
-//   mult[s][r][t] = sum_k w_k Re(X_k[r][s] exp(+i w_k t dt))      (k_synth)
+//   mult[s][r][t] = sum_k w_k Re(X_k[r][s] exp(+i w_k t dt))      (k_synth_tc; k_synth beyond
+//                                                                  2 nf = 64)
 // Traces are indexed q = s * nrec + r (the [ns][nrec][nt] gather layout); the spectra of one call
 // occupy columns s0 .. s0 + ns - 1 of a [nf][nrec][ld] array, so that several gathers (of
 // different lengths) can share one solve.
@@ -25,17 +26,8 @@ namespace egh {
 
 constexpr int NFMAX = 64;
 
-// ---------------------------------------------------------------------------------------------
-// Forward transform: 128 traces per block and one warp per group of 8 frequencies; lane l
-// accumulates traces l, l + 32, l + 64, l + 96 at its warp's 8 frequencies (64 running sums per
-// thread, each twiddle read reused over 4 traces and each sample over 8 frequencies).  The time
-// axis is split over a cluster of TD_S blocks, each taking a contiguous run of 32-sample stages
-// through a 3-deep ring of cp.async copies (zero-filled outside the gather): the samples
-// transposed into shared memory (row length 129, conflict-free both ways) and the stage's
-// twiddles padded to 8 per group.  The cluster's partial sums meet in block rank 0 through
-// distributed shared memory, added in rank order (deterministic).
-// ---------------------------------------------------------------------------------------------
-constexpr int TD_TR = 128, TD_T = 32, TD_RL = TD_TR + 1, TD_NS = 3, TD_S = 4;
+// CTAs per cluster along the time axis of the forward transform
+constexpr int TD_S = 4;
 
 // components of the tensor-core transform: 2 nf rounded up to 32
 __host__ __device__ inline int tt_ncomp(int nf) { return (2 * nf + 31) / 32 * 32; }
@@ -52,139 +44,16 @@ __device__ __forceinline__ void cp_async8(void* dst, const void* src, bool ok) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 
-size_t trace_dft_smem(int nf) {
-  const int nfp = 8 * ((nf + 7) / 8);
-  return (size_t)TD_NS * (TD_T * TD_RL * sizeof(float) + TD_T * nfp * sizeof(float2));
-}
-
-__global__ void __cluster_dims__(TD_S, 1, 1) __launch_bounds__(256)
-    k_trace_dft(const float* __restrict__ resid, int ntr, int nt_d, const float2* __restrict__ tw,
-                int nf, int nrec, int ld, int s0, float2* __restrict__ Dh) {
-  extern __shared__ float4 td_sm[];
-  namespace cg = cooperative_groups;
-  cg::cluster_group cluster = cg::this_cluster();
-  const int tid = threadIdx.x, lane = tid & 31, wg = tid >> 5;
-  const int nfp = blockDim.x >> 2;  // 8 per warp
-  float* Rb = reinterpret_cast<float*>(td_sm);                        // [TD_NS][TD_T][TD_RL]
-  float2* Wb = reinterpret_cast<float2*>(Rb + TD_NS * TD_T * TD_RL);  // [TD_NS][TD_T][nfp]
-  const int rank = (int)cluster.block_rank();
-  const int q0 = (blockIdx.x / TD_S) * TD_TR;
-  const int nst = (nt_d + TD_T - 1) / TD_T, per = (nst + TD_S - 1) / TD_S;
-  const int sbeg = min(nst, rank * per), send = min(nst, sbeg + per);
-  auto issue = [&](int s) {
-    if (s < send) {
-      float* R = Rb + (s % TD_NS) * (TD_T * TD_RL);
-      float2* W = Wb + (s % TD_NS) * (TD_T * nfp);
-      const int t0 = s * TD_T;
-      // consecutive threads copy consecutive samples of one trace (coalesced)
-      for (int e = tid; e < TD_TR * TD_T; e += blockDim.x) {
-        const int tt = e & (TD_T - 1), r = e >> 5;
-        const int q = q0 + r, t = t0 + tt;
-        const bool ok = q < ntr && t < nt_d;
-        cp_async4(R + tt * TD_RL + r, ok ? resid + (long long)q * nt_d + t : resid, ok);
-      }
-      for (int e = tid; e < TD_T * nfp; e += blockDim.x) {
-        const int tt = e / nfp, k = e % nfp, t = t0 + tt;
-        const bool ok = t < nt_d && k < nf;
-        cp_async8(W + e, ok ? tw + (long long)t * nf + k : tw, ok);
-      }
-    }
-    cp_async_commit();
-  };
-  float2 acc[4][8];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 8; ++j) acc[i][j] = make_float2(0.f, 0.f);
-  for (int s = sbeg; s < sbeg + TD_NS - 1; ++s) issue(s);
-  for (int s = sbeg; s < send; ++s) {
-    issue(s + TD_NS - 1);
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(TD_NS - 1) : "memory");
-    __syncthreads();
-    const float* R = Rb + (s % TD_NS) * (TD_T * TD_RL);
-    const float2* W = Wb + (s % TD_NS) * (TD_T * nfp);
-#pragma unroll 4
-    for (int tt = 0; tt < TD_T; ++tt) {
-      float x[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) x[i] = R[tt * TD_RL + lane + 32 * i];
-      const float4* wp = reinterpret_cast<const float4*>(W + tt * nfp + 8 * wg);
-      float2 w[8];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const float4 v = wp[j];
-        w[2 * j] = make_float2(v.x, v.y);
-        w[2 * j + 1] = make_float2(v.z, v.w);
-      }
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const float2 xx = make_float2(x[i], x[i]);
-#pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = __ffma2_rn(xx, w[j], acc[i][j]);  // packed FP32x2
-      }
-    }
-    __syncthreads();
-  }
-  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-  __syncthreads();
-  // partial sums to shared memory (the sample ring is free now): P[i * 8 + j][tid]
-  float2* P = reinterpret_cast<float2*>(td_sm);
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 8; ++j) P[(i * 8 + j) * blockDim.x + tid] = acc[i][j];
-  cluster.sync();
-  if (rank == 0) {
-    for (int r = 1; r < TD_S; ++r) {
-      const float2* Pr = cluster.map_shared_rank(P, r);
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const float2 v = Pr[(i * 8 + j) * blockDim.x + tid];
-          acc[i][j].x += v.x;
-          acc[i][j].y += v.y;
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int q = q0 + lane + 32 * i;
-      if (q < ntr) {
-        const int sidx = q / nrec, r = q % nrec;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int k = 8 * wg + j;
-          if (k < nf) Dh[((long long)k * nrec + r) * ld + s0 + sidx] = acc[i][j];
-        }
-      }
-    }
-  }
-  cluster.sync();  // the other blocks' shared memory stays live until rank 0 has read it
-}
-
 cudaError_t launch_trace_dft_tc(const float* resid, int ntr, int nt_d, const unsigned char* twt,
                                 int nf, int nrec, int ld, int s0, float2* Dh, int* err,
                                 cudaStream_t st);
 
-cudaError_t launch_trace_dft(const float* resid, int ntr, int nt_d, const float2* tw, int nf,
-                             int nrec, int ld, int s0, float2* Dh, cudaStream_t st,
-                             const unsigned char* twt, int* err) {
-  if (nf < 1 || nf > NFMAX) return cudaErrorInvalidValue;
-  // tensor cores when the twiddle tiles are given (N = 2 nf rounded up to 32 is at most 128)
-  if (twt && err && tt_ncomp(nf) <= 128)
-    return launch_trace_dft_tc(resid, ntr, nt_d, twt, nf, nrec, ld, s0, Dh, err, st);
-  const int groups = (nf + 7) / 8;
-  const size_t smem = trace_dft_smem(nf);
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_trace_dft, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-  }
-  count_launches(1);
-  const long long tiles = (ntr + TD_TR - 1) / TD_TR;
-  k_trace_dft<<<(unsigned)(tiles * TD_S), 32 * groups, smem, st>>>(resid, ntr, nt_d, tw, nf, nrec,
-                                                                    ld, s0, Dh);
-  return cudaGetLastError();
+cudaError_t launch_trace_dft(const float* resid, int ntr, int nt_d, int nf, int nrec, int ld,
+                             int s0, float2* Dh, cudaStream_t st, const unsigned char* twt,
+                             int* err) {
+  // N = 2 nf rounded up to 32 is at most 128 for nf <= 64
+  if (nf < 1 || nf > NFMAX || !twt || !err) return cudaErrorInvalidValue;
+  return launch_trace_dft_tc(resid, ntr, nt_d, twt, nf, nrec, ld, s0, Dh, err, st);
 }
 
 // ---------------------------------------------------------------------------------------------

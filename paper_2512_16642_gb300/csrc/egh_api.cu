@@ -925,7 +925,7 @@ static egh_status deblur_common(egh_ctx* ctx, const float* resid, int32_t ns, in
     dout = ctx->io_out;
   }
   CK(cudaEventRecord(ctx->ev[6], stream));
-  CK(launch_trace_dft(din, (int)ntr, nt_d, ctx->tw, ctx->nf, ctx->nrec, ns, 0, D, stream,
+  CK(launch_trace_dft(din, (int)ntr, nt_d, ctx->nf, ctx->nrec, ns, 0, D, stream,
                       ctx->twt_deb, ctx->d_err));
   const size_t dbytes = (size_t)ctx->nf * ntr * sizeof(float2);
   if (!diag && prec_mixed(ctx->prec)) {

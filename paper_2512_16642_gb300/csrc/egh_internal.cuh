@@ -119,12 +119,12 @@ cudaError_t launch_potrf_many(const PotrfItem* items, int count, int nmax, int b
 cudaError_t launch_potrf(float2* Lh, int n, int nf, int* status, cudaStream_t st, int piv64);
 
 // ---- deblur.cu --------------------------------------------------------------------------------
-// spectra of ntr = nrec * ns traces into columns s0 .. s0+ns-1 of D[nf][nrec][ld]
-// (on the tensor cores when twt, the transform's twiddle tiles for at least nt_d levels, and the
-// error flag err are given and 2 nf rounded up to 32 is at most 64; else on the CUDA cores)
-cudaError_t launch_trace_dft(const float* resid, int ntr, int nt_d, const float2* tw, int nf,
-                             int nrec, int ld, int s0, float2* Dh, cudaStream_t st,
-                             const unsigned char* twt = nullptr, int* err = nullptr);
+// spectra of ntr = nrec * ns traces into columns s0 .. s0+ns-1 of D[nf][nrec][ld] on the tensor
+// cores; twt: the transform's twiddle tiles for at least nt_d levels; err: the flag a bounded
+// wait sets (both required; nf <= 64)
+cudaError_t launch_trace_dft(const float* resid, int ntr, int nt_d, int nf, int nrec, int ld,
+                             int s0, float2* Dh, cudaStream_t st, const unsigned char* twt,
+                             int* err);
 cudaError_t launch_trsm(const float2* Lh, int n, int nf, float2* Dh, int ns, cudaStream_t st);
 // W = L^{-1} per frequency; X = W^H (W D) with scratch Y
 cudaError_t launch_trtri(const float2* Lh, int n, int nf, float2* Wh, cudaStream_t st);

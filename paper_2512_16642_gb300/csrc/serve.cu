@@ -193,7 +193,7 @@ cudaError_t run_batch(Server* sv, Batch* b, const HSet& h) {
   for (Request* r : b->reqs) {
     float* din = reinterpret_cast<float*>(sv->arena_base + r->off_in);
     if ((e = cudaMemcpyAsync(din, r->resid, r->bytes, cudaMemcpyHostToDevice, st))) return e;
-    if ((e = launch_trace_dft(din, r->ns * h.nrec, r->nt_d, h.tw, h.nf, h.nrec, ld, s0, D, st,
+    if ((e = launch_trace_dft(din, r->ns * h.nrec, r->nt_d, h.nf, h.nrec, ld, s0, D, st,
                               h.twt, sv->d_err)))
       return e;
     s0 += r->ns;
