@@ -192,7 +192,7 @@ def _max_over_ranks(ws, x):
 # ---------------------------------------------------------------------------------------------
 # the oracle on a bounded sample (cpu_baseline and the reference arm)
 # ---------------------------------------------------------------------------------------------
-def oracle_sample(c, green_steps=60, gram_receivers=None, deblur_sources=4):
+def oracle_sample(c, green_steps=200, gram_receivers=None, deblur_sources=4):
     """Times the FP64 oracle on parts of one update and extrapolates to the full update.
 
     Green: `cores` receivers propagated concurrently (one per thread) for `green_steps` of the
