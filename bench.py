@@ -128,22 +128,29 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.fh.close()
+        with open(self.path) as f:
+            out = self.parse(f)
+        os.unlink(self.path)
+        return out
+
+    @staticmethod
+    def parse(lines):
+        """Summary of `--format=csv,noheader,nounits` lines of FIELDS: median SM clock, maximum
+        SM clock and the throttle reasons seen active in any sample (None without samples)."""
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        with open(self.path) as f:
-            for ln in f:
-                parts = [x.strip() for x in ln.split(",")]
-                if len(parts) < 9:
-                    continue
-                try:
-                    sm.append(float(parts[1]))
-                    smax.append(float(parts[2]))
-                except ValueError:
-                    continue
-                for n, v in zip(names, parts[5:9]):
-                    if v.lower().startswith("active"):
-                        reasons.add(n)
-        os.unlink(self.path)
+        for ln in lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
