@@ -93,8 +93,8 @@ typedef enum {
  *   Green functions: impulse of unit amplitude at step 0 at each receiver,
  *   injected as 1/(dx dz), nt recorded levels n = 0..nt-1 of step dt (s);
  *   receivers at physical grid points (rec_iz[r], rec_ix[r]);
- *   nfreq frequencies freq_hz[k] in (0, 1/(2 dt)), arbitrary (not tied to
- *   an FFT grid).
+ *   nfreq (1..64) frequencies freq_hz[k] in (0, 1/(2 dt)), arbitrary (not
+ *   tied to an FFT grid).
  * Host arrays are copied by egh_create.
  */
 typedef struct {
@@ -305,7 +305,7 @@ typedef struct {
 egh_status egh_server_create(const egh_server_config *cfg, egh_server **out);
 
 /* Adds a resident Hessian set: Q_host [nfreq][nrec][nrec] complex64 (Hermitian positive
- * definite, host) at frequencies freq_hz (Hz) of a record with step dt (s); nt_record sets the
+ * definite, host; nfreq 1..64) at frequencies freq_hz (Hz) of a record with step dt (s); nt_record sets the
  * synthesis weight of a single frequency (1/(nt_record dt)); requests may have up to max_nt
  * samples per trace.  Q is factored on the device (EGH_ENOTPD if a pivot fails).  Blocks. */
 egh_status egh_server_add_set(egh_server *sv, int32_t nrec, int32_t nfreq, const double *freq_hz,
