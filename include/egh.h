@@ -203,7 +203,8 @@ egh_status egh_factor(egh_ctx *ctx, int32_t *bad_freq, void *stream);
  * w_k = 2 df_k dt, df_k = half the distance between neighbouring frequencies
  * (the full gap at the ends; 1/(nt dt) for a single frequency).
  * resid, mult: [ns][nrec][nt_d] float32, host or device (both the same kind);
- * nt_d may differ from the Green record length.  Requires egh_factor. */
+ * nt_d may differ from the Green record length; ns = 0 does nothing (the
+ * pointers may then be NULL).  Requires egh_factor. */
 egh_status egh_deblur(egh_ctx *ctx, const float *resid, int32_t ns, int32_t nt_d, float *mult, void *stream);
 
 /* Same solve, returning the frequency-domain multipliers X[k][r][s]

@@ -5,6 +5,7 @@
 // block stops, no trap), the column is scaled and cached in shared memory, and each warp updates
 // whole rows of the trailing lower triangle with coalesced row accesses.  The upper triangle is
 // zeroed at the end.
+#include <algorithm>
 #include <cmath>
 
 #include "egh_internal.cuh"
@@ -166,11 +167,15 @@ __device__ void potrf_block_panel(float2* __restrict__ A, int n, int* __restrict
   }
 }
 
-// shared memory of either form for matrices up to nmax
+// shared memory for every matrix size up to nmax: the blocked form for n <= CH_PANEL_NMAX needs
+// the panel, the column form beyond it one column; a batch may hold both kinds (217.6 KB for the
+// panel of an 800-row matrix)
 size_t potrf_smem(int nmax) {
-  if (nmax <= CH_PANEL_NMAX)
-    return sizeof(float2) * (size_t)nmax * CH_PS + sizeof(double) * (size_t)nmax;
-  return sizeof(float2) * (size_t)(nmax + (nmax & 1)) + sizeof(double) * (size_t)nmax;
+  const size_t np = (size_t)std::min(nmax, CH_PANEL_NMAX);
+  const size_t panel = sizeof(float2) * np * CH_PS + sizeof(double) * np;
+  if (nmax <= CH_PANEL_NMAX) return panel;
+  const size_t column = sizeof(float2) * (size_t)(nmax + (nmax & 1)) + sizeof(double) * (size_t)nmax;
+  return std::max(panel, column);
 }
 
 __device__ inline void potrf_any(float2* A, int n, int* status_k, int piv64, float2* buf, int& bad) {

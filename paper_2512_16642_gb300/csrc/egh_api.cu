@@ -891,8 +891,8 @@ static egh_status deblur_common(egh_ctx* ctx, const float* resid, int32_t ns, in
     return fail(ctx, EGH_ESTATE, "egh_deblur_diag needs egh_hessian first");
   if (!diag && ctx->state < ST_FACTORED) return fail(ctx, EGH_ESTATE, "egh_deblur needs egh_factor first");
   if (ns < 0 || nt_d < 1) return fail(ctx, EGH_EINVAL, "ns must be >= 0 and nt_d >= 1");
+  if (ns == 0) return EGH_OK;  // an empty gather: nothing is read or written (NULL allowed)
   if (!resid || (!mult && !X)) return fail(ctx, EGH_EINVAL, "NULL buffer");
-  if (ns == 0) return EGH_OK;
   const long long ntr = (long long)ns * ctx->nrec;
   if ((ntr + 63) / 64 > 65535) return fail(ctx, EGH_EINVAL, "too many traces in one call");
   const bool dev_in = pointer_is_device(resid);

@@ -67,6 +67,44 @@ def test_batched_factor_matches_single_and_oracle(prec):
             ctx.close()
 
 
+def test_batched_factor_mixes_panel_and_column_forms():
+    """A patch of 850 receivers (beyond the 800 rows whose 32-column panel fits in shared memory:
+    the column form) and one of 13 (the blocked panel form) factored in one persistent launch,
+    whose shared memory must hold either form: equal to the per-context factors bit for bit and
+    to the FP64 oracle's Cholesky of the same Hessians."""
+    import torch
+    from paper_2512_16642_gb300 import egh
+
+    c = synth.case_tiny(seed=17, nz=6, nx=860, nsponge=3, nrec=4, nt=24)
+    c["freqs"] = np.array([15.0, 30.0])
+    patches = [np.arange(0, 850), np.arange(5, 860, 66)]  # 850 and 13 receivers
+    v = torch.from_numpy(np.float32(c.vel_true)).cuda()
+    ctxs = [_patch_ctx(c, p, egh.EGH_PREC_MIXED) for p in patches]
+    try:
+        single = []
+        for ctx in ctxs:
+            ctx.green(v)
+            ctx.hessian(egh.EGH_MU_REL_MEANDIAG, c.mu_alpha)
+            ctx.factor()
+            single.append(ctx.get_hessian(True))
+            ctx.release_green()
+        with egh.Batch(ctxs) as b:
+            for _ in range(2):
+                b.factor()
+                for ctx, L1 in zip(ctxs, single):
+                    np.testing.assert_array_equal(ctx.get_hessian(True), L1)
+        for ctx in ctxs:
+            Q = ctx.get_hessian(False).astype(np.complex128)
+            Lo = oracle.cholesky(Q)
+            L = ctx.get_hessian(True).astype(np.complex128)
+            for k in range(c.freqs.size):
+                assert rel(L[k], Lo[k]) <= 1e-3, k
+                assert rel(L[k] @ L[k].conj().T, Q[k]) <= 1e-5, k
+    finally:
+        for ctx in ctxs:
+            ctx.close()
+
+
 def test_batched_factor_reports_failing_patch():
     import torch
     from paper_2512_16642_gb300 import egh

@@ -348,6 +348,9 @@ def test_argument_and_state_errors():
         ctx.green(np.float32(c.vel_true))  # host velocity
         ctx.hessian()
         ctx.factor()
+        e = torch.empty((0, 3, 16), device="cuda")  # an empty gather is a no-op
+        ctx.deblur(e, torch.empty_like(e))
+        ctx.deblur(np.zeros((0, 3, 16), np.float32), np.zeros((0, 3, 16), np.float32))
         r = torch.zeros((2, 3, 16), device="cuda")
         with pytest.raises(egh.EghError) as ei:
             ctx.deblur(r, np.zeros((2, 3, 16), np.float32))
