@@ -975,7 +975,7 @@ egh_status egh_deblur(egh_ctx* ctx, const float* resid, int32_t ns, int32_t nt_d
                       void* stream) {
   if (!ctx) return fail(nullptr, EGH_EINVAL, "ctx is NULL");
   CK(cudaSetDevice(ctx->dev));
-  if (!mult) return fail(ctx, EGH_EINVAL, "mult is NULL");
+  if (!mult && ns != 0) return fail(ctx, EGH_EINVAL, "mult is NULL");
   return deblur_common(ctx, resid, ns, nt_d, mult, nullptr, (cudaStream_t)stream);
 }
 
@@ -983,7 +983,7 @@ egh_status egh_deblur_freq(egh_ctx* ctx, const float* resid, int32_t ns, int32_t
                            void* stream) {
   if (!ctx) return fail(nullptr, EGH_EINVAL, "ctx is NULL");
   CK(cudaSetDevice(ctx->dev));
-  if (!X) return fail(ctx, EGH_EINVAL, "X is NULL");
+  if (!X && ns != 0) return fail(ctx, EGH_EINVAL, "X is NULL");
   return deblur_common(ctx, resid, ns, nt_d, nullptr, (float2*)X, (cudaStream_t)stream);
 }
 
@@ -991,7 +991,7 @@ egh_status egh_deblur_diag(egh_ctx* ctx, const float* resid, int32_t ns, int32_t
                            void* stream) {
   if (!ctx) return fail(nullptr, EGH_EINVAL, "ctx is NULL");
   CK(cudaSetDevice(ctx->dev));
-  if (!mult) return fail(ctx, EGH_EINVAL, "mult is NULL");
+  if (!mult && ns != 0) return fail(ctx, EGH_EINVAL, "mult is NULL");
   return deblur_common(ctx, resid, ns, nt_d, mult, nullptr, (cudaStream_t)stream, true);
 }
 
