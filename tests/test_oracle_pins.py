@@ -284,6 +284,20 @@ def test_hessian_hermitian_positive_definite():
     assert mx >= mu
 
 
+def test_mu_max_eig_closed_form():
+    """mu = alpha max_k lambda_max(H_k) on blocks with known spectra: H_k = a_k a_k^H + c_k I has
+    lambda_max = |a_k|^2 + c_k (the other eigenvalues are c_k)."""
+    rng = np.random.default_rng(3)
+    nf, n = 4, 6
+    a = rng.standard_normal((nf, n)) + 1j * rng.standard_normal((nf, n))
+    cst = np.array([0.5, 3.0, 0.1, 1.0])
+    H = np.einsum("ki,kj->kij", a, a.conj()) + cst[:, None, None] * np.eye(n)
+    lam = np.sum(np.abs(a) ** 2, axis=1) + cst
+    assert oracle.mu_max_eig(H, 0.01) == pytest.approx(0.01 * lam.max(), rel=1e-12)
+    # the largest block decides, wherever it sits
+    assert oracle.mu_max_eig(H[::-1], 1.0) == pytest.approx(lam.max(), rel=1e-12)
+
+
 def test_fig1_structure():
     """Fig. 1 (Nt = 7, Nr = 5): the time-domain Q is dense 35 x 35; replacing each block by its
     Fourier diagonal and permuting with Pi (vec(D) -> vec(D^T)) gives 5 x 5 diagonal blocks."""
