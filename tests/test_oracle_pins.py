@@ -267,6 +267,21 @@ def test_explicit_columns_from_forward_adjoint_solves(tiny):
         assert np.abs(col - ref).max() <= 1e-12 * np.abs(ref).max()
 
 
+def test_adjoint_dot_product(tiny):
+    """S^T is the adjoint of S: <S v, d> = <v, S^T d> for random volume sources v and traces d
+    (the time-reversed solve is exact because the scheme is symmetric)."""
+    c, g, gt, Q = tiny
+    nr, nt = gt.shape[:2]
+    rp = g.index(c.rec_iz, c.rec_ix)
+    rng = np.random.default_rng(21)
+    for _ in range(2):
+        v = rng.standard_normal((nt, g.NZ, g.NX))
+        d = rng.standard_normal((nr, nt))
+        lhs = np.sum(oracle.apply_S(g, c.dt, nt, rp, v) * d)
+        rhs = np.sum(v * oracle.apply_St(g, c.dt, nt, rp, d))
+        assert abs(lhs - rhs) <= 1e-12 * max(abs(lhs), abs(rhs))
+
+
 def test_hessian_hermitian_positive_definite():
     c, g = _tiny(nt=200, nsponge=4, nrec=5)
     freqs = np.array([10.0, 20.0, 35.0])
