@@ -62,6 +62,27 @@ def test_homogeneous_closed_form():
         assert abs(num / ref - 1.0) < tol, (f, abs(num / ref - 1.0))
 
 
+def test_grid_pad_and_sponge_invariants():
+    """The padded grid: velocity replicated from the nearest physical point, no damping on the
+    physical grid, damping symmetric about it, growing outward, and additive over the two axes
+    (a corner carries both profiles)."""
+    rng = np.random.default_rng(2)
+    nz, nx, ns = 7, 9, 4
+    v = 1500.0 + 1000.0 * rng.random((nz, nx))
+    g = oracle.Grid(v, 10.0, 12.5, ns, R=1e-3)
+    assert (g.NZ, g.NX) == (nz + 2 * ns, nx + 2 * ns)
+    iz = np.clip(np.arange(g.NZ) - ns, 0, nz - 1)
+    ix = np.clip(np.arange(g.NX) - ns, 0, nx - 1)
+    assert np.array_equal(g.vel, v[np.ix_(iz, ix)])
+    e = g.eta
+    assert np.all(e[ns:ns + nz, ns:ns + nx] == 0.0)
+    assert np.allclose(e, e[::-1, :], rtol=1e-14, atol=0) and np.allclose(e, e[:, ::-1], rtol=1e-14, atol=0)
+    zc, xc = g.NZ // 2, g.NX // 2
+    assert np.all(np.diff(e[:ns + 1, xc]) < 0) and np.all(np.diff(e[zc, :ns + 1]) < 0)
+    assert np.allclose(e[:ns, :ns], e[:ns, xc][:, None] + e[zc, :ns][None, :], rtol=1e-14, atol=0)
+    assert np.all(e >= 0.0)
+
+
 def test_sponge_absorbs_energy():
     """With the sponge the field decays; nothing grows over thousands of steps."""
     c, g = _tiny(nt=3000, nz=20, nx=20, nsponge=10, nrec=1, dt=1e-3)
