@@ -156,7 +156,7 @@ void egh_destroy(egh_ctx *ctx);
 
 /* Step (a): receiver-side Green functions and their transforms (Section
  * "Direct Hessian-inverse computation": one PDE solve per receiver with a
- * Dirac source at the receiver, Algorithm 2 step 2):
+ * Dirac source at the receiver, as Algorithm 2 computes them):
  *   ghat[r][k](x) = sum_{n<nt} g^r(n, x) exp(-i 2 pi f_k n dt)
  * over the whole padded grid.  vel: [nz][nx] float32 velocity (m/s), host or
  * device.  EGH_EINVAL if a velocity is not positive and finite or the CFL
