@@ -189,7 +189,8 @@ egh_status egh_green_bandlimited(egh_ctx *ctx, const float *vel, const float *wa
 egh_status egh_hessian(egh_ctx *ctx, egh_mu_mode mode, double mu_param, double *mu_out, void *stream);
 
 /* Step (c): Cholesky factors L_k L_k^H = Q_k of all frequencies in one launch
- * (Algorithm 2 "Invert each frequency-domain matrix").  Blocks until the
+ * (Algorithm 2 inverts each frequency's matrix; the factors stand in for
+ * the inverses).  Blocks until the
  * status is known.  EGH_ENOTPD if a pivot is not positive; *bad_freq (host,
  * may be NULL) receives the first failing frequency index, else -1.
  * Requires egh_hessian. */

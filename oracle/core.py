@@ -237,7 +237,7 @@ def add_mu(H, mu):
 
 
 # ----------------------------------------------------------------------------
-# Step (c): factorisation (Algorithm 2 "Invert each frequency-domain matrix";
+# Step (c): factorisation (Algorithm 2 inverts each frequency's matrix; here
 # the Hermitian positive-definite blocks are factored as Q = L L^H).
 # ----------------------------------------------------------------------------
 class NotPositiveDefinite(ValueError):

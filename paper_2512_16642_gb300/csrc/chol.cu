@@ -1,6 +1,6 @@
 // Cholesky factorisation of every frequency's Hessian, Q_k = L_k L_k^H, in one launch
-// (Algorithm 2 "Invert each frequency-domain matrix": the Hermitian positive-definite blocks
-// are factored and kept resident instead of inverted).  One block per frequency, right-looking:
+// (Algorithm 2 inverts each frequency's matrix; here the Hermitian positive-definite blocks
+// are factored and kept resident instead).  One block per frequency, right-looking:
 // for each column j the pivot is checked (non-positive or non-finite -> status[k] = j + 1 and the
 // block stops, no trap), the column is scaled and cached in shared memory, and each warp updates
 // whole rows of the trailing lower triangle with coalesced row accesses.  The upper triangle is
