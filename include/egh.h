@@ -214,8 +214,8 @@ egh_status egh_deblur(egh_ctx *ctx, const float *resid, int32_t ns, int32_t nt_d
 egh_status egh_deblur_freq(egh_ctx *ctx, const float *resid, int32_t ns, int32_t nt_d, void *X, void *stream);
 
 /* The diagonal-Hessian baseline the paper compares against (its introduction: earlier work
- * replaced the Hessian by a scaled identity; its examples run multiplier-based FWI with the
- * diagonal Hessian approximation): each frequency's system Q_k X_k = D_k solved with Q_k's
+ * replaced the Hessian by a scaled identity; its examples also compare against keeping only
+ * the Hessian's diagonal): each frequency's system Q_k X_k = D_k solved with Q_k's
  * diagonal only, X_k[r][s] = D_k[r][s] / Q_k[r][r], then synthesised as egh_deblur.  Same
  * buffers and errors as egh_deblur; requires egh_hessian (no factorisation). */
 egh_status egh_deblur_diag(egh_ctx *ctx, const float *resid, int32_t ns, int32_t nt_d, float *mult,
