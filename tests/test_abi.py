@@ -79,3 +79,22 @@ def test_null_context_is_rejected(lib):
     assert lib.egh_green(None, None, None) == egh.EGH_EINVAL
     assert lib.egh_factor(None, None, None) == egh.EGH_EINVAL
     lib.egh_destroy(None)
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """No fallback: without the compiled library every entry point raises (a fresh process, so
+    that no library is loaded yet)."""
+    import sys
+
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "from paper_2512_16642_gb300 import egh\n"
+            "egh.LIB_PATH = %r\n"
+            "egh.load.__defaults__ = (egh.LIB_PATH,)\n"
+            "try:\n"
+            "    egh.Context(4, 4, 10.0, 10.0, 1, 1e-3, 1e-3, 4, [0], [0], [10.0])\n"
+            "except RuntimeError as e:\n"
+            "    print('raised:', e)\n"
+            "else:\n"
+            "    print('no error')\n") % (ROOT, str(tmp_path / "libegh.so"))
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
+    assert "raised: libegh.so not built" in out.stdout, out.stdout + out.stderr
