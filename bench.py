@@ -439,15 +439,18 @@ def run_salt(args):
     clk.start()
     l0 = ctxs[0].stats()["kernel_launches"]
     res = [step() for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    _barrier(ws)
     clocks = clk.stop()
     launches = ctxs[0].stats()["kernel_launches"] - l0
     total = statistics.mean(r[0] for r in res) / 1e3
     fac = statistics.mean(r[1] for r in res)
     ps = sum(ctx.stats()["point_steps"] for ctx in ctxs)
+    total_max = _max_over_ranks(ws, total)  # every rank takes part in the reduction
     if rank == 0:
         print(json.dumps({
-            "metric": METRIC, "value": _max_over_ranks(ws, total) / ws, "unit": UNIT, "n_gpus": ws,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total * 1e3,
+            "metric": METRIC, "value": total_max / ws, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_max * 1e3,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": "salt 1701x351 (padded 1741x391), dx 10 m, three surface patches of "
