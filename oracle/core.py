@@ -329,8 +329,7 @@ def deblur(L, resid, freqs, dt, nt_ref=None):
 def deblur_diag(Q, resid, freqs, dt, nt_ref=None):
     """Diagonal-Hessian baseline (the introduction's scaled-identity approximation of earlier
     work; the examples also run the multiplier method keeping only the Hessian's diagonal):
-    X_k = D_k / diag(Q_k),
-    then the same synthesis."""
+    X_k = D_k / diag(Q_k), then the same synthesis."""
     D = dtft_traces(resid, freqs, dt)
     d = np.real(np.einsum("kii->ki", Q))
     X = D / d[:, :, None]
