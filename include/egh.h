@@ -205,7 +205,11 @@ egh_status egh_factor(egh_ctx *ctx, int32_t *bad_freq, void *stream);
  * (the full gap at the ends; 1/(nt dt) for a single frequency).
  * resid, mult: [ns][nrec][nt_d] float32, host or device (both the same kind);
  * nt_d may differ from the Green record length; ns = 0 does nothing (the
- * pointers may then be NULL).  Requires egh_factor. */
+ * pointers may then be NULL).  Requires egh_factor.  With host buffers the call
+ * returns when the multipliers are on the host and reports EGH_ETIMEOUT if a
+ * bounded device wait of its transforms ran out; with device buffers it returns
+ * before the work completes, and such an expiry is reported by the next call
+ * that waits for the device (egh_green, egh_hessian, a host-buffer deblur). */
 egh_status egh_deblur(egh_ctx *ctx, const float *resid, int32_t ns, int32_t nt_d, float *mult, void *stream);
 
 /* Same solve, returning the frequency-domain multipliers X[k][r][s]
@@ -260,12 +264,15 @@ egh_status egh_get_hessian(egh_ctx *ctx, int32_t factored, void *host_out);
  *       npts a positive multiple of 16 (pad with zeros);
  *   H   [nfreq][nrec][nrec] complex64 output, 8-byte aligned.
  * It allocates nothing: its split-sum workspace is a fixed 32 MiB array in
- * device memory defined by the library (every GPU that loads the library
- * holds it until the process exits), which limits nfreq x (number of 32-
+ * device memory defined by the library, which limits nfreq x (number of 32-
  * receiver tile pairs, t (t + 1) / 2 with t = ceil(nrec / 32)) to 2048; larger
  * sizes return EGH_EINVAL with a message in egh_last_error(NULL).  The first
  * call on a device, made while that device is current, looks up the array's
- * device address; make that first call before any stream capture.  All calls
+ * device address.  CUDA loads a library's device code lazily by default, so
+ * that first lookup is what reserves the 32 MiB on the device (held until the
+ * process exits): make the first call at start-up, before another allocator
+ * reserves the device's memory, and before any stream capture.  Later calls
+ * take no device memory at all.  All calls
  * share the one array and each overwrites what it uses, so calls that overlap
  * on the GPU (different streams, or different host threads) race and must be
  * ordered by the caller.  Work is queued on `stream`; the call returns
@@ -321,12 +328,24 @@ egh_status egh_server_submit(egh_server *sv, int32_t set_id, const float *resid_
                              int32_t nt_d, float *mult_host, int64_t *request_id);
 
 /* Waits (up to timeout_s) for a request; *latency_s (may be NULL) receives its submission-to-
- * completion time.  The id is released.  EGH_ETIMEOUT if it has not finished. */
+ * completion time.  EGH_ETIMEOUT with the id kept if it has not finished within timeout_s.
+ * Otherwise the id is released and the request's own status is returned: EGH_OK; EGH_ETIMEOUT
+ * if a bounded device wait ran out in its batch (its multipliers are not valid; the server
+ * stays usable); EGH_ECUDA if its batch could not be launched or the server stopped before
+ * running it.  egh_server_last_error tells the cases apart. */
 egh_status egh_server_wait(egh_server *sv, int64_t request_id, double timeout_s, double *latency_s);
 
 /* Waits (up to timeout_s) until nothing is queued or in flight.  EGH_ETIMEOUT also when a
- * transform's bounded device wait ran out since the last drain (the server stays usable). */
+ * bounded device wait ran out in some batch since the last drain (those requests returned
+ * EGH_ETIMEOUT from egh_server_wait; the server stays usable). */
 egh_status egh_server_drain(egh_server *sv, double timeout_s);
+
+/* Test hook of the failure path (the paper has no counterpart): the forward transforms of the
+ * next `count` batches each have one bounded device wait run out, on an mbarrier that nothing
+ * signals, after about 0.2 ms.  The kernel then records its batch's error flag, lets its copies
+ * in flight land, frees its tensor memory and returns, exactly as when staged data never arrive;
+ * nothing faults or hangs.  Those batches' requests return EGH_ETIMEOUT. */
+egh_status egh_server_test_expire_wait(egh_server *sv, int32_t count);
 
 /* hold != 0: admission pauses (requests already in flight finish; new submissions queue);
  * hold == 0: admission resumes, and the queued requests are packed into batches together
@@ -348,6 +367,14 @@ void egh_server_destroy(egh_server *sv);
  * keep their factored Hessians resident while only one holds its Green functions.  egh_hessian
  * and egh_get_green then return EGH_ESTATE until egh_green runs again.  Blocks. */
 egh_status egh_release_green(egh_ctx *ctx);
+
+/* Test hook of the failure path (the paper has no counterpart): in the next `count` transform
+ * launches of this context (the Green stage's on-the-fly transform, the deblur's forward
+ * transform), the first block has one bounded device wait run out, on an mbarrier that nothing
+ * signals, after about 0.2 ms; the kernel records the context's error flag, lets its copies in
+ * flight land, frees its tensor memory and returns.  The call that waits for that work returns
+ * EGH_ETIMEOUT and the context stays usable.  count = 0 cancels. */
+egh_status egh_test_expire_wait(egh_ctx *ctx, int32_t count);
 
 /* ---- Batched factorisation --------------------------------------------------------------- *
  * A batch groups contexts (survey patches of one model, any receiver counts, one device, one

@@ -46,14 +46,14 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 
 cudaError_t launch_trace_dft_tc(const float* resid, int ntr, int nt_d, const unsigned char* twt,
                                 int nf, int nrec, int ld, int s0, float2* Dh, int* err,
-                                cudaStream_t st);
+                                int expire, cudaStream_t st);
 
 cudaError_t launch_trace_dft(const float* resid, int ntr, int nt_d, int nf, int nrec, int ld,
                              int s0, float2* Dh, cudaStream_t st, const unsigned char* twt,
-                             int* err) {
+                             int* err, int expire) {
   // N = 2 nf rounded up to 32 is at most 128 for nf <= 64
   if (nf < 1 || nf > NFMAX || !twt || !err) return cudaErrorInvalidValue;
-  return launch_trace_dft_tc(resid, ntr, nt_d, twt, nf, nrec, ld, s0, Dh, err, st);
+  return launch_trace_dft_tc(resid, ntr, nt_d, twt, nf, nrec, ld, s0, Dh, err, expire, st);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -85,12 +85,12 @@ template <int N, bool VEC>
 __global__ void __cluster_dims__(TD_S, 1, 1) __launch_bounds__(256)
     k_trace_dft_tc(const float* __restrict__ resid, int ntr, int nt_d,
                    const unsigned char* __restrict__ twt, int nf, int nrec, int ld, int s0,
-                   float2* __restrict__ Dh, int* __restrict__ err) {
+                   float2* __restrict__ Dh, int* __restrict__ err, int expire) {
   extern __shared__ __align__(1024) unsigned char tt_dsm[];
   unsigned char* sm = tt_dsm + ((1024 - (tc::smem_u32(tt_dsm) & 1023)) & 1023);
   constexpr unsigned BT = 2u * N * 128u;           // one twiddle tile (hi + lo)
   constexpr unsigned STG = 2u * TT_A + BT;         // one stage
-  __shared__ __align__(8) unsigned long long bars[6];  // bfull[2], mdone[2], blk[2]
+  __shared__ __align__(8) unsigned long long bars[7];  // bfull[2], mdone[2], blk[2], never
   __shared__ unsigned tslot;
   __shared__ int fail;
   namespace cg = cooperative_groups;
@@ -108,7 +108,7 @@ __global__ void __cluster_dims__(TD_S, 1, 1) __launch_bounds__(256)
   constexpr unsigned NCOL = 2 * N <= 32 ? 32 : (2 * N <= 64 ? 64 : (2 * N <= 128 ? 128 : 256));
   if (warp == 0) tc::tmem_alloc(&tslot, NCOL);
   if (tid == 0) {
-    for (int i = 0; i < 6; ++i) tc::mbar_init(bar0 + 8u * i, 1);
+    for (int i = 0; i < 7; ++i) tc::mbar_init(bar0 + 8u * i, 1);
     fail = 0;
     tc::mbar_init_fence();
   }
@@ -210,7 +210,10 @@ __global__ void __cluster_dims__(TD_S, 1, 1) __launch_bounds__(256)
     tc::fence_proxy_async();
     __syncthreads();
     if (tid == 0) {
-      if (!tc::mbar_wait(bfull(b), (s >> 1) & 1)) {
+      // test hook: the first CTA's first wait runs out (bars[6] never completes a phase)
+      if (s == 0 && expire && blockIdx.x == 0 && !tc::mbar_wait_unsignalled(bar0 + 48u)) {
+        fail = 1;
+      } else if (!tc::mbar_wait(bfull(b), (s >> 1) & 1)) {
         fail = 1;
       } else {
         waited_b = s + 1;
@@ -294,7 +297,7 @@ __global__ void __cluster_dims__(TD_S, 1, 1) __launch_bounds__(256)
 
 cudaError_t launch_trace_dft_tc(const float* resid, int ntr, int nt_d, const unsigned char* twt,
                                 int nf, int nrec, int ld, int s0, float2* Dh, int* err,
-                                cudaStream_t st) {
+                                int expire, cudaStream_t st) {
   const int N = tt_ncomp(nf);
   const size_t smem = trace_dft_tc_smem(nf);
   const bool vec = (nt_d & 3) == 0 && (reinterpret_cast<uintptr_t>(resid) & 15) == 0;
@@ -307,7 +310,7 @@ cudaError_t launch_trace_dft_tc(const float* resid, int ntr, int nt_d, const uns
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) \
       return e;                                                                                \
     count_launches(1);                                                                         \
-    kern<<<grid, 256, smem, st>>>(resid, ntr, nt_d, twt, nf, nrec, ld, s0, Dh, err);           \
+    kern<<<grid, 256, smem, st>>>(resid, ntr, nt_d, twt, nf, nrec, ld, s0, Dh, err, expire);   \
     return cudaGetLastError();                                                                 \
   }
   EGH_TT_CASE(32)

@@ -87,6 +87,7 @@ struct egh_ctx {
   double* lmax = nullptr;
   float* vchk = nullptr;
   int* d_err = nullptr;  // set by bounded device waits that ran out
+  int expire = 0;        // test hook: transform launches whose first CTA has one wait run out
   float* vel_stage = nullptr;
   float2* Dh = nullptr;
   size_t Dh_cap = 0;
@@ -665,8 +666,11 @@ egh_status green_run(egh_ctx* ctx, const float* vel, cudaStream_t stream, const 
       CK(cudaEventRecord(ctx->fd_done[g & 1], fs));
       CK(cudaStreamWaitEvent(ctx->side, ctx->fd_done[g & 1], 0));
       CK(cudaEventRecord(ctx->ev_dft[2 * g], ctx->side));
+      const int expire = ctx->expire > 0 ? 1 : 0;
+      ctx->expire -= expire;
       CK(launch_dft_tc(ctx->tmap, twt, ctx->nf, sbase, m1 - m0, m0, L, ctx->gh, ctx->ghb,
-                       (m1 == ntd && ctx->ghb) ? 1 : 0, b0, nb, ctx->nrec, ctx->d_err, ctx->side));
+                       (m1 == ntd && ctx->ghb) ? 1 : 0, b0, nb, ctx->nrec, ctx->d_err, expire,
+                       ctx->side));
       CK(cudaEventRecord(ctx->ev_dft[2 * g + 1], ctx->side));
       CK(cudaEventRecord(ctx->dft_done[g & 1], ctx->side));
     }
@@ -835,7 +839,8 @@ egh_status egh_hessian(egh_ctx* ctx, egh_mu_mode mode, double mu_param, double* 
     CK(cudaStreamSynchronize(stream));
     if (derr) {
       CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), stream));
-      return fail(ctx, EGH_ETIMEOUT, "a bounded wait for staged operands ran out in the Gram");
+      return fail(ctx, EGH_ETIMEOUT, "a bounded device wait ran out (in the Gram, or in an earlier "
+                                     "deblur on device buffers)");
     }
   }
   if (!std::isfinite(mu)) return fail(ctx, EGH_EINVAL, "mu is not finite");
@@ -925,8 +930,10 @@ static egh_status deblur_common(egh_ctx* ctx, const float* resid, int32_t ns, in
     dout = ctx->io_out;
   }
   CK(cudaEventRecord(ctx->ev[6], stream));
+  const int expire = ctx->expire > 0 ? 1 : 0;
+  ctx->expire -= expire;
   CK(launch_trace_dft(din, (int)ntr, nt_d, ctx->nf, ctx->nrec, ns, 0, D, stream,
-                      ctx->twt_deb, ctx->d_err));
+                      ctx->twt_deb, ctx->d_err, expire));
   const size_t dbytes = (size_t)ctx->nf * ntr * sizeof(float2);
   if (!diag && prec_mixed(ctx->prec)) {
     // one step of iterative refinement: residual in FP64, correction solved with the FP32 factors
@@ -1131,6 +1138,13 @@ egh_status egh_get_stats(egh_ctx* ctx, egh_stats* out) {
   ctx->st.kernel_launches = launches_so_far();
   ctx->st.fd_rows = ctx->fd_tz;
   *out = ctx->st;
+  return EGH_OK;
+}
+
+egh_status egh_test_expire_wait(egh_ctx* ctx, int32_t count) {
+  if (!ctx) return fail(nullptr, EGH_EINVAL, "ctx is NULL");
+  if (count < 0) return fail(ctx, EGH_EINVAL, "count must be >= 0");
+  ctx->expire = count;
   return EGH_OK;
 }
 

@@ -81,7 +81,8 @@ std::vector<unsigned char> dft_twiddle_tiles(const std::vector<double>& f, doubl
 cudaError_t make_snap_tmap(CUtensorMap* tm, void* base, long long G, int Bp, int nslot);
 cudaError_t launch_dft_tc(const CUtensorMap& tmap, const unsigned char* twt, int nf, int slot0,
                           int kcount, int n0, const Layout& L, float* gh, __nv_bfloat16* ghb,
-                          int last, int rec0, int nvalid, int nrec_all, int* err, cudaStream_t st);
+                          int last, int rec0, int nvalid, int nrec_all, int* err, int expire,
+                          cudaStream_t st);
 
 // ---- gram_tc.cu -------------------------------------------------------------------------------
 // Gram on the tensor cores from the bf16 hi/lo transforms ghb[nrec][nf][re/im][hi/lo][G].
@@ -121,10 +122,10 @@ cudaError_t launch_potrf(float2* Lh, int n, int nf, int* status, cudaStream_t st
 // ---- deblur.cu --------------------------------------------------------------------------------
 // spectra of ntr = nrec * ns traces into columns s0 .. s0+ns-1 of D[nf][nrec][ld] on the tensor
 // cores; twt: the transform's twiddle tiles for at least nt_d levels; err: the flag a bounded
-// wait sets (both required; nf <= 64)
+// wait sets (both required; nf <= 64); expire: test hook, the first CTA's first wait runs out
 cudaError_t launch_trace_dft(const float* resid, int ntr, int nt_d, int nf, int nrec, int ld,
                              int s0, float2* Dh, cudaStream_t st, const unsigned char* twt,
-                             int* err);
+                             int* err, int expire = 0);
 cudaError_t launch_trsm(const float2* Lh, int n, int nf, float2* Dh, int ns, cudaStream_t st);
 // W = L^{-1} per frequency; X = W^H (W D) with scratch Y
 cudaError_t launch_trtri(const float2* Lh, int n, int nf, float2* Wh, cudaStream_t st);

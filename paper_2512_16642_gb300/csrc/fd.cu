@@ -506,13 +506,13 @@ __global__ void __launch_bounds__(128)
     k_dft_tc(const __grid_constant__ CUtensorMap tmap, const unsigned char* __restrict__ twt,
              int N, int nf, int slot0, int kcount, int n0, long long G, float* __restrict__ gh,
              __nv_bfloat16* __restrict__ ghb, int last, int rec0, int nvalid, int nrec_all,
-             int* __restrict__ err) {
+             int* __restrict__ err, int expire) {
   extern __shared__ __align__(1024) unsigned char dsm[];
   unsigned char* sm = dsm + ((1024 - (tc::smem_u32(dsm) & 1023)) & 1023);
   unsigned char* As = sm;                               // [TD_ST][TD_R][TD_AB]
   unsigned char* Bs = sm + TD_ST * TD_R * TD_AB;        // [2][plane][N][128 B]
   const unsigned tile = 2u * (unsigned)N * 128u;
-  __shared__ __align__(8) unsigned long long bars[2 * TD_ST + 1];  // full[], empty[], done
+  __shared__ __align__(8) unsigned long long bars[2 * TD_ST + 2];  // full[], empty[], done, never
   __shared__ unsigned tslot;
   __shared__ int fail;
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -526,7 +526,7 @@ __global__ void __launch_bounds__(128)
   auto empty = [&](int i) { return bar0 + 8u * (TD_ST + i); };
   const unsigned done = bar0 + 8u * (2 * TD_ST);
   if (tid == 0) {
-    for (int i = 0; i < 2 * TD_ST + 1; ++i) tc::mbar_init(bar0 + 8u * i, 1);
+    for (int i = 0; i < 2 * TD_ST + 2; ++i) tc::mbar_init(bar0 + 8u * i, 1);
     fail = 0;
     tc::mbar_init_fence();
   }
@@ -558,7 +558,11 @@ __global__ void __launch_bounds__(128)
       int issued = 0, landed = 0;
       bool ok = true;
       for (; issued < min(nst, TD_ST); ++issued) issue(issued);
-      for (int s = 0; s < nst; ++s) {
+      // test hook: the first CTA's first wait runs out (the last barrier never completes a phase)
+      if (expire && blockIdx.x == 0 && blockIdx.y == 0 &&
+          !tc::mbar_wait_unsignalled(bar0 + 8u * (2 * TD_ST + 1)))
+        ok = false;
+      for (int s = 0; ok && s < nst; ++s) {
         const int buf = s % TD_ST;
         if (!tc::mbar_wait(full(buf), (s / TD_ST) & 1)) {
           ok = false;
@@ -648,7 +652,8 @@ __global__ void __launch_bounds__(128)
 
 cudaError_t launch_dft_tc(const CUtensorMap& tmap, const unsigned char* twt, int nf, int slot0,
                           int kcount, int n0, const Layout& L, float* gh, __nv_bfloat16* ghb,
-                          int last, int rec0, int nvalid, int nrec_all, int* err, cudaStream_t st) {
+                          int last, int rec0, int nvalid, int nrec_all, int* err, int expire,
+                          cudaStream_t st) {
   const int N = dft_ncomp(nf);
   if (L.G % TD_M != 0 || N > 128 || kcount < 1 || slot0 % TD_S != 0 || n0 % TD_S != 0 ||
       nvalid < 1)
@@ -660,7 +665,7 @@ cudaError_t launch_dft_tc(const CUtensorMap& tmap, const unsigned char* twt, int
   dim3 grid((unsigned)(L.G / TD_M), (unsigned)((nvalid + TD_R - 1) / TD_R));
   count_launches(1);
   k_dft_tc<<<grid, 128, smem, st>>>(tmap, twt, N, nf, slot0, kcount, n0, L.G, gh, ghb, last, rec0,
-                                    nvalid, nrec_all, err);
+                                    nvalid, nrec_all, err, expire);
   return cudaGetLastError();
 }
 

@@ -5,7 +5,9 @@
 // loop that forbids device allocation (and the implicit synchronisation of cudaMalloc/cudaFree)
 // once it is running.  For them this entry point runs the same Gram kernels as egh_hessian but
 // takes the split-sum workspace from a fixed array in device memory that the library defines
-// at file scope.  Every GPU that loads the library holds that array until the process exits.
+// at file scope.  CUDA loads this file's device code lazily (on first use, by default), so the
+// array's 32 MiB are reserved on a device by the first call there and held until the process
+// exits; callers make that first call at start-up, before their own allocator takes the memory.
 //
 // In host code `g_gram_scratch` names a host-side stand-in, not device memory: its device
 // address is obtained with cudaGetSymbolAddress once per device (on the first call made while

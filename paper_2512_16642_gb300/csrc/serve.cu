@@ -100,6 +100,8 @@ struct Request {
   float* mult = nullptr;
   double t_submit = 0, t_done = 0;
   bool done = false;
+  egh_status status = EGH_OK;  // EGH_ETIMEOUT: a bounded device wait of its batch ran out
+  std::string msg;             // why the request failed
   size_t off_in = 0, off_out = 0, bytes = 0;
 };
 
@@ -117,7 +119,10 @@ struct Server {
   int prec = EGH_PREC_FP32;
   int nslots = 0, max_batch = 0;
   char* arena_base = nullptr;
-  int* d_err = nullptr;  // set by a kernel whose bounded wait ran out
+  int* d_err = nullptr;  // [slots] device flags, set by a kernel whose bounded wait ran out
+  int* h_err = nullptr;  // [slots] pinned host copies, read when a batch completes
+  int expire = 0;        // test hook: batches whose forward transform has one wait run out
+  long long device_timeouts = 0;  // batches with an expired wait since the last drain
   Arena arena;
   std::vector<HSet> sets;
   std::vector<cudaStream_t> streams;
@@ -162,9 +167,16 @@ void CUDART_CB batch_done(void* p) {
   {
     std::lock_guard<std::mutex> lk(sv->mu);
     const double t = now_s();
+    // the slot's error flag was copied to the host just before this callback
+    const bool expired = sv->h_err[b->slot] != 0;
+    if (expired) ++sv->device_timeouts;
     for (Request* r : b->reqs) {
       r->t_done = t;
       r->done = true;
+      if (expired) {
+        r->status = EGH_ETIMEOUT;
+        r->msg = "a bounded device wait ran out in this request's batch; its multipliers are not valid";
+      }
       sv->arena.release(r->off_in, r->bytes);
       sv->arena.release(r->off_out, r->bytes);
       sv->latencies.push_back(t - r->t_submit);
@@ -182,19 +194,21 @@ void CUDART_CB batch_done(void* p) {
 }
 
 // Enqueues one batch on its slot's stream (called by the worker with the lock released).
-cudaError_t run_batch(Server* sv, Batch* b, const HSet& h) {
+cudaError_t run_batch(Server* sv, Batch* b, const HSet& h, int expire) {
   cudaStream_t st = sv->streams[b->slot];
+  int* err = sv->d_err + b->slot;
   int ld = 0;
   for (Request* r : b->reqs) ld += r->ns;
   float2* D = reinterpret_cast<float2*>(sv->arena_base + b->off_d);
   const size_t dsz = (size_t)h.nf * h.nrec * ld;
   cudaError_t e;
+  if ((e = cudaMemsetAsync(err, 0, sizeof(int), st))) return e;
   int s0 = 0;
   for (Request* r : b->reqs) {
     float* din = reinterpret_cast<float*>(sv->arena_base + r->off_in);
     if ((e = cudaMemcpyAsync(din, r->resid, r->bytes, cudaMemcpyHostToDevice, st))) return e;
     if ((e = launch_trace_dft(din, r->ns * h.nrec, r->nt_d, h.nf, h.nrec, ld, s0, D, st,
-                              h.twt, sv->d_err)))
+                              h.twt, err, s0 == 0 ? expire : 0)))
       return e;
     s0 += r->ns;
   }
@@ -214,12 +228,34 @@ cudaError_t run_batch(Server* sv, Batch* b, const HSet& h) {
   for (Request* r : b->reqs) {
     float* dout = reinterpret_cast<float*>(sv->arena_base + r->off_out);
     if ((e = launch_synth(D, h.nrec, r->ns, ld, s0, h.nf, h.w, h.tw, r->nt_d, dout, st, h.tws,
-                          sv->d_err)))
+                          err)))
       return e;
     if ((e = cudaMemcpyAsync(r->mult, dout, r->bytes, cudaMemcpyDeviceToHost, st))) return e;
     s0 += r->ns;
   }
+  if ((e = cudaMemcpyAsync(sv->h_err + b->slot, err, sizeof(int), cudaMemcpyDeviceToHost, st)))
+    return e;
   return cudaLaunchHostFunc(st, batch_done, b);
+}
+
+// A batch whose work could not be enqueued: its requests fail with EGH_ECUDA, and its memory and
+// slot are released once whatever was enqueued on its stream has finished (caller holds the lock).
+void batch_failed(Server* sv, Batch* b, const std::string& msg) {
+  cudaStreamSynchronize(sv->streams[b->slot]);
+  cudaGetLastError();
+  const double t = now_s();
+  for (Request* r : b->reqs) {
+    r->t_done = t;
+    r->done = true;
+    r->status = EGH_ECUDA;
+    r->msg = msg;
+    sv->arena.release(r->off_in, r->bytes);
+    sv->arena.release(r->off_out, r->bytes);
+  }
+  sv->arena.release(b->off_d, b->bytes_d);
+  sv->slot_busy[b->slot] = false;
+  --sv->in_flight;
+  delete b;
 }
 
 // Worker: admits queued requests in arrival order into free slots while their buffers fit.
@@ -320,11 +356,15 @@ void worker_loop(Server* sv) {
     sv->peak_in_flight = std::max(sv->peak_in_flight, sv->in_flight);
     ++sv->batches;
     const HSet hs = h;  // the set list may grow while the lock is released
+    const int expire = sv->expire > 0 ? 1 : 0;
+    if (expire) --sv->expire;
     lk.unlock();
-    const cudaError_t e = run_batch(sv, b, hs);
+    const cudaError_t e = run_batch(sv, b, hs, expire);
     lk.lock();
     if (e != cudaSuccess) {
+      // the batch's requests fail; queued requests fail at egh_server_wait (the server stops)
       sv->worker_error = std::string("batch launch: ") + cudaGetErrorString(e);
+      batch_failed(sv, b, sv->worker_error);
       sv->stop = true;
       sv->cv_done.notify_all();
       break;
@@ -360,13 +400,17 @@ egh_status egh_server_create(const egh_server_config* cfg, egh_server** out) {
     delete sv;
     return fail(nullptr, EGH_ENOMEM, std::string("arena: ") + cudaGetErrorString(e));
   }
-  if ((e = cudaMalloc(&sv->d_err, sizeof(int))) != cudaSuccess ||
-      (e = cudaMemset(sv->d_err, 0, sizeof(int))) != cudaSuccess) {
+  const size_t flag_bytes = sizeof(int) * (size_t)cfg->slots;
+  if ((e = cudaMalloc(&sv->d_err, flag_bytes)) != cudaSuccess ||
+      (e = cudaMemset(sv->d_err, 0, flag_bytes)) != cudaSuccess ||
+      (e = cudaMallocHost(&sv->h_err, flag_bytes)) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(sv->arena_base);
+    cudaFree(sv->d_err);
     delete sv;
-    return fail(nullptr, EGH_ENOMEM, std::string("error flag: ") + cudaGetErrorString(e));
+    return fail(nullptr, EGH_ENOMEM, std::string("error flags: ") + cudaGetErrorString(e));
   }
+  std::memset(sv->h_err, 0, flag_bytes);
   sv->arena.reset((size_t)cfg->hbm_budget_bytes);
   sv->streams.resize(sv->nslots);
   sv->slot_busy.assign(sv->nslots, false);
@@ -497,12 +541,24 @@ egh_status egh_server_wait(egh_server* sv, int64_t request_id, double timeout_s,
   Request* r = it->second;
   const bool ok = sv->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s),
                                        [&] { return r->done || !sv->worker_error.empty(); });
-  if (!sv->worker_error.empty()) return fail(sv, EGH_ECUDA, sv->worker_error);
-  if (!ok) return fail(sv, EGH_ETIMEOUT, "request not finished within the timeout");
-  if (latency_s) *latency_s = r->t_done - r->t_submit;
+  if (!r->done && sv->worker_error.empty() && !ok)
+    return fail(sv, EGH_ETIMEOUT, "request not finished within the timeout (id kept)");
+  // finished, failed, or never to run (the worker stopped): the id is released
+  egh_status s = EGH_OK;
+  std::string msg;
+  if (r->done) {
+    s = r->status;
+    msg = r->msg;
+    if (latency_s) *latency_s = r->t_done - r->t_submit;
+  } else {
+    s = EGH_ECUDA;
+    msg = sv->worker_error;
+    auto q = std::find(sv->queue.begin(), sv->queue.end(), r);
+    if (q != sv->queue.end()) sv->queue.erase(q);
+  }
   sv->reqs.erase(it);
   delete r;
-  return EGH_OK;
+  return s == EGH_OK ? EGH_OK : fail(sv, s, msg);
 }
 
 egh_status egh_server_drain(egh_server* sv, double timeout_s) {
@@ -513,14 +569,20 @@ egh_status egh_server_drain(egh_server* sv, double timeout_s) {
   });
   if (!sv->worker_error.empty()) return fail(sv, EGH_ECUDA, sv->worker_error);
   if (!ok) return fail(sv, EGH_ETIMEOUT, "requests still in flight after the timeout");
-  int derr = 0;  // every batch has completed: the flag is final for them
-  if (cudaSetDevice(sv->dev) != cudaSuccess ||
-      cudaMemcpy(&derr, sv->d_err, sizeof derr, cudaMemcpyDeviceToHost) != cudaSuccess)
-    return fail(sv, EGH_ECUDA, "reading the error flag");
-  if (derr) {
-    cudaMemset(sv->d_err, 0, sizeof(int));
-    return fail(sv, EGH_ETIMEOUT, "a bounded wait for staged twiddles ran out in a transform");
+  // every batch has completed, so every batch's error flag has been read
+  if (sv->device_timeouts) {
+    const long long n = sv->device_timeouts;
+    sv->device_timeouts = 0;
+    return fail(sv, EGH_ETIMEOUT, std::to_string(n) + " batch(es) had a bounded device wait run out "
+                                  "since the last drain (their requests returned EGH_ETIMEOUT)");
   }
+  return EGH_OK;
+}
+
+egh_status egh_server_test_expire_wait(egh_server* sv, int32_t count) {
+  if (!sv || count < 0) return fail(sv, EGH_EINVAL, "NULL server or negative count");
+  std::lock_guard<std::mutex> lk(sv->mu);
+  sv->expire = count;
   return EGH_OK;
 }
 
@@ -599,6 +661,7 @@ void egh_server_destroy(egh_server* sv) {
   }
   cudaFree(sv->arena_base);
   cudaFree(sv->d_err);
+  cudaFreeHost(sv->h_err);
   for (auto& kv : sv->reqs) delete kv.second;
   delete sv;
 }

@@ -65,6 +65,19 @@ __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
   return false;
 }
 
+// Test hook of the bounded waits: waits, for at most kExpireNs, on the phase of an mbarrier that
+// nothing completes, so it always gives up; callers then take the same failure path as when
+// staged data never land (the kernel records its error flag, drains its copies and returns).
+constexpr unsigned long long kExpireNs = 200000ull;
+__device__ __forceinline__ bool mbar_wait_unsignalled(unsigned bar) {
+  const unsigned long long t0 = globaltimer_ns();
+  for (long long i = 0; i < kWaitLimit; ++i) {
+    if (mbar_try_wait(bar, 0)) return true;
+    if (globaltimer_ns() - t0 > kExpireNs) return false;
+  }
+  return false;
+}
+
 __device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned bytes,
                                          unsigned bar) {
   asm volatile(

@@ -100,6 +100,8 @@ _SIGS = {
     "egh_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "egh_version": ([], ctypes.c_int32),
     "egh_release_green": ([_vp], ctypes.c_int),
+    "egh_test_expire_wait": ([_vp, ctypes.c_int32], ctypes.c_int),
+    "egh_server_test_expire_wait": ([_vp, ctypes.c_int32], ctypes.c_int),
     "egh_batch_create": ([ctypes.POINTER(_vp), ctypes.c_int32, ctypes.POINTER(_vp)], ctypes.c_int),
     "egh_batch_factor": ([_vp, _i32p, _i32p, _vp], ctypes.c_int),
     "egh_batch_last_error": ([_vp], ctypes.c_char_p),
@@ -282,8 +284,25 @@ def egh_get_stats(ctx):
     return st.as_dict()
 
 
+def egh_test_expire_wait(ctx, count=1):
+    _check(load().egh_test_expire_wait(ctx, int(count)), ctx)
+
+
+def _nbytes(buf):
+    if isinstance(buf, np.ndarray):
+        return buf.nbytes
+    return buf.numel() * buf.element_size()
+
+
 def egh_gram_noalloc(gh, nrec, nfreq, npts, H, stream=None):
     """Gram of caller-owned device transforms into caller-owned H, allocating nothing."""
+    need_gh = 4 * int(nrec) * int(nfreq) * 2 * int(npts)
+    need_h = 8 * int(nfreq) * int(nrec) * int(nrec)
+    if int(nrec) > 0 and int(nfreq) > 0 and int(npts) > 0:
+        if _nbytes(gh) < need_gh:
+            raise ValueError(f"gh holds {_nbytes(gh)} bytes, needs {need_gh} (nrec x nfreq x 2 x npts float32)")
+        if _nbytes(H) < need_h:
+            raise ValueError(f"H holds {_nbytes(H)} bytes, needs {need_h} (nfreq x nrec x nrec complex64)")
     pg, cg = _ptr(gh)
     ph, chh = _ptr(H)
     _check(load().egh_gram_noalloc(pg, int(nrec), int(nfreq), int(npts), ph, _stream(stream, cg or chh)),
@@ -360,6 +379,9 @@ class Context:
         out = np.zeros((nr, self.nf, NZ, NX), dtype=np.complex64)
         egh_get_green(self.h, r0, nr, out)
         return out
+
+    def test_expire_wait(self, count=1):
+        egh_test_expire_wait(self.h, count)
 
     def release_green(self):
         _check(load().egh_release_green(self.h), self.h)
@@ -472,6 +494,9 @@ class Server:
 
     def reset_stats(self):
         _check_server(load().egh_server_reset_stats(self.h), self.h)
+
+    def test_expire_wait(self, count=1):
+        _check_server(load().egh_server_test_expire_wait(self.h, int(count)), self.h)
 
     def hold(self, on=True):
         """Pauses (on) or resumes (off) admission; requests submitted while held queue and are

@@ -173,6 +173,14 @@ def test_salt_patches_full_size_sampled():
                     b.factor()
                     for ctx, L in zip(ctxs, L1):
                         np.testing.assert_array_equal(ctx.get_hessian(True), L)
+            # the deblur at the largest patch's shape (341 receivers, 40 frequencies: the
+            # synthesis of 2 nf > 64 components), from the batched factors
+            rd = synth.bandlimited_noise(np.random.default_rng(21), (6, 341, 2000), c.dt, 2.0,
+                                         10.0).astype(np.float32)
+            rt = torch.from_numpy(rd).cuda()
+            mt = torch.empty_like(rt)
+            ctxs[2].deblur(rt, mt)
+            mult = mt.cpu().numpy()
         finally:
             for ctx in ctxs:
                 ctx.close()
@@ -196,3 +204,10 @@ def test_salt_patches_full_size_sampled():
         for k in range(c.freqs.size):
             back = np.linalg.norm(L[k] @ L[k].conj().T - Q[p][k]) / np.linalg.norm(Q[p][k])
             assert back <= 1e-5, (p, k, back)
+    # steps a5-a7 element by element: the oracle's Cholesky, solve and synthesis on the GPU's own
+    # Hessians of that patch (pinned entry by entry above) for sampled sources
+    srcs = [0, 3, 5]
+    om = oracle.deblur(oracle.cholesky(Q[2]), rd[srcs].astype(np.float64), c.freqs, c.dt,
+                       nt_ref=c.nt)[0]
+    for i, s in enumerate(srcs):
+        assert rel(mult[s], om[i]) <= 1e-3, s

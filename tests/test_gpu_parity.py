@@ -406,5 +406,54 @@ def test_layered_full_size_sampled():
             ctx.deblur(rt[5:9].contiguous(), part)
             torch.cuda.synchronize()
             assert torch.equal(part, mt[5:9])
+            # steps a5-a7 at the benchmark's shape, element by element: the oracle's Cholesky,
+            # solve and synthesis on this context's Hessians (pinned entry by entry above) for
+            # sampled sources against the GPU multipliers
+            srcs = [0, 57, 114]
+            om = oracle.deblur(oracle.cholesky(Q), r32[srcs].astype(np.float64), c.freqs, c.dt,
+                               nt_ref=c.nt)[0]
+            mh = mt.cpu().numpy()
+            for i, s in enumerate(srcs):
+                assert rel(mh[s], om[i]) <= MULT_TOL, (prec, s)
             st = ctx.stats()
             assert st["pde_solves"] == 231
+
+
+def test_bounded_wait_expiry_is_reported_and_context_recovers():
+    """Failure path of the bounded device waits.  With the test hook, one block of the next
+    transform launch waits on an mbarrier that nothing signals and gives up after about 0.2 ms:
+    the kernel records the context's error flag, lets its copies land, frees its tensor memory
+    and returns (nothing faults or hangs).  The call reports EGH_ETIMEOUT, and the same context
+    then gives the results of a run without the hook, bit for bit: for the Green stage's
+    transform (egh_green) and for the deblur's forward transform (host-buffer egh_deblur)."""
+    torch = _torch()
+    from paper_2512_16642_gb300 import egh
+
+    c = synth.case_tiny(seed=3, nz=24, nx=40, nsponge=6, nrec=5, nt=120)
+    v = torch.from_numpy(np.float32(c.vel_true)).cuda()
+    r32 = np.random.default_rng(4).standard_normal((3, 5, 120)).astype(np.float32)
+    with _ctx(c) as ctx:
+        ctx.green(v)
+        ref_gh = ctx.get_green()
+        ctx.hessian()
+        ctx.factor()
+        ref = np.empty_like(r32)
+        ctx.deblur(r32, ref)
+        ctx.test_expire_wait(1)
+        with pytest.raises(egh.EghError) as ei:
+            ctx.green(v)
+        assert ei.value.status == egh.EGH_ETIMEOUT
+        with pytest.raises(egh.EghError) as ei:  # the failed stage leaves no Hessian to build
+            ctx.hessian()
+        assert ei.value.status == egh.EGH_ESTATE
+        ctx.green(v)
+        assert np.array_equal(ctx.get_green(), ref_gh)
+        ctx.hessian()
+        ctx.factor()
+        ctx.test_expire_wait(1)
+        out = np.empty_like(r32)
+        with pytest.raises(egh.EghError) as ei:
+            ctx.deblur(r32, out)
+        assert ei.value.status == egh.EGH_ETIMEOUT
+        ctx.deblur(r32, out)
+        assert np.array_equal(out, ref)

@@ -175,3 +175,40 @@ def test_many_frequencies(nt_d):
         out = _pinned(r.shape, torch)
         sv.wait(sv.submit(sid, rin, out))
     assert rel(out.numpy(), ref) <= MULT_TOL
+
+
+def test_bounded_wait_expiry_fails_only_its_request():
+    """A batch whose forward transform has a bounded device wait run out (test hook: one block
+    waits on an mbarrier that nothing signals, about 0.2 ms) fails its own requests with
+    EGH_ETIMEOUT through egh_server_wait, and only those: the next request gets the multipliers
+    of a clean run bit for bit, the server stays usable, and the next drain reports that a wait
+    ran out since the previous drain (and the one after it does not)."""
+    import torch
+    from paper_2512_16642_gb300 import egh
+
+    rng = np.random.default_rng(77)
+    Q, f = _hpd_set(rng, 11, 4)
+    r = synth.bandlimited_noise(rng, (3, 11, 400), 1e-3, 2.0, 10.0)
+    with egh.Server(64 << 20, slots=2, max_batch_sources=8, precision=1) as sv:
+        sid = sv.add_set(Q, f, 1e-3, 1000, 512)
+        rin = _pinned(r.shape, torch, r)
+        ref = _pinned(r.shape, torch)
+        sv.wait(sv.submit(sid, rin, ref))
+        sv.drain()
+        sv.test_expire_wait(1)
+        bad = _pinned(r.shape, torch)
+        rid = sv.submit(sid, rin, bad)
+        with pytest.raises(egh.EghError) as ei:
+            sv.wait(rid)
+        assert ei.value.status == egh.EGH_ETIMEOUT and "bounded device wait" in str(ei.value)
+        with pytest.raises(egh.EghError):  # the id was released with its status
+            sv.wait(rid)
+        out = _pinned(r.shape, torch)
+        sv.wait(sv.submit(sid, rin, out))
+        assert np.array_equal(out.numpy(), ref.numpy())
+        with pytest.raises(egh.EghError) as ei:
+            sv.drain()
+        assert ei.value.status == egh.EGH_ETIMEOUT
+        sv.drain()
+        st = sv.stats()
+        assert st["completed"] == 3

@@ -1,11 +1,12 @@
-"""egh_gram_noalloc, the allocation-free Gram entry point, against egh_hessian.
+"""egh_gram_noalloc, the allocation-free Gram entry point, against egh_hessian and FP64.
 
 For callers that cannot call cudaMalloc (device memory already reserved by another allocator,
 or a running service loop that forbids allocation), egh_gram_noalloc computes the per-frequency
 Gram from caller-owned device buffers with a fixed scratch array inside the library.  This test
-compares it, through the C ABI, with the Hessian of the regular entry point (mu = 0) on the same
-Green-function transforms, within the Hessian tolerance of the parity tests, on two calls in a
-row (the second on a smaller problem, so stale scratch from the first would show)."""
+compares it, through the C ABI, with the Hessian of the regular entry point (mu = 0) and with an
+FP64 Gram of the same transforms computed on the host, within the Hessian tolerance of the
+parity tests, on two calls in a row (the second on a smaller problem, so stale scratch from the
+first would show), and checks that the second call takes no device memory."""
 import numpy as np
 import pytest
 
@@ -43,26 +44,33 @@ def test_gram_noalloc_matches_hessian_two_calls():
         ref = ctx.get_hessian(False).astype(np.complex128)
         gh = ctx.get_green()
     nr, nf = gh.shape[:2]
+    # the same Gram in FP64 on the host, H[k][i][j] = sum_x g_i conj(g_j)
+    g64 = gh.reshape(nr, nf, -1).astype(np.complex128)
+    ref64 = np.einsum("ikx,jkx->kij", g64, g64.conj())
     npts = (gh[0, 0].size + 15) // 16 * 16
     d_gh = torch.from_numpy(_planar(gh, npts)).cuda()
-
-    # call 1: all 70 receivers (3 tiles of 32)
+    sub = 20
+    d_sub = d_gh[:sub].contiguous()
     H = torch.full((nf, nr, nr), float("nan"), dtype=torch.complex64, device="cuda")
+    H2 = torch.full((nf, sub, sub), float("nan"), dtype=torch.complex64, device="cuda")
+
+    # call 1: all 70 receivers (3 tiles of 32); its first use on this device loads the scratch
     egh.egh_gram_noalloc(d_gh, nr, nf, npts, H)
     torch.cuda.synchronize()
     h = H.cpu().numpy().astype(np.complex128)
     for k in range(nf):
         assert rel(h[k], ref[k]) <= HESS_TOL, k
+        assert rel(h[k], ref64[k]) <= HESS_TOL, k
 
-    # call 2: the first 20 receivers only
-    sub = 20
-    d_sub = d_gh[:sub].contiguous()
-    H2 = torch.full((nf, sub, sub), float("nan"), dtype=torch.complex64, device="cuda")
+    # call 2: the first 20 receivers only; it must take no device memory
+    free0 = torch.cuda.mem_get_info()[0]
     egh.egh_gram_noalloc(d_sub, sub, nf, npts, H2)
     torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
     h2 = H2.cpu().numpy().astype(np.complex128)
     for k in range(nf):
         assert rel(h2[k], ref[k][:sub, :sub]) <= HESS_TOL, k
+        assert rel(h2[k], ref64[k][:sub, :sub]) <= HESS_TOL, k
 
 
 def test_gram_noalloc_rejects_what_it_cannot_do():
@@ -82,3 +90,11 @@ def test_gram_noalloc_rejects_what_it_cannot_do():
     with pytest.raises(egh.EghError) as ei:
         egh.egh_gram_noalloc(big, 1, 1, 10, H)
     assert ei.value.status == egh.EGH_EINVAL
+    # buffers smaller than the sizes say are refused before the call
+    small_gh = torch.zeros((2, 1, 2, 16), device="cuda")
+    with pytest.raises(ValueError):
+        egh.egh_gram_noalloc(small_gh, 4, 1, 16, H)
+    gh_ok = torch.zeros((8, 1, 2, 16), device="cuda")
+    small_h = torch.empty((1, 4, 4), dtype=torch.complex64, device="cuda")
+    with pytest.raises(ValueError):
+        egh.egh_gram_noalloc(gh_ok, 8, 1, 16, small_h)
