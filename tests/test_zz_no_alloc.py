@@ -78,19 +78,23 @@ def test_gram_noalloc_rejects_what_it_cannot_do():
 
     from paper_2512_16642_gb300 import egh
 
+    lib = egh.load()
+
+    def raw(gh_ptr, nrec, nfreq, npts, h_ptr):  # the C entry point itself, no wrapper checks
+        return lib.egh_gram_noalloc(gh_ptr, nrec, nfreq, npts, h_ptr, torch.cuda.current_stream().cuda_stream)
+
     H = torch.empty((64, 8, 8), dtype=torch.complex64, device="cuda")
     big = torch.empty((16,), device="cuda")
-    with pytest.raises(egh.EghError) as ei:  # 1000 receivers x 64 frequencies exceed the scratch
-        egh.egh_gram_noalloc(big, 1000, 64, 16, H)
-    assert ei.value.status == egh.EGH_EINVAL and "scratch" in str(ei.value)
-    host = np.zeros((8, 1, 2, 16), np.float32)
-    with pytest.raises(egh.EghError) as ei:  # host memory is refused before any launch
+    # 1000 receivers x 64 frequencies exceed the scratch: refused before any launch
+    assert raw(big.data_ptr(), 1000, 64, 16, H.data_ptr()) == egh.EGH_EINVAL
+    assert "scratch" in lib.egh_last_error(None).decode()
+    host = np.zeros((8, 1, 2, 16), np.float32)  # host memory is refused before any launch
+    assert raw(host.ctypes.data, 8, 1, 16, H.data_ptr()) == egh.EGH_EINVAL
+    assert raw(big.data_ptr(), 1, 1, 10, H.data_ptr()) == egh.EGH_EINVAL  # npts not a multiple of 16
+    with pytest.raises(egh.EghError) as ei:  # the same through the binding
         egh.egh_gram_noalloc(host, 8, 1, 16, H)
     assert ei.value.status == egh.EGH_EINVAL
-    with pytest.raises(egh.EghError) as ei:
-        egh.egh_gram_noalloc(big, 1, 1, 10, H)
-    assert ei.value.status == egh.EGH_EINVAL
-    # buffers smaller than the sizes say are refused before the call
+    # buffers smaller than the sizes say are refused by the binding before the call
     small_gh = torch.zeros((2, 1, 2, 16), device="cuda")
     with pytest.raises(ValueError):
         egh.egh_gram_noalloc(small_gh, 4, 1, 16, H)
