@@ -119,7 +119,16 @@ typedef struct {
                                 egh_green of the context: the smallest count whose tiles fit one
                                 wave of resident blocks is kept unless another is 3% faster */
     int32_t precision;       /* egh_precision of the Hessian stage (0 = EGH_PREC_FP32) */
-    int32_t reserved[3];     /* must be zero */
+    int32_t fd_kernel;       /* FD solver of the Green stage: 0 = library choice (the resident
+                                solver whenever the state of at least one receiver pair fits a
+                                block's shared memory, else the per-step kernel); 1 = resident:
+                                the batch's wavefield stays in shared memory for a whole transform
+                                chunk, one block per SM (EGH_EINVAL if it does not fit); 2 = one
+                                kernel per time step, state in global memory.  Both give identical
+                                levels.  With the resident solver, batch_receivers = 0 takes the
+                                most receivers whose state fits (at most 16), and fd_rows does not
+                                apply (its rows per segment are timed on the first egh_green) */
+    int32_t reserved[2];     /* must be zero */
 } egh_config;
 
 typedef struct egh_ctx egh_ctx;
@@ -142,6 +151,9 @@ typedef struct {
     int64_t fd_launches;       /* last egh_green: FD step launches */
     int64_t dft_launches;      /* last egh_green: transform launches */
     double gram_ms;            /* last egh_hessian: device time of the Gram kernel */
+    int64_t fd_steps;          /* last egh_green: FD time steps computed (all batches) */
+    int32_t fd_kernel;         /* FD solver in use: 1 resident, 2 per step */
+    int32_t fd_tiles;          /* resident solver: blocks (tiles) per launch, else 0 */
 } egh_stats;
 
 /* Validates the configuration and allocates the device state on the current
@@ -368,13 +380,17 @@ void egh_server_destroy(egh_server *sv);
  * and egh_get_green then return EGH_ESTATE until egh_green runs again.  Blocks. */
 egh_status egh_release_green(egh_ctx *ctx);
 
-/* Test hook of the failure path (the paper has no counterpart): in the next `count` transform
- * launches of this context (the Green stage's on-the-fly transform, the deblur's forward
- * transform), the first block has one bounded device wait run out, on an mbarrier that nothing
- * signals, after about 0.2 ms; the kernel records the context's error flag, lets its copies in
- * flight land, frees its tensor memory and returns.  The call that waits for that work returns
- * EGH_ETIMEOUT and the context stays usable.  count = 0 cancels. */
-egh_status egh_test_expire_wait(egh_ctx *ctx, int32_t count);
+/* Test hook of the failure path (the paper has no counterpart).  In the next `count` launches
+ * of one kind of kernel of this context, the first block has one bounded device wait run out
+ * after about 0.2 ms, on a condition that nothing ever satisfies (an mbarrier phase, or a step
+ * count no block publishes); the kernel then takes its failure path exactly as when staged data
+ * or a neighbour never arrive: it records the context's error flag, lets its copies in flight
+ * land, frees its tensor memory and returns, and the resident solver's other blocks see its
+ * abort flag and return too.  Nothing faults or hangs.  The call that waits for that work
+ * returns EGH_ETIMEOUT and the context stays usable.  kind: 0 = the Green stage's on-the-fly
+ * transform, 1 = the resident FD solver, 2 = the deblur's forward transform.  count = 0
+ * cancels. */
+egh_status egh_test_expire_wait(egh_ctx *ctx, int32_t kind, int32_t count);
 
 /* ---- Batched factorisation --------------------------------------------------------------- *
  * A batch groups contexts (survey patches of one model, any receiver counts, one device, one

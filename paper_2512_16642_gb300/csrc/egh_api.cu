@@ -47,7 +47,13 @@ struct egh_ctx {
   std::vector<double> freqs;
   std::vector<float> wsyn;
   int B = 0, K = 0, splits = 0;
-  int fd_tz = 0;  // FD rows per warp (0 = library default)
+  int fd_tz = 0;  // FD rows per warp of the per-step kernel (0 = library default)
+  int fd_kernel = 2;  // 1: resident solver (fd_resident.cu), 2: one kernel per step (fd.cu)
+  ResGeom rg{};       // resident solver: tile grid and pairs per block
+  int res_sr = 0;     // resident solver: rows per z-march segment (0 = timed on first egh_green)
+  float4* xbuf = nullptr;  // resident solver: halo exchange strips
+  int* rflags = nullptr;   // resident solver: per-tile step counters + abort flag
+  long long fd_steps = 0;  // last egh_green: FD steps computed
   int prec = EGH_PREC_FP32;
   int splits_tc = 0;  // grid-sum splits of the tensor-core Gram
   bool tune_splits = false;  // time half / once / twice the default splits on the first Gram
@@ -87,7 +93,8 @@ struct egh_ctx {
   double* lmax = nullptr;
   float* vchk = nullptr;
   int* d_err = nullptr;  // set by bounded device waits that ran out
-  int expire = 0;        // test hook: transform launches whose first CTA has one wait run out
+  int expire[3] = {0, 0, 0};  // test hook: launches (Green transform, resident FD, deblur
+                              // transform) whose first block has one wait run out
   float* vel_stage = nullptr;
   float2* Dh = nullptr;
   size_t Dh_cap = 0;
@@ -276,7 +283,7 @@ cudaError_t zero_snap_slot(egh_ctx* ctx, int j, cudaStream_t st) {
 }
 
 void free_all(egh_ctx* c) {
-  void* ptrs[] = {c->tws_deb, c->twt_deb, c->twt_bl, c->Wh, c->Dr, c->Rr, c->coef, c->lev, c->snap, c->twt, c->gh, c->ghb, c->part, c->Qh, c->Lh, c->tw, c->w_dev,
+  void* ptrs[] = {c->xbuf, c->rflags, c->tws_deb, c->twt_deb, c->twt_bl, c->Wh, c->Dr, c->Rr, c->coef, c->lev, c->snap, c->twt, c->gh, c->ghb, c->part, c->Qh, c->Lh, c->tw, c->w_dev,
                   c->rec_pts, c->status, c->dsum, c->lmax, c->vchk, c->d_err, c->vel_stage, c->Dh,
                   c->io_in, c->io_out};
   for (void* p : ptrs)
@@ -397,6 +404,7 @@ egh_status egh_create(const egh_config* cfg, egh_ctx** out) {
   const egh_config& c = *cfg;
   for (int v : c.reserved)
     if (v != 0) return fail(nullptr, EGH_EINVAL, "reserved config fields must be zero");
+  if (c.fd_kernel < 0 || c.fd_kernel > 2) return fail(nullptr, EGH_EINVAL, "fd_kernel must be 0, 1 or 2");
   if (c.nz < 1 || c.nx < 1) return fail(nullptr, EGH_EINVAL, "nz and nx must be >= 1");
   if (!(c.dz > 0) || !(c.dx > 0)) return fail(nullptr, EGH_EINVAL, "dz and dx must be > 0");
   if (c.nsponge < 0) return fail(nullptr, EGH_EINVAL, "nsponge must be >= 0");
@@ -435,9 +443,7 @@ egh_status egh_create(const egh_config* cfg, egh_ctx** out) {
   ctx->rec_iz.assign(c.rec_iz, c.rec_iz + c.nrec);
   ctx->rec_ix.assign(c.rec_ix, c.rec_ix + c.nrec);
   ctx->freqs.assign(c.freq_hz, c.freq_hz + c.nfreq);
-  ctx->B = c.batch_receivers ? std::min(c.batch_receivers, c.nrec) : std::min(c.nrec, 16);
   ctx->K = c.dft_chunk ? c.dft_chunk : 512;
-  ctx->Bp = 2 * ((ctx->B + 1) / 2);
   ctx->fd_tz = c.fd_rows;
 
   Layout& L = ctx->L;
@@ -448,6 +454,34 @@ egh_status egh_create(const egh_config* cfg, egh_ctx** out) {
   L.F = (long long)(L.NZ + 2 * GUARD) * L.PX;
   L.org = (long long)GUARD * L.PX;
   L.G = round_up((long long)L.NZ * L.PX, 256);
+
+  // FD solver: resident when the state of the batch's pairs fits a block's shared memory
+  {
+    const int want = c.batch_receivers ? c.batch_receivers : 16;
+    bool res = false;
+    if (c.fd_kernel != 2) {
+      res = fd_resident_plan(L, (want + 1) / 2, &ctx->rg) &&
+            !(c.batch_receivers && (c.batch_receivers + 1) / 2 > ctx->rg.P);
+      if (res) {
+        const int np = (std::min(c.batch_receivers ? c.batch_receivers : 2 * ctx->rg.P, c.nrec) + 1) / 2;
+        for (int sr : {6, 8, 11, 16})
+          if (fd_resident_prepare(ctx->rg, sr, np) != cudaSuccess) res = false;
+        cudaGetLastError();
+      }
+      if (!res && c.fd_kernel == 1) {
+        delete ctx;
+        return fail(nullptr, EGH_EINVAL,
+                    "fd_kernel = 1: the batch's state does not fit a block's shared memory with one "
+                    "block per SM resident (grid too large, or batch_receivers too many)");
+      }
+    }
+    ctx->fd_kernel = res ? 1 : 2;
+    if (res)
+      ctx->B = c.batch_receivers ? std::min(c.batch_receivers, c.nrec) : std::min(c.nrec, 2 * ctx->rg.P);
+    else
+      ctx->B = c.batch_receivers ? std::min(c.batch_receivers, c.nrec) : std::min(c.nrec, 16);
+    ctx->Bp = 2 * ((ctx->B + 1) / 2);
+  }
 
   ctx->prec = c.precision;
   {
@@ -481,6 +515,10 @@ egh_status egh_create(const egh_config* cfg, egh_ctx** out) {
   } while (0)
   ALLOC(ctx->coef, F * sizeof(float2), "coefficients");
   ALLOC(ctx->lev, (size_t)3 * ((ctx->B + 1) / 2) * F * sizeof(float2), "FD state");
+  if (ctx->fd_kernel == 1) {
+    ALLOC(ctx->xbuf, fd_resident_xbuf_float4(ctx->rg) * sizeof(float4), "FD halo exchange");
+    ALLOC(ctx->rflags, sizeof(int) * (ctx->rg.TR * ctx->rg.TC + 1), "FD step counters");
+  }
   std::vector<unsigned char> twt = dft_twiddle_tiles(ctx->freqs, c.dt, c.nt);
   ALLOC(ctx->twt, twt.size(), "twiddle tiles");
   ALLOC(ctx->part,
@@ -595,7 +633,48 @@ egh_status green_run(egh_ctx* ctx, const float* vel, cudaStream_t stream, const 
   CK(cudaStreamWaitEvent(ctx->fdst, ctx->ev_side, 0));
   cudaStream_t fs = ctx->fdst;
   const float src_scale = (float)(1.0 / (ctx->dx * ctx->dz));
-  if (ctx->fd_tz == 0) {
+  const long long per = (long long)ctx->Bp * L.G;  // snapshot ring: elements per slot
+  // resident solver: levels ta .. t1-1 of a chunk whose level t0 sits in ring slot sbase
+  auto resident = [&](int ta, int t0, int t1, int sbase, int np, int D, int sr, int expire) {
+    return launch_fd_resident(ctx->rg, sr, ctx->lev, (ctx->B + 1) / 2, L, ctx->coef, ctx->S, np, ta,
+                              t1 - ta, t0, D, sbase, ctx->snap, per, 2LL * K * per, L.G, ctx->xbuf,
+                              ctx->rflags, ctx->d_err, expire, fs);
+  };
+  if (ctx->fd_kernel == 1 && ctx->res_sr == 0) {
+    // rows per z-march segment of the resident solver: time each choice on this grid (24 steps
+    // of a full batch writing their snapshots, as the run does; the run rewrites every state and
+    // ring slot it reads), best of three passes after a warm-up; the default is kept unless
+    // another choice is 3% faster
+    const int np = (std::min(B, ctx->nrec) + 1) / 2;
+    const int def_sr = fd_resident_sr_default();
+    float best = 1e30f, def_ms = 1e30f;
+    int best_sr = def_sr;
+    for (int sr : {6, 8, 11, 16}) {
+      float sr_best = 1e30f;
+      for (int rep = 0; rep < 4; ++rep) {
+        float ms = 0.f;
+        CK(cudaEventRecord(ctx->ev_tune[0], fs));
+        CK(resident(2, 0, 26, 0, np, 1, sr, 0));
+        CK(cudaEventRecord(ctx->ev_tune[1], fs));
+        CK(cudaEventSynchronize(ctx->ev_tune[1]));
+        CK(cudaEventElapsedTime(&ms, ctx->ev_tune[0], ctx->ev_tune[1]));
+        if (rep > 0) sr_best = std::min(sr_best, ms);
+      }
+      if (sr_best < best) {
+        best = sr_best;
+        best_sr = sr;
+      }
+      if (sr == def_sr) def_ms = sr_best;
+    }
+    int derr = 0;  // a wait that ran out in the timing pass
+    CK(cudaMemcpy(&derr, ctx->d_err, sizeof derr, cudaMemcpyDeviceToHost));
+    if (derr) {
+      CK(cudaMemset(ctx->d_err, 0, sizeof(int)));
+      return fail(ctx, EGH_ETIMEOUT, "a bounded wait for a neighbouring tile ran out in the FD solver");
+    }
+    ctx->res_sr = best < 0.97f * def_ms ? best_sr : def_sr;
+  }
+  if (ctx->fd_kernel == 2 && ctx->fd_tz == 0) {
     // Rows per warp of the FD step: time each choice on this grid (steps of a full batch that
     // write their snapshots, as the run does; the run below rewrites every state slot and ring
     // slot it reads), best of three passes of 24 steps per choice.
@@ -629,6 +708,7 @@ egh_status green_run(egh_ctx* ctx, const float* vel, cudaStream_t stream, const 
   const int D = decim;
   const int ntd = (nt + D - 1) / D;  // recorded levels 0, D, 2D, ... < nt
   const int nchunk = (ntd + K - 1) / K;
+  long long fd_steps = 0, fd_kernel_launches = 0;
   long long g = 0;  // chunks so far over all batches: chunk g uses ring slots (g % 2) K ..
   for (int b0 = 0; b0 < ctx->nrec; b0 += B) {
     const int nb = std::min(B, ctx->nrec - b0);
@@ -661,13 +741,23 @@ egh_status green_run(egh_ctx* ctx, const float* vel, cudaStream_t stream, const 
         CK(launch_inject(slot(ctx, t), L.F, ctx->rec_pts + b0, ctx->coef, nb, wav[t - 1], src_scale,
                          L.org, so, fs));
       }
-      if ((s = fd_chunk_steps(ctx, tw, t0, t1, sbase, np, D))) return s;
+      if (ctx->fd_kernel == 1) {
+        if (tw < t1) {
+          const int expire = ctx->expire[1] > 0 ? 1 : 0;
+          ctx->expire[1] -= expire;
+          CK(resident(tw, t0, t1, sbase, np, D, ctx->res_sr, expire));
+        }
+      } else if ((s = fd_chunk_steps(ctx, tw, t0, t1, sbase, np, D))) {
+        return s;
+      }
+      fd_steps += std::max(0, t1 - std::max(t0, 2));
+      if (ctx->fd_kernel == 1 && tw < t1) ++fd_kernel_launches;
       CK(cudaEventRecord(ctx->ev_fd[2 * g + 1], fs));
       CK(cudaEventRecord(ctx->fd_done[g & 1], fs));
       CK(cudaStreamWaitEvent(ctx->side, ctx->fd_done[g & 1], 0));
       CK(cudaEventRecord(ctx->ev_dft[2 * g], ctx->side));
-      const int expire = ctx->expire > 0 ? 1 : 0;
-      ctx->expire -= expire;
+      const int expire = ctx->expire[0] > 0 ? 1 : 0;
+      ctx->expire[0] -= expire;
       CK(launch_dft_tc(ctx->tmap, twt, ctx->nf, sbase, m1 - m0, m0, L, ctx->gh, ctx->ghb,
                        (m1 == ntd && ctx->ghb) ? 1 : 0, b0, nb, ctx->nrec, ctx->d_err, expire,
                        ctx->side));
@@ -686,7 +776,8 @@ egh_status green_run(egh_ctx* ctx, const float* vel, cudaStream_t stream, const 
   CK(cudaStreamSynchronize(stream));
   if (derr) {
     CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), stream));
-    return fail(ctx, EGH_ETIMEOUT, "a bounded wait for staged snapshots ran out in the transform");
+    return fail(ctx, EGH_ETIMEOUT, "a bounded device wait ran out in the Green stage (staged snapshots "
+                                   "in the transform, or a neighbouring tile in the FD solver)");
   }
   {
     // per-kernel device time of this call: FD steps (memsets, impulse and graph replay of each
@@ -701,8 +792,12 @@ egh_status green_run(egh_ctx* ctx, const float* vel, cudaStream_t stream, const 
     }
     ctx->st.fd_ms = fd;
     ctx->st.dft_ms = dft;
-    ctx->st.fd_launches = (long long)((ctx->nrec + B - 1) / B) * std::max(0, nt - 2);
+    ctx->st.fd_launches = ctx->fd_kernel == 1 ? fd_kernel_launches
+                                              : (long long)((ctx->nrec + B - 1) / B) * std::max(0, nt - 2);
     ctx->st.dft_launches = g;
+    ctx->st.fd_steps = fd_steps;
+    ctx->st.fd_kernel = ctx->fd_kernel;
+    ctx->st.fd_tiles = ctx->fd_kernel == 1 ? ctx->rg.TR * ctx->rg.TC : 0;
   }
   ctx->st.pde_solves = ctx->nrec;
   ctx->st.point_steps = (long long)ctx->nrec * nt * L.NZ * L.NX;
@@ -930,8 +1025,8 @@ static egh_status deblur_common(egh_ctx* ctx, const float* resid, int32_t ns, in
     dout = ctx->io_out;
   }
   CK(cudaEventRecord(ctx->ev[6], stream));
-  const int expire = ctx->expire > 0 ? 1 : 0;
-  ctx->expire -= expire;
+  const int expire = ctx->expire[2] > 0 ? 1 : 0;
+  ctx->expire[2] -= expire;
   CK(launch_trace_dft(din, (int)ntr, nt_d, ctx->nf, ctx->nrec, ns, 0, D, stream,
                       ctx->twt_deb, ctx->d_err, expire));
   const size_t dbytes = (size_t)ctx->nf * ntr * sizeof(float2);
@@ -1136,15 +1231,19 @@ egh_status egh_get_stats(egh_ctx* ctx, egh_stats* out) {
       *ms[i] = t;
     }
   ctx->st.kernel_launches = launches_so_far();
-  ctx->st.fd_rows = ctx->fd_tz;
+  ctx->st.fd_rows = ctx->fd_kernel == 1 ? ctx->res_sr : ctx->fd_tz;
+  ctx->st.fd_kernel = ctx->fd_kernel;
+  ctx->st.fd_tiles = ctx->fd_kernel == 1 ? ctx->rg.TR * ctx->rg.TC : 0;
   *out = ctx->st;
   return EGH_OK;
 }
 
-egh_status egh_test_expire_wait(egh_ctx* ctx, int32_t count) {
+egh_status egh_test_expire_wait(egh_ctx* ctx, int32_t kind, int32_t count) {
   if (!ctx) return fail(nullptr, EGH_EINVAL, "ctx is NULL");
-  if (count < 0) return fail(ctx, EGH_EINVAL, "count must be >= 0");
-  ctx->expire = count;
+  if (count < 0 || kind < 0 || kind > 2) return fail(ctx, EGH_EINVAL, "kind must be 0..2, count >= 0");
+  if (kind == 1 && ctx->fd_kernel != 1)
+    return fail(ctx, EGH_EINVAL, "this context does not use the resident FD solver");
+  ctx->expire[kind] = count;
   return EGH_OK;
 }
 

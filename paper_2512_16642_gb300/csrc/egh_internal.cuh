@@ -84,6 +84,33 @@ cudaError_t launch_dft_tc(const CUtensorMap& tmap, const unsigned char* twt, int
                           int last, int rec0, int nvalid, int nrec_all, int* err, int expire,
                           cudaStream_t st);
 
+// ---- fd_resident.cu ---------------------------------------------------------------------------
+// The padded grid as TR x TC tiles of TZ x TX points (TX % 4 == 0), one block per tile, all
+// resident at once; P receiver pairs of a batch held in each block's shared memory.
+struct ResGeom {
+  int TR, TC, TZ, TX;
+  int P;
+  size_t smem;  // dynamic shared memory per block
+};
+// Tile grid with the most pairs (<= want_pairs, <= 8) whose state fits a block's shared memory,
+// then the smallest tile; false if not even one pair fits.
+bool fd_resident_plan(const Layout& L, int want_pairs, ResGeom* g);
+size_t fd_resident_xbuf_float4(const ResGeom& g);  // halo exchange buffer (float4)
+int fd_resident_sr_default();                         // rows per z-march segment
+bool fd_resident_sr_valid(int sr);                    // 6, 8, 11 or 16
+// shared-memory limit of every instance, and a check that the grid is co-resident (sr, np:
+// the launch's segment rows and pairs, which set its block size)
+cudaError_t fd_resident_prepare(const ResGeom& g, int sr, int np);
+// Levels ta .. ta+nsteps-1 of np pairs (ta >= 2), from the state slots of levels ta-1, ta-2 of
+// lev ([3][pslot][F]) to the slots of the last two levels; level t's bf16 hi/lo snapshot goes to
+// ring slot sbase + (t - t0) / decim when t % decim == 0 (snap: hi plane of ring slot 0, or
+// null).  flags: tiles + 1 ints (zeroed here).  Cooperative launch.
+cudaError_t launch_fd_resident(const ResGeom& g, int sr, float2* lev, int pslot, const Layout& L,
+                               const float2* coef, const Stencil& S, int np, int ta, int nsteps,
+                               int t0, int decim, int sbase, __nv_bfloat16* snap, long long sslot,
+                               long long splane, long long srec, float4* xbuf, int* flags,
+                               int* err, int expire, cudaStream_t st);
+
 // ---- gram_tc.cu -------------------------------------------------------------------------------
 // Gram on the tensor cores from the bf16 hi/lo transforms ghb[nrec][nf][re/im][hi/lo][G].
 __host__ __device__ int gram_tc_blocks(int nrec);

@@ -34,7 +34,8 @@ class egh_config(ctypes.Structure):
         ("nfreq", ctypes.c_int32), ("freq_hz", _f64p),
         ("batch_receivers", ctypes.c_int32), ("dft_chunk", ctypes.c_int32),
         ("gram_splits", ctypes.c_int32), ("fd_rows", ctypes.c_int32),
-        ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3),
+        ("precision", ctypes.c_int32), ("fd_kernel", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 2),
     ]
 
 
@@ -50,7 +51,8 @@ class egh_stats(ctypes.Structure):
         ("fd_rows", ctypes.c_int32), ("pad_", ctypes.c_int32),
         ("fd_ms", ctypes.c_double), ("dft_ms", ctypes.c_double),
         ("fd_launches", ctypes.c_int64), ("dft_launches", ctypes.c_int64),
-        ("gram_ms", ctypes.c_double),
+        ("gram_ms", ctypes.c_double), ("fd_steps", ctypes.c_int64),
+        ("fd_kernel", ctypes.c_int32), ("fd_tiles", ctypes.c_int32),
     ]
 
     def as_dict(self):
@@ -100,7 +102,7 @@ _SIGS = {
     "egh_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "egh_version": ([], ctypes.c_int32),
     "egh_release_green": ([_vp], ctypes.c_int),
-    "egh_test_expire_wait": ([_vp, ctypes.c_int32], ctypes.c_int),
+    "egh_test_expire_wait": ([_vp, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
     "egh_server_test_expire_wait": ([_vp, ctypes.c_int32], ctypes.c_int),
     "egh_batch_create": ([ctypes.POINTER(_vp), ctypes.c_int32, ctypes.POINTER(_vp)], ctypes.c_int),
     "egh_batch_factor": ([_vp, _i32p, _i32p, _vp], ctypes.c_int),
@@ -184,7 +186,7 @@ def _i32(a):
 
 # ---- the ABI calls, same names -----------------------------------------------------------
 def egh_create(nz, nx, dz, dx, nsponge, sponge_R, dt, nt, rec_iz, rec_ix, freq_hz,
-               batch_receivers=0, dft_chunk=0, gram_splits=0, fd_rows=0, precision=0):
+               batch_receivers=0, dft_chunk=0, gram_splits=0, fd_rows=0, precision=0, fd_kernel=0):
     lib = load()
     riz, riz_p = _i32(rec_iz)
     rix, rix_p = _i32(rec_ix)
@@ -192,7 +194,7 @@ def egh_create(nz, nx, dz, dx, nsponge, sponge_R, dt, nt, rec_iz, rec_ix, freq_h
     cfg = egh_config(int(nz), int(nx), float(dz), float(dx), int(nsponge), float(sponge_R), float(dt),
                      int(nt), int(riz.size), riz_p, rix_p, int(f.size), f.ctypes.data_as(_f64p),
                      int(batch_receivers), int(dft_chunk), int(gram_splits), int(fd_rows),
-                     int(precision))
+                     int(precision), int(fd_kernel))
     h = _vp()
     _check(lib.egh_create(ctypes.byref(cfg), ctypes.byref(h)), None)
     return h
@@ -284,8 +286,11 @@ def egh_get_stats(ctx):
     return st.as_dict()
 
 
-def egh_test_expire_wait(ctx, count=1):
-    _check(load().egh_test_expire_wait(ctx, int(count)), ctx)
+EXPIRE_GREEN_TRANSFORM, EXPIRE_FD_RESIDENT, EXPIRE_DEBLUR_TRANSFORM = range(3)
+
+
+def egh_test_expire_wait(ctx, kind, count=1):
+    _check(load().egh_test_expire_wait(ctx, int(kind), int(count)), ctx)
 
 
 def _nbytes(buf):
@@ -380,8 +385,8 @@ class Context:
         egh_get_green(self.h, r0, nr, out)
         return out
 
-    def test_expire_wait(self, count=1):
-        egh_test_expire_wait(self.h, count)
+    def test_expire_wait(self, kind, count=1):
+        egh_test_expire_wait(self.h, kind, count)
 
     def release_green(self):
         _check(load().egh_release_green(self.h), self.h)

@@ -40,16 +40,18 @@ def test_exports_every_declared_symbol(lib):
 def test_struct_layout_matches_header(tmp_path):
     src = tmp_path / "layout.c"
     src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "egh.h"\n'
-                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(egh_config),'
+                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(egh_config),'
                    ' offsetof(egh_config, freq_hz), offsetof(egh_config, reserved), sizeof(egh_stats),'
                    ' offsetof(egh_stats, mu), offsetof(egh_stats, gram_splits), offsetof(egh_config, fd_rows),'
-                   ' offsetof(egh_stats, fd_rows), offsetof(egh_stats, gram_ms));return 0;}\n')
+                   ' offsetof(egh_stats, fd_rows), offsetof(egh_stats, gram_ms), offsetof(egh_config, fd_kernel),'
+                   ' offsetof(egh_stats, fd_tiles));return 0;}\n')
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = list(map(int, subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()))
     ref = [ctypes.sizeof(egh.egh_config), egh.egh_config.freq_hz.offset, egh.egh_config.reserved.offset,
            ctypes.sizeof(egh.egh_stats), egh.egh_stats.mu.offset, egh.egh_stats.gram_splits.offset,
-           egh.egh_config.fd_rows.offset, egh.egh_stats.fd_rows.offset, egh.egh_stats.gram_ms.offset]
+           egh.egh_config.fd_rows.offset, egh.egh_stats.fd_rows.offset, egh.egh_stats.gram_ms.offset,
+           egh.egh_config.fd_kernel.offset, egh.egh_stats.fd_tiles.offset]
     assert got == ref
 
 

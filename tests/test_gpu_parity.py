@@ -420,12 +420,14 @@ def test_layered_full_size_sampled():
 
 
 def test_bounded_wait_expiry_is_reported_and_context_recovers():
-    """Failure path of the bounded device waits.  With the test hook, one block of the next
-    transform launch waits on an mbarrier that nothing signals and gives up after about 0.2 ms:
-    the kernel records the context's error flag, lets its copies land, frees its tensor memory
-    and returns (nothing faults or hangs).  The call reports EGH_ETIMEOUT, and the same context
-    then gives the results of a run without the hook, bit for bit: for the Green stage's
-    transform (egh_green) and for the deblur's forward transform (host-buffer egh_deblur)."""
+    """Failure path of the bounded device waits.  With the test hook, the first block of the next
+    launch of one kernel waits on a condition that nothing satisfies and gives up after about
+    0.2 ms: the kernel records the context's error flag, lets its copies land, frees its tensor
+    memory and returns (the resident solver's other blocks see its abort flag and return too);
+    nothing faults or hangs.  The call reports EGH_ETIMEOUT, and the same context then gives the
+    results of a run without the hook, bit for bit: for the Green stage's transform, for the
+    resident FD solver's neighbour wait (egh_green) and for the deblur's forward transform
+    (host-buffer egh_deblur)."""
     torch = _torch()
     from paper_2512_16642_gb300 import egh
 
@@ -433,27 +435,60 @@ def test_bounded_wait_expiry_is_reported_and_context_recovers():
     v = torch.from_numpy(np.float32(c.vel_true)).cuda()
     r32 = np.random.default_rng(4).standard_normal((3, 5, 120)).astype(np.float32)
     with _ctx(c) as ctx:
+        assert ctx.stats()["fd_kernel"] == 1  # the resident solver fits this grid
         ctx.green(v)
         ref_gh = ctx.get_green()
         ctx.hessian()
         ctx.factor()
         ref = np.empty_like(r32)
         ctx.deblur(r32, ref)
-        ctx.test_expire_wait(1)
-        with pytest.raises(egh.EghError) as ei:
+        for kind in (egh.EXPIRE_GREEN_TRANSFORM, egh.EXPIRE_FD_RESIDENT):
+            ctx.test_expire_wait(kind, 1)
+            with pytest.raises(egh.EghError) as ei:
+                ctx.green(v)
+            assert ei.value.status == egh.EGH_ETIMEOUT, kind
+            with pytest.raises(egh.EghError) as ei:  # the failed stage leaves no Hessian to build
+                ctx.hessian()
+            assert ei.value.status == egh.EGH_ESTATE
             ctx.green(v)
-        assert ei.value.status == egh.EGH_ETIMEOUT
-        with pytest.raises(egh.EghError) as ei:  # the failed stage leaves no Hessian to build
-            ctx.hessian()
-        assert ei.value.status == egh.EGH_ESTATE
-        ctx.green(v)
-        assert np.array_equal(ctx.get_green(), ref_gh)
+            assert np.array_equal(ctx.get_green(), ref_gh), kind
         ctx.hessian()
         ctx.factor()
-        ctx.test_expire_wait(1)
+        ctx.test_expire_wait(egh.EXPIRE_DEBLUR_TRANSFORM, 1)
         out = np.empty_like(r32)
         with pytest.raises(egh.EghError) as ei:
             ctx.deblur(r32, out)
         assert ei.value.status == egh.EGH_ETIMEOUT
         ctx.deblur(r32, out)
         assert np.array_equal(out, ref)
+    with _ctx(c, fd_kernel=2) as ctx:  # the hook needs the resident solver
+        with pytest.raises(egh.EghError) as ei:
+            ctx.test_expire_wait(egh.EXPIRE_FD_RESIDENT, 1)
+        assert ei.value.status == egh.EGH_EINVAL
+
+
+@pytest.mark.parametrize("case", ["small", "layered_slice", "ragged"])
+def test_resident_solver_equals_per_step_kernel(case):
+    """The resident FD solver (state in shared memory for a whole transform chunk, one tile per
+    SM, halos exchanged between blocks every step) and the per-step kernel run the same
+    operations in the same order, so their transforms agree bit for bit, across batches of
+    different sizes (8 or 16 receivers per batch against 16), ragged last batches and tiles, and
+    chunk boundaries where the resident solver saves and reloads its state."""
+    torch = _torch()
+    if case == "small":
+        c, kw = synth.case_small(), {}
+    elif case == "layered_slice":
+        c, kw = synth.slice_case(synth.case_layered(), nrec=10, nt=300), {"dft_chunk": 128}
+    else:
+        c, kw = synth.case_tiny(seed=11, nz=13, nx=29, nsponge=5, nrec=7, nt=77), {"dft_chunk": 32}
+    v = torch.from_numpy(np.float32(c.vel_start)).cuda()
+    out = {}
+    for fk in (1, 2):
+        with _ctx(c, fd_kernel=fk, **kw) as ctx:
+            ctx.green(v)
+            out[fk] = ctx.get_green()
+            st = ctx.stats()
+            assert st["fd_kernel"] == fk and st["fd_steps"] > 0
+            if fk == 1:
+                assert st["fd_tiles"] > 1
+    assert np.array_equal(out[1], out[2])
