@@ -68,6 +68,8 @@ def _args():
                         "deblur kernels alone at the layered shape (for profiling captures)")
     p.add_argument("--precision", choices=["mixed", "fp32"], default="mixed",
                    help="Hessian arithmetic: bf16x3 tensor-core Gram (mixed) or FP32 CUDA-core Gram")
+    p.add_argument("--fd-kernel", type=int, choices=[0, 1, 2], default=0,
+                   help="FD solver: 0 library choice, 1 resident, 2 one kernel per step")
     p.add_argument("--dft-chunk", type=int, default=1024,
                    help="levels per transform chunk (0 = library default 512; 1024 halves the "
                         "transform's accumulator traffic of 512 for a 46 GB snapshot ring)")
@@ -512,7 +514,7 @@ def run_ours(args):
         args.e2e_steps, args.no_cpu_baseline = 0, True
     nr, ns, nt, nf = c.rec_ix.size, c.src_ix.size, c.nt, c.freqs.size
     ctx = egh.Context(c.nz, c.nx, c.dz, c.dx, c.nsponge, c.sponge_R, c.dt, c.nt, c.rec_iz, c.rec_ix, c.freqs,
-                      dft_chunk=args.dft_chunk,
+                      dft_chunk=args.dft_chunk, fd_kernel=args.fd_kernel,
                       precision=egh.EGH_PREC_MIXED if args.precision == "mixed" else egh.EGH_PREC_FP32)
     stream = torch.cuda.current_stream()
     v_start = torch.from_numpy(np.float32(c.vel_start)).cuda()
@@ -660,7 +662,7 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32/bf16x3" if args.precision == "mixed" else "f32/bf16x3-transform",
         "data": "synthetic",
         "config": _workload(c, {"batch_receivers": st["batch_receivers"], "dft_chunk": st["dft_chunk"],
-                                "gram_splits": st["gram_splits"], "fd_rows": st["fd_rows"],
+                                "gram_splits": st["gram_splits"], "fd_rows": st["fd_rows"], "fd_kernel": st["fd_kernel"],
                                 "precision": args.precision,
                                 "residuals": "forward modelling (true - start)" if args.resid == "model"
                                 else "seeded band-limited noise 2-10 Hz"}),

@@ -517,7 +517,7 @@ egh_status egh_create(const egh_config* cfg, egh_ctx** out) {
   ALLOC(ctx->lev, (size_t)3 * ((ctx->B + 1) / 2) * F * sizeof(float2), "FD state");
   if (ctx->fd_kernel == 1) {
     ALLOC(ctx->xbuf, fd_resident_xbuf_float4(ctx->rg) * sizeof(float4), "FD halo exchange");
-    ALLOC(ctx->rflags, sizeof(int) * (ctx->rg.TR * ctx->rg.TC + 1), "FD step counters");
+    ALLOC(ctx->rflags, sizeof(int) * fd_resident_flags(ctx->rg), "FD step counters");
   }
   std::vector<unsigned char> twt = dft_twiddle_tiles(ctx->freqs, c.dt, c.nt);
   ALLOC(ctx->twt, twt.size(), "twiddle tiles");

@@ -96,6 +96,7 @@ struct ResGeom {
 // then the smallest tile; false if not even one pair fits.
 bool fd_resident_plan(const Layout& L, int want_pairs, ResGeom* g);
 size_t fd_resident_xbuf_float4(const ResGeom& g);  // halo exchange buffer (float4)
+size_t fd_resident_flags(const ResGeom& g);        // step counters + abort flag (ints)
 int fd_resident_sr_default();                         // rows per z-march segment
 bool fd_resident_sr_valid(int sr);                    // 6, 8, 11 or 16
 // shared-memory limit of every instance, and a check that the grid is co-resident (sr, np:
@@ -104,7 +105,7 @@ cudaError_t fd_resident_prepare(const ResGeom& g, int sr, int np);
 // Levels ta .. ta+nsteps-1 of np pairs (ta >= 2), from the state slots of levels ta-1, ta-2 of
 // lev ([3][pslot][F]) to the slots of the last two levels; level t's bf16 hi/lo snapshot goes to
 // ring slot sbase + (t - t0) / decim when t % decim == 0 (snap: hi plane of ring slot 0, or
-// null).  flags: tiles + 1 ints (zeroed here).  Cooperative launch.
+// null).  flags: fd_resident_flags(g) ints (zeroed here).  Cooperative launch.
 cudaError_t launch_fd_resident(const ResGeom& g, int sr, float2* lev, int pslot, const Layout& L,
                                const float2* coef, const Stencil& S, int np, int ta, int nsteps,
                                int t0, int decim, int sbase, __nv_bfloat16* snap, long long sslot,

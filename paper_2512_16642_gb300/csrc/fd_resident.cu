@@ -12,11 +12,12 @@
 // halo.  The eighth-order Laplacian is a cross, so corners are never exchanged.  Only the
 // snapshots the transform reads, and the state at the chunk's ends, reach DRAM.
 //
-// Work inside a block: a unit is (receiver pair, 4 adjacent columns, a segment of SR rows); its
-// thread marches down the segment with the z first differences in registers, as fd.cu does, and
-// reads the x neighbours from shared memory.  Rows of shared memory are stored as two planes of
-// float4 (even and odd float4 slots) so that the threads of one quarter-warp, which take adjacent
-// column quads, read adjacent 16-byte words.
+// Work inside a block: the batch's pairs are split into NG groups; each group is a set of warps
+// with its own named barrier and its own step counters, so that while one group waits for its
+// neighbours' strips the other computes.  A unit is (receiver pair, 2 adjacent columns, a segment
+// of SR rows): its thread marches down the segment with the z first differences in registers, as
+// fd.cu does, and reads the x neighbours from shared memory (one float4 = both receivers of the
+// pair at 2 points, adjacent threads on adjacent words).
 //
 // Every wait on another block is bounded: on expiry the block records the error flag and an
 // abort flag that every other block's wait also watches, so the whole grid returns.
@@ -32,7 +33,11 @@ namespace egh {
 
 namespace {
 
-constexpr int RES_MAXT = 384;  // threads per block at most (a thread takes several units beyond)
+constexpr int RES_MAXT = 640;  // threads per block at most
+// threads per block at most for SR rows per segment: short segments (more units) take more
+// threads at fewer registers; long segments keep their window in registers at fewer threads
+__host__ __device__ constexpr int res_maxt(int sr) { return sr <= 8 ? 640 : 448; }
+constexpr int RES_E = 4;  // exchange elements of a pair per thread at most
 
 __device__ __forceinline__ float2 rsub2(float2 a, float2 b) {
   return __ffma2_rn(b, make_float2(-1.f, -1.f), a);  // a - b, one rounding
@@ -75,6 +80,21 @@ __device__ __forceinline__ int ld_relaxed(const int* p) {
   asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
+// named barrier `id` over `n` threads (whole warps)
+__device__ __forceinline__ void gbar(int id, int n) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+// the same with an OR of a predicate over the participating threads
+__device__ __forceinline__ bool gbar_or(int id, int n, bool pred) {
+  unsigned r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, %2, %3, p;\n"
+      " selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((unsigned)pred), "r"(id), "r"(n)
+      : "memory");
+  return r != 0;
+}
 
 struct ResArgs {
   float2* lev;        // [3][pslot][F] state slots (level t in slot t mod 3)
@@ -89,22 +109,23 @@ struct ResArgs {
   __nv_bfloat16* snap;   // ring base (hi plane of slot 0), or null for no snapshots
   long long sslot, splane, srec;  // elements per ring slot, hi -> lo plane, per receiver
   float4* xbuf;       // [2][tiles][P][SB] exchange strips
-  int* flags;         // [tiles] steps completed in this launch (zeroed before the launch)
-  int* abort_flag;    // set by a block whose wait ran out (zeroed before the launch)
+  int* flags;         // [NG][tiles] steps completed in this launch, then the abort flag (zeroed
+                      // before the launch)
   int* err;           // the context's error flag
   int expire;         // test hook: block 0's first wait runs out
+  int GT;             // threads per group (whole warps)
   Stencil C;          // cumulative weights C_j
 };
 
 template <int SR>
-__global__ void __launch_bounds__(RES_MAXT, 1) k_fd_resident(const ResArgs a, const ResGeom g) {
+__global__ void __launch_bounds__(res_maxt(SR), 1) k_fd_resident(const ResArgs a, const ResGeom g) {
   extern __shared__ __align__(16) float4 rsm[];
   const int tid = threadIdx.x, nthr = blockDim.x;
-  const int TZ = g.TZ, TX = g.TX, TXH = TX / 2, TXQ = TX / 4;
-  const int RS = TXH + 4, RS2 = RS / 2;  // float4 slots per row (2 halo slots each side), per plane
+  const int TZ = g.TZ, TX = g.TX, TXH = TX / 2;
+  const int RS = TXH + 4;                // float4 slots per row (2 halo slots each side)
   const int LV = (TZ + 8) * RS;          // float4 per (level, pair)
   float4* lv = rsm;                      // [2][P][LV]
-  float4* cf = rsm + 2 * g.P * LV;       // [TZ][TXH], two planes per row
+  float4* cf = rsm + 2 * g.P * LV;       // [TZ][TXH]
   const int tile = blockIdx.x, ntiles = g.TR * g.TC;
   const int trow = tile / g.TC, tcol = tile % g.TC;
   const int z0 = trow * TZ, x0 = tcol * TX;
@@ -112,22 +133,22 @@ __global__ void __launch_bounds__(RES_MAXT, 1) k_fd_resident(const ResArgs a, co
   const bool has[4] = {trow > 0, trow + 1 < g.TR, tcol > 0, tcol + 1 < g.TC};
   const int nbr[4] = {tile - g.TC, tile + g.TC, tile - 1, tile + 1};
   const int np = a.np;
-  auto sidx = [&](int r, int j) { return (r + 4) * RS + (j & 1) * RS2 + (j >> 1); };
   auto lvl = [&](int b, int p) { return lv + (size_t)(b * g.P + p) * LV; };
+  auto sidx = [&](int r, int j) { return (r + 4) * RS + j; };
 
-  // ---- load both levels (interior and halo) and the coefficients
+  // ---- load both levels (interior and halo) and the coefficients (whole block)
   const int s_cur = (a.ta - 1) % 3, s_prev = (a.ta - 2 + 3) % 3;
   for (int b = 0; b < 2; ++b) {
     const int s = b == 0 ? s_cur : s_prev;
-    const long long sbase = (long long)s * a.pslot * a.F;
+    const long long sb = (long long)s * a.pslot * a.F;
     for (int e = tid; e < np * LV; e += nthr) {
       const int p = e / LV, k = e % LV, r = k / RS - 4, j = k % RS;
       const int z = z0 + r, x = x0 + 2 * j - 4;
       float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
       if (z >= 0 && z < a.NZ && x >= 0 && x < a.NX)
-        v = __ldcg(reinterpret_cast<const float4*>(a.lev + sbase + (long long)p * a.F + a.org +
+        v = __ldcg(reinterpret_cast<const float4*>(a.lev + sb + (long long)p * a.F + a.org +
                                                    (long long)z * a.PX + x));
-      lvl(b, p)[sidx(r, j)] = v;
+      lvl(b, p)[k] = v;
     }
   }
   for (int e = tid; e < TZ * TXH; e += nthr) {
@@ -135,9 +156,58 @@ __global__ void __launch_bounds__(RES_MAXT, 1) k_fd_resident(const ResArgs a, co
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
     if (z < a.NZ && x < a.NX)
       v = __ldg(reinterpret_cast<const float4*>(a.coef + a.org + (long long)z * a.PX + x));
-    cf[r * TXH + (j & 1) * TXQ + (j >> 1)] = v;
+    cf[e] = v;
   }
   __syncthreads();
+
+  // ---- this thread's group: pairs [p0, p1), local thread lt of GT, barrier id 1 + gi
+  const int GT = a.GT, gi = tid / GT, lt = tid % GT;
+  const int NG = nthr / GT, PG = (g.P + NG - 1) / NG;
+  const int p0 = min(np, gi * PG), p1 = min(np, p0 + PG);
+  const int bid = 1 + gi;
+  int* gflags = a.flags + gi * ntiles;
+  int* abort_flag = a.flags + NG * ntiles;
+  // strip elements k = lt + i GT (i < RES_E) of a pair's SB-float4 exchange block: N = rows 0..3,
+  // S = rows TZ-4..TZ-1 (4 x TXH each), W = columns 0..3, E = columns TX-4..TX-1 (TZ x 2 each).
+  // Publishing copies the new level's boundary element to the block; filling copies the matching
+  // neighbour element into the halo.  Packed: pub slot | halo slot << 16, and neighbour offset |
+  // side << 16 | valid << 18.
+  const int nN = 4 * TXH, nW = 2 * TZ, SB = 2 * nN + 2 * nW;
+  int ent_s[RES_E], ent_n[RES_E];
+#pragma unroll
+  for (int i = 0; i < RES_E; ++i) {
+    const int k = lt + i * GT;
+    int pub = 0, halo = 0, src = 0, side = 0, valid = 0;
+    if (k < SB) {
+      if (k < nN) {  // N: rows 0..3 <-> the upper tile fills my rows -4..-1 from its S
+        side = 0;
+        pub = sidx(k / TXH, 2 + k % TXH);
+        halo = sidx(-4 + k / TXH, 2 + k % TXH);
+        src = nN + k;
+      } else if (k < 2 * nN) {  // S: rows TZ-4..TZ-1 <-> my rows TZ..TZ+3 from the lower N
+        const int kk = k - nN;
+        side = 1;
+        pub = sidx(TZ - 4 + kk / TXH, 2 + kk % TXH);
+        halo = sidx(TZ + kk / TXH, 2 + kk % TXH);
+        src = kk;
+      } else if (k < 2 * nN + nW) {  // W: columns 0..3 <-> my columns -4..-1 from the left E
+        const int kk = k - 2 * nN;
+        side = 2;
+        pub = sidx(kk >> 1, 2 + (kk & 1));
+        halo = sidx(kk >> 1, kk & 1);
+        src = k + nW;
+      } else {  // E: columns TX-4..TX-1 <-> my columns TX..TX+3 from the right W
+        const int kk = k - 2 * nN - nW;
+        side = 3;
+        pub = sidx(kk >> 1, RS - 4 + (kk & 1));
+        halo = sidx(kk >> 1, RS - 2 + (kk & 1));
+        src = k - nW;
+      }
+      valid = has[side] ? 1 : 0;
+    }
+    ent_s[i] = pub | (halo << 16);
+    ent_n[i] = src | (side << 16) | (valid << 18);
+  }
 
   float2 cz2[4], cx2[4];
 #pragma unroll
@@ -146,37 +216,34 @@ __global__ void __launch_bounds__(RES_MAXT, 1) k_fd_resident(const ResArgs a, co
     cx2[j] = make_float2(a.C.cx[j], a.C.cx[j]);
   }
   const int nseg = (TZ + SR - 1) / SR;
-  const int nunits = np * TXQ * nseg;
-  const int nN = 4 * TXH, nW = 2 * TZ, SB = 2 * nN + 2 * nW;
+  const int nunits = (p1 - p0) * TXH * nseg;
   bool failed = false;
-  int it = 0;
-  for (; it < a.nsteps; ++it) {
+  for (int it = 0; it < a.nsteps; ++it) {
     const int t = a.ta + it;
     const int bc = it & 1, bn = bc ^ 1;  // current level, previous level (overwritten by the new)
     __nv_bfloat16* sl = nullptr;
     if (a.snap && t % a.decim == 0) sl = a.snap + (long long)(a.sbase + (t - a.t0) / a.decim) * a.sslot;
-    for (int u = tid; u < nunits; u += nthr) {
-      const int q = u % TXQ, seg = (u / TXQ) % nseg, p = u / (TXQ * nseg);
-      const float4* cu = lvl(bc, p);
-      float4* pv = lvl(bn, p);
+    for (int u = lt; u < nunits; u += GT) {
+      const int q = u % TXH, seg = (u / TXH) % nseg, p = p0 + u / (TXH * nseg);
+      const float4* cu = lvl(bc, p) + q;  // slot q + 2 is this unit's centre
+      float4* pv = lvl(bn, p) + q + 2;
+      const float4* cq = cf + q;
       const int r0 = seg * SR;
-      const int xq = x0 + 4 * q;  // padded column of the unit's first point
-      // z first differences at the unit's 4 points: dz[i][m] = u(z-3+m) - u(z-4+m) for row z
-      float2 dz[4][8], ul[4];
+      const int x = x0 + 2 * q;  // padded column of the unit's first point
+      const bool ok0 = x < a.NX, ok1 = x + 1 < a.NX;
+      // z first differences: dz[pt][m] = u(z-3+m) - u(z-4+m) at the current row z
+      float2 dz[2][8], ul[2];
       {
-        const float4 v0 = cu[sidx(r0 - 4, 2 * q + 2)], v1 = cu[sidx(r0 - 4, 2 * q + 3)];
-        ul[0] = make_float2(v0.x, v0.y);
-        ul[1] = make_float2(v0.z, v0.w);
-        ul[2] = make_float2(v1.x, v1.y);
-        ul[3] = make_float2(v1.z, v1.w);
+        const float4 v = cu[sidx(r0 - 4, 2)];
+        ul[0] = make_float2(v.x, v.y);
+        ul[1] = make_float2(v.z, v.w);
       }
 #pragma unroll
       for (int k = 1; k < 8; ++k) {
-        const float4 v0 = cu[sidx(r0 - 4 + k, 2 * q + 2)], v1 = cu[sidx(r0 - 4 + k, 2 * q + 3)];
-        const float2 nv[4] = {make_float2(v0.x, v0.y), make_float2(v0.z, v0.w),
-                              make_float2(v1.x, v1.y), make_float2(v1.z, v1.w)};
+        const float4 v = cu[sidx(r0 - 4 + k, 2)];
+        const float2 nv[2] = {make_float2(v.x, v.y), make_float2(v.z, v.w)};
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < 2; ++i) {
           dz[i][k] = rsub2(nv[i], ul[i]);
           ul[i] = nv[i];
         }
@@ -186,107 +253,78 @@ __global__ void __launch_bounds__(RES_MAXT, 1) k_fd_resident(const ResArgs a, co
         const int r = r0 + ii;
         if (r >= TZ) break;
         {
-          const float4 v0 = cu[sidx(r + 4, 2 * q + 2)], v1 = cu[sidx(r + 4, 2 * q + 3)];
-          const float2 nv[4] = {make_float2(v0.x, v0.y), make_float2(v0.z, v0.w),
-                                make_float2(v1.x, v1.y), make_float2(v1.z, v1.w)};
+          const float4 v = cu[sidx(r + 4, 2)];
+          const float2 nv[2] = {make_float2(v.x, v.y), make_float2(v.z, v.w)};
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
+          for (int i = 0; i < 2; ++i) {
 #pragma unroll
             for (int m = 0; m < 7; ++m) dz[i][m] = dz[i][m + 1];
             dz[i][7] = rsub2(nv[i], ul[i]);
             ul[i] = nv[i];
           }
         }
-        // u^n at row r, points 4q - 4 .. 4q + 7 (both receivers of the pair)
-        float2 w[12];
+        // u^n at row r, points x - 4 .. x + 5 (both receivers of the pair)
+        const float4* xr = cu + sidx(r, 0);
+        const float4 A0 = xr[0], A1 = xr[1], A2 = xr[2], A3 = xr[3], A4 = xr[4];
+        const float2 w[10] = {make_float2(A0.x, A0.y), make_float2(A0.z, A0.w), make_float2(A1.x, A1.y),
+                              make_float2(A1.z, A1.w), make_float2(A2.x, A2.y), make_float2(A2.z, A2.w),
+                              make_float2(A3.x, A3.y), make_float2(A3.z, A3.w), make_float2(A4.x, A4.y),
+                              make_float2(A4.z, A4.w)};
+        float2 e[9];
 #pragma unroll
-        for (int s = 0; s < 6; ++s) {
-          const float4 A = cu[sidx(r, 2 * q + s)];
-          w[2 * s] = make_float2(A.x, A.y);
-          w[2 * s + 1] = make_float2(A.z, A.w);
-        }
-        float2 e[11];
-#pragma unroll
-        for (int m = 0; m < 11; ++m) e[m] = rsub2(w[m + 1], w[m]);
-        const float4 o01 = pv[sidx(r, 2 * q + 2)], o23 = pv[sidx(r, 2 * q + 3)];
-        const float4 c01 = cf[r * TXH + q], c23 = cf[r * TXH + TXQ + q];
-        const float2 o[4] = {make_float2(o01.x, o01.y), make_float2(o01.z, o01.w),
-                             make_float2(o23.x, o23.y), make_float2(o23.z, o23.w)};
-        const float2 c1[4] = {make_float2(c01.x, c01.x), make_float2(c01.z, c01.z),
-                              make_float2(c23.x, c23.x), make_float2(c23.z, c23.z)};
-        const float2 c3[4] = {make_float2(c01.y, c01.y), make_float2(c01.w, c01.w),
-                              make_float2(c23.y, c23.y), make_float2(c23.w, c23.w)};
-        float2 v[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const float2 l = rlap2(dz[i], e + i, cz2, cx2);
-          // u^{n+1} = c3 L u + c1 (u - u^{n-1}) + u^{n-1}
-          v[i] = __ffma2_rn(c3[i], l, __ffma2_rn(c1[i], rsub2(w[i + 4], o[i]), o[i]));
-          if (xq + i >= a.NX) v[i] = make_float2(0.f, 0.f);
-        }
-        if (r < VR && xq < a.NX) {
-          pv[sidx(r, 2 * q + 2)] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
-          pv[sidx(r, 2 * q + 3)] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
+        for (int m = 0; m < 9; ++m) e[m] = rsub2(w[m + 1], w[m]);
+        const float4 uo = pv[sidx(r, 0)], cc = cq[r * TXH];
+        const float2 l0 = rlap2(dz[0], e, cz2, cx2), l1 = rlap2(dz[1], e + 1, cz2, cx2);
+        // u^{n+1} = c3 L u + c1 (u - u^{n-1}) + u^{n-1}
+        const float2 o0 = make_float2(uo.x, uo.y), o1 = make_float2(uo.z, uo.w);
+        const float2 v0 = __ffma2_rn(make_float2(cc.y, cc.y), l0,
+                                     __ffma2_rn(make_float2(cc.x, cc.x), rsub2(w[4], o0), o0));
+        float2 v1 = __ffma2_rn(make_float2(cc.w, cc.w), l1,
+                               __ffma2_rn(make_float2(cc.z, cc.z), rsub2(w[5], o1), o1));
+        if (!ok1) v1 = make_float2(0.f, 0.f);
+        if (r < VR && ok0) {
+          pv[sidx(r, 0)] = make_float4(v0.x, v0.y, v1.x, v1.y);
           if (sl) {
-            unsigned ha0, la0, ha1, la1, hb0, lb0, hb1, lb1;
-            rsplit(v[0].x, v[1].x, ha0, la0);
-            rsplit(v[2].x, v[3].x, ha1, la1);
-            rsplit(v[0].y, v[1].y, hb0, lb0);
-            rsplit(v[2].y, v[3].y, hb1, lb1);
-            __nv_bfloat16* sp = sl + (long long)(2 * p) * a.srec + (long long)(z0 + r) * a.PX + xq;
-            __stcs(reinterpret_cast<uint2*>(sp), make_uint2(ha0, ha1));
-            __stcs(reinterpret_cast<uint2*>(sp + a.splane), make_uint2(la0, la1));
-            __stcs(reinterpret_cast<uint2*>(sp + a.srec), make_uint2(hb0, hb1));
-            __stcs(reinterpret_cast<uint2*>(sp + a.srec + a.splane), make_uint2(lb0, lb1));
+            unsigned ha, la, hb, lb;
+            rsplit(v0.x, v1.x, ha, la);
+            rsplit(v0.y, v1.y, hb, lb);
+            __nv_bfloat16* sp = sl + (long long)(2 * p) * a.srec + (long long)(z0 + r) * a.PX + x;
+            __stcs(reinterpret_cast<unsigned*>(sp), ha);
+            __stcs(reinterpret_cast<unsigned*>(sp + a.splane), la);
+            __stcs(reinterpret_cast<unsigned*>(sp + a.srec), hb);
+            __stcs(reinterpret_cast<unsigned*>(sp + a.srec + a.splane), lb);
           }
         }
       }
     }
-    __syncthreads();  // the new level is complete in shared memory
-    // ---- publish the new level's boundary strips, then this block's step count
+    gbar(bid, GT);  // the group's new level is complete in shared memory
+    // ---- publish the new level's boundary strips, then the group's step count
     float4* xme = a.xbuf + ((size_t)(it & 1) * ntiles + tile) * g.P * SB;
-    for (int e = tid; e < np * SB; e += nthr) {
-      const int p = e / SB, k = e % SB;
-      int r, j;
-      if (k < nN) {
-        if (!has[0]) continue;
-        r = k / TXH;
-        j = 2 + k % TXH;
-      } else if (k < 2 * nN) {
-        if (!has[1]) continue;
-        r = TZ - 4 + (k - nN) / TXH;
-        j = 2 + (k - nN) % TXH;
-      } else if (k < 2 * nN + nW) {
-        if (!has[2]) continue;
-        r = (k - 2 * nN) >> 1;
-        j = 2 + ((k - 2 * nN) & 1);
-      } else {
-        if (!has[3]) continue;
-        r = (k - 2 * nN - nW) >> 1;
-        j = RS - 4 + ((k - 2 * nN - nW) & 1);
-      }
-      __stcg(xme + (size_t)p * SB + k, lvl(bn, p)[sidx(r, j)]);
-    }
-    __syncthreads();
-    if (tid == 0) {
+#pragma unroll
+    for (int i = 0; i < RES_E; ++i)
+      if ((ent_n[i] >> 18) & 1)
+        for (int p = p0; p < p1; ++p)
+          __stcg(xme + (size_t)p * SB + lt + i * GT, lvl(bn, p)[ent_s[i] & 0xffff]);
+    gbar(bid, GT);
+    if (lt == 0) {
       __threadfence();
-      st_release(a.flags + tile, it + 1);
+      st_release(gflags + tile, it + 1);
     }
     // ---- wait for the neighbours' strips of this step (bounded; an abort ends every wait)
     bool ok = true;
-    if (tid < 4 && has[tid]) {
-      const int* f = a.flags + nbr[tid];
+    if (lt < 4 && has[lt] && p1 > p0) {
+      const int* f = gflags + nbr[lt];
       const unsigned long long tw0 = tc::globaltimer_ns();
       long long polls = 0;
       while (ld_acquire(f) < it + 1) {
-        if (ld_relaxed(a.abort_flag)) {
+        if (ld_relaxed(abort_flag)) {
           ok = false;
           break;
         }
         if ((++polls & 15) == 0 && tc::globaltimer_ns() - tw0 > tc::kWaitNs) {
           ok = false;
           atomicExch(a.err, 1);
-          atomicExch(a.abort_flag, 1);
+          atomicExch(abort_flag, 1);
           break;
         }
       }
@@ -294,75 +332,59 @@ __global__ void __launch_bounds__(RES_MAXT, 1) k_fd_resident(const ResArgs a, co
     if (it == 0 && a.expire && tile == 0 && tid == 0) {
       // test hook: wait for a step count that no block ever publishes, for a short time
       const unsigned long long tw0 = tc::globaltimer_ns();
-      while (ld_acquire(a.flags + tile) < INT_MAX) {
+      while (ld_acquire(gflags + tile) < INT_MAX) {
         if (tc::globaltimer_ns() - tw0 > tc::kExpireNs) {
           ok = false;
           atomicExch(a.err, 1);
-          atomicExch(a.abort_flag, 1);
+          atomicExch(abort_flag, 1);
           break;
         }
       }
     }
-    if (__syncthreads_or(!ok)) {
+    if (gbar_or(bid, GT, !ok)) {
       failed = true;
       break;
     }
     if (it + 1 == a.nsteps) break;  // the last level needs no halo
     // ---- the neighbours' strips into the new level's halo
     const float4* xb = a.xbuf + (size_t)(it & 1) * ntiles * g.P * SB;
-    for (int e = tid; e < np * SB; e += nthr) {
-      const int p = e / SB, k = e % SB;
-      int r, j;
-      const float4* src;
-      if (k < nN) {  // rows -4 .. -1 <- the upper tile's last four rows
-        if (!has[0]) continue;
-        r = -4 + k / TXH;
-        j = 2 + k % TXH;
-        src = xb + ((size_t)nbr[0] * g.P + p) * SB + nN + k;
-      } else if (k < 2 * nN) {  // rows TZ .. TZ + 3 <- the lower tile's first four rows
-        if (!has[1]) continue;
-        const int kk = k - nN;
-        r = TZ + kk / TXH;
-        j = 2 + kk % TXH;
-        src = xb + ((size_t)nbr[1] * g.P + p) * SB + kk;
-      } else if (k < 2 * nN + nW) {  // columns -4 .. -1 <- the left tile's last four columns
-        if (!has[2]) continue;
-        const int kk = k - 2 * nN;
-        r = kk >> 1;
-        j = kk & 1;
-        src = xb + ((size_t)nbr[2] * g.P + p) * SB + 2 * nN + nW + kk;
-      } else {  // columns TX .. TX + 3 <- the right tile's first four columns
-        if (!has[3]) continue;
-        const int kk = k - 2 * nN - nW;
-        r = kk >> 1;
-        j = RS - 2 + (kk & 1);
-        src = xb + ((size_t)nbr[3] * g.P + p) * SB + 2 * nN + kk;
+#pragma unroll
+    for (int i = 0; i < RES_E; ++i)
+      if ((ent_n[i] >> 18) & 1) {
+        const float4* src = xb + (size_t)nbr[(ent_n[i] >> 16) & 3] * g.P * SB + (ent_n[i] & 0xffff);
+        for (int p = p0; p < p1; ++p) lvl(bn, p)[ent_s[i] >> 16] = __ldcg(src + (size_t)p * SB);
       }
-      lvl(bn, p)[sidx(r, j)] = __ldcg(src);
-    }
-    __syncthreads();
+    gbar(bid, GT);
   }
-  if (failed) return;
+  // every group has left its loop (a failed group may leave early; the others then see its abort)
+  if (__syncthreads_or(failed)) return;
   // ---- the last two levels back to their state slots (valid interior points)
   const int t1 = a.ta + a.nsteps;
   for (int b = 0; b < 2; ++b) {
     const int buf = b == 0 ? (a.nsteps & 1) : ((a.nsteps + 1) & 1);
     const int s = b == 0 ? (t1 - 1) % 3 : (t1 - 2) % 3;
-    const long long sbase = (long long)s * a.pslot * a.F;
+    const long long sb = (long long)s * a.pslot * a.F;
     for (int e = tid; e < np * VR * TXH; e += nthr) {
       const int p = e / (VR * TXH), k = e % (VR * TXH), r = k / TXH, j = 2 + k % TXH;
       const int z = z0 + r, x = x0 + 2 * j - 4;
       if (x < a.NX)
-        __stcg(reinterpret_cast<float4*>(a.lev + sbase + (long long)p * a.F + a.org +
+        __stcg(reinterpret_cast<float4*>(a.lev + sb + (long long)p * a.F + a.org +
                                          (long long)z * a.PX + x),
                lvl(buf, p)[sidx(r, j)]);
     }
   }
 }
 
-int res_threads(const ResGeom& g, int sr, int np) {
-  const int units = np * (g.TX / 4) * ((g.TZ + sr - 1) / sr);
-  return std::max(32, std::min(RES_MAXT, (units + 31) / 32 * 32));
+// Pair groups per block (two when there are two pairs or more, so that one group computes while
+// the other exchanges) and threads per group: one per unit, enough that no thread handles more
+// than RES_E exchange elements of a pair, whole warps.
+int res_groups(const ResGeom& g) { return g.P >= 2 ? 2 : 1; }
+int res_group_threads(const ResGeom& g, int sr) {
+  const int NG = res_groups(g), PG = (g.P + NG - 1) / NG;
+  const int units = PG * (g.TX / 2) * ((g.TZ + sr - 1) / sr);
+  const int SB = 8 * (g.TX / 2) + 4 * g.TZ;
+  const int gt = std::max((units + 31) / 32, (SB + 32 * RES_E - 1) / (32 * RES_E)) * 32;
+  return std::min(gt, res_maxt(sr) / NG / 32 * 32);
 }
 
 }  // namespace
@@ -388,6 +410,8 @@ bool fd_resident_plan(const Layout& L, int want_pairs, ResGeom* out) {
     const int TX = ((L.NX + tcmax - 1) / tcmax + 3) / 4 * 4;
     const int TC = (L.NX + TX - 1) / TX;
     if (TR * TC > sms || TZ < 4 || TX < 4) continue;
+    // no thread of a group takes more than RES_E exchange elements of a pair
+    if (8 * (TX / 2) + 4 * TZ > RES_E * (res_maxt(16) / 2 / 32 * 32)) continue;
     int P = std::min(want_pairs, 8);
     while (P >= 1 && res_smem(TZ, TX, P) > (size_t)optin) --P;
     if (P < 1) continue;
@@ -402,6 +426,8 @@ bool fd_resident_plan(const Layout& L, int want_pairs, ResGeom* out) {
   *out = best;
   return true;
 }
+
+size_t fd_resident_flags(const ResGeom& g) { return (size_t)res_groups(g) * g.TR * g.TC + 1; }
 
 size_t fd_resident_xbuf_float4(const ResGeom& g) {
   return (size_t)2 * g.TR * g.TC * g.P * (8 * (g.TX / 2) + 4 * g.TZ);
@@ -432,7 +458,8 @@ cudaError_t fd_resident_prepare(const ResGeom& g, int sr, int np) {
   int dev = 0, sms = 0, occ = 0;
   if ((e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)))
     return e;
-  const int thr = res_threads(g, sr, np);
+  const int thr = res_groups(g) * res_group_threads(g, sr);
+  (void)np;
   switch (sr) {
     case 6: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fd_resident<6>, thr, g.smem); break;
     case 8: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fd_resident<8>, thr, g.smem); break;
@@ -473,9 +500,9 @@ cudaError_t launch_fd_resident(const ResGeom& g, int sr, float2* lev, int pslot,
   a.srec = srec;
   a.xbuf = xbuf;
   a.flags = flags;
-  a.abort_flag = flags + g.TR * g.TC;
   a.err = err;
   a.expire = expire;
+  a.GT = res_group_threads(g, sr);
   // cumulative weights C_j = sum_{k>=j} c_k of the first-difference form (as fd.cu)
   float az = 0.f, ax = 0.f;
   for (int k = 3; k >= 0; --k) {
@@ -484,11 +511,12 @@ cudaError_t launch_fd_resident(const ResGeom& g, int sr, float2* lev, int pslot,
     a.C.cz[k] = az;
     a.C.cx[k] = ax;
   }
-  cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(int) * (g.TR * g.TC + 1), st);
+  cudaError_t e =
+      cudaMemsetAsync(flags, 0, sizeof(int) * ((size_t)res_groups(g) * g.TR * g.TC + 1), st);
   if (e != cudaSuccess) return e;
   ResGeom gg = g;
   void* args[] = {&a, &gg};
-  const dim3 grid(g.TR * g.TC), block(res_threads(g, sr, np));
+  const dim3 grid(g.TR * g.TC), block(res_groups(g) * a.GT);
   count_launches(1);
   switch (sr) {
     case 6: return cudaLaunchCooperativeKernel((void*)k_fd_resident<6>, grid, block, args, g.smem, st);
