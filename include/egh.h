@@ -119,15 +119,15 @@ typedef struct {
                                 egh_green of the context: the smallest count whose tiles fit one
                                 wave of resident blocks is kept unless another is 3% faster */
     int32_t precision;       /* egh_precision of the Hessian stage (0 = EGH_PREC_FP32) */
-    int32_t fd_kernel;       /* FD solver of the Green stage: 0 = library choice (the resident
-                                solver whenever the state of at least one receiver pair fits a
-                                block's shared memory, else the per-step kernel); 1 = resident:
-                                the batch's wavefield stays in shared memory for a whole transform
-                                chunk, one block per SM (EGH_EINVAL if it does not fit); 2 = one
-                                kernel per time step, state in global memory.  Both give identical
-                                levels.  With the resident solver, batch_receivers = 0 takes the
-                                most receivers whose state fits (at most 16), and fd_rows does not
-                                apply (its rows per segment are timed on the first egh_green) */
+    int32_t fd_kernel;       /* FD solver of the Green stage: 0 or 2 = one kernel per time step,
+                                state in global memory (L2-resident), the faster one on a GB300;
+                                1 = resident: the batch's wavefield stays in shared memory for a
+                                whole transform chunk, one block per SM in a cooperative launch,
+                                halos exchanged between neighbouring blocks every step (EGH_EINVAL
+                                if it does not fit).  Both give identical levels.  With the
+                                resident solver, batch_receivers = 0 takes the most receivers whose
+                                state fits (at most 16) and fd_rows does not apply (its rows per
+                                segment are timed on the first egh_green) */
     int32_t reserved[2];     /* must be zero */
 } egh_config;
 

@@ -455,11 +455,12 @@ egh_status egh_create(const egh_config* cfg, egh_ctx** out) {
   L.org = (long long)GUARD * L.PX;
   L.G = round_up((long long)L.NZ * L.PX, 256);
 
-  // FD solver: resident when the state of the batch's pairs fits a block's shared memory
+  // FD solver: the per-step kernel, or on request the resident solver when the state of the
+  // batch's pairs fits a block's shared memory
   {
     const int want = c.batch_receivers ? c.batch_receivers : 16;
     bool res = false;
-    if (c.fd_kernel != 2) {
+    if (c.fd_kernel == 1) {
       res = fd_resident_plan(L, (want + 1) / 2, &ctx->rg) &&
             !(c.batch_receivers && (c.batch_receivers + 1) / 2 > ctx->rg.P);
       if (res) {

@@ -434,7 +434,7 @@ def test_bounded_wait_expiry_is_reported_and_context_recovers():
     c = synth.case_tiny(seed=3, nz=24, nx=40, nsponge=6, nrec=5, nt=120)
     v = torch.from_numpy(np.float32(c.vel_true)).cuda()
     r32 = np.random.default_rng(4).standard_normal((3, 5, 120)).astype(np.float32)
-    with _ctx(c) as ctx:
+    with _ctx(c, fd_kernel=1) as ctx:
         assert ctx.stats()["fd_kernel"] == 1  # the resident solver fits this grid
         ctx.green(v)
         ref_gh = ctx.get_green()
@@ -461,7 +461,7 @@ def test_bounded_wait_expiry_is_reported_and_context_recovers():
         assert ei.value.status == egh.EGH_ETIMEOUT
         ctx.deblur(r32, out)
         assert np.array_equal(out, ref)
-    with _ctx(c, fd_kernel=2) as ctx:  # the hook needs the resident solver
+    with _ctx(c) as ctx:  # the default per-step kernel: the resident solver's hook is refused
         with pytest.raises(egh.EghError) as ei:
             ctx.test_expire_wait(egh.EXPIRE_FD_RESIDENT, 1)
         assert ei.value.status == egh.EGH_EINVAL
