@@ -572,6 +572,14 @@ def run_ours(args):
     clocks = clk.stop()
     launches = ctx.stats()["kernel_launches"] - l0
     total_ms = t_start.elapsed_time(t_end)
+    refinement = None
+    if args.precision == "mixed":
+        cb, rf = ctx.get_refinement()
+        refinement = {"threshold": 2000.0, "refined_frequencies": int(rf.sum()), "of": int(rf.size),
+                      "cond_bound_min": float(cb.min()), "cond_bound_max": float(cb.max()),
+                      "note": "solves of a frequency get one refinement step when its condition "
+                              "bound (||Q||_F over the smaller of mu and a power estimate of "
+                              "lambda_min) exceeds the threshold"}
     green_ms = [e[0].elapsed_time(e[1]) for e in recs]
     bf_ms = [e[0].elapsed_time(e[2]) for e in recs]
     deb_ms = [e[2].elapsed_time(e[3]) for e in recs]
@@ -671,6 +679,7 @@ def run_ours(args):
                       "hessian_factor": statistics.mean(bf_ms) - statistics.mean(green_ms),
                       "deblur": statistics.mean(deb_ms)},
         "deblur_sources_per_s": ns / (statistics.mean(deb_ms) / 1e3),
+        "refinement": refinement,
         "other_precision": other or None,
         "serving": serving,
         "variants": variants,

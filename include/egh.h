@@ -70,9 +70,12 @@ typedef enum {
  *   EGH_PREC_MIXED:      Gram as bf16x3 products on the tensor cores with FP32 accumulation (each
  *                        transform stored as bf16 hi + lo; about 1e-5 relative against FP64);
  *                        FP32 Cholesky with FP64 pivots; solves as products with the explicit
- *                        inverse factor followed by one step of iterative refinement whose
- *                        residual D - Q X is accumulated to FP64-class accuracy (about 2^-48
- *                        relative) by a compensated FP32 dot product;
+ *                        inverse factor; at the frequencies whose condition bound exceeds a
+ *                        threshold (egh_set_refinement; default 2000, where an FP32-class solve's
+ *                        error of about 1e-7 cond could approach the multipliers' tolerance) one
+ *                        step of iterative refinement follows, whose residual D - Q X is
+ *                        accumulated to FP64-class accuracy (about 2^-48 relative) by a
+ *                        compensated FP32 dot product;
  *   EGH_PREC_MIXED_FP64: as EGH_PREC_MIXED with the refinement residual accumulated in FP64
  *                        arithmetic (the same rounded residual, several times slower on a GB300,
  *                        whose FP64 rate is a small fraction of its FP32 rate). */
@@ -223,6 +226,19 @@ egh_status egh_factor(egh_ctx *ctx, int32_t *bad_freq, void *stream);
  * before the work completes, and such an expiry is reported by the next call
  * that waits for the device (egh_green, egh_hessian, a host-buffer deblur). */
 egh_status egh_deblur(egh_ctx *ctx, const float *resid, int32_t ns, int32_t nt_d, float *mult, void *stream);
+
+/* Threshold of the selective refinement of the mixed precisions (the paper has no counterpart:
+ * its precision is not stated).  egh_factor bounds each cond(Q_k) by ||Q_k||_F times the smaller
+ * of 1/mu (lambda_min >= mu) and 1.25 times a 40-step power estimate of lambda_max(Q_k^{-1})
+ * computed with the inverse factor; the solves of the frequencies whose bound exceeds the
+ * threshold get one refinement step.  0 refines every frequency, infinity none.  Applies from the
+ * next egh_factor.  EGH_EINVAL if negative or NaN. */
+egh_status egh_set_refinement(egh_ctx *ctx, double threshold);
+
+/* The last egh_factor's condition bounds (cond_bound [nfreq], host, may be NULL) and which
+ * frequencies are refined (refined [nfreq] 0/1, host, may be NULL).  Mixed precisions only
+ * (EGH_EINVAL otherwise); EGH_ESTATE before egh_factor. */
+egh_status egh_get_refinement(egh_ctx *ctx, double *cond_bound, int32_t *refined);
 
 /* Same solve, returning the frequency-domain multipliers X[k][r][s]
  * (complex64, [nfreq][nrec][ns]) instead of synthesising them in time.

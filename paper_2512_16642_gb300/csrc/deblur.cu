@@ -564,10 +564,10 @@ constexpr int CG_T = 32;
 template <bool CONJT>
 __global__ void __launch_bounds__(256)
     k_cgemm(const float2* __restrict__ Wh, int n, const float2* __restrict__ Bh, int ld,
-            float2* __restrict__ Ch) {
+            float2* __restrict__ Ch, const int* __restrict__ kl) {
   __shared__ float2 As[CG_T][CG_T + 1];  // As[r][kk] = op(W)[row0 + r][k0 + kk]
   __shared__ float2 Bs[CG_T][CG_T + 1];  // Bs[kk][c] = B[k0 + kk][col0 + c]
-  const int k = blockIdx.z;
+  const int k = kl ? kl[blockIdx.z] : blockIdx.z;
   const float2* W = Wh + (long long)k * n * n;
   const float2* B = Bh + (long long)k * n * ld;
   float2* C = Ch + (long long)k * n * ld;
@@ -623,13 +623,15 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-// X = W^H (W D) through the scratch Y (both n x ld per frequency); D and X may alias.
-cudaError_t launch_inverse_solve(const float2* Wh, int n, int nf, const float2* D, float2* Y,
-                                 float2* X, int ld, cudaStream_t st) {
-  const dim3 grid((ld + CG_T - 1) / CG_T, (n + CG_T - 1) / CG_T, nf);
+// X = W^H (W D) through the scratch Y (both n x ld per frequency); D and X may alias.  With kl,
+// only the nk frequencies kl[0 .. nk-1] (device list); else all nk = nf.
+cudaError_t launch_inverse_solve(const float2* Wh, int n, int nk, const float2* D, float2* Y,
+                                 float2* X, int ld, cudaStream_t st, const int* kl) {
+  if (nk < 1) return cudaSuccess;
+  const dim3 grid((ld + CG_T - 1) / CG_T, (n + CG_T - 1) / CG_T, nk);
   count_launches(2);
-  k_cgemm<false><<<grid, 256, 0, st>>>(Wh, n, D, ld, Y);
-  k_cgemm<true><<<grid, 256, 0, st>>>(Wh, n, Y, ld, X);
+  k_cgemm<false><<<grid, 256, 0, st>>>(Wh, n, D, ld, Y, kl);
+  k_cgemm<true><<<grid, 256, 0, st>>>(Wh, n, Y, ld, X, kl);
   return cudaGetLastError();
 }
 
@@ -641,9 +643,10 @@ cudaError_t launch_inverse_solve(const float2* Wh, int n, int nf, const float2* 
 // ---------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(32 * TS_W)
     k_resid64(const float2* __restrict__ Qh, int n, const float2* __restrict__ Xh,
-              const float2* __restrict__ Dh, int ns, float2* __restrict__ Rh) {
+              const float2* __restrict__ Dh, int ns, float2* __restrict__ Rh,
+                 const int* __restrict__ kl) {
   extern __shared__ float2 Xs[];  // [n][32]
-  const int k = blockIdx.y;
+  const int k = kl ? kl[blockIdx.y] : blockIdx.y;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int col = blockIdx.x * 32 + lane;
   const bool valid = col < ns;
@@ -705,9 +708,10 @@ __device__ __forceinline__ void dot2_add2(float2& s, float2& c, float2 a, float2
 
 __global__ void __launch_bounds__(32 * TS_W)
     k_resid_dot2(const float2* __restrict__ Qh, int n, const float2* __restrict__ Xh,
-                 const float2* __restrict__ Dh, int ns, float2* __restrict__ Rh) {
+                 const float2* __restrict__ Dh, int ns, float2* __restrict__ Rh,
+                 const int* __restrict__ kl) {
   extern __shared__ float2 Xs[];  // [n][32]
-  const int k = blockIdx.y;
+  const int k = kl ? kl[blockIdx.y] : blockIdx.y;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int col = blockIdx.x * 32 + lane;
   const bool valid = col < ns;
@@ -747,7 +751,8 @@ __global__ void __launch_bounds__(32 * TS_W)
 }
 
 cudaError_t launch_resid(const float2* Qh, int n, int nf, const float2* Xh, const float2* Dh,
-                         int ns, float2* Rh, bool fp64, cudaStream_t st) {
+                         int ns, float2* Rh, bool fp64, cudaStream_t st, const int* kl) {
+  if (nf < 1) return cudaSuccess;
   const size_t smem = sizeof(float2) * 32 * (size_t)n;
   if (smem > 48 * 1024) {
     cudaError_t e = fp64 ? cudaFuncSetAttribute(k_resid64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
@@ -760,9 +765,9 @@ cudaError_t launch_resid(const float2* Qh, int n, int nf, const float2* Xh, cons
   const int groups = std::max(1, std::min((n + TS_W - 1) / TS_W, (4 * 152 + blocks - 1) / blocks));
   const dim3 grid((ns + 31) / 32, nf, groups);
   if (fp64)
-    k_resid64<<<grid, 32 * TS_W, smem, st>>>(Qh, n, Xh, Dh, ns, Rh);
+    k_resid64<<<grid, 32 * TS_W, smem, st>>>(Qh, n, Xh, Dh, ns, Rh, kl);
   else
-    k_resid_dot2<<<grid, 32 * TS_W, smem, st>>>(Qh, n, Xh, Dh, ns, Rh);
+    k_resid_dot2<<<grid, 32 * TS_W, smem, st>>>(Qh, n, Xh, Dh, ns, Rh, kl);
   return cudaGetLastError();
 }
 
@@ -790,22 +795,27 @@ cudaError_t launch_diag_solve(const float2* Qh, int n, int nf, float2* Dh, int n
 }
 
 // X += R (complex, all frequencies and sources)
-__global__ void k_add_correction(float2* __restrict__ X, const float2* __restrict__ R, long long m) {
+// X_k += R_k for the frequencies of the list (m = elements per frequency), all when kl is null.
+__global__ void k_add_correction(float2* __restrict__ X, const float2* __restrict__ R, long long m,
+                                 const int* __restrict__ kl) {
+  const long long off = (long long)(kl ? kl[blockIdx.y] : blockIdx.y) * m;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m;
        i += (long long)gridDim.x * blockDim.x) {
-    const float2 r = R[i];
-    float2 x = X[i];
+    const float2 r = R[off + i];
+    float2 x = X[off + i];
     x.x += r.x;
     x.y += r.y;
-    X[i] = x;
+    X[off + i] = x;
   }
 }
 
-cudaError_t launch_add_correction(float2* X, const float2* R, long long m, cudaStream_t st) {
+cudaError_t launch_add_correction(float2* X, const float2* R, long long m, int nk, cudaStream_t st,
+                                  const int* kl) {
+  if (nk < 1) return cudaSuccess;
   long long blocks = (m + 255) / 256;
-  if (blocks > 4096) blocks = 4096;
+  if (blocks > 512) blocks = 512;
   count_launches(1);
-  k_add_correction<<<(int)blocks, 256, 0, st>>>(X, R, m);
+  k_add_correction<<<dim3((unsigned)blocks, (unsigned)nk), 256, 0, st>>>(X, R, m, kl);
   return cudaGetLastError();
 }
 

@@ -74,6 +74,12 @@ struct egh_ctx {
   unsigned char* twt_deb = nullptr;  // the deblur transform's twiddle tiles (tw_len levels)
   unsigned char* tws_deb = nullptr;  // the synthesis twiddle tiles (tw_len samples)
   float2* Wh = nullptr;  // mixed precision: W = L^{-1} per frequency (solves as products)
+  double* fro2 = nullptr;  // mixed precision: ||Q_k||_F^2 of the last factorisation
+  int* kref = nullptr;     // mixed precision: frequencies whose solves are refined (device list)
+  int nref = 0;            // their number
+  double refine_cond = kRefineCond;   // refinement threshold on the bound ||Q_k||_F / mu
+  std::vector<double> cond_bound;     // the bound per frequency (last factorisation)
+  std::vector<int> refined;           // 1 where the solves are refined
   int tw_len = 0;
   cudaStream_t side = nullptr;                 // the transform's stream inside egh_green (low priority)
   cudaStream_t fdst = nullptr;                 // the FD stream inside egh_green (high priority)
@@ -283,7 +289,7 @@ cudaError_t zero_snap_slot(egh_ctx* ctx, int j, cudaStream_t st) {
 }
 
 void free_all(egh_ctx* c) {
-  void* ptrs[] = {c->xbuf, c->rflags, c->tws_deb, c->twt_deb, c->twt_bl, c->Wh, c->Dr, c->Rr, c->coef, c->lev, c->snap, c->twt, c->gh, c->ghb, c->part, c->Qh, c->Lh, c->tw, c->w_dev,
+  void* ptrs[] = {c->fro2, c->kref, c->xbuf, c->rflags, c->tws_deb, c->twt_deb, c->twt_bl, c->Wh, c->Dr, c->Rr, c->coef, c->lev, c->snap, c->twt, c->gh, c->ghb, c->part, c->Qh, c->Lh, c->tw, c->w_dev,
                   c->rec_pts, c->status, c->dsum, c->lmax, c->vchk, c->d_err, c->vel_stage, c->Dh,
                   c->io_in, c->io_out};
   for (void* p : ptrs)
@@ -530,8 +536,11 @@ egh_status egh_create(const egh_config* cfg, egh_ctx** out) {
         "gram");
   ALLOC(ctx->Qh, (size_t)c.nfreq * c.nrec * c.nrec * sizeof(float2), "Qh");
   ALLOC(ctx->Lh, (size_t)c.nfreq * c.nrec * c.nrec * sizeof(float2), "Lh");
-  if (prec_mixed(ctx->prec))
+  if (prec_mixed(ctx->prec)) {
     ALLOC(ctx->Wh, (size_t)c.nfreq * c.nrec * c.nrec * sizeof(float2), "inverse factors");
+    ALLOC(ctx->fro2, (size_t)2 * c.nfreq * sizeof(double), "condition estimates");
+    ALLOC(ctx->kref, (size_t)c.nfreq * sizeof(int), "refined frequencies");
+  }
   ALLOC(ctx->w_dev, (size_t)c.nfreq * sizeof(float), "weights");
   ALLOC(ctx->rec_pts, (size_t)c.nrec * sizeof(int), "receivers");
   ALLOC(ctx->status, (size_t)c.nfreq * sizeof(int), "status");
@@ -966,13 +975,39 @@ egh_status egh_factor(egh_ctx* ctx, int32_t* bad_freq, void* stream_) {
   CK(cudaMemcpyAsync(ctx->Lh, ctx->Qh, bytes, cudaMemcpyDeviceToDevice, stream));
   CK(launch_potrf(ctx->Lh, ctx->nrec, ctx->nf, ctx->status, stream,
                   prec_mixed(ctx->prec) ? 1 : 0));
-  if (ctx->Wh) CK(launch_trtri(ctx->Lh, ctx->nrec, ctx->nf, ctx->Wh, stream));
+  if (ctx->Wh) {
+    CK(launch_trtri(ctx->Lh, ctx->nrec, ctx->nf, ctx->Wh, stream));
+    CK(launch_fro2(ctx->Qh, ctx->nrec, ctx->nf, ctx->fro2, stream));
+    CK(launch_inv_power(ctx->Wh, ctx->nrec, ctx->nf, ctx->fro2 + ctx->nf, stream));
+  }
   CK(cudaEventRecord(ctx->ev[5], stream));
   ctx->ev_rec[2] = true;
   std::vector<int> stv(ctx->nf);
+  std::vector<double> fro2(2 * ctx->nf, 0.0);
   CK(cudaMemcpyAsync(stv.data(), ctx->status, stv.size() * sizeof(int), cudaMemcpyDeviceToHost,
                      stream));
+  if (ctx->Wh)
+    CK(cudaMemcpyAsync(fro2.data(), ctx->fro2, fro2.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                       stream));
   CK(cudaStreamSynchronize(stream));
+  if (ctx->Wh) {
+    // selective refinement: the solves of frequency k get one refinement step when its condition
+    // bound (||Q_k||_F over the smaller of mu and the power estimate of lambda_min) exceeds the
+    // threshold
+    ctx->cond_bound.assign(ctx->nf, 0.0);
+    ctx->refined.assign(ctx->nf, 0);
+    std::vector<int> list;
+    for (int k = 0; k < ctx->nf; ++k) {
+      ctx->cond_bound[k] = cond_bound(fro2[k], fro2[ctx->nf + k], ctx->mu);
+      if (ctx->cond_bound[k] > ctx->refine_cond) {
+        list.push_back(k);
+        ctx->refined[k] = 1;
+      }
+    }
+    ctx->nref = (int)list.size();
+    if (!list.empty())
+      CK(cudaMemcpy(ctx->kref, list.data(), list.size() * sizeof(int), cudaMemcpyHostToDevice));
+  }
   for (int k = 0; k < ctx->nf; ++k)
     if (stv[k]) {
       if (bad_freq) *bad_freq = k;
@@ -1031,11 +1066,13 @@ static egh_status deblur_common(egh_ctx* ctx, const float* resid, int32_t ns, in
   CK(launch_trace_dft(din, (int)ntr, nt_d, ctx->nf, ctx->nrec, ns, 0, D, stream,
                       ctx->twt_deb, ctx->d_err, expire));
   const size_t dbytes = (size_t)ctx->nf * ntr * sizeof(float2);
-  if (!diag && prec_mixed(ctx->prec)) {
+  const bool refine = !diag && prec_mixed(ctx->prec) && ctx->nref > 0;
+  if (!diag && prec_mixed(ctx->prec) &&
+      (s = ensure_buf(ctx, (void**)&ctx->Rr, &ctx->Rr_cap, dbytes, stream, "solve scratch")))
+    return s;
+  if (refine) {
     // one step of iterative refinement: residual in FP64, correction solved with the FP32 factors
     if ((s = ensure_buf(ctx, (void**)&ctx->Dr, &ctx->Dr_cap, dbytes, stream, "refinement rhs")))
-      return s;
-    if ((s = ensure_buf(ctx, (void**)&ctx->Rr, &ctx->Rr_cap, dbytes, stream, "refinement residual")))
       return s;
     CK(cudaMemcpyAsync(ctx->Dr, D, dbytes, cudaMemcpyDeviceToDevice, stream));
   }
@@ -1045,10 +1082,13 @@ static egh_status deblur_common(egh_ctx* ctx, const float* resid, int32_t ns, in
     // X = W^H W D (products with the explicit inverse factor), residual D - Q X in FP64, the
     // correction solved the same way
     CK(launch_inverse_solve(ctx->Wh, ctx->nrec, ctx->nf, D, ctx->Rr, D, ns, stream));
-    CK(launch_resid(ctx->Qh, ctx->nrec, ctx->nf, D, ctx->Dr, ns, ctx->Rr,
-                    ctx->prec == EGH_PREC_MIXED_FP64, stream));
-    CK(launch_inverse_solve(ctx->Wh, ctx->nrec, ctx->nf, ctx->Rr, ctx->Dr, ctx->Rr, ns, stream));
-    CK(launch_add_correction(D, ctx->Rr, (long long)ctx->nf * ntr, stream));
+    if (refine) {  // the frequencies whose condition bound asks for it
+      CK(launch_resid(ctx->Qh, ctx->nrec, ctx->nref, D, ctx->Dr, ns, ctx->Rr,
+                      ctx->prec == EGH_PREC_MIXED_FP64, stream, ctx->kref));
+      CK(launch_inverse_solve(ctx->Wh, ctx->nrec, ctx->nref, ctx->Rr, ctx->Dr, ctx->Rr, ns, stream,
+                              ctx->kref));
+      CK(launch_add_correction(D, ctx->Rr, ntr, ctx->nref, stream, ctx->kref));
+    }
   } else {
     CK(launch_trsm(ctx->Lh, ctx->nrec, ctx->nf, D, ns, stream));
   }
@@ -1236,6 +1276,25 @@ egh_status egh_get_stats(egh_ctx* ctx, egh_stats* out) {
   ctx->st.fd_kernel = ctx->fd_kernel;
   ctx->st.fd_tiles = ctx->fd_kernel == 1 ? ctx->rg.TR * ctx->rg.TC : 0;
   *out = ctx->st;
+  return EGH_OK;
+}
+
+egh_status egh_set_refinement(egh_ctx* ctx, double threshold) {
+  if (!ctx) return fail(nullptr, EGH_EINVAL, "ctx is NULL");
+  if (!(threshold >= 0)) return fail(ctx, EGH_EINVAL, "threshold must be >= 0 (inf: never refine)");
+  ctx->refine_cond = threshold;
+  return EGH_OK;
+}
+
+egh_status egh_get_refinement(egh_ctx* ctx, double* cond_bound, int32_t* refined) {
+  if (!ctx) return fail(nullptr, EGH_EINVAL, "ctx is NULL");
+  if (!prec_mixed(ctx->prec)) return fail(ctx, EGH_EINVAL, "only the mixed precisions refine");
+  if (ctx->state < ST_FACTORED || ctx->cond_bound.empty())
+    return fail(ctx, EGH_ESTATE, "egh_get_refinement needs egh_factor first");
+  for (int k = 0; k < ctx->nf; ++k) {
+    if (cond_bound) cond_bound[k] = ctx->cond_bound[k];
+    if (refined) refined[k] = ctx->refined[k];
+  }
   return EGH_OK;
 }
 

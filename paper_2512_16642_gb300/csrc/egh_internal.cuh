@@ -155,17 +155,36 @@ cudaError_t launch_trace_dft(const float* resid, int ntr, int nt_d, int nf, int 
                              int s0, float2* Dh, cudaStream_t st, const unsigned char* twt,
                              int* err, int expire = 0);
 cudaError_t launch_trsm(const float2* Lh, int n, int nf, float2* Dh, int ns, cudaStream_t st);
-// W = L^{-1} per frequency; X = W^H (W D) with scratch Y
+// W = L^{-1} per frequency; X = W^H (W D) with scratch Y, for the nk frequencies of the device
+// list kl (all nk = nf when kl is null)
 cudaError_t launch_trtri(const float2* Lh, int n, int nf, float2* Wh, cudaStream_t st);
-cudaError_t launch_inverse_solve(const float2* Wh, int n, int nf, const float2* D, float2* Y,
-                                 float2* X, int ld, cudaStream_t st);
+cudaError_t launch_inverse_solve(const float2* Wh, int n, int nk, const float2* D, float2* Y,
+                                 float2* X, int ld, cudaStream_t st, const int* kl = nullptr);
 // diagonal-Hessian baseline: D_k[r][s] /= Q_k[r][r]
 cudaError_t launch_diag_solve(const float2* Qh, int n, int nf, float2* Dh, int ns, cudaStream_t st);
-// refinement residual R = D - Q X: FP64 arithmetic (fp64) or the compensated FP32 dot product
+// refinement residual R = D - Q X: FP64 arithmetic (fp64) or the compensated FP32 dot product;
+// frequencies of the device list kl (nf of them), all when kl is null
 cudaError_t launch_resid(const float2* Qh, int n, int nf, const float2* Xh, const float2* Dh,
-                         int ns, float2* Rh, bool fp64, cudaStream_t st);
+                         int ns, float2* Rh, bool fp64, cudaStream_t st, const int* kl = nullptr);
 inline bool prec_mixed(int prec) { return prec == EGH_PREC_MIXED || prec == EGH_PREC_MIXED_FP64; }
-cudaError_t launch_add_correction(float2* X, const float2* R, long long m, cudaStream_t st);
+// X_k += R_k (m elements per frequency) for the nk frequencies of kl (all when kl is null)
+cudaError_t launch_add_correction(float2* X, const float2* R, long long m, int nk, cudaStream_t st,
+                                  const int* kl = nullptr);
+// ||Q_k||_F^2 per frequency (FP64 sums) into d_out[nf]
+cudaError_t launch_fro2(const float2* Qh, int n, int nf, double* d_out, cudaStream_t st);
+// lambda_max(W_k^H W_k) = 1 / lambda_min(Q_k) by power iteration (from below) into lam[nf]
+cudaError_t launch_inv_power(const float2* Wh, int n, int nf, double* lam, cudaStream_t st);
+// Condition bound of a factorisation from ||Q||_F^2, the power estimate of 1/lambda_min (with a
+// margin for its approach from below) and, when known (> 0), mu <= lambda_min.
+inline double cond_bound(double fro2, double inv_lmin, double mu) {
+  double c = 1.25 * sqrt(fro2) * inv_lmin;
+  if (mu > 0 && sqrt(fro2) / mu < c) c = sqrt(fro2) / mu;
+  return c;
+}
+// Frequencies whose factorisation's solve gets one step of iterative refinement: the bound
+// cond(Q_k) <= ||Q_k||_F / mu (lambda_min >= mu) above this threshold, where an FP32-class solve
+// (relative error about 1e-7 cond) could approach the multipliers' tolerance.
+constexpr double kRefineCond = 2000.0;
 // (on the tensor cores when tws, the synthesis twiddle tiles for at least nt_d samples, and err
 // are given and 2 nf <= 64; else on the CUDA cores)
 cudaError_t launch_synth(const float2* Dh, int nrec, int ns, int ld, int s0, int nf, const float* w,

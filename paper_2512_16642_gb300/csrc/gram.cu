@@ -183,6 +183,103 @@ cudaError_t launch_diag_sum(const float2* Qh, int nrec, int nf, double* d_sum, c
   return cudaGetLastError();
 }
 
+// ||Q_k||_F^2 per frequency: one block per frequency, FP32 squares summed in FP64.
+__global__ void k_fro2(const float2* __restrict__ Qh, int n, double* d_out) {
+  __shared__ double red[256];
+  const long long n2 = (long long)n * n;
+  const float2* A = Qh + (long long)blockIdx.x * n2;
+  double s = 0.0;
+  for (long long t = threadIdx.x; t < n2; t += blockDim.x) {
+    const float2 a = A[t];
+    s += (double)a.x * a.x + (double)a.y * a.y;
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) d_out[blockIdx.x] = red[0];
+}
+
+cudaError_t launch_fro2(const float2* Qh, int n, int nf, double* d_out, cudaStream_t st) {
+  count_launches(1);
+  k_fro2<<<nf, 256, 0, st>>>(Qh, n, d_out);
+  return cudaGetLastError();
+}
+
+// Largest eigenvalue of Q_k^{-1} = W_k^H W_k (W = L^{-1}, lower triangular) by 40 steps of
+// power iteration in FP32, one block per frequency: lam[k] = ||W^H W v|| / ||v|| for the last v.
+// It approaches 1 / lambda_min(Q_k) from below.
+__global__ void k_inv_power(const float2* __restrict__ Wh, int n, double* lam) {
+  extern __shared__ float2 pv[];  // v [n], y [n]
+  __shared__ float red[256];
+  float2* v = pv;
+  float2* y = pv + n;
+  const float2* W = Wh + (long long)blockIdx.x * n * n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = make_float2(1.f + 0.01f * (i % 7), 0.f);
+  __syncthreads();
+  float norm = 0.f;
+  auto reduce = [&](float x) {
+    red[threadIdx.x] = x;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+      __syncthreads();
+    }
+    const float r = red[0];
+    __syncthreads();
+    return r;
+  };
+  float vv = reduce([&] {
+    float a = 0.f;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) a += v[i].x * v[i].x + v[i].y * v[i].y;
+    return a;
+  }());
+  for (int it = 0; it < 40; ++it) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {  // y = W v
+      float re = 0.f, im = 0.f;
+      for (int j = 0; j <= i; ++j) {
+        const float2 a = W[(long long)i * n + j], b = v[j];
+        re = fmaf(a.x, b.x, fmaf(-a.y, b.y, re));
+        im = fmaf(a.x, b.y, fmaf(a.y, b.x, im));
+      }
+      y[i] = make_float2(re, im);
+    }
+    __syncthreads();
+    float a2 = 0.f;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {  // v' = W^H y
+      float re = 0.f, im = 0.f;
+      for (int j = i; j < n; ++j) {
+        const float2 a = W[(long long)j * n + i], b = y[j];
+        re = fmaf(a.x, b.x, fmaf(a.y, b.y, re));
+        im = fmaf(a.x, b.y, fmaf(-a.y, b.x, im));
+      }
+      v[i] = make_float2(re, im);
+      a2 += re * re + im * im;
+    }
+    __syncthreads();
+    const float w2 = reduce(a2);
+    norm = sqrtf(w2 / vv);
+    const float sc = 1.f / sqrtf(w2);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = make_float2(v[i].x * sc, v[i].y * sc);
+    vv = 1.f;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) lam[blockIdx.x] = norm;
+}
+
+cudaError_t launch_inv_power(const float2* Wh, int n, int nf, double* lam, cudaStream_t st) {
+  const size_t smem = sizeof(float2) * 2 * (size_t)n;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_inv_power, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  count_launches(1);
+  k_inv_power<<<nf, 256, smem, st>>>(Wh, n, lam);
+  return cudaGetLastError();
+}
+
 // Largest eigenvalue of each Hermitian H_k by power iteration (fixed 300 iterations, Rayleigh
 // quotient), one block per frequency; d_lmax[k].
 constexpr int PI_ITERS = 300;

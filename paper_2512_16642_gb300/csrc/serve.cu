@@ -88,6 +88,8 @@ struct HSet {
   int nrec = 0, nf = 0, tw_len = 0;
   float2 *Qh = nullptr, *Lh = nullptr, *tw = nullptr;
   float2* Wh = nullptr;  // mixed precision: W = L^{-1}
+  int* kref = nullptr;   // mixed precision: frequencies whose solves are refined (device list)
+  int nref = 0;
   unsigned char* twt = nullptr;  // tensor-core transform twiddle tiles (tw_len levels)
   unsigned char* tws = nullptr;  // tensor-core synthesis twiddle tiles (tw_len samples)
   float* w = nullptr;
@@ -215,12 +217,17 @@ cudaError_t run_batch(Server* sv, Batch* b, const HSet& h, int expire) {
   if (prec_mixed(sv->prec)) {
     float2* Dr = D + dsz;
     float2* R = D + 2 * dsz;
-    if ((e = cudaMemcpyAsync(Dr, D, dsz * sizeof(float2), cudaMemcpyDeviceToDevice, st))) return e;
-    if ((e = launch_inverse_solve(h.Wh, h.nrec, h.nf, D, R, D, ld, st))) return e;
-    if ((e = launch_resid(h.Qh, h.nrec, h.nf, D, Dr, ld, R, sv->prec == EGH_PREC_MIXED_FP64, st)))
+    if (h.nref > 0 &&
+        (e = cudaMemcpyAsync(Dr, D, dsz * sizeof(float2), cudaMemcpyDeviceToDevice, st)))
       return e;
-    if ((e = launch_inverse_solve(h.Wh, h.nrec, h.nf, R, Dr, R, ld, st))) return e;
-    if ((e = launch_add_correction(D, R, (long long)dsz, st))) return e;
+    if ((e = launch_inverse_solve(h.Wh, h.nrec, h.nf, D, R, D, ld, st))) return e;
+    if (h.nref > 0) {  // the frequencies whose condition bound asks for refinement
+      if ((e = launch_resid(h.Qh, h.nrec, h.nref, D, Dr, ld, R, sv->prec == EGH_PREC_MIXED_FP64, st,
+                            h.kref)))
+        return e;
+      if ((e = launch_inverse_solve(h.Wh, h.nrec, h.nref, R, Dr, R, ld, st, h.kref))) return e;
+      if ((e = launch_add_correction(D, R, (long long)h.nrec * ld, h.nref, st, h.kref))) return e;
+    }
   } else {
     if ((e = launch_trsm(h.Lh, h.nrec, h.nf, D, ld, st))) return e;
   }
@@ -440,7 +447,10 @@ egh_status egh_server_add_set(egh_server* sv, int32_t nrec, int32_t nfreq, const
   const std::vector<float> w = synthesis_weights(f, dt, nt_record);
   int* status = nullptr;
   cudaStream_t st = sv->streams[0];
+  double* d_cond = nullptr;
   auto cleanup = [&]() {
+    cudaFree(d_cond);
+    cudaFree(h.kref);
     cudaFree(h.twt);
     cudaFree(h.tws);
     cudaFree(h.Wh);
@@ -471,13 +481,30 @@ egh_status egh_server_add_set(egh_server* sv, int32_t nrec, int32_t nfreq, const
   }
   if (!e) e = cudaMemcpy(h.w, w.data(), w.size() * sizeof(float), cudaMemcpyHostToDevice);
   if (!e) e = launch_potrf(h.Lh, nrec, nfreq, status, st, prec_mixed(sv->prec) ? 1 : 0);
+  std::vector<double> cond(2 * nfreq, 0.0);
   if (!e && prec_mixed(sv->prec)) {
     e = cudaMalloc(&h.Wh, qn * sizeof(float2));
     if (!e) e = launch_trtri(h.Lh, nrec, nfreq, h.Wh, st);
+    if (!e) e = cudaMalloc(&d_cond, 2 * nfreq * sizeof(double));
+    if (!e) e = launch_fro2(h.Qh, nrec, nfreq, d_cond, st);
+    if (!e) e = launch_inv_power(h.Wh, nrec, nfreq, d_cond + nfreq, st);
+    if (!e) e = cudaMemcpyAsync(cond.data(), d_cond, 2 * nfreq * sizeof(double), cudaMemcpyDeviceToHost, st);
   }
   std::vector<int> stv(nfreq, 0);
   if (!e) e = cudaMemcpyAsync(stv.data(), status, nfreq * sizeof(int), cudaMemcpyDeviceToHost, st);
   if (!e) e = cudaStreamSynchronize(st);
+  if (!e && prec_mixed(sv->prec)) {
+    // selective refinement as for a context (the penalty of a set is not known: lambda_min comes
+    // from the power estimate alone)
+    std::vector<int> list;
+    for (int k = 0; k < nfreq; ++k)
+      if (cond_bound(cond[k], cond[nfreq + k], 0.0) > kRefineCond) list.push_back(k);
+    h.nref = (int)list.size();
+    if (!list.empty()) {
+      e = cudaMalloc(&h.kref, list.size() * sizeof(int));
+      if (!e) e = cudaMemcpy(h.kref, list.data(), list.size() * sizeof(int), cudaMemcpyHostToDevice);
+    }
+  }
   if (e) {
     cudaGetLastError();
     cleanup();
@@ -486,6 +513,8 @@ egh_status egh_server_add_set(egh_server* sv, int32_t nrec, int32_t nfreq, const
   }
   cudaFree(status);
   status = nullptr;
+  cudaFree(d_cond);
+  d_cond = nullptr;
   for (int k = 0; k < nfreq; ++k)
     if (stv[k]) {
       cleanup();
@@ -651,6 +680,7 @@ void egh_server_destroy(egh_server* sv) {
   for (auto& s : sv->streams) cudaStreamSynchronize(s);
   for (auto& s : sv->streams) cudaStreamDestroy(s);
   for (HSet& h : sv->sets) {
+    cudaFree(h.kref);
     cudaFree(h.twt);
     cudaFree(h.tws);
     cudaFree(h.Wh);

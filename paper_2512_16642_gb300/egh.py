@@ -103,6 +103,8 @@ _SIGS = {
     "egh_version": ([], ctypes.c_int32),
     "egh_release_green": ([_vp], ctypes.c_int),
     "egh_test_expire_wait": ([_vp, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
+    "egh_set_refinement": ([_vp, ctypes.c_double], ctypes.c_int),
+    "egh_get_refinement": ([_vp, _f64p, _i32p], ctypes.c_int),
     "egh_server_test_expire_wait": ([_vp, ctypes.c_int32], ctypes.c_int),
     "egh_batch_create": ([ctypes.POINTER(_vp), ctypes.c_int32, ctypes.POINTER(_vp)], ctypes.c_int),
     "egh_batch_factor": ([_vp, _i32p, _i32p, _vp], ctypes.c_int),
@@ -289,6 +291,18 @@ def egh_get_stats(ctx):
 EXPIRE_GREEN_TRANSFORM, EXPIRE_FD_RESIDENT, EXPIRE_DEBLUR_TRANSFORM = range(3)
 
 
+def egh_set_refinement(ctx, threshold):
+    _check(load().egh_set_refinement(ctx, float(threshold)), ctx)
+
+
+def egh_get_refinement(ctx, nfreq):
+    """(condition bounds [nfreq] float64, refined [nfreq] bool) of the last factorisation."""
+    cb = np.zeros(int(nfreq), np.float64)
+    rf = np.zeros(int(nfreq), np.int32)
+    _check(load().egh_get_refinement(ctx, cb.ctypes.data_as(_f64p), rf.ctypes.data_as(_i32p)), ctx)
+    return cb, rf.astype(bool)
+
+
 def egh_test_expire_wait(ctx, kind, count=1):
     _check(load().egh_test_expire_wait(ctx, int(kind), int(count)), ctx)
 
@@ -387,6 +401,12 @@ class Context:
 
     def test_expire_wait(self, kind, count=1):
         egh_test_expire_wait(self.h, kind, count)
+
+    def set_refinement(self, threshold):
+        egh_set_refinement(self.h, threshold)
+
+    def get_refinement(self):
+        return egh_get_refinement(self.h, self.nf)
 
     def release_green(self):
         _check(load().egh_release_green(self.h), self.h)

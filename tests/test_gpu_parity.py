@@ -168,10 +168,14 @@ def test_precision_form_small(small):
     Xs = {}
     for prec in (egh.EGH_PREC_FP32, egh.EGH_PREC_MIXED, egh.EGH_PREC_MIXED_FP64):
         with _ctx(c, precision=prec) as ctx:
+            if prec != egh.EGH_PREC_FP32:
+                ctx.set_refinement(0.0)  # every frequency refined, to compare the two residuals
             ctx.green(torch.from_numpy(np.float32(c.vel_start)).cuda())
             ctx.hessian(egh.EGH_MU_REL_MEANDIAG, c.mu_alpha)
             Q = ctx.get_hessian(False).astype(np.complex128)
             ctx.factor()
+            if prec != egh.EGH_PREC_FP32:
+                assert ctx.get_refinement()[1].all()
             X = torch.empty((nf, nr, ns), dtype=torch.complex64, device="cuda")
             ctx.deblur_freq(torch.from_numpy(r32).cuda(), X)
             Xh = X.cpu().numpy().astype(np.complex128)
@@ -196,6 +200,52 @@ def test_precision_form_small(small):
     for k in range(nf):
         d = rel(Xs[egh.EGH_PREC_MIXED][k], Xs[egh.EGH_PREC_MIXED_FP64][k])
         assert d <= 1e-6, (k, d)
+
+
+def test_selective_refinement_small(small):
+    """Selective refinement of the mixed precision on the 101x101 case made ill-conditioned
+    (mu = 1e-3 of the mean diagonal).  The residuals are impulses at t = 0 whose values are exact
+    in bf16, so the GPU's spectra equal them exactly and the solve is isolated: the solutions
+    with every frequency refined and with none are compared with the exact FP64 solution of the
+    GPU's own Hessians.  Checked: the condition bounds of egh_get_refinement are not below the
+    true condition numbers (less a margin for the power estimate); refinement gains at least a
+    factor 10 where the unrefined solve is poor; the default threshold refines exactly the
+    frequencies whose bound exceeds it, and those solutions are the refined ones bit for bit."""
+    torch = _torch()
+    from paper_2512_16642_gb300 import egh
+
+    c, _, _ = small
+    nf, nr, ns = c.freqs.size, c.rec_ix.size, 6
+    rng = np.random.default_rng(17)
+    r32 = np.zeros((ns, nr, 64), np.float32)
+    r32[:, :, 0] = rng.choice(np.array([-2.0, -1.0, 1.0, 2.0], np.float32), size=(ns, nr))
+    D = np.repeat(r32[:, :, 0].T[None].astype(np.complex128), nf, axis=0)  # [nf][nr][ns]
+    rt = torch.from_numpy(r32).cuda()
+    X = {}
+    with _ctx(c, precision=egh.EGH_PREC_MIXED) as ctx:
+        ctx.green(torch.from_numpy(np.float32(c.vel_start)).cuda())
+        ctx.hessian(egh.EGH_MU_REL_MEANDIAG, 1e-3)
+        Q = ctx.get_hessian(False).astype(np.complex128)
+        Xe = oracle.chol_solve(oracle.cholesky(Q), D)
+        cond = np.array([np.linalg.cond(Q[k]) for k in range(nf)])
+        for name, thr in (("all", 0.0), ("none", np.inf), ("default", 2000.0)):
+            ctx.set_refinement(thr)
+            ctx.factor()
+            bound, refined = ctx.get_refinement()
+            Xd = torch.empty((nf, nr, ns), dtype=torch.complex64, device="cuda")
+            ctx.deblur_freq(rt, Xd)
+            X[name] = Xd.cpu().numpy()
+            if name == "default":
+                assert np.array_equal(refined, bound > thr)
+        assert np.all(bound >= 0.8 * cond), (bound, cond)
+    err = {n: np.array([rel(X[n][k], Xe[k]) for k in range(nf)]) for n in X}
+    print("cond", cond, "bound", bound, "err", err)
+    assert np.all(err["all"] <= 1e-4), err["all"]
+    for k in range(nf):
+        if err["none"][k] > 1e-4:
+            assert err["all"][k] * 10 <= err["none"][k], k
+        ref = X["all"][k] if refined[k] else X["none"][k]
+        assert np.array_equal(X["default"][k], ref), k
 
 
 def test_diagonal_baseline_small(small):
