@@ -575,7 +575,7 @@ def run_ours(args):
     refinement = None
     if args.precision == "mixed":
         cb, rf = ctx.get_refinement()
-        refinement = {"threshold": 2000.0, "refined_frequencies": int(rf.sum()), "of": int(rf.size),
+        refinement = {"threshold": 1e4, "refined_frequencies": int(rf.sum()), "of": int(rf.size),
                       "cond_bound_min": float(cb.min()), "cond_bound_max": float(cb.max()),
                       "note": "solves of a frequency get one refinement step when its condition "
                               "bound (||Q||_F over the smaller of mu and a power estimate of "

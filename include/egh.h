@@ -71,8 +71,9 @@ typedef enum {
  *                        transform stored as bf16 hi + lo; about 1e-5 relative against FP64);
  *                        FP32 Cholesky with FP64 pivots; solves as products with the explicit
  *                        inverse factor; at the frequencies whose condition bound exceeds a
- *                        threshold (egh_set_refinement; default 2000, where an FP32-class solve's
- *                        error of about 1e-7 cond could approach the multipliers' tolerance) one
+ *                        threshold (egh_set_refinement; default 1e4: unrefined solutions have a
+ *                        relative error of about 1e-8 cond, measured, and the bound exceeds cond
+ *                        about twofold, so they stay near or below 1e-4) one
  *                        step of iterative refinement follows, whose residual D - Q X is
  *                        accumulated to FP64-class accuracy (about 2^-48 relative) by a
  *                        compensated FP32 dot product;

@@ -181,10 +181,11 @@ inline double cond_bound(double fro2, double inv_lmin, double mu) {
   if (mu > 0 && sqrt(fro2) / mu < c) c = sqrt(fro2) / mu;
   return c;
 }
-// Frequencies whose factorisation's solve gets one step of iterative refinement: the bound
-// cond(Q_k) <= ||Q_k||_F / mu (lambda_min >= mu) above this threshold, where an FP32-class solve
-// (relative error about 1e-7 cond) could approach the multipliers' tolerance.
-constexpr double kRefineCond = 2000.0;
+// Frequencies whose solves get one step of iterative refinement: condition bound above this
+// threshold.  The products with the inverse factor give solutions with a relative error of about
+// 1e-8 cond (measured on the 101x101 case, cond 200-1800) and the bound exceeds cond about
+// twofold, so unrefined solutions stay near or below 1e-4, a tenth of the multipliers' tolerance.
+constexpr double kRefineCond = 1e4;
 // (on the tensor cores when tws, the synthesis twiddle tiles for at least nt_d samples, and err
 // are given and 2 nf <= 64; else on the CUDA cores)
 cudaError_t launch_synth(const float2* Dh, int nrec, int ns, int ld, int s0, int nf, const float* w,

@@ -228,7 +228,7 @@ def test_selective_refinement_small(small):
         Q = ctx.get_hessian(False).astype(np.complex128)
         Xe = oracle.chol_solve(oracle.cholesky(Q), D)
         cond = np.array([np.linalg.cond(Q[k]) for k in range(nf)])
-        for name, thr in (("all", 0.0), ("none", np.inf), ("default", 2000.0)):
+        for name, thr in (("all", 0.0), ("none", np.inf), ("default", 1e4)):
             ctx.set_refinement(thr)
             ctx.factor()
             bound, refined = ctx.get_refinement()
