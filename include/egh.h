@@ -409,6 +409,44 @@ egh_status egh_release_green(egh_ctx *ctx);
  * cancels. */
 egh_status egh_test_expire_wait(egh_ctx *ctx, int32_t kind, int32_t count);
 
+/* ---- Sharded update (several GPUs, one process per GPU) --------------------------------------- *
+ * The Green solves are independent per receiver and each frequency's Hessian and factorisation
+ * are independent of the others (Algorithm 2), so an update shards across GPUs: rank r solves the
+ * receivers of its block for all frequencies (a context with those receivers), one all-to-all
+ * exchange moves the transforms from receiver blocks to frequency blocks (egh_export_green on the
+ * sending side, egh_import_green on a context that holds every receiver and the rank's
+ * frequencies), the penalty needs one all-reduce of the ranks' diagonal sums (egh_hessian with
+ * EGH_MU_ABS and mu_param 0, egh_diag_sum, the sum over ranks, egh_set_mu), each rank factors its
+ * frequencies, and the multipliers are the sum over ranks of each rank's deblur at its frequencies
+ * (the synthesis is linear in the frequencies; egh_set_synthesis_frequencies gives each rank the
+ * weights of the full frequency list).  The collectives belong to the caller (e.g. NCCL through
+ * torch.distributed). */
+
+/* Copies the transforms of frequencies k0 .. k0+nk-1 of every receiver of the context to d_out
+ * ([nrec][nk][re/im][G] float32, device, caller-owned; G = the padded grid's points at the device
+ * pitch, egh_stats nz_pad x pitch rounded up to 256).  Requires egh_green.  Queued on stream. */
+egh_status egh_export_green(egh_ctx *ctx, int32_t k0, int32_t nk, float *d_out, void *stream);
+
+/* Sets the context's transforms from d_in ([nrec][nfreq][re/im][G] float32, device, the layout of
+ * egh_export_green) instead of solving: the context then stands as after egh_green (no snapshot
+ * ring is allocated).  Its grid must be the one of the contexts that solved.  Blocks. */
+egh_status egh_import_green(egh_ctx *ctx, const float *d_in, void *stream);
+
+/* *out = sum over k, i of Re Q_k[i][i] of the context's current Hessians (with the penalty they
+ * hold: none after egh_hessian with EGH_MU_ABS and mu_param 0).  Requires egh_hessian.  Blocks. */
+egh_status egh_diag_sum(egh_ctx *ctx, double *out);
+
+/* Replaces the penalty of the current Hessians by mu (Q_k = H_k + mu I; from a penalty of 0 the
+ * result is the one egh_hessian gives with that mu, bit for bit).  Factors are invalidated.
+ * Requires egh_hessian.  Blocks. */
+egh_status egh_set_mu(egh_ctx *ctx, double mu, void *stream);
+
+/* The context's frequencies are entries k0 .. k0+nfreq-1 of the full list all_freq_hz[nall]
+ * (host): its synthesis weights become those of the full list (the end weights of a frequency
+ * block differ from those of the block alone).  EGH_EINVAL if the entries differ. */
+egh_status egh_set_synthesis_frequencies(egh_ctx *ctx, const double *all_freq_hz, int32_t nall,
+                                         int32_t k0);
+
 /* ---- Batched factorisation --------------------------------------------------------------- *
  * A batch groups contexts (survey patches of one model, any receiver counts, one device, one
  * precision) whose Hessians are factored together: egh_batch_factor factors every frequency of

@@ -310,12 +310,17 @@ void free_all(egh_ctx* c) {
 
 // The Green-stage buffers (snapshot ring, transforms, bf16 transforms) are the largest; egh_green
 // allocates them on its first call and again after egh_release_green freed them.
-egh_status ensure_green_buffers(egh_ctx* ctx) {
-  if (ctx->gh) return EGH_OK;
+egh_status ensure_green_buffers(egh_ctx* ctx, bool with_ring = true) {
   const Layout& L = ctx->L;
   const size_t snap_bytes = (size_t)2 * 2 * ctx->K * ctx->Bp * (size_t)L.G * sizeof(__nv_bfloat16);
   egh_status s;
-  if ((s = dalloc(ctx, (void**)&ctx->snap, snap_bytes, "snapshot ring"))) return s;
+  if (with_ring && !ctx->snap) {
+    if ((s = dalloc(ctx, (void**)&ctx->snap, snap_bytes, "snapshot ring"))) return s;
+    // padding points of every snapshot slot stay zero for the life of the buffer
+    CK(cudaMemset(ctx->snap, 0, snap_bytes));
+    CK(make_snap_tmap(&ctx->tmap, ctx->snap, L.G, ctx->Bp, 2 * ctx->K));
+  }
+  if (ctx->gh) return EGH_OK;
   if ((s = dalloc(ctx, (void**)&ctx->gh, (size_t)ctx->nrec * ctx->nf * 2 * (size_t)L.G * sizeof(float),
                   "green transforms")))
     return s;
@@ -324,9 +329,6 @@ egh_status ensure_green_buffers(egh_ctx* ctx) {
                   (size_t)ctx->nrec * ctx->nf * 4 * (size_t)L.G * sizeof(__nv_bfloat16),
                   "bf16 transforms")))
     return s;
-  // padding points of every snapshot slot stay zero for the life of the buffer
-  CK(cudaMemset(ctx->snap, 0, snap_bytes));
-  CK(make_snap_tmap(&ctx->tmap, ctx->snap, L.G, ctx->Bp, 2 * ctx->K));
   if (ctx->ghb) CK(make_ghb_tmap(&ctx->tmap_ghb, ctx->ghb, L.G, ctx->nf, ctx->nrec));
   return EGH_OK;
 }
@@ -1276,6 +1278,76 @@ egh_status egh_get_stats(egh_ctx* ctx, egh_stats* out) {
   ctx->st.fd_kernel = ctx->fd_kernel;
   ctx->st.fd_tiles = ctx->fd_kernel == 1 ? ctx->rg.TR * ctx->rg.TC : 0;
   *out = ctx->st;
+  return EGH_OK;
+}
+
+egh_status egh_export_green(egh_ctx* ctx, int32_t k0, int32_t nk, float* d_out, void* stream_) {
+  if (!ctx) return fail(nullptr, EGH_EINVAL, "ctx is NULL");
+  CK(cudaSetDevice(ctx->dev));
+  if (ctx->state < ST_GREEN || !ctx->gh) return fail(ctx, EGH_ESTATE, "egh_export_green needs egh_green first");
+  if (k0 < 0 || nk < 0 || k0 + nk > ctx->nf) return fail(ctx, EGH_EINVAL, "frequency range outside 0..nfreq");
+  if (nk == 0) return EGH_OK;
+  if (!d_out || !pointer_is_device(d_out)) return fail(ctx, EGH_EINVAL, "d_out must be device memory");
+  const size_t plane = 2 * (size_t)ctx->L.G * sizeof(float);  // one frequency of one receiver
+  CK(cudaMemcpy2DAsync(d_out, nk * plane, ctx->gh + (size_t)k0 * 2 * ctx->L.G, ctx->nf * plane,
+                       nk * plane, ctx->nrec, cudaMemcpyDeviceToDevice, (cudaStream_t)stream_));
+  return EGH_OK;
+}
+
+egh_status egh_import_green(egh_ctx* ctx, const float* d_in, void* stream_) {
+  if (!ctx) return fail(nullptr, EGH_EINVAL, "ctx is NULL");
+  CK(cudaSetDevice(ctx->dev));
+  if (!d_in || !pointer_is_device(d_in)) return fail(ctx, EGH_EINVAL, "d_in must be device memory");
+  cudaStream_t stream = (cudaStream_t)stream_;
+  ctx->state = ST_CREATED;
+  egh_status s = ensure_green_buffers(ctx, false);  // no snapshot ring: no solve runs here
+  if (s) return s;
+  const size_t n = (size_t)ctx->nrec * ctx->nf * 2 * ctx->L.G;
+  CK(cudaMemcpyAsync(ctx->gh, d_in, n * sizeof(float), cudaMemcpyDeviceToDevice, stream));
+  if (ctx->ghb) CK(launch_gh_to_ghb(ctx->gh, ctx->nrec, ctx->nf, ctx->L.G, ctx->ghb, stream));
+  CK(cudaStreamSynchronize(stream));
+  ctx->st.pde_solves = 0;
+  ctx->st.point_steps = 0;
+  ctx->state = ST_GREEN;
+  return EGH_OK;
+}
+
+egh_status egh_diag_sum(egh_ctx* ctx, double* out) {
+  if (!ctx || !out) return fail(ctx, EGH_EINVAL, "NULL argument");
+  CK(cudaSetDevice(ctx->dev));
+  if (ctx->state < ST_HESSIAN) return fail(ctx, EGH_ESTATE, "egh_diag_sum needs egh_hessian first");
+  CK(launch_diag_sum(ctx->Qh, ctx->nrec, ctx->nf, ctx->dsum, 0));
+  CK(cudaMemcpy(out, ctx->dsum, sizeof(double), cudaMemcpyDeviceToHost));
+  return EGH_OK;
+}
+
+egh_status egh_set_mu(egh_ctx* ctx, double mu, void* stream_) {
+  if (!ctx) return fail(nullptr, EGH_EINVAL, "ctx is NULL");
+  CK(cudaSetDevice(ctx->dev));
+  if (ctx->state < ST_HESSIAN) return fail(ctx, EGH_ESTATE, "egh_set_mu needs egh_hessian first");
+  if (!std::isfinite(mu) || mu < 0) return fail(ctx, EGH_EINVAL, "mu must be finite and >= 0");
+  cudaStream_t stream = (cudaStream_t)stream_;
+  CK(launch_add_mu_copy_delta(ctx->Qh, ctx->Lh, ctx->nrec, ctx->nf, ctx->mu, mu, stream));
+  CK(cudaStreamSynchronize(stream));
+  ctx->mu = mu;
+  ctx->st.mu = mu;
+  ctx->state = ST_HESSIAN;
+  return EGH_OK;
+}
+
+egh_status egh_set_synthesis_frequencies(egh_ctx* ctx, const double* all_freq_hz, int32_t nall,
+                                         int32_t k0) {
+  if (!ctx || !all_freq_hz) return fail(ctx, EGH_EINVAL, "NULL argument");
+  CK(cudaSetDevice(ctx->dev));
+  if (nall < ctx->nf || k0 < 0 || k0 + ctx->nf > nall)
+    return fail(ctx, EGH_EINVAL, "the context's frequencies must be entries k0.. of the full list");
+  for (int k = 0; k < ctx->nf; ++k)
+    if (all_freq_hz[k0 + k] != ctx->freqs[k])
+      return fail(ctx, EGH_EINVAL, "the full list's entries k0.. differ from the context's frequencies");
+  const std::vector<double> f(all_freq_hz, all_freq_hz + nall);
+  const std::vector<float> w = synthesis_weights(f, ctx->dt, ctx->nt);
+  ctx->wsyn.assign(w.begin() + k0, w.begin() + k0 + ctx->nf);
+  CK(cudaMemcpy(ctx->w_dev, ctx->wsyn.data(), ctx->wsyn.size() * sizeof(float), cudaMemcpyHostToDevice));
   return EGH_OK;
 }
 

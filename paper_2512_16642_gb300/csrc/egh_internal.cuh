@@ -120,6 +120,8 @@ int gram_tc_splits(int nrec, int nf, long long G);
 cudaError_t make_ghb_tmap(CUtensorMap* tm, void* base, long long G, int nf, int nrec);
 cudaError_t launch_gram_tc(const CUtensorMap& tmap, int nrec, int nf, long long G, int splits,
                            float* part, int* err, cudaStream_t st);
+cudaError_t launch_gh_to_ghb(const float* gh, int nrec, int nf, long long G, __nv_bfloat16* ghb,
+                             cudaStream_t st);
 cudaError_t launch_gram_tc_finish(const float* part, int nrec, int nf, int splits, float2* Qh,
                                   cudaStream_t st);
 
@@ -133,6 +135,8 @@ cudaError_t launch_gram_finish(const float* part, int nrec, int nf, int splits, 
 cudaError_t launch_diag_sum(const float2* Qh, int nrec, int nf, double* d_sum, cudaStream_t st);
 cudaError_t launch_lambda_max(const float2* Qh, int nrec, int nf, double* d_lmax, cudaStream_t st);
 cudaError_t launch_add_mu_copy(float2* Qh, float2* Lh, int nrec, int nf, float mu, cudaStream_t st);
+cudaError_t launch_add_mu_copy_delta(float2* Qh, float2* Lh, int nrec, int nf, double mu_old,
+                                     double mu_new, cudaStream_t st);
 
 // ---- chol.cu ----------------------------------------------------------------------------------
 // piv64: FP64 diagonal and pivots (mixed precision)

@@ -374,4 +374,32 @@ cudaError_t launch_add_mu_copy(float2* Qh, float2* Lh, int nrec, int nf, float m
   return cudaGetLastError();
 }
 
+// The penalty of the Hessians changed from mu_old to mu_new: Qh's diagonal has mu_old removed
+// (when nonzero) and mu_new added, and Lh = Qh.  From mu_old = 0 the result is the one of
+// launch_add_mu_copy with mu_new, bit for bit.
+__global__ void k_set_mu_copy(float2* __restrict__ Qh, float2* __restrict__ Lh, long long n2,
+                              int nrec, float mu_old, float mu_new) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n2;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long local = t % ((long long)nrec * nrec);
+    float2 v = Qh[t];
+    if (local / nrec == local % nrec) {
+      if (mu_old != 0.f) v.x -= mu_old;
+      v.x += mu_new;
+      Qh[t] = v;
+    }
+    Lh[t] = v;
+  }
+}
+
+cudaError_t launch_add_mu_copy_delta(float2* Qh, float2* Lh, int nrec, int nf, double mu_old,
+                                     double mu_new, cudaStream_t st) {
+  const long long n2 = (long long)nf * nrec * nrec;
+  long long blocks = (n2 + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  count_launches(1);
+  k_set_mu_copy<<<(int)blocks, 256, 0, st>>>(Qh, Lh, n2, nrec, (float)mu_old, (float)mu_new);
+  return cudaGetLastError();
+}
+
 }  // namespace egh

@@ -80,6 +80,35 @@ cudaError_t make_ghb_tmap(CUtensorMap* tm, void* base, long long G, int nf, int 
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// The Gram's bf16 operands from FP32 transforms gh[nrec][nf][re/im][G]: hi = bf16(g),
+// lo = bf16(g - hi), blocked by 64 points as ghb[nf][G/64][hi/lo][nrec x re/im][64] (the layout the
+// transform's last chunk writes, from the same values).
+__global__ void k_gh_to_ghb(const float* __restrict__ gh, int nrec, int nf, long long G,
+                            __nv_bfloat16* __restrict__ ghb) {
+  const long long total = (long long)nrec * nf * 2 * G;
+  const long long rows = 2LL * nrec;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long p = t % G, c2 = (t / G) % (2LL * nf), r = t / (2LL * nf * G);
+    const float v = gh[t];
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
+    __nv_bfloat16* q = ghb + (((c2 >> 1) * (G >> 6) + (p >> 6)) * 2 * rows + 2 * r + (c2 & 1)) * 64 +
+                       (p & 63);
+    q[0] = h;
+    q[rows * 64] = l;
+  }
+}
+
+cudaError_t launch_gh_to_ghb(const float* gh, int nrec, int nf, long long G, __nv_bfloat16* ghb,
+                             cudaStream_t st) {
+  const long long total = (long long)nrec * nf * 2 * G;
+  const long long blocks = std::min<long long>((total + 255) / 256, 152LL * 16);
+  count_launches(1);
+  k_gh_to_ghb<<<(unsigned)blocks, 256, 0, st>>>(gh, nrec, nf, G, ghb);
+  return cudaGetLastError();
+}
+
 __device__ __forceinline__ void tma_load_5d(unsigned dst, const void* tmap, int c0, int c1, int c2,
                                             int c3, int c4, unsigned bar) {
   asm volatile(

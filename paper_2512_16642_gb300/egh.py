@@ -104,6 +104,11 @@ _SIGS = {
     "egh_release_green": ([_vp], ctypes.c_int),
     "egh_test_expire_wait": ([_vp, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
     "egh_set_refinement": ([_vp, ctypes.c_double], ctypes.c_int),
+    "egh_export_green": ([_vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp], ctypes.c_int),
+    "egh_import_green": ([_vp, _vp, _vp], ctypes.c_int),
+    "egh_diag_sum": ([_vp, _f64p], ctypes.c_int),
+    "egh_set_mu": ([_vp, ctypes.c_double, _vp], ctypes.c_int),
+    "egh_set_synthesis_frequencies": ([_vp, _f64p, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
     "egh_get_refinement": ([_vp, _f64p, _i32p], ctypes.c_int),
     "egh_server_test_expire_wait": ([_vp, ctypes.c_int32], ctypes.c_int),
     "egh_batch_create": ([ctypes.POINTER(_vp), ctypes.c_int32, ctypes.POINTER(_vp)], ctypes.c_int),
@@ -291,6 +296,31 @@ def egh_get_stats(ctx):
 EXPIRE_GREEN_TRANSFORM, EXPIRE_FD_RESIDENT, EXPIRE_DEBLUR_TRANSFORM = range(3)
 
 
+def egh_export_green(ctx, k0, nk, out, stream=None):
+    p, cu = _ptr(out)
+    _check(load().egh_export_green(ctx, int(k0), int(nk), p, _stream(stream, cu)), ctx)
+
+
+def egh_import_green(ctx, gh, stream=None):
+    p, cu = _ptr(gh)
+    _check(load().egh_import_green(ctx, p, _stream(stream, cu)), ctx)
+
+
+def egh_diag_sum(ctx):
+    out = ctypes.c_double(0.0)
+    _check(load().egh_diag_sum(ctx, ctypes.byref(out)), ctx)
+    return out.value
+
+
+def egh_set_mu(ctx, mu, stream=None):
+    _check(load().egh_set_mu(ctx, float(mu), _stream(stream, True)), ctx)
+
+
+def egh_set_synthesis_frequencies(ctx, all_freq_hz, k0):
+    f = np.ascontiguousarray(all_freq_hz, dtype=np.float64)
+    _check(load().egh_set_synthesis_frequencies(ctx, f.ctypes.data_as(_f64p), int(f.size), int(k0)), ctx)
+
+
 def egh_set_refinement(ctx, threshold):
     _check(load().egh_set_refinement(ctx, float(threshold)), ctx)
 
@@ -401,6 +431,29 @@ class Context:
 
     def test_expire_wait(self, kind, count=1):
         egh_test_expire_wait(self.h, kind, count)
+
+    def export_green(self, k0, nk, out, stream=None):
+        egh_export_green(self.h, k0, nk, out, stream)
+
+    def import_green(self, gh, stream=None):
+        egh_import_green(self.h, gh, stream)
+
+    def diag_sum(self):
+        return egh_diag_sum(self.h)
+
+    def set_mu(self, mu, stream=None):
+        egh_set_mu(self.h, mu, stream)
+
+    def set_synthesis_frequencies(self, all_freq_hz, k0):
+        egh_set_synthesis_frequencies(self.h, all_freq_hz, k0)
+
+    def transform_buffer(self, nr, nk):
+        """Zeroed device buffer [nr][nk][re/im][G] float32 for egh_export_green / egh_import_green."""
+        import torch
+
+        st = self.stats()
+        G = (st["nz_pad"] * st["pitch"] + 255) // 256 * 256
+        return torch.zeros((int(nr), int(nk), 2, G), dtype=torch.float32, device="cuda")
 
     def set_refinement(self, threshold):
         egh_set_refinement(self.h, threshold)
