@@ -68,6 +68,9 @@ def _args():
                         "deblur kernels alone at the layered shape (for profiling captures)")
     p.add_argument("--precision", choices=["mixed", "fp32"], default="mixed",
                    help="Hessian arithmetic: bf16x3 tensor-core Gram (mixed) or FP32 CUDA-core Gram")
+    p.add_argument("--sharded", action="store_true",
+                   help="run the sharded update (receiver-sharded Green solves, one exchange to "
+                        "frequency shards); the default whenever more than one rank runs")
     p.add_argument("--fd-kernel", type=int, choices=[0, 1, 2], default=0,
                    help="FD solver: 0 library choice, 1 resident, 2 one kernel per step")
     p.add_argument("--dft-chunk", type=int, default=1024,
@@ -725,6 +728,121 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
 
 
+def run_sharded(args):
+    """One model update of the layered workload split over the ranks (strong scaling): each rank
+    solves its block of receivers, one exchange moves the transforms to frequency blocks, the
+    penalty comes from one all-reduce, each rank factors and deblurs its frequencies and the
+    multipliers are summed over the ranks (paper_2512_16642_gb300.sharded).  value = build +
+    factor seconds per update (Green solves, exchange, Hessians, penalty, factorisation), the max
+    over ranks; the deblur and the end-to-end update from pinned host buffers ride along."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    from paper_2512_16642_gb300 import egh, sharded
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    c = synth.case_layered()
+    if args.slice:
+        c = synth.slice_case(c, nrec=args.slice_receivers, nt=args.slice_nt)
+        args.e2e_steps = 0
+    nr, ns, nt, nf = c.rec_ix.size, c.src_ix.size, c.nt, c.freqs.size
+    geom = {k: c[k] for k in ("nz", "nx", "dz", "dx", "nsponge", "sponge_R", "dt", "nt", "rec_iz",
+                              "rec_ix", "freqs")}
+    prec = egh.EGH_PREC_MIXED if args.precision == "mixed" else egh.EGH_PREC_FP32
+    shard = sharded.Shard(geom, rank, ws, precision=prec, dft_chunk=args.dft_chunk)
+    stream = torch.cuda.current_stream()
+    vel = torch.from_numpy(np.float32(c.vel_start)).cuda()
+    noise = synth.bandlimited_noise(np.random.default_rng(5), (ns, nr, nt), c.dt, 2.0, 10.0)
+    resid = torch.from_numpy(noise.astype(np.float32)).cuda()
+    mult = torch.empty_like(resid)
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def step(v, r, m):
+        e = [ev() for _ in range(3)]
+        e[0].record(stream)
+        sends = shard.green(v)
+        recvs = shard.receive_buffers()
+        if ws > 1:
+            sharded.exchange(sends, recvs, rank)
+        else:
+            recvs[0].copy_(sends[0])
+        shard.assemble(recvs)
+        d = torch.tensor([shard.hessian()], dtype=torch.float64, device="cuda")
+        if ws > 1:
+            dist.all_reduce(d)
+        shard.factor(float(d.item()), c.mu_alpha)
+        e[1].record(stream)
+        shard.deblur(r, m)
+        if ws > 1:
+            dist.all_reduce(m)
+        e[2].record(stream)
+        return e
+
+    for _ in range(args.warmup):
+        step(vel, resid, mult)
+    torch.cuda.synchronize()
+    _barrier(ws)
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    ctxs = [x for x in (shard.green_ctx, shard.hess_ctx) if x is not None]
+    l0 = ctxs[0].stats()["kernel_launches"]
+    t0, t1 = ev(), ev()
+    t0.record(stream)
+    recs = [step(vel, resid, mult) for _ in range(args.steps)]
+    t1.record(stream)
+    torch.cuda.synchronize()
+    _barrier(ws)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    launches = ctxs[0].stats()["kernel_launches"] - l0
+    bf = statistics.mean(e[0].elapsed_time(e[1]) for e in recs) / 1e3
+    deb = statistics.mean(e[1].elapsed_time(e[2]) for e in recs)
+    bf_max = _max_over_ranks(ws, bf)
+    ms_step = _max_over_ranks(ws, t0.elapsed_time(t1) / args.steps)
+    # end to end from pinned host buffers: the velocity and residuals copied in, the multipliers
+    # copied out, inside the timed span
+    e2e = None
+    if args.e2e_steps > 0:
+        v_host = torch.from_numpy(np.float32(c.vel_start)).pin_memory()
+        r_host = resid.cpu().pin_memory()
+        m_host = torch.empty_like(r_host).pin_memory()
+        times = []
+        for i in range(args.e2e_steps + 1):
+            torch.cuda.synchronize()
+            _barrier(ws)
+            a = time.perf_counter()
+            vel.copy_(v_host, non_blocking=True)
+            resid.copy_(r_host, non_blocking=True)
+            step(vel, resid, mult)
+            m_host.copy_(mult, non_blocking=True)
+            torch.cuda.synchronize()
+            if i > 0:
+                times.append(time.perf_counter() - a)
+        e2e_v = _max_over_ranks(ws, statistics.mean(times))
+        e2e = {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": int(v_host.numel() * 4 + r_host.numel() * 4),
+               "d2h_bytes_per_step": int(m_host.numel() * 4),
+               "note": "whole sharded update (build, factor and deblur) per rank from pinned host "
+                       "velocity and residuals to pinned host multipliers, max over ranks"}
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": bf_max, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False,
+            "scaling": "strong", "vs_baseline": None,
+            "dtype": "f32/bf16x3" if args.precision == "mixed" else "f32/bf16x3-transform",
+            "data": "synthetic",
+            "config": _workload(c, {"precision": args.precision, "parallelism": f"sharded{ws}",
+                                    "receiver_blocks": shard.rb, "frequency_blocks": shard.kb,
+                                    "residuals": "seeded band-limited noise 2-10 Hz"}),
+            "stages_ms": {"build_factor": bf * 1e3, "deblur": deb},
+            "deblur_sources_per_s": ns / (deb / 1e3),
+            "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks}), flush=True)
+    shard.close()
+
+
 def run_deblur(args):
     """The deblur kernels alone at the layered workload's shape (231 receivers, 26 frequencies
     3.0:0.2:8.0 Hz, 115 sources x 4000 samples), through a serving set so that no Green stage
@@ -766,6 +884,8 @@ def main():
         run_salt(args)
     elif args.workload == "deblur":
         run_deblur(args)
+    elif args.sharded or int(os.environ.get("WORLD_SIZE", "1")) > 1:
+        run_sharded(args)
     else:
         run_ours(args)
 
