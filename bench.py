@@ -63,6 +63,8 @@ def _args():
                    help="receivers of the profiling slice (231 gives the full-size Hessian)")
     p.add_argument("--slice-nt", type=int, default=1024, help="time steps of the profiling slice")
     p.add_argument("--no-serving", action="store_true", help="skip the serving-form measurement")
+    p.add_argument("--no-batched", action="store_true",
+                   help="skip the batched-form (salt, three patches) leg of the default run")
     p.add_argument("--workload", choices=["layered", "salt", "deblur"], default="layered",
                    help="layered (the benchmark workload), the batched salt-patch form, or the "
                         "deblur kernels alone at the layered shape (for profiling captures)")
@@ -247,6 +249,23 @@ def oracle_sample(c, green_steps=200, gram_receivers=None, deblur_sources=4):
             "sample": sample}
 
 
+def serving_error(serving):
+    """Relative L2 error of each kept serving request's multipliers against the FP64 oracle
+    (Cholesky of the set's Hessians, transform, solve, synthesis): part of the cpu_baseline leg."""
+    import numpy as np
+
+    import oracle
+
+    errs, L_cache = [], {}
+    for smp in serving["_samples"]:
+        Q, f, dt, nt_rec = serving["_sets"][smp["set"]]
+        if smp["set"] not in L_cache:
+            L_cache[smp["set"]] = oracle.cholesky(Q.astype(np.complex128))
+        ref = oracle.deblur(L_cache[smp["set"]], smp["resid"].astype(np.float64), f, dt, nt_ref=nt_rec)[0]
+        errs.append(float(np.linalg.norm(smp["mult"] - ref) / np.linalg.norm(ref)))
+    return errs
+
+
 def _workload(c, extra=None):
     if c.rec_ix.size == 231 and c.nt == 4000:
         name = ("layered-faulted 921x301 (padded 961x341), dx 10 m, 231 receivers, 115 sources, "
@@ -346,14 +365,15 @@ def serve_bench(torch, egh, precision, requests=240, seed=11):
     shapes = ((101, 20), (211, 27), (331, 33), (461, 40))
     dt, max_nt = 1e-3, 4096
     with egh.Server(24 << 30, slots=6, max_batch_sources=128, precision=precision) as sv:
-        ids = []
+        ids, sets_host = [], []
         for nrec, nf in shapes:
             A = torch.randn((nf, nrec, 2 * nrec), dtype=torch.complex64, device="cuda",
                             generator=torch.Generator(device="cuda").manual_seed(seed + nrec))
             Q = A @ A.conj().transpose(1, 2) / (2 * nrec)
             mu = 0.05 * torch.diagonal(Q, dim1=1, dim2=2).real.mean()
-            Q = Q + mu * torch.eye(nrec, device="cuda")
-            ids.append(sv.add_set(Q.cpu().numpy(), np.linspace(2.0, 10.0, nf), dt, 4000, max_nt))
+            Q = (Q + mu * torch.eye(nrec, device="cuda")).cpu().numpy()
+            ids.append(sv.add_set(Q, np.linspace(2.0, 10.0, nf), dt, 4000, max_nt))
+            sets_host.append((Q, np.linspace(2.0, 10.0, nf), dt, 4000))
         # a pool of pinned buffers, one per request in flight at most
         pool = 8
         maxb = 64 * 461 * 4000
@@ -391,6 +411,16 @@ def serve_bench(torch, egh, precision, requests=240, seed=11):
         rate = 0.7 * full["completed"] / full["span_s"]
         gaps = rng.exponential(1.0 / rate, size=requests)
         st = run(np.cumsum(gaps) - gaps[0])
+        # a seeded sample of requests of the two smaller sets, kept (inputs, results, Hessians)
+        # for the check against the FP64 oracle in the cpu_baseline leg
+        samples = []
+        for sid, ns, nt_d in [(0, 3, 2400), (1, 2, 3100), (0, 17, 2000), (1, 5, 4000)]:
+            nr = shapes[sid][0]
+            r = synth.bandlimited_noise(rng, (ns, nr, nt_d), dt, 2.0, 10.0).astype(np.float32)
+            rin = torch.from_numpy(r).pin_memory()
+            out = torch.empty_like(rin).pin_memory()
+            sv.wait(sv.submit(ids[sid], rin, out))
+            samples.append({"set": sid, "resid": r, "mult": out.numpy().copy()})
     return {"workload": "4 resident Hessian sets Nr 101/211/331/461, Nf 20/27/33/40 (synthetic HPD "
                         "A A^H/m + 0.05 mean diag I), Poisson arrivals at 70% of capacity, "
                         f"{requests} requests of U{{1..64}} sources x nt U{{2000..4000}}",
@@ -399,7 +429,58 @@ def serve_bench(torch, egh, precision, requests=240, seed=11):
             "p50_ms": st["p50_s"] * 1e3, "p99_ms": st["p99_s"] * 1e3, "mean_ms": st["mean_s"] * 1e3,
             "arrival_rate_per_s": rate, "capacity_sources_per_s": srcs / full["span_s"],
             "batches": st["batches"], "requests": st["completed"],
-            "peak_in_flight": st["peak_in_flight"], "peak_arena_bytes": st["peak_bytes_in_use"]}
+            "peak_in_flight": st["peak_in_flight"], "peak_arena_bytes": st["peak_bytes_in_use"],
+            "_sets": sets_host, "_samples": samples}
+
+
+def salt_bench(torch, egh, precision, ev, stream, steps=1, warmup=1):
+    """The batched form (three patches of the 1701x351 salt model, 161/257/341 receivers, nt 6000,
+    40 frequencies 2-10 Hz each, all 120 Hessians factored in one persistent launch under a CUDA
+    graph), as a leg of the default run: update seconds, the batched factorisation, and the Green
+    stage's rate on 12 B per receiver point-step."""
+    import numpy as np
+
+    import synth
+
+    c = synth.case_salt_patches()
+    prec = egh.EGH_PREC_MIXED if precision == "mixed" else egh.EGH_PREC_FP32
+    v = torch.from_numpy(np.float32(c.vel_true)).cuda()
+    ctxs = [egh.Context(c.nz, c.nx, c.dz, c.dx, c.nsponge, c.sponge_R, c.dt, c.nt,
+                        np.zeros(p.size, np.int32), p, c.freqs, precision=prec) for p in c.patches]
+    batch = egh.Batch(ctxs)
+    try:
+        def step():
+            e = [ev() for _ in range(3)]
+            e[0].record(stream)
+            for ctx in ctxs:
+                ctx.green(v)
+                ctx.hessian(egh.EGH_MU_REL_MEANDIAG, 1e-2)
+                ctx.release_green()
+            e[1].record(stream)
+            batch.factor()
+            e[2].record(stream)
+            torch.cuda.synchronize()
+            return e[0].elapsed_time(e[2]) / 1e3, e[1].elapsed_time(e[2])
+
+        for _ in range(warmup):
+            step()
+        res = [step() for _ in range(steps)]
+        ps = sum(ctx.stats()["point_steps"] for ctx in ctxs)
+        upd = statistics.mean(r[0] for r in res)
+        fac = statistics.mean(r[1] for r in res)
+        hbm, _ = _peaks()
+        gs = 12.0 * ps / (upd - fac / 1e3) / 1e9
+        return {"workload": "salt 1701x351 (padded 1741x391), three patches of 161/257/341 receivers, "
+                            "nt 6000, 40 frequencies 2-10 Hz each, mu 1e-2 mean diag",
+                "precision": precision, "update_build_factor_s": upd, "batched_factor_ms": fac,
+                "hessians": 120, "green_and_hessian_gbs": gs, "green_and_hessian_frac": gs / hbm,
+                "note": "Green stage + Hessians per patch (Green buffers released after each), then "
+                        "the 120 Hessians factored in one persistent launch (CUDA graph); "
+                        "12 B per receiver point-step"}
+    finally:
+        batch.close()
+        for ctx in ctxs:
+            ctx.close()
 
 
 def run_salt(args):
@@ -664,9 +745,31 @@ def run_ours(args):
                 hf.append(e0.elapsed_time(e1))
             other = {"precision": "fp32" if alt == egh.EGH_PREC_FP32 else "mixed",
                      "hessian_factor_ms": min(hf)}
+            # the whole update in the other arithmetic (Green stage, Hessians, factors, deblur)
+            m2 = torch.empty_like(resid)
+            e = [ev() for _ in range(4)]
+            e[0].record(stream)
+            ctx2.green(v_start)
+            e[1].record(stream)
+            ctx2.hessian(egh.EGH_MU_REL_MEANDIAG, c.mu_alpha)
+            ctx2.factor()
+            e[2].record(stream)
+            ctx2.deblur(resid, m2)
+            e[3].record(stream)
+            torch.cuda.synchronize()
+            other.update({"update_build_factor_s": e[0].elapsed_time(e[2]) / 1e3,
+                          "green_ms": e[0].elapsed_time(e[1]), "deblur_ms": e[2].elapsed_time(e[3]),
+                          "deblur_sources_per_s": ns / (e[2].elapsed_time(e[3]) / 1e3),
+                          "mult_rel_diff_vs_headline": float((m2 - mult).norm() / mult.norm())})
+            del m2
     variants = None
     if not args.slice and not args.no_serving:
         variants = variants_bench(torch, egh, ctx, c, v_start, resid, mult, stream, ev)
+    batched = None
+    if not args.slice and not args.no_batched and ws == 1:
+        ctx.close()  # the salt workload's largest patch needs the device memory
+        torch.cuda.empty_cache()
+        batched = salt_bench(torch, egh, args.precision, ev, stream)
     line = {
         "metric": METRIC, "value": bf_s_max / ws, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
@@ -725,6 +828,17 @@ def run_ours(args):
         line["cpu_baseline"] = {"value": ob["build_factor_s"], "unit": UNIT, "cores": ob["cores"],
                                 "kind": "oracle", "sample": ob["sample"],
                                 "deblur_sources_per_s": ob["sources_per_s"]}
+        if serving is not None:
+            errs = serving_error(serving)
+            serving["rel_err_vs_oracle"] = errs
+            serving["max_rel_err_vs_oracle"] = max(errs)
+            serving["error_note"] = ("multipliers of 4 kept requests (sets of 101 and 211 receivers) "
+                                     "against the FP64 oracle; tolerance 1e-3")
+    if serving is not None:
+        serving.pop("_sets", None)
+        serving.pop("_samples", None)
+    if batched is not None:
+        line["batched"] = batched
     print(json.dumps(line), flush=True)
 
 

@@ -159,6 +159,17 @@ egh_status dalloc(egh_ctx* ctx, void** p, size_t bytes, const char* what) {
   return EGH_OK;
 }
 
+// The device address of a page-locked host buffer mapped into the device's address space, or
+// null (pageable memory, or no mapping).
+void* mapped_host(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 // 1 = device (or managed) memory, 0 = host memory (pinned or pageable).
 int pointer_is_device(const void* p) {
   cudaPointerAttributes a;
@@ -1041,8 +1052,14 @@ static egh_status deblur_common(egh_ctx* ctx, const float* resid, int32_t ns, in
   egh_status s = ensure_twiddles(ctx, nt_d, stream);
   if (s) return s;
   const size_t nbytes = (size_t)ntr * nt_d * sizeof(float);
+  // Page-locked host buffers are mapped into the device's address space: the forward transform
+  // reads the residuals and the synthesis writes the multipliers through the mapping (over the
+  // CPU-GPU link, no staging copy).  Pageable host memory is staged through device buffers.
   const float* din = resid;
-  if (!dev_in) {
+  const float* in_map = dev_in ? nullptr : static_cast<const float*>(mapped_host(resid));
+  if (in_map) {
+    din = in_map;
+  } else if (!dev_in) {
     if ((s = ensure_buf(ctx, (void**)&ctx->io_in, &ctx->io_in_cap, nbytes, stream, "resid staging")))
       return s;
     CK(cudaMemcpyAsync(ctx->io_in, resid, nbytes, cudaMemcpyHostToDevice, stream));
@@ -1056,7 +1073,10 @@ static egh_status deblur_common(egh_ctx* ctx, const float* resid, int32_t ns, in
     D = ctx->Dh;
   }
   float* dout = mult;
-  if (!X && !dev_out) {
+  float* out_map = (!X && !dev_out) ? static_cast<float*>(mapped_host(mult)) : nullptr;
+  if (out_map) {
+    dout = out_map;
+  } else if (!X && !dev_out) {
     if ((s = ensure_buf(ctx, (void**)&ctx->io_out, &ctx->io_out_cap, nbytes, stream,
                         "mult staging")))
       return s;
@@ -1100,7 +1120,7 @@ static egh_status deblur_common(egh_ctx* ctx, const float* resid, int32_t ns, in
   ctx->ev_rec[3] = true;
   ctx->st.deblur_sources = ns;
   if (!X && !dev_out) {
-    CK(cudaMemcpyAsync(mult, dout, nbytes, cudaMemcpyDeviceToHost, stream));
+    if (!out_map) CK(cudaMemcpyAsync(mult, dout, nbytes, cudaMemcpyDeviceToHost, stream));
     CK(cudaStreamSynchronize(stream));
   } else if (!dev_in) {
     CK(cudaStreamSynchronize(stream));
