@@ -285,21 +285,28 @@ def _workload(c, extra=None):
 def gram_roofline(precision, nr, nf, npts, c, ms, peak, kind):
     """The Gram kernel against the tensor peak (mixed) or as FP32 CUDA-core work (fp32).  Issued
     tensor work: 64-receiver panel pairs on and above the diagonal, each 128 x 128 x G per
-    frequency, 3 bf16 products (hi hi, hi lo, lo hi); algorithmic work: the Hermitian half of
-    8 Nf Nr^2 G real flops of the complex Gram."""
+    frequency (G: the grid sum's length at the device pitch), 3 bf16 products (hi hi, hi lo,
+    lo hi).  Algorithmic work: the Hermitian half of the complex Gram over the padded grid's
+    Nx = NZ x NX points, 8 Nf Nr^2 Nx (Nr + 1) / (2 Nr) real flops, against the bf16 peak and
+    against the bf16x3 rate (a third of it: three products per flop of the FP32-class result)."""
     NZ, NX = c.nz + 2 * c.nsponge, c.nx + 2 * c.nsponge
     PX = max(64, -(-(NX + 4) // 64) * 64)  # row pitch of the device levels
     G = -(-(NZ * PX) // 256) * 256  # padded point count the Gram sums over
+    Nx = NZ * NX
     n64 = -(-nr // 64)
     issued = n64 * (n64 + 1) / 2 * 128 * 128 * 2 * 3 * G * nf
-    alg = 8.0 * nf * nr * nr * G * (nr + 1) / (2 * nr)
+    alg = 8.0 * nf * nr * nr * Nx * (nr + 1) / (2 * nr)
+    alg_tf = alg / (ms * 1e-3) / 1e12
     out = {"kernel": "k_gram_tc (bf16x3 tcgen05 Gram)" if precision == "mixed" else "k_gram_partial (FP32)",
-           "ms": ms, "algorithmic_tflops": alg / (ms * 1e-3) / 1e12}
+           "ms": ms, "algorithmic_tflops": alg_tf, "algorithmic_flops": alg, "nx_points": Nx}
     if precision == "mixed":
         out.update({"bound": "tensor", "achieved": issued / (ms * 1e-3) / 1e12, "peak": peak,
                     "peak_kind": kind, "unit": "TFLOP/s", "frac": issued / (ms * 1e-3) / 1e12 / peak,
-                    "note": "achieved = issued bf16 MMA flops (3 products) / kernel time (CUDA events "
-                            "around the launch inside egh_hessian)"})
+                    "algorithmic_frac_of_bf16": alg_tf / peak,
+                    "algorithmic_frac_of_bf16x3": alg_tf / (peak / 3.0),
+                    "note": "achieved = issued bf16 MMA flops (3 products, padded panels and pitch) / "
+                            "kernel time (CUDA events around the launch inside egh_hessian); "
+                            "algorithmic = Hermitian half over the Nx grid points"})
     return out
 
 
