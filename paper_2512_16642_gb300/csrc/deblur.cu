@@ -623,15 +623,11 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-// X = W^H (W D) through the scratch Y (both n x ld per frequency); D and X may alias.  With kl,
-// only the nk frequencies kl[0 .. nk-1] (device list); else all nk = nf.
-cudaError_t launch_inverse_solve(const float2* Wh, int n, int nk, const float2* D, float2* Y,
-                                 float2* X, int ld, cudaStream_t st, const int* kl) {
-  if (nk < 1) return cudaSuccess;
-  const dim3 grid((ld + CG_T - 1) / CG_T, (n + CG_T - 1) / CG_T, nk);
-  count_launches(2);
-  k_cgemm<false><<<grid, 256, 0, st>>>(Wh, n, D, ld, Y, kl);
-  k_cgemm<true><<<grid, 256, 0, st>>>(Wh, n, Y, ld, X, kl);
+// Q^{-1} = W^H W per frequency (dense Hermitian n x n), the operator of the tensor-core solve.
+cudaError_t launch_gram_inverse(const float2* Wh, int n, int nf, float2* Ph, cudaStream_t st) {
+  const dim3 grid((n + CG_T - 1) / CG_T, (n + CG_T - 1) / CG_T, nf);
+  count_launches(1);
+  k_cgemm<true><<<grid, 256, 0, st>>>(Wh, n, Wh, n, Ph, nullptr);
   return cudaGetLastError();
 }
 

@@ -73,12 +73,14 @@ struct egh_ctx {
   float2 *Qh = nullptr, *Lh = nullptr, *tw = nullptr;
   unsigned char* twt_deb = nullptr;  // the deblur transform's twiddle tiles (tw_len levels)
   unsigned char* tws_deb = nullptr;  // the synthesis twiddle tiles (tw_len samples)
-  float2* Wh = nullptr;  // mixed precision: W = L^{-1} per frequency (solves as products)
+  float2* Wh = nullptr;  // mixed precision: W = L^{-1} per frequency
+  float2* Ph = nullptr;  // mixed precision: Q^{-1} = W^H W per frequency (solves as one product)
   double* fro2 = nullptr;  // mixed precision: ||Q_k||_F^2 of the last factorisation
   int* kref = nullptr;     // mixed precision: frequencies whose solves are refined (device list)
   int nref = 0;            // their number
   double refine_cond = kRefineCond;   // refinement threshold on the bound ||Q_k||_F / mu
   std::vector<double> cond_bound;     // the bound per frequency (last factorisation)
+  std::vector<double> cond_host;      // its inputs: ||Q_k||_F^2, then 1 / lambda_min estimates
   std::vector<int> refined;           // 1 where the solves are refined
   int tw_len = 0;
   cudaStream_t side = nullptr;                 // the transform's stream inside egh_green (low priority)
@@ -125,6 +127,7 @@ struct egh_batch {
   int* status = nullptr;       // device, one per item
   cudaStream_t cap = nullptr;  // capture stream
   cudaGraphExec_t graph = nullptr;
+  int graph_launches = 0;      // kernels in one replay of the graph
   cudaEvent_t ev[2] = {};
   std::string err;
 };
@@ -300,7 +303,7 @@ cudaError_t zero_snap_slot(egh_ctx* ctx, int j, cudaStream_t st) {
 }
 
 void free_all(egh_ctx* c) {
-  void* ptrs[] = {c->fro2, c->kref, c->xbuf, c->rflags, c->tws_deb, c->twt_deb, c->twt_bl, c->Wh, c->Dr, c->Rr, c->coef, c->lev, c->snap, c->twt, c->gh, c->ghb, c->part, c->Qh, c->Lh, c->tw, c->w_dev,
+  void* ptrs[] = {c->Ph, c->fro2, c->kref, c->xbuf, c->rflags, c->tws_deb, c->twt_deb, c->twt_bl, c->Wh, c->Dr, c->Rr, c->coef, c->lev, c->snap, c->twt, c->gh, c->ghb, c->part, c->Qh, c->Lh, c->tw, c->w_dev,
                   c->rec_pts, c->status, c->dsum, c->lmax, c->vchk, c->d_err, c->vel_stage, c->Dh,
                   c->io_in, c->io_out};
   for (void* p : ptrs)
@@ -389,6 +392,39 @@ egh_status fd_chunk_steps(egh_ctx* ctx, int ta, int t0, int t1, int sbase, int n
   }
   CK(cudaGraphLaunch(it->second, ctx->fdst));
   count_launches(t1 - ta);
+  return EGH_OK;
+}
+
+// Selective refinement of the mixed precisions, step 1 (queued on `stream` after the inverse
+// factors): ||Q_k||_F^2 and the power estimate of 1 / lambda_min(Q_k), copied to the host buffer.
+egh_status refine_plan(egh_ctx* ctx, cudaStream_t stream) {
+  if (!ctx->Wh) return EGH_OK;
+  CK(launch_fro2(ctx->Qh, ctx->nrec, ctx->nf, ctx->fro2, stream));
+  CK(launch_inv_power(ctx->Wh, ctx->nrec, ctx->nf, ctx->fro2 + ctx->nf, stream));
+  ctx->cond_host.assign(2 * ctx->nf, 0.0);
+  CK(cudaMemcpyAsync(ctx->cond_host.data(), ctx->fro2, 2 * ctx->nf * sizeof(double),
+                     cudaMemcpyDeviceToHost, stream));
+  return EGH_OK;
+}
+
+// Step 2 (after the stream is synchronised): the solves of frequency k get one refinement step
+// when its condition bound (||Q_k||_F over the smaller of mu and the power estimate of
+// lambda_min) exceeds the threshold; the list goes to the device.
+egh_status refine_list(egh_ctx* ctx) {
+  if (!ctx->Wh) return EGH_OK;
+  ctx->cond_bound.assign(ctx->nf, 0.0);
+  ctx->refined.assign(ctx->nf, 0);
+  std::vector<int> list;
+  for (int k = 0; k < ctx->nf; ++k) {
+    ctx->cond_bound[k] = cond_bound(ctx->cond_host[k], ctx->cond_host[ctx->nf + k], ctx->mu);
+    if (ctx->cond_bound[k] > ctx->refine_cond) {
+      list.push_back(k);
+      ctx->refined[k] = 1;
+    }
+  }
+  ctx->nref = (int)list.size();
+  if (!list.empty())
+    CK(cudaMemcpy(ctx->kref, list.data(), list.size() * sizeof(int), cudaMemcpyHostToDevice));
   return EGH_OK;
 }
 
@@ -551,6 +587,7 @@ egh_status egh_create(const egh_config* cfg, egh_ctx** out) {
   ALLOC(ctx->Lh, (size_t)c.nfreq * c.nrec * c.nrec * sizeof(float2), "Lh");
   if (prec_mixed(ctx->prec)) {
     ALLOC(ctx->Wh, (size_t)c.nfreq * c.nrec * c.nrec * sizeof(float2), "inverse factors");
+    ALLOC(ctx->Ph, (size_t)c.nfreq * c.nrec * c.nrec * sizeof(float2), "inverse Hessians");
     ALLOC(ctx->fro2, (size_t)2 * c.nfreq * sizeof(double), "condition estimates");
     ALLOC(ctx->kref, (size_t)c.nfreq * sizeof(int), "refined frequencies");
   }
@@ -990,37 +1027,17 @@ egh_status egh_factor(egh_ctx* ctx, int32_t* bad_freq, void* stream_) {
                   prec_mixed(ctx->prec) ? 1 : 0));
   if (ctx->Wh) {
     CK(launch_trtri(ctx->Lh, ctx->nrec, ctx->nf, ctx->Wh, stream));
-    CK(launch_fro2(ctx->Qh, ctx->nrec, ctx->nf, ctx->fro2, stream));
-    CK(launch_inv_power(ctx->Wh, ctx->nrec, ctx->nf, ctx->fro2 + ctx->nf, stream));
+    CK(launch_gram_inverse(ctx->Wh, ctx->nrec, ctx->nf, ctx->Ph, stream));
   }
+  egh_status rs = refine_plan(ctx, stream);  // queues its kernels; reads them after the sync
+  if (rs) return rs;
   CK(cudaEventRecord(ctx->ev[5], stream));
   ctx->ev_rec[2] = true;
   std::vector<int> stv(ctx->nf);
-  std::vector<double> fro2(2 * ctx->nf, 0.0);
   CK(cudaMemcpyAsync(stv.data(), ctx->status, stv.size() * sizeof(int), cudaMemcpyDeviceToHost,
                      stream));
-  if (ctx->Wh)
-    CK(cudaMemcpyAsync(fro2.data(), ctx->fro2, fro2.size() * sizeof(double), cudaMemcpyDeviceToHost,
-                       stream));
   CK(cudaStreamSynchronize(stream));
-  if (ctx->Wh) {
-    // selective refinement: the solves of frequency k get one refinement step when its condition
-    // bound (||Q_k||_F over the smaller of mu and the power estimate of lambda_min) exceeds the
-    // threshold
-    ctx->cond_bound.assign(ctx->nf, 0.0);
-    ctx->refined.assign(ctx->nf, 0);
-    std::vector<int> list;
-    for (int k = 0; k < ctx->nf; ++k) {
-      ctx->cond_bound[k] = cond_bound(fro2[k], fro2[ctx->nf + k], ctx->mu);
-      if (ctx->cond_bound[k] > ctx->refine_cond) {
-        list.push_back(k);
-        ctx->refined[k] = 1;
-      }
-    }
-    ctx->nref = (int)list.size();
-    if (!list.empty())
-      CK(cudaMemcpy(ctx->kref, list.data(), list.size() * sizeof(int), cudaMemcpyHostToDevice));
-  }
+  if ((rs = refine_list(ctx))) return rs;
   for (int k = 0; k < ctx->nf; ++k)
     if (stv[k]) {
       if (bad_freq) *bad_freq = k;
@@ -1092,29 +1109,29 @@ static egh_status deblur_common(egh_ctx* ctx, const float* resid, int32_t ns, in
   if (!diag && prec_mixed(ctx->prec) &&
       (s = ensure_buf(ctx, (void**)&ctx->Rr, &ctx->Rr_cap, dbytes, stream, "solve scratch")))
     return s;
-  if (refine) {
-    // one step of iterative refinement: residual in FP64, correction solved with the FP32 factors
-    if ((s = ensure_buf(ctx, (void**)&ctx->Dr, &ctx->Dr_cap, dbytes, stream, "refinement rhs")))
-      return s;
-    CK(cudaMemcpyAsync(ctx->Dr, D, dbytes, cudaMemcpyDeviceToDevice, stream));
-  }
+  if (refine &&  // the refinement residual
+      (s = ensure_buf(ctx, (void**)&ctx->Dr, &ctx->Dr_cap, dbytes, stream, "refinement residual")))
+    return s;
+  float2* Xs = D;  // the solutions the synthesis reads
   if (diag) {
     CK(launch_diag_solve(ctx->Qh, ctx->nrec, ctx->nf, D, ns, stream));
   } else if (prec_mixed(ctx->prec)) {
-    // X = W^H W D (products with the explicit inverse factor), residual D - Q X in FP64, the
-    // correction solved the same way
-    CK(launch_inverse_solve(ctx->Wh, ctx->nrec, ctx->nf, D, ctx->Rr, D, ns, stream));
-    if (refine) {  // the frequencies whose condition bound asks for it
-      CK(launch_resid(ctx->Qh, ctx->nrec, ctx->nref, D, ctx->Dr, ns, ctx->Rr,
+    // Y = Q^{-1} D, one product on the tensor cores; at the frequencies whose condition bound asks
+    // for it, the residual R = D - Q Y to FP64-class accuracy and the correction Y += Q^{-1} R
+    float2* Y = ctx->Rr;
+    CK(launch_cmm_tc(ctx->Ph, ctx->nrec, ctx->nf, D, ns, Y, nullptr, ctx->d_err, stream));
+    if (refine) {
+      CK(launch_resid(ctx->Qh, ctx->nrec, ctx->nref, Y, D, ns, ctx->Dr,
                       ctx->prec == EGH_PREC_MIXED_FP64, stream, ctx->kref));
-      CK(launch_inverse_solve(ctx->Wh, ctx->nrec, ctx->nref, ctx->Rr, ctx->Dr, ctx->Rr, ns, stream,
-                              ctx->kref));
-      CK(launch_add_correction(D, ctx->Rr, ntr, ctx->nref, stream, ctx->kref));
+      CK(launch_cmm_tc(ctx->Ph, ctx->nrec, ctx->nref, ctx->Dr, ns, D, ctx->kref, ctx->d_err, stream));
+      CK(launch_add_correction(Y, D, ntr, ctx->nref, stream, ctx->kref));
     }
+    Xs = Y;
+    if (X) CK(cudaMemcpyAsync(X, Y, dbytes, cudaMemcpyDeviceToDevice, stream));
   } else {
     CK(launch_trsm(ctx->Lh, ctx->nrec, ctx->nf, D, ns, stream));
   }
-  if (!X) CK(launch_synth(D, ctx->nrec, ns, ns, 0, ctx->nf, ctx->w_dev, ctx->tw, nt_d, dout, stream,
+  if (!X) CK(launch_synth(Xs, ctx->nrec, ns, ns, 0, ctx->nf, ctx->w_dev, ctx->tw, nt_d, dout, stream,
                            ctx->tws_deb, ctx->d_err));
   CK(cudaEventRecord(ctx->ev[7], stream));
   ctx->ev_rec[3] = true;
@@ -1494,8 +1511,10 @@ static cudaError_t batch_enqueue(egh_batch* b, int threads, cudaStream_t st) {
   if ((e = launch_potrf_many(b->items, b->count, b->nmax, std::min(b->count, 2 * 152), threads,
                              b->piv64, st)))
     return e;
-  for (egh_ctx* c : b->ctxs)
+  for (egh_ctx* c : b->ctxs) {
     if (c->Wh && (e = launch_trtri(c->Lh, c->nrec, c->nf, c->Wh, st))) return e;
+    if (c->Ph && (e = launch_gram_inverse(c->Wh, c->nrec, c->nf, c->Ph, st))) return e;
+  }
   return cudaSuccess;
 }
 
@@ -1511,6 +1530,7 @@ egh_status egh_batch_factor(egh_batch* b, int32_t* bad_ctx, int32_t* bad_freq, v
     // launch shape: time each block size on these matrices and keep the fastest; then capture
     // the copies and the launch once as a CUDA graph
     float best = 1e30f;
+    const long long l0 = launches_so_far();
     for (int th : {256, 512, 1024}) {
       float ms = 0.f;
       for (int rep = 0; rep < 2; ++rep) {
@@ -1525,10 +1545,12 @@ egh_status egh_batch_factor(egh_batch* b, int32_t* bad_ctx, int32_t* bad_freq, v
         b->threads = th;
       }
     }
-    count_launches(-6);  // tuning launches are not part of the factorisation
+    count_launches(-(int)(launches_so_far() - l0));  // tuning launches are not part of the factorisation
+    const long long l1 = launches_so_far();
     BCK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = batch_enqueue(b, b->threads, b->cap);
-    count_launches(-1);  // counted at each replay
+    b->graph_launches = (int)(launches_so_far() - l1);
+    count_launches(-b->graph_launches);  // counted at each replay
     cudaGraph_t g = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(b->cap, &g);
     if (e == cudaSuccess) e = e2;
@@ -1537,10 +1559,18 @@ egh_status egh_batch_factor(egh_batch* b, int32_t* bad_ctx, int32_t* bad_freq, v
     if (e != cudaSuccess) return bfail(b, EGH_ECUDA, std::string("batch graph: ") + cudaGetErrorString(e));
   }
   BCK(cudaGraphLaunch(b->graph, stream));
-  count_launches(1);
+  count_launches(b->graph_launches);
+  for (egh_ctx* c : b->ctxs) {  // the selective refinement's bounds of every mixed context
+    const egh_status rs = refine_plan(c, stream);
+    if (rs) return bfail(b, rs, c->err);
+  }
   std::vector<int> stv(b->count);
   BCK(cudaMemcpyAsync(stv.data(), b->status, sizeof(int) * b->count, cudaMemcpyDeviceToHost, stream));
   BCK(cudaStreamSynchronize(stream));
+  for (egh_ctx* c : b->ctxs) {
+    const egh_status rs = refine_list(c);
+    if (rs) return bfail(b, rs, c->err);
+  }
   int o = 0;
   for (int i = 0; i < (int)b->ctxs.size(); ++i) {
     egh_ctx* c = b->ctxs[i];

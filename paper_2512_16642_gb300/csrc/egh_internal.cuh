@@ -159,11 +159,15 @@ cudaError_t launch_trace_dft(const float* resid, int ntr, int nt_d, int nf, int 
                              int s0, float2* Dh, cudaStream_t st, const unsigned char* twt,
                              int* err, int expire = 0);
 cudaError_t launch_trsm(const float2* Lh, int n, int nf, float2* Dh, int ns, cudaStream_t st);
-// W = L^{-1} per frequency; X = W^H (W D) with scratch Y, for the nk frequencies of the device
-// list kl (all nk = nf when kl is null)
+// W = L^{-1} per frequency
 cudaError_t launch_trtri(const float2* Lh, int n, int nf, float2* Wh, cudaStream_t st);
-cudaError_t launch_inverse_solve(const float2* Wh, int n, int nk, const float2* D, float2* Y,
-                                 float2* X, int ld, cudaStream_t st, const int* kl = nullptr);
+// Q^{-1}_k = W_k^H W_k (dense) from the inverse factors
+cudaError_t launch_gram_inverse(const float2* Wh, int n, int nf, float2* Ph, cudaStream_t st);
+// C_k = A_k B_k (complex, A_k n x n, B_k and C_k n x ld, row-major; C must not alias B) on the
+// tensor cores with FP32-class products (three-term bf16 splits), for the nk frequencies of the
+// device list kl (all when null); err: the flag a bounded wait sets (solve_tc.cu)
+cudaError_t launch_cmm_tc(const float2* A, int n, int nk, const float2* B, int ld, float2* C,
+                          const int* kl, int* err, cudaStream_t st);
 // diagonal-Hessian baseline: D_k[r][s] /= Q_k[r][r]
 cudaError_t launch_diag_solve(const float2* Qh, int n, int nf, float2* Dh, int ns, cudaStream_t st);
 // refinement residual R = D - Q X: FP64 arithmetic (fp64) or the compensated FP32 dot product;

@@ -133,15 +133,7 @@ __device__ __forceinline__ void tma_load_5d(unsigned dst, const void* tmap, int 
 constexpr int GC_J = 8 * (GC_P / GC_K);  // stages per TMEM accumulation block (96 accumulations)
 
 // K-major shared-memory descriptor of the 64-byte swizzle (8-row groups 512 bytes apart)
-__device__ __forceinline__ uint64_t sdesc_sw64(unsigned saddr) {
-  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
-  d |= (uint64_t)1 << 16;
-  d |= (uint64_t)(512 >> 4) << 32;
-  d |= (uint64_t)1 << 46;
-  d |= (uint64_t)4 << 61;
-  return d;
-}
-__device__ __forceinline__ uint64_t gc_desc(unsigned saddr) { return sdesc_sw64(saddr); }
+__device__ __forceinline__ uint64_t gc_desc(unsigned saddr) { return tc::sdesc_sw64(saddr); }
 
 __global__ void __launch_bounds__(288)
     k_gram_tc(const __grid_constant__ CUtensorMap tmap, int nrec, long long split_len, long long G,

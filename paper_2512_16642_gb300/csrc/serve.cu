@@ -88,6 +88,7 @@ struct HSet {
   int nrec = 0, nf = 0, tw_len = 0;
   float2 *Qh = nullptr, *Lh = nullptr, *tw = nullptr;
   float2* Wh = nullptr;  // mixed precision: W = L^{-1}
+  float2* Ph = nullptr;  // mixed precision: Q^{-1} = W^H W
   int* kref = nullptr;   // mixed precision: frequencies whose solves are refined (device list)
   int nref = 0;
   unsigned char* twt = nullptr;  // tensor-core transform twiddle tiles (tw_len levels)
@@ -214,27 +215,28 @@ cudaError_t run_batch(Server* sv, Batch* b, const HSet& h, int expire) {
       return e;
     s0 += r->ns;
   }
+  float2* Xs = D;  // the solutions the synthesis reads
   if (prec_mixed(sv->prec)) {
-    float2* Dr = D + dsz;
+    // Y = Q^{-1} D on the tensor cores; at the frequencies whose condition bound asks for it, the
+    // residual R = D - Q Y to FP64-class accuracy and the correction Y += Q^{-1} R
+    float2* Y = D + dsz;
     float2* R = D + 2 * dsz;
-    if (h.nref > 0 &&
-        (e = cudaMemcpyAsync(Dr, D, dsz * sizeof(float2), cudaMemcpyDeviceToDevice, st)))
-      return e;
-    if ((e = launch_inverse_solve(h.Wh, h.nrec, h.nf, D, R, D, ld, st))) return e;
-    if (h.nref > 0) {  // the frequencies whose condition bound asks for refinement
-      if ((e = launch_resid(h.Qh, h.nrec, h.nref, D, Dr, ld, R, sv->prec == EGH_PREC_MIXED_FP64, st,
+    if ((e = launch_cmm_tc(h.Ph, h.nrec, h.nf, D, ld, Y, nullptr, err, st))) return e;
+    if (h.nref > 0) {
+      if ((e = launch_resid(h.Qh, h.nrec, h.nref, Y, D, ld, R, sv->prec == EGH_PREC_MIXED_FP64, st,
                             h.kref)))
         return e;
-      if ((e = launch_inverse_solve(h.Wh, h.nrec, h.nref, R, Dr, R, ld, st, h.kref))) return e;
-      if ((e = launch_add_correction(D, R, (long long)h.nrec * ld, h.nref, st, h.kref))) return e;
+      if ((e = launch_cmm_tc(h.Ph, h.nrec, h.nref, R, ld, D, h.kref, err, st))) return e;
+      if ((e = launch_add_correction(Y, D, (long long)h.nrec * ld, h.nref, st, h.kref))) return e;
     }
+    Xs = Y;
   } else {
     if ((e = launch_trsm(h.Lh, h.nrec, h.nf, D, ld, st))) return e;
   }
   s0 = 0;
   for (Request* r : b->reqs) {
     float* dout = reinterpret_cast<float*>(sv->arena_base + r->off_out);
-    if ((e = launch_synth(D, h.nrec, r->ns, ld, s0, h.nf, h.w, h.tw, r->nt_d, dout, st, h.tws,
+    if ((e = launch_synth(Xs, h.nrec, r->ns, ld, s0, h.nf, h.w, h.tw, r->nt_d, dout, st, h.tws,
                           err)))
       return e;
     if ((e = cudaMemcpyAsync(r->mult, dout, r->bytes, cudaMemcpyDeviceToHost, st))) return e;
@@ -451,6 +453,7 @@ egh_status egh_server_add_set(egh_server* sv, int32_t nrec, int32_t nfreq, const
   auto cleanup = [&]() {
     cudaFree(d_cond);
     cudaFree(h.kref);
+    cudaFree(h.Ph);
     cudaFree(h.twt);
     cudaFree(h.tws);
     cudaFree(h.Wh);
@@ -485,6 +488,8 @@ egh_status egh_server_add_set(egh_server* sv, int32_t nrec, int32_t nfreq, const
   if (!e && prec_mixed(sv->prec)) {
     e = cudaMalloc(&h.Wh, qn * sizeof(float2));
     if (!e) e = launch_trtri(h.Lh, nrec, nfreq, h.Wh, st);
+    if (!e) e = cudaMalloc(&h.Ph, qn * sizeof(float2));
+    if (!e) e = launch_gram_inverse(h.Wh, nrec, nfreq, h.Ph, st);
     if (!e) e = cudaMalloc(&d_cond, 2 * nfreq * sizeof(double));
     if (!e) e = launch_fro2(h.Qh, nrec, nfreq, d_cond, st);
     if (!e) e = launch_inv_power(h.Wh, nrec, nfreq, d_cond + nfreq, st);
@@ -681,6 +686,7 @@ void egh_server_destroy(egh_server* sv) {
   for (auto& s : sv->streams) cudaStreamDestroy(s);
   for (HSet& h : sv->sets) {
     cudaFree(h.kref);
+    cudaFree(h.Ph);
     cudaFree(h.twt);
     cudaFree(h.tws);
     cudaFree(h.Wh);

@@ -123,6 +123,17 @@ __device__ __forceinline__ uint64_t sdesc_sw128(unsigned saddr) {
   return d;
 }
 
+// K-major, 64-byte swizzle (rows of 64 bytes; the 16-byte chunk c of row r at c ^ ((r / 2) % 4)),
+// stride between 8-row atoms 512 bytes
+__device__ __forceinline__ uint64_t sdesc_sw64(unsigned saddr) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(512 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)4 << 61;
+  return d;
+}
+
 // shared-memory matrix descriptor with explicit leading/stride byte offsets, 128-byte swizzle.
 // K-major: lbo unused, sbo = bytes between 8-row groups.  MN-major: lbo = bytes between
 // 64-element (128-byte) atoms along M/N, sbo = bytes between 8-row groups along K.

@@ -242,6 +242,9 @@ def test_selective_refinement_small(small):
     err = {n: np.array([rel(X[n][k], Xe[k]) for k in range(nf)]) for n in X}
     print("cond", cond, "bound", bound, "err", err)
     assert np.all(err["all"] <= 1e-4), err["all"]
+    # the one product with Q^{-1} on the tensor cores (three-term bf16 splits): FP32-class, its
+    # error a few 1e-8 times the condition number (2e-5 at cond 1838 with FP32 CUDA-core products)
+    assert np.all(err["none"] <= 4e-8 * cond), (err["none"], cond)
     for k in range(nf):
         if err["none"][k] > 1e-4:
             assert err["all"][k] * 10 <= err["none"][k], k
