@@ -14,6 +14,7 @@
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cfloat>
 #include <cmath>
 #include <complex>
@@ -126,13 +127,13 @@ cudaError_t launch_build_coef(const float* vel, const Layout& L, double dz, doub
 // transform reads.
 // ---------------------------------------------------------------------------------------------
 #ifndef EGH_FD_P
-#define EGH_FD_P 4
+#define EGH_FD_P 2
 #endif
 #ifndef EGH_FD_MINB
 #define EGH_FD_MINB 1
 #endif
-constexpr int FD_RING = 16;     // ring rows per warp (power of two)
-constexpr int FD_D = 11;        // u^n rows in flight ahead of the window's leading row
+constexpr int FD_RING = 12;     // ring rows per warp (indices are compile-time: any count)
+constexpr int FD_D = 7;         // u^n rows in flight ahead of the window's leading row
 constexpr int FD_P = EGH_FD_P;  // u^{n-1} / coefficient rows prefetched ahead
 static_assert(FD_D + 5 <= FD_RING && FD_D + 8 >= FD_RING, "ring rows must cover the prefetch distance");
 
@@ -217,7 +218,7 @@ __global__ void __launch_bounds__(32 * FD_MAXPAIRS, EGH_FD_MINB)
     if (k < nload) {
       const int z = z0 - 4 + k;
       const int r = z * PX2;
-      const unsigned dst = ring0 + (unsigned)((k & (FD_RING - 1)) * 36) * 16u;
+      const unsigned dst = ring0 + (unsigned)((k % FD_RING) * 36) * 16u;
       cp_async16(dst + (unsigned)(lane + 2) * 16u, uc + r + xh);
       // halo columns are read only for rows that are computed (0 <= z < NZ): there they stay
       // inside the level (previous row's padding, next row's first columns); a guard row's halo
@@ -279,7 +280,7 @@ __global__ void __launch_bounds__(32 * FD_MAXPAIRS, EGH_FD_MINB)
       pc[i % FD_P] = __ldg(cf + (z0 + i + FD_P) * PX2);
     }
     {
-      const float4 v = ring[(i + 8) & (FD_RING - 1)][lane + 2];  // u^n at row z + 4
+      const float4 v = ring[(i + 8) % FD_RING][lane + 2];  // u^n at row z + 4
       const float2 nv[2] = {make_float2(v.x, v.y), make_float2(v.z, v.w)};
 #pragma unroll
       for (int p = 0; p < 2; ++p) {
@@ -289,7 +290,7 @@ __global__ void __launch_bounds__(32 * FD_MAXPAIRS, EGH_FD_MINB)
         ul[p] = nv[p];
       }
     }
-    const float4* xr = ring[(i + 4) & (FD_RING - 1)];  // u^n at row z, points x0 - 4 .. x0 + 67
+    const float4* xr = ring[(i + 4) % FD_RING];  // u^n at row z, points x0 - 4 .. x0 + 67
     const float4 A0 = xr[lane], A1 = xr[lane + 1], A2 = xr[lane + 2], A3 = xr[lane + 3],
                  A4 = xr[lane + 4];
     __syncwarp();  // every lane has read ring row i + 4 before it is refilled
@@ -338,6 +339,8 @@ __global__ void __launch_bounds__(32 * FD_MAXPAIRS, EGH_FD_MINB)
 
 int fd_rows_per_warp_default() { return EGH_FD_TZDEF; }
 
+int fd_block_smem(int npairs) { return (int)(sizeof(float4) * FD_RING * 36 * npairs); }
+
 // Rows per warp that fill one wave: the smallest choice whose tiles (PX/64 x ceil(NZ / TZ) CTAs)
 // all fit the GPU's resident CTA slots at once, so that no SM carries more rows than another;
 // the library default if none does.
@@ -346,7 +349,7 @@ int fd_rows_one_wave(const Layout& L, int npairs) {
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return EGH_FD_TZDEF;
-  const size_t smem = sizeof(float4) * FD_RING * 36 * npairs;
+  const size_t smem = fd_block_smem(npairs);
   const int threads = 32 * npairs;
   auto fits = [&](auto kern, int tz) {
     int occ = 0;
@@ -374,6 +377,12 @@ cudaError_t fd_prepare(int nf) {
   if ((e = cudaFuncSetAttribute(k_fd_step<20>, cudaFuncAttributeMaxDynamicSharedMemorySize, fd_smem))) return e;
   if ((e = cudaFuncSetAttribute(k_fd_step<24>, cudaFuncAttributeMaxDynamicSharedMemorySize, fd_smem))) return e;
   if ((e = cudaFuncSetAttribute(k_fd_step<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, fd_smem))) return e;
+  // the FD steps and the transform beside them share each SM's shared memory: ask for all of it
+  for (const void* f : {(const void*)k_fd_step<12>, (const void*)k_fd_step<16>, (const void*)k_fd_step<18>,
+                        (const void*)k_fd_step<20>, (const void*)k_fd_step<24>, (const void*)k_fd_step<32>})
+    if ((e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                  (int)cudaSharedmemCarveoutMaxShared)))
+      return e;
   (void)nf;
   return cudaSuccess;
 }
@@ -395,7 +404,7 @@ cudaError_t launch_fd_step(const float2* ucur, const float2* uprev, float2* unex
   if (npairs < 1 || npairs > FD_MAXPAIRS) return cudaErrorInvalidValue;
   count_launches(1);
   const dim3 blk(32, npairs);
-  const size_t smem = sizeof(float4) * FD_RING * 36 * npairs;
+  const size_t smem = fd_block_smem(npairs);
   const int org = (int)L.org;
   switch (tz) {
 #define EGH_FD_CASE(T)                                                                          \
@@ -474,52 +483,67 @@ cudaError_t launch_record(const float2* u, long long pstride, const int* rec_pts
 // in bf16x3: u = u_hi + u_lo (split by the FD step), W = W_hi + W_lo (split on the host), and
 // u_hi W_hi + u_hi W_lo + u_lo W_hi accumulated in FP32 in TMEM (the dropped u_lo W_lo and the
 // splits themselves are ~2^-17 relative).  The chunk that ends the record also writes the final
-// transforms' bf16 hi/lo split (the Gram's operands).  D = A B^T with M = 128 points per CTA, N = 2 nf
-// rounded up to 32, K = levels in stages of 32; TD_R receivers per CTA share the twiddle tiles.
+// transforms' bf16 hi/lo split (the Gram's operands).  One tile is D = A B^T for 128 points of
+// one receiver: M = 128, N = 2 nf rounded up to 32, K = the chunk's levels in stages of 32.
 // A (snapshots) is MN-major: a 4-D TMA box {64 points, 1 receiver, 32 levels, 2 planes} lands as
-// [plane][level][64 points] 128-byte rows with the 128-byte swizzle (two boxes per receiver).
+// [plane][level][64 points] 128-byte rows with the 128-byte swizzle (two boxes per stage).
 // B (twiddles) is K-major in host-swizzled tiles of 64 levels (one 128-byte row per component),
-// one 1-D bulk copy per tile.  One thread issues the copies and the MMAs over a TD_ST-stage ring;
-// at the end every thread reads its point's row of TMEM and adds it into gh (plain store for the
-// chunk that starts at level 0).  Every mbarrier wait is bounded: on expiry the CTA records the
-// error flag, waits (bounded) for its copies and MMAs in flight, frees its TMEM and leaves.
+// one 1-D bulk copy per tile.
+//
+// The kernel is persistent and small so that it runs BESIDE the FD steps of the next chunk: one
+// CTA per SM (a fixed grid of at most one CTA per SM walks the tiles), 128 threads at 32
+// registers and 66.5 KB of shared memory, which fit next to the two FD CTAs an SM holds (2 x 256
+// threads x 120 registers, 2 x 55 KB).  Launched as a grid of thousands of short CTAs, the
+// transform's CTAs took whole SMs between FD launches and the FD steps waited for them, so that
+// the two ran one after the other; side by side they share the SMs, and the FD steps, which are
+// bound by issue and latency, lose less than the transform's run time.
+// One thread issues the copies and the MMAs over a TD_ST-stage ring; after a tile's last stage
+// every thread reads its point's row of TMEM in groups of 8 columns and adds it into gh (plain
+// store for the chunk that starts at level 0).  Every mbarrier wait is bounded: on expiry the
+// CTA records the error flag, waits (bounded) for its copies and MMAs in flight, frees its TMEM
+// and leaves.
 // ---------------------------------------------------------------------------------------------
-#ifndef EGH_TD_R
-#define EGH_TD_R 1
-#endif
 #ifndef EGH_TD_ST
 #define EGH_TD_ST 2
 #endif
-constexpr int TD_M = 128;                // points per CTA (MMA M)
-constexpr int TD_R = EGH_TD_R;           // receivers per CTA
+constexpr int TD_M = 128;                // points per tile (MMA M)
 constexpr int TD_S = 32;                 // levels per stage
 constexpr int TD_ST = EGH_TD_ST;         // stages in flight
-constexpr unsigned TD_AB = 16384;        // one receiver's stage: 2 atoms x 2 planes x 32 x 128 B
+constexpr unsigned TD_AB = 16384;        // one stage of A: 2 atoms x 2 planes x 32 x 128 B
+constexpr int TD_NMAX = 128;             // largest N (TMEM columns: N rounded up to a power of two)
 
 int dft_ncomp(int nf) { return (2 * nf + 31) / 32 * 32; }
 
 size_t dft_smem(int nf) {
-  return 1024 + (size_t)TD_ST * TD_R * TD_AB + 2 * 2 * (size_t)dft_ncomp(nf) * 128;
+  return 1024 + (size_t)TD_ST * TD_AB + 2 * 2 * (size_t)dft_ncomp(nf) * 128;
 }
 
-__global__ void __launch_bounds__(128)
+__device__ __forceinline__ void tmem_ld8(unsigned taddr, float (&v)[8]) {
+  unsigned q[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(q[0]), "=r"(q[1]), "=r"(q[2]), "=r"(q[3]), "=r"(q[4]), "=r"(q[5]), "=r"(q[6]),
+                 "=r"(q[7])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(q[i]);
+}
+
+__global__ void __launch_bounds__(128, 16)
     k_dft_tc(const __grid_constant__ CUtensorMap tmap, const unsigned char* __restrict__ twt,
              int N, int nf, int slot0, int kcount, int n0, long long G, float* __restrict__ gh,
              __nv_bfloat16* __restrict__ ghb, int last, int rec0, int nvalid, int nrec_all,
              int* __restrict__ err, int expire) {
   extern __shared__ __align__(1024) unsigned char dsm[];
   unsigned char* sm = dsm + ((1024 - (tc::smem_u32(dsm) & 1023)) & 1023);
-  unsigned char* As = sm;                               // [TD_ST][TD_R][TD_AB]
-  unsigned char* Bs = sm + TD_ST * TD_R * TD_AB;        // [2][plane][N][128 B]
+  unsigned char* As = sm;                       // [TD_ST][TD_AB]
+  unsigned char* Bs = sm + TD_ST * TD_AB;       // [2][plane][N][128 B]
   const unsigned tile = 2u * (unsigned)N * 128u;
   __shared__ __align__(8) unsigned long long bars[2 * TD_ST + 2];  // full[], empty[], done, never
   __shared__ unsigned tslot;
   __shared__ int fail;
   const int tid = threadIdx.x, warp = tid >> 5;
-  const int rg = blockIdx.y * TD_R;
-  const int nr = min(TD_R, nvalid - rg);
-  unsigned ncols = 32;
-  while (ncols < (unsigned)(TD_R * N)) ncols <<= 1;
+  const unsigned ncols = N <= 32 ? 32u : N <= 64 ? 64u : 128u;
   if (warp == 0) tc::tmem_alloc(&tslot, ncols);
   const unsigned bar0 = tc::smem_u32(&bars[0]);
   auto full = [&](int i) { return bar0 + 8u * i; };
@@ -534,23 +558,28 @@ __global__ void __launch_bounds__(128)
   __syncthreads();
   tc::tc_fence_after();
   const unsigned tmem = tslot;
-  const int p0 = blockIdx.x * TD_M;
+  const int npb = (int)(G / TD_M);       // 128-point blocks
+  const int ntile = npb * nvalid;        // tiles: block-major within a receiver
   const int nst = (kcount + TD_S - 1) / TD_S;
-  if (warp == 0) {
+  const bool first = n0 == 0;
+  // stage q of this CTA (counted over all its tiles) uses buffer q % TD_ST in phase (q / TD_ST) & 1
+  int q0 = 0, it = 0;
+  for (int t = blockIdx.x; t < ntile; t += gridDim.x, ++it, q0 += nst) {
+    const int r = t / npb;
+    const int p0 = (t - r * npb) * TD_M;
     if (tid == 0) {
       const unsigned idesc = tc::idesc_bf16(TD_M, N, 1, 0);
       // snapshots are read once: stream them through L2 as evict-first so that the FD's state
       // levels, which the concurrent FD steps re-read, stay resident
       const uint64_t pol = tc::l2_evict_first_policy();
       auto issue = [&](int s) {
-        const int buf = s % TD_ST;
+        const int buf = (q0 + s) % TD_ST;
         const int n = n0 + s * TD_S;
         const bool newtile = s == 0 || (n & 63) == 0;
-        tc::mbar_expect_tx(full(buf), (unsigned)nr * TD_AB + (newtile ? tile : 0u));
-        for (int r = 0; r < nr; ++r)
-          for (int m = 0; m < 2; ++m)
-            tc::tma_load_4d_hint(tc::smem_u32(As + (buf * TD_R + r) * TD_AB + m * 8192), &tmap,
-                                 p0 + 64 * m, rg + r, slot0 + s * TD_S, 0, full(buf), pol);
+        tc::mbar_expect_tx(full(buf), TD_AB + (newtile ? tile : 0u));
+        for (int m = 0; m < 2; ++m)
+          tc::tma_load_4d_hint(tc::smem_u32(As + buf * TD_AB + m * 8192), &tmap, p0 + 64 * m, r,
+                               slot0 + s * TD_S, 0, full(buf), pol);
         if (newtile)
           tc::bulk_g2s(tc::smem_u32(Bs + ((n >> 6) & 1) * tile), twt + (size_t)(n >> 6) * tile, tile,
                        full(buf));
@@ -559,12 +588,13 @@ __global__ void __launch_bounds__(128)
       bool ok = true;
       for (; issued < min(nst, TD_ST); ++issued) issue(issued);
       // test hook: the first CTA's first wait runs out (the last barrier never completes a phase)
-      if (expire && blockIdx.x == 0 && blockIdx.y == 0 &&
+      if (expire && blockIdx.x == 0 && it == 0 &&
           !tc::mbar_wait_unsignalled(bar0 + 8u * (2 * TD_ST + 1)))
         ok = false;
       for (int s = 0; ok && s < nst; ++s) {
-        const int buf = s % TD_ST;
-        if (!tc::mbar_wait(full(buf), (s / TD_ST) & 1)) {
+        const int q = q0 + s;
+        const int buf = q % TD_ST;
+        if (!tc::mbar_wait(full(buf), (q / TD_ST) & 1)) {
           ok = false;
           break;
         }
@@ -573,22 +603,19 @@ __global__ void __launch_bounds__(128)
         const int n = n0 + s * TD_S;
         const unsigned bh = tc::smem_u32(Bs + ((n >> 6) & 1) * tile) + (unsigned)(n & 63) * 2u;
         const unsigned bl = bh + (unsigned)N * 128u;
-        for (int r = 0; r < nr; ++r) {
-          const unsigned ab = tc::smem_u32(As + (buf * TD_R + r) * TD_AB);
-          const unsigned dt = tmem + (unsigned)(r * N);
+        const unsigned ab = tc::smem_u32(As + buf * TD_AB);
 #pragma unroll
-          for (int ks = 0; ks < 2; ++ks) {
-            const uint64_t ahi = tc::sdesc_sw128_lbo_sbo(ab + ks * 2048, 8192, 1024);
-            const uint64_t alo = tc::sdesc_sw128_lbo_sbo(ab + 4096 + ks * 2048, 8192, 1024);
-            const uint64_t bhi = tc::sdesc_sw128(bh + ks * 32), blo = tc::sdesc_sw128(bl + ks * 32);
-            tc::mma_bf16(dt, ahi, bhi, idesc, s > 0 || ks > 0);
-            tc::mma_bf16(dt, ahi, blo, idesc, true);
-            tc::mma_bf16(dt, alo, bhi, idesc, true);
-          }
+        for (int ks = 0; ks < 2; ++ks) {
+          const uint64_t ahi = tc::sdesc_sw128_lbo_sbo(ab + ks * 2048, 8192, 1024);
+          const uint64_t alo = tc::sdesc_sw128_lbo_sbo(ab + 4096 + ks * 2048, 8192, 1024);
+          const uint64_t bhi = tc::sdesc_sw128(bh + ks * 32), blo = tc::sdesc_sw128(bl + ks * 32);
+          tc::mma_bf16(tmem, ahi, bhi, idesc, s > 0 || ks > 0);
+          tc::mma_bf16(tmem, ahi, blo, idesc, true);
+          tc::mma_bf16(tmem, alo, bhi, idesc, true);
         }
         tc::mma_commit(empty(buf));
         if (issued < nst) {  // the next stage to issue reuses this stage's buffer
-          if (!tc::mbar_wait(empty(buf), (s / TD_ST) & 1)) {
+          if (!tc::mbar_wait(empty(buf), (q / TD_ST) & 1)) {
             ok = false;
             break;
           }
@@ -600,50 +627,52 @@ __global__ void __launch_bounds__(128)
         fail = 1;
         atomicExch(err, 1);
         // let the copies in flight land (bounded) before the CTA leaves
-        for (int s = landed; s < issued; ++s) tc::mbar_wait(full(s % TD_ST), (s / TD_ST) & 1);
+        for (int s = landed; s < issued; ++s)
+          tc::mbar_wait(full((q0 + s) % TD_ST), ((q0 + s) / TD_ST) & 1);
       }
       tc::mma_commit(done);  // arrives once every MMA issued so far has completed
     }
     __syncwarp();
-  }
-  const bool okd = tc::mbar_wait(done, 0);
-  if (!__syncthreads_or(!okd) && !fail) {
+    const bool okd = tc::mbar_wait(done, it & 1);
+    if (__syncthreads_or(!okd || (tid == 0 && fail))) {
+      if (tid == 0) atomicExch(err, 1);
+      break;
+    }
     tc::tc_fence_after();
-    const bool first = n0 == 0;
     const long long p = p0 + tid;
-    for (int r = 0; r < nr; ++r) {
-      const long long row0 = (long long)(rec0 + rg + r) * 2 * nf;  // first plane of this receiver
-      float* g = gh + row0 * G + p;
-      for (int c0 = 0; c0 < N; c0 += 32) {
-        float v[32], o[32];
-        tc::tmem_ld32(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(r * N + c0), v);
-        // all loads of the group before any store: the 32 column planes are distinct
+    const long long row0 = (long long)(rec0 + r) * 2 * nf;  // first plane of this receiver
+    float* g = gh + row0 * G + p;
+    for (int c0 = 0; c0 < N; c0 += 8) {
+      float v[8], o[8];
+      tmem_ld8(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c0, v);
+      // all loads of the group before any store: the 8 column planes are distinct
 #pragma unroll
-        for (int i = 0; i < 32; ++i)
-          o[i] = (!first && c0 + i < 2 * nf) ? __ldcs(g + (long long)(c0 + i) * G) : 0.f;
+      for (int i = 0; i < 8; ++i)
+        o[i] = (!first && c0 + i < 2 * nf) ? __ldcs(g + (long long)(c0 + i) * G) : 0.f;
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const int c = c0 + i;
-          if (c < 2 * nf) {
-            const float sum = o[i] + v[i];
-            __stcs(g + (long long)c * G, sum);
-            if (last) {
-              // the Gram's operands: hi = bf16(g), lo = bf16(g - hi), blocked by 64 points as
-              // [freq][G/64][hi|lo][receiver, re/im][64] (each 64-receiver box is contiguous)
-              const __nv_bfloat16 h = __float2bfloat16_rn(sum);
-              const __nv_bfloat16 l = __float2bfloat16_rn(sum - __bfloat162float(h));
-              const long long rows = 2LL * nrec_all;
-              __nv_bfloat16* q = ghb + (((long long)(c >> 1) * (G >> 6) + (p >> 6)) * 2 * rows +
-                                        2LL * (rec0 + rg + r) + (c & 1)) * 64 + (p & 63);
-              q[0] = h;
-              q[rows * 64] = l;
-            }
+      for (int i = 0; i < 8; ++i) {
+        const int c = c0 + i;
+        if (c < 2 * nf) {
+          const float sum = o[i] + v[i];
+          __stcs(g + (long long)c * G, sum);
+          if (last) {
+            // the Gram's operands: hi = bf16(g), lo = bf16(g - hi), blocked by 64 points as
+            // [freq][G/64][hi|lo][receiver, re/im][64] (each 64-receiver box is contiguous)
+            const __nv_bfloat16 h = __float2bfloat16_rn(sum);
+            const __nv_bfloat16 l = __float2bfloat16_rn(sum - __bfloat162float(h));
+            const long long rows = 2LL * nrec_all;
+            __nv_bfloat16* qp = ghb + (((long long)(c >> 1) * (G >> 6) + (p >> 6)) * 2 * rows +
+                                       2LL * (rec0 + r) + (c & 1)) * 64 + (p & 63);
+            qp[0] = h;
+            qp[rows * 64] = l;
           }
         }
       }
     }
-  } else if (tid == 0) {
-    atomicExch(err, 1);
+    // every thread has read TMEM before the next tile's first MMA overwrites it
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
   }
   tc::tc_fence_before();
   __syncthreads();
@@ -653,16 +682,38 @@ __global__ void __launch_bounds__(128)
 cudaError_t launch_dft_tc(const CUtensorMap& tmap, const unsigned char* twt, int nf, int slot0,
                           int kcount, int n0, const Layout& L, float* gh, __nv_bfloat16* ghb,
                           int last, int rec0, int nvalid, int nrec_all, int* err, int expire,
-                          cudaStream_t st) {
+                          int per_sm, int beside_smem, cudaStream_t st) {
   const int N = dft_ncomp(nf);
-  if (L.G % TD_M != 0 || N > 128 || kcount < 1 || slot0 % TD_S != 0 || n0 % TD_S != 0 ||
-      nvalid < 1)
+  if (L.G % TD_M != 0 || N > TD_NMAX || kcount < 1 || slot0 % TD_S != 0 || n0 % TD_S != 0 ||
+      nvalid < 1 || per_sm < 1 || per_sm > 3 || beside_smem < 0)
     return cudaErrorInvalidValue;
-  const size_t smem = dft_smem(nf);
-  cudaError_t e =
-      cudaFuncSetAttribute(k_dft_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  dim3 grid((unsigned)(L.G / TD_M), (unsigned)((nvalid + TD_R - 1) / TD_R));
+  cudaError_t e;
+  int dev = 0, sms = 0, sm_smem = 0, reserved = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+      (e = cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) !=
+          cudaSuccess ||
+      (e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev)) !=
+          cudaSuccess)
+    return e;
+  cudaFuncAttributes fa;
+  if ((e = cudaFuncGetAttributes(&fa, k_dft_tc)) != cudaSuccess) return e;
+  size_t smem = dft_smem(nf);
+  if (beside_smem > 0) {
+    // Beside two FD CTAs of beside_smem bytes each: the largest size that still fits there, if
+    // that size also keeps a second transform CTA off the SM.  A CTA per SM is then all an SM
+    // can take, wherever the launch finds free room (at a chunk boundary, SMs whose FD CTAs
+    // have left would otherwise take two or three and hold back the next FD step).
+    const long long cta = (long long)fa.sharedSizeBytes + reserved;
+    const long long fit = (long long)sm_smem - 2LL * (beside_smem + reserved) - cta;
+    if (fit >= (long long)smem && 2 * (fit + cta) > sm_smem) smem = (size_t)fit;
+  }
+  if ((e = cudaFuncSetAttribute(k_dft_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) ||
+      (e = cudaFuncSetAttribute(k_dft_tc, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                (int)cudaSharedmemCarveoutMaxShared)))
+    return e;
+  const long long ntile = (L.G / TD_M) * nvalid;
+  const int grid = (int)std::min<long long>((long long)sms * per_sm, ntile);
   count_launches(1);
   k_dft_tc<<<grid, 128, smem, st>>>(tmap, twt, N, nf, slot0, kcount, n0, L.G, gh, ghb, last, rec0,
                                     nvalid, nrec_all, err, expire);

@@ -554,12 +554,12 @@ class Server:
 
     def wait(self, request_id, timeout_s=60.0):
         lat = ctypes.c_double(0.0)
-        try:
-            _check_server(load().egh_server_wait(self.h, int(request_id), float(timeout_s), ctypes.byref(lat)),
-                          self.h)
-        finally:
-            pass
-        self._keep.pop(request_id, None)
+        st = load().egh_server_wait(self.h, int(request_id), float(timeout_s), ctypes.byref(lat))
+        if st != EGH_ETIMEOUT:
+            # finished or failed: the id is released and no kernel touches the buffers any more
+            # (on EGH_ETIMEOUT they stay referenced until the server closes)
+            self._keep.pop(request_id, None)
+        _check_server(st, self.h)
         return lat.value
 
     def drain(self, timeout_s=120.0):
