@@ -38,14 +38,12 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM traffic (read + write bytes) per launch of the FD step and of the transform from the
 # committed ncu capture (profiles/), valid only for the kernel sources it was taken from (sha256
 # of csrc/fd.cu); None until a capture exists.
-KERNEL_TRAFFIC = {"fd_sha256": "1bf095bbded34f4a8fc7375b269fc6130e726bfcf20cb11988a6ca4548f930fa",
-                  "k_fd_step": 31.98e6,   # 1.59 MB read + 30.40 MB write per launch (18 rows per warp)
-                  "k_dft_tc": 25.23e9,    # 22.91 GB read + 2.32 GB write per 1024-level launch
-                  # the Gram kernel's source is unchanged since these counters were taken (the file
-                  # has gained the separate operand-conversion kernel of the sharded update)
-                  "gram_sha256": "e2829950df060d653d12e81fa9dd85622935c4671508f461f3501a07ee5c7557",
+KERNEL_TRAFFIC = {"fd_sha256": "be2aaa37e52718203c1348779bdee5e9744c2e5cadf8e186db572eb79e434090",
+                  "k_fd_step": 34.36e6,   # 2.97 MB read + 31.39 MB write per launch (18 rows per warp)
+                  "k_dft_tc": 25.27e9,    # 22.95 GB read + 2.33 GB write per 1024-level launch
+                  "gram_sha256": "f9de315c9b531216c4542c842f967a76ddf97ec6b8c30623a20ace1b44982cd4",
                   # per launch at 231 receivers x 26 frequencies, by grid-sum splits (read + write)
-                  "k_gram_tc": {8: 32.52e9, 16: 24.13e9, 32: 18.02e9}}
+                  "k_gram_tc": {8: 32.98e9, 16: 24.54e9, 32: 18.09e9}}
 
 
 def _args():

@@ -818,13 +818,17 @@ egh_status green_run(egh_ctx* ctx, const float* vel, cudaStream_t stream, const 
       CK(cudaEventRecord(ctx->ev_dft[2 * g], ctx->side));
       const int expire = ctx->expire[0] > 0 ? 1 : 0;
       ctx->expire[0] -= expire;
-      // beside the next chunk's FD steps the transform takes one CTA per SM (sized to fit next
-      // to two FD CTAs of a full batch); the record's last chunk runs alone and takes three
+      // Beside the next chunk's FD steps the transform takes one CTA per SM (sized to fit next
+      // to two FD CTAs of a full batch); the record's last chunk runs alone and takes three.  With
+      // more than 32 frequencies one CTA per SM no longer keeps pace with the FD steps (measured:
+      // 40 frequencies on the salt grid, transform 5.9 s against FD steps 5.1 s per patch), so
+      // there the transform takes one CTA per tile and fills the SMs between FD launches.
       const bool alone = b0 + B >= ctx->nrec && c == nchunk - 1;
-      const int beside = ctx->fd_kernel == 1 ? 0 : fd_block_smem((std::min(B, ctx->nrec) + 1) / 2);
+      const bool slim = dft_ncomp(ctx->nf) <= 64 && ctx->fd_kernel != 1;
+      const int beside = fd_block_smem((std::min(B, ctx->nrec) + 1) / 2);
       CK(launch_dft_tc(ctx->tmap, twt, ctx->nf, sbase, m1 - m0, m0, L, ctx->gh, ctx->ghb,
                        (m1 == ntd && ctx->ghb) ? 1 : 0, b0, nb, ctx->nrec, ctx->d_err, expire,
-                       alone ? 3 : 1, alone ? 0 : beside, ctx->side));
+                       alone ? 3 : slim ? 1 : 0, (alone || !slim) ? 0 : beside, ctx->side));
       CK(cudaEventRecord(ctx->ev_dft[2 * g + 1], ctx->side));
       CK(cudaEventRecord(ctx->dft_done[g & 1], ctx->side));
     }

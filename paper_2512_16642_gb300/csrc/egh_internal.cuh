@@ -80,8 +80,9 @@ std::vector<unsigned char> dft_twiddle_tiles(const std::vector<double>& f, doubl
                                              const std::vector<std::complex<double>>* scale = nullptr);
 cudaError_t make_snap_tmap(CUtensorMap* tm, void* base, long long G, int Bp, int nslot);
 // per_sm: CTAs per SM of the persistent transform (1 beside the FD steps, more when it runs
-// alone); beside_smem: dynamic shared memory of one FD CTA that the transform runs beside (0:
-// none), which sizes the transform's CTAs so that an SM holds one of them next to two FD CTAs
+// alone; 0: one CTA per tile); beside_smem: dynamic shared memory of one FD CTA that the
+// transform runs beside (0: none), which sizes the transform's CTAs so that an SM holds one of
+// them next to two FD CTAs
 cudaError_t launch_dft_tc(const CUtensorMap& tmap, const unsigned char* twt, int nf, int slot0,
                           int kcount, int n0, const Layout& L, float* gh, __nv_bfloat16* ghb,
                           int last, int rec0, int nvalid, int nrec_all, int* err, int expire,

@@ -497,26 +497,29 @@ cudaError_t launch_record(const float2* u, long long pstride, const int* rec_pts
 // transform's CTAs took whole SMs between FD launches and the FD steps waited for them, so that
 // the two ran one after the other; side by side they share the SMs, and the FD steps, which are
 // bound by issue and latency, lose less than the transform's run time.
-// One thread issues the copies and the MMAs over a TD_ST-stage ring; after a tile's last stage
+// One thread issues the copies and the MMAs over a ring of nring stages (3 beside the FD steps,
+// where the padded shared memory has room; 2 alone): the copies of stage s + nring are issued
+// once the MMAs of stage s are done, which with two twiddle buffers (one per 64 levels) keeps a
+// twiddle buffer from being refilled while MMAs still read it for nring <= 3.  After a tile's
+// last stage
 // every thread reads its point's row of TMEM in groups of 8 columns and adds it into gh (plain
 // store for the chunk that starts at level 0).  Every mbarrier wait is bounded: on expiry the
 // CTA records the error flag, waits (bounded) for its copies and MMAs in flight, frees its TMEM
 // and leaves.
 // ---------------------------------------------------------------------------------------------
-#ifndef EGH_TD_ST
-#define EGH_TD_ST 2
-#endif
 constexpr int TD_M = 128;                // points per tile (MMA M)
 constexpr int TD_S = 32;                 // levels per stage
-constexpr int TD_ST = EGH_TD_ST;         // stages in flight
+constexpr int TD_STMAX = 3;              // stages in flight at most
 constexpr unsigned TD_AB = 16384;        // one stage of A: 2 atoms x 2 planes x 32 x 128 B
 constexpr int TD_NMAX = 128;             // largest N (TMEM columns: N rounded up to a power of two)
 
 int dft_ncomp(int nf) { return (2 * nf + 31) / 32 * 32; }
 
-size_t dft_smem(int nf) {
-  return 1024 + (size_t)TD_ST * TD_AB + 2 * 2 * (size_t)dft_ncomp(nf) * 128;
+// dynamic shared memory for a ring of nring stages
+size_t dft_smem_ring(int nf, int nring) {
+  return 1024 + (size_t)nring * TD_AB + 2 * 2 * (size_t)dft_ncomp(nf) * 128;
 }
+size_t dft_smem(int nf) { return dft_smem_ring(nf, 2); }
 
 __device__ __forceinline__ void tmem_ld8(unsigned taddr, float (&v)[8]) {
   unsigned q[8];
@@ -533,13 +536,13 @@ __global__ void __launch_bounds__(128, 16)
     k_dft_tc(const __grid_constant__ CUtensorMap tmap, const unsigned char* __restrict__ twt,
              int N, int nf, int slot0, int kcount, int n0, long long G, float* __restrict__ gh,
              __nv_bfloat16* __restrict__ ghb, int last, int rec0, int nvalid, int nrec_all,
-             int* __restrict__ err, int expire) {
+             int* __restrict__ err, int expire, int nring) {
   extern __shared__ __align__(1024) unsigned char dsm[];
   unsigned char* sm = dsm + ((1024 - (tc::smem_u32(dsm) & 1023)) & 1023);
-  unsigned char* As = sm;                       // [TD_ST][TD_AB]
-  unsigned char* Bs = sm + TD_ST * TD_AB;       // [2][plane][N][128 B]
+  unsigned char* As = sm;                       // [nring][TD_AB]
+  unsigned char* Bs = sm + nring * TD_AB;       // [2][plane][N][128 B]
   const unsigned tile = 2u * (unsigned)N * 128u;
-  __shared__ __align__(8) unsigned long long bars[2 * TD_ST + 2];  // full[], empty[], done, never
+  __shared__ __align__(8) unsigned long long bars[2 * TD_STMAX + 2];  // full[], empty[], done, never
   __shared__ unsigned tslot;
   __shared__ int fail;
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -547,10 +550,10 @@ __global__ void __launch_bounds__(128, 16)
   if (warp == 0) tc::tmem_alloc(&tslot, ncols);
   const unsigned bar0 = tc::smem_u32(&bars[0]);
   auto full = [&](int i) { return bar0 + 8u * i; };
-  auto empty = [&](int i) { return bar0 + 8u * (TD_ST + i); };
-  const unsigned done = bar0 + 8u * (2 * TD_ST);
+  auto empty = [&](int i) { return bar0 + 8u * (TD_STMAX + i); };
+  const unsigned done = bar0 + 8u * (2 * TD_STMAX);
   if (tid == 0) {
-    for (int i = 0; i < 2 * TD_ST + 2; ++i) tc::mbar_init(bar0 + 8u * i, 1);
+    for (int i = 0; i < 2 * TD_STMAX + 2; ++i) tc::mbar_init(bar0 + 8u * i, 1);
     fail = 0;
     tc::mbar_init_fence();
   }
@@ -562,7 +565,7 @@ __global__ void __launch_bounds__(128, 16)
   const int ntile = npb * nvalid;        // tiles: block-major within a receiver
   const int nst = (kcount + TD_S - 1) / TD_S;
   const bool first = n0 == 0;
-  // stage q of this CTA (counted over all its tiles) uses buffer q % TD_ST in phase (q / TD_ST) & 1
+  // stage q of this CTA (counted over all its tiles) uses buffer q % nring in phase (q / nring) & 1
   int q0 = 0, it = 0;
   for (int t = blockIdx.x; t < ntile; t += gridDim.x, ++it, q0 += nst) {
     const int r = t / npb;
@@ -573,7 +576,7 @@ __global__ void __launch_bounds__(128, 16)
       // levels, which the concurrent FD steps re-read, stay resident
       const uint64_t pol = tc::l2_evict_first_policy();
       auto issue = [&](int s) {
-        const int buf = (q0 + s) % TD_ST;
+        const int buf = (q0 + s) % nring;
         const int n = n0 + s * TD_S;
         const bool newtile = s == 0 || (n & 63) == 0;
         tc::mbar_expect_tx(full(buf), TD_AB + (newtile ? tile : 0u));
@@ -586,15 +589,15 @@ __global__ void __launch_bounds__(128, 16)
       };
       int issued = 0, landed = 0;
       bool ok = true;
-      for (; issued < min(nst, TD_ST); ++issued) issue(issued);
+      for (; issued < min(nst, nring); ++issued) issue(issued);
       // test hook: the first CTA's first wait runs out (the last barrier never completes a phase)
       if (expire && blockIdx.x == 0 && it == 0 &&
-          !tc::mbar_wait_unsignalled(bar0 + 8u * (2 * TD_ST + 1)))
+          !tc::mbar_wait_unsignalled(bar0 + 8u * (2 * TD_STMAX + 1)))
         ok = false;
       for (int s = 0; ok && s < nst; ++s) {
         const int q = q0 + s;
-        const int buf = q % TD_ST;
-        if (!tc::mbar_wait(full(buf), (q / TD_ST) & 1)) {
+        const int buf = q % nring;
+        if (!tc::mbar_wait(full(buf), (q / nring) & 1)) {
           ok = false;
           break;
         }
@@ -615,7 +618,7 @@ __global__ void __launch_bounds__(128, 16)
         }
         tc::mma_commit(empty(buf));
         if (issued < nst) {  // the next stage to issue reuses this stage's buffer
-          if (!tc::mbar_wait(empty(buf), (q / TD_ST) & 1)) {
+          if (!tc::mbar_wait(empty(buf), (q / nring) & 1)) {
             ok = false;
             break;
           }
@@ -628,7 +631,7 @@ __global__ void __launch_bounds__(128, 16)
         atomicExch(err, 1);
         // let the copies in flight land (bounded) before the CTA leaves
         for (int s = landed; s < issued; ++s)
-          tc::mbar_wait(full((q0 + s) % TD_ST), ((q0 + s) / TD_ST) & 1);
+          tc::mbar_wait(full((q0 + s) % nring), ((q0 + s) / nring) & 1);
       }
       tc::mma_commit(done);  // arrives once every MMA issued so far has completed
     }
@@ -685,7 +688,7 @@ cudaError_t launch_dft_tc(const CUtensorMap& tmap, const unsigned char* twt, int
                           int per_sm, int beside_smem, cudaStream_t st) {
   const int N = dft_ncomp(nf);
   if (L.G % TD_M != 0 || N > TD_NMAX || kcount < 1 || slot0 % TD_S != 0 || n0 % TD_S != 0 ||
-      nvalid < 1 || per_sm < 1 || per_sm > 3 || beside_smem < 0)
+      nvalid < 1 || per_sm < 0 || per_sm > 3 || beside_smem < 0)
     return cudaErrorInvalidValue;
   cudaError_t e;
   int dev = 0, sms = 0, sm_smem = 0, reserved = 0;
@@ -698,25 +701,37 @@ cudaError_t launch_dft_tc(const CUtensorMap& tmap, const unsigned char* twt, int
     return e;
   cudaFuncAttributes fa;
   if ((e = cudaFuncGetAttributes(&fa, k_dft_tc)) != cudaSuccess) return e;
-  size_t smem = dft_smem(nf);
+  int nring = 2;
+  size_t smem = dft_smem_ring(nf, 2);
   if (beside_smem > 0) {
     // Beside two FD CTAs of beside_smem bytes each: the largest size that still fits there, if
     // that size also keeps a second transform CTA off the SM.  A CTA per SM is then all an SM
     // can take, wherever the launch finds free room (at a chunk boundary, SMs whose FD CTAs
-    // have left would otherwise take two or three and hold back the next FD step).
+    // have left would otherwise take two or three and hold back the next FD step).  The padded
+    // size holds a third stage where it has room: one CTA per SM keeps three copies in flight.
     const long long cta = (long long)fa.sharedSizeBytes + reserved;
     const long long fit = (long long)sm_smem - 2LL * (beside_smem + reserved) - cta;
-    if (fit >= (long long)smem && 2 * (fit + cta) > sm_smem) smem = (size_t)fit;
+    if (fit >= (long long)smem && 2 * (fit + cta) > sm_smem) {
+      smem = (size_t)fit;
+      if ((long long)dft_smem_ring(nf, 3) <= fit) nring = 3;
+    }
   }
   if ((e = cudaFuncSetAttribute(k_dft_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) ||
       (e = cudaFuncSetAttribute(k_dft_tc, cudaFuncAttributePreferredSharedMemoryCarveout,
                                 (int)cudaSharedmemCarveoutMaxShared)))
     return e;
+  // a persistent grid (per_sm > 0) must be resident at once: at most the SM's occupancy; per_sm
+  // = 0 launches one CTA per tile
+  int occ = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_dft_tc, 128, smem)) != cudaSuccess)
+    return e;
+  if (occ < 1) return cudaErrorInvalidConfiguration;
   const long long ntile = (L.G / TD_M) * nvalid;
-  const int grid = (int)std::min<long long>((long long)sms * per_sm, ntile);
+  const int grid = (int)(per_sm == 0 ? ntile
+                                     : std::min<long long>((long long)sms * std::min(per_sm, occ), ntile));
   count_launches(1);
   k_dft_tc<<<grid, 128, smem, st>>>(tmap, twt, N, nf, slot0, kcount, n0, L.G, gh, ghb, last, rec0,
-                                    nvalid, nrec_all, err, expire);
+                                    nvalid, nrec_all, err, expire, nring);
   return cudaGetLastError();
 }
 
