@@ -6,8 +6,8 @@
 //                    k_cgemm once per factorisation; the product on the tensor cores in
 //                    solve_tc.cu), then at ill-conditioned frequencies
 //                    X_k += Q_k^{-1} (D_k - Q_k X_k)                (k_resid_dot2 or k_resid64)
-//   mult[s][r][t] = sum_k w_k Re(X_k[r][s] exp(+i w_k t dt))      (k_synth_tc; k_synth beyond
-//                                                                  2 nf = 64)
+//   mult[s][r][t] = sum_k w_k Re(X_k[r][s] exp(+i w_k t dt))      (k_synth_tc; k_synth without
+//                                                                  the twiddle tiles)
 // Traces are indexed q = s * nrec + r (the [ns][nrec][nt] gather layout); the spectra of one call
 // occupy columns s0 .. s0 + ns - 1 of a [nf][nrec][ld] array, so that several gathers (of
 // different lengths) can share one solve.
@@ -820,27 +820,38 @@ cudaError_t launch_add_correction(float2* X, const float2* R, long long m, int n
 // ---------------------------------------------------------------------------------------------
 // Synthesis on the tensor cores: mult[q][t] = sum_c A[q][c] B[t][c] with A[q][2k] = w_k Re X_k,
 // A[q][2k+1] = w_k Im X_k (the weighted solutions of trace q) and B[t][2k] = cos(theta),
-// B[t][2k+1] = -sin(theta) (host tiles of 256 samples x 64 components, bf16 hi/lo, K-major
-// 128-byte swizzle).  128 traces x SC_SEG tiles of 256 samples per CTA: the threads gather,
-// weight and split their solutions into the A tile once, then every 256-sample tile is one
-// bf16x3 M128 x N256 x K64 product into one of two TMEM buffers, drained by eight warps (lane
-// quarter w % 4, column half w / 4) straight to global memory while the next tile's MMAs run.
-// Needs 2 nf <= 64.  Every wait is bounded.
+// B[t][2k+1] = -sin(theta) (host tiles, bf16 hi/lo, K-major 128-byte swizzle).  The components
+// come in KC chunks of 64: KC = 1 for 2 nf <= 64 (tiles of 256 samples, two B buffers), KC = 2
+// for 2 nf <= 128 (tiles of 128 samples, one B buffer refilled as soon as a tile's MMAs are done,
+// while the previous tile drains).  128 traces x 1024 samples per CTA: the threads gather, weight
+// and split their solutions into the A tile once, then every sample tile is one bf16x3
+// M128 x N(256 or 128) x K(64 KC) product into one of two TMEM buffers, drained by eight warps
+// (lane quarter w % 4, column half w / 4) straight to global memory while the next tile's MMAs
+// run.  Every wait is bounded.
 // ---------------------------------------------------------------------------------------------
-constexpr int SC_M = 128, SC_N = 256, SC_SEG = 4;  // tiles of 256 samples per CTA
+constexpr int SC_M = 128;
 constexpr int SC_STG = 36;  // row length (floats) of the per-warp 32 x 32 staging tiles
-constexpr unsigned SC_A = SC_M * 128;         // one A plane (hi or lo)
-constexpr unsigned SC_B = 2u * SC_N * 128u;   // one B tile (hi + lo)
+constexpr unsigned SC_CH = SC_M * 128;  // one 64-component chunk of an A plane (hi or lo)
+constexpr unsigned SC_B = 65536u;       // one B tile (hi + lo): 2 planes x KC x (256 / KC) x 128 B
 
-size_t synth_tc_smem() {
-  return 1024 + 2 * (size_t)SC_A + 2 * (size_t)SC_B + 8 * 32 * SC_STG * sizeof(float);
+__host__ __device__ constexpr int sc_kc(int nf) { return 2 * nf <= 64 ? 1 : 2; }
+__host__ __device__ constexpr int sc_n(int kc) { return kc == 1 ? 256 : 128; }  // samples per tile
+
+size_t synth_tc_smem(int kc) {
+  // A (2 planes x kc chunks), B buffers (2 for kc = 1, 1 for kc = 2), staging, alignment slack
+  return 1024 + 2 * (size_t)kc * SC_CH + (kc == 1 ? 2 : 1) * (size_t)SC_B +
+         8 * 32 * SC_STG * sizeof(float);
 }
 
-template <bool VEC>
+template <bool VEC, int KC>
 __global__ void __launch_bounds__(256)
     k_synth_tc(const float2* __restrict__ Dh, int nrec, int ld, int s0, int nf,
                const float* __restrict__ w, const unsigned char* __restrict__ tws, int nt_d,
                float* __restrict__ mult, int ntr, int* __restrict__ err) {
+  constexpr int SN = sc_n(KC);          // samples per tile (MMA N)
+  constexpr int NB = KC == 1 ? 2 : 1;   // B buffers
+  constexpr int SEG = 1024 / SN;        // tiles per CTA
+  constexpr unsigned SA = KC * SC_CH;   // one A plane
   extern __shared__ __align__(1024) unsigned char sc_dsm[];
   unsigned char* sm = sc_dsm + ((1024 - (tc::smem_u32(sc_dsm) & 1023)) & 1023);
   __shared__ __align__(8) unsigned long long bars[4];  // bfull[2], mdone[2]
@@ -848,26 +859,27 @@ __global__ void __launch_bounds__(256)
   __shared__ int fail;
   const int tid = threadIdx.x, warp = tid >> 5;
   const int q0 = blockIdx.x * SC_M;
-  const int j0 = blockIdx.y * SC_SEG;  // first 256-sample tile of this CTA
-  const int ntile = min(SC_SEG, (nt_d + SC_N - 1) / SC_N - j0);
+  const int j0 = blockIdx.y * SEG;  // first sample tile of this CTA
+  const int ntile = min(SEG, (nt_d + SN - 1) / SN - j0);
   const unsigned bar0 = tc::smem_u32(&bars[0]);
   auto bfull = [&](int i) { return bar0 + 8u * i; };
   auto mdone = [&](int i) { return bar0 + 8u * (2 + i); };
-  if (warp == 0) tc::tmem_alloc(&tslot, 2 * SC_N);
+  if (warp == 0) tc::tmem_alloc(&tslot, 2 * SN);
   if (tid == 0) {
     for (int i = 0; i < 4; ++i) tc::mbar_init(bar0 + 8u * i, 1);
     fail = 0;
     tc::mbar_init_fence();
   }
-  const unsigned ah = tc::smem_u32(sm), al = ah + SC_A;
-  auto b_hi = [&](int b) { return tc::smem_u32(sm + 2 * SC_A + (size_t)b * SC_B); };
-  float* stage_all = reinterpret_cast<float*>(sm + 2 * SC_A + 2 * SC_B);  // [8 warps][32][SC_STG]
-  // A tile: row m = trace q0 + m, components c = 2k (re), 2k + 1 (im), zero past 2 nf and ntr
+  const unsigned ah = tc::smem_u32(sm), al = ah + SA;
+  auto b_hi = [&](int b) { return tc::smem_u32(sm + 2 * SA + (size_t)b * SC_B); };
+  float* stage_all = reinterpret_cast<float*>(sm + 2 * SA + NB * SC_B);  // [8 warps][32][SC_STG]
+  // A tile: row m = trace q0 + m, components c = 2k (re), 2k + 1 (im), zero past 2 nf and ntr;
+  // the threads of half h take frequencies 16 KC h .. 16 KC h + 16 KC - 1
   {
     const int m = tid & (SC_M - 1), q = q0 + m;
     const int sidx = q / nrec, r = q % nrec;
 #pragma unroll 4
-    for (int k = (tid >> 7) * 16; k < (tid >> 7) * 16 + 16; ++k) {
+    for (int k = (tid >> 7) * 16 * KC; k < (tid >> 7) * 16 * KC + 16 * KC; ++k) {
       float2 x = make_float2(0.f, 0.f);
       if (q < ntr && k < nf) {
         x = Dh[((long long)k * nrec + r) * ld + s0 + sidx];
@@ -878,9 +890,10 @@ __global__ void __launch_bounds__(256)
       const __nv_bfloat162 h = __floats2bfloat162_rn(x.x, x.y);
       const float2 hf = __bfloat1622float2(h);
       const __nv_bfloat162 l = __floats2bfloat162_rn(x.x - hf.x, x.y - hf.y);
-      // bytes 4k .. 4k + 3 of row m: chunk k / 4, offset 4 (k % 4)
-      const unsigned off =
-          (unsigned)((m >> 3) * 1024 + (m & 7) * 128 + ((((k >> 2) ^ (m & 7))) << 4) + ((k & 3) << 2));
+      // chunk k / 32; bytes 4 (k % 32) .. + 3 of row m: 16-byte chunk (k % 32) / 4, offset 4 (k % 4)
+      const int kl = k & 31;
+      const unsigned off = (unsigned)((k >> 5) * SC_CH + (m >> 3) * 1024 + (m & 7) * 128 +
+                                      ((((kl >> 2) ^ (m & 7))) << 4) + ((kl & 3) << 2));
       asm volatile("st.shared.u32 [%0], %1;" ::"r"(ah + off), "r"(*reinterpret_cast<const unsigned*>(&h))
                    : "memory");
       asm volatile("st.shared.u32 [%0], %1;" ::"r"(al + off), "r"(*reinterpret_cast<const unsigned*>(&l))
@@ -893,15 +906,15 @@ __global__ void __launch_bounds__(256)
   tc::tc_fence_after();
   const unsigned tmem = tslot;
   auto issue_b = [&](int j) {
-    tc::mbar_expect_tx(bfull(j & 1), SC_B);
-    tc::bulk_g2s(b_hi(j & 1), tws + (size_t)(j0 + j) * SC_B, SC_B, bfull(j & 1));
+    tc::mbar_expect_tx(bfull(j % NB), SC_B);
+    tc::bulk_g2s(b_hi(j % NB), tws + (size_t)(j0 + j) * SC_B, SC_B, bfull(j % NB));
   };
   if (tid == 0 && ntile > 0) issue_b(0);
-  const unsigned idesc = tc::idesc_bf16(SC_M, SC_N, 0, 0);
+  const unsigned idesc = tc::idesc_bf16(SC_M, SN, 0, 0);
   const bool vec = VEC;
   int issued = ntile > 0 ? 1 : 0, waited = 0;
   bool ok = true;
-  auto epilogue = [&](int j) {  // TMEM buffer j % 2 -> mult[q][256 (j0 + j) ..]
+  auto epilogue = [&](int j) {  // TMEM buffer j % 2 -> mult[q][SN (j0 + j) ..]
     const bool got = tc::mbar_wait(mdone(j & 1), (j >> 1) & 1);
     if (!__all_sync(0xffffffffu, got)) {
       ok = false;
@@ -910,19 +923,19 @@ __global__ void __launch_bounds__(256)
     tc::tc_fence_after();
     const int qq = warp & 3, hh = warp >> 2, lane = tid & 31;
     const unsigned base =
-        tmem + ((unsigned)(qq * 32) << 16) + (unsigned)((j & 1) * SC_N + hh * (SC_N / 2));
+        tmem + ((unsigned)(qq * 32) << 16) + (unsigned)((j & 1) * SN + hh * (SN / 2));
     // each 32 x 32 block goes through this warp's staging tile so that a store instruction
     // writes four full 128-byte rows: lanes 8i .. 8i + 7 cover row 4p + i of pass p
     float* stg = stage_all + warp * (32 * SC_STG);
 #pragma unroll 1
-    for (int c0 = hh * (SC_N / 2); c0 < (hh + 1) * (SC_N / 2); c0 += 32) {
+    for (int c0 = hh * (SN / 2); c0 < (hh + 1) * (SN / 2); c0 += 32) {
       float v[32];
-      tc::tmem_ld32(base + (unsigned)(c0 - hh * (SC_N / 2)), v);
+      tc::tmem_ld32(base + (unsigned)(c0 - hh * (SN / 2)), v);
 #pragma unroll
       for (int i = 0; i < 32; i += 4)
         *reinterpret_cast<float4*>(stg + lane * SC_STG + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
       __syncwarp();
-      const int t = (j0 + j) * SC_N + c0 + 4 * (lane & 7);
+      const int t = (j0 + j) * SN + c0 + 4 * (lane & 7);
 #pragma unroll
       for (int pp = 0; pp < 8; ++pp) {
         const int rl = 4 * pp + (lane >> 3);
@@ -947,23 +960,35 @@ __global__ void __launch_bounds__(256)
   for (int j = 0; j < ntile; ++j) {
     if (tid == 0) {
       // TMEM buffer j % 2 was drained by the epilogue of tile j - 2 (before the last barrier)
-      if (!tc::mbar_wait(bfull(j & 1), (j >> 1) & 1)) {
+      if (!tc::mbar_wait(bfull(j % NB), (j / NB) & 1)) {
         fail = 1;
       } else {
         waited = j + 1;
         tc::tc_fence_after();
-        const unsigned dt = tmem + (unsigned)((j & 1) * SC_N);
-        const unsigned bh = b_hi(j & 1), bl = bh + SC_N * 128;
+        const unsigned dt = tmem + (unsigned)((j & 1) * SN);
+        const unsigned bh = b_hi(j % NB), bl = bh + KC * SN * 128;
 #pragma unroll
-        for (int ks = 0; ks < 4; ++ks) {
-          const unsigned o = 32u * ks;
-          const uint64_t dah = tc::sdesc_sw128(ah + o), dal = tc::sdesc_sw128(al + o);
-          const uint64_t dbh = tc::sdesc_sw128(bh + o), dbl = tc::sdesc_sw128(bl + o);
-          tc::mma_bf16(dt, dah, dbh, idesc, ks > 0);
-          tc::mma_bf16(dt, dah, dbl, idesc, true);
-          tc::mma_bf16(dt, dal, dbh, idesc, true);
-        }
+        for (int kc = 0; kc < KC; ++kc)
+#pragma unroll
+          for (int ks = 0; ks < 4; ++ks) {
+            const unsigned oa = kc * SC_CH + 32u * ks, ob = kc * SN * 128 + 32u * ks;
+            const uint64_t dah = tc::sdesc_sw128(ah + oa), dal = tc::sdesc_sw128(al + oa);
+            const uint64_t dbh = tc::sdesc_sw128(bh + ob), dbl = tc::sdesc_sw128(bl + ob);
+            tc::mma_bf16(dt, dah, dbh, idesc, kc > 0 || ks > 0);
+            tc::mma_bf16(dt, dah, dbl, idesc, true);
+            tc::mma_bf16(dt, dal, dbh, idesc, true);
+          }
         tc::mma_commit(mdone(j & 1));
+        // one B buffer: the next tile's twiddles load once this tile's MMAs are done, while
+        // the previous tile drains
+        if (NB == 1 && j + 1 < ntile) {
+          if (!tc::mbar_wait(mdone(j & 1), (j >> 1) & 1)) {
+            fail = 1;
+          } else {
+            issue_b(j + 1);
+            issued = j + 2;
+          }
+        }
       }
     }
     __syncthreads();
@@ -978,7 +1003,7 @@ __global__ void __launch_bounds__(256)
         break;
       }
     }
-    if (tid == 0 && j + 1 < ntile) {
+    if (NB == 2 && tid == 0 && j + 1 < ntile) {
       if (j == 0 || ok) {
         issue_b(j + 1);
         issued = j + 2;
@@ -988,38 +1013,40 @@ __global__ void __launch_bounds__(256)
   }
   if (ok && ntile > 0) epilogue(ntile - 1);
   if (tid == 0) {  // no copy or MMA left in flight (bounded)
-    for (int j = waited; j < issued; ++j) tc::mbar_wait(bfull(j & 1), (j >> 1) & 1);
+    for (int j = waited; j < issued; ++j) tc::mbar_wait(bfull(j % NB), (j / NB) & 1);
     if (waited > 0) tc::mbar_wait(mdone((waited - 1) & 1), ((waited - 1) >> 1) & 1);
   }
   const bool okall = __syncthreads_and(ok) && !fail;
   if (!okall && tid == 0) atomicExch(err, 1);
   tc::tc_fence_before();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, 2 * SC_N);
+  if (warp == 0) tc::tmem_dealloc(tmem, 2 * SN);
 }
 
-// Synthesis twiddle tiles: for every 256 samples, a hi and a lo tile of [256 samples][64
-// components] bf16 in the K-major 128-byte swizzle (row t, component c at byte (t/8)*1024 +
+// Synthesis twiddle tiles: for every sample tile (256 samples for 2 nf <= 64, else 128), a hi and
+// a lo plane, each [KC chunks of 64 components][tile samples][64 components] bf16 in the K-major
+// 128-byte swizzle (row t, component c of chunk kc at byte kc * rows * 128 + (t/8)*1024 +
 // (t%8)*128 + (((2c/16) ^ (t%8)) * 16) + 2c%16); component 2k = cos(2 pi f_k t dt), 2k + 1 =
 // -sin(2 pi f_k t dt) with the phase reduced as 2 pi frac(f_k t dt) in double precision; hi =
 // bf16(w), lo = bf16(w - hi); components >= 2 nf and samples >= nt are zero.
 std::vector<unsigned char> synth_twiddle_tiles(const std::vector<double>& f, double dt, int nt) {
   const int nf = (int)f.size();
-  const int ntile = (nt + SC_N - 1) / SC_N;
+  const int kc_n = sc_kc(nf), sn = sc_n(kc_n);
+  const int ntile = (nt + sn - 1) / sn;
   std::vector<unsigned char> out((size_t)ntile * SC_B, 0);
   for (int t = 0; t < nt; ++t) {
-    unsigned char* hi = out.data() + (size_t)(t / SC_N) * SC_B;
-    unsigned char* lo = hi + (size_t)SC_N * 128;
-    const int r = t % SC_N;
-    for (int k = 0; k < nf && 2 * k + 1 < 64; ++k) {
+    unsigned char* hi = out.data() + (size_t)(t / sn) * SC_B;
+    unsigned char* lo = hi + (size_t)kc_n * sn * 128;
+    const int r = t % sn;
+    for (int k = 0; k < nf && 2 * k + 1 < 64 * kc_n; ++k) {
       double ph = f[k] * (double)t * dt;
       ph -= std::floor(ph);
       const double a = 2.0 * M_PI * ph;
       const double v[2] = {std::cos(a), -std::sin(a)};
       for (int qq = 0; qq < 2; ++qq) {
-        const int c = 2 * k + qq;
-        const size_t off = (size_t)(r >> 3) * 1024 + (r & 7) * 128 +
-                           ((((2 * c) >> 4) ^ (r & 7)) << 4) + ((2 * c) & 15);
+        const int c = 2 * k + qq, kc = c / 64, cl = c % 64;
+        const size_t off = (size_t)kc * sn * 128 + (size_t)(r >> 3) * 1024 + (r & 7) * 128 +
+                           ((((2 * cl) >> 4) ^ (r & 7)) << 4) + ((2 * cl) & 15);
         const __nv_bfloat16 h = __float2bfloat16_rn((float)v[qq]);
         const __nv_bfloat16 l = __float2bfloat16_rn((float)(v[qq] - (double)__bfloat162float(h)));
         std::memcpy(hi + off, &h, 2);
@@ -1034,14 +1061,16 @@ cudaError_t launch_synth_tc(const float2* Dh, int nrec, int ns, int ld, int s0, 
                             const float* w, const unsigned char* tws, int nt_d, float* mult,
                             int* err, cudaStream_t st) {
   const int ntr = nrec * ns;
-  const size_t smem = synth_tc_smem();
+  const int kc = sc_kc(nf), sn = sc_n(kc);
+  const size_t smem = synth_tc_smem(kc);
   const bool vec = (nt_d & 3) == 0 && (reinterpret_cast<uintptr_t>(mult) & 15) == 0;
-  auto kern = vec ? k_synth_tc<true> : k_synth_tc<false>;
+  auto kern = kc == 1 ? (vec ? k_synth_tc<true, 1> : k_synth_tc<false, 1>)
+                      : (vec ? k_synth_tc<true, 2> : k_synth_tc<false, 2>);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   count_launches(1);
-  const int ntile = (nt_d + SC_N - 1) / SC_N;
-  const dim3 grid((ntr + SC_M - 1) / SC_M, (ntile + SC_SEG - 1) / SC_SEG);
+  const int ntile = (nt_d + sn - 1) / sn, seg = 1024 / sn;
+  const dim3 grid((ntr + SC_M - 1) / SC_M, (ntile + seg - 1) / seg);
   kern<<<grid, 256, smem, st>>>(Dh, nrec, ld, s0, nf, w, tws, nt_d, mult, ntr, err);
   return cudaGetLastError();
 }
@@ -1050,7 +1079,7 @@ cudaError_t launch_synth(const float2* Dh, int nrec, int ns, int ld, int s0, int
                          const float2* tw, int nt_d, float* mult, cudaStream_t st,
                          const unsigned char* tws, int* err) {
   if (nf > NFMAX) return cudaErrorInvalidValue;
-  if (tws && err && 2 * nf <= 64)
+  if (tws && err && 2 * nf <= 128)
     return launch_synth_tc(Dh, nrec, ns, ld, s0, nf, w, tws, nt_d, mult, err, st);
   const int ntr = nrec * ns;
   const size_t smem = sizeof(float2) * (size_t)nf * SY_TR + 2 * sizeof(float) * (size_t)nf * SY_TP;
