@@ -113,7 +113,11 @@ typedef struct {
     const int32_t *rec_ix; /* [nrec], host */
     int32_t nfreq;
     const double *freq_hz; /* [nfreq], host */
-    int32_t batch_receivers; /* receivers propagated together; 0 = min(nrec, 16) */
+    int32_t batch_receivers; /* receivers propagated together; 0 = chosen by the library: with
+                                the per-step FD kernel and more than 8 receivers, the first
+                                egh_green times the FD step per receiver for 8, 16 and 32 (at
+                                most nrec) and keeps 16 unless another is 3% faster; else
+                                min(nrec, 16) */
     int32_t dft_chunk;       /* levels per transform chunk: 32, 64, ..., 2048; 0 = 512 (the
                                 snapshot ring holds 2 chunks x batch_receivers levels) */
     int32_t gram_splits;     /* split of the grid sum in the Gram; 0 = chosen by the library
@@ -146,7 +150,8 @@ typedef struct {
     double mu;                 /* penalty used by the last egh_hessian */
     int32_t nz_pad, nx_pad;    /* padded grid */
     int32_t pitch;             /* row pitch (floats) of the device wavefield layout */
-    int32_t batch_receivers, dft_chunk, gram_splits;
+    int32_t batch_receivers, dft_chunk, gram_splits;  /* batch_receivers: in use (the timed
+                                                          choice once egh_green has run) */
     int64_t kernel_launches;   /* kernels this library has launched since it was loaded (all contexts) */
     int32_t fd_rows;           /* FD rows per warp in use (0 until chosen) */
     int32_t pad_;

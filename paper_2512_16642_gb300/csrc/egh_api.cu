@@ -47,6 +47,8 @@ struct egh_ctx {
   std::vector<double> freqs;
   std::vector<float> wsyn;
   int B = 0, K = 0, splits = 0;
+  int Bcap = 0;         // receivers the FD state slots hold (>= B)
+  bool tune_B = false;  // B is timed on the first egh_green (8, 16 or 32 receivers)
   int fd_tz = 0;  // FD rows per warp of the per-step kernel (0 = library default)
   int fd_kernel = 2;  // 1: resident solver (fd_resident.cu), 2: one kernel per step (fd.cu)
   ResGeom rg{};       // resident solver: tile grid and pairs per block
@@ -284,7 +286,7 @@ egh_status prepare_model(egh_ctx* ctx, const float* vel, cudaStream_t stream) {
 
 // FD state slot of level t: [3][B/2][F] float2.
 float2* slot(egh_ctx* ctx, int t) {
-  return ctx->lev + (long long)(t % 3) * ((ctx->B + 1) / 2) * ctx->L.F;
+  return ctx->lev + (long long)(t % 3) * ((ctx->Bcap + 1) / 2) * ctx->L.F;
 }
 
 // Snapshot output for ring slot j (0 .. 2K-1).
@@ -537,6 +539,10 @@ egh_status egh_create(const egh_config* cfg, egh_ctx** out) {
     else
       ctx->B = c.batch_receivers ? std::min(c.batch_receivers, c.nrec) : std::min(c.nrec, 16);
     ctx->Bp = 2 * ((ctx->B + 1) / 2);
+    // with the per-step kernel and no batch given, B is timed on the first egh_green among 8,
+    // 16 and 32 receivers: the state slots hold the largest
+    ctx->tune_B = !res && c.batch_receivers == 0 && c.nrec > 8;
+    ctx->Bcap = ctx->tune_B ? std::min(c.nrec, 32) : ctx->B;
   }
 
   ctx->prec = c.precision;
@@ -570,7 +576,7 @@ egh_status egh_create(const egh_config* cfg, egh_ctx** out) {
     }                                                           \
   } while (0)
   ALLOC(ctx->coef, F * sizeof(float2), "coefficients");
-  ALLOC(ctx->lev, (size_t)3 * ((ctx->B + 1) / 2) * F * sizeof(float2), "FD state");
+  ALLOC(ctx->lev, (size_t)3 * ((ctx->Bcap + 1) / 2) * F * sizeof(float2), "FD state");
   if (ctx->fd_kernel == 1) {
     ALLOC(ctx->xbuf, fd_resident_xbuf_float4(ctx->rg) * sizeof(float4), "FD halo exchange");
     ALLOC(ctx->rflags, sizeof(int) * fd_resident_flags(ctx->rg), "FD step counters");
@@ -604,7 +610,7 @@ egh_status egh_create(const egh_config* cfg, egh_ctx** out) {
     CK(cudaMemset(ctx->coef, 0, F * sizeof(float2)));
     // guard rows and padding columns of every state slot, and the padding points of every
     // snapshot slot, stay zero for the life of the context
-    CK(cudaMemset(ctx->lev, 0, (size_t)3 * ((ctx->B + 1) / 2) * F * sizeof(float2)));
+    CK(cudaMemset(ctx->lev, 0, (size_t)3 * ((ctx->Bcap + 1) / 2) * F * sizeof(float2)));
 
     CK(cudaMemcpy(ctx->twt, twt.data(), twt.size(), cudaMemcpyHostToDevice));
     CK(fd_prepare(c.nfreq));
@@ -624,7 +630,9 @@ egh_status egh_create(const egh_config* cfg, egh_ctx** out) {
     CK(cudaEventCreate(&ctx->ev_gram[0]));
     CK(cudaEventCreate(&ctx->ev_gram[1]));
     {
-      const long long nchunks = (long long)((c.nrec + ctx->B - 1) / ctx->B) * ((c.nt + ctx->K - 1) / ctx->K);
+      // the smallest batch a timing of B can choose has the most chunks
+      const int bmin = ctx->tune_B ? 8 : ctx->B;
+      const long long nchunks = (long long)((c.nrec + bmin - 1) / bmin) * ((c.nt + ctx->K - 1) / ctx->K);
       ctx->ev_fd.assign(2 * nchunks, nullptr);
       ctx->ev_dft.assign(2 * nchunks, nullptr);
       for (cudaEvent_t& e : ctx->ev_fd) CK(cudaEventCreate(&e));
@@ -676,13 +684,57 @@ namespace {
 // with the table ctx->twt.  Otherwise the band-limited form: wavelet sample s_n is injected at
 // the receiver into level n + 1, every decim-th level is recorded and transformed with `twt`
 // (which folds in the factor decim and the division by the wavelet's spectrum).
+// Receivers per batch, timed once per context before the ring (sized for the batch) exists: the
+// FD step's time per receiver-step for 8, 16 and 32 receivers (each with its one-wave rows per
+// warp; 24 steps on the state slots, which the run rewrites, best of three passes after a
+// warm-up).  16 is kept unless another is 3% faster per receiver.  The transform's work per
+// receiver does not depend on the batch, and it runs beside the FD steps for every choice.
+egh_status tune_batch(egh_ctx* ctx, cudaStream_t stream) {
+  const Layout& L = ctx->L;
+  cudaStream_t fs = ctx->fdst;
+  CK(cudaEventRecord(ctx->ev_tune[0], stream));  // after the coefficients
+  CK(cudaStreamWaitEvent(fs, ctx->ev_tune[0], 0));
+  const SnapOut none{nullptr, 0, 0};
+  const int def_b = std::min(ctx->Bcap, 16);
+  float best = 1e30f, def_per = 1e30f;
+  int best_b = def_b;
+  for (int b : {8, 16, 32}) {
+    if (b > ctx->Bcap) continue;
+    const int np = (b + 1) / 2, tz = fd_rows_one_wave(L, np);
+    float tb = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {
+      float ms = 0.f;
+      CK(cudaEventRecord(ctx->ev_tune[0], fs));
+      for (int t = 2; t < 26; ++t)
+        CK(launch_fd_step(slot(ctx, t - 1), slot(ctx, t - 2), slot(ctx, t), ctx->coef, L, ctx->S,
+                          np, none, fs, tz));
+      CK(cudaEventRecord(ctx->ev_tune[1], fs));
+      CK(cudaEventSynchronize(ctx->ev_tune[1]));
+      CK(cudaEventElapsedTime(&ms, ctx->ev_tune[0], ctx->ev_tune[1]));
+      if (rep > 0) tb = std::min(tb, ms);
+    }
+    const float per = tb / (float)b;
+    if (per < best) {
+      best = per;
+      best_b = b;
+    }
+    if (b == def_b) def_per = per;
+  }
+  ctx->B = best < 0.97f * def_per ? best_b : def_b;
+  ctx->Bp = 2 * ((ctx->B + 1) / 2);
+  ctx->st.batch_receivers = ctx->B;
+  ctx->tune_B = false;
+  return EGH_OK;
+}
+
 egh_status green_run(egh_ctx* ctx, const float* vel, cudaStream_t stream, const float* wav, int nw,
                      int decim, const unsigned char* twt) {
   CK(cudaSetDevice(ctx->dev));
   ctx->state = ST_CREATED;
-  egh_status s = ensure_green_buffers(ctx);
+  egh_status s = prepare_model(ctx, vel, stream);
   if (s) return s;
-  s = prepare_model(ctx, vel, stream);
+  if (ctx->tune_B && (s = tune_batch(ctx, stream))) return s;
+  s = ensure_green_buffers(ctx);
   if (s) return s;
   const Layout& L = ctx->L;
   const int K = ctx->K, B = ctx->B, nt = ctx->nt;
@@ -696,7 +748,7 @@ egh_status green_run(egh_ctx* ctx, const float* vel, cudaStream_t stream, const 
   const long long per = (long long)ctx->Bp * L.G;  // snapshot ring: elements per slot
   // resident solver: levels ta .. t1-1 of a chunk whose level t0 sits in ring slot sbase
   auto resident = [&](int ta, int t0, int t1, int sbase, int np, int D, int sr, int expire) {
-    return launch_fd_resident(ctx->rg, sr, ctx->lev, (ctx->B + 1) / 2, L, ctx->coef, ctx->S, np, ta,
+    return launch_fd_resident(ctx->rg, sr, ctx->lev, (ctx->Bcap + 1) / 2, L, ctx->coef, ctx->S, np, ta,
                               t1 - ta, t0, D, sbase, ctx->snap, per, 2LL * K * per, L.G, ctx->xbuf,
                               ctx->rflags, ctx->d_err, expire, fs);
   };
@@ -825,7 +877,7 @@ egh_status green_run(egh_ctx* ctx, const float* vel, cudaStream_t stream, const 
       // there the transform takes one CTA per tile and fills the SMs between FD launches.
       const bool alone = b0 + B >= ctx->nrec && c == nchunk - 1;
       const bool slim = dft_ncomp(ctx->nf) <= 64 && ctx->fd_kernel != 1;
-      const int beside = fd_block_smem((std::min(B, ctx->nrec) + 1) / 2);
+      const long long beside = fd_sm_smem((std::min(B, ctx->nrec) + 1) / 2, ctx->fd_tz);
       CK(launch_dft_tc(ctx->tmap, twt, ctx->nf, sbase, m1 - m0, m0, L, ctx->gh, ctx->ghb,
                        (m1 == ntd && ctx->ghb) ? 1 : 0, b0, nb, ctx->nrec, ctx->d_err, expire,
                        alone ? 3 : slim ? 1 : 0, (alone || !slim) ? 0 : beside, ctx->side));

@@ -80,15 +80,18 @@ std::vector<unsigned char> dft_twiddle_tiles(const std::vector<double>& f, doubl
                                              const std::vector<std::complex<double>>* scale = nullptr);
 cudaError_t make_snap_tmap(CUtensorMap* tm, void* base, long long G, int Bp, int nslot);
 // per_sm: CTAs per SM of the persistent transform (1 beside the FD steps, more when it runs
-// alone; 0: one CTA per tile); beside_smem: dynamic shared memory of one FD CTA that the
-// transform runs beside (0: none), which sizes the transform's CTAs so that an SM holds one of
-// them next to two FD CTAs
+// alone; 0: one CTA per tile); beside_smem: shared memory (reserved parts included) of the FD
+// CTAs an SM holds beside the transform (0: none), which sizes the transform's CTAs so that an
+// SM holds one of them next to the FD CTAs and never two
 cudaError_t launch_dft_tc(const CUtensorMap& tmap, const unsigned char* twt, int nf, int slot0,
                           int kcount, int n0, const Layout& L, float* gh, __nv_bfloat16* ghb,
                           int last, int rec0, int nvalid, int nrec_all, int* err, int expire,
-                          int per_sm, int beside_smem, cudaStream_t st);
+                          int per_sm, long long beside_smem, cudaStream_t st);
 // dynamic shared memory of one k_fd_step CTA for npairs receiver pairs
 int fd_block_smem(int npairs);
+// shared memory (reserved parts included) of the k_fd_step CTAs of npairs pairs and tz rows per
+// warp that one SM holds at once; 0 if it cannot be queried
+long long fd_sm_smem(int npairs, int tz);
 
 // ---- fd_resident.cu ---------------------------------------------------------------------------
 // The padded grid as TR x TC tiles of TZ x TX points (TX % 4 == 0), one block per tile, all

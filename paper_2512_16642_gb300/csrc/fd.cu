@@ -341,6 +341,29 @@ int fd_rows_per_warp_default() { return EGH_FD_TZDEF; }
 
 int fd_block_smem(int npairs) { return (int)(sizeof(float4) * FD_RING * 36 * npairs); }
 
+long long fd_sm_smem(int npairs, int tz) {
+  int dev = 0, occ = 0, reserved = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess)
+    return 0;
+  const void* k = nullptr;
+  switch (tz) {
+    case 12: k = (const void*)k_fd_step<12>; break;
+    case 16: k = (const void*)k_fd_step<16>; break;
+    case 18: k = (const void*)k_fd_step<18>; break;
+    case 20: k = (const void*)k_fd_step<20>; break;
+    case 24: k = (const void*)k_fd_step<24>; break;
+    case 32: k = (const void*)k_fd_step<32>; break;
+    default: k = (const void*)k_fd_step<EGH_FD_TZDEF>; break;
+  }
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, 32 * npairs, fd_block_smem(npairs)) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return (long long)occ * (fd_block_smem(npairs) + reserved);
+}
+
 // Rows per warp that fill one wave: the smallest choice whose tiles (PX/64 x ceil(NZ / TZ) CTAs)
 // all fit the GPU's resident CTA slots at once, so that no SM carries more rows than another;
 // the library default if none does.
@@ -685,7 +708,7 @@ __global__ void __launch_bounds__(128, 16)
 cudaError_t launch_dft_tc(const CUtensorMap& tmap, const unsigned char* twt, int nf, int slot0,
                           int kcount, int n0, const Layout& L, float* gh, __nv_bfloat16* ghb,
                           int last, int rec0, int nvalid, int nrec_all, int* err, int expire,
-                          int per_sm, int beside_smem, cudaStream_t st) {
+                          int per_sm, long long beside_smem, cudaStream_t st) {
   const int N = dft_ncomp(nf);
   if (L.G % TD_M != 0 || N > TD_NMAX || kcount < 1 || slot0 % TD_S != 0 || n0 % TD_S != 0 ||
       nvalid < 1 || per_sm < 0 || per_sm > 3 || beside_smem < 0)
@@ -704,13 +727,14 @@ cudaError_t launch_dft_tc(const CUtensorMap& tmap, const unsigned char* twt, int
   int nring = 2;
   size_t smem = dft_smem_ring(nf, 2);
   if (beside_smem > 0) {
-    // Beside two FD CTAs of beside_smem bytes each: the largest size that still fits there, if
-    // that size also keeps a second transform CTA off the SM.  A CTA per SM is then all an SM
-    // can take, wherever the launch finds free room (at a chunk boundary, SMs whose FD CTAs
-    // have left would otherwise take two or three and hold back the next FD step).  The padded
-    // size holds a third stage where it has room: one CTA per SM keeps three copies in flight.
+    // Beside the FD CTAs an SM holds (beside_smem bytes of shared memory in all, reserved parts
+    // included): the largest size that still fits there, if that size also keeps a second
+    // transform CTA off the SM.  A CTA per SM is then all an SM can take, wherever the launch
+    // finds free room (at a chunk boundary, SMs whose FD CTAs have left would otherwise take two
+    // or three and hold back the next FD step).  The padded size holds a third stage where it
+    // has room: one CTA per SM keeps three copies in flight.
     const long long cta = (long long)fa.sharedSizeBytes + reserved;
-    const long long fit = (long long)sm_smem - 2LL * (beside_smem + reserved) - cta;
+    const long long fit = (long long)sm_smem - beside_smem - cta;
     if (fit >= (long long)smem && 2 * (fit + cta) > sm_smem) {
       smem = (size_t)fit;
       if ((long long)dft_smem_ring(nf, 3) <= fit) nring = 3;

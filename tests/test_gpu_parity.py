@@ -346,6 +346,36 @@ def test_ragged_case():
     assert rel(gm["mult"], o["mult"]) <= MULT_TOL
 
 
+def test_timed_batch_equals_given_batch():
+    """batch_receivers = 0 with more than 8 receivers: the first egh_green times 8, 16 and 32
+    receivers per batch and reports its choice; the Green functions and Hessians are the same bit
+    for bit as with that batch given (a receiver's solve and transform do not depend on the
+    batch), and match the FP64 oracle."""
+    c = synth.case_tiny(seed=12, nz=21, nx=45, nsponge=6, nrec=40, nt=70, dt=1e-3)
+    c["freqs"] = np.array([11.0, 27.0])
+    rng = np.random.default_rng(6)
+    resid = synth.bandlimited_noise(rng, (3, 40, 90), c.dt, 5.0, 40.0)
+    torch = _torch()
+    from paper_2512_16642_gb300 import egh
+
+    with _ctx(c, dft_chunk=32) as ctx:
+        assert ctx.stats()["batch_receivers"] == 16  # before the first egh_green
+        ctx.green(torch.from_numpy(np.asarray(c.vel_true, np.float32)).cuda())
+        chosen = ctx.stats()["batch_receivers"]
+        gh_auto = ctx.get_green()
+        ctx.hessian(egh.EGH_MU_REL_MEANDIAG, c.mu_alpha)
+        Q_auto = ctx.get_hessian(False)
+    assert chosen in (8, 16, 32)
+    g = _gpu_only(c, c.vel_true, resid, batch_receivers=chosen, dft_chunk=32)
+    np.testing.assert_array_equal(gh_auto, g["gh"])
+    np.testing.assert_array_equal(Q_auto, g["Q"])
+    o, g8 = _run_both(c, c.vel_true, resid=resid, ctx_kw=dict(batch_receivers=8, dft_chunk=32))
+    np.testing.assert_array_equal(g8["gh"], g["gh"])
+    assert rel(g["gh"], o["gh"]) <= GREEN_TOL
+    for k in range(2):
+        assert rel(g["Q"][k], o["Q"][k]) <= HESS_TOL
+
+
 def test_single_receiver_single_frequency_two_steps():
     c = synth.case_tiny(seed=3, nz=9, nx=9, nsponge=2, nrec=1, nt=2)
     c["freqs"] = np.array([50.0])
