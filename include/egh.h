@@ -119,7 +119,10 @@ typedef struct {
                                 most nrec) and keeps 16 unless another is 3% faster; else
                                 min(nrec, 16) */
     int32_t dft_chunk;       /* levels per transform chunk: 32, 64, ..., 2048; 0 = 512 (the
-                                snapshot ring holds 2 chunks x batch_receivers levels) */
+                                snapshot ring holds 2 chunks x batch_receivers levels); a
+                                chunk longer than the record is cut to the smallest power of
+                                two, at least 32, that holds nt levels (the same arithmetic in
+                                one chunk, a smaller ring) */
     int32_t gram_splits;     /* split of the grid sum in the Gram; 0 = chosen by the library
                                 (tensor-core Gram: half, once or twice a default, timed on the
                                 first egh_hessian) */
@@ -451,6 +454,31 @@ egh_status egh_set_mu(egh_ctx *ctx, double mu, void *stream);
  * block differ from those of the block alone).  EGH_EINVAL if the entries differ. */
 egh_status egh_set_synthesis_frequencies(egh_ctx *ctx, const double *all_freq_hz, int32_t nall,
                                          int32_t k0);
+
+/* ---- Checkpoint of a factored Hessian set ------------------------------------------------- *
+ * The Hessians of Algorithm 2 depend only on the model and the receivers; a set built once can
+ * be stored and reused by later runs without the Green stage.  File layout (little-endian):
+ *   bytes 0-7   magic "EGHQSET1";
+ *   bytes 8-15  uint64 length H of the header;
+ *   H bytes     JSON header: format, version, nrec, nfreq, freq_hz[nfreq], dt, nt, precision, mu,
+ *               rec_iz[nrec], rec_ix[nrec] (physical grid), and per array its name, dtype,
+ *               shape and byte offset in the payload;
+ *   payload     Q [nfreq][nrec][nrec] complex64 (H_k + mu I, as egh_get_hessian with factored =
+ *               0 returns it), then L [nfreq][nrec][nrec] complex64 (the factors, as
+ *               egh_get_hessian with factored = 1 returns them).
+ * Doubles are written with 17 significant digits, so they read back bit for bit. */
+
+/* Writes the context's factored set to `path` (host file, overwritten).  EGH_ESTATE before
+ * egh_factor; EGH_EINVAL if the file cannot be written.  Blocks. */
+egh_status egh_save(egh_ctx *ctx, const char *path);
+
+/* Reads a set written by egh_save into a context created with the same receivers, frequencies,
+ * record (dt, nt) and precision: Q and mu are loaded and factored again (the same kernels, so the
+ * factors equal the saved ones on the same library and device), after which the context stands
+ * as after egh_factor: egh_deblur, egh_get_hessian and egh_save work without egh_green.
+ * EGH_EINVAL if the file cannot be read, is not such a file, is truncated, or does not match the
+ * context; EGH_ENOTPD as egh_factor.  Blocks. */
+egh_status egh_load(egh_ctx *ctx, const char *path);
 
 /* ---- Batched factorisation --------------------------------------------------------------- *
  * A batch groups contexts (survey patches of one model, any receiver counts, one device, one

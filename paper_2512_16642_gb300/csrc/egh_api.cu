@@ -501,6 +501,8 @@ egh_status egh_create(const egh_config* cfg, egh_ctx** out) {
   ctx->rec_ix.assign(c.rec_ix, c.rec_ix + c.nrec);
   ctx->freqs.assign(c.freq_hz, c.freq_hz + c.nfreq);
   ctx->K = c.dft_chunk ? c.dft_chunk : 512;
+  // a record shorter than the chunk is one chunk either way: keep the ring no longer than it
+  while (ctx->K > 32 && ctx->K / 2 >= c.nt) ctx->K /= 2;
   ctx->fd_tz = c.fd_rows;
 
   Layout& L = ctx->L;
@@ -1648,6 +1650,163 @@ egh_status egh_batch_factor(egh_batch* b, int32_t* bad_ctx, int32_t* bad_freq, v
 
 const char* egh_batch_last_error(const egh_batch* b) {
   return b ? b->err.c_str() : egh_last_error(nullptr);
+}
+
+}  // extern "C"
+
+namespace {
+
+constexpr char kSetMagic[8] = {'E', 'G', 'H', 'Q', 'S', 'E', 'T', '1'};
+
+void json_num(std::string& s, double v) {
+  char b[40];
+  snprintf(b, sizeof b, "%.17g", v);
+  s += b;
+}
+
+template <class T>
+void json_array(std::string& s, const std::vector<T>& v) {
+  s += '[';
+  for (size_t i = 0; i < v.size(); ++i) {
+    if (i) s += ", ";
+    json_num(s, (double)v[i]);
+  }
+  s += ']';
+}
+
+// The text after "key": in the header, or nullptr.
+const char* json_find(const std::string& h, const char* key) {
+  const std::string k = std::string("\"") + key + "\":";
+  const size_t p = h.find(k);
+  return p == std::string::npos ? nullptr : h.c_str() + p + k.size();
+}
+
+bool json_get(const std::string& h, const char* key, double* out) {
+  const char* p = json_find(h, key);
+  if (!p) return false;
+  char* end = nullptr;
+  *out = std::strtod(p, &end);
+  return end != p;
+}
+
+bool json_get_array(const std::string& h, const char* key, std::vector<double>* out) {
+  const char* p = json_find(h, key);
+  if (!p) return false;
+  while (*p == ' ') ++p;
+  if (*p++ != '[') return false;
+  out->clear();
+  for (;;) {
+    while (*p == ' ') ++p;
+    if (*p == ']') return true;
+    char* end = nullptr;
+    const double v = std::strtod(p, &end);
+    if (end == p) return false;
+    out->push_back(v);
+    p = end;
+    while (*p == ' ') ++p;
+    if (*p == ',') ++p;
+    else if (*p != ']') return false;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+egh_status egh_save(egh_ctx* ctx, const char* path) {
+  if (!ctx || !path) return fail(ctx, EGH_EINVAL, "NULL argument");
+  CK(cudaSetDevice(ctx->dev));
+  if (ctx->state < ST_FACTORED) return fail(ctx, EGH_ESTATE, "egh_save needs egh_factor first");
+  const size_t n = (size_t)ctx->nf * ctx->nrec * ctx->nrec;
+  std::vector<float2> q(n), l(n);
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpy(q.data(), ctx->Qh, n * sizeof(float2), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(l.data(), ctx->Lh, n * sizeof(float2), cudaMemcpyDeviceToHost));
+  const unsigned long long bytes = n * sizeof(float2);
+  std::string h = "{\"format\": \"egh Hessian set\", \"version\": 1, \"nrec\": ";
+  json_num(h, ctx->nrec);
+  h += ", \"nfreq\": ";
+  json_num(h, ctx->nf);
+  h += ", \"freq_hz\": ";
+  json_array(h, ctx->freqs);
+  h += ", \"dt\": ";
+  json_num(h, ctx->dt);
+  h += ", \"nt\": ";
+  json_num(h, ctx->nt);
+  h += ", \"precision\": ";
+  json_num(h, ctx->prec);
+  h += ", \"mu\": ";
+  json_num(h, ctx->mu);
+  h += ", \"rec_iz\": ";
+  json_array(h, ctx->rec_iz);
+  h += ", \"rec_ix\": ";
+  json_array(h, ctx->rec_ix);
+  const std::string shape =
+      "[" + std::to_string(ctx->nf) + ", " + std::to_string(ctx->nrec) + ", " + std::to_string(ctx->nrec) + "]";
+  h += ", \"arrays\": [{\"name\": \"Q\", \"dtype\": \"complex64\", \"shape\": " + shape +
+       ", \"offset\": 0}, {\"name\": \"L\", \"dtype\": \"complex64\", \"shape\": " + shape +
+       ", \"offset\": " + std::to_string(bytes) + "}]}";
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return fail(ctx, EGH_EINVAL, std::string("egh_save: cannot open ") + path);
+  const unsigned long long hl = h.size();
+  bool ok = std::fwrite(kSetMagic, 1, 8, f) == 8 && std::fwrite(&hl, 8, 1, f) == 1 &&
+            std::fwrite(h.data(), 1, h.size(), f) == h.size() &&
+            std::fwrite(q.data(), sizeof(float2), n, f) == n &&
+            std::fwrite(l.data(), sizeof(float2), n, f) == n;
+  ok = (std::fclose(f) == 0) && ok;
+  if (!ok) return fail(ctx, EGH_EINVAL, std::string("egh_save: write failed: ") + path);
+  return EGH_OK;
+}
+
+egh_status egh_load(egh_ctx* ctx, const char* path) {
+  if (!ctx || !path) return fail(ctx, EGH_EINVAL, "NULL argument");
+  CK(cudaSetDevice(ctx->dev));
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(ctx, EGH_EINVAL, std::string("egh_load: cannot open ") + path);
+  auto bad = [&](const std::string& why) {
+    std::fclose(f);
+    return fail(ctx, EGH_EINVAL, "egh_load: " + why);
+  };
+  char magic[8];
+  unsigned long long hl = 0;
+  if (std::fread(magic, 1, 8, f) != 8 || std::memcmp(magic, kSetMagic, 8) != 0)
+    return bad("not a Hessian set file");
+  if (std::fread(&hl, 8, 1, f) != 1 || hl == 0 || hl > (64ull << 20)) return bad("bad header length");
+  std::string h(hl, '\0');
+  if (std::fread(&h[0], 1, hl, f) != hl) return bad("truncated header");
+  double nrec = 0, nfreq = 0, dt = 0, nt = 0, prec = 0, mu = 0;
+  std::vector<double> fr, iz, ix;
+  if (!json_get(h, "nrec", &nrec) || !json_get(h, "nfreq", &nfreq) || !json_get(h, "dt", &dt) ||
+      !json_get(h, "nt", &nt) || !json_get(h, "precision", &prec) || !json_get(h, "mu", &mu) ||
+      !json_get_array(h, "freq_hz", &fr) || !json_get_array(h, "rec_iz", &iz) ||
+      !json_get_array(h, "rec_ix", &ix))
+    return bad("incomplete header");
+  if ((int)nrec != ctx->nrec || (int)nfreq != ctx->nf || (int)fr.size() != ctx->nf ||
+      (int)iz.size() != ctx->nrec || (int)ix.size() != ctx->nrec)
+    return bad("receiver or frequency count differs from the context's");
+  for (int k = 0; k < ctx->nf; ++k)
+    if (fr[k] != ctx->freqs[k]) return bad("frequencies differ from the context's");
+  for (int r = 0; r < ctx->nrec; ++r)
+    if ((int)iz[r] != ctx->rec_iz[r] || (int)ix[r] != ctx->rec_ix[r])
+      return bad("receiver positions differ from the context's");
+  if (dt != ctx->dt || (int)nt != ctx->nt) return bad("record (dt, nt) differs from the context's");
+  if ((int)prec != ctx->prec) return bad("precision differs from the context's");
+  if (!std::isfinite(mu) || mu < 0) return bad("mu is not a finite non-negative number");
+  const size_t n = (size_t)ctx->nf * ctx->nrec * ctx->nrec;
+  std::vector<float2> q(n);
+  if (std::fread(q.data(), sizeof(float2), n, f) != n) return bad("truncated payload (Q)");
+  {
+    std::vector<float2> l(n);  // the saved factors: present, recomputed below
+    if (std::fread(l.data(), sizeof(float2), n, f) != n) return bad("truncated payload (L)");
+  }
+  std::fclose(f);
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpy(ctx->Qh, q.data(), n * sizeof(float2), cudaMemcpyHostToDevice));
+  ctx->mu = mu;
+  ctx->st.mu = mu;
+  ctx->state = ST_HESSIAN;
+  int32_t bad_freq = -1;
+  return egh_factor(ctx, &bad_freq, nullptr);
 }
 
 }  // extern "C"

@@ -108,6 +108,8 @@ _SIGS = {
     "egh_import_green": ([_vp, _vp, _vp], ctypes.c_int),
     "egh_diag_sum": ([_vp, _f64p], ctypes.c_int),
     "egh_set_mu": ([_vp, ctypes.c_double, _vp], ctypes.c_int),
+    "egh_save": ([_vp, ctypes.c_char_p], ctypes.c_int),
+    "egh_load": ([_vp, ctypes.c_char_p], ctypes.c_int),
     "egh_set_synthesis_frequencies": ([_vp, _f64p, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
     "egh_get_refinement": ([_vp, _f64p, _i32p], ctypes.c_int),
     "egh_server_test_expire_wait": ([_vp, ctypes.c_int32], ctypes.c_int),
@@ -443,6 +445,14 @@ class Context:
 
     def set_mu(self, mu, stream=None):
         egh_set_mu(self.h, mu, stream)
+
+    def save(self, path):
+        """Writes the factored Hessian set to a file (egh_save)."""
+        _check(load().egh_save(self.h, os.fsencode(path)), self.h)
+
+    def load(self, path):
+        """Reads a Hessian set written by save into this context and factors it (egh_load)."""
+        _check(load().egh_load(self.h, os.fsencode(path)), self.h)
 
     def set_synthesis_frequencies(self, all_freq_hz, k0):
         egh_set_synthesis_frequencies(self.h, all_freq_hz, k0)

@@ -576,3 +576,70 @@ def test_resident_solver_equals_per_step_kernel(case):
             if fk == 1:
                 assert st["fd_tiles"] > 1
     assert np.array_equal(out[1], out[2])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_save_load_hessian_set(precision, tmp_path):
+    """egh_save after egh_factor, egh_load into a fresh context of the same receivers,
+    frequencies, record and precision: the loaded context deblurs without a Green stage, with the
+    same Hessians, factors and multipliers bit for bit.  The file's header is JSON with the
+    stated fields; a context with other frequencies, a truncated file and another file are
+    rejected with EGH_EINVAL, and saving before egh_factor is EGH_ESTATE."""
+    import json
+    import struct
+
+    torch = _torch()
+    from paper_2512_16642_gb300 import egh
+
+    c = synth.case_tiny(seed=13, nz=19, nx=33, nsponge=5, nrec=12, nt=60, dt=1e-3)
+    c["freqs"] = np.array([13.0, 21.0, 29.0])
+    rng = np.random.default_rng(8)
+    resid = synth.bandlimited_noise(rng, (4, 12, 80), c.dt, 5.0, 40.0).astype(np.float32)
+    rt = torch.from_numpy(resid).cuda()
+    path = str(tmp_path / "set.eghq")
+    with _ctx(c, precision=precision) as a:
+        with pytest.raises(egh.EghError) as ei:
+            a.save(path)
+        assert ei.value.status == egh.EGH_ESTATE
+        a.green(torch.from_numpy(np.asarray(c.vel_true, np.float32)).cuda())
+        mu = a.hessian(egh.EGH_MU_REL_MEANDIAG, c.mu_alpha)
+        a.factor()
+        Qa, La = a.get_hessian(False), a.get_hessian(True)
+        ma = torch.empty_like(rt)
+        a.deblur(rt, ma)
+        a.save(path)
+    raw = open(path, "rb").read()
+    assert raw[:8] == b"EGHQSET1"
+    (hl,) = struct.unpack("<Q", raw[8:16])
+    hdr = json.loads(raw[16:16 + hl].decode())
+    assert hdr["nrec"] == 12 and hdr["nfreq"] == 3 and hdr["precision"] == precision
+    assert hdr["freq_hz"] == [13.0, 21.0, 29.0] and hdr["mu"] == mu and hdr["nt"] == 60
+    assert [x["name"] for x in hdr["arrays"]] == ["Q", "L"]
+    n = 3 * 12 * 12
+    payload = np.frombuffer(raw[16 + hl:], dtype=np.complex64)
+    assert payload.size == 2 * n
+    np.testing.assert_array_equal(payload[:n].reshape(3, 12, 12), Qa)
+    np.testing.assert_array_equal(payload[n:].reshape(3, 12, 12), La)
+    with _ctx(c, precision=precision) as b:
+        b.load(path)
+        np.testing.assert_array_equal(b.get_hessian(False), Qa)
+        np.testing.assert_array_equal(b.get_hessian(True), La)
+        mb = torch.empty_like(rt)
+        b.deblur(rt, mb)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(mb.cpu().numpy(), ma.cpu().numpy())
+    c2 = synth.case_tiny(seed=13, nz=19, nx=33, nsponge=5, nrec=12, nt=60, dt=1e-3)
+    c2["freqs"] = np.array([13.0, 21.0, 30.0])
+    bad = str(tmp_path / "short.eghq")
+    open(bad, "wb").write(raw[: len(raw) - 100])
+    other = str(tmp_path / "other.bin")
+    open(other, "wb").write(b"not a set" * 10)
+    with _ctx(c2, precision=precision) as d:
+        with pytest.raises(egh.EghError) as ei:
+            d.load(path)
+        assert ei.value.status == egh.EGH_EINVAL
+    with _ctx(c, precision=precision) as e:
+        for p in (bad, other, str(tmp_path / "missing.eghq")):
+            with pytest.raises(egh.EghError) as ei:
+                e.load(p)
+            assert ei.value.status == egh.EGH_EINVAL
