@@ -18,6 +18,7 @@
 #include <vector>
 
 #include <cooperative_groups.h>
+#include <cudaTypedefs.h>
 
 #include "egh_internal.cuh"
 #include "tc.cuh"
@@ -50,11 +51,20 @@ cudaError_t launch_trace_dft_tc(const float* resid, int ntr, int nt_d, const uns
                                 int nf, int nrec, int ld, int s0, float2* Dh, int* err,
                                 int expire, cudaStream_t st);
 
+cudaError_t launch_trace_tma(const float* resid, int ntr, int nt_d, const unsigned char* twt,
+                             int nf, int nrec, int ld, int s0, float2* Dh, int* err, int expire,
+                             cudaStream_t st);
+cudaError_t make_f32_tmap(CUtensorMap* tm, const void* base, long long rows, long long cols,
+                          int box_cols, int box_rows, bool swizzle);
+
 cudaError_t launch_trace_dft(const float* resid, int ntr, int nt_d, int nf, int nrec, int ld,
                              int s0, float2* Dh, cudaStream_t st, const unsigned char* twt,
-                             int* err, int expire) {
+                             int* err, int expire, bool dev_in) {
   // N = 2 nf rounded up to 32 is at most 128 for nf <= 64
   if (nf < 1 || nf > NFMAX || !twt || !err) return cudaErrorInvalidValue;
+  const bool vec = (nt_d & 3) == 0 && (reinterpret_cast<uintptr_t>(resid) & 15) == 0;
+  if (dev_in && vec && tt_ncomp(nf) <= 64 && ntr > 0)
+    return launch_trace_tma(resid, ntr, nt_d, twt, nf, nrec, ld, s0, Dh, err, expire, st);
   return launch_trace_dft_tc(resid, ntr, nt_d, twt, nf, nrec, ld, s0, Dh, err, expire, st);
 }
 
@@ -297,6 +307,349 @@ __global__ void __cluster_dims__(TD_S, 1, 1) __launch_bounds__(256)
   if (warp == 0) tc::tmem_dealloc(tmem, NCOL);
 }
 
+// ---------------------------------------------------------------------------------------------
+// Forward transform from device memory, persistent and split by warp role.  The time axis of a
+// trace tile is cut into H fixed parts (H = 2 from two stages on: stages [0, nst/2) and
+// [nst/2, nst)); a unit is one part of one tile, and each CTA (one per SM) takes an even share
+// of the units.  Warp 9 (one thread) streams the units' fp32 samples into a ring of TMA stages
+// (128 traces x 64 samples; rows past ntr and samples past nt_d read as zero), reloading a
+// slot as soon as it has been read; warp 8 (one thread) loads the twiddle tiles and issues the
+// bf16x3 MMAs (A hi against the twiddles' hi and lo planes as one MMA of twice the width, then
+// A lo against hi); warps 0-7 split each stage into the bf16 hi/lo A tiles and drain the TMEM
+// blocks (TT_J stages each, counted from the part's start) into FP32 register totals, which
+// they add into the zeroed spectra at the part's end.  With two parts
+// the spectrum is 0 + a + b in either order, the same bits (floating-point addition commutes),
+// and the parts depend on the trace length alone: a trace's spectrum does not depend on the
+// other traces of the call.  mbarriers carry every hand-off; every wait is bounded and gives up
+// early once another role has failed.
+// ---------------------------------------------------------------------------------------------
+constexpr int TP_EPI = 256;  // threads of warps 0-7
+#ifndef EGH_TP_R
+#define EGH_TP_R 3
+#endif
+#ifndef EGH_TP_A
+#define EGH_TP_A 2
+#endif
+#ifndef EGH_TP_B
+#define EGH_TP_B 4
+#endif
+constexpr int TP_R = EGH_TP_R;  // fp32 ring stages
+constexpr int TP_A = EGH_TP_A;  // A tiles (the converters fill one while the MMAs read another)
+constexpr int TP_B = EGH_TP_B;  // twiddle tiles in flight (loaded TP_B - 2 stages ahead)
+constexpr unsigned TP_STAGE = TT_M * TT_K * 4;  // one fp32 ring stage
+
+size_t trace_tma_smem(int N) {
+  // ring, A tiles (hi + lo), twiddle tiles (hi + lo), alignment slack
+  return 1024 + (size_t)TP_R * TP_STAGE + TP_A * 2 * (size_t)TT_A + TP_B * 2 * (size_t)N * 128;
+}
+
+// the stages of unit u (part u % H of tile u / H)
+struct TpUnit {
+  int tile, sb, nr;
+};
+__device__ __forceinline__ TpUnit tp_unit(long long u, int H, int nst) {
+  const int half = (int)(u % H);
+  TpUnit r;
+  r.tile = (int)(u / H);
+  r.sb = half * nst / H;
+  r.nr = (half + 1) * nst / H - r.sb;
+  return r;
+}
+
+template <int N>
+__global__ void __launch_bounds__(TP_EPI + 64, 1)
+    k_trace_tma(const __grid_constant__ CUtensorMap tm_in, int ntr, int nt_d,
+                const unsigned char* __restrict__ twt, int nf, int nrec, int ld, int s0, int H,
+                float2* __restrict__ Dh, int* __restrict__ err, int expire) {
+  constexpr int R = TP_R;
+  constexpr unsigned BT = 2u * N * 128u;  // one twiddle tile (hi + lo)
+  constexpr int NH = N / 2;
+  extern __shared__ __align__(1024) unsigned char tp_dsm[];
+  unsigned char* sm = tp_dsm + ((1024 - (tc::smem_u32(tp_dsm) & 1023)) & 1023);
+  constexpr int NB = TP_B, NA = TP_A;
+  // rfull[R], rempty[R], bfull[NB], afull[NA], mdone[NA], blkd[2], tempty[2], never
+  __shared__ __align__(8) unsigned long long bars[2 * R + NB + 2 * NA + 5];
+  __shared__ unsigned tslot;
+  __shared__ int fail_s;
+  volatile int* fail = &fail_s;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ntile = (ntr + TT_M - 1) / TT_M, nst = (nt_d + TT_K - 1) / TT_K;
+  const long long U = (long long)ntile * H;
+  const long long u0 = U * blockIdx.x / gridDim.x;
+  const int n = (int)(U * (blockIdx.x + 1) / gridDim.x - u0);  // units of this CTA
+  const unsigned bar0 = tc::smem_u32(&bars[0]);
+  auto rfull = [&](int i) { return bar0 + 8u * i; };
+  auto rempty = [&](int i) { return bar0 + 8u * (R + i); };
+  auto bfull = [&](int i) { return bar0 + 8u * (2 * R + i); };
+  // A tile g % NA: filled for stage g (afull), read by stage g's MMAs (mdone); phase g / NA
+  auto afull = [&](int g) { return bar0 + 8u * (2 * R + NB + g % NA); };
+  auto mdone = [&](int g) { return bar0 + 8u * (2 * R + NB + NA + g % NA); };
+  auto blkd = [&](int i) { return bar0 + 8u * (2 * R + NB + 2 * NA + i); };
+  auto tempty = [&](int i) { return bar0 + 8u * (2 * R + NB + 2 * NA + 2 + i); };
+  const unsigned never = bar0 + 8u * (2 * R + NB + 2 * NA + 4);
+  // TMEM: two block buffers of 2N columns: [0, N) hi.hi + lo.hi, [N, 2N) hi.lo
+  if (warp == 0) tc::tmem_alloc(&tslot, 4 * N);
+  if (tid == 0) {
+    for (int i = 0; i < R; ++i) {
+      tc::mbar_init(rfull(i), 1);
+      tc::mbar_init(rempty(i), TP_EPI);
+    }
+    for (int i = 0; i < NB; ++i) tc::mbar_init(bfull(i), 1);
+    for (int i = 0; i < NA; ++i) {
+      tc::mbar_init(afull(i), TP_EPI);
+      tc::mbar_init(mdone(i), 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      tc::mbar_init(blkd(i), 1);
+      tc::mbar_init(tempty(i), TP_EPI);
+    }
+    tc::mbar_init(never, 1);
+    fail_s = 0;
+    tc::mbar_init_fence();
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const unsigned tmem = tslot;
+  const unsigned ring0 = tc::smem_u32(sm);
+  const unsigned abuf0 = ring0 + R * TP_STAGE;  // A tiles: hi plane, then lo plane
+  const unsigned bbuf0 = abuf0 + NA * 2 * TT_A;
+  // stages of this CTA in order: unit i, stage s of the unit
+  struct Cur {
+    int i, s;
+    TpUnit t;
+  };
+  auto cur_init = [&](Cur& c) {
+    c.i = 0;
+    c.s = 0;
+    c.t = tp_unit(u0, H, nst);
+  };
+  auto cur_next = [&](Cur& c) {
+    if (++c.s == c.t.nr) {
+      c.s = 0;
+      if (++c.i < n) c.t = tp_unit(u0 + c.i, H, nst);
+    }
+  };
+  bool ok = true;
+  if (warp == 8) {
+    if (lane == 0 && n > 0) {
+      int G = 0;  // stages of this CTA
+      for (int i = 0; i < n; ++i) G += tp_unit(u0 + i, H, nst).nr;
+      Cur mc, bc;  // next MMA stage, next twiddle load
+      cur_init(mc);
+      cur_init(bc);
+      auto issue_b = [&](int g) {
+        tc::mbar_expect_tx(bfull(g % NB), BT);
+        tc::bulk_g2s(bbuf0 + (g % NB) * BT, twt + (size_t)(bc.t.sb + bc.s) * BT, BT, bfull(g % NB));
+        cur_next(bc);
+      };
+      // A hi against the twiddles' hi and lo planes in one MMA (N = 2N: the planes are adjacent
+      // rows of one K-major tile), then A lo against the hi plane
+      const unsigned idesc2 = tc::idesc_bf16(TT_M, 2 * N, 0, 0), idesc = tc::idesc_bf16(TT_M, N, 0, 0);
+      int issued_b = 0, issued_m = 0, b = -1;
+      for (; issued_b < min(NB - 1, G); ++issued_b) issue_b(issued_b);
+      // test hook: the first CTA's first wait runs out (`never` completes no phase)
+      if (expire && blockIdx.x == 0 && !tc::mbar_wait_unsignalled(never)) ok = false;
+      for (int g = 0; g < G && ok; ++g) {
+        const int s = mc.s;
+        const bool first = s % TT_J == 0, last = (s + 1) % TT_J == 0 || s == mc.t.nr - 1;
+        if (first) ++b;  // TMEM block of this stage
+        // twiddles of stage j = issued_b (at most g + NB - 2) into the buffer that stage j - NB's
+        // MMAs read, issued two stages ago (so that this thread does not wait on the MMAs it
+        // has just issued)
+        while (issued_b < G && issued_b <= g + NB - 2) {
+          const int jm = issued_b - NB;
+          if (jm >= 0 && !tc::mbar_wait_or(mdone(jm), (jm / NA) & 1, fail)) {
+            ok = false;
+            break;
+          }
+          issue_b(issued_b);
+          ++issued_b;
+        }
+        if (!ok) break;
+        if (!tc::mbar_wait_or(afull(g), (g / NA) & 1, fail) ||
+            !tc::mbar_wait_or(bfull(g % NB), (g / NB) & 1, fail)) {
+          ok = false;
+          break;
+        }
+        // a block's TMEM buffer was drained two blocks ago
+        if (first && b >= 2 && !tc::mbar_wait_or(tempty(b & 1), ((b - 2) >> 1) & 1, fail)) {
+          ok = false;
+          break;
+        }
+        tc::tc_fence_after();
+        const unsigned dt = tmem + (unsigned)((b & 1) * 2 * N);
+        const unsigned ah = abuf0 + (g % NA) * 2 * TT_A, al = ah + TT_A;
+        const unsigned bh = bbuf0 + (g % NB) * BT;
+#pragma unroll
+        for (int ks = 0; ks < TT_K / 16; ++ks) {
+          const unsigned o = 32u * ks;
+          const uint64_t dah = tc::sdesc_sw128(ah + o), dal = tc::sdesc_sw128(al + o);
+          const uint64_t dbh = tc::sdesc_sw128(bh + o);
+          tc::mma_bf16(dt, dah, dbh, idesc2, !(first && ks == 0));
+          tc::mma_bf16(dt, dal, dbh, idesc, true);
+        }
+        tc::mma_commit(mdone(g));
+        issued_m = g + 1;
+        if (last) tc::mma_commit(blkd(b & 1));
+        cur_next(mc);
+      }
+      if (!ok) *fail = 1;
+      // leave no copy or MMA in flight: the last issue of each twiddle buffer and the last MMAs
+      // (bounded)
+      for (int i = 0; i < NB; ++i) {
+        const int nis = issued_b > i ? (issued_b - 1 - i) / NB + 1 : 0;
+        if (nis > 0) tc::mbar_wait(bfull(i), (nis - 1) & 1);
+      }
+      if (issued_m > 0) tc::mbar_wait(mdone(issued_m - 1), ((issued_m - 1) / NA) & 1);
+    }
+  } else if (warp == 9) {
+    // the ring: a slot is loaded again as soon as the converters have read it
+    if (lane == 0 && n > 0) {
+      int G = 0;
+      for (int i = 0; i < n; ++i) G += tp_unit(u0 + i, H, nst).nr;
+      Cur lc;
+      cur_init(lc);
+      int issued_r = 0;
+      for (; issued_r < G; ++issued_r) {
+        const int slot = issued_r % R;
+        if (issued_r >= R && !tc::mbar_wait_or(rempty(slot), (issued_r / R - 1) & 1, fail)) {
+          ok = false;
+          break;
+        }
+        tc::mbar_expect_tx(rfull(slot), TP_STAGE);
+        tc::tma_load_2d(ring0 + slot * TP_STAGE, &tm_in, (lc.t.sb + lc.s) * TT_K, lc.t.tile * TT_M,
+                        rfull(slot));
+        cur_next(lc);
+      }
+      if (!ok) *fail = 1;
+      for (int i = 0; i < R; ++i) {  // the last issue of each slot has landed (bounded)
+        const int nis = issued_r > i ? (issued_r - 1 - i) / R + 1 : 0;
+        if (nis > 0) tc::mbar_wait(rfull(i), (nis - 1) & 1);
+      }
+    }
+  } else {
+    const int qq = warp & 3, hh = warp >> 2, row = qq * 32 + lane;
+    float tot[NH];
+#pragma unroll
+    for (int c = 0; c < NH; ++c) tot[c] = 0.f;
+    auto convert = [&](int g) -> bool {
+      const int slot = g % R;
+      if (!tc::mbar_wait_or(rfull(slot), (g / R) & 1, fail)) return false;
+      const unsigned rs = ring0 + slot * TP_STAGE;
+      float4 v[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int e = i * TP_EPI + tid;  // row e / 16, float4 e % 16 of the stage
+        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                     : "=f"(v[i].x), "=f"(v[i].y), "=f"(v[i].z), "=f"(v[i].w)
+                     : "r"(rs + 16u * e));
+      }
+      tc::mbar_arrive(rempty(slot));
+      // split into bf16 hi / lo while the MMAs of stage g - NA may still read the A tile
+      unsigned hl[8][4];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const __nv_bfloat162 h01 = __floats2bfloat162_rn(v[i].x, v[i].y);
+        const __nv_bfloat162 h23 = __floats2bfloat162_rn(v[i].z, v[i].w);
+        const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
+        const __nv_bfloat162 l01 = __floats2bfloat162_rn(v[i].x - f01.x, v[i].y - f01.y);
+        const __nv_bfloat162 l23 = __floats2bfloat162_rn(v[i].z - f23.x, v[i].w - f23.y);
+        hl[i][0] = *reinterpret_cast<const unsigned*>(&h01);
+        hl[i][1] = *reinterpret_cast<const unsigned*>(&h23);
+        hl[i][2] = *reinterpret_cast<const unsigned*>(&l01);
+        hl[i][3] = *reinterpret_cast<const unsigned*>(&l23);
+      }
+      if (g >= NA && !tc::mbar_wait_or(mdone(g), (g / NA - 1) & 1, fail)) return false;
+      const unsigned ah = abuf0 + (g % NA) * 2 * TT_A;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int e = i * TP_EPI + tid, m = e >> 4, c4 = e & 15;
+        const unsigned off = (unsigned)((m >> 3) * 1024 + (m & 7) * 128 +
+                                        ((((c4 >> 1) ^ (m & 7))) << 4) + ((c4 & 1) << 3));
+        st_shared_v2(ah + off, hl[i][0], hl[i][1]);
+        st_shared_v2(ah + TT_A + off, hl[i][2], hl[i][3]);
+      }
+      tc::fence_proxy_async();
+      tc::mbar_arrive(afull(g));
+      return true;
+    };
+    auto drain = [&](int b) -> bool {  // TMEM block b into the totals
+      const bool got = tc::mbar_wait_or(blkd(b & 1), (b >> 1) & 1, fail);
+      if (!__all_sync(0xffffffffu, got)) return false;
+      tc::tc_fence_after();
+      const unsigned base =
+          tmem + ((unsigned)(qq * 32) << 16) + (unsigned)((b & 1) * 2 * N + hh * NH);
+#pragma unroll
+      for (int c0 = 0; c0 < NH; c0 += 16) {
+        float x[16], y[16];
+        tc::tmem_ld16(base + (unsigned)c0, x);          // hi.hi + lo.hi
+        tc::tmem_ld16(base + (unsigned)(N + c0), y);    // hi.lo
+#pragma unroll
+        for (int i = 0; i < 16; ++i) tot[c0 + i] += x[i] + y[i];
+      }
+      tc::tc_fence_before();
+      tc::mbar_arrive(tempty(b & 1));
+      return true;
+    };
+    auto emit = [&](int tile) {  // a unit's totals into the spectra: components 2 kk, 2 kk + 1
+      const int q = tile * TT_M + row;
+      if (q < ntr) {
+        const int sidx = q / nrec, r = q % nrec;
+#pragma unroll
+        for (int p = 0; p < NH / 2; ++p) {
+          const int kk = hh * (NH / 2) + p;
+          if (kk < nf) {
+            float2* d = Dh + ((long long)kk * nrec + r) * ld + s0 + sidx;
+            const float2 x = make_float2(tot[2 * p], tot[2 * p + 1]);
+            if (H == 1)
+              *d = x;
+            else
+              atomicAdd(d, x);
+          }
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < NH; ++c) tot[c] = 0.f;
+    };
+    int g = 0, blk = 0, pend = -1, pend_tile = -1;
+    for (int i = 0; i < n && ok; ++i) {
+      const TpUnit t = tp_unit(u0 + i, H, nst);
+      for (int s = 0; s < t.nr; ++s) {
+        if (!convert(g)) {
+          ok = false;
+          break;
+        }
+        ++g;
+        // the block that ended one stage ago; after a unit's last block, its totals go out
+        if (pend >= 0) {
+          if (!drain(pend)) {
+            ok = false;
+            break;
+          }
+          if (pend_tile >= 0) emit(pend_tile);
+          pend = -1;
+        }
+        if ((s + 1) % TT_J == 0 || s == t.nr - 1) {
+          pend = blk++;
+          pend_tile = s == t.nr - 1 ? t.tile : -1;
+        }
+      }
+    }
+    if (ok && pend >= 0) {
+      ok = drain(pend);
+      if (ok && pend_tile >= 0) emit(pend_tile);
+    }
+    if (!ok) *fail = 1;
+  }
+  const bool okall = __syncthreads_and(ok) && !*fail;
+  if (!okall && tid == 0) atomicExch(err, 1);
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  if (warp == 0) tc::tmem_dealloc(tmem, 4 * N);
+}
+
 cudaError_t launch_trace_dft_tc(const float* resid, int ntr, int nt_d, const unsigned char* twt,
                                 int nf, int nrec, int ld, int s0, float2* Dh, int* err,
                                 int expire, cudaStream_t st) {
@@ -321,6 +674,34 @@ cudaError_t launch_trace_dft_tc(const float* resid, int ntr, int nt_d, const uns
   EGH_TT_CASE(128)
 #undef EGH_TT_CASE
   return cudaErrorInvalidValue;
+}
+
+// Persistent transform: one CTA per SM, at most one per unit.  With two parts per tile the
+// spectra of the call's columns are zeroed first (the parts add into them).
+cudaError_t launch_trace_tma(const float* resid, int ntr, int nt_d, const unsigned char* twt,
+                             int nf, int nrec, int ld, int s0, float2* Dh, int* err, int expire,
+                             cudaStream_t st) {
+  const int N = tt_ncomp(nf);
+  const size_t smem = trace_tma_smem(N);
+  auto kern = N == 32 ? k_trace_tma<32> : k_trace_tma<64>;
+  cudaError_t e;
+  int dev = 0, sms = 0;
+  if ((e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)))
+    return e;
+  if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+    return e;
+  const int ntile = (ntr + TT_M - 1) / TT_M, nst = (nt_d + TT_K - 1) / TT_K;
+  const int H = nst >= 2 ? 2 : 1;
+  if (H == 2 &&
+      (e = cudaMemset2DAsync(Dh + s0, (size_t)ld * sizeof(float2), 0,
+                             (size_t)(ntr / nrec) * sizeof(float2), (size_t)nf * nrec, st)))
+    return e;
+  CUtensorMap tm;
+  if ((e = make_f32_tmap(&tm, resid, ntr, nt_d, TT_K, TT_M, false))) return e;
+  const int grid = (int)std::min<long long>((long long)ntile * H, sms);
+  count_launches(1);
+  kern<<<grid, TP_EPI + 64, smem, st>>>(tm, ntr, nt_d, twt, nf, nrec, ld, s0, H, Dh, err, expire);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -1023,6 +1404,296 @@ __global__ void __launch_bounds__(256)
   if (warp == 0) tc::tmem_dealloc(tmem, 2 * SN);
 }
 
+// ---------------------------------------------------------------------------------------------
+// Synthesis operands: the A tiles of k_synth_tma as they sit in shared memory, built once per
+// call in global memory.  Tile qt holds traces qt * 128 + m; its image is a hi plane and a lo
+// plane of KC 64-component chunks each (bf16, K-major, 128-byte swizzle), component 2k =
+// Re(w_k D[k][r][s]), 2k + 1 = Im, zero past 2 nf.  One block per (receiver r, 32 sources):
+// the spectra are read along the sources (contiguous) and each trace's row is written as
+// 16-byte chunks.
+// ---------------------------------------------------------------------------------------------
+constexpr int SP_SB = 32;  // sources per block of the operand transpose
+
+template <int KC>
+__global__ void __launch_bounds__(256)
+    k_synth_operands(const float2* __restrict__ Dh, int nrec, int ns, int ld, int s0, int nf,
+                     const float* __restrict__ w, unsigned char* __restrict__ img) {
+  constexpr int NK = 32 * KC;           // frequencies of the A tile
+  constexpr unsigned SA = KC * SC_CH;   // one plane of a tile image
+  __shared__ float2 T[NK][SP_SB + 1];
+  const int r = blockIdx.x, sb = blockIdx.y * SP_SB, tid = threadIdx.x;
+  for (int e = tid; e < NK * SP_SB; e += 256) {
+    const int k = e / SP_SB, sl = e % SP_SB, sidx = sb + sl;
+    float2 x = make_float2(0.f, 0.f);
+    if (k < nf && sidx < ns) {
+      const float2 d = Dh[((long long)k * nrec + r) * ld + s0 + sidx];
+      const float wk = w[k];
+      x = make_float2(d.x * wk, d.y * wk);
+    }
+    T[k][sl] = x;
+  }
+  __syncthreads();
+  // 16-byte chunk ch of a plane row covers frequencies 4 ch .. 4 ch + 3
+  for (int e = tid; e < SP_SB * (NK / 4); e += 256) {
+    const int sl = e / (NK / 4), ch = e % (NK / 4), sidx = sb + sl;
+    if (sidx >= ns) continue;
+    const long long q = (long long)sidx * nrec + r;
+    const int m = (int)(q % SC_M);
+    unsigned hi[4], lo[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float2 x = T[4 * ch + i][sl];
+      const __nv_bfloat162 h = __floats2bfloat162_rn(x.x, x.y);
+      const float2 hf = __bfloat1622float2(h);
+      const __nv_bfloat162 l = __floats2bfloat162_rn(x.x - hf.x, x.y - hf.y);
+      hi[i] = *reinterpret_cast<const unsigned*>(&h);
+      lo[i] = *reinterpret_cast<const unsigned*>(&l);
+    }
+    const int cc = ch & 7;  // chunk within the 64-component block ch / 8
+    const size_t off = (size_t)(q / SC_M) * 2 * SA + (size_t)(ch >> 3) * SC_CH + (m >> 3) * 1024 +
+                       (m & 7) * 128 + ((cc ^ (m & 7)) << 4);
+    *reinterpret_cast<uint4*>(img + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+    *reinterpret_cast<uint4*>(img + off + SA) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+  }
+}
+
+size_t synth_operands_bytes(int nf, long long ntr) {
+  return (size_t)((ntr + SC_M - 1) / SC_M) * 2 * sc_kc(nf) * SC_CH;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Persistent synthesis into device memory: the same products as k_synth_tc, one CTA per SM over
+// an even share of the (trace tile, sample tile) units, roles split by warp.  Warp 8 (one
+// thread) loads the twiddle tiles (two buffers) and issues each unit's bf16x3 MMAs into one of
+// two TMEM buffers; warps 0-7 fill the A tile of a new trace tile (once the last MMAs that read
+// the old one are done), then drain each finished TMEM buffer: a 32 x 32 block per step goes
+// through a 128-byte-swizzled staging tile and out with one TMA store (rows past ntr and
+// samples past nt_d are clipped by the copy).  mbarriers carry every hand-off; every wait is
+// bounded and gives up early once another role has failed.
+// ---------------------------------------------------------------------------------------------
+constexpr int SP_EPI = 256;  // epilogue threads (warps 0-7); warp 8 issues copies and MMAs
+
+__host__ __device__ constexpr int sp_nstg(int kc) { return kc == 1 ? 2 : 1; }  // staging tiles per warp
+
+size_t synth_tma_smem(int kc) {
+  // A (2 planes x kc chunks), 2 B buffers, staging tiles of 4 KB, alignment slack
+  return 1024 + 2 * (size_t)kc * SC_CH + 2 * (size_t)SC_B + 8 * (size_t)sp_nstg(kc) * 4096;
+}
+
+template <int KC>
+__global__ void __launch_bounds__(SP_EPI + 32, 1)
+    k_synth_tma(const __grid_constant__ CUtensorMap tm_out, const float2* __restrict__ Dh, int nrec,
+                int ld, int s0, int nf, const float* __restrict__ w,
+                const unsigned char* __restrict__ tws, int nt_d, int ntr,
+                const unsigned char* __restrict__ aimg, int* __restrict__ err) {
+  constexpr int SN = sc_n(KC);         // samples per unit (MMA N)
+  constexpr unsigned SA = KC * SC_CH;  // one A plane
+  constexpr int NSTG = sp_nstg(KC);
+  extern __shared__ __align__(1024) unsigned char sp_dsm[];
+  unsigned char* sm = sp_dsm + ((1024 - (tc::smem_u32(sp_dsm) & 1023)) & 1023);
+  // bfull[2], mdone[2], tempty[2], afull (A filled by warps 0-7), aload (A copied from aimg)
+  __shared__ __align__(8) unsigned long long bars[8];
+  __shared__ unsigned tslot;
+  __shared__ int fail_s;
+  volatile int* fail = &fail_s;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nj = (nt_d + SN - 1) / SN;  // sample tiles per trace tile
+  const long long U = (long long)((ntr + SC_M - 1) / SC_M) * nj;
+  const long long u0 = U * blockIdx.x / gridDim.x;
+  const int n = (int)(U * (blockIdx.x + 1) / gridDim.x - u0);
+  const unsigned bar0 = tc::smem_u32(&bars[0]);
+  auto bfull = [&](int i) { return bar0 + 8u * i; };
+  auto mdone = [&](int i) { return bar0 + 8u * (2 + i); };
+  auto tempty = [&](int i) { return bar0 + 8u * (4 + i); };
+  const unsigned afull = bar0 + 48u, aload = bar0 + 56u;
+  if (warp == 0) tc::tmem_alloc(&tslot, 2 * SN);
+  if (tid == 0) {
+    for (int i = 0; i < 4; ++i) tc::mbar_init(bar0 + 8u * i, 1);
+    tc::mbar_init(tempty(0), SP_EPI);
+    tc::mbar_init(tempty(1), SP_EPI);
+    tc::mbar_init(afull, SP_EPI);
+    tc::mbar_init(aload, 1);
+    fail_s = 0;
+    tc::mbar_init_fence();
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const unsigned tmem = tslot;
+  const unsigned ah = tc::smem_u32(sm), al = ah + SA;
+  auto b_hi = [&](int b) { return tc::smem_u32(sm + 2 * SA + (size_t)b * SC_B); };
+  const unsigned stg0 = tc::smem_u32(sm + 2 * SA + 2 * SC_B);
+  bool ok = true;
+  if (warp == 8) {
+    if (lane == 0 && n > 0) {
+      auto issue_b = [&](int i) {
+        const int j = (int)((u0 + i) % nj);
+        tc::mbar_expect_tx(bfull(i & 1), SC_B);
+        tc::bulk_g2s(b_hi(i & 1), tws + (size_t)j * SC_B, SC_B, bfull(i & 1));
+      };
+      const unsigned idesc = tc::idesc_bf16(SC_M, SN, 0, 0);
+      int issued_b = 0, waited_b = 0, issued_m = 0, tiles = 0;
+      long long qt_prev = -1;
+      issue_b(0);
+      issued_b = 1;
+      if (n > 1) {
+        issue_b(1);
+        issued_b = 2;
+      }
+      for (int i = 0; i < n; ++i) {
+        const long long qt = (u0 + i) / nj;
+        if (qt != qt_prev) {  // the A tile of this trace tile
+          if (aimg) {
+            // copied from its image once the previous tile's last MMAs are done
+            if (i >= 1 && !tc::mbar_wait_or(mdone((i - 1) & 1), ((i - 1) >> 1) & 1, fail)) {
+              ok = false;
+              break;
+            }
+            tc::mbar_expect_tx(aload, 2 * SA);
+            tc::bulk_g2s(ah, aimg + (size_t)qt * 2 * SA, 2 * SA, aload);
+            if (!tc::mbar_wait_or(aload, tiles & 1, fail)) {
+              ok = false;
+              break;
+            }
+          } else if (!tc::mbar_wait_or(afull, tiles & 1, fail)) {  // filled by warps 0-7
+            ok = false;
+            break;
+          }
+          ++tiles;
+          qt_prev = qt;
+        }
+        if (!tc::mbar_wait_or(bfull(i & 1), (i >> 1) & 1, fail)) {
+          ok = false;
+          break;
+        }
+        waited_b = i + 1;
+        // TMEM buffer i % 2 was drained by the epilogue of unit i - 2
+        if (i >= 2 && !tc::mbar_wait_or(tempty(i & 1), ((i - 2) >> 1) & 1, fail)) {
+          ok = false;
+          break;
+        }
+        tc::tc_fence_after();
+        const unsigned dt = tmem + (unsigned)((i & 1) * SN);
+        const unsigned bh = b_hi(i & 1), bl = bh + KC * SN * 128;
+#pragma unroll
+        for (int kc = 0; kc < KC; ++kc)
+#pragma unroll
+          for (int ks = 0; ks < 4; ++ks) {
+            const unsigned oa = kc * SC_CH + 32u * ks, ob = kc * SN * 128 + 32u * ks;
+            const uint64_t dah = tc::sdesc_sw128(ah + oa), dal = tc::sdesc_sw128(al + oa);
+            const uint64_t dbh = tc::sdesc_sw128(bh + ob), dbl = tc::sdesc_sw128(bl + ob);
+            tc::mma_bf16(dt, dah, dbh, idesc, kc > 0 || ks > 0);
+            tc::mma_bf16(dt, dah, dbl, idesc, true);
+            tc::mma_bf16(dt, dal, dbh, idesc, true);
+          }
+        tc::mma_commit(mdone(i & 1));
+        issued_m = i + 1;
+        // B buffer i % 2 takes unit i + 2's twiddles once this unit's MMAs are done
+        if (i + 2 < n) {
+          if (!tc::mbar_wait_or(mdone(i & 1), (i >> 1) & 1, fail)) {
+            ok = false;
+            break;
+          }
+          issue_b(i + 2);
+          issued_b = i + 3;
+        }
+      }
+      if (!ok) *fail = 1;
+      // leave no copy or MMA in flight (bounded)
+      for (int i = waited_b; i < issued_b; ++i) tc::mbar_wait(bfull(i & 1), (i >> 1) & 1);
+      if (issued_m > 0) tc::mbar_wait(mdone((issued_m - 1) & 1), ((issued_m - 1) >> 1) & 1);
+    }
+  } else {
+    // A tile of trace tile qt: row m = trace qt * 128 + m, components c = 2k (re), 2k + 1 (im),
+    // zero past 2 nf and ntr; the threads of half h take frequencies 16 KC h .. 16 KC h + 16 KC - 1
+    auto fill_a = [&](long long qt) {
+      const int m = tid & (SC_M - 1);
+      const long long q = qt * SC_M + m;
+      const int sidx = (int)(q / nrec), r = (int)(q % nrec);
+      const int kb = (tid >> 7) * 16 * KC;
+      float2 x[16 * KC];
+#pragma unroll
+      for (int i = 0; i < 16 * KC; ++i) {
+        const int k = kb + i;
+        x[i] = make_float2(0.f, 0.f);
+        if (q < ntr && k < nf) {
+          const float2 d = Dh[((long long)k * nrec + r) * ld + s0 + sidx];
+          const float wk = w[k];
+          x[i] = make_float2(d.x * wk, d.y * wk);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 16 * KC; ++i) {
+        const int k = kb + i;
+        const __nv_bfloat162 h = __floats2bfloat162_rn(x[i].x, x[i].y);
+        const float2 hf = __bfloat1622float2(h);
+        const __nv_bfloat162 l = __floats2bfloat162_rn(x[i].x - hf.x, x[i].y - hf.y);
+        const int kl = k & 31;
+        const unsigned off = (unsigned)((k >> 5) * SC_CH + (m >> 3) * 1024 + (m & 7) * 128 +
+                                        ((((kl >> 2) ^ (m & 7))) << 4) + ((kl & 3) << 2));
+        asm volatile("st.shared.u32 [%0], %1;" ::"r"(ah + off), "r"(*reinterpret_cast<const unsigned*>(&h))
+                     : "memory");
+        asm volatile("st.shared.u32 [%0], %1;" ::"r"(al + off), "r"(*reinterpret_cast<const unsigned*>(&l))
+                     : "memory");
+      }
+      tc::fence_proxy_async();
+      tc::mbar_arrive(afull);
+    };
+    if (n > 0 && !aimg) fill_a(u0 / nj);
+    const int qq = warp & 3, hh = warp >> 2;
+    int cnt = 0;  // staging tiles used by this warp
+    for (int i = 0; i < n; ++i) {
+      const long long u = u0 + i, qt = u / nj;
+      const int j = (int)(u % nj);
+      if (!tc::mbar_wait_or(mdone(i & 1), (i >> 1) & 1, fail)) {
+        ok = false;
+        break;
+      }
+      tc::tc_fence_after();
+      // the next unit starts a new trace tile: refill A now that its last MMAs are done
+      if (!aimg && i + 1 < n && (u + 1) / nj != qt) fill_a(qt + 1);
+      const unsigned base =
+          tmem + ((unsigned)(qq * 32) << 16) + (unsigned)((i & 1) * SN + hh * (SN / 2));
+#pragma unroll 1
+      for (int c0 = 0; c0 < SN / 2; c0 += 32) {
+        float v[32];
+        tc::tmem_ld32(base + (unsigned)c0, v);
+        if (cnt >= NSTG) {  // the staging tile's previous store has read it
+          if (lane == 0) tc::bulk_wait_read<NSTG - 1>();
+          __syncwarp();
+        }
+        const unsigned sb = stg0 + (unsigned)((warp * NSTG + cnt % NSTG) * 4096);
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(
+                           sb + lane * 128 + ((k ^ (lane & 7)) << 4)),
+                       "f"(v[4 * k]), "f"(v[4 * k + 1]), "f"(v[4 * k + 2]), "f"(v[4 * k + 3])
+                       : "memory");
+        tc::fence_proxy_async();
+        __syncwarp();
+        if (lane == 0) {
+          // a box that starts past the last sample or trace writes nothing: not issued (the
+          // group is still committed, so that the staging tiles' group count stays in step)
+          const int t = j * SN + hh * (SN / 2) + c0, q = (int)(qt * SC_M) + qq * 32;
+          if (t < nt_d && q < ntr) tc::tma_store_2d(&tm_out, sb, t, q);
+          tc::bulk_commit();
+        }
+        ++cnt;
+      }
+      tc::tc_fence_before();
+      tc::mbar_arrive(tempty(i & 1));
+    }
+    if (!ok) *fail = 1;
+    if (lane == 0) tc::bulk_wait_all();
+  }
+  const bool okall = __syncthreads_and(ok) && !*fail;
+  if (!okall && tid == 0) atomicExch(err, 1);
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  if (warp == 0) tc::tmem_dealloc(tmem, 2 * SN);
+}
+
 // Synthesis twiddle tiles: for every sample tile (256 samples for 2 nf <= 64, else 128), a hi and
 // a lo plane, each [KC chunks of 64 components][tile samples][64 components] bf16 in the K-major
 // 128-byte swizzle (row t, component c of chunk kc at byte kc * rows * 128 + (t/8)*1024 +
@@ -1057,16 +1728,73 @@ std::vector<unsigned char> synth_twiddle_tiles(const std::vector<double>& f, dou
   return out;
 }
 
+// Tensor map of a [rows][cols] fp32 array (row pitch cols) for box_cols x box_rows boxes, with
+// or without the 128-byte swizzle.
+cudaError_t make_f32_tmap(CUtensorMap* tm, const void* base, long long rows, long long cols,
+                          int box_cols, int box_rows, bool swizzle) {
+  static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
+  if (!enc) {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    cudaError_t e =
+        cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t str[1] = {(cuuint64_t)cols * 4};
+  const cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+  const cuuint32_t es[2] = {1, 1};
+  const CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, str,
+                         box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         swizzle ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 cudaError_t launch_synth_tc(const float2* Dh, int nrec, int ns, int ld, int s0, int nf,
                             const float* w, const unsigned char* tws, int nt_d, float* mult,
-                            int* err, cudaStream_t st) {
+                            int* err, cudaStream_t st, bool dev_out, unsigned char* scratch,
+                            size_t scratch_bytes) {
   const int ntr = nrec * ns;
   const int kc = sc_kc(nf), sn = sc_n(kc);
-  const size_t smem = synth_tc_smem(kc);
   const bool vec = (nt_d & 3) == 0 && (reinterpret_cast<uintptr_t>(mult) & 15) == 0;
+  cudaError_t e;
+  if (vec && dev_out && ntr > 0) {
+    // device memory: the persistent kernel with TMA stores, one CTA per SM; its A tiles come
+    // from operand images built first when a scratch buffer of their size is given
+    CUtensorMap tm;
+    if ((e = make_f32_tmap(&tm, mult, ntr, nt_d, 32, 32, true))) return e;
+    unsigned char* aimg = nullptr;
+    if (scratch && scratch_bytes >= synth_operands_bytes(nf, ntr) &&
+        (reinterpret_cast<uintptr_t>(scratch) & 15) == 0) {
+      aimg = scratch;
+      const dim3 pg((unsigned)nrec, (unsigned)((ns + SP_SB - 1) / SP_SB));
+      count_launches(1);
+      if (kc == 1)
+        k_synth_operands<1><<<pg, 256, 0, st>>>(Dh, nrec, ns, ld, s0, nf, w, aimg);
+      else
+        k_synth_operands<2><<<pg, 256, 0, st>>>(Dh, nrec, ns, ld, s0, nf, w, aimg);
+      if ((e = cudaGetLastError())) return e;
+    }
+    const size_t smem = synth_tma_smem(kc);
+    auto kern = kc == 1 ? k_synth_tma<1> : k_synth_tma<2>;
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+      return e;
+    int dev = 0, sms = 0;
+    if ((e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)))
+      return e;
+    const long long units = (long long)((ntr + SC_M - 1) / SC_M) * ((nt_d + sn - 1) / sn);
+    const int grid = (int)std::min<long long>(units, sms);
+    count_launches(1);
+    kern<<<grid, SP_EPI + 32, smem, st>>>(tm, Dh, nrec, ld, s0, nf, w, tws, nt_d, ntr, aimg, err);
+    return cudaGetLastError();
+  }
+  const size_t smem = synth_tc_smem(kc);
   auto kern = kc == 1 ? (vec ? k_synth_tc<true, 1> : k_synth_tc<false, 1>)
                       : (vec ? k_synth_tc<true, 2> : k_synth_tc<false, 2>);
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   count_launches(1);
   const int ntile = (nt_d + sn - 1) / sn, seg = 1024 / sn;
@@ -1077,10 +1805,12 @@ cudaError_t launch_synth_tc(const float2* Dh, int nrec, int ns, int ld, int s0, 
 
 cudaError_t launch_synth(const float2* Dh, int nrec, int ns, int ld, int s0, int nf, const float* w,
                          const float2* tw, int nt_d, float* mult, cudaStream_t st,
-                         const unsigned char* tws, int* err) {
+                         const unsigned char* tws, int* err, bool dev_out, unsigned char* scratch,
+                         size_t scratch_bytes) {
   if (nf > NFMAX) return cudaErrorInvalidValue;
   if (tws && err && 2 * nf <= 128)
-    return launch_synth_tc(Dh, nrec, ns, ld, s0, nf, w, tws, nt_d, mult, err, st);
+    return launch_synth_tc(Dh, nrec, ns, ld, s0, nf, w, tws, nt_d, mult, err, st, dev_out, scratch,
+                           scratch_bytes);
   const int ntr = nrec * ns;
   const size_t smem = sizeof(float2) * (size_t)nf * SY_TR + 2 * sizeof(float) * (size_t)nf * SY_TP;
   if (smem > 48 * 1024) {

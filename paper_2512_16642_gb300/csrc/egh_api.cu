@@ -112,6 +112,8 @@ struct egh_ctx {
   size_t Dr_cap = 0, Rr_cap = 0;
   float *io_in = nullptr, *io_out = nullptr;
   size_t io_in_cap = 0, io_out_cap = 0;
+  unsigned char* syn_ops = nullptr;  // the synthesis operand images
+  size_t syn_ops_cap = 0;
   int state = ST_CREATED;
   double mu = 0;
   cudaEvent_t ev[8] = {};
@@ -307,7 +309,7 @@ cudaError_t zero_snap_slot(egh_ctx* ctx, int j, cudaStream_t st) {
 void free_all(egh_ctx* c) {
   void* ptrs[] = {c->Ph, c->fro2, c->kref, c->xbuf, c->rflags, c->tws_deb, c->twt_deb, c->twt_bl, c->Wh, c->Dr, c->Rr, c->coef, c->lev, c->snap, c->twt, c->gh, c->ghb, c->part, c->Qh, c->Lh, c->tw, c->w_dev,
                   c->rec_pts, c->status, c->dsum, c->lmax, c->vchk, c->d_err, c->vel_stage, c->Dh,
-                  c->io_in, c->io_out};
+                  c->io_in, c->io_out, c->syn_ops};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t& e : c->ev)
@@ -1165,7 +1167,7 @@ static egh_status deblur_common(egh_ctx* ctx, const float* resid, int32_t ns, in
   const int expire = ctx->expire[2] > 0 ? 1 : 0;
   ctx->expire[2] -= expire;
   CK(launch_trace_dft(din, (int)ntr, nt_d, ctx->nf, ctx->nrec, ns, 0, D, stream,
-                      ctx->twt_deb, ctx->d_err, expire));
+                      ctx->twt_deb, ctx->d_err, expire, in_map == nullptr));
   const size_t dbytes = (size_t)ctx->nf * ntr * sizeof(float2);
   const bool refine = !diag && prec_mixed(ctx->prec) && ctx->nref > 0;
   if (!diag && prec_mixed(ctx->prec) &&
@@ -1193,8 +1195,15 @@ static egh_status deblur_common(egh_ctx* ctx, const float* resid, int32_t ns, in
   } else {
     CK(launch_trsm(ctx->Lh, ctx->nrec, ctx->nf, D, ns, stream));
   }
-  if (!X) CK(launch_synth(Xs, ctx->nrec, ns, ns, 0, ctx->nf, ctx->w_dev, ctx->tw, nt_d, dout, stream,
-                           ctx->tws_deb, ctx->d_err));
+  if (!X) {
+    const size_t ob = synth_operands_bytes(ctx->nf, ntr);
+    if (!out_map &&
+        (s = ensure_buf(ctx, (void**)&ctx->syn_ops, &ctx->syn_ops_cap, ob, stream, "synthesis operands")))
+      return s;
+    CK(launch_synth(Xs, ctx->nrec, ns, ns, 0, ctx->nf, ctx->w_dev, ctx->tw, nt_d, dout, stream,
+                    ctx->tws_deb, ctx->d_err, out_map == nullptr, out_map ? nullptr : ctx->syn_ops,
+                    out_map ? 0 : ctx->syn_ops_cap));
+  }
   CK(cudaEventRecord(ctx->ev[7], stream));
   ctx->ev_rec[3] = true;
   ctx->st.deblur_sources = ns;

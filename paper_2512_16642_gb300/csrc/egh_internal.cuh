@@ -164,9 +164,10 @@ cudaError_t launch_potrf(float2* Lh, int n, int nf, int* status, cudaStream_t st
 // spectra of ntr = nrec * ns traces into columns s0 .. s0+ns-1 of D[nf][nrec][ld] on the tensor
 // cores; twt: the transform's twiddle tiles for at least nt_d levels; err: the flag a bounded
 // wait sets (both required; nf <= 64); expire: test hook, the first CTA's first wait runs out
+// dev_in: resid is device memory (not a mapping of host memory), which the TMA form needs
 cudaError_t launch_trace_dft(const float* resid, int ntr, int nt_d, int nf, int nrec, int ld,
                              int s0, float2* Dh, cudaStream_t st, const unsigned char* twt,
-                             int* err, int expire = 0);
+                             int* err, int expire = 0, bool dev_in = false);
 cudaError_t launch_trsm(const float2* Lh, int n, int nf, float2* Dh, int ns, cudaStream_t st);
 // W = L^{-1} per frequency
 cudaError_t launch_trtri(const float2* Lh, int n, int nf, float2* Wh, cudaStream_t st);
@@ -205,9 +206,15 @@ inline double cond_bound(double fro2, double inv_lmin, double mu) {
 constexpr double kRefineCond = 1e4;
 // (on the tensor cores when tws, the synthesis twiddle tiles for at least nt_d samples, and err
 // are given and 2 nf <= 64; else on the CUDA cores)
+// dev_out: mult is device memory (not a mapping of host memory), which the TMA-store form needs;
+// scratch: device memory of scratch_bytes for the synthesis operand images (used when at least
+// synth_operands_bytes(nf, nrec * ns) and 16-byte aligned; else the kernel gathers them itself)
 cudaError_t launch_synth(const float2* Dh, int nrec, int ns, int ld, int s0, int nf, const float* w,
                          const float2* tw, int nt_d, float* mult, cudaStream_t st,
-                         const unsigned char* tws = nullptr, int* err = nullptr);
+                         const unsigned char* tws = nullptr, int* err = nullptr,
+                         bool dev_out = false, unsigned char* scratch = nullptr,
+                         size_t scratch_bytes = 0);
+size_t synth_operands_bytes(int nf, long long ntr);
 std::vector<unsigned char> synth_twiddle_tiles(const std::vector<double>& f, double dt, int nt);
 
 }  // namespace egh

@@ -211,7 +211,7 @@ cudaError_t run_batch(Server* sv, Batch* b, const HSet& h, int expire) {
     float* din = reinterpret_cast<float*>(sv->arena_base + r->off_in);
     if ((e = cudaMemcpyAsync(din, r->resid, r->bytes, cudaMemcpyHostToDevice, st))) return e;
     if ((e = launch_trace_dft(din, r->ns * h.nrec, r->nt_d, h.nf, h.nrec, ld, s0, D, st,
-                              h.twt, err, s0 == 0 ? expire : 0)))
+                              h.twt, err, s0 == 0 ? expire : 0, true)))
       return e;
     s0 += r->ns;
   }
@@ -236,8 +236,11 @@ cudaError_t run_batch(Server* sv, Batch* b, const HSet& h, int expire) {
   s0 = 0;
   for (Request* r : b->reqs) {
     float* dout = reinterpret_cast<float*>(sv->arena_base + r->off_out);
+    // the request's residual buffer, read by its forward transform above, holds the synthesis
+    // operand images when it is large enough
+    float* din = reinterpret_cast<float*>(sv->arena_base + r->off_in);
     if ((e = launch_synth(Xs, h.nrec, r->ns, ld, s0, h.nf, h.w, h.tw, r->nt_d, dout, st, h.tws,
-                          err)))
+                          err, true, reinterpret_cast<unsigned char*>(din), r->bytes)))
       return e;
     if ((e = cudaMemcpyAsync(r->mult, dout, r->bytes, cudaMemcpyDeviceToHost, st))) return e;
     s0 += r->ns;

@@ -212,3 +212,45 @@ def test_bounded_wait_expiry_fails_only_its_request():
         sv.drain()
         st = sv.stats()
         assert st["completed"] == 3
+
+
+@pytest.mark.parametrize("nrec,nf,ns,nt_d", [
+    (13, 5, 3, 4),          # one stage: clusters of one CTA
+    (21, 20, 23, 132),      # three stages (clusters of two), four ragged trace tiles
+    (21, 20, 1220, 300),    # 201 trace tiles: several per cluster; units across tile ends
+    (9, 12, 5, 8192),       # 128 stages: clusters of eight, two TMEM blocks per rank and tile
+    (9, 40, 7, 1028),       # 40 frequencies: 128-sample synthesis units, a 4-sample last one
+    (21, 26, 115, 4000),    # the benchmark's frequencies and trace length
+])
+def test_persistent_transforms_shapes(nrec, nf, ns, nt_d):
+    """The persistent forward transform (TMA stages, time axis split over a cluster, partials
+    summed by the owning rank through distributed shared memory) and the persistent synthesis
+    (TMA stores) on device buffers, at shapes that reach each of their edge cases, against the
+    FP64 oracle's transform, Cholesky solve and synthesis of the same Hessians."""
+    import torch
+    from paper_2512_16642_gb300 import egh
+
+    rng = np.random.default_rng(1000 + nt_d + ns)
+    Q, f = _hpd_set(rng, nrec, nf)
+    dt = 1e-3
+    nt_record = max(nt_d, 256)
+    # white residuals: every sample counts, however short the trace
+    r = rng.standard_normal((ns, nrec, nt_d)).astype(np.float32)
+    L = oracle.cholesky(Q.astype(np.complex128))
+    ref = oracle.deblur(L, r.astype(np.float64), f, dt, nt_ref=nt_record)[0]
+    with egh.Server(1 << 30, slots=2, max_batch_sources=2048, precision=1) as sv:
+        sid = sv.add_set(Q, f, dt, nt_record, max(nt_d, 1024))
+        rin = _pinned(r.shape, torch, r)
+        out = _pinned(r.shape, torch)
+        sv.wait(sv.submit(sid, rin, out))
+        # a subset of the sources alone: fewer trace tiles, the same arithmetic per trace
+        sub = slice(ns // 2, ns // 2 + 2)
+        rsub = _pinned(r[sub].shape, torch, r[sub])
+        osub = _pinned(r[sub].shape, torch)
+        sv.wait(sv.submit(sid, rsub, osub))
+    got = out.numpy()
+    assert np.all(np.isfinite(got))
+    assert np.array_equal(osub.numpy(), got[sub])
+    assert rel(got, ref) <= MULT_TOL
+    for s in range(0, ns, max(1, ns // 7)):
+        assert rel(got[s], ref[s]) <= MULT_TOL, s
