@@ -233,7 +233,12 @@ egh_status egh_factor(egh_ctx *ctx, int32_t *bad_freq, void *stream);
  * returns when the multipliers are on the host and reports EGH_ETIMEOUT if a
  * bounded device wait of its transforms ran out; with device buffers it returns
  * before the work completes, and such an expiry is reported by the next call
- * that waits for the device (egh_green, egh_hessian, a host-buffer deblur). */
+ * that waits for the device (egh_green, egh_hessian, a host-buffer deblur).
+ * A source's multipliers do not depend on the other sources of the call, bit
+ * for bit.  Device buffers and pageable host buffers (staged through device
+ * buffers) give the same bits; page-locked host buffers are read and written
+ * in place through their device mapping by transform kernels of their own,
+ * whose rounding differs (at the FP32 level of the transforms). */
 egh_status egh_deblur(egh_ctx *ctx, const float *resid, int32_t ns, int32_t nt_d, float *mult, void *stream);
 
 /* Threshold of the selective refinement of the mixed precisions (the paper has no counterpart:

@@ -336,6 +336,10 @@ constexpr int TP_EPI = 256;  // threads of warps 0-7
 constexpr int TP_R = EGH_TP_R;  // fp32 ring stages
 constexpr int TP_A = EGH_TP_A;  // A tiles (the converters fill one while the MMAs read another)
 constexpr int TP_B = EGH_TP_B;  // twiddle tiles in flight (loaded TP_B - 2 stages ahead)
+// The MMA thread waits for the MMAs of stage g - 2 before reusing a twiddle tile; that phase is
+// still the latest one of its mbarrier (mdone of A tile (g - 2) % TP_A) only with two or more A
+// tiles: with one, stage g - 1's MMAs may already have completed the next phase.
+static_assert(TP_A >= 2 && TP_B >= 3, "two A tiles and three twiddle tiles at least");
 constexpr unsigned TP_STAGE = TT_M * TT_K * 4;  // one fp32 ring stage
 
 size_t trace_tma_smem(int N) {
