@@ -38,8 +38,8 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM traffic (read + write bytes) per launch of the FD step and of the transform from the
 # committed ncu capture (profiles/), valid only for the kernel sources it was taken from (sha256
 # of csrc/fd.cu); None until a capture exists.
-KERNEL_TRAFFIC = {"fd_sha256": "fae7eb9a0f70e1fab3344bacd920dfa34dc94956243a42999c6363b8616c8008",
-                  "k_fd_step": 32.18e6,   # 1.65 MB read + 30.53 MB write per launch (18 rows per warp)
+KERNEL_TRAFFIC = {"fd_sha256": "8afae4dbb4943cb9c3c79b80b5e97a5bc7d87578b94ef69c01d0f0998c9a03a3",
+                  "k_fd_step": 32.13e6,   # 1.64 MB read + 30.49 MB write per launch (18 rows per warp)
                   "k_dft_tc": 48.10e9,    # 45.78 GB read + 2.33 GB write per 2048-level launch
                   "gram_sha256": "f9de315c9b531216c4542c842f967a76ddf97ec6b8c30623a20ace1b44982cd4",
                   # per launch at 231 receivers x 26 frequencies, by grid-sum splits (read + write)

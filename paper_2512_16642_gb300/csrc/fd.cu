@@ -569,7 +569,11 @@ __global__ void __launch_bounds__(128, 16)
   __shared__ unsigned tslot;
   __shared__ int fail;
   const int tid = threadIdx.x, warp = tid >> 5;
-  const unsigned ncols = N <= 32 ? 32u : N <= 64 ? 64u : 128u;
+  // N <= 64: A hi against the twiddles' hi and lo planes as one MMA of width 2N, then A lo
+  // against hi; columns [0, N) hold hi.hi + lo.hi and [N, 2N) hi.lo.  Wider N: three MMAs of
+  // width N (2N columns would not fit three CTAs' TMEM on one SM).
+  const bool two = N <= 64;
+  const unsigned ncols = N <= 32 ? 64u : N <= 64 ? 128u : 128u;
   if (warp == 0) tc::tmem_alloc(&tslot, ncols);
   const unsigned bar0 = tc::smem_u32(&bars[0]);
   auto full = [&](int i) { return bar0 + 8u * i; };
@@ -594,7 +598,7 @@ __global__ void __launch_bounds__(128, 16)
     const int r = t / npb;
     const int p0 = (t - r * npb) * TD_M;
     if (tid == 0) {
-      const unsigned idesc = tc::idesc_bf16(TD_M, N, 1, 0);
+      const unsigned idesc = tc::idesc_bf16(TD_M, N, 1, 0), idesc2 = tc::idesc_bf16(TD_M, 2 * N, 1, 0);
       // snapshots are read once: stream them through L2 as evict-first so that the FD's state
       // levels, which the concurrent FD steps re-read, stay resident
       const uint64_t pol = tc::l2_evict_first_policy();
@@ -635,8 +639,12 @@ __global__ void __launch_bounds__(128, 16)
           const uint64_t ahi = tc::sdesc_sw128_lbo_sbo(ab + ks * 2048, 8192, 1024);
           const uint64_t alo = tc::sdesc_sw128_lbo_sbo(ab + 4096 + ks * 2048, 8192, 1024);
           const uint64_t bhi = tc::sdesc_sw128(bh + ks * 32), blo = tc::sdesc_sw128(bl + ks * 32);
-          tc::mma_bf16(tmem, ahi, bhi, idesc, s > 0 || ks > 0);
-          tc::mma_bf16(tmem, ahi, blo, idesc, true);
+          if (two) {  // the lo plane is rows N .. 2N - 1 of the same K-major tile
+            tc::mma_bf16(tmem, ahi, bhi, idesc2, s > 0 || ks > 0);
+          } else {
+            tc::mma_bf16(tmem, ahi, bhi, idesc, s > 0 || ks > 0);
+            tc::mma_bf16(tmem, ahi, blo, idesc, true);
+          }
           tc::mma_bf16(tmem, alo, bhi, idesc, true);
         }
         tc::mma_commit(empty(buf));
@@ -671,6 +679,11 @@ __global__ void __launch_bounds__(128, 16)
     for (int c0 = 0; c0 < N; c0 += 8) {
       float v[8], o[8];
       tmem_ld8(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c0, v);
+      if (two) {  // the hi.lo columns, through o before o takes the old totals
+        tmem_ld8(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(N + c0), o);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] += o[i];
+      }
       // all loads of the group before any store: the 8 column planes are distinct
 #pragma unroll
       for (int i = 0; i < 8; ++i)
