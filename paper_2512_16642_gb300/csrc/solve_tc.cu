@@ -98,12 +98,13 @@ __global__ void __launch_bounds__(256, 1)
   __syncthreads();
   tc::tc_fence_after();
   const unsigned tmem = tslot;
-  // stage b: planes [A re 0,1,2][A im 0,1,2][B re 0,1,2][B im 0,1,2]
+  // stage b: planes [A re 0,1,2][A im 0,1,2][B re 0][B im 0][B re 1][B im 1][B re 2][B im 2]: a
+  // term's B re and B im planes are rows 0-63 and 64-127 of one 128-row K-major tile
   auto plane_a = [&](int b, int ri, int t) {
     return tc::smem_u32(sm + (size_t)b * CM_STAGE + (unsigned)(3 * ri + t) * CM_AP);
   };
   auto plane_b = [&](int b, int ri, int t) {
-    return tc::smem_u32(sm + (size_t)b * CM_STAGE + 6 * CM_AP + (unsigned)(3 * ri + t) * CM_BP);
+    return tc::smem_u32(sm + (size_t)b * CM_STAGE + 6 * CM_AP + (unsigned)(2 * t + ri) * CM_BP);
   };
   // this thread's pieces of a stage: A rows ra, ra + 64 (chunk ca: 8 consecutive k, 8 float2);
   // B column cb (chunk kb: 8 consecutive k, 8 float2)
@@ -182,6 +183,7 @@ __global__ void __launch_bounds__(256, 1)
       return;
     }
     tc::tc_fence_after();
+    // accumulator set: [0, N) Re A Re B, [N, 2N) Re A Im B + Im A Re B, [2N, 3N) Im A Im B
     const unsigned base = tmem + ((unsigned)(qq * 32) << 16) + (unsigned)((s & 1) * CM_ACC + hh * 32);
     float v[32];
     tc::tmem_ld32(base, v);
@@ -189,13 +191,13 @@ __global__ void __launch_bounds__(256, 1)
     for (int i = 0; i < 32; ++i) trr[i] += v[i];
     tc::tmem_ld32(base + CM_N, v);
 #pragma unroll
-    for (int i = 0; i < 32; ++i) tii[i] += v[i];
+    for (int i = 0; i < 32; ++i) tim[i] += v[i];
     tc::tmem_ld32(base + 2 * CM_N, v);
 #pragma unroll
-    for (int i = 0; i < 32; ++i) tim[i] += v[i];
+    for (int i = 0; i < 32; ++i) tii[i] += v[i];
     tc::tc_fence_before();
   };
-  const unsigned idesc = tc::idesc_bf16(CM_M, CM_N, 0, 0);
+  const unsigned idesc = tc::idesc_bf16(CM_M, CM_N, 0, 0), idesc2 = tc::idesc_bf16(CM_M, 2 * CM_N, 0, 0);
   int issued = 0;  // stages whose MMAs were issued (thread 0)
   if (nst > 0) load(0);
   for (int s = 0; s < nst; ++s) {
@@ -213,24 +215,28 @@ __global__ void __launch_bounds__(256, 1)
     if (tid == 0) {
       tc::tc_fence_after();
       const unsigned d = tmem + (unsigned)(b * CM_ACC);
-      const unsigned drr = d, dii = d + CM_N, dim = d + 2 * CM_N;
-      // term products smallest first (i + j = 2, then 1, then 0), both K steps of the stage
+      // term products smallest first (i + j = 2, then 1, then 0), both K steps of the stage.
+      // Re A x [Re B | Im B] -> columns [0, 2N) (Re Re, then Re Im into the imaginary sums);
+      // Im A x [Re B | Im B] -> columns [N, 3N) (Im Re onto the imaginary sums, Im Im).  The
+      // very first Im A product writes [2N, 3N) fresh, so it is issued as two N-wide MMAs.
       const int ti[6] = {2, 1, 0, 1, 0, 0}, tj[6] = {0, 1, 2, 0, 1, 0};
-      bool first_rr = true, first_ii = true, first_im = true;
 #pragma unroll
       for (int p = 0; p < 6; ++p) {
 #pragma unroll
         for (int ks = 0; ks < CM_K / 16; ++ks) {
           const unsigned o = 32u * ks;
+          const bool first = p == 0 && ks == 0;
           const uint64_t are = tc::sdesc_sw64(plane_a(b, 0, ti[p]) + o);
           const uint64_t aim = tc::sdesc_sw64(plane_a(b, 1, ti[p]) + o);
-          const uint64_t bre = tc::sdesc_sw64(plane_b(b, 0, tj[p]) + o);
-          const uint64_t bim = tc::sdesc_sw64(plane_b(b, 1, tj[p]) + o);
-          tc::mma_bf16(drr, are, bre, idesc, !first_rr);
-          tc::mma_bf16(dii, aim, bim, idesc, !first_ii);
-          tc::mma_bf16(dim, are, bim, idesc, !first_im);
-          tc::mma_bf16(dim, aim, bre, idesc, true);
-          first_rr = first_ii = first_im = false;
+          const uint64_t bri = tc::sdesc_sw64(plane_b(b, 0, tj[p]) + o);  // [Re B | Im B]
+          tc::mma_bf16(d, are, bri, idesc2, !first);
+          if (first) {
+            const uint64_t bim = tc::sdesc_sw64(plane_b(b, 1, tj[p]) + o);
+            tc::mma_bf16(d + CM_N, aim, bri, idesc, true);       // Im A Re B onto Re A Im B
+            tc::mma_bf16(d + 2 * CM_N, aim, bim, idesc, false);  // Im A Im B, fresh
+          } else {
+            tc::mma_bf16(d + CM_N, aim, bri, idesc2, true);
+          }
         }
       }
       tc::mma_commit(mdone(b));
