@@ -312,30 +312,25 @@ __global__ void __cluster_dims__(TD_S, 1, 1) __launch_bounds__(256)
 // trace tile is cut into H fixed parts (H = 2 from two stages on: stages [0, nst/2) and
 // [nst/2, nst)); a unit is one part of one tile, and each CTA (one per SM) takes an even share
 // of the units.  Warp 9 (one thread) streams the units' fp32 samples into a ring of TMA stages
-// (128 traces x 64 samples; rows past ntr and samples past nt_d read as zero), reloading a
-// slot as soon as it has been read; warp 8 (one thread) loads the twiddle tiles and issues the
-// bf16x3 MMAs (A hi against the twiddles' hi and lo planes as one MMA of twice the width, then
-// A lo against hi); warps 0-7 split each stage into the bf16 hi/lo A tiles and drain the TMEM
-// blocks (TT_J stages each, counted from the part's start) into FP32 register totals, which
-// they add into the zeroed spectra at the part's end.  With two parts
+// (128 traces x 64 samples as two 128-byte-swizzled boxes of 32 samples; rows past ntr and
+// samples past nt_d read as zero), reloading a slot as soon as it has been read; warp 8 (one
+// thread) loads the twiddle tiles and issues the bf16x3 MMAs (A hi against the twiddles' hi and
+// lo planes as one MMA of twice the width, then A lo against hi), with A read from tensor
+// memory; warps 0-7 (thread = trace row, warps 4-7 the second 32 samples) split each stage into
+// bf16 hi / lo, store the A tile into TMEM with tcgen05.st and drain the TMEM blocks (TT_J
+// stages each, counted from the part's start) into FP32 register totals, which they add into
+// the zeroed spectra at the part's end.  With A in TMEM, shared memory holds only the ring and
+// the twiddle tiles.  With two parts
 // the spectrum is 0 + a + b in either order, the same bits (floating-point addition commutes),
 // and the parts depend on the trace length alone: a trace's spectrum does not depend on the
 // other traces of the call.  mbarriers carry every hand-off; every wait is bounded and gives up
 // early once another role has failed.
 // ---------------------------------------------------------------------------------------------
 constexpr int TP_EPI = 256;  // threads of warps 0-7
-#ifndef EGH_TP_R
-#define EGH_TP_R 3
-#endif
-#ifndef EGH_TP_A
-#define EGH_TP_A 2
-#endif
-#ifndef EGH_TP_B
-#define EGH_TP_B 4
-#endif
-constexpr int TP_R = EGH_TP_R;  // fp32 ring stages
-constexpr int TP_A = EGH_TP_A;  // A tiles (the converters fill one while the MMAs read another)
-constexpr int TP_B = EGH_TP_B;  // twiddle tiles in flight (loaded TP_B - 2 stages ahead)
+constexpr int TP_A = 2;  // A tiles in TMEM (the converters fill one while the MMAs read another)
+constexpr int TP_B = 4;  // twiddle tiles in flight (loaded TP_B - 2 stages ahead)
+// fp32 ring stages: what shared memory holds beside the twiddle tiles
+__host__ __device__ constexpr int tp_ring(int N) { return N <= 32 ? 6 : 5; }
 // The MMA thread waits for the MMAs of stage g - 2 before reusing a twiddle tile; that phase is
 // still the latest one of its mbarrier (mdone of A tile (g - 2) % TP_A) only with two or more A
 // tiles: with one, stage g - 1's MMAs may already have completed the next phase.
@@ -343,8 +338,8 @@ static_assert(TP_A >= 2 && TP_B >= 3, "two A tiles and three twiddle tiles at le
 constexpr unsigned TP_STAGE = TT_M * TT_K * 4;  // one fp32 ring stage
 
 size_t trace_tma_smem(int N) {
-  // ring, A tiles (hi + lo), twiddle tiles (hi + lo), alignment slack
-  return 1024 + (size_t)TP_R * TP_STAGE + TP_A * 2 * (size_t)TT_A + TP_B * 2 * (size_t)N * 128;
+  // ring, twiddle tiles (hi + lo), alignment slack
+  return 1024 + (size_t)tp_ring(N) * TP_STAGE + TP_B * 2 * (size_t)N * 128;
 }
 
 // the stages of unit u (part u % H of tile u / H)
@@ -365,7 +360,7 @@ __global__ void __launch_bounds__(TP_EPI + 64, 1)
     k_trace_tma(const __grid_constant__ CUtensorMap tm_in, int ntr, int nt_d,
                 const unsigned char* __restrict__ twt, int nf, int nrec, int ld, int s0, int H,
                 float2* __restrict__ Dh, int* __restrict__ err, int expire) {
-  constexpr int R = TP_R;
+  constexpr int R = tp_ring(N);
   constexpr unsigned BT = 2u * N * 128u;  // one twiddle tile (hi + lo)
   constexpr int NH = N / 2;
   extern __shared__ __align__(1024) unsigned char tp_dsm[];
@@ -391,8 +386,10 @@ __global__ void __launch_bounds__(TP_EPI + 64, 1)
   auto blkd = [&](int i) { return bar0 + 8u * (2 * R + NB + 2 * NA + i); };
   auto tempty = [&](int i) { return bar0 + 8u * (2 * R + NB + 2 * NA + 2 + i); };
   const unsigned never = bar0 + 8u * (2 * R + NB + 2 * NA + 4);
-  // TMEM: two block buffers of 2N columns: [0, N) hi.hi + lo.hi, [N, 2N) hi.lo
-  if (warp == 0) tc::tmem_alloc(&tslot, 4 * N);
+  // TMEM: two block buffers of 2N columns ([0, N) hi.hi + lo.hi, [N, 2N) hi.lo), then the A tiles
+  // at column ACOL: per tile 32 columns of hi (64 samples, two bf16 each) and 32 of lo
+  constexpr unsigned ACOL = 4 * N, TCOLS = 4 * N + 64 * TP_A <= 256 ? 256 : 512;
+  if (warp == 0) tc::tmem_alloc(&tslot, TCOLS);
   if (tid == 0) {
     for (int i = 0; i < R; ++i) {
       tc::mbar_init(rfull(i), 1);
@@ -416,8 +413,7 @@ __global__ void __launch_bounds__(TP_EPI + 64, 1)
   tc::tc_fence_after();
   const unsigned tmem = tslot;
   const unsigned ring0 = tc::smem_u32(sm);
-  const unsigned abuf0 = ring0 + R * TP_STAGE;  // A tiles: hi plane, then lo plane
-  const unsigned bbuf0 = abuf0 + NA * 2 * TT_A;
+  const unsigned bbuf0 = ring0 + R * TP_STAGE;
   // stages of this CTA in order: unit i, stage s of the unit
   struct Cur {
     int i, s;
@@ -483,15 +479,13 @@ __global__ void __launch_bounds__(TP_EPI + 64, 1)
         }
         tc::tc_fence_after();
         const unsigned dt = tmem + (unsigned)((b & 1) * 2 * N);
-        const unsigned ah = abuf0 + (g % NA) * 2 * TT_A, al = ah + TT_A;
+        const unsigned ah = tmem + ACOL + (unsigned)((g % NA) * 64), al = ah + 32;
         const unsigned bh = bbuf0 + (g % NB) * BT;
 #pragma unroll
         for (int ks = 0; ks < TT_K / 16; ++ks) {
-          const unsigned o = 32u * ks;
-          const uint64_t dah = tc::sdesc_sw128(ah + o), dal = tc::sdesc_sw128(al + o);
-          const uint64_t dbh = tc::sdesc_sw128(bh + o);
-          tc::mma_bf16(dt, dah, dbh, idesc2, !(first && ks == 0));
-          tc::mma_bf16(dt, dal, dbh, idesc, true);
+          const uint64_t dbh = tc::sdesc_sw128(bh + 32u * ks);
+          tc::mma_bf16_ta(dt, ah + 8u * ks, dbh, idesc2, !(first && ks == 0));
+          tc::mma_bf16_ta(dt, al + 8u * ks, dbh, idesc, true);
         }
         tc::mma_commit(mdone(g));
         issued_m = g + 1;
@@ -522,8 +516,10 @@ __global__ void __launch_bounds__(TP_EPI + 64, 1)
           break;
         }
         tc::mbar_expect_tx(rfull(slot), TP_STAGE);
-        tc::tma_load_2d(ring0 + slot * TP_STAGE, &tm_in, (lc.t.sb + lc.s) * TT_K, lc.t.tile * TT_M,
-                        rfull(slot));
+        // two boxes of 128 traces x 32 samples (128-byte rows, 128-byte swizzle)
+        for (int h = 0; h < 2; ++h)
+          tc::tma_load_2d(ring0 + slot * TP_STAGE + h * (TP_STAGE / 2), &tm_in,
+                          (lc.t.sb + lc.s) * TT_K + 32 * h, lc.t.tile * TT_M, rfull(slot));
         cur_next(lc);
       }
       if (!ok) *fail = 1;
@@ -537,44 +533,40 @@ __global__ void __launch_bounds__(TP_EPI + 64, 1)
     float tot[NH];
 #pragma unroll
     for (int c = 0; c < NH; ++c) tot[c] = 0.f;
+    // thread: trace row `row` of the tile, samples 32 hh .. 32 hh + 31 of each stage (box hh)
     auto convert = [&](int g) -> bool {
       const int slot = g % R;
       if (!tc::mbar_wait_or(rfull(slot), (g / R) & 1, fail)) return false;
-      const unsigned rs = ring0 + slot * TP_STAGE;
+      const unsigned rs = ring0 + slot * TP_STAGE + hh * (TP_STAGE / 2) + row * 128;
       float4 v[8];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int e = i * TP_EPI + tid;  // row e / 16, float4 e % 16 of the stage
+      for (int c = 0; c < 8; ++c)  // 16-byte chunk c of the row sits at c ^ (row % 8)
         asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
-                     : "=f"(v[i].x), "=f"(v[i].y), "=f"(v[i].z), "=f"(v[i].w)
-                     : "r"(rs + 16u * e));
-      }
+                     : "=f"(v[c].x), "=f"(v[c].y), "=f"(v[c].z), "=f"(v[c].w)
+                     : "r"(rs + (unsigned)((c ^ (row & 7)) << 4)));
       tc::mbar_arrive(rempty(slot));
       // split into bf16 hi / lo while the MMAs of stage g - NA may still read the A tile
-      unsigned hl[8][4];
+      unsigned hi[16], lo[16];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const __nv_bfloat162 h01 = __floats2bfloat162_rn(v[i].x, v[i].y);
-        const __nv_bfloat162 h23 = __floats2bfloat162_rn(v[i].z, v[i].w);
+      for (int c = 0; c < 8; ++c) {
+        const __nv_bfloat162 h01 = __floats2bfloat162_rn(v[c].x, v[c].y);
+        const __nv_bfloat162 h23 = __floats2bfloat162_rn(v[c].z, v[c].w);
         const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
-        const __nv_bfloat162 l01 = __floats2bfloat162_rn(v[i].x - f01.x, v[i].y - f01.y);
-        const __nv_bfloat162 l23 = __floats2bfloat162_rn(v[i].z - f23.x, v[i].w - f23.y);
-        hl[i][0] = *reinterpret_cast<const unsigned*>(&h01);
-        hl[i][1] = *reinterpret_cast<const unsigned*>(&h23);
-        hl[i][2] = *reinterpret_cast<const unsigned*>(&l01);
-        hl[i][3] = *reinterpret_cast<const unsigned*>(&l23);
+        const __nv_bfloat162 l01 = __floats2bfloat162_rn(v[c].x - f01.x, v[c].y - f01.y);
+        const __nv_bfloat162 l23 = __floats2bfloat162_rn(v[c].z - f23.x, v[c].w - f23.y);
+        hi[2 * c] = *reinterpret_cast<const unsigned*>(&h01);
+        hi[2 * c + 1] = *reinterpret_cast<const unsigned*>(&h23);
+        lo[2 * c] = *reinterpret_cast<const unsigned*>(&l01);
+        lo[2 * c + 1] = *reinterpret_cast<const unsigned*>(&l23);
       }
-      if (g >= NA && !tc::mbar_wait_or(mdone(g), (g / NA - 1) & 1, fail)) return false;
-      const unsigned ah = abuf0 + (g % NA) * 2 * TT_A;
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int e = i * TP_EPI + tid, m = e >> 4, c4 = e & 15;
-        const unsigned off = (unsigned)((m >> 3) * 1024 + (m & 7) * 128 +
-                                        ((((c4 >> 1) ^ (m & 7))) << 4) + ((c4 & 1) << 3));
-        st_shared_v2(ah + off, hl[i][0], hl[i][1]);
-        st_shared_v2(ah + TT_A + off, hl[i][2], hl[i][3]);
-      }
-      tc::fence_proxy_async();
+      const bool freed = g < NA || tc::mbar_wait_or(mdone(g), (g / NA - 1) & 1, fail);
+      if (!__all_sync(0xffffffffu, freed)) return false;  // the TMEM stores are warp-wide
+      tc::tc_fence_after();
+      const unsigned at = tmem + ((unsigned)(qq * 32) << 16) + ACOL + (unsigned)((g % NA) * 64 + 16 * hh);
+      tc::tmem_st16(at, hi);
+      tc::tmem_st16(at + 32, lo);
+      tc::tmem_st_wait();
+      tc::tc_fence_before();
       tc::mbar_arrive(afull(g));
       return true;
     };
@@ -651,7 +643,7 @@ __global__ void __launch_bounds__(TP_EPI + 64, 1)
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
-  if (warp == 0) tc::tmem_dealloc(tmem, 4 * N);
+  if (warp == 0) tc::tmem_dealloc(tmem, TCOLS);
 }
 
 cudaError_t launch_trace_dft_tc(const float* resid, int ntr, int nt_d, const unsigned char* twt,
@@ -701,7 +693,7 @@ cudaError_t launch_trace_tma(const float* resid, int ntr, int nt_d, const unsign
                              (size_t)(ntr / nrec) * sizeof(float2), (size_t)nf * nrec, st)))
     return e;
   CUtensorMap tm;
-  if ((e = make_f32_tmap(&tm, resid, ntr, nt_d, TT_K, TT_M, false))) return e;
+  if ((e = make_f32_tmap(&tm, resid, ntr, nt_d, 32, TT_M, true))) return e;
   const int grid = (int)std::min<long long>((long long)ntile * H, sms);
   count_launches(1);
   kern<<<grid, TP_EPI + 64, smem, st>>>(tm, ntr, nt_d, twt, nf, nrec, ld, s0, H, Dh, err, expire);

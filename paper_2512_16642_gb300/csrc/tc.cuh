@@ -172,6 +172,32 @@ __device__ __forceinline__ void mma_bf16(unsigned dtmem, uint64_t adesc, uint64_
       : "memory");
 }
 
+// MMA with the A operand in tensor memory (rows in lanes 0..M-1, two bf16 per 32-bit column along
+// K, the layout tcgen05.st.32x32b writes: a thread's registers go to consecutive columns of its
+// lane) and B in shared memory
+__device__ __forceinline__ void mma_bf16_ta(unsigned dtmem, unsigned atmem, uint64_t bdesc,
+                                            unsigned idesc, bool accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(dtmem),
+      "r"(atmem), "l"(bdesc), "r"(idesc), "r"((int)accumulate)
+      : "memory");
+}
+
+// 16 consecutive columns of this warp's 32 TMEM lanes from 16 registers of each thread (one lane
+// per thread), then the wait for the stores
+__device__ __forceinline__ void tmem_st16(unsigned taddr, const unsigned (&r)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15,%16};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+      "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
 // L2 policy for data read once (streamed through L2 without displacing resident working sets)
 __device__ __forceinline__ uint64_t l2_evict_first_policy() {
   uint64_t p;
