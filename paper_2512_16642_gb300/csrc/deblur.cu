@@ -1,13 +1,16 @@
 // Deblurring of residual gathers against the factored Hessians (eq. Qsystem solved per frequency,
 // Section "Frequency domain inversion"):
-//   D[k][r][s] = sum_t resid[s][r][t] exp(-i w_k t dt)           (k_trace_dft_tc)
+//   D[k][r][s] = sum_t resid[s][r][t] exp(-i w_k t dt)           (k_trace_tma on device buffers,
+//                                                                  k_trace_dft_tc otherwise)
 //   X_k = L_k^{-H} L_k^{-1} D_k                                   (k_trsm, all sources as RHS)
 //   mixed precision: X_k = Q_k^{-1} D_k with Q_k^{-1} = W_k^H W_k, W_k = L_k^{-1} (k_trtri and
 //                    k_cgemm once per factorisation; the product on the tensor cores in
 //                    solve_tc.cu), then at ill-conditioned frequencies
 //                    X_k += Q_k^{-1} (D_k - Q_k X_k)                (k_resid_dot2 or k_resid64)
-//   mult[s][r][t] = sum_k w_k Re(X_k[r][s] exp(+i w_k t dt))      (k_synth_tc; k_synth without
-//                                                                  the twiddle tiles)
+//   mult[s][r][t] = sum_k w_k Re(X_k[r][s] exp(+i w_k t dt))      (k_synth_operands + k_synth_tma
+//                                                                  on device buffers, k_synth_tc
+//                                                                  otherwise; k_synth without the
+//                                                                  twiddle tiles)
 // Traces are indexed q = s * nrec + r (the [ns][nrec][nt] gather layout); the spectra of one call
 // occupy columns s0 .. s0 + ns - 1 of a [nf][nrec][ld] array, so that several gathers (of
 // different lengths) can share one solve.
