@@ -7,8 +7,10 @@
 // terms, x = x0 + x1 + x2 (x0 = bf16(x), x1 = bf16(x - x0), x2 = bf16(x - x0 - x1); 24 bits of
 // the significand), and each real product sum_k a b keeps the six term products down to 2^-16
 // relative (x2 y0, x1 y1, x0 y2, x1 y0, x0 y1, x0 y0; the dropped ones are 2^-24).  The complex
-// product accumulates three real ones, Re A Re B, Im A Im B and (Re A Im B + Im A Re B), into three
-// TMEM accumulators.  The tensor core's FP32 accumulation is not rounded to nearest (the Gram's
+// product accumulates three real ones, Re A Re B, Re A Im B + Im A Re B and Im A Im B, into three
+// adjacent TMEM accumulators: a term's B re and B im planes form one 128-row operand, so Re A x
+// [Re B | Im B] and Im A x [Re B | Im B] are two MMAs of width 128, the second offset by one
+// accumulator.  The tensor core's FP32 accumulation is not rounded to nearest (the Gram's
 // accumulators drifted by about 2^-24 per accumulation), so (1) within a stage the small term
 // products are accumulated first and the large x0 y0 ones last, which keeps the drift near one ulp
 // of the stage's sum per large accumulation, and (2) each stage's sums leave TMEM for FP32 register
